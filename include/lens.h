@@ -1,0 +1,255 @@
+/*
+ * lens.h -- C ABI of liblens, a GB300 (sm_103a) implementation of the ray-
+ * shooting deflection solver of Metcalf & Petkova, "GLAMER Part I: A Code for
+ * Gravitational Lensing Simulations with Adaptive Mesh Refinement"
+ * (arXiv:1312.1128).
+ *
+ * For every ray position x on the lens plane the library returns the
+ * deflection alpha (2 components), the convergence kappa and the shear
+ * gamma1, gamma2 (Sec. 3.2, Eqs. alpha, kappa, gamma_1, gamma_2) produced by
+ * point masses (Sec. 3.5), truncated-Gaussian smoothed particles (Sec. 3.1,
+ * Eq. smoothing) and analytic halos (Sec. 3.2), using the paper's tree
+ * algorithm (Sec. 3.2: equal-area quadtree, monopole + quadrupole cells,
+ * r_cut = r_cm / theta_force (Eq. r_cut), the 2D multipole acceptability
+ * criterion, big-particle lists) or, with LENS_DIRECT, the direct sum that
+ * the tree converges to at theta_force = 0 (Sec. 5.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Units: masses are given in "m-units", m = M / (pi Sigma_crit) (Sec. 2,
+ *   Sec. 3.5), so that a point mass deflects by alpha = m x / |x|^2.  The lens
+ *   equation is y = x - alpha(x) (Sec. 2, Eq. lens_eq).
+ * - Shear follows Eqs. gamma_1, gamma_2: gamma1 = (d1 alpha1 - d2 alpha2)/2,
+ *   gamma2 = d1 alpha2; the magnification matrix is
+ *   [[1-kappa-gamma1, -gamma2], [-gamma2, 1-kappa+gamma1]] (App. A).
+ * - Pointers named "device" are CUDA device (or managed) memory owned by the
+ *   caller; "host" pointers are ordinary host memory.  The library never
+ *   frees caller memory.  A lens_tree owns its internal device buffers until
+ *   lens_free_tree.
+ * - Every call is asynchronous on the CUDA stream it is given (NULL = the
+ *   legacy default stream), except where a call says it synchronises.  The
+ *   returned status reports argument, allocation and launch errors at once;
+ *   errors detected inside kernels are latched in the tree and reported by
+ *   lens_sync_status (and by the next lens_* call on that tree that
+ *   synchronises).  Kernels never trap, assert or spin without a bound.
+ * - n == 0 rays is a valid no-op.  NaN inputs propagate to the outputs.
+ * - One lens_tree must not be used by two calls concurrently (its scratch
+ *   buffers are shared); distinct trees are independent.
+ * - On failure, lens_last_error() returns a message for the calling thread.
+ */
+#ifndef LENS_H
+#define LENS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LENS_API_VERSION 1
+
+typedef enum lens_status {
+    LENS_OK = 0,
+    LENS_ERR_INVALID_ARG = 1,   /* bad pointer, size, kind, dtype or parameter */
+    LENS_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    LENS_ERR_OOM = 3,           /* device allocation failed */
+    LENS_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
+    LENS_ERR_INTERNAL = 5,      /* a device-side consistency check failed */
+    LENS_ERR_UNSUPPORTED = 6    /* valid request this build does not implement */
+} lens_status;
+
+/* Lens component kinds. */
+enum {
+    LENS_POINT = 0,  /* point mass: alpha = m r_hat / r (Sec. 3.5)                        */
+    LENS_GAUSS = 1,  /* truncated 2D Gaussian of width r_sm, cut at q r_sm (Sec. 3.1)      */
+    LENS_NFW = 2,    /* projected NFW, scale radius r_s, truncated in 2D at R_max; a point  *
+                      * mass outside R_max (Sec. 3.2 "analytic models")                    */
+    LENS_SIS = 3,    /* singular isothermal sphere, Einstein radius r_E (App. B)           */
+    LENS_DISK = 4    /* uniform disk of radius R; m < 0 subtracts a mass sheet (Sec. 3.5)   */
+};
+
+/* Element types of caller arrays. */
+enum { LENS_F32 = 0, LENS_F64 = 1 };
+
+/* Arithmetic precision of a tree (fixed at build time). */
+enum {
+    LENS_PREC_FP32 = 0,  /* FP32 interactions, compensated accumulation; FP32 outputs */
+    LENS_PREC_FP64 = 1   /* FP64 throughout; FP64 outputs                             */
+};
+
+/* Flags for the shooting calls. */
+enum {
+    LENS_ALPHA_ONLY = 1,  /* compute alpha only; kappa/gamma pointers may be NULL (Sec. 3.2) */
+    LENS_DIRECT = 2,      /* direct sum over every particle instead of the tree walk        */
+    LENS_ACCUMULATE = 4,  /* add to the output arrays instead of overwriting them           */
+    LENS_USE_GRAPH = 8    /* lens_shoot_batches: replay a cached CUDA graph of the launch    */
+};
+
+/* One particle species: a homogeneous set of particles of one kind (Sec. 3.1
+ * treats each species separately).  data is DEVICE memory, n x 4 elements of
+ * type dtype, row-major {x, y, m, p}:
+ *   LENS_POINT: p unused;                        shape unused
+ *   LENS_GAUSS: p = r_sm (> 0);                  shape = q (> 0), support q r_sm
+ *   LENS_NFW:   p = r_s (> 0);                   shape = R_max / r_s (> 0)
+ * Masses must be finite and >= 0 (the tree's centre-of-mass bounds rely on it). */
+typedef struct lens_species {
+    int32_t kind;
+    int32_t dtype;
+    int64_t n;
+    const void* data;
+    double shape;
+} lens_species;
+
+/* An analytic component evaluated directly for every ray (host memory).
+ *   LENS_POINT: m;  LENS_GAUSS: m, p0 = r_sm, p1 = q;  LENS_NFW: m, p0 = r_s,
+ *   p1 = R_max;  LENS_SIS: p0 = r_E (m unused);  LENS_DISK: m, p0 = R. */
+typedef struct lens_halo {
+    int32_t kind;
+    int32_t reserved;
+    double x, y, m, p0, p1;
+} lens_halo;
+
+typedef struct lens_params {
+    double theta;        /* opening angle theta_force of Eq. r_cut (>= 0; 0 = never accept a cell) */
+    int32_t leaf_max;    /* a box holding fewer than leaf_max particles is a leaf (>= 1; paper: 5)  */
+    int32_t precision;   /* LENS_PREC_FP32 or LENS_PREC_FP64                                          */
+    int32_t group_rays;  /* rays sharing one interaction list: 0 = autotuned/default, else 32 or 64   */
+    int32_t reserved;    /* must be 0 */
+} lens_params;
+
+typedef struct lens_tree lens_tree;  /* opaque, library-owned */
+
+/* Summary of a built tree, for inspection and tests. */
+typedef struct lens_tree_info {
+    int32_t n_species;
+    int32_t precision;
+    int64_t n_halos;
+    int64_t n_particles[8];   /* per species (first 8 species) */
+    int64_t n_nodes[8];
+    int64_t n_leaves[8];
+    int64_t n_big[8];         /* big-list entries (Sec. 3.2) */
+    int32_t depth[8];         /* deepest level (root = 0) */
+    double root[8][3];        /* root box centre x, y and half side */
+} lens_tree_info;
+
+/*
+ * lens_build_tree -- build the quadtree of every species (Sec. 3.2: equal-
+ * area quadtree; per box the monopole and quadrupole moments, r_cut of
+ * Eq. r_cut and the list of particles whose size exceeds half the box side
+ * and that no ancestor lists).
+ *   species, n_species: host array of n_species (0..8) descriptors; each
+ *       data pointer is device memory, read during the call only.
+ *   halos, n_halos: host array of analytic components evaluated for every
+ *       ray (may be NULL when n_halos == 0); copied.
+ *   params: host pointer; theta >= 0, leaf_max >= 1.
+ *   stream: cudaStream_t to build on (NULL = default stream).
+ *   out: receives the new tree on LENS_OK, NULL otherwise.
+ * The call synchronises on `stream` once to size the node arrays.
+ * Errors: LENS_ERR_INVALID_ARG for NULL pointers, negative sizes, unknown
+ * kinds or dtypes, theta < 0, leaf_max < 1 or a negative / non-finite mass or
+ * size found on the device; LENS_ERR_OOM; LENS_ERR_CUDA.
+ */
+lens_status lens_build_tree(const lens_species* species, int32_t n_species,
+                            const lens_halo* halos, int64_t n_halos,
+                            const lens_params* params, void* stream, lens_tree** out);
+
+/*
+ * lens_shoot_rays -- evaluate alpha, kappa, gamma at n rays (Sec. 3.2 tree
+ * walk; Sec. 3.3 ray-parallel evaluation).
+ *   origin_x, origin_y: FP64 origin added to every ray offset.
+ *   ray_dx, ray_dy: DEVICE arrays of n offsets of type ray_dtype; ray i sits
+ *       at (origin_x + ray_dx[i], origin_y + ray_dy[i]), formed in FP64, so a
+ *       microlensing patch keeps its resolution far from the coordinate zero.
+ *   alpha1 .. gamma2: DEVICE output arrays of n elements, float for an FP32
+ *       tree, double for an FP64 tree.  kappa, gamma1, gamma2 may be NULL
+ *       only with LENS_ALPHA_ONLY.
+ *   flags: LENS_ALPHA_ONLY, LENS_DIRECT, LENS_ACCUMULATE.
+ * Scratch buffers grow on demand (cudaMalloc, outside any graph capture).
+ */
+lens_status lens_shoot_rays(lens_tree* tree, double origin_x, double origin_y,
+                            const void* ray_dx, const void* ray_dy, int32_t ray_dtype, int64_t n,
+                            void* alpha1, void* alpha2, void* kappa, void* gamma1, void* gamma2,
+                            int32_t flags, void* stream);
+
+/*
+ * lens_shoot_batches -- evaluate many ray batches of uneven size in one
+ * persistent launch (the refinement batches of Sec. 4 / Sec. 3.3, "bigger
+ * chunks are more efficient").
+ *   n_batches: number of batches (>= 0).
+ *   offsets: HOST array of n_batches + 1 non-decreasing int64 with
+ *       offsets[0] = 0; batch b owns rays [offsets[b], offsets[b+1]).
+ *   origins: HOST array n_batches x 2 of FP64 batch origins.
+ *   ray_dx, ray_dy, outputs, flags: as lens_shoot_rays, over all
+ *       offsets[n_batches] rays.  LENS_USE_GRAPH captures the launch sequence
+ *       into a CUDA graph on first use for this (sizes, pointers, flags) key
+ *       and replays it afterwards; call lens_reserve first when the stream is
+ *       being captured by the caller.
+ */
+lens_status lens_shoot_batches(lens_tree* tree, int64_t n_batches, const int64_t* offsets,
+                               const double* origins, const void* ray_dx, const void* ray_dy,
+                               int32_t ray_dtype, void* alpha1, void* alpha2, void* kappa,
+                               void* gamma1, void* gamma2, int32_t flags, void* stream);
+
+/*
+ * lens_shoot_rays_backward -- vector-Jacobian product of lens_shoot_rays:
+ * given dL/d(outputs) at n rays, accumulates dL/d(particle mass, x, y) and
+ * dL/d(halo parameters).  No counterpart in the paper: it differentiates the
+ * tree approximation the forward computes (cells' monopole and quadrupole
+ * moments as functions of their particles), for lens-model fitting.
+ *   ray arguments: exactly those of the forward call.
+ *   g_alpha1, g_alpha2: DEVICE arrays of n gradients (output dtype); g_kappa,
+ *       g_gamma1, g_gamma2 must be NULL in this version (LENS_ERR_UNSUPPORTED
+ *       otherwise).
+ *   g_species: HOST array of n_species DEVICE pointers (NULL entries skip a
+ *       species); each receives n x 3 {dL/dm, dL/dx, dL/dy} in the tree's
+ *       precision, ADDED to its contents.
+ *   g_halos: DEVICE array n_halos x 3 doubles {dL/dm (dL/dr_E for SIS),
+ *       dL/dx, dL/dy}, added to, or NULL.
+ *   flags: LENS_DIRECT differentiates the direct sum instead of the tree.
+ */
+lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double origin_y,
+                                     const void* ray_dx, const void* ray_dy, int32_t ray_dtype,
+                                     int64_t n, const void* g_alpha1, const void* g_alpha2,
+                                     const void* g_kappa, const void* g_gamma1,
+                                     const void* g_gamma2, void* const* g_species,
+                                     void* g_halos, int32_t flags, void* stream);
+
+/* lens_reserve -- grow the tree's scratch for up to max_rays rays in up to
+ * max_batches batches, so that later calls of that size allocate nothing. */
+lens_status lens_reserve(lens_tree* tree, int64_t max_rays, int64_t max_batches);
+
+/* lens_sync_status -- synchronise `stream` and report (then clear) any error
+ * latched by a kernel of this tree. */
+lens_status lens_sync_status(lens_tree* tree, void* stream);
+
+/* lens_tree_get_info -- fill *info (host).  Synchronous, cheap. */
+lens_status lens_tree_get_info(const lens_tree* tree, lens_tree_info* info);
+
+/*
+ * lens_tree_export -- copy species s's tree to HOST arrays for inspection
+ * (any pointer may be NULL to skip it).  Node order is breadth first.
+ *   nodes: n_nodes x 8 floats (FP32 tree) or doubles (FP64 tree):
+ *          {x_cm, y_cm, M, r_cut^2, Re Q2, Im Q2, side, level}
+ *   links: n_nodes x 4 int32 {first child or first particle, count,
+ *          is_leaf, big-list count}
+ *   perm:  n particle indices in tree order (sorted index -> input index)
+ *   listed: n int32, 1 where the particle (input order) sits in a big list
+ * Synchronous.
+ */
+lens_status lens_tree_export(const lens_tree* tree, int32_t s, void* nodes, int32_t* links,
+                             int32_t* perm, int32_t* listed);
+
+/* lens_fp32_peak -- time a dependent-FFMA microbenchmark on every SM of the
+ * current device for about `iters` FMAs per thread and return the achieved
+ * FP32 rate in FLOP/s (FFMA = 2 flops) in *flops.  Synchronous. */
+lens_status lens_fp32_peak(int64_t iters, double* flops, void* stream);
+
+void lens_free_tree(lens_tree* tree);
+const char* lens_status_string(lens_status s);
+const char* lens_last_error(void);
+int32_t lens_api_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LENS_H */
