@@ -82,7 +82,9 @@ enum {
     LENS_ALPHA_ONLY = 1,  /* compute alpha only; kappa/gamma pointers may be NULL (Sec. 3.2) */
     LENS_DIRECT = 2,      /* direct sum over every particle instead of the tree walk        */
     LENS_ACCUMULATE = 4,  /* add to the output arrays instead of overwriting them           */
-    LENS_USE_GRAPH = 8    /* lens_shoot_batches: replay a cached CUDA graph of the launch    */
+    LENS_USE_GRAPH = 8,   /* lens_shoot_batches: replay a cached CUDA graph of the launch    */
+    LENS_COUNT = 16,      /* accumulate walk interaction counters (lens_tree_counters)     */
+    LENS_TIMING = 32      /* time the grouping and walk kernels (lens_last_timing)          */
 };
 
 /* One particle species: a homogeneous set of particles of one kind (Sec. 3.1
@@ -239,10 +241,36 @@ lens_status lens_tree_get_info(const lens_tree* tree, lens_tree_info* info);
 lens_status lens_tree_export(const lens_tree* tree, int32_t s, void* nodes, int32_t* links,
                              int32_t* perm, int32_t* listed);
 
+/*
+ * lens_tree_counters -- copy (and, if reset != 0, clear) the walk counters
+ * accumulated by shooting calls made with LENS_COUNT.  Synchronous.
+ *   out: HOST array of 8 int64:
+ *     [0] ray groups walked        [1] boxes visited (MAC evaluated)
+ *     [2] cells accepted           [3] leaf particles evaluated
+ *     [4] big-list entries scanned [5] big-list entries kept for a group
+ *     [6] ray-interactions evaluated: sum over groups of rays x (cells +
+ *         leaf particles + kept big entries)   [7] reserved (0)
+ * Counts are per species launch and summed over species.
+ */
+lens_status lens_tree_counters(lens_tree* tree, int64_t* out, int32_t reset);
+
+/*
+ * lens_last_timing -- device time of the last shooting call made with
+ * LENS_TIMING, measured with CUDA events on its stream: grouping (ray sort
+ * and group set-up) and walk (all species' walk or direct-sum kernels).
+ * Synchronises on those events.  Both are 0 if no timed call was made.
+ */
+lens_status lens_last_timing(lens_tree* tree, double* group_ms, double* walk_ms);
+
 /* lens_fp32_peak -- time a dependent-FFMA microbenchmark on every SM of the
  * current device for about `iters` FMAs per thread and return the achieved
  * FP32 rate in FLOP/s (FFMA = 2 flops) in *flops.  Synchronous. */
 lens_status lens_fp32_peak(int64_t iters, double* flops, void* stream);
+
+/* lens_kernel_launches -- number of CUDA kernels this library has launched
+ * in the process so far (all trees, all threads); a graph replay counts the
+ * kernels it contains once per replay only when they are enqueued eagerly. */
+int64_t lens_kernel_launches(void);
 
 void lens_free_tree(lens_tree* tree);
 const char* lens_status_string(lens_status s);

@@ -1,0 +1,342 @@
+"""GB300 ray shooting for gravitational lensing (GLAMER Part I, arXiv:1312.1128).
+
+Thin Python binding over liblens (include/lens.h): it marshals PyTorch CUDA
+tensors into the C ABI and back, nothing more -- every step of the path runs
+in the library's CUDA kernels.  There is no CPU fallback: if liblens.so is
+missing or CUDA is unavailable, the calls raise.
+
+    lens = Lens(species=[Species.gauss(parts, q=3.0)], halos=[Halo.sis(0, 0, 0.5)],
+                theta=0.3)
+    a1, a2, kappa, g1, g2 = lens.shoot(rx, ry)              # device tensors
+    alpha, kappa, gamma = shoot(lens, rx, ry, masses=...)  # differentiable
+
+Ray positions are an FP64 origin plus offsets (float32 or float64 tensors), so
+microlensing-scale patches keep their resolution (the paper stores alpha in
+higher precision than kappa/gamma for the same reason, Sec. 3.4).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = ["Lens", "Species", "Halo", "LensError", "shoot", "lib", "fp32_peak",
+           "POINT", "GAUSS", "NFW", "SIS", "DISK", "ALPHA_ONLY", "DIRECT", "ACCUMULATE", "USE_GRAPH",
+           "COUNT", "TIMING"]
+
+POINT, GAUSS, NFW, SIS, DISK = 0, 1, 2, 3, 4
+F32, F64 = 0, 1
+PREC_FP32, PREC_FP64 = 0, 1
+ALPHA_ONLY, DIRECT, ACCUMULATE, USE_GRAPH, COUNT, TIMING = 1, 2, 4, 8, 16, 32
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "liblens.so")
+_lib = None
+
+
+class LensError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"liblens status {status}: {msg}")
+        self.status = status
+
+
+class _Species(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("data", ctypes.c_void_p), ("shape", ctypes.c_double)]
+
+
+class _Halo(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("x", ctypes.c_double),
+                ("y", ctypes.c_double), ("m", ctypes.c_double), ("p0", ctypes.c_double),
+                ("p1", ctypes.c_double)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("leaf_max", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("group_rays", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("n_halos", ctypes.c_int64), ("n_particles", ctypes.c_int64 * 8),
+                ("n_nodes", ctypes.c_int64 * 8), ("n_leaves", ctypes.c_int64 * 8),
+                ("n_big", ctypes.c_int64 * 8), ("depth", ctypes.c_int32 * 8),
+                ("root", (ctypes.c_double * 3) * 8)]
+
+
+def lib():
+    """Load liblens.so (built by __graft_entry__.build() or _build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"liblens.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.lens_build_tree.argtypes = [ctypes.POINTER(_Species), i32, ctypes.POINTER(_Halo), i64,
+                                  ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]
+    L.lens_shoot_rays.argtypes = [vp, d, d, vp, vp, i32, i64, vp, vp, vp, vp, vp, i32, vp]
+    L.lens_shoot_batches.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_double), vp, vp, i32, vp, vp, vp, vp,
+                                     vp, i32, vp]
+    L.lens_shoot_rays_backward.argtypes = [vp, d, d, vp, vp, i32, i64, vp, vp, vp, vp, vp,
+                                           ctypes.POINTER(vp), vp, i32, vp]
+    L.lens_reserve.argtypes = [vp, i64, i64]
+    L.lens_sync_status.argtypes = [vp, vp]
+    L.lens_tree_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+    L.lens_tree_export.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.lens_fp32_peak.argtypes = [i64, ctypes.POINTER(ctypes.c_double), vp]
+    L.lens_tree_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), i32]
+    L.lens_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.lens_kernel_launches.argtypes = []
+    L.lens_kernel_launches.restype = ctypes.c_int64
+    L.lens_free_tree.argtypes = [vp]
+    L.lens_free_tree.restype = None
+    L.lens_status_string.restype = ctypes.c_char_p
+    L.lens_last_error.restype = ctypes.c_char_p
+    for name in ["lens_build_tree", "lens_shoot_rays", "lens_shoot_batches",
+                 "lens_shoot_rays_backward", "lens_reserve", "lens_sync_status",
+                 "lens_tree_get_info", "lens_tree_export", "lens_fp32_peak", "lens_api_version",
+                 "lens_tree_counters", "lens_last_timing"]:
+        getattr(L, name).restype = ctypes.c_int32
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise LensError(status, lib().lens_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("liblens takes CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("liblens takes contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Species:
+    """A homogeneous particle set: data is an (n, 4) CUDA tensor {x, y, m, p}."""
+    kind: int
+    data: object
+    shape: float = 0.0
+
+    @staticmethod
+    def points(data):
+        return Species(POINT, data, 0.0)
+
+    @staticmethod
+    def gauss(data, q: float = 3.0):
+        return Species(GAUSS, data, float(q))
+
+    @staticmethod
+    def nfw(data, conc: float):
+        return Species(NFW, data, float(conc))
+
+
+@dataclass
+class Halo:
+    kind: int
+    x: float
+    y: float
+    m: float = 0.0
+    p0: float = 0.0
+    p1: float = 0.0
+
+    @staticmethod
+    def sis(x, y, r_e):
+        return Halo(SIS, x, y, 0.0, r_e, 0.0)
+
+    @staticmethod
+    def disk(x, y, m, radius):
+        return Halo(DISK, x, y, m, radius, 0.0)
+
+    @staticmethod
+    def nfw(x, y, m, r_s, r_max):
+        return Halo(NFW, x, y, m, r_s, r_max)
+
+    @staticmethod
+    def point(x, y, m):
+        return Halo(POINT, x, y, m)
+
+    @staticmethod
+    def gauss(x, y, m, r_sm, q):
+        return Halo(GAUSS, x, y, m, r_sm, q)
+
+
+class Lens:
+    """A built lens: one quadtree per species plus analytic halos."""
+
+    def __init__(self, species=(), halos=(), theta: float = 0.1, leaf_max: int = 5,
+                 precision: str = "fp32", group_rays: int = 0, stream=None):
+        L = lib()
+        self._keep = []
+        sp = (_Species * max(1, len(species)))()
+        for i, s in enumerate(species):
+            t = s.data
+            torch = _torch()
+            if t.dim() != 2 or t.shape[1] != 4:
+                raise ValueError("species data must be (n, 4)")
+            if t.dtype not in (torch.float32, torch.float64):
+                raise ValueError("species data must be float32 or float64")
+            self._keep.append(t)
+            sp[i] = _Species(s.kind, F32 if t.dtype == torch.float32 else F64, t.shape[0],
+                             _dev_ptr(t) if t.shape[0] > 0 else None, s.shape)
+        hs = (_Halo * max(1, len(halos)))()
+        for i, h in enumerate(halos):
+            hs[i] = _Halo(h.kind, 0, h.x, h.y, h.m, h.p0, h.p1)
+        prec = {"fp32": PREC_FP32, "fp64": PREC_FP64}[precision]
+        params = _Params(float(theta), int(leaf_max), prec, int(group_rays), 0)
+        h = ctypes.c_void_p()
+        _check(L.lens_build_tree(sp, len(species), hs, len(halos), ctypes.byref(params),
+                                 _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        self.precision = precision
+        self.n_species = len(species)
+        self.n_halos = len(halos)
+        self.species = list(species)
+        self.halos = list(halos)
+        self.theta = theta
+
+    # ------------------------------------------------------------------
+    @property
+    def out_dtype(self):
+        torch = _torch()
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(lib().lens_tree_get_info(self._h, ctypes.byref(inf)))
+        k = inf.n_species
+        return dict(n_species=k, precision=inf.precision, n_halos=inf.n_halos,
+                    n_particles=list(inf.n_particles[:k]), n_nodes=list(inf.n_nodes[:k]),
+                    n_leaves=list(inf.n_leaves[:k]), n_big=list(inf.n_big[:k]),
+                    depth=list(inf.depth[:k]), root=[tuple(inf.root[i]) for i in range(k)])
+
+    def export(self, species: int = 0):
+        """Host copies of one species' tree: nodes (n_nodes, 8), links
+        (n_nodes, 4), perm (n,), listed (n,)."""
+        inf = self.info()
+        nn, n = inf["n_nodes"][species], inf["n_particles"][species]
+        nodes = np.zeros((nn, 8), np.float64 if self.precision == "fp64" else np.float32)
+        links = np.zeros((nn, 4), np.int32)
+        perm = np.zeros(n, np.int32)
+        listed = np.zeros(n, np.int32)
+        _check(lib().lens_tree_export(self._h, species, nodes.ctypes.data, links.ctypes.data,
+                                      perm.ctypes.data, listed.ctypes.data))
+        return nodes, links, perm, listed
+
+    def counters(self, reset: bool = True) -> dict:
+        """Walk counters accumulated by calls made with COUNT."""
+        a = (ctypes.c_int64 * 8)()
+        _check(lib().lens_tree_counters(self._h, a, 1 if reset else 0))
+        keys = ["groups", "visited", "cells", "leaf_particles", "big_scanned", "big_kept",
+                "ray_interactions", "reserved"]
+        return dict(zip(keys, list(a)))
+
+    def last_timing(self):
+        """(group_ms, walk_ms) of the last call made with TIMING."""
+        g, w = ctypes.c_double(), ctypes.c_double()
+        _check(lib().lens_last_timing(self._h, ctypes.byref(g), ctypes.byref(w)))
+        return g.value, w.value
+
+    def sync(self, stream=None):
+        _check(lib().lens_sync_status(self._h, _stream_ptr(stream)))
+
+    def reserve(self, max_rays: int, max_batches: int = 1):
+        _check(lib().lens_reserve(self._h, int(max_rays), int(max_batches)))
+
+    def _outs(self, n, alpha_only, out):
+        torch = _torch()
+        if out is None:
+            k = 2 if alpha_only else 5
+            out = [torch.empty(n, dtype=self.out_dtype, device="cuda") for _ in range(k)]
+            out += [None] * (5 - k)
+        return out
+
+    def shoot(self, dx, dy, origin=(0.0, 0.0), flags: int = 0, out=None, stream=None):
+        """alpha1, alpha2, kappa, gamma1, gamma2 at rays origin + (dx, dy)."""
+        torch = _torch()
+        n = dx.numel()
+        if dy.numel() != n or dx.dtype != dy.dtype:
+            raise ValueError("dx, dy must match in size and dtype")
+        out = self._outs(n, bool(flags & ALPHA_ONLY), out)
+        rd = F32 if dx.dtype == torch.float32 else F64
+        _check(lib().lens_shoot_rays(self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx),
+                                     _dev_ptr(dy), rd, n, *[_dev_ptr(o) for o in out], int(flags),
+                                     _stream_ptr(stream)))
+        return out
+
+    def shoot_batches(self, offsets, origins, dx, dy, flags: int = 0, out=None, stream=None):
+        """Many ray batches (host int64 offsets (B+1,), host float64 origins (B, 2))."""
+        torch = _torch()
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        origins = np.ascontiguousarray(origins, dtype=np.float64).reshape(-1, 2)
+        n = int(offsets[-1])
+        out = self._outs(n, bool(flags & ALPHA_ONLY), out)
+        rd = F32 if dx.dtype == torch.float32 else F64
+        _check(lib().lens_shoot_batches(
+            self._h, origins.shape[0], offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            origins.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _dev_ptr(dx), _dev_ptr(dy), rd,
+            *[_dev_ptr(o) for o in out], int(flags), _stream_ptr(stream)))
+        return out
+
+    def backward(self, dx, dy, g_alpha1, g_alpha2, origin=(0.0, 0.0), flags: int = 0,
+                 grads=None, g_halos=None, stream=None):
+        """Accumulate dL/d(m, x, y) of every particle (and halo parameters)."""
+        torch = _torch()
+        if grads is None:
+            grads = [torch.zeros(s.data.shape[0], 3, dtype=self.out_dtype, device="cuda")
+                     for s in self.species]
+        arr = (ctypes.c_void_p * max(1, len(grads)))(*[g.data_ptr() for g in grads])
+        rd = F32 if dx.dtype == torch.float32 else F64
+        _check(lib().lens_shoot_rays_backward(
+            self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx), _dev_ptr(dy), rd, dx.numel(),
+            _dev_ptr(g_alpha1), _dev_ptr(g_alpha2), None, None, None, arr,
+            _dev_ptr(g_halos) if g_halos is not None else None, int(flags), _stream_ptr(stream)))
+        return grads
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.lens_free_tree(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fp32_peak(iters: int = 4096, stream=None) -> float:
+    """Measured FP32 FFMA rate of the current GPU (FLOP/s)."""
+    v = ctypes.c_double()
+    _check(lib().lens_fp32_peak(int(iters), ctypes.byref(v), _stream_ptr(stream)))
+    return v.value
+
+
+def shoot(lens: Lens, dx, dy, origin=(0.0, 0.0), species_data=None):
+    """Differentiable alpha (n, 2) through lens_shoot_rays / _backward: the
+    gradient flows to the (n, 4) species tensors' (x, y, m) columns.  The lens
+    must have been built from ``species_data`` (its current values)."""
+    from ._autograd import shoot_alpha
+    return shoot_alpha(lens, dx, dy, origin, species_data)

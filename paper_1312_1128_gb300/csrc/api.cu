@@ -1,0 +1,465 @@
+// api.cu -- the C ABI of liblens (include/lens.h): argument checking, tree
+// ownership, error reporting and the FP32 peak microbenchmark.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <string>
+
+#include "tree.cuh"
+
+namespace lens {
+lens_status shoot(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig, const void* dx,
+                  const void* dy, int dtype, void* const out[5], int flags, cudaStream_t s);
+lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb);
+lens_status shoot_backward(lens_tree* t, double ox, double oy, const void* dx, const void* dy,
+                           int dtype, int64_t n, const void* const g[5], void* const* g_species,
+                           void* g_halos, int flags, cudaStream_t s);
+lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, const double* orig,
+                                const void* dx, const void* dy, int dtype, void* const out[5],
+                                int flags, cudaStream_t s);
+void free_graphs(lens_tree* t);
+}  // namespace lens
+
+static thread_local char g_msg[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+lens_status lens_set_error(lens_status s, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+lens_status lens_cuda_check(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return lens_set_error(LENS_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return lens_set_error(LENS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+using namespace lens;
+
+static double nfw_gX(double X)
+{
+    double u = 1.0 - X * X, F;
+    if (std::fabs(u) < 1e-4) {
+        double s = 0.0;
+        for (int k = 12; k >= 0; --k) s = s * u + 1.0 / (2 * k + 1);
+        F = s;
+    } else if (X < 1.0) {
+        F = std::acosh(1.0 / X) / std::sqrt(u);
+    } else {
+        F = std::acos(1.0 / X) / std::sqrt(-u);
+    }
+    return std::log(0.5 * X) + F;
+}
+
+static lens_status check_halo(const lens_halo& h, HaloDev& d)
+{
+    d = HaloDev{};
+    d.kind = h.kind;
+    d.x = h.x; d.y = h.y; d.m = h.m; d.p0 = h.p0; d.p1 = h.p1;
+    bool fin = std::isfinite(h.x) && std::isfinite(h.y) && std::isfinite(h.m) && std::isfinite(h.p0) &&
+               std::isfinite(h.p1);
+    if (!fin) return lens_set_error(LENS_ERR_INVALID_ARG, "halo with non-finite field");
+    switch (h.kind) {
+    case LENS_POINT:
+        return LENS_OK;
+    case LENS_GAUSS:
+        if (!(h.p0 > 0 && h.p1 > 0)) return lens_set_error(LENS_ERR_INVALID_ARG, "Gaussian halo needs r_sm > 0, q > 0");
+        d.c0 = 1.0 / (2.0 * h.p0 * h.p0);
+        d.c1 = 0.5 * h.p1 * h.p1;
+        d.c2 = 1.0 / (-std::expm1(-d.c1));
+        return LENS_OK;
+    case LENS_NFW:
+        if (!(h.p0 > 0 && h.p1 > 0)) return lens_set_error(LENS_ERR_INVALID_ARG, "NFW halo needs r_s > 0, R_max > 0");
+        d.c0 = h.m / nfw_gX(h.p1 / h.p0);
+        d.c1 = 1.0 / h.p0;
+        d.c2 = h.p1 * h.p1;
+        return LENS_OK;
+    case LENS_SIS:
+        if (!(h.p0 >= 0)) return lens_set_error(LENS_ERR_INVALID_ARG, "SIS halo needs r_E >= 0");
+        return LENS_OK;
+    case LENS_DISK:
+        if (!(h.p0 > 0)) return lens_set_error(LENS_ERR_INVALID_ARG, "disk halo needs R > 0");
+        d.c2 = h.p0 * h.p0;
+        return LENS_OK;
+    }
+    return lens_set_error(LENS_ERR_INVALID_ARG, "unknown halo kind %d", h.kind);
+}
+
+extern "C" {
+
+int32_t lens_api_version(void) { return LENS_API_VERSION; }
+
+int64_t lens_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+const char* lens_last_error(void) { return g_msg; }
+
+const char* lens_status_string(lens_status s)
+{
+    switch (s) {
+    case LENS_OK: return "ok";
+    case LENS_ERR_INVALID_ARG: return "invalid argument";
+    case LENS_ERR_CUDA: return "CUDA error";
+    case LENS_ERR_OOM: return "out of device memory";
+    case LENS_ERR_TIMEOUT: return "bounded device wait expired";
+    case LENS_ERR_INTERNAL: return "internal consistency check failed";
+    case LENS_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+void lens_free_tree(lens_tree* t)
+{
+    if (!t) return;
+    free_graphs(t);
+    for (auto& st : t->sp) free_species(st);
+    if (t->halos) cudaFree(t->halos);
+    if (t->d_err) cudaFree(t->d_err);
+    if (t->ray_scratch.ptr) cudaFree(t->ray_scratch.ptr);
+    if (t->d_stats) cudaFree(t->d_stats);
+    for (int i = 0; i < 3; ++i)
+        if (t->ev[i]) cudaEventDestroy(t->ev[i]);
+    delete t;
+}
+
+lens_status lens_build_tree(const lens_species* species, int32_t n_species, const lens_halo* halos,
+                            int64_t n_halos, const lens_params* params, void* stream, lens_tree** out)
+{
+    if (!out) return lens_set_error(LENS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!params) return lens_set_error(LENS_ERR_INVALID_ARG, "params is NULL");
+    if (n_species < 0 || n_species > 8) return lens_set_error(LENS_ERR_INVALID_ARG, "n_species must be 0..8");
+    if (n_species > 0 && !species) return lens_set_error(LENS_ERR_INVALID_ARG, "species is NULL");
+    if (n_halos < 0 || (n_halos > 0 && !halos)) return lens_set_error(LENS_ERR_INVALID_ARG, "bad halos");
+    if (!(params->theta >= 0.0) || !std::isfinite(params->theta))
+        return lens_set_error(LENS_ERR_INVALID_ARG, "theta must be finite and >= 0");
+    if (params->leaf_max < 1 || params->leaf_max > 64)
+        return lens_set_error(LENS_ERR_INVALID_ARG, "leaf_max must be in 1..64");
+    if (params->precision != LENS_PREC_FP32 && params->precision != LENS_PREC_FP64)
+        return lens_set_error(LENS_ERR_INVALID_ARG, "unknown precision %d", params->precision);
+    if (params->group_rays != 0 && params->group_rays != 32 && params->group_rays != 64)
+        return lens_set_error(LENS_ERR_INVALID_ARG, "group_rays must be 0, 32 or 64");
+    if (params->reserved != 0) return lens_set_error(LENS_ERR_INVALID_ARG, "reserved must be 0");
+    for (int i = 0; i < n_species; ++i) {
+        const lens_species& s = species[i];
+        if (s.kind != LENS_POINT && s.kind != LENS_GAUSS && s.kind != LENS_NFW)
+            return lens_set_error(LENS_ERR_INVALID_ARG, "species %d: kind must be POINT, GAUSS or NFW", i);
+        if (s.dtype != LENS_F32 && s.dtype != LENS_F64)
+            return lens_set_error(LENS_ERR_INVALID_ARG, "species %d: bad dtype", i);
+        if (s.n < 0 || s.n >= (1ll << 30))
+            return lens_set_error(LENS_ERR_INVALID_ARG, "species %d: n must be in [0, 2^30)", i);
+        if (s.n > 0 && !s.data) return lens_set_error(LENS_ERR_INVALID_ARG, "species %d: data is NULL", i);
+        if (s.kind != LENS_POINT && !(s.shape > 0.0 && std::isfinite(s.shape)))
+            return lens_set_error(LENS_ERR_INVALID_ARG, "species %d: shape must be > 0", i);
+    }
+    std::vector<HaloDev> hd((size_t)n_halos);
+    for (int64_t i = 0; i < n_halos; ++i) LENS_TRY(check_halo(halos[i], hd[i]));
+
+    lens_tree* t = new lens_tree();
+    t->precision = params->precision;
+    t->theta = params->theta;
+    t->leaf_max = params->leaf_max;
+    t->group_rays = params->group_rays == 0 ? 64 : params->group_rays;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto fail = [&](lens_status st) {
+        lens_free_tree(t);
+        return st;
+    };
+    cudaError_t e = cudaGetDevice(&t->device);
+    if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaGetDevice"));
+    e = cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
+    if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaDeviceGetAttribute"));
+    e = cudaMalloc((void**)&t->d_err, sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMalloc(err)"));
+    e = cudaMemsetAsync(t->d_err, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMemsetAsync"));
+    e = cudaMalloc((void**)&t->d_stats, 8 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMalloc(stats)"));
+    e = cudaMemsetAsync(t->d_stats, 0, 8 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMemsetAsync"));
+    t->halos_host.assign(halos, halos + n_halos);
+    t->n_halos = n_halos;
+    if (n_halos > 0) {
+        e = cudaMalloc((void**)&t->halos, n_halos * sizeof(HaloDev));
+        if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMalloc(halos)"));
+        e = cudaMemcpy(t->halos, hd.data(), n_halos * sizeof(HaloDev), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMemcpy(halos)"));
+    }
+    t->sp.resize(n_species);
+    for (int i = 0; i < n_species; ++i) {
+        lens_status st = build_species(t, t->sp[i], species[i], s);
+        if (st != LENS_OK) return fail(st);
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(lens_cuda_check(e, "tree build"));
+    uint32_t herr = 0;
+    e = cudaMemcpy(&herr, t->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMemcpy(err)"));
+    if (herr & DERR_BAD_INPUT)
+        return fail(lens_set_error(LENS_ERR_INVALID_ARG, "negative or non-finite particle mass or size"));
+    if (herr) return fail(lens_set_error(LENS_ERR_INTERNAL, "tree build check failed (code %u)", herr));
+    *out = t;
+    return LENS_OK;
+}
+
+static lens_status check_outputs(const lens_tree* t, void* a1, void* a2, void* k, void* g1, void* g2,
+                                 int32_t flags, int64_t n)
+{
+    if (!t) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
+    if (flags & ~(LENS_ALPHA_ONLY | LENS_DIRECT | LENS_ACCUMULATE | LENS_USE_GRAPH | LENS_COUNT | LENS_TIMING))
+        return lens_set_error(LENS_ERR_INVALID_ARG, "unknown flag bits");
+    if (n < 0 || n >= (1ll << 31)) return lens_set_error(LENS_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    if (n == 0) return LENS_OK;
+    if (!a1 || !a2) return lens_set_error(LENS_ERR_INVALID_ARG, "alpha outputs are NULL");
+    if (!(flags & LENS_ALPHA_ONLY) && (!k || !g1 || !g2))
+        return lens_set_error(LENS_ERR_INVALID_ARG, "kappa/gamma outputs are NULL without LENS_ALPHA_ONLY");
+    return LENS_OK;
+}
+
+lens_status lens_shoot_rays(lens_tree* tree, double origin_x, double origin_y, const void* ray_dx,
+                            const void* ray_dy, int32_t ray_dtype, int64_t n, void* alpha1, void* alpha2,
+                            void* kappa, void* gamma1, void* gamma2, int32_t flags, void* stream)
+{
+    LENS_TRY(check_outputs(tree, alpha1, alpha2, kappa, gamma1, gamma2, flags, n));
+    if (flags & LENS_USE_GRAPH) return lens_set_error(LENS_ERR_INVALID_ARG, "LENS_USE_GRAPH is for lens_shoot_batches");
+    if (ray_dtype != LENS_F32 && ray_dtype != LENS_F64) return lens_set_error(LENS_ERR_INVALID_ARG, "bad ray dtype");
+    if (!std::isfinite(origin_x) || !std::isfinite(origin_y))
+        return lens_set_error(LENS_ERR_INVALID_ARG, "origin must be finite");
+    if (n == 0) return LENS_OK;
+    if (!ray_dx || !ray_dy) return lens_set_error(LENS_ERR_INVALID_ARG, "ray arrays are NULL");
+    int64_t off[2] = {0, n};
+    double orig[2] = {origin_x, origin_y};
+    void* out[5] = {alpha1, alpha2, kappa, gamma1, gamma2};
+    return shoot(tree, 1, off, orig, ray_dx, ray_dy, ray_dtype, out, flags, (cudaStream_t)stream);
+}
+
+static lens_status check_batches(int64_t n_batches, const int64_t* offsets, const double* origins)
+{
+    if (n_batches < 0 || n_batches > (1 << 24)) return lens_set_error(LENS_ERR_INVALID_ARG, "bad n_batches");
+    if (!offsets) return lens_set_error(LENS_ERR_INVALID_ARG, "offsets is NULL");
+    if (n_batches > 0 && !origins) return lens_set_error(LENS_ERR_INVALID_ARG, "origins is NULL");
+    if (offsets[0] != 0) return lens_set_error(LENS_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int64_t b = 0; b < n_batches; ++b) {
+        if (offsets[b + 1] < offsets[b]) return lens_set_error(LENS_ERR_INVALID_ARG, "offsets must be non-decreasing");
+        if (!std::isfinite(origins[2 * b]) || !std::isfinite(origins[2 * b + 1]))
+            return lens_set_error(LENS_ERR_INVALID_ARG, "origins must be finite");
+    }
+    return LENS_OK;
+}
+
+lens_status lens_shoot_batches(lens_tree* tree, int64_t n_batches, const int64_t* offsets,
+                               const double* origins, const void* ray_dx, const void* ray_dy,
+                               int32_t ray_dtype, void* alpha1, void* alpha2, void* kappa, void* gamma1,
+                               void* gamma2, int32_t flags, void* stream)
+{
+    LENS_TRY(check_batches(n_batches, offsets, origins));
+    int64_t n = offsets[n_batches];
+    LENS_TRY(check_outputs(tree, alpha1, alpha2, kappa, gamma1, gamma2, flags, n));
+    if (ray_dtype != LENS_F32 && ray_dtype != LENS_F64) return lens_set_error(LENS_ERR_INVALID_ARG, "bad ray dtype");
+    if (n == 0) return LENS_OK;
+    if (!ray_dx || !ray_dy) return lens_set_error(LENS_ERR_INVALID_ARG, "ray arrays are NULL");
+    void* out[5] = {alpha1, alpha2, kappa, gamma1, gamma2};
+    if (flags & LENS_USE_GRAPH)
+        return graph_shoot_batches(tree, n_batches, offsets, origins, ray_dx, ray_dy, ray_dtype, out,
+                                   flags & ~LENS_USE_GRAPH, (cudaStream_t)stream);
+    return shoot(tree, n_batches, offsets, origins, ray_dx, ray_dy, ray_dtype, out, flags, (cudaStream_t)stream);
+}
+
+lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double origin_y, const void* ray_dx,
+                                     const void* ray_dy, int32_t ray_dtype, int64_t n, const void* g_alpha1,
+                                     const void* g_alpha2, const void* g_kappa, const void* g_gamma1,
+                                     const void* g_gamma2, void* const* g_species, void* g_halos,
+                                     int32_t flags, void* stream)
+{
+    if (!tree) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
+    if (flags & ~(LENS_DIRECT)) return lens_set_error(LENS_ERR_INVALID_ARG, "backward accepts LENS_DIRECT only");
+    if (n < 0 || n >= (1ll << 31)) return lens_set_error(LENS_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    if (g_kappa || g_gamma1 || g_gamma2)
+        return lens_set_error(LENS_ERR_UNSUPPORTED, "gradients of kappa and gamma are not implemented");
+    if (ray_dtype != LENS_F32 && ray_dtype != LENS_F64) return lens_set_error(LENS_ERR_INVALID_ARG, "bad ray dtype");
+    if (n == 0) return LENS_OK;
+    if (!ray_dx || !ray_dy || !g_alpha1 || !g_alpha2) return lens_set_error(LENS_ERR_INVALID_ARG, "NULL array");
+    if (tree->sp.size() > 0 && !g_species) return lens_set_error(LENS_ERR_INVALID_ARG, "g_species is NULL");
+    const void* g[5] = {g_alpha1, g_alpha2, nullptr, nullptr, nullptr};
+    return shoot_backward(tree, origin_x, origin_y, ray_dx, ray_dy, ray_dtype, n, g, g_species, g_halos,
+                          flags, (cudaStream_t)stream);
+}
+
+lens_status lens_reserve(lens_tree* tree, int64_t max_rays, int64_t max_batches)
+{
+    if (!tree) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
+    if (max_rays < 0 || max_batches < 1) return lens_set_error(LENS_ERR_INVALID_ARG, "bad reserve sizes");
+    return reserve_rays(tree, max_rays, max_batches);
+}
+
+lens_status lens_sync_status(lens_tree* tree, void* stream)
+{
+    if (!tree) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    LENS_CUDA(cudaStreamSynchronize(s));
+    uint32_t herr = 0;
+    LENS_CUDA(cudaMemcpy(&herr, tree->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (herr) {
+        LENS_CUDA(cudaMemset(tree->d_err, 0, sizeof(uint32_t)));
+        if (herr & DERR_BAD_INPUT) return lens_set_error(LENS_ERR_INVALID_ARG, "bad input found on the device");
+        return lens_set_error(LENS_ERR_INTERNAL, "device check failed (code %u)", herr);
+    }
+    return LENS_OK;
+}
+
+lens_status lens_tree_counters(lens_tree* t, int64_t* out, int32_t reset)
+{
+    if (!t || !out) return lens_set_error(LENS_ERR_INVALID_ARG, "NULL argument");
+    unsigned long long h[8];
+    LENS_CUDA(cudaDeviceSynchronize());
+    LENS_CUDA(cudaMemcpy(h, t->d_stats, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 8; ++i) out[i] = (int64_t)h[i];
+    if (reset) LENS_CUDA(cudaMemset(t->d_stats, 0, sizeof(h)));
+    return LENS_OK;
+}
+
+lens_status lens_last_timing(lens_tree* t, double* group_ms, double* walk_ms)
+{
+    if (!t || !group_ms || !walk_ms) return lens_set_error(LENS_ERR_INVALID_ARG, "NULL argument");
+    *group_ms = *walk_ms = 0.0;
+    if (!t->timed) return LENS_OK;
+    LENS_CUDA(cudaEventSynchronize(t->ev[2]));
+    float a = 0, b = 0;
+    LENS_CUDA(cudaEventElapsedTime(&a, t->ev[0], t->ev[1]));
+    LENS_CUDA(cudaEventElapsedTime(&b, t->ev[1], t->ev[2]));
+    *group_ms = a;
+    *walk_ms = b;
+    return LENS_OK;
+}
+
+lens_status lens_tree_get_info(const lens_tree* t, lens_tree_info* info)
+{
+    if (!t || !info) return lens_set_error(LENS_ERR_INVALID_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n_species = (int32_t)t->sp.size();
+    info->precision = t->precision;
+    info->n_halos = t->n_halos;
+    for (size_t i = 0; i < t->sp.size() && i < 8; ++i) {
+        const SpeciesTree& s = t->sp[i];
+        info->n_particles[i] = s.n;
+        info->n_nodes[i] = s.n_nodes;
+        info->n_leaves[i] = s.n_leaves;
+        info->n_big[i] = s.n_big;
+        info->depth[i] = s.depth;
+        info->root[i][0] = s.root_cx;
+        info->root[i][1] = s.root_cy;
+        info->root[i][2] = s.root_half;
+    }
+    return LENS_OK;
+}
+
+lens_status lens_tree_export(const lens_tree* t, int32_t si, void* nodes, int32_t* links, int32_t* perm,
+                             int32_t* listed)
+{
+    if (!t) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
+    if (si < 0 || si >= (int32_t)t->sp.size()) return lens_set_error(LENS_ERR_INVALID_ARG, "bad species index");
+    const SpeciesTree& s = t->sp[si];
+    int64_t nn = s.n_nodes, n = s.n;
+    LENS_CUDA(cudaDeviceSynchronize());
+    if (nodes && nn > 0) {
+        bool dbl = s.prec == LENS_PREC_FP64;
+        size_t es = dbl ? 8 : 4;
+        std::vector<char> A(nn * 4 * es), B(nn * 2 * es);
+        std::vector<float> rcm(nn);
+        std::vector<uint8_t> lev(nn);
+        LENS_CUDA(cudaMemcpy(A.data(), s.nodeA, A.size(), cudaMemcpyDeviceToHost));
+        LENS_CUDA(cudaMemcpy(B.data(), s.nodeB, B.size(), cudaMemcpyDeviceToHost));
+        LENS_CUDA(cudaMemcpy(lev.data(), s.node_level, nn, cudaMemcpyDeviceToHost));
+        for (int64_t b = 0; b < nn; ++b) {
+            double v[8];
+            for (int k = 0; k < 4; ++k)
+                v[k] = dbl ? ((double*)A.data())[4 * b + k] : ((float*)A.data())[4 * b + k];
+            for (int k = 0; k < 2; ++k)
+                v[4 + k] = dbl ? ((double*)B.data())[2 * b + k] : ((float*)B.data())[2 * b + k];
+            v[6] = 2.0 * s.root_half / (double)(1u << lev[b]);
+            v[7] = lev[b];
+            for (int k = 0; k < 8; ++k) {
+                if (dbl) ((double*)nodes)[8 * b + k] = v[k];
+                else ((float*)nodes)[8 * b + k] = (float)v[k];
+            }
+        }
+    }
+    if (links && nn > 0) {
+        std::vector<int4> L(nn);
+        LENS_CUDA(cudaMemcpy(L.data(), s.link, nn * sizeof(int4), cudaMemcpyDeviceToHost));
+        for (int64_t b = 0; b < nn; ++b) {
+            links[4 * b] = L[b].x;
+            links[4 * b + 1] = L[b].y & kCountMask;
+            links[4 * b + 2] = (L[b].y & kLeafBit) ? 1 : 0;
+            links[4 * b + 3] = L[b].w;
+        }
+    }
+    if (perm && n > 0) LENS_CUDA(cudaMemcpy(perm, s.perm, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (listed && n > 0) {
+        std::vector<uint32_t> P(n);
+        std::vector<uint8_t> Ls(n, 0);
+        LENS_CUDA(cudaMemcpy(P.data(), s.perm, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        if (s.listed) LENS_CUDA(cudaMemcpy(Ls.data(), s.listed, n, cudaMemcpyDeviceToHost));
+        for (int64_t j = 0; j < n; ++j) listed[P[j]] = Ls[j];
+    }
+    return LENS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------- FP32 peak microbenchmark
+
+// Eight independent dependent-FFMA chains per thread (enough ILP to keep the
+// FP32 pipes busy), written to memory at the end so nothing is eliminated.
+__global__ void k_ffma_peak(float* sink, int64_t iters, float a, float b)
+{
+    float x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6,
+          x7 = x0 + 7;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            x0 = fmaf(x0, a, b); x1 = fmaf(x1, a, b); x2 = fmaf(x2, a, b); x3 = fmaf(x3, a, b);
+            x4 = fmaf(x4, a, b); x5 = fmaf(x5, a, b); x6 = fmaf(x6, a, b); x7 = fmaf(x7, a, b);
+        }
+    }
+    float r = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+    if (r == 1234.5f) sink[0] = r;
+}
+
+extern "C" lens_status lens_fp32_peak(int64_t iters, double* flops, void* stream)
+{
+    if (!flops || iters < 1) return lens_set_error(LENS_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    LENS_CUDA(cudaGetDevice(&dev));
+    LENS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    float* sink = nullptr;
+    LENS_CUDA(cudaMalloc(&sink, sizeof(float)));
+    const int threads = 256, blocks = sms * 8;
+    cudaEvent_t e0, e1;
+    LENS_CUDA(cudaEventCreate(&e0));
+    LENS_CUDA(cudaEventCreate(&e1));
+    { k_ffma_peak<<<blocks, threads, 0, s>>>(sink, iters / 8 + 1, 0.999f, 0.001f); note_launch(); }  // warm up
+    LENS_CUDA(cudaEventRecord(e0, s));
+    { k_ffma_peak<<<blocks, threads, 0, s>>>(sink, iters, 0.999f, 0.001f); note_launch(); }
+    LENS_CUDA(cudaEventRecord(e1, s));
+    LENS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    LENS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    double total = 2.0 * 8.0 * 16.0 * (double)iters * (double)threads * (double)blocks;
+    *flops = total / (ms * 1e-3);
+    return LENS_OK;
+}

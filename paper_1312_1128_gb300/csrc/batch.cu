@@ -1,0 +1,82 @@
+// batch.cu -- CUDA-graph replay of the batched shoot (uneven refinement
+// batches, Sec. 4 / Sec. 3.3): the kernel sequence of one lens_shoot_batches
+// call is captured once per (sizes, pointers, flags) key and replayed.
+#include <vector>
+
+#include "tree.cuh"
+
+namespace lens {
+
+struct ShootPlan {
+    int64_t n = 0, nb = 0;
+    uint64_t ng = 0;
+    int R = 1;
+};
+lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig,
+                           cudaStream_t s, ShootPlan* plan);
+lens_status enqueue_shoot(lens_tree* t, const ShootPlan& plan, const void* dx, const void* dy, int dtype,
+                          void* const out[5], int flags, cudaStream_t s);
+
+struct GraphEntry {
+    int64_t n, nb;
+    uint64_t ng;
+    const void *dx, *dy;
+    int dtype, flags;
+    void* out[5];
+    void* scratch;
+    cudaGraphExec_t exec;
+};
+
+void free_graphs(lens_tree* t)
+{
+    for (GraphEntry* g : t->graphs) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        delete g;
+    }
+    t->graphs.clear();
+}
+
+lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, const double* orig,
+                                const void* dx, const void* dy, int dtype, void* const out[5],
+                                int flags, cudaStream_t s)
+{
+    ShootPlan plan;
+    LENS_TRY(upload_batches(t, nb, off, orig, s, &plan));
+    for (GraphEntry* g : t->graphs) {
+        bool same = g->n == plan.n && g->nb == plan.nb && g->ng == plan.ng && g->dx == dx && g->dy == dy &&
+                    g->dtype == dtype && g->flags == flags && g->scratch == t->ray_scratch.ptr;
+        for (int q = 0; q < 5 && same; ++q) same = g->out[q] == out[q];
+        if (same) {
+            LENS_CUDA(cudaGraphLaunch(g->exec, s));
+            return LENS_OK;
+        }
+    }
+    // first use of this key: run eagerly, then capture for the next calls
+    LENS_TRY(enqueue_shoot(t, plan, dx, dy, dtype, out, flags, s));
+    cudaStream_t cs;
+    LENS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return lens_cuda_check(e, "cudaStreamBeginCapture");
+    }
+    lens_status st = enqueue_shoot(t, plan, dx, dy, dtype, out, flags, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (st != LENS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return lens_cuda_check(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return lens_cuda_check(e, "cudaGraphInstantiate");
+    GraphEntry* g = new GraphEntry{plan.n, plan.nb, plan.ng, dx, dy, dtype, flags, {}, t->ray_scratch.ptr, exec};
+    for (int q = 0; q < 5; ++q) g->out[q] = out[q];
+    t->graphs.push_back(g);
+    return LENS_OK;
+}
+
+}  // namespace lens

@@ -1,0 +1,722 @@
+// build.cu -- quadtree construction on the GPU (Sec. 3.2).
+//
+// The paper inserts particles into an equal-area quadtree and, while the tree
+// is built, computes each box's monopole and quadrupole moments, r_cut
+// (Eq. r_cut) and its big-particle list.  Here the same tree is produced in
+// bulk-parallel form:
+//   1. stage + bounding box  -> square root box
+//   2. 48-bit Morton keys (24 levels) -> radix sort: every box is a run of
+//      equal key prefixes in the sorted order;
+//   3. topology without a level loop: particle j's leaf level is one past the
+//      deepest level at which a window of leaf_max consecutive keys containing
+//      j shares its prefix; j "owns" the boxes it starts (levels from
+//      lcp(K[j-1], K[j]) + 1 down to its leaf level), so a scan of the owned
+//      counts numbers every box in depth-first preorder;
+//   4. a stable sort by level gives breadth-first order (children contiguous);
+//   5. moments bottom-up, one launch per level, in FP64, stored in FP32 (or
+//      FP64) with r_cut^2 rounded up;
+//   6. big lists: a particle whose support radius s exceeds lambda times the
+//      side of a box on its path is listed at the shallowest such box; lists
+//      are grouped per box by a stable sort (deterministic order).
+#include <algorithm>
+#include <cmath>
+
+#include "profiles.cuh"
+#include "sort.cuh"
+#include "tree.cuh"
+
+namespace lens {
+
+struct RootBox {
+    double cx, cy, half, x0, y0;
+};
+
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+
+__device__ __forceinline__ int lcp_digits(uint64_t a, uint64_t b)
+{
+    uint64_t x = a ^ b;
+    if (x == 0) return kMaxDepth;
+    return (__clzll((long long)x) - (64 - kKeyBits)) >> 1;
+}
+
+__device__ __forceinline__ uint64_t spread24(uint32_t v)
+{
+    uint64_t x = v & 0xffffffu;
+    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t compact24(uint64_t x)
+{
+    x &= 0x5555555555555555ull;
+    x = (x | (x >> 1)) & 0x3333333333333333ull;
+    x = (x | (x >> 2)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x >> 4)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x >> 8)) & 0x0000ffff0000ffffull;
+    x = (x | (x >> 16)) & 0x00000000ffffffffull;
+    return (uint32_t)x & 0xffffffu;
+}
+
+// ------------------------------------------------------------- 1. stage
+
+template <typename T>
+__global__ void k_stage(const void* data, int dtype, int64_t n, int kind, vec4_t<T>* staged,
+                        unsigned long long* bbox, uint32_t* err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = i < n;
+    double x = 0, y = 0, m = 0, p = 0;
+    if (valid) {
+        if (dtype == LENS_F32) {
+            const float* d = (const float*)data + 4 * i;
+            x = d[0]; y = d[1]; m = d[2]; p = d[3];
+        } else {
+            const double* d = (const double*)data + 4 * i;
+            x = d[0]; y = d[1]; m = d[2]; p = d[3];
+        }
+        bool ok = isfinite(x) && isfinite(y) && isfinite(m) && m >= 0.0;
+        if (kind != LENS_POINT) ok = ok && isfinite(p) && p > 0.0;
+        if (!ok) {
+            atomicOr(err, DERR_BAD_INPUT);
+            x = y = m = 0.0;
+            p = 1.0;
+        }
+        vec4_t<T> r;
+        r.x = (T)x; r.y = (T)y; r.z = (T)m; r.w = (T)p;
+        staged[i] = r;
+        x = (double)r.x;
+        y = (double)r.y;
+    }
+    // warp-aggregated bounding box of the stored (rounded) positions
+    unsigned long long xmin = valid ? dbl_to_ordered(x) : ~0ull, xmax = valid ? dbl_to_ordered(x) : 0ull;
+    unsigned long long ymin = valid ? dbl_to_ordered(y) : ~0ull, ymax = valid ? dbl_to_ordered(y) : 0ull;
+    for (int o = 16; o; o >>= 1) {
+        xmin = min(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
+        xmax = max(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        ymin = min(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+        ymax = max(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+    }
+    if ((threadIdx.x & 31) == 0 && xmax != 0ull) {
+        atomicMin(&bbox[0], xmin);
+        atomicMax(&bbox[1], xmax);
+        atomicMin(&bbox[2], ymin);
+        atomicMax(&bbox[3], ymax);
+    }
+}
+
+__global__ void k_root(const unsigned long long* bbox, RootBox* rb)
+{
+    double x0 = ordered_to_dbl(bbox[0]), x1 = ordered_to_dbl(bbox[1]);
+    double y0 = ordered_to_dbl(bbox[2]), y1 = ordered_to_dbl(bbox[3]);
+    double cx = 0.5 * (x0 + x1), cy = 0.5 * (y0 + y1);
+    double half = 0.5 * fmax(x1 - x0, y1 - y0);
+    double scale = fmax(1.0, fmax(fabs(cx), fabs(cy)));
+    if (!(half > 1e-12 * scale)) half = 1e-12 * scale;
+    half *= 1.0 + 1.0 / 65536.0;  // every particle strictly inside
+    rb->cx = cx;
+    rb->cy = cy;
+    rb->half = half;
+    rb->x0 = cx - half;
+    rb->y0 = cy - half;
+}
+
+// ----------------------------------------------------------- 2. Morton
+
+template <typename T>
+__global__ void k_morton(const vec4_t<T>* staged, int64_t n, const RootBox* rb, uint64_t* keys,
+                         uint32_t* vals)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    vec4_t<T> r = staged[i];
+    double inv = 16777216.0 / (2.0 * rb->half);
+    double fx = ((double)r.x - rb->x0) * inv, fy = ((double)r.y - rb->y0) * inv;
+    uint32_t qx = (uint32_t)fmin(fmax(floor(fx), 0.0), 16777215.0);
+    uint32_t qy = (uint32_t)fmin(fmax(floor(fy), 0.0), 16777215.0);
+    keys[i] = spread24(qx) | (spread24(qy) << 1);
+    vals[i] = (uint32_t)i;
+}
+
+template <typename T>
+__global__ void k_gather(const vec4_t<T>* staged, const uint32_t* perm, int64_t n, vec4_t<T>* sorted)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) sorted[j] = staged[perm[j]];
+}
+
+// --------------------------------------------------------- 3. topology
+
+// Leaf level L_j and the number of boxes particle j starts.
+__global__ void k_levels(const uint64_t* K, int64_t n, int N, uint8_t* Lp, uint32_t* cnt)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int D = -1;
+    int64_t a0 = j - N + 1 > 0 ? j - N + 1 : 0;
+    int64_t a1 = j < n - N ? j : n - N;
+    for (int64_t a = a0; a <= a1; ++a) {
+        int w = lcp_digits(K[a], K[a + N - 1]);
+        D = w > D ? w : D;
+    }
+    int L = D + 1 < kMaxDepth ? D + 1 : kMaxDepth;
+    int s = j == 0 ? 0 : lcp_digits(K[j - 1], K[j]) + 1;
+    Lp[j] = (uint8_t)L;
+    cnt[j] = L >= s ? (uint32_t)(L - s + 1) : 0u;
+}
+
+// First index e > j whose key leaves j's box at level l (n if none).
+__device__ __forceinline__ int64_t run_end(const uint64_t* K, int64_t n, int64_t j, int l)
+{
+    if (l == 0) return n;
+    uint64_t kj = K[j];
+    int64_t lo = j, hi = n;  // lcp(kj, K[lo]) >= l; hi is the first failing candidate
+    while (hi - lo > 1) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (lcp_digits(kj, K[mid]) >= l) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+// First index f <= j that shares j's box at level l.
+__device__ __forceinline__ int64_t run_start(const uint64_t* K, int64_t j, int l)
+{
+    if (l == 0) return 0;
+    uint64_t kj = K[j];
+    int64_t lo = -1, hi = j;  // hi shares; lo is a failing candidate
+    while (hi - lo > 1) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (lcp_digits(kj, K[mid]) >= l) hi = mid;
+        else lo = mid;
+    }
+    return hi;
+}
+
+__device__ __forceinline__ int first_level(const uint64_t* K, int64_t j)
+{
+    return j == 0 ? 0 : lcp_digits(K[j - 1], K[j]) + 1;
+}
+
+// Preorder id of the box at level l containing particle j (l <= L_j).
+__device__ __forceinline__ uint32_t node_at(const uint64_t* K, const uint32_t* off, int64_t j, int l)
+{
+    int64_t f = run_start(K, j, l);
+    return off[f] + (uint32_t)(l - first_level(K, f));
+}
+
+__global__ void k_nodes(const uint64_t* K, int64_t n, const uint8_t* Lp, const uint32_t* off,
+                        uint32_t n_nodes, uint32_t* lvl, uint32_t* first, uint32_t* count,
+                        uint32_t* skip, uint8_t* isleaf)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int L = Lp[j], s = first_level(K, j);
+    for (int l = s; l <= L; ++l) {
+        uint32_t v = off[j] + (uint32_t)(l - s);
+        int64_t e = run_end(K, n, j, l);
+        lvl[v] = (uint32_t)l;
+        first[v] = (uint32_t)j;
+        count[v] = (uint32_t)(e - j);
+        isleaf[v] = l == L ? 1 : 0;
+        skip[v] = e < n ? off[e] : n_nodes;
+    }
+}
+
+__global__ void k_nchild(uint32_t n_nodes, const uint8_t* isleaf, const uint32_t* skip,
+                         uint8_t* nchild, uint32_t* err)
+{
+    uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_nodes) return;
+    if (isleaf[v]) { nchild[v] = 0; return; }
+    uint32_t c = v + 1, end = skip[v];
+    int k = 0;
+    while (c < end && k < 5) { ++k; c = skip[c]; }
+    if (k < 1 || k > 4) atomicOr(err, DERR_INDEX);
+    nchild[v] = (uint8_t)(k > 4 ? 4 : k);
+}
+
+__global__ void k_invert(const uint32_t* bfs2pre, uint32_t n_nodes, uint32_t* pre2bfs)
+{
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n_nodes) pre2bfs[bfs2pre[b]] = b;
+}
+
+__global__ void k_level_bounds(const uint32_t* lvl_sorted, uint32_t n_nodes, uint32_t* level_start)
+{
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_nodes) return;
+    uint32_t l = lvl_sorted[b];
+    if (b == 0 || lvl_sorted[b - 1] != l) level_start[l] = b;
+    if (b == n_nodes - 1) level_start[kMaxDepth + 1] = l;  // deepest level
+}
+
+__global__ void k_links(uint32_t n_nodes, const uint32_t* bfs2pre, const uint32_t* pre2bfs,
+                        const uint32_t* lvl, const uint32_t* first, const uint32_t* count,
+                        const uint8_t* isleaf, const uint8_t* nchild, int4* link, uint8_t* node_level,
+                        uint32_t* n_leaves)
+{
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_nodes) return;
+    uint32_t v = bfs2pre[b];
+    int4 L;
+    if (isleaf[v]) {
+        L.x = (int)first[v];
+        L.y = (int)count[v] | kLeafBit;
+        atomicAdd(n_leaves, 1u);
+    } else {
+        L.x = (int)pre2bfs[v + 1];
+        L.y = (int)nchild[v];
+    }
+    L.z = 0;
+    L.w = 0;
+    link[b] = L;
+    node_level[b] = (uint8_t)lvl[v];
+}
+
+// ---------------------------------------------------------- 5. moments
+
+__device__ __forceinline__ float f32_up(double x) { return __double2float_ru(x); }
+
+template <typename T> __device__ __forceinline__ T round_up(double x);
+template <> __device__ __forceinline__ float round_up<float>(double x) { return __double2float_ru(x); }
+template <> __device__ __forceinline__ double round_up<double>(double x) { return x * (1.0 + 4e-16); }
+
+template <typename T>
+__global__ void k_moments(uint32_t b0, uint32_t b1, const uint32_t* bfs2pre, const uint32_t* lvl,
+                          const uint32_t* first, const int4* link, const vec4_t<T>* sorted,
+                          const uint64_t* K, const RootBox* rb, double theta, dbl4* mom,
+                          double2* q2, vec4_t<T>* nodeA, typename V2<T>::type* nodeB, float* rcm_out)
+{
+    uint32_t b = b0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= b1) return;
+    uint32_t v = bfs2pre[b];
+    int l = (int)lvl[v];
+    double side = 2.0 * rb->half / (double)(1u << l);
+    uint64_t key = K[first[v]];
+    uint32_t ix = compact24(key) >> (kMaxDepth - l), iy = compact24(key >> 1) >> (kMaxDepth - l);
+    double cx = rb->x0 + (ix + 0.5) * side, cy = rb->y0 + (iy + 0.5) * side;
+    int4 L = link[b];
+    double M = 0, sx = 0, sy = 0, qr = 0, qi = 0;
+    if (L.y & kLeafBit) {
+        int cnt = L.y & kCountMask;
+        for (int k = 0; k < cnt; ++k) {
+            vec4_t<T> r = sorted[L.x + k];
+            double m = (double)r.z;
+            M += m;
+            sx += m * ((double)r.x - cx);
+            sy += m * ((double)r.y - cy);
+        }
+        double dx = M > 0 ? sx / M : 0.0, dy = M > 0 ? sy / M : 0.0;
+        for (int k = 0; k < cnt; ++k) {
+            vec4_t<T> r = sorted[L.x + k];
+            double m = (double)r.z;
+            double ax = (double)r.x - cx - dx, ay = (double)r.y - cy - dy;
+            qr += m * (ax * ax - ay * ay);
+            qi += m * 2.0 * ax * ay;
+        }
+        sx = dx;
+        sy = dy;
+    } else {
+        for (int k = 0; k < L.y; ++k) {
+            dbl4 c = mom[L.x + k];
+            M += c.x;
+            sx += c.x * (c.y - cx);
+            sy += c.x * (c.z - cy);
+        }
+        double dx = M > 0 ? sx / M : 0.0, dy = M > 0 ? sy / M : 0.0;
+        for (int k = 0; k < L.y; ++k) {
+            dbl4 c = mom[L.x + k];
+            double2 cq = q2[L.x + k];
+            double ax = c.y - cx - dx, ay = c.z - cy - dy;
+            qr += cq.x + c.x * (ax * ax - ay * ay);
+            qi += cq.y + c.x * 2.0 * ax * ay;
+        }
+        sx = dx;
+        sy = dy;
+    }
+    double cmx = cx + sx, cmy = cy + sy;
+    mom[b] = make_dbl4(M, cmx, cmy, side);
+    q2[b] = make_double2(qr, qi);
+    // r_cm: distance from the centre of mass to the farthest corner of the box
+    double ex = fabs(sx) + 0.5 * side, ey = fabs(sy) + 0.5 * side;
+    double rcm = sqrt(ex * ex + ey * ey);
+    double rc2 = theta > 0.0 ? (rcm / theta) * (rcm / theta) : INFINITY;
+    vec4_t<T> A;
+    A.x = (T)cmx; A.y = (T)cmy; A.z = (T)M; A.w = round_up<T>(rc2);
+    nodeA[b] = A;
+    typename V2<T>::type B;
+    B.x = (T)qr; B.y = (T)qi;
+    nodeB[b] = B;
+    rcm_out[b] = __double2float_rd(rcm);
+}
+
+// ------------------------------------------- 6. records and big lists
+
+// Full-profile records (see walk.cu for their use).
+template <typename T>
+__global__ void k_records(const vec4_t<T>* sorted, int64_t n, int kind, double shape, double gX,
+                          vec4_t<T>* e0, vec4_t<T>* e1, vec4_t<T>* leaf0)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    vec4_t<T> r = sorted[j], a;
+    a.x = r.x; a.y = r.y; a.z = r.z;
+    double p = (double)r.w;
+    if (kind == LENS_POINT) {
+        a.w = (T)0;
+    } else if (kind == LENS_GAUSS) {
+        a.w = (T)(1.0 / (2.0 * p * p));
+    } else {
+        double Rm = shape * p;
+        a.w = (T)(Rm * Rm);
+        vec4_t<T> b;
+        b.x = (T)((double)r.z / gX);
+        b.y = (T)(1.0 / p);
+        b.z = (T)0;
+        b.w = (T)0;
+        e1[j] = b;
+    }
+    e0[j] = a;
+    if (leaf0) leaf0[j] = a;
+}
+
+__device__ __forceinline__ double support_radius(int kind, double shape, double p)
+{
+    return kind == LENS_POINT ? 0.0 : shape * p;
+}
+
+template <typename T>
+__global__ void k_biglevel(const vec4_t<T>* sorted, const uint64_t* K, int64_t n, const uint8_t* Lp,
+                           const uint32_t* off, const uint32_t* pre2bfs, const float* rcm,
+                           const RootBox* rb, int kind, double shape, double theta, double lambda,
+                           uint32_t n_nodes, uint32_t* bkey, uint32_t* bval, double* r0sq,
+                           uint32_t* n_big)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s = support_radius(kind, shape, (double)sorted[j].w);
+    int L = Lp[j];
+    int lp = -1;
+    double side0 = 2.0 * rb->half;
+    for (int l = 0; l <= L; ++l) {
+        if (s > lambda * side0 / (double)(1u << l)) { lp = l; break; }
+    }
+    bval[j] = (uint32_t)j;
+    if (lp < 0) {
+        bkey[j] = n_nodes;
+        r0sq[j] = 0.0;
+        return;
+    }
+    bkey[j] = pre2bfs[node_at(K, off, j, lp)];
+    // softening radius of the listed particle inside its leaf: any cell whose
+    // multipole contains the particle and is accepted lies farther than
+    // r_cm(leaf) (1/theta - 1) from the ray (r_cm grows towards the root)
+    double r0;
+    if (theta <= 0.0) r0 = s;
+    else if (theta >= 1.0) r0 = 0.0;
+    else {
+        double rl = (double)rcm[pre2bfs[node_at(K, off, j, L)]];
+        r0 = fmin(s, rl * (1.0 / theta - 1.0));
+    }
+    r0 *= 0.999;
+    r0sq[j] = r0 * r0;
+    atomicAdd(n_big, 1u);
+}
+
+__global__ void k_bigcsr(const uint32_t* skey, int64_t n, uint32_t n_nodes, int4* link, uint32_t* end)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t k = skey[i];
+    if (k >= n_nodes) return;
+    if (i == 0 || skey[i - 1] != k) link[k].z = (int)i;
+    if (i == n - 1 || skey[i + 1] != k) end[k] = (uint32_t)(i + 1);
+}
+
+__global__ void k_bigcount(uint32_t n_nodes, int4* link, const uint32_t* end)
+{
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_nodes) return;
+    uint32_t e = end[b];
+    if (e) link[b].w = (int)(e - (uint32_t)link[b].z);
+}
+
+template <typename T>
+__global__ void k_bigrecords(const uint32_t* sval, int64_t nbig, const vec4_t<T>* e0,
+                             const vec4_t<T>* e1, const vec4_t<T>* sorted, const double* r0sq,
+                             int kind, double shape, vec4_t<T>* big0, vec4_t<T>* big1,
+                             uint32_t* big_pid, vec4_t<T>* leaf0, uint8_t* listed)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nbig) return;
+    uint32_t j = sval[i];
+    big0[i] = e0[j];
+    double s = support_radius(kind, shape, (double)sorted[j].w);
+    vec4_t<T> b;
+    b.x = (T)r0sq[j];
+    b.y = (T)(s * s);
+    if (kind == LENS_NFW) {
+        vec4_t<T> q = e1[j];
+        b.z = q.x;
+        b.w = q.y;
+    } else {
+        b.z = (T)0;
+        b.w = (T)0;
+    }
+    big1[i] = b;
+    big_pid[i] = j;
+    leaf0[j].w = -(T)r0sq[j];  // listed: a softened point inside leaves
+    listed[j] = 1;
+}
+
+__global__ void k_iota_u32(uint32_t* a, uint32_t n)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = i;
+}
+
+// ================================================================ host
+
+template <typename T>
+static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species& in, cudaStream_t s)
+{
+    using T4 = vec4_t<T>;
+    using T2 = typename V2<T>::type;
+    const int64_t n = in.n;
+    const int TB = 256;
+    const unsigned G = grid_for(n, TB);
+    // temporaries (stream ordered)
+    T4* staged = nullptr;
+    T4* sorted = nullptr;
+    unsigned long long* bbox = nullptr;
+    RootBox* rb = nullptr;
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = std::max(radix_sort_temp_bytes<uint64_t>(n), scan_temp_bytes(n + 1));
+    LENS_CUDA(cudaMallocAsync((void**)&staged, n * sizeof(T4), s));
+    LENS_CUDA(cudaMallocAsync((void**)&sorted, n * sizeof(T4), s));
+    LENS_CUDA(cudaMallocAsync((void**)&bbox, 4 * sizeof(unsigned long long), s));
+    LENS_CUDA(cudaMallocAsync((void**)&rb, sizeof(RootBox), s));
+    LENS_CUDA(cudaMallocAsync((void**)&k0, n * sizeof(uint64_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&k1, n * sizeof(uint64_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&v0, (n + 1) * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&v1, (n + 1) * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync(&tmp, tmp_bytes, s));
+
+    unsigned long long init[4] = {~0ull, 0ull, ~0ull, 0ull};
+    LENS_CUDA(cudaMemcpyAsync(bbox, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    { k_stage<T><<<G, TB, 0, s>>>(in.data, in.dtype, n, in.kind, staged, bbox, t->d_err); note_launch(); }
+    { k_root<<<1, 1, 0, s>>>(bbox, rb); note_launch(); }
+    { k_morton<T><<<G, TB, 0, s>>>(staged, n, rb, k0, v0); note_launch(); }
+    uint64_t* K;
+    uint32_t* P;
+    radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, kKeyBits, tmp, s, &K, &P);
+    { k_gather<T><<<G, TB, 0, s>>>(staged, P, n, sorted); note_launch(); }
+
+    // topology
+    uint8_t* Lp = nullptr;
+    uint32_t* off = nullptr;   // n + 1: owned-box offsets, last = n_nodes
+    LENS_CUDA(cudaMallocAsync((void**)&Lp, n, s));
+    LENS_CUDA(cudaMallocAsync((void**)&off, (n + 1) * sizeof(uint32_t), s));
+    { k_levels<<<G, TB, 0, s>>>(K, n, t->leaf_max, Lp, off); note_launch(); }
+    scan_exclusive_u32(off, off, n, off + n, tmp, s);
+    uint32_t n_nodes = 0;
+    LENS_CUDA(cudaMemcpyAsync(&n_nodes, off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    LENS_CUDA(cudaStreamSynchronize(s));
+    if (n_nodes == 0 || n_nodes > (uint32_t)kCountMask)
+        return lens_set_error(LENS_ERR_INTERNAL, "tree build: bad node count %u", n_nodes);
+    st.n_nodes = n_nodes;
+    const unsigned GN = grid_for(n_nodes, TB);
+    {
+        // the level sort and scans below run over n_nodes elements
+        size_t need = std::max(radix_sort_temp_bytes<uint32_t>(n_nodes), scan_temp_bytes((int64_t)n_nodes + 1));
+        if (need > tmp_bytes) {
+            cudaFreeAsync(tmp, s);
+            tmp_bytes = need;
+            LENS_CUDA(cudaMallocAsync(&tmp, tmp_bytes, s));
+        }
+    }
+
+    uint32_t *lvl = nullptr, *first = nullptr, *count = nullptr, *skip = nullptr;
+    uint32_t *lk1 = nullptr, *lv0 = nullptr, *lv1 = nullptr, *pre2bfs = nullptr;
+    uint32_t *level_start = nullptr, *counters = nullptr;
+    uint8_t *isleaf = nullptr, *nchild = nullptr;
+    LENS_CUDA(cudaMallocAsync((void**)&lvl, n_nodes * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&first, n_nodes * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&count, n_nodes * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&skip, n_nodes * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&lk1, n_nodes * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&lv0, n_nodes * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&lv1, n_nodes * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&pre2bfs, n_nodes * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&level_start, (kMaxDepth + 2) * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&counters, 4 * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync((void**)&isleaf, n_nodes, s));
+    LENS_CUDA(cudaMallocAsync((void**)&nchild, n_nodes, s));
+    LENS_CUDA(cudaMemsetAsync(counters, 0, 4 * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMemsetAsync(level_start, 0xff, (kMaxDepth + 2) * sizeof(uint32_t), s));
+    { k_nodes<<<G, TB, 0, s>>>(K, n, Lp, off, n_nodes, lvl, first, count, skip, isleaf); note_launch(); }
+    { k_nchild<<<GN, TB, 0, s>>>(n_nodes, isleaf, skip, nchild, t->d_err); note_launch(); }
+    // breadth-first order: stable sort of preorder ids by level
+    LENS_CUDA(cudaMemcpyAsync(lv0, lvl, n_nodes * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    uint32_t* ids = nullptr;  // values of the level sort: preorder ids
+    LENS_CUDA(cudaMallocAsync((void**)&ids, n_nodes * sizeof(uint32_t), s));
+    { k_iota_u32<<<GN, TB, 0, s>>>(ids, n_nodes); note_launch(); }
+    uint32_t *lvl_sorted, *bfs2pre;
+    radix_sort_pairs<uint32_t>(lv0, ids, lv1, lk1, n_nodes, 0, 8, tmp, s, &lvl_sorted, &bfs2pre);
+    { k_invert<<<GN, TB, 0, s>>>(bfs2pre, n_nodes, pre2bfs); note_launch(); }
+    { k_level_bounds<<<GN, TB, 0, s>>>(lvl_sorted, n_nodes, level_start); note_launch(); }
+    std::vector<uint32_t> ls(kMaxDepth + 2);
+    LENS_CUDA(cudaMemcpyAsync(ls.data(), level_start, ls.size() * sizeof(uint32_t),
+                              cudaMemcpyDeviceToHost, s));
+
+    // persistent node arrays
+    LENS_CUDA(cudaMalloc(&st.nodeA, n_nodes * sizeof(T4)));
+    LENS_CUDA(cudaMalloc(&st.nodeB, n_nodes * sizeof(T2)));
+    LENS_CUDA(cudaMalloc((void**)&st.link, n_nodes * sizeof(int4)));
+    LENS_CUDA(cudaMalloc((void**)&st.node_rcm, n_nodes * sizeof(float)));
+    LENS_CUDA(cudaMalloc((void**)&st.node_level, n_nodes));
+    LENS_CUDA(cudaMalloc((void**)&st.perm, n * sizeof(uint32_t)));
+    LENS_CUDA(cudaMalloc(&st.exact0, n * sizeof(T4)));
+    if (in.kind == LENS_NFW) LENS_CUDA(cudaMalloc(&st.exact1, n * sizeof(T4)));
+    if (in.kind != LENS_POINT) {
+        LENS_CUDA(cudaMalloc(&st.leaf0, n * sizeof(T4)));
+        LENS_CUDA(cudaMalloc((void**)&st.listed, n));
+        LENS_CUDA(cudaMemsetAsync(st.listed, 0, n, s));
+    }
+    LENS_CUDA(cudaMemcpyAsync(st.perm, P, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+
+    { k_links<<<GN, TB, 0, s>>>(n_nodes, bfs2pre, pre2bfs, lvl, first, count, isleaf, nchild, st.link,
+                              st.node_level, counters); note_launch(); }
+    LENS_CUDA(cudaStreamSynchronize(s));  // level table on the host
+    int depth = (int)ls[kMaxDepth + 1];
+    if (depth < 0 || depth > kMaxDepth)
+        return lens_set_error(LENS_ERR_INTERNAL, "tree build: bad depth %d", depth);
+    st.depth = depth;
+    st.level_start.assign(depth + 2, 0);
+    for (int l = 0; l <= depth; ++l) st.level_start[l] = ls[l];
+    st.level_start[depth + 1] = n_nodes;
+
+    dbl4* mom = nullptr;
+    double2* q2 = nullptr;
+    LENS_CUDA(cudaMallocAsync((void**)&mom, n_nodes * sizeof(dbl4), s));
+    LENS_CUDA(cudaMallocAsync((void**)&q2, n_nodes * sizeof(double2), s));
+    for (int l = depth; l >= 0; --l) {
+        uint32_t b0 = (uint32_t)st.level_start[l], b1 = (uint32_t)st.level_start[l + 1];
+        if (b1 > b0)
+            { k_moments<T><<<grid_for(b1 - b0, TB), TB, 0, s>>>(
+                b0, b1, bfs2pre, lvl, first, st.link, sorted, K, rb, t->theta, mom, q2, (T4*)st.nodeA,
+                (T2*)st.nodeB, st.node_rcm); note_launch(); }
+    }
+
+    // records
+    double gX = 1.0;
+    if (in.kind == LENS_NFW) {
+        double F, f, g;
+        // host evaluation of g(X) = ln(X/2) + F(X), X = R_max / r_s
+        double X = in.shape;
+        if (std::fabs(1.0 - X * X) < 1e-4) {
+            double u = 1.0 - X * X, sF = 0.0;
+            for (int k = 12; k >= 0; --k) sF = sF * u + 1.0 / (2 * k + 1);
+            F = sF;
+        } else if (X < 1.0) {
+            F = std::acosh(1.0 / X) / std::sqrt(1.0 - X * X);
+        } else {
+            F = std::acos(1.0 / X) / std::sqrt(X * X - 1.0);
+        }
+        g = std::log(0.5 * X) + F;
+        (void)f;
+        gX = g;
+    }
+    { k_records<T><<<G, TB, 0, s>>>(sorted, n, in.kind, in.shape, gX, (T4*)st.exact0, (T4*)st.exact1,
+                                  (T4*)st.leaf0); note_launch(); }
+
+    if (in.kind != LENS_POINT) {
+        double lambda = 0.5;
+        if (t->theta > 0.0) lambda = std::min(0.5, std::max(0.0, (1.0 / t->theta - 1.0) / std::sqrt(2.0)));
+        double* r0sq = nullptr;
+        uint32_t *bk0 = nullptr, *bk1 = nullptr, *bv0 = nullptr, *bv1 = nullptr, *end = nullptr;
+        LENS_CUDA(cudaMallocAsync((void**)&r0sq, n * sizeof(double), s));
+        LENS_CUDA(cudaMallocAsync((void**)&bk0, n * sizeof(uint32_t), s));
+        LENS_CUDA(cudaMallocAsync((void**)&bk1, n * sizeof(uint32_t), s));
+        LENS_CUDA(cudaMallocAsync((void**)&bv0, n * sizeof(uint32_t), s));
+        LENS_CUDA(cudaMallocAsync((void**)&bv1, n * sizeof(uint32_t), s));
+        LENS_CUDA(cudaMallocAsync((void**)&end, n_nodes * sizeof(uint32_t), s));
+        LENS_CUDA(cudaMemsetAsync(end, 0, n_nodes * sizeof(uint32_t), s));
+        { k_biglevel<T><<<G, TB, 0, s>>>(sorted, K, n, Lp, off, pre2bfs, st.node_rcm, rb, in.kind, in.shape,
+                                       t->theta, lambda, n_nodes, bk0, bv0, r0sq, counters + 1); note_launch(); }
+        int bits = 1;
+        while (bits < 32 && ((1ull << bits) <= (uint64_t)n_nodes)) ++bits;
+        bits = (bits + 7) & ~7;
+        uint32_t *skey, *sval;
+        radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, n, 0, bits, tmp, s, &skey, &sval);
+        { k_bigcsr<<<G, TB, 0, s>>>(skey, n, n_nodes, st.link, end); note_launch(); }
+        { k_bigcount<<<GN, TB, 0, s>>>(n_nodes, st.link, end); note_launch(); }
+        uint32_t nbig = 0;
+        LENS_CUDA(cudaMemcpyAsync(&nbig, counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        LENS_CUDA(cudaStreamSynchronize(s));
+        st.n_big = nbig;
+        if (nbig > 0) {
+            LENS_CUDA(cudaMalloc(&st.big0, nbig * sizeof(T4)));
+            LENS_CUDA(cudaMalloc(&st.big1, nbig * sizeof(T4)));
+            LENS_CUDA(cudaMalloc((void**)&st.big_pid, nbig * sizeof(uint32_t)));
+            { k_bigrecords<T><<<grid_for(nbig, TB), TB, 0, s>>>(
+                sval, nbig, (T4*)st.exact0, (T4*)st.exact1, sorted, r0sq, in.kind, in.shape, (T4*)st.big0,
+                (T4*)st.big1, st.big_pid, (T4*)st.leaf0, st.listed); note_launch(); }
+        }
+        cudaFreeAsync(r0sq, s); cudaFreeAsync(bk0, s); cudaFreeAsync(bk1, s);
+        cudaFreeAsync(bv0, s); cudaFreeAsync(bv1, s); cudaFreeAsync(end, s);
+    }
+
+    uint32_t nleaves = 0;
+    LENS_CUDA(cudaMemcpyAsync(&nleaves, counters, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    RootBox hrb;
+    LENS_CUDA(cudaMemcpyAsync(&hrb, rb, sizeof(RootBox), cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(staged, s); cudaFreeAsync(sorted, s); cudaFreeAsync(bbox, s); cudaFreeAsync(rb, s);
+    cudaFreeAsync(k0, s); cudaFreeAsync(k1, s); cudaFreeAsync(v0, s); cudaFreeAsync(v1, s);
+    cudaFreeAsync(tmp, s); cudaFreeAsync(Lp, s); cudaFreeAsync(off, s); cudaFreeAsync(lvl, s);
+    cudaFreeAsync(first, s); cudaFreeAsync(count, s); cudaFreeAsync(skip, s); cudaFreeAsync(lk1, s);
+    cudaFreeAsync(lv0, s); cudaFreeAsync(lv1, s); cudaFreeAsync(pre2bfs, s);
+    cudaFreeAsync(level_start, s); cudaFreeAsync(counters, s); cudaFreeAsync(isleaf, s);
+    cudaFreeAsync(nchild, s); cudaFreeAsync(ids, s); cudaFreeAsync(mom, s); cudaFreeAsync(q2, s);
+    LENS_CUDA(cudaStreamSynchronize(s));
+    st.n_leaves = nleaves;
+    st.root_cx = hrb.cx;
+    st.root_cy = hrb.cy;
+    st.root_half = hrb.half;
+    return LENS_OK;
+}
+
+lens_status build_species(lens_tree* t, SpeciesTree& st, const lens_species& in, cudaStream_t s)
+{
+    st.kind = in.kind;
+    st.prec = t->precision;
+    st.n = in.n;
+    st.shape = in.shape;
+    if (in.kind == LENS_GAUSS) {
+        st.Uq = 0.5 * in.shape * in.shape;
+        st.invNq = 1.0 / (-std::expm1(-st.Uq));
+    }
+    if (in.n == 0) return LENS_OK;
+    if (t->precision == LENS_PREC_FP64) return build_typed<double>(t, st, in, s);
+    return build_typed<float>(t, st, in, s);
+}
+
+void free_species(SpeciesTree& st)
+{
+    void* ptrs[] = {st.nodeA, st.nodeB, st.link, st.node_rcm, st.node_level, st.exact0, st.exact1,
+                    st.leaf0, st.big0, st.big1, st.perm, st.big_pid, st.listed};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    st = SpeciesTree();
+}
+
+}  // namespace lens

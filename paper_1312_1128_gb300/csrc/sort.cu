@@ -1,0 +1,223 @@
+// sort.cu -- device-wide exclusive scan and stable LSD radix sort of
+// (key, value) pairs, used by the tree build (Morton order, level order,
+// big-list grouping) and by ray grouping.  Hand-written; no CUB/Thrust.
+#include "sort.cuh"
+
+namespace lens {
+
+// ------------------------------------------------------------------ scan
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Exclusive scan across the block; *total (shared) receives the block sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total)
+{
+    __shared__ uint32_t warp_tot[kScanThreads / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
+        uint32_t s = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = s - t;
+        if (lane == kScanThreads / 32 - 1) *total = s;
+    }
+    __syncthreads();
+    uint32_t r = warp_tot[wid] + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void scan_reduce_kernel(const uint32_t* in, int64_t n, uint32_t* block_sums)
+{
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
+        if (idx < n) s += in[idx];
+    }
+    __shared__ uint32_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Each thread owns kScanItems consecutive elements.
+__global__ void scan_apply_kernel(const uint32_t* in, uint32_t* out, int64_t n,
+                                  const uint32_t* block_offsets, uint32_t* total_out, int64_t nblocks)
+{
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0u;
+        s += v[i];
+    }
+    __shared__ uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, &tot) + (block_offsets ? block_offsets[blockIdx.x] : 0u);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+    if (total_out && blockIdx.x == nblocks - 1 && threadIdx.x == 0)
+        *total_out = (block_offsets ? block_offsets[blockIdx.x] : 0u) + tot;
+}
+
+size_t scan_temp_bytes(int64_t n)
+{
+    size_t bytes = 0;
+    while (n > kScanTile) {
+        int64_t nb = (n + kScanTile - 1) / kScanTile;
+        bytes += ((size_t)nb * sizeof(uint32_t) + 255) & ~(size_t)255;
+        n = nb;
+    }
+    return bytes + 256;
+}
+
+// Exclusive scan of n uint32 (in-place allowed).  total (device, optional)
+// receives the sum.  tmp must hold scan_temp_bytes(n).
+void scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
+                        void* tmp, cudaStream_t s)
+{
+    if (n <= 0) {
+        if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+        return;
+    }
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 1) {
+        { scan_apply_kernel<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total, 1); note_launch(); }
+        return;
+    }
+    uint32_t* sums = (uint32_t*)tmp;
+    void* rest = (char*)tmp + (((size_t)nb * sizeof(uint32_t) + 255) & ~(size_t)255);
+    { scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums); note_launch(); }
+    scan_exclusive_u32(sums, sums, nb, nullptr, rest, s);
+    { scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums, total, nb); note_launch(); }
+}
+
+// ------------------------------------------------------------ radix sort
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadix = 256;
+
+template <typename K>
+__global__ void radix_hist_kernel(const K* keys, int64_t n, int shift, uint32_t* hist, int64_t nblocks)
+{
+    __shared__ uint32_t cnt[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) cnt[d] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&cnt[(uint32_t)(keys[idx] >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
+        hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+}
+
+// Stable scatter: element (block, r, t) precedes (block, r', t') iff
+// (r, t) < (r', t'), i.e. global index order, and equal digits keep it.
+template <typename K>
+__global__ void radix_scatter_kernel(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
+                                     int64_t n, int shift, const uint32_t* offs, int64_t nblocks)
+{
+    __shared__ uint32_t wcnt[kSortThreads / 32][kRadix];
+    __shared__ uint32_t run[kRadix];
+    __shared__ uint32_t base_off[kRadix];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+        run[d] = 0;
+        base_off[d] = offs[(int64_t)d * nblocks + blockIdx.x];
+    }
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; ++r) {
+        for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads)
+            (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
+        bool valid = idx < n;
+        K key = valid ? kin[idx] : K(0);
+        uint32_t d = valid ? ((uint32_t)(key >> shift) & 0xffu) : 0xffffffffu;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < kRadix; dd += kSortThreads) {
+            uint32_t s = run[dd];
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                uint32_t t = wcnt[w][dd];
+                wcnt[w][dd] = s;
+                s += t;
+            }
+            run[dd] = s;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = base_off[d] + wcnt[wid][d] + rank;
+            kout[pos] = key;
+            vout[pos] = vin[idx];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename K>
+size_t radix_sort_temp_bytes(int64_t n)
+{
+    int64_t nb = (n + kSortTile - 1) / kSortTile;
+    size_t hist = ((size_t)nb * kRadix * sizeof(uint32_t) + 255) & ~(size_t)255;
+    return hist + scan_temp_bytes(nb * kRadix) + 256;
+}
+
+// Sort (keys, vals) by bits [begin_bit, end_bit) of the key.  Uses the
+// alternate buffers; on return *kres / *vres point at the sorted data (one of
+// the two buffers).  n must be < 2^32.
+template <typename K>
+void radix_sort_pairs(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int begin_bit,
+                      int end_bit, void* tmp, cudaStream_t s, K** kres, uint32_t** vres)
+{
+    K* ki = k0; uint32_t* vi = v0;
+    K* ko = k1; uint32_t* vo = v1;
+    if (n > 1) {
+        int64_t nb = (n + kSortTile - 1) / kSortTile;
+        uint32_t* hist = (uint32_t*)tmp;
+        void* stmp = (char*)tmp + (((size_t)nb * kRadix * sizeof(uint32_t) + 255) & ~(size_t)255);
+        for (int b = begin_bit; b < end_bit; b += 8) {
+            { radix_hist_kernel<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ki, n, b, hist, nb); note_launch(); }
+            scan_exclusive_u32(hist, hist, nb * kRadix, nullptr, stmp, s);
+            { radix_scatter_kernel<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, b, hist, nb); note_launch(); }
+            K* tk = ki; ki = ko; ko = tk;
+            uint32_t* tv = vi; vi = vo; vo = tv;
+        }
+    }
+    *kres = ki;
+    *vres = vi;
+}
+
+template size_t radix_sort_temp_bytes<uint64_t>(int64_t);
+template size_t radix_sort_temp_bytes<uint32_t>(int64_t);
+template void radix_sort_pairs<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, int64_t, int, int,
+                                         void*, cudaStream_t, uint64_t**, uint32_t**);
+template void radix_sort_pairs<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t, int, int,
+                                         void*, cudaStream_t, uint32_t**, uint32_t**);
+
+}  // namespace lens

@@ -1,0 +1,86 @@
+// tree.cuh -- device data of a built lens and the internal entry points that
+// the C ABI (api.cu) drives.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace lens {
+
+// Link word y: particle/child count with the leaf flag in bit 30.
+constexpr int kLeafBit = 1 << 30;
+constexpr int kCountMask = kLeafBit - 1;
+
+// One species' quadtree.  Node arrays are in breadth-first order (children of
+// a node are contiguous); particle arrays in Morton order.
+struct SpeciesTree {
+    int kind = LENS_POINT;
+    int prec = LENS_PREC_FP32;
+    int64_t n = 0;
+    int64_t n_nodes = 0, n_leaves = 0, n_big = 0;
+    int depth = 0;
+    double root_cx = 0, root_cy = 0, root_half = 0;
+    double shape = 0;          // q (GAUSS) or R_max / r_s (NFW)
+    double Uq = 0, invNq = 0;  // GAUSS: q^2/2 and 1/(1 - e^{-q^2/2})
+    std::vector<int64_t> level_start;  // BFS offset of each level, depth + 2 entries
+
+    // node data (BFS order); element type T = float or double by prec
+    void* nodeA = nullptr;     // T4 {x_cm, y_cm, M, r_cut^2}
+    void* nodeB = nullptr;     // T2 {Re Q2, Im Q2}
+    int4* link = nullptr;      // {first child | first particle, count | leaf bit, big start, big count}
+    float* node_rcm = nullptr; // r_cm (distance from the centre of mass to the farthest corner)
+    uint8_t* node_level = nullptr;
+    // particles (Morton order)
+    void* exact0 = nullptr;    // T4 full-profile records (see walk)
+    void* exact1 = nullptr;    // T4 second record (NFW only)
+    void* leaf0 = nullptr;     // T4 leaf records: listed particles marked as softened points
+    void* big0 = nullptr;      // T4 big-list records (full profile)
+    void* big1 = nullptr;      // T4 {r0^2, s^2, A, B}
+    uint32_t* perm = nullptr;  // Morton position -> input index
+    uint32_t* big_pid = nullptr;  // big entry -> Morton position
+    uint8_t* listed = nullptr;    // per Morton position: 1 if in a big list
+};
+
+struct HaloDev {
+    int32_t kind, pad;
+    double x, y, m, p0, p1;
+    double c0, c1, c2;  // derived constants (GAUSS: c, Uq, invNq; NFW: A, B, R^2)
+};
+
+struct DevScratch {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct GraphEntry;
+
+}  // namespace lens
+
+struct lens_tree {
+    int precision = LENS_PREC_FP32;
+    double theta = 0.1;
+    int leaf_max = 5;
+    int group_rays = 32;
+    std::vector<lens::SpeciesTree> sp;
+    std::vector<lens_halo> halos_host;
+    lens::HaloDev* halos = nullptr;  // device copy
+    int64_t n_halos = 0;
+    uint32_t* d_err = nullptr;       // device error word
+    // shoot scratch (grown on demand)
+    lens::DevScratch ray_scratch;
+    int64_t ray_cap = 0, batch_cap = 0;
+    int num_sms = 0;
+    int device = 0;
+    std::vector<lens::GraphEntry*> graphs;
+    unsigned long long* d_stats = nullptr;  // 8 walk counters (LENS_COUNT)
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // LENS_TIMING: start, grouped, walked
+    bool timed = false;
+};
+
+namespace lens {
+
+lens_status build_species(lens_tree* t, SpeciesTree& st, const lens_species& in, cudaStream_t s);
+void free_species(SpeciesTree& st);
+
+}  // namespace lens

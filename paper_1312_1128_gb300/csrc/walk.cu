@@ -1,0 +1,849 @@
+// walk.cu -- ray grouping and the warp-cooperative tree walk (Sec. 3.2 tree
+// walk, Sec. 3.3 ray-parallel evaluation), plus the direct sum (Sec. 5.1,
+// theta_force = 0) and the analytic components evaluated for every ray.
+//
+// One warp owns a group of up to 32*R spatially sorted rays and walks the tree
+// once for the whole group:
+//   - up to 32 candidate boxes are taken from the warp's stack at a time, one
+//     per lane, and the MAC |x - x_cm| > r_cut is applied to the group's
+//     bounding box (accepting a box only if every ray of the group would);
+//   - accepted boxes go to a far buffer (monopole + quadrupole), opened leaves
+//     to a near buffer of particle records, opened internal boxes push their
+//     children; the big list of every visited box is scanned and the
+//     particles whose support reaches the group's box go to a big buffer;
+//   - full buffers are evaluated by all lanes, each lane for its own rays,
+//     with the records broadcast from shared memory; partial sums are folded
+//     into Neumaier-compensated totals after every buffer.
+// Big-particle semantics (Sec. 3.2): every box's moments include all its
+// particles as point masses.  A listed particle counts inside leaves as a
+// point mass softened within r0 = min(s, r_cm(leaf)(1/theta - 1)), which is
+// exactly the point mass wherever a cell containing it can be accepted, and
+// its box's list adds (full profile - softened point) for rays inside its
+// support s.  The softening removes the cancellation of a huge point term
+// against its correction when a ray passes close to a listed particle.
+#include <algorithm>
+
+#include "profiles.cuh"
+#include "sort.cuh"
+#include "walk.cuh"
+
+namespace lens {
+
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+template <typename T> using v2_t = typename V2<T>::type;
+
+// ------------------------------------------------------------ grouping
+
+__device__ __forceinline__ int batch_of(const int64_t* boff, int nb, int64_t i)
+{
+    int lo = 0, hi = nb;  // boff[lo] <= i < boff[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (boff[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double ray_offset(const void* p, int dtype, int64_t i)
+{
+    return dtype == LENS_F32 ? (double)((const float*)p)[i] : ((const double*)p)[i];
+}
+
+__global__ void k_ray_bbox(const int64_t* boff, int nb, const double* borig, const void* dx,
+                           const void* dy, int dtype, int64_t n, unsigned long long* bbox)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = i < n;
+    int b = valid ? batch_of(boff, nb, i) : -1;
+    double px = 0, py = 0;
+    if (valid) {
+        px = borig[2 * b] + ray_offset(dx, dtype, i);
+        py = borig[2 * b + 1] + ray_offset(dy, dtype, i);
+    }
+    unsigned full = 0xffffffffu;
+    int b0 = __shfl_sync(full, b, 0);
+    bool uniform = __all_sync(full, valid && b == b0);
+    unsigned long long x0 = dbl_to_ordered(px), x1 = x0, y0 = dbl_to_ordered(py), y1 = y0;
+    if (uniform) {
+        for (int o = 16; o; o >>= 1) {
+            x0 = min(x0, __shfl_xor_sync(full, x0, o));
+            x1 = max(x1, __shfl_xor_sync(full, x1, o));
+            y0 = min(y0, __shfl_xor_sync(full, y0, o));
+            y1 = max(y1, __shfl_xor_sync(full, y1, o));
+        }
+        if ((threadIdx.x & 31) != 0) return;
+    } else if (!valid) {
+        return;
+    }
+    atomicMin(&bbox[4 * b + 0], x0);
+    atomicMax(&bbox[4 * b + 1], x1);
+    atomicMin(&bbox[4 * b + 2], y0);
+    atomicMax(&bbox[4 * b + 3], y1);
+}
+
+__global__ void k_bbox_init(unsigned long long* bbox, int64_t nb)
+{
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    bbox[4 * b] = ~0ull;
+    bbox[4 * b + 1] = 0ull;
+    bbox[4 * b + 2] = ~0ull;
+    bbox[4 * b + 3] = 0ull;
+}
+
+__device__ __forceinline__ uint32_t spread16(uint32_t x)
+{
+    x &= 0xffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+__global__ void k_ray_keys(const int64_t* boff, int nb, const double* borig, const void* dx,
+                           const void* dy, int dtype, int64_t n, const unsigned long long* bbox,
+                           uint64_t* keys, uint32_t* vals)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b = batch_of(boff, nb, i);
+    double px = borig[2 * b] + ray_offset(dx, dtype, i);
+    double py = borig[2 * b + 1] + ray_offset(dy, dtype, i);
+    double x0 = ordered_to_dbl(bbox[4 * b]), x1 = ordered_to_dbl(bbox[4 * b + 1]);
+    double y0 = ordered_to_dbl(bbox[4 * b + 2]), y1 = ordered_to_dbl(bbox[4 * b + 3]);
+    double ext = fmax(x1 - x0, y1 - y0);
+    double inv = ext > 0 ? 65535.99 / ext : 0.0;
+    uint32_t qx = (uint32_t)fmin(fmax((px - x0) * inv, 0.0), 65535.0);
+    uint32_t qy = (uint32_t)fmin(fmax((py - y0) * inv, 0.0), 65535.0);
+    keys[i] = ((uint64_t)b << 32) | (uint64_t)(spread16(qx) | (spread16(qy) << 1));
+    vals[i] = (uint32_t)i;
+}
+
+template <typename T, int R>
+__global__ void k_groups(int64_t n_groups, const int64_t* boff, const uint32_t* gfirst, int nb,
+                         const double* borig, const void* dx, const void* dy, int dtype,
+                         const uint32_t* svals, v2_t<T>* gH, vec4_t<T>* gbox, uint2* grange,
+                         v2_t<T>* ray_l, uint32_t* ray_idx)
+{
+    const unsigned full = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= n_groups) return;
+    int lo = 0, hi = nb;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if ((int64_t)gfirst[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    const int b = lo;
+    const int GR = 32 * R;
+    int64_t first = boff[b] + (g - (int64_t)gfirst[b]) * GR;
+    int64_t cnt64 = boff[b + 1] - first;
+    int count = (int)(cnt64 < GR ? cnt64 : GR);
+    double px[R], py[R];
+    uint32_t idx[R];
+    bool v[R];
+    double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int k = r * 32 + lane;
+        v[r] = k < count;
+        idx[r] = 0;
+        px[r] = py[r] = 0.0;
+        if (v[r]) {
+            idx[r] = svals[first + k];
+            px[r] = borig[2 * b] + ray_offset(dx, dtype, idx[r]);
+            py[r] = borig[2 * b + 1] + ray_offset(dy, dtype, idx[r]);
+            xmin = fmin(xmin, px[r]); xmax = fmax(xmax, px[r]);
+            ymin = fmin(ymin, py[r]); ymax = fmax(ymax, py[r]);
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        xmin = fmin(xmin, __shfl_xor_sync(full, xmin, o));
+        xmax = fmax(xmax, __shfl_xor_sync(full, xmax, o));
+        ymin = fmin(ymin, __shfl_xor_sync(full, ymin, o));
+        ymax = fmax(ymax, __shfl_xor_sync(full, ymax, o));
+    }
+    T Hx = (T)(0.5 * (xmin + xmax)), Hy = (T)(0.5 * (ymin + ymax));
+    T lxmin = (T)INFINITY, lxmax = (T)-INFINITY, lymin = (T)INFINITY, lymax = (T)-INFINITY;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (!v[r]) continue;
+        T lx = (T)(px[r] - (double)Hx), ly = (T)(py[r] - (double)Hy);
+        lxmin = fmin(lxmin, lx); lxmax = fmax(lxmax, lx);
+        lymin = fmin(lymin, ly); lymax = fmax(lymax, ly);
+        v2_t<T> l;
+        l.x = lx;
+        l.y = ly;
+        ray_l[first + r * 32 + lane] = l;
+        ray_idx[first + r * 32 + lane] = idx[r];
+    }
+    for (int o = 16; o; o >>= 1) {
+        lxmin = fmin(lxmin, __shfl_xor_sync(full, lxmin, o));
+        lxmax = fmax(lxmax, __shfl_xor_sync(full, lxmax, o));
+        lymin = fmin(lymin, __shfl_xor_sync(full, lymin, o));
+        lymax = fmax(lymax, __shfl_xor_sync(full, lymax, o));
+    }
+    if (lane == 0) {
+        T cx = T(0.5) * (lxmin + lxmax), cy = T(0.5) * (lymin + lymax);
+        T hx = fmax(lxmax - cx, cx - lxmin), hy = fmax(lymax - cy, cy - lymin);
+        // inflate so that every ray is inside after rounding
+        hx = hx * T(1.0 + 1e-5) + T(1e-30);
+        hy = hy * T(1.0 + 1e-5) + T(1e-30);
+        v2_t<T> H;
+        H.x = Hx;
+        H.y = Hy;
+        gH[g] = H;
+        vec4_t<T> bx;
+        bx.x = cx; bx.y = cy; bx.z = hx; bx.w = hy;
+        gbox[g] = bx;
+        grange[g] = make_uint2((uint32_t)first, (uint32_t)count);
+    }
+}
+
+// ---------------------------------------------------------------- walk
+
+template <typename T> struct WalkParams {
+    const vec4_t<T>* nodeA;
+    const v2_t<T>* nodeB;
+    const int4* link;
+    const vec4_t<T>* leaf0;   // near records (listed particles marked)
+    const vec4_t<T>* leaf1;   // NFW second record
+    const vec4_t<T>* big0;
+    const vec4_t<T>* big1;
+    int64_t n_part;
+    T Uq, invNq;
+    const v2_t<T>* gH;
+    const vec4_t<T>* gbox;
+    const uint2* grange;
+    const v2_t<T>* ray_l;
+    const uint32_t* ray_idx;
+    int64_t n_groups;
+    const HaloDev* halos;
+    int n_halos;
+    T* out[5];
+    int accumulate;
+    uint32_t* counter;
+    int* stack;
+    uint32_t* err;
+    unsigned long long* stats;  // optional walk counters
+};
+
+template <int KIND, typename T> struct WalkShared {
+    T fdx[kFarCap], fdy[kFarCap], fM[kFarCap], fqr[kFarCap], fqi[kFarCap];
+    vec4_t<T> n0[kNearCap];
+    vec4_t<T> n1[KIND == LENS_NFW ? kNearCap : 1];
+    vec4_t<T> b0[KIND == LENS_POINT ? 1 : kBigCap];
+    vec4_t<T> b1[KIND == LENS_POINT ? 1 : kBigCap];
+    int rs_off[33];
+    int rs_first[32];
+};
+
+template <int KIND, typename T, int R, bool AO> struct WalkCtx {
+    const WalkParams<T>& P;
+    WalkShared<KIND, T>& S;
+    T lx[R], ly[R];
+    Acc5<T> part[R];
+    Comp5<T> tot[R];
+    v2_t<T> H;
+    vec4_t<T> box;
+
+    LENS_DEV WalkCtx(const WalkParams<T>& p, WalkShared<KIND, T>& s) : P(p), S(s) {}
+
+    LENS_DEV void fold()
+    {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            tot[r].add(part[r]);
+            part[r].zero();
+        }
+    }
+
+    LENS_DEV void flush_far(int nf)
+    {
+        for (int c = 0; c < nf; ++c) {
+            T dx = S.fdx[c], dy = S.fdy[c], M = S.fM[c], qr = S.fqr[c], qi = S.fqi[c];
+#pragma unroll
+            for (int r = 0; r < R; ++r) cell_terms<T, AO>(part[r], lx[r] - dx, ly[r] - dy, M, qr, qi);
+        }
+        fold();
+    }
+
+    // Leaf particles: full profile unless marked as a listed (softened) point.
+    LENS_DEV void flush_near(int nn)
+    {
+        for (int i = 0; i < nn; ++i) {
+            vec4_t<T> q = S.n0[i];
+            vec4_t<T> q1;
+            if constexpr (KIND == LENS_NFW) q1 = S.n1[i];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                T wx = lx[r] - q.x, wy = ly[r] - q.y;
+                T r2 = fma(wx, wx, wy * wy);
+                T kb, kap = T(0), Dp;
+                if (KIND == LENS_POINT) {
+                    point_terms(q.z, r2, kb, Dp);
+                } else if (KIND == LENS_GAUSS) {
+                    if (q.w > T(0)) gauss_terms(q.z, q.w, r2, P.Uq, P.invNq, kb, kap, Dp);
+                    else point_terms(q.z, fmax(r2, -q.w), kb, Dp);
+                } else {
+                    if (q.w > T(0)) nfw_terms(q.z, q.w, q1.x, q1.y, r2, kb, kap, Dp);
+                    else point_terms(q.z, fmax(r2, -q.w), kb, Dp);
+                }
+                part[r].template radial<AO>(wx, wy, kb, kap, Dp);
+            }
+        }
+        fold();
+    }
+
+    // Big-list corrections: (full profile - softened point) inside the support.
+    LENS_DEV void flush_big(int nb)
+    {
+        for (int i = 0; i < nb; ++i) {
+            vec4_t<T> q = S.b0[i], q1 = S.b1[i];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                T wx = lx[r] - q.x, wy = ly[r] - q.y;
+                T r2 = fma(wx, wx, wy * wy);
+                if (r2 < q1.y) {
+                    T kb, kap, Dp, kbp, Dpp;
+                    if (KIND == LENS_GAUSS) gauss_terms(q.z, q.w, r2, P.Uq, P.invNq, kb, kap, Dp);
+                    else nfw_terms(q.z, q.w, q1.z, q1.w, r2, kb, kap, Dp);
+                    point_terms(q.z, fmax(r2, q1.x), kbp, Dpp);
+                    part[r].template radial<AO>(wx, wy, kb - kbp, kap, Dp - Dpp);
+                }
+            }
+        }
+        fold();
+    }
+
+    // Analytic components for every ray (Sec. 3.2 analytic models, App. B).
+    LENS_DEV void halos()
+    {
+        for (int h = 0; h < P.n_halos; ++h) {
+            const HaloDev& hd = P.halos[h];
+            T hx = (T)((double)H.x - hd.x), hy = (T)((double)H.y - hd.y);
+            int kind = hd.kind;
+            T m = (T)hd.m;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                T wx = lx[r] + hx, wy = ly[r] + hy;
+                T r2 = fma(wx, wx, wy * wy);
+                T kb = T(0), kap = T(0), Dp = T(0);
+                if (kind == LENS_POINT) {
+                    point_terms(m, r2, kb, Dp);
+                } else if (kind == LENS_GAUSS) {
+                    gauss_terms(m, (T)hd.c0, r2, (T)hd.c1, (T)hd.c2, kb, kap, Dp);
+                } else if (kind == LENS_NFW) {
+                    nfw_terms(m, (T)hd.c2, (T)hd.c0, (T)hd.c1, r2, kb, kap, Dp);
+                } else if (kind == LENS_SIS) {
+                    if (r2 > T(0)) {
+                        T rr = sqrt(r2), re = (T)hd.p0;
+                        kb = re / rr;
+                        kap = T(0.5) * kb;
+                        Dp = kap / r2;
+                    }
+                } else {  // uniform disk
+                    T R2 = (T)hd.c2;
+                    if (r2 < R2) {
+                        kb = m / R2;
+                        kap = kb;
+                        Dp = T(0);
+                    } else {
+                        point_terms(m, r2, kb, Dp);
+                    }
+                }
+                part[r].template radial<AO>(wx, wy, kb, kap, Dp);
+            }
+        }
+        fold();
+    }
+};
+
+// Append, in order, the items of up to 32 index ranges (one per lane) to a
+// shared buffer, flushing it whenever fewer than 32 slots remain.
+template <int KIND, typename T, int R, bool AO, bool BIG>
+LENS_DEV void append_ranges(WalkCtx<KIND, T, R, AO>& C, int cnt, int first, int& nbuf,
+                            const vec4_t<T>* src0, const vec4_t<T>* src1, int& n_seen, int& n_kept)
+{
+    const unsigned full = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    int tot;
+    int off = warp_exclusive_scan(cnt, &tot);
+    if (tot == 0) return;
+    n_seen += tot;
+    WalkShared<KIND, T>& S = C.S;
+    S.rs_off[lane] = off;
+    S.rs_first[lane] = first;
+    if (lane == 31) S.rs_off[32] = tot;
+    __syncwarp();
+    const int cap = BIG ? kBigCap : kNearCap;
+    for (int base = 0; base < tot; base += 32) {
+        if (nbuf + 32 > cap) {
+            if constexpr (BIG) C.flush_big(nbuf);
+            else C.flush_near(nbuf);
+            nbuf = 0;
+            __syncwarp();
+        }
+        int i = base + lane;
+        bool have = i < tot;
+        vec4_t<T> q0, q1;
+        bool keep = false;
+        if (have) {
+            int lo = 0, hi = 32;  // last lane o with rs_off[o] <= i
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (S.rs_off[mid] <= i) lo = mid;
+                else hi = mid;
+            }
+            int p = S.rs_first[lo] + (i - S.rs_off[lo]);
+            q0 = src0[p];
+            if constexpr (BIG || KIND == LENS_NFW) q1 = src1[p];
+            q0.x -= C.H.x;
+            q0.y -= C.H.y;
+            keep = true;
+            if constexpr (BIG) {
+                // does the support reach the group's bounding box?
+                T ex = fmax(fabs(q0.x - C.box.x) - C.box.z, T(0));
+                T ey = fmax(fabs(q0.y - C.box.y) - C.box.w, T(0));
+                keep = fma(ex, ex, ey * ey) < q1.y;
+            }
+        }
+        unsigned ball = __ballot_sync(full, keep);
+        if (keep) {
+            int slot = nbuf + __popc(ball & ((1u << lane) - 1u));
+            if constexpr (BIG) {
+                S.b0[slot] = q0;
+                S.b1[slot] = q1;
+            } else {
+                S.n0[slot] = q0;
+                if constexpr (KIND == LENS_NFW) S.n1[slot] = q1;
+            }
+        }
+        nbuf += __popc(ball);
+        n_kept += __popc(ball);
+        __syncwarp();
+    }
+}
+
+template <int KIND, typename T, int R, bool AO, bool DIRECT>
+__global__ void __launch_bounds__(kWalkWarps * 32)
+walk_kernel(WalkParams<T> P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned full = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WalkShared<KIND, T>& S = reinterpret_cast<WalkShared<KIND, T>*>(smem_raw)[warp];
+    int* stack = P.stack + ((int64_t)blockIdx.x * kWalkWarps + warp) * kStackCap;
+    WalkCtx<KIND, T, R, AO> C(P, S);
+    uint32_t ridx[R];
+    bool rv[R];
+
+    for (;;) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(P.counter, 1u);
+        g = __shfl_sync(full, g, 0);
+        if ((int64_t)g >= P.n_groups) break;
+        C.H = P.gH[g];
+        C.box = P.gbox[g];
+        uint2 rg = P.grange[g];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int k = r * 32 + lane;
+            rv[r] = k < (int)rg.y;
+            if (rv[r]) {
+                v2_t<T> l = P.ray_l[rg.x + k];
+                C.lx[r] = l.x;
+                C.ly[r] = l.y;
+                ridx[r] = P.ray_idx[rg.x + k];
+            } else {
+                C.lx[r] = C.box.x;
+                C.ly[r] = C.box.y;
+                ridx[r] = 0;
+            }
+            C.part[r].zero();
+            C.tot[r].zero();
+        }
+
+        int c_vis = 0, c_acc = 0, c_near = 0, c_bigs = 0, c_bigk = 0, c_dummy = 0;
+        if (KIND >= 0 && P.n_part > 0) {
+            int nn = 0, nb = 0;
+            if (DIRECT) {
+                // every particle with its full profile
+                for (int64_t base = 0; base < P.n_part; base += 0x40000000) {
+                    int64_t rem = P.n_part - base;
+                    int c = (int)(rem < 0x40000000 ? rem : 0x40000000);
+                    append_ranges<KIND, T, R, AO, false>(C, lane == 0 ? c : 0, (int)base, nn, P.leaf0,
+                                                          P.leaf1, c_near, c_dummy);
+                }
+                C.flush_near(nn);
+            } else {
+                int nf = 0, sp = 1;
+                if (lane == 0) stack[0] = 0;
+                __syncwarp();
+                while (sp > 0) {
+                    int k = sp < 32 ? sp : 32;
+                    sp -= k;
+                    int v = lane < k ? stack[sp + lane] : -1;
+                    __syncwarp();
+                    bool valid = v >= 0, acc = false, leaf = false, open = false;
+                    vec4_t<T> A;
+                    int4 Lk = make_int4(0, 0, 0, 0);
+                    T dxv = T(0), dyv = T(0);
+                    if (valid) {
+                        A = P.nodeA[v];
+                        Lk = P.link[v];
+                        dxv = A.x - C.H.x;
+                        dyv = A.y - C.H.y;
+                        T ex = fmax(fabs(dxv - C.box.x) - C.box.z, T(0));
+                        T ey = fmax(fabs(dyv - C.box.y) - C.box.w, T(0));
+                        acc = fma(ex, ex, ey * ey) > A.w;
+                        leaf = !acc && (Lk.y & kLeafBit);
+                        open = !acc && !leaf;
+                    }
+                    unsigned ball = __ballot_sync(full, acc);
+                    if (acc) {
+                        int pos = nf + __popc(ball & ((1u << lane) - 1u));
+                        v2_t<T> Q = P.nodeB[v];
+                        S.fdx[pos] = dxv;
+                        S.fdy[pos] = dyv;
+                        S.fM[pos] = A.z;
+                        S.fqr[pos] = Q.x;
+                        S.fqi[pos] = Q.y;
+                    }
+                    nf += __popc(ball);
+                    c_vis += k;
+                    c_acc += __popc(ball);
+                    int nc = open ? Lk.y : 0;
+                    int totc;
+                    int offc = warp_exclusive_scan(nc, &totc);
+                    if (sp + totc > kStackCap) {
+                        if (lane == 0) atomicOr(P.err, DERR_STACK_OVERFLOW);
+                        break;
+                    }
+                    for (int c = 0; c < nc; ++c) stack[sp + offc + c] = Lk.x + c;
+                    sp += totc;
+                    append_ranges<KIND, T, R, AO, false>(C, leaf ? (Lk.y & kCountMask) : 0, Lk.x, nn,
+                                                          P.leaf0, P.leaf1, c_near, c_dummy);
+                    if constexpr (KIND != LENS_POINT)
+                        append_ranges<KIND, T, R, AO, true>(C, valid ? Lk.w : 0, Lk.z, nb, P.big0,
+                                                             P.big1, c_bigs, c_bigk);
+                    __syncwarp();
+                    if (nf >= 32) {
+                        C.flush_far(nf);
+                        nf = 0;
+                        __syncwarp();
+                    }
+                }
+                C.flush_far(nf);
+                C.flush_near(nn);
+                if constexpr (KIND != LENS_POINT) C.flush_big(nb);
+            }
+        }
+        if (P.n_halos > 0) C.halos();
+        if (P.stats && lane == 0) {
+            unsigned long long nr = rg.y;
+            atomicAdd(&P.stats[0], 1ull);
+            atomicAdd(&P.stats[1], (unsigned long long)c_vis);
+            atomicAdd(&P.stats[2], (unsigned long long)c_acc);
+            atomicAdd(&P.stats[3], (unsigned long long)c_near);
+            atomicAdd(&P.stats[4], (unsigned long long)c_bigs);
+            atomicAdd(&P.stats[5], (unsigned long long)c_bigk);
+            atomicAdd(&P.stats[6], nr * (unsigned long long)(c_acc + c_near + c_bigk));
+        }
+
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (!rv[r]) continue;
+            uint32_t i = ridx[r];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (AO && q >= 2) break;
+                T val = C.tot[r].get(q);
+                if (P.accumulate) val += P.out[q][i];
+                P.out[q][i] = val;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------- host side
+
+struct Layout {
+    size_t boff, borig, gfirst, bbox, k0, k1, v0, v1, tmp, rl, ridx, gH, gbox, grange, counter,
+        stack, total;
+};
+
+static Layout make_layout(int64_t n, int64_t nb, int64_t slots)
+{
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    Layout L{};
+    int64_t ng = n / 32 + nb + 1;
+    size_t o = 0;
+    L.boff = o; o += al((nb + 1) * sizeof(int64_t));
+    L.borig = o; o += al(nb * 2 * sizeof(double));
+    L.gfirst = o; o += al((nb + 1) * sizeof(uint32_t));
+    L.bbox = o; o += al(nb * 4 * sizeof(unsigned long long));
+    L.k0 = o; o += al(n * sizeof(uint64_t));
+    L.k1 = o; o += al(n * sizeof(uint64_t));
+    L.v0 = o; o += al(n * sizeof(uint32_t));
+    L.v1 = o; o += al(n * sizeof(uint32_t));
+    L.tmp = o; o += al(radix_sort_temp_bytes<uint64_t>(n));
+    L.rl = o; o += al(n * 2 * sizeof(double));
+    L.ridx = o; o += al(n * sizeof(uint32_t));
+    L.gH = o; o += al(ng * 2 * sizeof(double));
+    L.gbox = o; o += al(ng * 4 * sizeof(double));
+    L.grange = o; o += al(ng * sizeof(uint2));
+    L.counter = o; o += al(64 * sizeof(uint32_t));
+    L.stack = o; o += al((size_t)slots * kStackCap * sizeof(int));
+    L.total = o;
+    return L;
+}
+
+template <int KIND, typename T, int R, bool AO, bool DIRECT>
+static int walk_blocks_per_sm()
+{
+    static int cached = -1;
+    if (cached < 0) {
+        size_t smem = kWalkWarps * sizeof(WalkShared<KIND, T>);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(walk_kernel<KIND, T, R, AO, DIRECT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<KIND, T, R, AO, DIRECT>,
+                                                      kWalkWarps * 32, smem);
+        cached = nb > 0 ? nb : 1;
+    }
+    return cached;
+}
+
+void free_graphs(lens_tree* t);
+
+static int max_slots(lens_tree* t) { return t->num_sms * 16 * kWalkWarps; }
+
+lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb)
+{
+    if (n <= t->ray_cap && nb <= t->batch_cap && t->ray_scratch.ptr) return LENS_OK;
+    int64_t nn = std::max(n, t->ray_cap), bb = std::max(nb, t->batch_cap);
+    Layout L = make_layout(nn, bb, max_slots(t));
+    free_graphs(t);  // captured graphs point into the old scratch
+    if (t->ray_scratch.ptr) cudaFree(t->ray_scratch.ptr);
+    t->ray_scratch.ptr = nullptr;
+    t->ray_cap = t->batch_cap = 0;
+    cudaError_t e = cudaMalloc(&t->ray_scratch.ptr, L.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return lens_set_error(LENS_ERR_OOM, "cannot allocate %zu bytes of ray scratch", L.total);
+    }
+    t->ray_scratch.bytes = L.total;
+    t->ray_cap = nn;
+    t->batch_cap = bb;
+    return LENS_OK;
+}
+
+template <int KIND, typename T, int R, bool AO, bool DIRECT>
+static void launch_one(const WalkParams<T>& P, int num_sms, cudaStream_t s)
+{
+    size_t smem = kWalkWarps * sizeof(WalkShared<KIND, T>);
+    int bps = walk_blocks_per_sm<KIND, T, R, AO, DIRECT>();
+    if (bps > 16) bps = 16;  // stack slots are allocated for 16 blocks per SM
+    int grid = num_sms * bps;
+    { walk_kernel<KIND, T, R, AO, DIRECT><<<grid, kWalkWarps * 32, smem, s>>>(P); note_launch(); }
+}
+
+template <typename T, int R, bool AO, bool DIRECT>
+static void launch_kind(int kind, const WalkParams<T>& P, int num_sms, cudaStream_t s)
+{
+    if (kind == LENS_POINT) launch_one<LENS_POINT, T, R, AO, DIRECT>(P, num_sms, s);
+    else if (kind == LENS_GAUSS) launch_one<LENS_GAUSS, T, R, AO, DIRECT>(P, num_sms, s);
+    else launch_one<LENS_NFW, T, R, AO, DIRECT>(P, num_sms, s);
+}
+
+template <typename T, int R>
+static void launch_dispatch(int kind, bool ao, bool direct, const WalkParams<T>& P, int num_sms,
+                            cudaStream_t s)
+{
+    if (direct) {
+        if (ao) launch_kind<T, R, true, true>(kind, P, num_sms, s);
+        else launch_kind<T, R, false, true>(kind, P, num_sms, s);
+    } else {
+        if (ao) launch_kind<T, R, true, false>(kind, P, num_sms, s);
+        else launch_kind<T, R, false, false>(kind, P, num_sms, s);
+    }
+}
+
+// Host-side plan of one shoot call: sizes fixed by the batch table.
+struct ShootPlan {
+    int64_t n = 0, nb = 0;
+    uint64_t ng = 0;
+    int R = 1;
+};
+
+static int rays_per_lane(const lens_tree* t)
+{
+    return (t->precision == LENS_PREC_FP64 || t->group_rays <= 32) ? 1 : 2;
+}
+
+// Copy the batch table to the device (stream ordered) and size the groups.
+lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig,
+                           cudaStream_t s, ShootPlan* plan)
+{
+    const int64_t n = h_off[nb];
+    const int R = rays_per_lane(t);
+    const int GR = 32 * R;
+    LENS_TRY(reserve_rays(t, n, nb));
+    Layout L = make_layout(t->ray_cap, t->batch_cap, max_slots(t));
+    char* base = (char*)t->ray_scratch.ptr;
+    // pageable host copies: the driver stages them before returning
+    std::vector<uint32_t> gf(nb + 1);
+    uint64_t ng = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        gf[b] = (uint32_t)ng;
+        ng += (uint64_t)((h_off[b + 1] - h_off[b] + GR - 1) / GR);
+    }
+    gf[nb] = (uint32_t)ng;
+    LENS_CUDA(cudaMemcpyAsync(base + L.boff, h_off, (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    LENS_CUDA(cudaMemcpyAsync(base + L.borig, h_orig, nb * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    LENS_CUDA(cudaMemcpyAsync(base + L.gfirst, gf.data(), (nb + 1) * sizeof(uint32_t),
+                              cudaMemcpyHostToDevice, s));
+    plan->n = n;
+    plan->nb = nb;
+    plan->ng = ng;
+    plan->R = R;
+    return LENS_OK;
+}
+
+// Enqueue the kernels of one shoot call (no allocation, no host sync: safe
+// to capture into a CUDA graph).
+template <typename T>
+static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void* dx, const void* dy,
+                                 int dtype, void* const out[5], int flags, cudaStream_t s)
+{
+    using T4 = vec4_t<T>;
+    using T2 = v2_t<T>;
+    const int64_t n = plan.n, nb = plan.nb;
+    const uint64_t ng = plan.ng;
+    const int R = plan.R;
+    Layout L = make_layout(t->ray_cap, t->batch_cap, max_slots(t));
+    char* base = (char*)t->ray_scratch.ptr;
+    int64_t* d_boff = (int64_t*)(base + L.boff);
+    double* d_borig = (double*)(base + L.borig);
+    uint32_t* d_gfirst = (uint32_t*)(base + L.gfirst);
+    unsigned long long* d_bbox = (unsigned long long*)(base + L.bbox);
+    T2* ray_l = (T2*)(base + L.rl);
+    uint32_t* ray_idx = (uint32_t*)(base + L.ridx);
+    T2* gH = (T2*)(base + L.gH);
+    T4* gbox = (T4*)(base + L.gbox);
+    uint2* grange = (uint2*)(base + L.grange);
+    uint32_t* counter = (uint32_t*)(base + L.counter);
+    int* stack = (int*)(base + L.stack);
+    const bool timing = (flags & LENS_TIMING) != 0;
+    if (timing) {
+        for (int i = 0; i < 3; ++i)
+            if (!t->ev[i]) LENS_CUDA(cudaEventCreate(&t->ev[i]));
+        LENS_CUDA(cudaEventRecord(t->ev[0], s));
+    }
+    if (n > 0) {
+        const int TB = 256;
+        { k_bbox_init<<<grid_for(nb, 128), 128, 0, s>>>(d_bbox, nb); note_launch(); }
+        { k_ray_bbox<<<grid_for(n, TB), TB, 0, s>>>(d_boff, (int)nb, d_borig, dx, dy, dtype, n, d_bbox); note_launch(); }
+        uint64_t* k0 = (uint64_t*)(base + L.k0);
+        uint64_t* k1 = (uint64_t*)(base + L.k1);
+        uint32_t* v0 = (uint32_t*)(base + L.v0);
+        uint32_t* v1 = (uint32_t*)(base + L.v1);
+        { k_ray_keys<<<grid_for(n, TB), TB, 0, s>>>(d_boff, (int)nb, d_borig, dx, dy, dtype, n, d_bbox, k0, v0); note_launch(); }
+        int bbits = 0;
+        while ((1ll << bbits) < nb) ++bbits;
+        int end_bit = (32 + bbits + 7) & ~7;
+        uint64_t* sk;
+        uint32_t* sv;
+        radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, end_bit, base + L.tmp, s, &sk, &sv);
+        unsigned gg = grid_for((int64_t)ng * 32, TB);
+        if (R == 1)
+            { k_groups<T, 1><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
+                                             sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
+        else
+            { k_groups<T, 2><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
+                                             sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
+    }
+
+    if (timing) LENS_CUDA(cudaEventRecord(t->ev[1], s));
+    WalkParams<T> P{};
+    P.stats = (flags & LENS_COUNT) ? t->d_stats : nullptr;
+    P.gH = gH; P.gbox = gbox; P.grange = grange; P.ray_l = ray_l; P.ray_idx = ray_idx;
+    P.n_groups = (int64_t)ng;
+    P.stack = stack;
+    P.err = t->d_err;
+    for (int q = 0; q < 5; ++q) P.out[q] = (T*)out[q];
+    const bool ao = (flags & LENS_ALPHA_ONLY) != 0;
+    const bool direct = (flags & LENS_DIRECT) != 0;
+    bool first_launch = true;
+    int launches = 0;
+    for (size_t si = 0; si < t->sp.size(); ++si) {
+        const SpeciesTree& st = t->sp[si];
+        if (st.n == 0) continue;
+        P.nodeA = (const T4*)st.nodeA;
+        P.nodeB = (const T2*)st.nodeB;
+        P.link = st.link;
+        P.leaf0 = (const T4*)((direct || st.kind == LENS_POINT) ? st.exact0 : st.leaf0);
+        P.leaf1 = (const T4*)st.exact1;
+        P.big0 = (const T4*)st.big0;
+        P.big1 = (const T4*)st.big1;
+        P.n_part = st.n;
+        P.Uq = (T)st.Uq;
+        P.invNq = (T)st.invNq;
+        P.halos = t->halos;
+        P.n_halos = first_launch ? (int)t->n_halos : 0;
+        P.accumulate = first_launch ? ((flags & LENS_ACCUMULATE) ? 1 : 0) : 1;
+        P.counter = counter + 2 * launches;
+        LENS_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(uint32_t), s));
+        if (n > 0) {
+            if (R == 1) launch_dispatch<T, 1>(st.kind, ao, direct, P, t->num_sms, s);
+            else launch_dispatch<T, 2>(st.kind, ao, direct, P, t->num_sms, s);
+        }
+        first_launch = false;
+        ++launches;
+    }
+    if (first_launch && n > 0) {
+        // no particles at all: analytic components only
+        P.n_part = 0;
+        P.halos = t->halos;
+        P.n_halos = (int)t->n_halos;
+        P.accumulate = (flags & LENS_ACCUMULATE) ? 1 : 0;
+        P.counter = counter;
+        LENS_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(uint32_t), s));
+        if (R == 1) launch_dispatch<T, 1>(LENS_POINT, ao, true, P, t->num_sms, s);
+        else launch_dispatch<T, 2>(LENS_POINT, ao, true, P, t->num_sms, s);
+    }
+    if (timing) {
+        LENS_CUDA(cudaEventRecord(t->ev[2], s));
+        t->timed = true;
+    }
+    LENS_CUDA(cudaGetLastError());
+    return LENS_OK;
+}
+
+lens_status enqueue_shoot(lens_tree* t, const ShootPlan& plan, const void* dx, const void* dy, int dtype,
+                          void* const out[5], int flags, cudaStream_t s)
+{
+    if (t->precision == LENS_PREC_FP64) return enqueue_typed<double>(t, plan, dx, dy, dtype, out, flags, s);
+    return enqueue_typed<float>(t, plan, dx, dy, dtype, out, flags, s);
+}
+
+lens_status shoot(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig, const void* dx,
+                  const void* dy, int dtype, void* const out[5], int flags, cudaStream_t s)
+{
+    ShootPlan plan;
+    LENS_TRY(upload_batches(t, nb, h_off, h_orig, s, &plan));
+    return enqueue_shoot(t, plan, dx, dy, dtype, out, flags, s);
+}
+
+// Scratch views shared with the backward walk.
+void* scratch_base(lens_tree* t) { return t->ray_scratch.ptr; }
+
+}  // namespace lens

@@ -1,0 +1,228 @@
+"""GPU parity: liblens (through its C ABI) against the FP64 oracle.
+
+Bars: direct sum FP64 <= 1e-12 relative; direct sum FP32 <= 1e-5 in alpha,
+kappa and gamma; tree median alpha error <= 1e-3 at theta = 0.3 and <= 1e-4
+at theta = 0.1 (error metric in lens_testutil).  Kappa from the tree is exact
+up to FP32 rounding for sized particles (only particles whose support covers
+the ray carry surface density, Sec. 5.1 halo test).
+"""
+import numpy as np
+import pytest
+
+import lensgen
+import oracle
+from lens_testutil import comps_gauss, comps_nfw, comps_points, rel_errors, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1312_1128_gb300 as L  # noqa: E402
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def edge_mask(comps, rx, ry, rel=1e-6):
+    """Rays within a relative 1e-6 of some component's support edge, where the
+    FP32 and FP64 inside/outside decisions may legitimately differ (kappa
+    jumps there by the truncated profile's edge value)."""
+    m = np.zeros(rx.size, bool)
+    sizes = np.where(comps["type"] == oracle.GAUSS, comps["p0"] * comps["p1"],
+                     np.where(comps["type"] == oracle.NFW, comps["p1"],
+                              np.where(comps["type"] == oracle.DISK, comps["p0"], 0.0)))
+    sel = sizes > 0
+    cx, cy, s = comps["x"][sel], comps["y"][sel], sizes[sel]
+    for i in range(rx.size):
+        r = np.hypot(rx[i] - cx, ry[i] - cy)
+        m[i] = np.any(np.abs(r / s - 1.0) < rel)
+    return m
+
+
+# ----------------------------------------------------------- direct sums
+
+def test_direct_fp64_point_disk():
+    """2,000 equal point masses in the unit disk, 64 x 64 grid, FP64."""
+    w = lensgen.workload_point_disk()
+    p = w["points"]
+    lens = L.Lens([L.Species.points(cu(p))], theta=0.1, precision="fp64")
+    out = lens.shoot(cu(w["rx"]), cu(w["ry"]), flags=L.DIRECT)
+    lens.sync()
+    got = to_np(out)
+    ref = oracle.direct_sum(comps_points(p), w["rx"], w["ry"])
+    ea, ek, eg = rel_errors(got, ref)
+    assert ea.max() <= 1e-12 and eg.max() <= 1e-12
+    assert np.all(got[:, 2] == 0.0)
+
+
+def mixed_lens_inputs(seed=5):
+    g = lensgen.rng(seed)
+    gauss = lensgen.nfw_particles(3000, seed, nsph=16)
+    nfw = lensgen.nfw_halo_field(60, seed + 1, rs_at_1e4=0.03, box=0.8)
+    pts = lensgen.point_disk(300, seed + 2, total_mass=0.05)
+    halos = [L.Halo.sis(0.1, -0.05, 0.15), L.Halo.disk(-0.2, 0.1, -0.02, 0.3),
+             L.Halo.gauss(0.3, 0.3, 0.01, 0.05, 3.0), L.Halo.nfw(-0.4, -0.3, 0.02, 0.05, 0.2),
+             L.Halo.point(0.5, -0.5, 0.003)]
+    comps = oracle.concat(
+        comps_gauss(gauss, 3.0), comps_nfw(nfw, 3.0), comps_points(pts),
+        oracle.make_components(oracle.SIS, 0.1, -0.05, 0.0, 0.15),
+        oracle.make_components(oracle.DISK, -0.2, 0.1, -0.02, 0.3),
+        oracle.make_components(oracle.GAUSS, 0.3, 0.3, 0.01, 0.05, 3.0),
+        oracle.make_components(oracle.NFW, -0.4, -0.3, 0.02, 0.05, 0.2),
+        oracle.make_components(oracle.POINT, 0.5, -0.5, 0.003))
+    rx = g.uniform(-0.9, 0.9, 1024).astype(np.float32)
+    ry = g.uniform(-0.9, 0.9, 1024).astype(np.float32)
+    species = [L.Species.gauss(cu(gauss), 3.0), L.Species.nfw(cu(nfw), 3.0), L.Species.points(cu(pts))]
+    return species, halos, comps, rx, ry
+
+
+@pytest.mark.parametrize("group_rays", [32, 64])
+def test_direct_fp32_mixed(group_rays):
+    species, halos, comps, rx, ry = mixed_lens_inputs()
+    lens = L.Lens(species, halos, theta=0.3, group_rays=group_rays)
+    out = lens.shoot(cu(rx), cu(ry), flags=L.DIRECT)
+    lens.sync()
+    got = to_np(out)
+    ref = oracle.direct_sum(comps, rx.astype(np.float64), ry.astype(np.float64))
+    amb = edge_mask(comps, rx.astype(np.float64), ry.astype(np.float64))
+    assert amb.sum() <= 0.01 * rx.size
+    ea, ek, eg = rel_errors(got, ref)
+    ok = ~amb
+    assert ea[ok].max() <= 1e-5, ea[ok].max()
+    assert ek[ok].max() <= 1e-5, ek[ok].max()
+    assert eg[ok].max() <= 1e-5, eg[ok].max()
+
+
+# ------------------------------------------------------------- tree mode
+
+@pytest.mark.parametrize("theta,bar", [(0.3, 1e-3), (0.1, 1e-4)])
+def test_tree_gauss_nfw_sph(theta, bar):
+    """Smoothed NFW particles, r_sm = 32nd 3D neighbour, q = 3 (Sec. 3.1)."""
+    parts = lensgen.nfw_particles(20000, 7, nsph=32)
+    g = lensgen.rng(8)
+    rx = g.uniform(-1, 1, 4096).astype(np.float32)
+    ry = g.uniform(-1, 1, 4096).astype(np.float32)
+    lens = L.Lens([L.Species.gauss(cu(parts), 3.0)], theta=theta)
+    got = to_np(lens.shoot(cu(rx), cu(ry)))
+    lens.sync()
+    comps = comps_gauss(parts, 3.0)
+    ref = oracle.direct_sum(comps, rx.astype(np.float64), ry.astype(np.float64))
+    ea, ek, eg = rel_errors(got, ref)
+    assert np.median(ea) <= bar, np.median(ea)
+    assert np.median(eg) <= bar
+    amb = edge_mask(comps, rx.astype(np.float64), ry.astype(np.float64))
+    assert ek[~amb].max() <= 1e-5, ek[~amb].max()
+
+
+def test_tree_points_fp64_theta01():
+    w = lensgen.workload_point_disk()
+    p = w["points"]
+    lens = L.Lens([L.Species.points(cu(p))], theta=0.1, precision="fp64")
+    got = to_np(lens.shoot(cu(w["rx"]), cu(w["ry"])))
+    lens.sync()
+    ref = oracle.direct_sum(comps_points(p), w["rx"], w["ry"])
+    ea, _, eg = rel_errors(got, ref)
+    assert np.median(ea) <= 1e-4 and np.median(eg) <= 1e-4
+    assert np.all(got[:, 2] == 0.0)
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.55, 0.8])
+def test_tree_halo_kappa_exact(theta):
+    """Sec. 5.1 halo test: NFW halos, sizes uniform up to 0.3, c = 3: kappa
+    from the tree equals the direct sum at any opening angle."""
+    h = lensgen.nfw_test_halos(1000, 21, 0.3)
+    g = lensgen.rng(22)
+    rx = g.uniform(-1, 1, 1024).astype(np.float32)
+    ry = g.uniform(-1, 1, 1024).astype(np.float32)
+    lens = L.Lens([L.Species.nfw(cu(h), 3.0)], theta=theta)
+    got = to_np(lens.shoot(cu(rx), cu(ry)))
+    lens.sync()
+    comps = comps_nfw(h, 3.0)
+    ref = oracle.direct_sum(comps, rx.astype(np.float64), ry.astype(np.float64))
+    amb = edge_mask(comps, rx.astype(np.float64), ry.astype(np.float64))
+    _, ek, _ = rel_errors(got, ref)
+    assert ek[~amb].max() <= 1e-5, ek[~amb].max()
+
+
+def test_microlensing_patch_fp64_offsets():
+    """Stars in the unit disk + SIS, rays on a 1e-6-wide patch at (0.5, 0):
+    FP64 origin + FP32 offsets keep the patch resolved."""
+    w = lensgen.workload_microlensing(n_stars=100_000, n_grid=32)
+    p = w["points"]
+    lens = L.Lens([L.Species.points(cu(p))], [L.Halo.sis(0.0, 0.0, w["sis_re"])], theta=0.1)
+    got = to_np(lens.shoot(cu(w["dx"]), cu(w["dy"]), origin=w["origin"]))
+    lens.sync()
+    comps = oracle.concat(comps_points(p), oracle.make_components(oracle.SIS, 0, 0, 0, w["sis_re"]))
+    rx = w["origin"][0] + w["dx"].astype(np.float64)
+    ry = w["origin"][1] + w["dy"].astype(np.float64)
+    ref = oracle.direct_sum(comps, rx, ry)
+    ea, _, eg = rel_errors(got, ref)
+    assert np.median(ea) <= 1e-4 and np.median(eg) <= 1e-4
+    # across the patch the shear changes by ~1e-3 of itself; FP32 absolute
+    # coordinates (ulp(0.5) ~ 6e-8) would step it in ~17 levels.  The direct
+    # sum must follow the oracle ray by ray to 1e-3 of that variation.
+    dirc = to_np(lens.shoot(cu(w["dx"]), cu(w["dy"]), origin=w["origin"], flags=L.DIRECT))
+    lens.sync()
+    for q in (3, 4):
+        assert np.abs(dirc[:, q] - ref[:, q]).max() <= 1e-3 * np.ptp(ref[:, q])
+
+
+def test_batches_and_graph_replay():
+    """Uneven refinement batches in one launch, eager and graph-replayed."""
+    w = lensgen.workload_mixed_batches(n_halos=100, n_stars=20000, n_batches=12, nmin=50, nmax=3000)
+    lens = L.Lens([L.Species.points(cu(w["points"])), L.Species.nfw(cu(w["nfw"]), 3.0)], theta=0.3)
+    dx, dy = cu(w["dx"]), cu(w["dy"])
+    eager = to_np(lens.shoot_batches(w["offsets"], w["origins"], dx, dy))
+    outs = [torch.empty(dx.numel(), device="cuda") for _ in range(5)]
+    for _ in range(3):
+        for o in outs:
+            o.fill_(float("nan"))
+        lens.shoot_batches(w["offsets"], w["origins"], dx, dy, flags=L.USE_GRAPH, out=outs)
+        lens.sync()
+        np.testing.assert_array_equal(to_np(outs), eager)
+    comps = oracle.concat(comps_points(w["points"]), comps_nfw(w["nfw"], 3.0))
+    b = np.repeat(np.arange(len(w["offsets"]) - 1), np.diff(w["offsets"]))
+    rx = w["origins"][b, 0] + w["dx"].astype(np.float64)
+    ry = w["origins"][b, 1] + w["dy"].astype(np.float64)
+    sel = np.arange(0, rx.size, max(1, rx.size // 3000))
+    ref = oracle.direct_sum(comps, rx[sel], ry[sel])
+    ea, _, _ = rel_errors(eager[sel], ref)
+    assert np.median(ea) <= 1e-3
+
+
+# --------------------------------------------------- edge cases and flags
+
+def test_empty_ragged_and_flags():
+    parts = lensgen.nfw_particles(2000, 31, nsph=16)
+    lens = L.Lens([L.Species.gauss(cu(parts), 3.0), L.Species.points(cu(np.zeros((0, 4), np.float32)))],
+                  [L.Halo.sis(0.0, 0.0, 0.1)], theta=0.3)
+    # n = 0 is a no-op
+    e = torch.empty(0, device="cuda")
+    lens.shoot(e, e)
+    g = lensgen.rng(32)
+    for n in [1, 31, 33, 65, 1000]:
+        rx = g.uniform(-0.5, 0.5, n).astype(np.float32)
+        ry = g.uniform(-0.5, 0.5, n).astype(np.float32)
+        full = to_np(lens.shoot(cu(rx), cu(ry)))
+        ao = lens.shoot(cu(rx), cu(ry), flags=L.ALPHA_ONLY)
+        np.testing.assert_allclose(to_np(ao[:2]), full[:, :2], rtol=1e-6, atol=1e-7)
+        acc = [cu(np.ones(n, np.float32)) for _ in range(5)]
+        lens.shoot(cu(rx), cu(ry), flags=L.ACCUMULATE, out=acc)
+        np.testing.assert_allclose(to_np(acc), full + 1.0, rtol=1e-6, atol=1e-6)
+    lens.sync()
+    # halos only
+    only = L.Lens([], [L.Halo.sis(0.0, 0.0, 0.5)], theta=0.3)
+    o = to_np(only.shoot(cu(np.array([0.3], np.float32)), cu(np.array([0.4], np.float32))))
+    np.testing.assert_allclose(o[0, :2], [0.3, 0.4], rtol=1e-6)   # r_E * x / |x| with |x| = 0.5
+    assert o[0, 2] == pytest.approx(0.5, rel=1e-6)                 # r_E / (2 r)
+
+
+def test_invalid_inputs_are_rejected():
+    bad = np.array([[0.0, 0.0, -1.0, 0.1]], np.float32)
+    with pytest.raises(L.LensError):
+        L.Lens([L.Species.gauss(cu(bad), 3.0)])
+    with pytest.raises(L.LensError):
+        L.Lens([], theta=-1.0)
