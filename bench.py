@@ -134,6 +134,13 @@ def max_over_ranks(ws, v: float, device=None) -> float:
 
 # ------------------------------------------------------------ CPU oracle
 
+def bench_config(ws: int) -> dict:
+    return {"workload": WORKLOAD, "n_particles": 1_000_000, "grid": 2048, "theta": THETA,
+            "kernel": "gauss q=3, r_sm = 32nd 3D neighbour", "leaf_max": 5,
+            "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": f"independent replicas x{ws}"}
+
+
 def oracle_rays_per_sec(w, budget_s: float, seed: int = 7):
     """FP64 direct sum over all particles (the oracle as it stands) on a
     time-bounded random sample of the grid rays."""
@@ -171,12 +178,11 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_rays / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n_particles": 1_000_000,
-                                             "grid": 2048, "theta": 0.0, "kernel": "gauss q=3",
-                                             "l2": "n/a (CPU)"},
+            "data": "synthetic", "config": bench_config(ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{samples} random grid rays of the workload, FP64 direct "
-                                       f"sum over all 1e6 particles, {per_step:.0f} s per step"},
+                                       f"sum over all 1e6 particles (the tree's theta -> 0 limit), "
+                                       f"{per_step:.0f} s per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -199,11 +205,17 @@ def run_gpu(args, ws, rank, local):
     species = [L.Species.gauss(parts, w["q"])]
     lib = L.lib()
 
+    tuned = {"group_rays": 32}
+
     def step(flags=L.TIMING):
-        lens = L.Lens(species, theta=THETA)
+        lens = L.Lens(species, theta=THETA, group_rays=tuned["group_rays"])
         lens.shoot(rx, ry, flags=flags, out=outs)
         return lens
 
+    # autotune the ray-group size once on this lens and these rays (warm-up)
+    lens = L.Lens(species, theta=THETA)
+    tuned["group_rays"] = lens.autotune(rx, ry)
+    lens.close()
     for _ in range(args.warmup):
         step().close()
     torch.cuda.synchronize()
@@ -229,6 +241,7 @@ def run_gpu(args, ws, rank, local):
         g_ms, w_ms = lens.last_timing()
         group_ms.append(g_ms)
         walk_ms.append(w_ms)
+        build_phases = [round(x, 3) for x in lens.info()["build_ms"][0]]
         lens.close()
     barrier(ws)
     launches = lib.lens_kernel_launches() - launches0
@@ -278,10 +291,7 @@ def run_gpu(args, ws, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_particles": 1_000_000, "grid": 2048, "theta": THETA,
-                       "kernel": "gauss q=3, r_sm = 32nd 3D neighbour", "leaf_max": 5,
-                       "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": f"independent replicas x{ws}"},
+            "config": bench_config(ws), "tuning": {"group_rays": tuned["group_rays"]},
             "e2e": {"value": ws * n_rays / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -291,6 +301,7 @@ def run_gpu(args, ws, rank, local):
                          "fp32_ffma_measured": measured_peak,
                          "useful_flops_per_ray": fpr, "walk_ms": w_ms,
                          "group_ms": float(np.mean(group_ms))},
+            "build_ms_phases": build_phases,
             "interactions": {k: cnt[k] for k in ["groups", "visited", "cells", "leaf_particles",
                                                  "big_scanned", "big_kept", "ray_interactions"]},
             "clocks": clk, "gpu_launches": int(launches)}

@@ -132,6 +132,8 @@ typedef struct lens_tree_info {
     int64_t n_big[8];         /* big-list entries (Sec. 3.2) */
     int32_t depth[8];         /* deepest level (root = 0) */
     double root[8][3];        /* root box centre x, y and half side */
+    double build_ms[8][4];    /* host wall time of the build phases: sort + topology
+                                 count, node layout, moments + big lists, finish */
 } lens_tree_info;
 
 /*
@@ -215,6 +217,17 @@ lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double or
                                      const void* g_kappa, const void* g_gamma1,
                                      const void* g_gamma2, void* const* g_species,
                                      void* g_halos, int32_t flags, void* stream);
+
+/*
+ * lens_autotune -- pick the ray-group size (rays sharing one interaction
+ * list: 32 or 64) for this tree by timing the walk on the given rays (at most
+ * the first 1,048,576; same arguments as lens_shoot_rays) with CUDA events,
+ * and keep the faster one for later calls.  *group_rays receives the choice.
+ * Synchronous; allocates temporary outputs on the device.
+ */
+lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, const void* ray_dx,
+                          const void* ray_dy, int32_t ray_dtype, int64_t n, void* stream,
+                          int32_t* group_rays);
 
 /* lens_reserve -- grow the tree's scratch for up to max_rays rays in up to
  * max_batches batches, so that later calls of that size allocate nothing. */

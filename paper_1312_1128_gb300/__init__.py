@@ -64,7 +64,7 @@ class _Info(ctypes.Structure):
                 ("n_halos", ctypes.c_int64), ("n_particles", ctypes.c_int64 * 8),
                 ("n_nodes", ctypes.c_int64 * 8), ("n_leaves", ctypes.c_int64 * 8),
                 ("n_big", ctypes.c_int64 * 8), ("depth", ctypes.c_int32 * 8),
-                ("root", (ctypes.c_double * 3) * 8)]
+                ("root", (ctypes.c_double * 3) * 8), ("build_ms", (ctypes.c_double * 4) * 8)]
 
 
 def lib():
@@ -85,6 +85,7 @@ def lib():
     L.lens_shoot_rays_backward.argtypes = [vp, d, d, vp, vp, i32, i64, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(vp), vp, i32, vp]
     L.lens_reserve.argtypes = [vp, i64, i64]
+    L.lens_autotune.argtypes = [vp, d, d, vp, vp, i32, i64, vp, ctypes.POINTER(ctypes.c_int32)]
     L.lens_sync_status.argtypes = [vp, vp]
     L.lens_tree_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
     L.lens_tree_export.argtypes = [vp, i32, vp, vp, vp, vp]
@@ -100,7 +101,7 @@ def lib():
     for name in ["lens_build_tree", "lens_shoot_rays", "lens_shoot_batches",
                  "lens_shoot_rays_backward", "lens_reserve", "lens_sync_status",
                  "lens_tree_get_info", "lens_tree_export", "lens_fp32_peak", "lens_api_version",
-                 "lens_tree_counters", "lens_last_timing"]:
+                 "lens_tree_counters", "lens_last_timing", "lens_autotune"]:
         getattr(L, name).restype = ctypes.c_int32
     _lib = L
     return L
@@ -229,7 +230,8 @@ class Lens:
         return dict(n_species=k, precision=inf.precision, n_halos=inf.n_halos,
                     n_particles=list(inf.n_particles[:k]), n_nodes=list(inf.n_nodes[:k]),
                     n_leaves=list(inf.n_leaves[:k]), n_big=list(inf.n_big[:k]),
-                    depth=list(inf.depth[:k]), root=[tuple(inf.root[i]) for i in range(k)])
+                    depth=list(inf.depth[:k]), root=[tuple(inf.root[i]) for i in range(k)],
+                    build_ms=[tuple(inf.build_ms[i]) for i in range(k)])
 
     def export(self, species: int = 0):
         """Host copies of one species' tree: nodes (n_nodes, 8), links
@@ -260,6 +262,16 @@ class Lens:
 
     def sync(self, stream=None):
         _check(lib().lens_sync_status(self._h, _stream_ptr(stream)))
+
+    def autotune(self, dx, dy, origin=(0.0, 0.0), stream=None) -> int:
+        """Time the walk with 32- and 64-ray groups on these rays; keep and
+        return the faster group size."""
+        torch = _torch()
+        g = ctypes.c_int32()
+        rd = F32 if dx.dtype == torch.float32 else F64
+        _check(lib().lens_autotune(self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx),
+                                   _dev_ptr(dy), rd, dx.numel(), _stream_ptr(stream), ctypes.byref(g)))
+        return g.value
 
     def reserve(self, max_rays: int, max_batches: int = 1):
         _check(lib().lens_reserve(self._h, int(max_rays), int(max_batches)))

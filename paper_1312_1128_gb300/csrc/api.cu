@@ -12,7 +12,7 @@
 namespace lens {
 lens_status shoot(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig, const void* dx,
                   const void* dy, int dtype, void* const out[5], int flags, cudaStream_t s);
-lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb);
+lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s);
 lens_status shoot_backward(lens_tree* t, double ox, double oy, const void* dx, const void* dy,
                            int dtype, int64_t n, const void* const g[5], void* const* g_species,
                            void* g_halos, int flags, cudaStream_t s);
@@ -121,11 +121,12 @@ const char* lens_status_string(lens_status s)
 void lens_free_tree(lens_tree* t)
 {
     if (!t) return;
+    cudaDeviceSynchronize();  // no kernel of this tree may still be running
     free_graphs(t);
     for (auto& st : t->sp) free_species(st);
     if (t->halos) cudaFree(t->halos);
     if (t->d_err) cudaFree(t->d_err);
-    if (t->ray_scratch.ptr) cudaFree(t->ray_scratch.ptr);
+    if (t->ray_scratch.ptr) cudaFreeAsync(t->ray_scratch.ptr, 0);
     if (t->d_stats) cudaFree(t->d_stats);
     for (int i = 0; i < 3; ++i)
         if (t->ev[i]) cudaEventDestroy(t->ev[i]);
@@ -169,7 +170,7 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
     t->precision = params->precision;
     t->theta = params->theta;
     t->leaf_max = params->leaf_max;
-    t->group_rays = params->group_rays == 0 ? 64 : params->group_rays;
+    t->group_rays = params->group_rays == 0 ? 32 : params->group_rays;
     cudaStream_t s = (cudaStream_t)stream;
     auto fail = [&](lens_status st) {
         lens_free_tree(t);
@@ -177,6 +178,16 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
     };
     cudaError_t e = cudaGetDevice(&t->device);
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaGetDevice"));
+    {
+        // Tree arrays and ray scratch come from the device's stream-ordered
+        // pool; keep freed blocks in the pool so rebuilding a lens allocates
+        // at pool speed instead of cudaMalloc speed.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, t->device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    }
     e = cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaDeviceGetAttribute"));
     e = cudaMalloc((void**)&t->d_err, sizeof(uint32_t));
@@ -295,11 +306,55 @@ lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double or
                           flags, (cudaStream_t)stream);
 }
 
+lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, const void* ray_dx,
+                          const void* ray_dy, int32_t ray_dtype, int64_t n, void* stream,
+                          int32_t* group_rays)
+{
+    if (!tree || !group_rays) return lens_set_error(LENS_ERR_INVALID_ARG, "NULL argument");
+    if (ray_dtype != LENS_F32 && ray_dtype != LENS_F64) return lens_set_error(LENS_ERR_INVALID_ARG, "bad ray dtype");
+    if (n <= 0 || !ray_dx || !ray_dy) return lens_set_error(LENS_ERR_INVALID_ARG, "no rays to tune on");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t m = n < (1 << 20) ? n : (1 << 20);
+    size_t es = tree->precision == LENS_PREC_FP64 ? 8 : 4;
+    void* buf = nullptr;
+    LENS_CUDA(cudaMallocAsync(&buf, 5 * m * es, s));
+    void* out[5];
+    for (int q = 0; q < 5; ++q) out[q] = (char*)buf + q * m * es;
+    int64_t off[2] = {0, m};
+    double orig[2] = {origin_x, origin_y};
+    const int cand[2] = {32, 64};
+    double best = 1e300;
+    int best_g = tree->group_rays;
+    lens_status st = LENS_OK;
+    for (int c = 0; c < 2 && st == LENS_OK; ++c) {
+        if (tree->precision == LENS_PREC_FP64 && cand[c] != 32) continue;
+        tree->group_rays = cand[c];
+        double ms = 0;
+        for (int rep = 0; rep < 2 && st == LENS_OK; ++rep) {  // first run warms up
+            st = shoot(tree, 1, off, orig, ray_dx, ray_dy, ray_dtype, out, LENS_TIMING, s);
+            if (st != LENS_OK) break;
+            double g = 0, w = 0;
+            st = lens_last_timing(tree, &g, &w);
+            ms = g + w;
+        }
+        if (st == LENS_OK && ms < best) {
+            best = ms;
+            best_g = cand[c];
+        }
+    }
+    cudaFreeAsync(buf, s);
+    tree->group_rays = best_g;
+    *group_rays = best_g;
+    return st;
+}
+
 lens_status lens_reserve(lens_tree* tree, int64_t max_rays, int64_t max_batches)
 {
     if (!tree) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
     if (max_rays < 0 || max_batches < 1) return lens_set_error(LENS_ERR_INVALID_ARG, "bad reserve sizes");
-    return reserve_rays(tree, max_rays, max_batches);
+    LENS_TRY(reserve_rays(tree, max_rays, max_batches, 0));
+    LENS_CUDA(cudaStreamSynchronize(0));
+    return LENS_OK;
 }
 
 lens_status lens_sync_status(lens_tree* tree, void* stream)
@@ -359,6 +414,7 @@ lens_status lens_tree_get_info(const lens_tree* t, lens_tree_info* info)
         info->root[i][0] = s.root_cx;
         info->root[i][1] = s.root_cy;
         info->root[i][2] = s.root_half;
+        for (int k = 0; k < 4; ++k) info->build_ms[i][k] = s.phase_ms[k];
     }
     return LENS_OK;
 }

@@ -19,6 +19,7 @@
 //      side of a box on its path is listed at the shallowest such box; lists
 //      are grouped per box by a stable sort (deterministic order).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 
 #include "profiles.cuh"
@@ -451,29 +452,82 @@ __global__ void k_bigcount(uint32_t n_nodes, int4* link, const uint32_t* end)
 template <typename T>
 __global__ void k_bigrecords(const uint32_t* sval, int64_t nbig, const vec4_t<T>* e0,
                              const vec4_t<T>* e1, const vec4_t<T>* sorted, const double* r0sq,
-                             int kind, double shape, vec4_t<T>* big0, vec4_t<T>* big1,
+                             int kind, double shape, double invNq, vec4_t<T>* big0, vec4_t<T>* big1,
                              uint32_t* big_pid, vec4_t<T>* leaf0, uint8_t* listed)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nbig) return;
     uint32_t j = sval[i];
-    big0[i] = e0[j];
+    vec4_t<T> q = e0[j];
     double s = support_radius(kind, shape, (double)sorted[j].w);
-    vec4_t<T> b;
-    b.x = (T)r0sq[j];
-    b.y = (T)(s * s);
+    vec4_t<T> a, b;
+    a.x = q.x;
+    a.y = q.y;
+    a.z = (T)(s * s);
+    a.w = r0sq[j] > 0.0 ? (T)(1.0 / r0sq[j]) : (T)INFINITY;  // 1/r0^2
+    b.x = q.z;  // m
     if (kind == LENS_NFW) {
-        vec4_t<T> q = e1[j];
-        b.z = q.x;
-        b.w = q.y;
-    } else {
-        b.z = (T)0;
+        vec4_t<T> q1 = e1[j];
+        b.y = q1.x;  // A = m / g(X)
+        b.z = q1.y;  // B = 1 / r_s
         b.w = (T)0;
+    } else {
+        double c = (double)q.w, sig = (double)sorted[j].w;
+        b.y = (T)(c * 1.4426950408889634074);                 // c log2(e), c = 1/(2 r_sm^2)
+        b.z = (T)((double)q.z * c * invNq);                   // m c / N_q
+        b.w = (T)(2.0 * sig * sig);                           // 1 / c
     }
+    big0[i] = a;
     big1[i] = b;
     big_pid[i] = j;
     leaf0[j].w = -(T)r0sq[j];  // listed: a softened point inside leaves
     listed[j] = 1;
+}
+
+template <typename T> __device__ __forceinline__ T round_dn(double x);
+template <> __device__ __forceinline__ float round_dn<float>(double x) { return __double2float_rd(x); }
+template <> __device__ __forceinline__ double round_dn<double>(double x) { return x; }
+template <typename T> __device__ __forceinline__ T round_upx(double x);
+template <> __device__ __forceinline__ float round_upx<float>(double x) { return __double2float_ru(x); }
+template <> __device__ __forceinline__ double round_upx<double>(double x) { return x; }
+
+// Bounding box of the support squares [x - s, x + s] x [y - s, y + s] of big
+// entries [b, e): per 32-entry chunk and per node list (conservative bounds
+// for skipping a list or a chunk whose supports cannot reach a ray group).
+template <typename T>
+__device__ __forceinline__ vec4_t<T> support_box(const vec4_t<T>* big0, int64_t b, int64_t e)
+{
+    double x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
+    for (int64_t i = b; i < e; ++i) {
+        vec4_t<T> q = big0[i];
+        double s = sqrt((double)q.z);
+        x0 = fmin(x0, (double)q.x - s); x1 = fmax(x1, (double)q.x + s);
+        y0 = fmin(y0, (double)q.y - s); y1 = fmax(y1, (double)q.y + s);
+    }
+    vec4_t<T> r;
+    r.x = round_dn<T>(x0); r.y = round_dn<T>(y0); r.z = round_upx<T>(x1); r.w = round_upx<T>(y1);
+    return r;
+}
+
+template <typename T>
+__global__ void k_chunkbox(const vec4_t<T>* big0, int64_t nbig, int64_t nchunks, vec4_t<T>* out)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    int64_t b = 32 * c, e = b + 32 < nbig ? b + 32 : nbig;
+    out[c] = support_box<T>(big0, b, e);
+}
+
+template <typename T>
+__global__ void k_nodebox(const int4* link, uint32_t n_nodes, const vec4_t<T>* big0, vec4_t<T>* out)
+{
+    uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_nodes) return;
+    int4 L = link[v];
+    vec4_t<T> r;
+    if (L.w > 0) r = support_box<T>(big0, L.z, (int64_t)L.z + L.w);
+    else { r.x = r.y = (T)INFINITY; r.z = r.w = (T)-INFINITY; }
+    out[v] = r;
 }
 
 __global__ void k_iota_u32(uint32_t* a, uint32_t n)
@@ -489,6 +543,13 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
 {
     using T4 = vec4_t<T>;
     using T2 = typename V2<T>::type;
+    using clk = std::chrono::steady_clock;
+    auto t_start = clk::now();
+    auto lap = [&](int k) {
+        auto now = clk::now();
+        st.phase_ms[k] = std::chrono::duration<double, std::milli>(now - t_start).count();
+        t_start = now;
+    };
     const int64_t n = in.n;
     const int TB = 256;
     const unsigned G = grid_for(n, TB);
@@ -533,6 +594,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     LENS_CUDA(cudaStreamSynchronize(s));
     if (n_nodes == 0 || n_nodes > (uint32_t)kCountMask)
         return lens_set_error(LENS_ERR_INTERNAL, "tree build: bad node count %u", n_nodes);
+    lap(0);
     st.n_nodes = n_nodes;
     const unsigned GN = grid_for(n_nodes, TB);
     {
@@ -579,17 +641,17 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
                               cudaMemcpyDeviceToHost, s));
 
     // persistent node arrays
-    LENS_CUDA(cudaMalloc(&st.nodeA, n_nodes * sizeof(T4)));
-    LENS_CUDA(cudaMalloc(&st.nodeB, n_nodes * sizeof(T2)));
-    LENS_CUDA(cudaMalloc((void**)&st.link, n_nodes * sizeof(int4)));
-    LENS_CUDA(cudaMalloc((void**)&st.node_rcm, n_nodes * sizeof(float)));
-    LENS_CUDA(cudaMalloc((void**)&st.node_level, n_nodes));
-    LENS_CUDA(cudaMalloc((void**)&st.perm, n * sizeof(uint32_t)));
-    LENS_CUDA(cudaMalloc(&st.exact0, n * sizeof(T4)));
-    if (in.kind == LENS_NFW) LENS_CUDA(cudaMalloc(&st.exact1, n * sizeof(T4)));
+    LENS_CUDA(cudaMallocAsync(&st.nodeA, n_nodes * sizeof(T4), s));
+    LENS_CUDA(cudaMallocAsync(&st.nodeB, n_nodes * sizeof(T2), s));
+    LENS_CUDA(cudaMallocAsync((void**)&st.link, n_nodes * sizeof(int4), s));
+    LENS_CUDA(cudaMallocAsync((void**)&st.node_rcm, n_nodes * sizeof(float), s));
+    LENS_CUDA(cudaMallocAsync((void**)&st.node_level, n_nodes, s));
+    LENS_CUDA(cudaMallocAsync((void**)&st.perm, n * sizeof(uint32_t), s));
+    LENS_CUDA(cudaMallocAsync(&st.exact0, n * sizeof(T4), s));
+    if (in.kind == LENS_NFW) LENS_CUDA(cudaMallocAsync(&st.exact1, n * sizeof(T4), s));
     if (in.kind != LENS_POINT) {
-        LENS_CUDA(cudaMalloc(&st.leaf0, n * sizeof(T4)));
-        LENS_CUDA(cudaMalloc((void**)&st.listed, n));
+        LENS_CUDA(cudaMallocAsync(&st.leaf0, n * sizeof(T4), s));
+        LENS_CUDA(cudaMallocAsync((void**)&st.listed, n, s));
         LENS_CUDA(cudaMemsetAsync(st.listed, 0, n, s));
     }
     LENS_CUDA(cudaMemcpyAsync(st.perm, P, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
@@ -597,6 +659,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     { k_links<<<GN, TB, 0, s>>>(n_nodes, bfs2pre, pre2bfs, lvl, first, count, isleaf, nchild, st.link,
                               st.node_level, counters); note_launch(); }
     LENS_CUDA(cudaStreamSynchronize(s));  // level table on the host
+    lap(1);
     int depth = (int)ls[kMaxDepth + 1];
     if (depth < 0 || depth > kMaxDepth)
         return lens_set_error(LENS_ERR_INTERNAL, "tree build: bad depth %d", depth);
@@ -663,14 +726,21 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
         uint32_t nbig = 0;
         LENS_CUDA(cudaMemcpyAsync(&nbig, counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         LENS_CUDA(cudaStreamSynchronize(s));
+        lap(2);
         st.n_big = nbig;
         if (nbig > 0) {
-            LENS_CUDA(cudaMalloc(&st.big0, nbig * sizeof(T4)));
-            LENS_CUDA(cudaMalloc(&st.big1, nbig * sizeof(T4)));
-            LENS_CUDA(cudaMalloc((void**)&st.big_pid, nbig * sizeof(uint32_t)));
+            LENS_CUDA(cudaMallocAsync(&st.big0, nbig * sizeof(T4), s));
+            LENS_CUDA(cudaMallocAsync(&st.big1, nbig * sizeof(T4), s));
+            LENS_CUDA(cudaMallocAsync((void**)&st.big_pid, nbig * sizeof(uint32_t), s));
             { k_bigrecords<T><<<grid_for(nbig, TB), TB, 0, s>>>(
-                sval, nbig, (T4*)st.exact0, (T4*)st.exact1, sorted, r0sq, in.kind, in.shape, (T4*)st.big0,
+                sval, nbig, (T4*)st.exact0, (T4*)st.exact1, sorted, r0sq, in.kind, in.shape, st.invNq, (T4*)st.big0,
                 (T4*)st.big1, st.big_pid, (T4*)st.leaf0, st.listed); note_launch(); }
+            st.n_chunks = ((int64_t)nbig + 31) / 32;
+            LENS_CUDA(cudaMallocAsync(&st.big_chunk, st.n_chunks * sizeof(T4), s));
+            LENS_CUDA(cudaMallocAsync(&st.node_bigbox, (size_t)n_nodes * sizeof(T4), s));
+            { k_chunkbox<T><<<grid_for(st.n_chunks, TB), TB, 0, s>>>((T4*)st.big0, nbig, st.n_chunks,
+                                                                   (T4*)st.big_chunk); note_launch(); }
+            { k_nodebox<T><<<GN, TB, 0, s>>>(st.link, n_nodes, (T4*)st.big0, (T4*)st.node_bigbox); note_launch(); }
         }
         cudaFreeAsync(r0sq, s); cudaFreeAsync(bk0, s); cudaFreeAsync(bk1, s);
         cudaFreeAsync(bv0, s); cudaFreeAsync(bv1, s); cudaFreeAsync(end, s);
@@ -688,6 +758,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     cudaFreeAsync(level_start, s); cudaFreeAsync(counters, s); cudaFreeAsync(isleaf, s);
     cudaFreeAsync(nchild, s); cudaFreeAsync(ids, s); cudaFreeAsync(mom, s); cudaFreeAsync(q2, s);
     LENS_CUDA(cudaStreamSynchronize(s));
+    lap(3);
     st.n_leaves = nleaves;
     st.root_cx = hrb.cx;
     st.root_cy = hrb.cy;
@@ -713,9 +784,10 @@ lens_status build_species(lens_tree* t, SpeciesTree& st, const lens_species& in,
 void free_species(SpeciesTree& st)
 {
     void* ptrs[] = {st.nodeA, st.nodeB, st.link, st.node_rcm, st.node_level, st.exact0, st.exact1,
-                    st.leaf0, st.big0, st.big1, st.perm, st.big_pid, st.listed};
+                    st.leaf0, st.big0, st.big1, st.perm, st.big_pid, st.listed, st.big_chunk,
+                    st.node_bigbox};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, 0);
     st = SpeciesTree();
 }
 

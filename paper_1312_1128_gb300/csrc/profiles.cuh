@@ -92,13 +92,11 @@ template <typename T> LENS_DEV void point_terms(T m, T r2s, T& kb, T& Dp)
 //   h1 = sum_k (-u)^k/(k+1)!,   g = sum_{n>=1} (-1)^(n+1) n u^n/(n+1)!.
 LENS_DEV void gauss_h1_g(float u, float e, float& h1, float& g)
 {
-    if (u < 0.5f) {
-        h1 = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u,
-             -1.0f / 3628800, 1.0f / 362880), -1.0f / 40320), 1.0f / 5040), -1.0f / 720),
-             1.0f / 120), -1.0f / 24), 1.0f / 6), -0.5f), 1.0f);
-        g = u * fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u,
-            1.0f / 403200, -1.0f / 45360), 1.0f / 5760), -1.0f / 840), 1.0f / 144),
-            -1.0f / 30), 1.0f / 8), -1.0f / 3), 0.5f);
+    if (u < 0.25f) {
+        h1 = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u,
+             -1.0f / 40320, 1.0f / 5040), -1.0f / 720), 1.0f / 120), -1.0f / 24), 1.0f / 6), -0.5f), 1.0f);
+        g = u * fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u,
+            -1.0f / 45360, 1.0f / 5760), -1.0f / 840), 1.0f / 144), -1.0f / 30), 1.0f / 8), -1.0f / 3), 0.5f);
     } else {
         h1 = (1.0f - e) * rcp(u);
         g = h1 - e;
@@ -117,6 +115,26 @@ LENS_DEV void gauss_h1_g(double u, double e, double& h1, double& g)
         h1 = -expm1(-u) / u;
         g = h1 - e;
     }
+}
+
+// Same h1, g with 1/u supplied (inv_u = 1/(r^2 c)), so the direct branch
+// needs no reciprocal of its own.
+LENS_DEV void gauss_h1_g_inv(float u, float e, float inv_u, float& h1, float& g)
+{
+    if (u < 0.25f) {
+        h1 = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u,
+             -1.0f / 40320, 1.0f / 5040), -1.0f / 720), 1.0f / 120), -1.0f / 24), 1.0f / 6), -0.5f), 1.0f);
+        g = u * fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u,
+            -1.0f / 45360, 1.0f / 5760), -1.0f / 840), 1.0f / 144), -1.0f / 30), 1.0f / 8), -1.0f / 3), 0.5f);
+    } else {
+        h1 = (1.0f - e) * inv_u;
+        g = h1 - e;
+    }
+}
+LENS_DEV void gauss_h1_g_inv(double u, double e, double inv_u, double& h1, double& g)
+{
+    (void)inv_u;
+    gauss_h1_g(u, e, h1, g);
 }
 
 // Exact Gaussian terms for a particle with c > 0 (c = 1/(2 r_sm^2)); outside
@@ -138,6 +156,87 @@ LENS_DEV void gauss_terms(T m, T c, T r2, T Uq, T invNq, T& kb, T& kap, T& Dp)
         kap = T(0);
         Dp = kb * inv;
     }
+}
+
+// Gaussian big-list correction in base-2 form, FP32: with t = r^2 c log2(e)
+// (c' = c log2 e stored per particle) e^-u = 2^-t costs one ex2, and the
+// small-u series above are rewritten in t (u = t ln 2):
+//   h1 = sum_k (-ln2)^k t^k/(k+1)!,   g = t sum_j b_j ln2^(j+1) t^j,
+// b = {1/2, -1/3, 1/8, -1/30, 1/144, -1/840, 1/5760, -1/45360}; u < 1/4
+// becomes t < 1/(4 ln 2).
+namespace gser {
+constexpr double L = 0.69314718055994530942;
+constexpr float kTSeries = (float)(0.25 / L);
+constexpr float h(int k, double fact, int sgn)
+{
+    double p = 1.0;
+    for (int i = 0; i < k; ++i) p *= L;
+    return (float)(sgn * p / fact);
+}
+constexpr float gco(int j, double b)
+{
+    double p = 1.0;
+    for (int i = 0; i <= j; ++i) p *= L;
+    return (float)(b * p);
+}
+constexpr float H0 = 1.0f, H1 = h(1, 2.0, -1), H2 = h(2, 6.0, 1), H3 = h(3, 24.0, -1), H4 = h(4, 120.0, 1),
+                H5 = h(5, 720.0, -1), H6 = h(6, 5040.0, 1), H7 = h(7, 40320.0, -1);
+constexpr float G0 = gco(0, 1.0 / 2), G1 = gco(1, -1.0 / 3), G2 = gco(2, 1.0 / 8), G3 = gco(3, -1.0 / 30),
+                G4 = gco(4, 1.0 / 144), G5 = gco(5, -1.0 / 840), G6 = gco(6, 1.0 / 5760),
+                G7 = gco(7, -1.0 / 45360);
+}  // namespace gser
+
+LENS_DEV float exp2neg(float t)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-t));
+    return r;
+}
+
+// Correction (full truncated Gaussian - softened point) at offset w.
+// q = {., ., s^2, 1/r0^2}, q1 = {m, c log2 e, m c / N_q, 1/c}; Uq2 = q^2/2 log2 e.
+// Outside the support both terms are the same point mass: the result is 0.
+template <bool AO>
+LENS_DEV void gauss_correction(Acc5<float>& acc, float wx, float wy, const float4& q, const float4& q1,
+                               float Uq2)
+{
+    using namespace gser;
+    float r2 = fmaf(wx, wx, wy * wy);
+    float inv = r2 > 0.0f ? rcp(r2) : 0.0f;
+    float inv_s = fminf(inv, q.w);
+    float kbp = q1.x * inv_s;
+    float t = r2 * q1.y;
+    float e = exp2neg(t);
+    float h1, g;
+    if (t < kTSeries) {
+        h1 = fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, H7, H6), H5), H4), H3), H2), H1), H0);
+        g = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, G7, G6), G5), G4), G3), G2), G1), G0);
+    } else {
+        h1 = (1.0f - e) * (inv * q1.w);
+        g = h1 - e;
+    }
+    bool in = t < Uq2;
+    float dkb = in ? fmaf(q1.z, h1, -kbp) : 0.0f;
+    float kap = in ? q1.z * e : 0.0f;
+    float dDp = in ? fmaf(q1.z * g, inv, -kbp * inv_s) : 0.0f;
+    acc.template radial<AO>(wx, wy, dkb, kap, dDp);
+}
+
+// FP64 form of the same correction (q1.y holds c log2 e as well).
+template <bool AO>
+LENS_DEV void gauss_correction(Acc5<double>& acc, double wx, double wy, const dbl4& q, const dbl4& q1,
+                               double Uq2)
+{
+    const double L = 0.69314718055994530942;
+    double r2 = fma(wx, wx, wy * wy);
+    double inv = r2 > 0.0 ? 1.0 / r2 : 0.0;
+    double inv_s = fmin(inv, q.w);
+    double kbp = q1.x * inv_s;
+    double u = r2 * q1.y * L;
+    if (!(r2 * q1.y < Uq2)) return;
+    double e = exp(-u), h1, g;
+    gauss_h1_g(u, e, h1, g);
+    acc.template radial<AO>(wx, wy, fma(q1.z, h1, -kbp), q1.z * e, fma(q1.z * g, inv, -kbp * inv_s));
 }
 
 // ------------------------------------------------------- projected NFW

@@ -24,6 +24,7 @@ struct SpeciesTree {
     double shape = 0;          // q (GAUSS) or R_max / r_s (NFW)
     double Uq = 0, invNq = 0;  // GAUSS: q^2/2 and 1/(1 - e^{-q^2/2})
     std::vector<int64_t> level_start;  // BFS offset of each level, depth + 2 entries
+    double phase_ms[4] = {0, 0, 0, 0};   // host wall time of the build phases
 
     // node data (BFS order); element type T = float or double by prec
     void* nodeA = nullptr;     // T4 {x_cm, y_cm, M, r_cut^2}
@@ -35,8 +36,11 @@ struct SpeciesTree {
     void* exact0 = nullptr;    // T4 full-profile records (see walk)
     void* exact1 = nullptr;    // T4 second record (NFW only)
     void* leaf0 = nullptr;     // T4 leaf records: listed particles marked as softened points
-    void* big0 = nullptr;      // T4 big-list records (full profile)
-    void* big1 = nullptr;      // T4 {r0^2, s^2, A, B}
+    void* big0 = nullptr;      // T4 big-list test records {x, y, s^2, r0^2}
+    void* big1 = nullptr;      // T4 {m, c, 0, 0} (GAUSS) or {m, A, B, 0} (NFW)
+    void* big_chunk = nullptr; // T4 per 32 big entries: bounding box of their support squares
+    void* node_bigbox = nullptr;  // T4 per node: bounding box of its list's support squares
+    int64_t n_chunks = 0;
     uint32_t* perm = nullptr;  // Morton position -> input index
     uint32_t* big_pid = nullptr;  // big entry -> Morton position
     uint8_t* listed = nullptr;    // per Morton position: 1 if in a big list

@@ -168,7 +168,17 @@ __global__ void k_groups(int64_t n_groups, const int64_t* boff, const uint32_t* 
         ymin = fmin(ymin, __shfl_xor_sync(full, ymin, o));
         ymax = fmax(ymax, __shfl_xor_sync(full, ymax, o));
     }
-    T Hx = (T)(0.5 * (xmin + xmax)), Hy = (T)(0.5 * (ymin + ymax));
+    // Anchor: if every ray of the group is exactly representable in T (for
+    // example FP32 rays with origin 0), H = 0 keeps each separation a single
+    // rounding of (ray - particle); otherwise H is the T value nearest the
+    // group centre, so that far from the coordinate zero the small offsets
+    // l = ray - H keep their resolution.
+    bool exact = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (v[r]) exact = exact && (double)(T)px[r] == px[r] && (double)(T)py[r] == py[r];
+    exact = __all_sync(full, exact);
+    T Hx = exact ? T(0) : (T)(0.5 * (xmin + xmax)), Hy = exact ? T(0) : (T)(0.5 * (ymin + ymax));
     T lxmin = (T)INFINITY, lxmax = (T)-INFINITY, lymin = (T)INFINITY, lymax = (T)-INFINITY;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -213,10 +223,12 @@ template <typename T> struct WalkParams {
     const int4* link;
     const vec4_t<T>* leaf0;   // near records (listed particles marked)
     const vec4_t<T>* leaf1;   // NFW second record
-    const vec4_t<T>* big0;
-    const vec4_t<T>* big1;
+    const vec4_t<T>* big0;       // {x, y, s^2, r0^2}
+    const vec4_t<T>* big1;       // {m, c | A, B, 0}
+    const vec4_t<T>* big_chunk;  // support bounding box per 32 entries
+    const vec4_t<T>* node_bigbox;
     int64_t n_part;
-    T Uq, invNq;
+    T Uq, invNq, Uq2;
     const v2_t<T>* gH;
     const vec4_t<T>* gbox;
     const uint2* grange;
@@ -241,6 +253,7 @@ template <int KIND, typename T> struct WalkShared {
     vec4_t<T> b1[KIND == LENS_POINT ? 1 : kBigCap];
     int rs_off[33];
     int rs_first[32];
+    int rs_end[32];
 };
 
 template <int KIND, typename T, int R, bool AO> struct WalkCtx {
@@ -300,21 +313,39 @@ template <int KIND, typename T, int R, bool AO> struct WalkCtx {
         fold();
     }
 
-    // Big-list corrections: (full profile - softened point) inside the support.
+    // Big-list corrections: (full profile - softened point); zero outside the
+    // support, where both are the same point mass.
+    // b0 = {x - H.x, y - H.y, s^2, 1/r0^2}; b1 = {m, c log2 e, m c / N_q, 1/c}
+    // (GAUSS) or {m, A, B, 0} (NFW).  1/max(r^2, r0^2) = min(1/r^2, 1/r0^2).
+    // Two entries per iteration for instruction-level parallelism.
     LENS_DEV void flush_big(int nb)
     {
-        for (int i = 0; i < nb; ++i) {
+        int i = 0;
+        if constexpr (KIND == LENS_GAUSS) {
+            for (; i + 1 < nb; i += 2) {
+                vec4_t<T> q = S.b0[i], q1 = S.b1[i], p = S.b0[i + 1], p1 = S.b1[i + 1];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    gauss_correction<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q, q1, P.Uq2);
+                    gauss_correction<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p, p1, P.Uq2);
+                }
+            }
+        }
+        for (; i < nb; ++i) {
             vec4_t<T> q = S.b0[i], q1 = S.b1[i];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 T wx = lx[r] - q.x, wy = ly[r] - q.y;
-                T r2 = fma(wx, wx, wy * wy);
-                if (r2 < q1.y) {
-                    T kb, kap, Dp, kbp, Dpp;
-                    if (KIND == LENS_GAUSS) gauss_terms(q.z, q.w, r2, P.Uq, P.invNq, kb, kap, Dp);
-                    else nfw_terms(q.z, q.w, q1.z, q1.w, r2, kb, kap, Dp);
-                    point_terms(q.z, fmax(r2, q1.x), kbp, Dpp);
-                    part[r].template radial<AO>(wx, wy, kb - kbp, kap, Dp - Dpp);
+                if constexpr (KIND == LENS_GAUSS) {
+                    gauss_correction<AO>(part[r], wx, wy, q, q1, P.Uq2);
+                } else {
+                    T r2 = fma(wx, wx, wy * wy);
+                    T inv = r2 > T(0) ? rcp(r2) : T(0);
+                    T inv_s = fmin(inv, q.w);
+                    T kbp = q1.x * inv_s;
+                    T kb, kap, Dp;
+                    nfw_terms(q1.x, q.z, q1.y, q1.z, r2, kb, kap, Dp);
+                    part[r].template radial<AO>(wx, wy, kb - kbp, kap, Dp - kbp * inv_s);
                 }
             }
         }
@@ -430,8 +461,99 @@ LENS_DEV void append_ranges(WalkCtx<KIND, T, R, AO>& C, int cnt, int first, int&
     }
 }
 
+// Does the box {x0, y0, x1, y1} (frame coordinates) reach the group's ray
+// box?  The subtraction of H is rounded; a relative margin keeps the test
+// conservative.
+template <typename T>
+LENS_DEV bool box_reaches_group(const vec4_t<T>& b, const v2_t<T>& H, const vec4_t<T>& g)
+{
+    const T eps = sizeof(T) == 4 ? T(4.8e-7) : T(8.9e-16);
+    T x0 = b.x - H.x, x1 = b.z - H.x, y0 = b.y - H.y, y1 = b.w - H.y;
+    T tx = eps * (fabs(b.x) + fabs(b.z) + T(2) * fabs(H.x)), ty = eps * (fabs(b.y) + fabs(b.w) + T(2) * fabs(H.y));
+    return x0 - tx <= g.x + g.z && x1 + tx >= g.x - g.z && y0 - ty <= g.y + g.w && y1 + ty >= g.y - g.w;
+}
+
+// Big lists of the visited boxes (one list per lane: entries [z, z + w) of
+// the big arrays).  A list whose support box misses the group is skipped;
+// otherwise its 32-entry chunks are tested by their support boxes and the
+// entries of the chunks that pass are tested one by one; entries whose
+// support reaches the group's box are appended to the big buffer.
+template <int KIND, typename T, int R, bool AO>
+LENS_DEV void append_big(WalkCtx<KIND, T, R, AO>& C, bool has, int v, int z, int w, int& nbuf,
+                         int& n_seen, int& n_kept)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const WalkParams<T>& P = C.P;
+    WalkShared<KIND, T>& S = C.S;
+    int cnt = 0;
+    if (has) {
+        vec4_t<T> nb4 = P.node_bigbox[v];
+        if (box_reaches_group<T>(nb4, C.H, C.box)) cnt = ((z + w - 1) >> 5) - (z >> 5) + 1;
+    }
+    int tot;
+    int off = warp_exclusive_scan(cnt, &tot);
+    if (tot == 0) return;
+    S.rs_off[lane] = off;
+    S.rs_first[lane] = z;
+    S.rs_end[lane] = z + w;
+    if (lane == 31) S.rs_off[32] = tot;
+    __syncwarp();
+    for (int base = 0; base < tot; base += 32) {
+        int i = base + lane;
+        int cid = -1, own = 0;
+        bool pass = false;
+        if (i < tot) {
+            int lo = 0, hi = 32;
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (S.rs_off[mid] <= i) lo = mid;
+                else hi = mid;
+            }
+            own = lo;
+            cid = (S.rs_first[lo] >> 5) + (i - S.rs_off[lo]);
+            pass = box_reaches_group<T>(P.big_chunk[cid], C.H, C.box);
+        }
+        unsigned ball = __ballot_sync(full, pass);
+        while (ball) {
+            int src = __ffs(ball) - 1;
+            ball &= ball - 1;
+            int c = __shfl_sync(full, cid, src);
+            int o = __shfl_sync(full, own, src);
+            if (nbuf + 32 > kBigCap) {
+                C.flush_big(nbuf);
+                nbuf = 0;
+                __syncwarp();
+            }
+            int e = 32 * c + lane;
+            bool keep = false;
+            vec4_t<T> q0, q1;
+            bool inr = e >= S.rs_first[o] && e < S.rs_end[o];
+            n_seen += __popc(__ballot_sync(full, inr));
+            if (inr) {
+                q0 = P.big0[e];
+                q0.x -= C.H.x;
+                q0.y -= C.H.y;
+                T ex = fmax(fabs(q0.x - C.box.x) - C.box.z, T(0));
+                T ey = fmax(fabs(q0.y - C.box.y) - C.box.w, T(0));
+                keep = fma(ex, ex, ey * ey) < q0.z;
+            }
+            unsigned kb = __ballot_sync(full, keep);
+            if (keep) {
+                q1 = P.big1[e];
+                int slot = nbuf + __popc(kb & ((1u << lane) - 1u));
+                S.b0[slot] = q0;
+                S.b1[slot] = q1;
+            }
+            nbuf += __popc(kb);
+            n_kept += __popc(kb);
+            __syncwarp();
+        }
+    }
+}
+
 template <int KIND, typename T, int R, bool AO, bool DIRECT>
-__global__ void __launch_bounds__(kWalkWarps * 32)
+__global__ void __launch_bounds__(kWalkWarps * 32, sizeof(T) == 4 ? 6 : 2)
 walk_kernel(WalkParams<T> P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -530,8 +652,7 @@ walk_kernel(WalkParams<T> P)
                     append_ranges<KIND, T, R, AO, false>(C, leaf ? (Lk.y & kCountMask) : 0, Lk.x, nn,
                                                           P.leaf0, P.leaf1, c_near, c_dummy);
                     if constexpr (KIND != LENS_POINT)
-                        append_ranges<KIND, T, R, AO, true>(C, valid ? Lk.w : 0, Lk.z, nb, P.big0,
-                                                             P.big1, c_bigs, c_bigk);
+                        append_big<KIND, T, R, AO>(C, valid && Lk.w > 0, v, Lk.z, Lk.w, nb, c_bigs, c_bigk);
                     __syncwarp();
                     if (nf >= 32) {
                         C.flush_far(nf);
@@ -614,6 +735,10 @@ static int walk_blocks_per_sm()
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(walk_kernel<KIND, T, R, AO, DIRECT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // the walk keeps its working set in shared memory and registers:
+        // prefer the largest shared-memory carveout
+        cudaFuncSetAttribute(walk_kernel<KIND, T, R, AO, DIRECT>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<KIND, T, R, AO, DIRECT>,
                                                       kWalkWarps * 32, smem);
@@ -626,16 +751,16 @@ void free_graphs(lens_tree* t);
 
 static int max_slots(lens_tree* t) { return t->num_sms * 16 * kWalkWarps; }
 
-lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb)
+lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s)
 {
     if (n <= t->ray_cap && nb <= t->batch_cap && t->ray_scratch.ptr) return LENS_OK;
     int64_t nn = std::max(n, t->ray_cap), bb = std::max(nb, t->batch_cap);
     Layout L = make_layout(nn, bb, max_slots(t));
     free_graphs(t);  // captured graphs point into the old scratch
-    if (t->ray_scratch.ptr) cudaFree(t->ray_scratch.ptr);
+    if (t->ray_scratch.ptr) cudaFreeAsync(t->ray_scratch.ptr, s);
     t->ray_scratch.ptr = nullptr;
     t->ray_cap = t->batch_cap = 0;
-    cudaError_t e = cudaMalloc(&t->ray_scratch.ptr, L.total);
+    cudaError_t e = cudaMallocAsync(&t->ray_scratch.ptr, L.total, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return lens_set_error(LENS_ERR_OOM, "cannot allocate %zu bytes of ray scratch", L.total);
@@ -696,7 +821,7 @@ lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const
     const int64_t n = h_off[nb];
     const int R = rays_per_lane(t);
     const int GR = 32 * R;
-    LENS_TRY(reserve_rays(t, n, nb));
+    LENS_TRY(reserve_rays(t, n, nb, s));
     Layout L = make_layout(t->ray_cap, t->batch_cap, max_slots(t));
     char* base = (char*)t->ray_scratch.ptr;
     // pageable host copies: the driver stages them before returning
@@ -794,9 +919,12 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
         P.leaf1 = (const T4*)st.exact1;
         P.big0 = (const T4*)st.big0;
         P.big1 = (const T4*)st.big1;
+        P.big_chunk = (const T4*)st.big_chunk;
+        P.node_bigbox = (const T4*)st.node_bigbox;
         P.n_part = st.n;
         P.Uq = (T)st.Uq;
         P.invNq = (T)st.invNq;
+        P.Uq2 = (T)(st.Uq * 1.4426950408889634074);
         P.halos = t->halos;
         P.n_halos = first_launch ? (int)t->n_halos : 0;
         P.accumulate = first_launch ? ((flags & LENS_ACCUMULATE) ? 1 : 0) : 1;

@@ -38,3 +38,25 @@ def rel_errors(got, ref):
 
 def to_np(outs):
     return np.stack([o.double().cpu().numpy() for o in outs], axis=1)
+
+
+EPS32 = 2.0 ** -24
+
+
+def within_fp32_bar(got, ref, absum, rel=1e-5, k=8.0):
+    """Per output and ray: |d| <= rel * max(|ref|, 1e-3 median |ref|) or, for
+    an ill-conditioned sum, |d| <= k * eps32 * sum |term| (the error any sum
+    of FP32-evaluated terms can carry; the oracle's absum is sum |term|).
+    Returns (ok mask (nr, 3), fraction of rays that needed the second form)."""
+    ok = np.zeros((got.shape[0], 3), bool)
+    cond = np.zeros((got.shape[0], 3), bool)
+    for j, cols in enumerate(([0, 1], [2], [3, 4])):
+        d = np.linalg.norm(got[:, cols] - ref[:, cols], axis=1)
+        r = np.linalg.norm(ref[:, cols], axis=1)
+        a = np.linalg.norm(absum[:, cols], axis=1)
+        floor = 1e-3 * np.median(r) if np.median(r) > 0 else 0.0
+        first = d <= rel * np.maximum(r, floor)
+        second = d <= k * EPS32 * a
+        ok[:, j] = first | second
+        cond[:, j] = ~first & second
+    return ok, cond.any(axis=1).mean()

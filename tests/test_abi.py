@@ -1,0 +1,74 @@
+"""The C ABI without a GPU: liblens loads, exports every function that
+include/lens.h declares, and rejects bad arguments with a status code before
+touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1312_1128_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "lens.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lens_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_status_strings(lib):
+    lib.lens_api_version.restype = ctypes.c_int32
+    assert lib.lens_api_version() == 1
+    lib.lens_status_string.restype = ctypes.c_char_p
+    lib.lens_status_string.argtypes = [ctypes.c_int]
+    assert lib.lens_status_string(0) == b"ok"
+    assert lib.lens_status_string(1) == b"invalid argument"
+    assert lib.lens_status_string(99) == b"unknown status"
+
+
+def test_bad_arguments_return_status(lib):
+    import paper_1312_1128_gb300 as L
+    L.lib()  # sets argtypes
+    lt = L.lib()
+    h = ctypes.c_void_p()
+    # NULL params
+    assert lt.lens_build_tree(None, 0, None, 0, None, None, ctypes.byref(h)) == 1
+    assert h.value is None
+    # negative theta, bad leaf size, unknown precision, reserved != 0
+    for th, leaf, prec, res in [(-1.0, 5, 0, 0), (0.1, 0, 0, 0), (0.1, 5, 7, 0), (0.1, 5, 0, 3)]:
+        p = L._Params(th, leaf, prec, 0, res)
+        assert lt.lens_build_tree(None, 0, None, 0, ctypes.byref(p), None, ctypes.byref(h)) == 1
+    # unknown species kind
+    sp = (L._Species * 1)(L._Species(9, 0, 10, 1, 3.0))
+    p = L._Params(0.1, 5, 0, 0, 0)
+    assert lt.lens_build_tree(sp, 1, None, 0, ctypes.byref(p), None, ctypes.byref(h)) == 1
+    assert b"kind" in lt.lens_last_error()
+    # a halo with a non-positive radius
+    hs = (L._Halo * 1)(L._Halo(4, 0, 0.0, 0.0, 1.0, -1.0, 0.0))
+    assert lt.lens_build_tree(None, 0, hs, 1, ctypes.byref(p), None, ctypes.byref(h)) == 1
+    # shooting with a NULL tree
+    assert lt.lens_shoot_rays(None, 0.0, 0.0, None, None, 0, 10, None, None, None, None, None, 0, None) == 1
+    # batches: offsets must start at 0 and not decrease
+    off = (ctypes.c_int64 * 3)(1, 2, 3)
+    org = (ctypes.c_double * 4)(0, 0, 0, 0)
+    assert lt.lens_shoot_batches(None, 2, off, org, None, None, 0, None, None, None, None, None, 0, None) == 1
+    off = (ctypes.c_int64 * 3)(0, 5, 3)
+    assert lt.lens_shoot_batches(None, 2, off, org, None, None, 0, None, None, None, None, None, 0, None) == 1
+    # backward: kappa/gamma gradients are declared unsupported in this version
+    assert lt.lens_shoot_rays_backward(None, 0.0, 0.0, None, None, 0, 1, None, None, None, None, None,
+                                       None, None, 0, None) == 1

@@ -11,7 +11,7 @@ import pytest
 
 import lensgen
 import oracle
-from lens_testutil import comps_gauss, comps_nfw, comps_points, rel_errors, to_np
+from lens_testutil import comps_gauss, comps_nfw, comps_points, rel_errors, to_np, within_fp32_bar
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -86,14 +86,13 @@ def test_direct_fp32_mixed(group_rays):
     out = lens.shoot(cu(rx), cu(ry), flags=L.DIRECT)
     lens.sync()
     got = to_np(out)
-    ref = oracle.direct_sum(comps, rx.astype(np.float64), ry.astype(np.float64))
+    ref, absum = oracle.direct_sum(comps, rx.astype(np.float64), ry.astype(np.float64), with_absum=True)
     amb = edge_mask(comps, rx.astype(np.float64), ry.astype(np.float64))
     assert amb.sum() <= 0.01 * rx.size
-    ea, ek, eg = rel_errors(got, ref)
-    ok = ~amb
-    assert ea[ok].max() <= 1e-5, ea[ok].max()
-    assert ek[ok].max() <= 1e-5, ek[ok].max()
-    assert eg[ok].max() <= 1e-5, eg[ok].max()
+    ok, frac_cond = within_fp32_bar(got, ref, absum)
+    bad = np.where(~ok[~amb].all(axis=1))[0]
+    assert bad.size == 0, (bad, rel_errors(got, ref)[2][~amb][bad])
+    assert frac_cond <= 0.02
 
 
 # ------------------------------------------------------------- tree mode
