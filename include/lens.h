@@ -221,7 +221,7 @@ lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double or
 /*
  * lens_autotune -- pick the ray-group size (rays sharing one interaction
  * list: 32 or 64) for this tree by timing the walk on the given rays (at most
- * the first 1,048,576; same arguments as lens_shoot_rays) with CUDA events,
+ * the first 8,388,608; same arguments as lens_shoot_rays) with CUDA events,
  * and keep the faster one for later calls.  *group_rays receives the choice.
  * Synchronous; allocates temporary outputs on the device.
  */

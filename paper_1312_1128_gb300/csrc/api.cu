@@ -314,7 +314,7 @@ lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, con
     if (ray_dtype != LENS_F32 && ray_dtype != LENS_F64) return lens_set_error(LENS_ERR_INVALID_ARG, "bad ray dtype");
     if (n <= 0 || !ray_dx || !ray_dy) return lens_set_error(LENS_ERR_INVALID_ARG, "no rays to tune on");
     cudaStream_t s = (cudaStream_t)stream;
-    int64_t m = n < (1 << 20) ? n : (1 << 20);
+    int64_t m = n < (1 << 23) ? n : (1 << 23);
     size_t es = tree->precision == LENS_PREC_FP64 ? 8 : 4;
     void* buf = nullptr;
     LENS_CUDA(cudaMallocAsync(&buf, 5 * m * es, s));

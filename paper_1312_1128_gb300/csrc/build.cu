@@ -518,16 +518,51 @@ __global__ void k_chunkbox(const vec4_t<T>* big0, int64_t nbig, int64_t nchunks,
     out[c] = support_box<T>(big0, b, e);
 }
 
+// One warp per node: the node's list [z, z + w) is covered by the boxes of
+// its whole 32-entry chunks plus the single entries of the partial chunks at
+// its two ends; lanes stride over both and reduce.
 template <typename T>
-__global__ void k_nodebox(const int4* link, uint32_t n_nodes, const vec4_t<T>* big0, vec4_t<T>* out)
+__global__ void k_nodebox(const int4* link, uint32_t n_nodes, const vec4_t<T>* big0,
+                          const vec4_t<T>* chunk, vec4_t<T>* out)
 {
-    uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
     if (v >= n_nodes) return;
     int4 L = link[v];
-    vec4_t<T> r;
-    if (L.w > 0) r = support_box<T>(big0, L.z, (int64_t)L.z + L.w);
-    else { r.x = r.y = (T)INFINITY; r.z = r.w = (T)-INFINITY; }
-    out[v] = r;
+    int64_t z = L.z, e = (int64_t)L.z + L.w;
+    int64_t c0 = (z + 31) >> 5, c1 = e >> 5;  // whole chunks [c0, c1)
+    double x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
+    if (c0 < c1) {
+        for (int64_t c = c0 + lane; c < c1; c += 32) {
+            vec4_t<T> b = chunk[c];
+            x0 = fmin(x0, (double)b.x); y0 = fmin(y0, (double)b.y);
+            x1 = fmax(x1, (double)b.z); y1 = fmax(y1, (double)b.w);
+        }
+    }
+    int64_t head_end = c0 < c1 ? 32 * c0 : e, tail_begin = c0 < c1 ? 32 * c1 : e;
+    for (int64_t i = z + lane; i < head_end; i += 32) {
+        vec4_t<T> q = big0[i];
+        double s = sqrt((double)q.z);
+        x0 = fmin(x0, (double)q.x - s); x1 = fmax(x1, (double)q.x + s);
+        y0 = fmin(y0, (double)q.y - s); y1 = fmax(y1, (double)q.y + s);
+    }
+    for (int64_t i = tail_begin + lane; i < e; i += 32) {
+        vec4_t<T> q = big0[i];
+        double s = sqrt((double)q.z);
+        x0 = fmin(x0, (double)q.x - s); x1 = fmax(x1, (double)q.x + s);
+        y0 = fmin(y0, (double)q.y - s); y1 = fmax(y1, (double)q.y + s);
+    }
+    for (int o = 16; o; o >>= 1) {
+        x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    }
+    if (lane == 0) {
+        vec4_t<T> r;
+        r.x = round_dn<T>(x0); r.y = round_dn<T>(y0); r.z = round_upx<T>(x1); r.w = round_upx<T>(y1);
+        out[v] = r;
+    }
 }
 
 __global__ void k_iota_u32(uint32_t* a, uint32_t n)
@@ -740,7 +775,8 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
             LENS_CUDA(cudaMallocAsync(&st.node_bigbox, (size_t)n_nodes * sizeof(T4), s));
             { k_chunkbox<T><<<grid_for(st.n_chunks, TB), TB, 0, s>>>((T4*)st.big0, nbig, st.n_chunks,
                                                                    (T4*)st.big_chunk); note_launch(); }
-            { k_nodebox<T><<<GN, TB, 0, s>>>(st.link, n_nodes, (T4*)st.big0, (T4*)st.node_bigbox); note_launch(); }
+            { k_nodebox<T><<<grid_for((int64_t)n_nodes * 32, TB), TB, 0, s>>>(st.link, n_nodes, (T4*)st.big0,
+                                                                          (T4*)st.big_chunk, (T4*)st.node_bigbox); note_launch(); }
         }
         cudaFreeAsync(r0sq, s); cudaFreeAsync(bk0, s); cudaFreeAsync(bk1, s);
         cudaFreeAsync(bv0, s); cudaFreeAsync(bv1, s); cudaFreeAsync(end, s);

@@ -222,6 +222,35 @@ LENS_DEV void gauss_correction(Acc5<float>& acc, float wx, float wy, const float
     acc.template radial<AO>(wx, wy, dkb, kap, dDp);
 }
 
+// The same correction when every ray of the group is inside the support and
+// outside the softening radius (decided per entry when it is queued): no
+// selects, and 1/max(r^2, r0^2) = 1/r^2.
+template <bool AO>
+LENS_DEV void gauss_correction_fast(Acc5<float>& acc, float wx, float wy, const float4& q1)
+{
+    using namespace gser;
+    float r2 = fmaf(wx, wx, wy * wy);
+    float inv = rcp(r2);
+    float t = r2 * q1.y;
+    float e = exp2neg(t);
+    float h1, g;
+    if (t < kTSeries) {
+        h1 = fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, H7, H6), H5), H4), H3), H2), H1), H0);
+        g = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, G7, G6), G5), G4), G3), G2), G1), G0);
+    } else {
+        h1 = (1.0f - e) * (inv * q1.w);
+        g = h1 - e;
+    }
+    float minv = q1.x * inv;
+    acc.template radial<AO>(wx, wy, fmaf(q1.z, h1, -minv), q1.z * e, fmaf(q1.z, g, -minv) * inv);
+}
+template <bool AO>
+LENS_DEV void gauss_correction_fast(Acc5<double>& acc, double wx, double wy, const dbl4& q1)
+{
+    dbl4 q{0.0, 0.0, INFINITY, INFINITY};  // no softening: 1/r0^2 = +inf
+    gauss_correction<AO>(acc, wx, wy, q, q1, INFINITY);
+}
+
 // FP64 form of the same correction (q1.y holds c log2 e as well).
 template <bool AO>
 LENS_DEV void gauss_correction(Acc5<double>& acc, double wx, double wy, const dbl4& q, const dbl4& q1,

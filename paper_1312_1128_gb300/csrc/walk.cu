@@ -55,6 +55,8 @@ __device__ __forceinline__ double ray_offset(const void* p, int dtype, int64_t i
 __global__ void k_ray_bbox(const int64_t* boff, int nb, const double* borig, const void* dx,
                            const void* dy, int dtype, int64_t n, unsigned long long* bbox)
 {
+    __shared__ unsigned long long red[4][8];
+    __shared__ int bsame;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = i < n;
     int b = valid ? batch_of(boff, nb, i) : -1;
@@ -63,21 +65,43 @@ __global__ void k_ray_bbox(const int64_t* boff, int nb, const double* borig, con
         px = borig[2 * b] + ray_offset(dx, dtype, i);
         py = borig[2 * b + 1] + ray_offset(dy, dtype, i);
     }
-    unsigned full = 0xffffffffu;
-    int b0 = __shfl_sync(full, b, 0);
-    bool uniform = __all_sync(full, valid && b == b0);
-    unsigned long long x0 = dbl_to_ordered(px), x1 = x0, y0 = dbl_to_ordered(py), y1 = y0;
-    if (uniform) {
+    // whole block in one batch (the common case): reduce in the block, then
+    // four atomics per block
+    int64_t first = (int64_t)blockIdx.x * blockDim.x;
+    int64_t last = first + blockDim.x - 1 < n - 1 ? first + blockDim.x - 1 : n - 1;
+    if (threadIdx.x == 0) bsame = batch_of(boff, nb, first) == batch_of(boff, nb, last);
+    __syncthreads();
+    const unsigned full = 0xffffffffu;
+    unsigned long long x0 = valid ? dbl_to_ordered(px) : ~0ull, x1 = valid ? dbl_to_ordered(px) : 0ull;
+    unsigned long long y0 = valid ? dbl_to_ordered(py) : ~0ull, y1 = valid ? dbl_to_ordered(py) : 0ull;
+    if (bsame) {
         for (int o = 16; o; o >>= 1) {
             x0 = min(x0, __shfl_xor_sync(full, x0, o));
             x1 = max(x1, __shfl_xor_sync(full, x1, o));
             y0 = min(y0, __shfl_xor_sync(full, y0, o));
             y1 = max(y1, __shfl_xor_sync(full, y1, o));
         }
-        if ((threadIdx.x & 31) != 0) return;
-    } else if (!valid) {
+        int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) {
+            red[0][w] = x0; red[1][w] = x1; red[2][w] = y0; red[3][w] = y1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int bb = batch_of(boff, nb, first);
+            for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+                red[0][0] = min(red[0][0], red[0][k]);
+                red[1][0] = max(red[1][0], red[1][k]);
+                red[2][0] = min(red[2][0], red[2][k]);
+                red[3][0] = max(red[3][0], red[3][k]);
+            }
+            atomicMin(&bbox[4 * bb + 0], red[0][0]);
+            atomicMax(&bbox[4 * bb + 1], red[1][0]);
+            atomicMin(&bbox[4 * bb + 2], red[2][0]);
+            atomicMax(&bbox[4 * bb + 3], red[3][0]);
+        }
         return;
     }
+    if (!valid) return;
     atomicMin(&bbox[4 * b + 0], x0);
     atomicMax(&bbox[4 * b + 1], x1);
     atomicMin(&bbox[4 * b + 2], y0);
@@ -322,12 +346,24 @@ template <int KIND, typename T, int R, bool AO> struct WalkCtx {
     {
         int i = 0;
         if constexpr (KIND == LENS_GAUSS) {
+            // b0.w < 0 marks an entry whose support holds the whole group and
+            // whose softening radius no ray reaches (the common case)
             for (; i + 1 < nb; i += 2) {
                 vec4_t<T> q = S.b0[i], q1 = S.b1[i], p = S.b0[i + 1], p1 = S.b1[i + 1];
+                if (q.w < T(0) && p.w < T(0)) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    gauss_correction<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q, q1, P.Uq2);
-                    gauss_correction<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p, p1, P.Uq2);
+                    for (int r = 0; r < R; ++r) {
+                        gauss_correction_fast<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1);
+                        gauss_correction_fast<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p1);
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if (q.w < T(0)) gauss_correction_fast<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1);
+                        else gauss_correction<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q, q1, P.Uq2);
+                        if (p.w < T(0)) gauss_correction_fast<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p1);
+                        else gauss_correction<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p, p1, P.Uq2);
+                    }
                 }
             }
         }
@@ -337,7 +373,8 @@ template <int KIND, typename T, int R, bool AO> struct WalkCtx {
             for (int r = 0; r < R; ++r) {
                 T wx = lx[r] - q.x, wy = ly[r] - q.y;
                 if constexpr (KIND == LENS_GAUSS) {
-                    gauss_correction<AO>(part[r], wx, wy, q, q1, P.Uq2);
+                    if (q.w < T(0)) gauss_correction_fast<AO>(part[r], wx, wy, q1);
+                    else gauss_correction<AO>(part[r], wx, wy, q, q1, P.Uq2);
                 } else {
                     T r2 = fma(wx, wx, wy * wy);
                     T inv = r2 > T(0) ? rcp(r2) : T(0);
@@ -536,7 +573,14 @@ LENS_DEV void append_big(WalkCtx<KIND, T, R, AO>& C, bool has, int v, int z, int
                 q0.y -= C.H.y;
                 T ex = fmax(fabs(q0.x - C.box.x) - C.box.z, T(0));
                 T ey = fmax(fabs(q0.y - C.box.y) - C.box.w, T(0));
-                keep = fma(ex, ex, ey * ey) < q0.z;
+                T near2 = fma(ex, ex, ey * ey);
+                keep = near2 < q0.z;
+                if constexpr (KIND == LENS_GAUSS) {
+                    // whole group inside the support and beyond the softening radius?
+                    T fx = fabs(q0.x - C.box.x) + C.box.z, fy = fabs(q0.y - C.box.y) + C.box.w;
+                    T far2 = fma(fx, fx, fy * fy) * T(1.000001);
+                    if (keep && far2 < q0.z && near2 > T(0) && near2 * q0.w >= T(1.000001)) q0.w = T(-1);
+                }
             }
             unsigned kb = __ballot_sync(full, keep);
             if (keep) {
