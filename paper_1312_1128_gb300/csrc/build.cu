@@ -465,7 +465,7 @@ __global__ void k_bigrecords(const uint32_t* sval, int64_t nbig, const vec4_t<T>
     a.y = q.y;
     a.z = (T)(s * s);
     a.w = r0sq[j] > 0.0 ? (T)(1.0 / r0sq[j]) : (T)INFINITY;  // 1/r0^2
-    b.x = q.z;  // m
+    b.x = kind == LENS_GAUSS ? (T)((double)q.z * invNq) : q.z;  // m/N_q (GAUSS) or m
     if (kind == LENS_NFW) {
         vec4_t<T> q1 = e1[j];
         b.y = q1.x;  // A = m / g(X)

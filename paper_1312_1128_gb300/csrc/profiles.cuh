@@ -193,18 +193,20 @@ LENS_DEV float exp2neg(float t)
     return r;
 }
 
-// Correction (full truncated Gaussian - softened point) at offset w.
-// q = {., ., s^2, 1/r0^2}, q1 = {m, c log2 e, m c / N_q, 1/c}; Uq2 = q^2/2 log2 e.
+// Correction (full truncated Gaussian - softened point) at offset w, for an
+// entry that some ray of the group approaches within its softening radius.
+// q = {., ., s^2, 1/r0^2}, q1 = {m/N_q, c log2 e, m c / N_q, 1/c};
+// Uq2 = q^2/2 log2 e.
 // Outside the support both terms are the same point mass: the result is 0.
 template <bool AO>
 LENS_DEV void gauss_correction(Acc5<float>& acc, float wx, float wy, const float4& q, const float4& q1,
-                               float Uq2)
+                               float Uq2, float Nq)
 {
     using namespace gser;
     float r2 = fmaf(wx, wx, wy * wy);
     float inv = r2 > 0.0f ? rcp(r2) : 0.0f;
     float inv_s = fminf(inv, q.w);
-    float kbp = q1.x * inv_s;
+    float kbp = (q1.x * Nq) * inv_s;
     float t = r2 * q1.y;
     float e = exp2neg(t);
     float h1, g;
@@ -222,45 +224,50 @@ LENS_DEV void gauss_correction(Acc5<float>& acc, float wx, float wy, const float
     acc.template radial<AO>(wx, wy, dkb, kap, dDp);
 }
 
-// The same correction when every ray of the group is inside the support and
-// outside the softening radius (decided per entry when it is queued): no
-// selects, and 1/max(r^2, r0^2) = 1/r^2.
+// The same correction when no ray of the group is inside the softening
+// radius (decided per entry when it is queued), written without cancellation:
+// with Mt(<r) = m (1 - e^-min(u, q^2/2)) / N_q (a point mass m outside),
+//   kb_exact - kb_point = (m/N_q)(1/r^2)(e^-q^2/2 - e^-min(u, q^2/2)),
+// exactly 0 outside the support and well conditioned as u -> 0 (no series,
+// no branch); kappa = m c e^-u / N_q inside, 0 outside; for the shear
+// D = kb - kappa, so D_exact - D_point = (kb_exact - kb_point) - kappa.
+// q1 = {m/N_q, c log2 e, m c / N_q, 1/c}; Uq2 = q^2/2 log2 e; eU = e^-q^2/2.
 template <bool AO>
-LENS_DEV void gauss_correction_fast(Acc5<float>& acc, float wx, float wy, const float4& q1)
+LENS_DEV void gauss_correction_fast(Acc5<float>& acc, float wx, float wy, const float4& q1, float Uq2,
+                                    float eU)
 {
-    using namespace gser;
     float r2 = fmaf(wx, wx, wy * wy);
     float inv = rcp(r2);
     float t = r2 * q1.y;
-    float e = exp2neg(t);
-    float h1, g;
-    if (t < kTSeries) {
-        h1 = fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, H7, H6), H5), H4), H3), H2), H1), H0);
-        g = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, G7, G6), G5), G4), G3), G2), G1), G0);
-    } else {
-        h1 = (1.0f - e) * (inv * q1.w);
-        g = h1 - e;
-    }
-    float minv = q1.x * inv;
-    acc.template radial<AO>(wx, wy, fmaf(q1.z, h1, -minv), q1.z * e, fmaf(q1.z, g, -minv) * inv);
+    float e = exp2neg(fminf(t, Uq2));
+    float dkb = (q1.x * inv) * (eU - e);
+    float kap = t < Uq2 ? q1.z * e : 0.0f;
+    acc.template radial<AO>(wx, wy, dkb, kap, (dkb - kap) * inv);
 }
 template <bool AO>
-LENS_DEV void gauss_correction_fast(Acc5<double>& acc, double wx, double wy, const dbl4& q1)
+LENS_DEV void gauss_correction_fast(Acc5<double>& acc, double wx, double wy, const dbl4& q1, double Uq2,
+                                    double eU)
 {
-    dbl4 q{0.0, 0.0, INFINITY, INFINITY};  // no softening: 1/r0^2 = +inf
-    gauss_correction<AO>(acc, wx, wy, q, q1, INFINITY);
+    const double L = 0.69314718055994530942;
+    double r2 = fma(wx, wx, wy * wy);
+    double inv = 1.0 / r2;
+    double t = r2 * q1.y;
+    double e = exp(-fmin(t, Uq2) * L);
+    double dkb = (q1.x * inv) * (eU - e);
+    double kap = t < Uq2 ? q1.z * e : 0.0;
+    acc.template radial<AO>(wx, wy, dkb, kap, (dkb - kap) * inv);
 }
 
 // FP64 form of the same correction (q1.y holds c log2 e as well).
 template <bool AO>
 LENS_DEV void gauss_correction(Acc5<double>& acc, double wx, double wy, const dbl4& q, const dbl4& q1,
-                               double Uq2)
+                               double Uq2, double Nq)
 {
     const double L = 0.69314718055994530942;
     double r2 = fma(wx, wx, wy * wy);
     double inv = r2 > 0.0 ? 1.0 / r2 : 0.0;
     double inv_s = fmin(inv, q.w);
-    double kbp = q1.x * inv_s;
+    double kbp = (q1.x * Nq) * inv_s;
     double u = r2 * q1.y * L;
     if (!(r2 * q1.y < Uq2)) return;
     double e = exp(-u), h1, g;

@@ -22,6 +22,7 @@
 // support s.  The softening removes the cancellation of a huge point term
 // against its correction when a ray passes close to a listed particle.
 #include <algorithm>
+#include <cmath>
 
 #include "profiles.cuh"
 #include "sort.cuh"
@@ -252,7 +253,7 @@ template <typename T> struct WalkParams {
     const vec4_t<T>* big_chunk;  // support bounding box per 32 entries
     const vec4_t<T>* node_bigbox;
     int64_t n_part;
-    T Uq, invNq, Uq2;
+    T Uq, invNq, Uq2, Nq, eU;
     const v2_t<T>* gH;
     const vec4_t<T>* gbox;
     const uint2* grange;
@@ -339,30 +340,30 @@ template <int KIND, typename T, int R, bool AO> struct WalkCtx {
 
     // Big-list corrections: (full profile - softened point); zero outside the
     // support, where both are the same point mass.
-    // b0 = {x - H.x, y - H.y, s^2, 1/r0^2}; b1 = {m, c log2 e, m c / N_q, 1/c}
-    // (GAUSS) or {m, A, B, 0} (NFW).  1/max(r^2, r0^2) = min(1/r^2, 1/r0^2).
+    // b0 = {x - H.x, y - H.y, s^2, 1/r0^2}; b1 = {m/N_q, c log2 e, m c / N_q,
+    // 1/c} (GAUSS) or {m, A, B, 0} (NFW).  1/max(r^2, r0^2) = min(1/r^2, 1/r0^2).
     // Two entries per iteration for instruction-level parallelism.
     LENS_DEV void flush_big(int nb)
     {
         int i = 0;
         if constexpr (KIND == LENS_GAUSS) {
-            // b0.w < 0 marks an entry whose support holds the whole group and
-            // whose softening radius no ray reaches (the common case)
+            // b0.w < 0 marks an entry whose softening radius no ray of the
+            // group reaches (the common case)
             for (; i + 1 < nb; i += 2) {
                 vec4_t<T> q = S.b0[i], q1 = S.b1[i], p = S.b0[i + 1], p1 = S.b1[i + 1];
                 if (q.w < T(0) && p.w < T(0)) {
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        gauss_correction_fast<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1);
-                        gauss_correction_fast<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p1);
+                        gauss_correction_fast<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1, P.Uq2, P.eU);
+                        gauss_correction_fast<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p1, P.Uq2, P.eU);
                     }
                 } else {
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        if (q.w < T(0)) gauss_correction_fast<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1);
-                        else gauss_correction<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q, q1, P.Uq2);
-                        if (p.w < T(0)) gauss_correction_fast<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p1);
-                        else gauss_correction<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p, p1, P.Uq2);
+                        if (q.w < T(0)) gauss_correction_fast<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1, P.Uq2, P.eU);
+                        else gauss_correction<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q, q1, P.Uq2, P.Nq);
+                        if (p.w < T(0)) gauss_correction_fast<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p1, P.Uq2, P.eU);
+                        else gauss_correction<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p, p1, P.Uq2, P.Nq);
                     }
                 }
             }
@@ -373,8 +374,8 @@ template <int KIND, typename T, int R, bool AO> struct WalkCtx {
             for (int r = 0; r < R; ++r) {
                 T wx = lx[r] - q.x, wy = ly[r] - q.y;
                 if constexpr (KIND == LENS_GAUSS) {
-                    if (q.w < T(0)) gauss_correction_fast<AO>(part[r], wx, wy, q1);
-                    else gauss_correction<AO>(part[r], wx, wy, q, q1, P.Uq2);
+                    if (q.w < T(0)) gauss_correction_fast<AO>(part[r], wx, wy, q1, P.Uq2, P.eU);
+                    else gauss_correction<AO>(part[r], wx, wy, q, q1, P.Uq2, P.Nq);
                 } else {
                     T r2 = fma(wx, wx, wy * wy);
                     T inv = r2 > T(0) ? rcp(r2) : T(0);
@@ -576,10 +577,8 @@ LENS_DEV void append_big(WalkCtx<KIND, T, R, AO>& C, bool has, int v, int z, int
                 T near2 = fma(ex, ex, ey * ey);
                 keep = near2 < q0.z;
                 if constexpr (KIND == LENS_GAUSS) {
-                    // whole group inside the support and beyond the softening radius?
-                    T fx = fabs(q0.x - C.box.x) + C.box.z, fy = fabs(q0.y - C.box.y) + C.box.w;
-                    T far2 = fma(fx, fx, fy * fy) * T(1.000001);
-                    if (keep && far2 < q0.z && near2 > T(0) && near2 * q0.w >= T(1.000001)) q0.w = T(-1);
+                    // every ray of the group beyond the softening radius?
+                    if (keep && near2 > T(0) && near2 * q0.w >= T(1.000001)) q0.w = T(-1);
                 }
             }
             unsigned kb = __ballot_sync(full, keep);
@@ -969,6 +968,8 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
         P.Uq = (T)st.Uq;
         P.invNq = (T)st.invNq;
         P.Uq2 = (T)(st.Uq * 1.4426950408889634074);
+        P.Nq = (T)(st.invNq > 0 ? 1.0 / st.invNq : 0.0);
+        P.eU = (T)std::exp(-st.Uq);
         P.halos = t->halos;
         P.n_halos = first_launch ? (int)t->n_halos : 0;
         P.accumulate = first_launch ? ((flags & LENS_ACCUMULATE) ? 1 : 0) : 1;
