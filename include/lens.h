@@ -229,6 +229,34 @@ lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, con
                           const void* ray_dy, int32_t ray_dtype, int64_t n, void* stream,
                           int32_t* group_rays);
 
+/*
+ * lens_shoot_rays_direct_noalloc -- the direct sum of lens_shoot_rays with
+ * LENS_DIRECT, for callers that cannot allocate device memory during the
+ * call: code that runs while another component owns the device allocator,
+ * latency-bound loops that cannot absorb the device-wide synchronisation a
+ * cudaMalloc may cause, or deployments that reserve a fixed device budget up
+ * front.  The paper has no counterpart; it is a deployment variant only.
+ *   Arguments, output layout and results are those of lens_shoot_rays with
+ *   LENS_DIRECT (rays are grouped 32 at a time in their input order instead
+ *   of being sorted, so results can differ from it by FP32 rounding).
+ *   flags: LENS_ALPHA_ONLY and LENS_ACCUMULATE only.
+ *   n: at most 262,144 rays per call; larger n returns LENS_ERR_INVALID_ARG
+ *   and launches nothing.
+ * Scratch: a fixed 5.4 MiB device array defined in the library, present on
+ * every GPU that loads the library until the process exits.  The first call
+ * on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  The call makes
+ * no cudaMalloc, cudaFree or other allocating call.  All calls share the one
+ * array, which keeps the last call's contents (the call clears what must
+ * start at zero): calls that overlap on the GPU, on any streams, race, so
+ * order them (one stream, or events).  The tree must have been built on the
+ * current device.
+ */
+lens_status lens_shoot_rays_direct_noalloc(lens_tree* tree, double origin_x, double origin_y,
+                                           const void* ray_dx, const void* ray_dy, int32_t ray_dtype,
+                                           int64_t n, void* alpha1, void* alpha2, void* kappa,
+                                           void* gamma1, void* gamma2, int32_t flags, void* stream);
+
 /* lens_reserve -- grow the tree's scratch for up to max_rays rays in up to
  * max_batches batches, so that later calls of that size allocate nothing. */
 lens_status lens_reserve(lens_tree* tree, int64_t max_rays, int64_t max_batches);

@@ -85,6 +85,7 @@ def lib():
     L.lens_shoot_rays_backward.argtypes = [vp, d, d, vp, vp, i32, i64, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(vp), vp, i32, vp]
     L.lens_reserve.argtypes = [vp, i64, i64]
+    L.lens_shoot_rays_direct_noalloc.argtypes = [vp, d, d, vp, vp, i32, i64, vp, vp, vp, vp, vp, i32, vp]
     L.lens_autotune.argtypes = [vp, d, d, vp, vp, i32, i64, vp, ctypes.POINTER(ctypes.c_int32)]
     L.lens_sync_status.argtypes = [vp, vp]
     L.lens_tree_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
@@ -101,7 +102,8 @@ def lib():
     for name in ["lens_build_tree", "lens_shoot_rays", "lens_shoot_batches",
                  "lens_shoot_rays_backward", "lens_reserve", "lens_sync_status",
                  "lens_tree_get_info", "lens_tree_export", "lens_fp32_peak", "lens_api_version",
-                 "lens_tree_counters", "lens_last_timing", "lens_autotune"]:
+                 "lens_tree_counters", "lens_last_timing", "lens_autotune",
+                 "lens_shoot_rays_direct_noalloc"]:
         getattr(L, name).restype = ctypes.c_int32
     _lib = L
     return L
@@ -295,6 +297,16 @@ class Lens:
         _check(lib().lens_shoot_rays(self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx),
                                      _dev_ptr(dy), rd, n, *[_dev_ptr(o) for o in out], int(flags),
                                      _stream_ptr(stream)))
+        return out
+
+    def shoot_direct_noalloc(self, dx, dy, out, origin=(0.0, 0.0), flags: int = 0, stream=None):
+        """Direct sum into caller-provided outputs without any device
+        allocation (at most 262,144 rays per call; see lens.h)."""
+        torch = _torch()
+        rd = F32 if dx.dtype == torch.float32 else F64
+        _check(lib().lens_shoot_rays_direct_noalloc(
+            self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx), _dev_ptr(dy), rd, dx.numel(),
+            *[_dev_ptr(o) for o in out], int(flags), _stream_ptr(stream)))
         return out
 
     def shoot_batches(self, offsets, origins, dx, dy, flags: int = 0, out=None, stream=None):

@@ -22,6 +22,7 @@
 // support s.  The softening removes the cancellation of a huge point term
 // against its correction when a ray passes close to a listed particle.
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 
 #include "profiles.cuh"
@@ -1020,3 +1021,198 @@ lens_status shoot(lens_tree* t, int64_t nb, const int64_t* h_off, const double* 
 void* scratch_base(lens_tree* t) { return t->ray_scratch.ptr; }
 
 }  // namespace lens
+
+// ===================================================== allocation-free shoot
+//
+// lens_shoot_rays_direct_noalloc: the direct sum over every particle of a
+// built tree, for callers that must not allocate device memory while they
+// shoot rays.  Its ray-group scratch (work counters, per-group anchors and
+// boxes, per-ray offsets and indices) lives in one file-scope device array of
+// fixed size instead of the tree's on-demand buffers; rays are grouped in
+// their input order, 32 per group, so no sort buffers are needed.
+
+namespace lens {
+
+constexpr int64_t kNoAllocMaxRays = 262144;
+constexpr size_t kNoAllocGroups = (size_t)(kNoAllocMaxRays / 32 + 1);
+constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+// byte offsets of the pieces (every piece 256-byte aligned; sizes for FP64)
+constexpr size_t kNaCounters = 0;  // one work counter per launch (64 launches)
+constexpr size_t kNaRayL = kNaCounters + 256;
+constexpr size_t kNaRayIdx = kNaRayL + al256((size_t)kNoAllocMaxRays * 2 * sizeof(double));
+constexpr size_t kNaGH = kNaRayIdx + al256((size_t)kNoAllocMaxRays * sizeof(uint32_t));
+constexpr size_t kNaGBox = kNaGH + al256(kNoAllocGroups * 2 * sizeof(double));
+constexpr size_t kNaGRange = kNaGBox + al256(kNoAllocGroups * 4 * sizeof(double));
+constexpr size_t kNoAllocBytes = kNaGRange + al256(kNoAllocGroups * sizeof(uint2));
+
+// One copy per device that loads the library, held until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+template <typename T>
+__global__ void k_groups_inorder(int64_t n, double ox, double oy, const void* dx, const void* dy, int dtype,
+                                 int64_t n_groups, v2_t<T>* gH, vec4_t<T>* gbox, uint2* grange,
+                                 v2_t<T>* ray_l, uint32_t* ray_idx)
+{
+    const unsigned full = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= n_groups) return;
+    int64_t i = 32 * g + lane;
+    bool v = i < n;
+    double px = v ? ox + ray_offset(dx, dtype, i) : 0.0, py = v ? oy + ray_offset(dy, dtype, i) : 0.0;
+    double xmin = v ? px : INFINITY, xmax = v ? px : -INFINITY, ymin = v ? py : INFINITY, ymax = v ? py : -INFINITY;
+    for (int o = 16; o; o >>= 1) {
+        xmin = fmin(xmin, __shfl_xor_sync(full, xmin, o));
+        xmax = fmax(xmax, __shfl_xor_sync(full, xmax, o));
+        ymin = fmin(ymin, __shfl_xor_sync(full, ymin, o));
+        ymax = fmax(ymax, __shfl_xor_sync(full, ymax, o));
+    }
+    bool exact = !v || ((double)(T)px == px && (double)(T)py == py);
+    exact = __all_sync(full, exact);
+    T Hx = exact ? T(0) : (T)(0.5 * (xmin + xmax)), Hy = exact ? T(0) : (T)(0.5 * (ymin + ymax));
+    T lx = v ? (T)(px - (double)Hx) : T(0), ly = v ? (T)(py - (double)Hy) : T(0);
+    T lxmin = v ? lx : (T)INFINITY, lxmax = v ? lx : (T)-INFINITY, lymin = v ? ly : (T)INFINITY,
+      lymax = v ? ly : (T)-INFINITY;
+    for (int o = 16; o; o >>= 1) {
+        lxmin = fmin(lxmin, __shfl_xor_sync(full, lxmin, o));
+        lxmax = fmax(lxmax, __shfl_xor_sync(full, lxmax, o));
+        lymin = fmin(lymin, __shfl_xor_sync(full, lymin, o));
+        lymax = fmax(lymax, __shfl_xor_sync(full, lymax, o));
+    }
+    if (v) {
+        v2_t<T> l;
+        l.x = lx;
+        l.y = ly;
+        ray_l[i] = l;
+        ray_idx[i] = (uint32_t)i;
+    }
+    if (lane == 0) {
+        T cx = T(0.5) * (lxmin + lxmax), cy = T(0.5) * (lymin + lymax);
+        T hx = fmax(lxmax - cx, cx - lxmin) * T(1.0 + 1e-5) + T(1e-30);
+        T hy = fmax(lymax - cy, cy - lymin) * T(1.0 + 1e-5) + T(1e-30);
+        v2_t<T> H;
+        H.x = Hx;
+        H.y = Hy;
+        gH[g] = H;
+        vec4_t<T> bx;
+        bx.x = cx; bx.y = cy; bx.z = hx; bx.w = hy;
+        gbox[g] = bx;
+        int64_t cnt = n - 32 * g;
+        grange[g] = make_uint2((uint32_t)(32 * g), (uint32_t)(cnt < 32 ? cnt : 32));
+    }
+}
+
+// Device address of the scratch array, looked up once per device with that
+// device current (the host-side name of a __device__ array is only a handle).
+static unsigned char* noalloc_scratch_ptr(int dev, lens_status* st)
+{
+    static std::mutex mu;
+    static unsigned char* ptrs[256] = {nullptr};
+    if (dev < 0 || dev >= 256) {
+        *st = lens_set_error(LENS_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            *st = lens_cuda_check(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress");
+            return nullptr;
+        }
+        ptrs[dev] = (unsigned char*)p;
+    }
+    *st = LENS_OK;
+    return ptrs[dev];
+}
+
+template <typename T>
+static lens_status noalloc_typed(lens_tree* t, double ox, double oy, const void* dx, const void* dy,
+                                 int dtype, int64_t n, void* const out[5], int flags, cudaStream_t s)
+{
+    using T4 = vec4_t<T>;
+    using T2 = v2_t<T>;
+    lens_status st;
+    unsigned char* base = noalloc_scratch_ptr(t->device, &st);
+    if (!base) return st;
+    uint32_t* counters = (uint32_t*)(base + kNaCounters);
+    T2* ray_l = (T2*)(base + kNaRayL);
+    uint32_t* ray_idx = (uint32_t*)(base + kNaRayIdx);
+    T2* gH = (T2*)(base + kNaGH);
+    T4* gbox = (T4*)(base + kNaGBox);
+    uint2* grange = (uint2*)(base + kNaGRange);
+    const int64_t ng = (n + 31) / 32;
+    // the work counters must start at zero: the array keeps the last call's values
+    LENS_CUDA(cudaMemsetAsync(counters, 0, 256, s));
+    { k_groups_inorder<T><<<grid_for(ng * 32, 256), 256, 0, s>>>(n, ox, oy, dx, dy, dtype, ng, gH, gbox, grange,
+                                                                 ray_l, ray_idx); note_launch(); }
+    WalkParams<T> P{};
+    P.gH = gH; P.gbox = gbox; P.grange = grange; P.ray_l = ray_l; P.ray_idx = ray_idx;
+    P.n_groups = ng;
+    P.stack = (int*)base;  // the direct sum never touches a stack
+    P.err = t->d_err;
+    for (int q = 0; q < 5; ++q) P.out[q] = (T*)out[q];
+    const bool ao = (flags & LENS_ALPHA_ONLY) != 0;
+    int launches = 0;
+    bool first_launch = true;
+    for (size_t si = 0; si < t->sp.size(); ++si) {
+        const SpeciesTree& sp = t->sp[si];
+        if (sp.n == 0) continue;
+        P.leaf0 = (const T4*)sp.exact0;
+        P.leaf1 = (const T4*)sp.exact1;
+        P.n_part = sp.n;
+        P.Uq = (T)sp.Uq;
+        P.invNq = (T)sp.invNq;
+        P.halos = t->halos;
+        P.n_halos = first_launch ? (int)t->n_halos : 0;
+        P.accumulate = first_launch ? ((flags & LENS_ACCUMULATE) ? 1 : 0) : 1;
+        P.counter = counters + launches;
+        launch_dispatch<T, 1>(sp.kind, ao, true, P, t->num_sms, s);
+        first_launch = false;
+        ++launches;
+    }
+    if (first_launch) {
+        P.n_part = 0;
+        P.halos = t->halos;
+        P.n_halos = (int)t->n_halos;
+        P.accumulate = (flags & LENS_ACCUMULATE) ? 1 : 0;
+        P.counter = counters;
+        launch_dispatch<T, 1>(LENS_POINT, ao, true, P, t->num_sms, s);
+    }
+    LENS_CUDA(cudaGetLastError());
+    return LENS_OK;
+}
+
+}  // namespace lens
+
+extern "C" lens_status lens_shoot_rays_direct_noalloc(lens_tree* tree, double origin_x, double origin_y,
+                                                      const void* ray_dx, const void* ray_dy,
+                                                      int32_t ray_dtype, int64_t n, void* alpha1,
+                                                      void* alpha2, void* kappa, void* gamma1, void* gamma2,
+                                                      int32_t flags, void* stream)
+{
+    using namespace lens;
+    if (!tree) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
+    if (flags & ~(LENS_ALPHA_ONLY | LENS_ACCUMULATE))
+        return lens_set_error(LENS_ERR_INVALID_ARG, "only LENS_ALPHA_ONLY and LENS_ACCUMULATE apply here");
+    if (n < 0) return lens_set_error(LENS_ERR_INVALID_ARG, "n must be >= 0");
+    if (n > kNoAllocMaxRays)
+        return lens_set_error(LENS_ERR_INVALID_ARG,
+                              "lens_shoot_rays_direct_noalloc takes at most %lld rays per call (got %lld)",
+                              (long long)kNoAllocMaxRays, (long long)n);
+    if (ray_dtype != LENS_F32 && ray_dtype != LENS_F64) return lens_set_error(LENS_ERR_INVALID_ARG, "bad ray dtype");
+    if (!std::isfinite(origin_x) || !std::isfinite(origin_y))
+        return lens_set_error(LENS_ERR_INVALID_ARG, "origin must be finite");
+    if (n == 0) return LENS_OK;
+    if (!ray_dx || !ray_dy || !alpha1 || !alpha2) return lens_set_error(LENS_ERR_INVALID_ARG, "NULL array");
+    if (!(flags & LENS_ALPHA_ONLY) && (!kappa || !gamma1 || !gamma2))
+        return lens_set_error(LENS_ERR_INVALID_ARG, "kappa/gamma outputs are NULL without LENS_ALPHA_ONLY");
+    int dev = -1;
+    LENS_CUDA(cudaGetDevice(&dev));
+    if (dev != tree->device) return lens_set_error(LENS_ERR_INVALID_ARG, "tree was built on another device");
+    void* out[5] = {alpha1, alpha2, kappa, gamma1, gamma2};
+    cudaStream_t s = (cudaStream_t)stream;
+    if (tree->precision == LENS_PREC_FP64)
+        return noalloc_typed<double>(tree, origin_x, origin_y, ray_dx, ray_dy, ray_dtype, n, out, flags, s);
+    return noalloc_typed<float>(tree, origin_x, origin_y, ray_dx, ray_dy, ray_dtype, n, out, flags, s);
+}
