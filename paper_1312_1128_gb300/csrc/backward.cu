@@ -1,15 +1,734 @@
-// backward.cu -- adjoint of the tree walk (placeholder until implemented).
-#include "tree.cuh"
+// backward.cu -- adjoint of the tree walk: gradient of a loss of the
+// deflection with respect to particle masses and positions and halo
+// parameters (no counterpart in the paper; it differentiates the tree
+// approximation of Sec. 3.2 that the forward walk computes).
+//
+// The rays are grouped exactly as in the forward call and every group walks
+// the tree with the same acceptance tests, so it meets the same accepted
+// cells, opened leaves and big-list entries.  The buffers are evaluated
+// transposed: each lane owns one buffered entry (cell or particle) and loops
+// over the group's rays, whose offsets and upstream gradients G = dL/dalpha
+// sit in shared memory; a lane ends with its entry's gradient and adds it
+// with one atomic per quantity.
+//
+//   particle terms (leaf particles, big-list corrections, halos): alpha is
+//   linear in the mass, so dalpha/dm = alpha/m, and dalpha/dx_p = -J with J
+//   the term's own Jacobian [[kappa+g1, g2], [g2, kappa-g1]] (Eqs. kappa,
+//   gamma_1, gamma_2);
+//   far cells, conj(alpha) = M/w + Q2/w^3 with w = x - x_cm: per cell the
+//   adjoints a = dL/dM, C = dL/dQ2 and B = dL/dz_cm (dL = Re(G dA) with
+//   A = conj(alpha)).  Since dM = dm_i, dz_cm = (dm_i d_i + m_i dz_i)/M and
+//   dQ2 = dm_i d_i^2 + 2 m_i d_i dz_i (d_i = z_i - z_cm), a particle inside
+//   the cell receives dL/dm_i = Re P(d_i) and dL/dz_i = m_i P'(d_i) with the
+//   quadratic P(d) = a + (B/M) d + C d^2.  The polynomials of all accepted
+//   ancestors are re-centred and summed from the root down, then evaluated at
+//   every particle of every leaf.
+#include <algorithm>
+#include <cmath>
+
+#include "profiles.cuh"
+#include "walk_shared.cuh"
 
 namespace lens {
+
+template <typename T> struct BackParams {
+    const vec4_t<T>* nodeA;
+    const v2_t<T>* nodeB;
+    const int4* link;
+    const vec4_t<T>* leaf0;
+    const vec4_t<T>* leaf1;
+    const vec4_t<T>* big0;
+    const vec4_t<T>* big1;
+    const vec4_t<T>* big_chunk;
+    const vec4_t<T>* node_bigbox;
+    const uint32_t* big_pid;
+    int64_t n_part;
+    T Uq, invNq, Uq2, Nq, eU;
+    const v2_t<T>* gH;
+    const vec4_t<T>* gbox;
+    const uint2* grange;
+    const v2_t<T>* ray_l;
+    const uint32_t* ray_idx;
+    int64_t n_groups;
+    const T* ga1;   // dL/dalpha1 per caller ray
+    const T* ga2;
+    const HaloDev* halos;
+    int n_halos;
+    double* ghalo;  // n_halos x 3, or null
+    float* adj;     // n_nodes x 5: dL/dM, dL/dQ2 (re, im), dL/dz_cm (re, im)
+    float* gpart;   // n x 3 in tree order: dL/dm, dL/dx, dL/dy
+    uint32_t* counter;
+    int* stack;
+    uint32_t* err;
+};
+
+constexpr int kMaxGroup = 64;
+
+template <int KIND, typename T> struct BackShared {
+    T rx[kMaxGroup], ry[kMaxGroup], rg1[kMaxGroup], rg2[kMaxGroup];
+    T fdx[kFarCap], fdy[kFarCap], fM[kFarCap], fqr[kFarCap], fqi[kFarCap];
+    int fnode[kFarCap];
+    vec4_t<T> n0[kNearCap];
+    vec4_t<T> n1[KIND == LENS_NFW ? kNearCap : 1];
+    int npid[kNearCap];
+    vec4_t<T> b0[KIND == LENS_POINT ? 1 : kBigCap];
+    vec4_t<T> b1[KIND == LENS_POINT ? 1 : kBigCap];
+    int bpid[KIND == LENS_POINT ? 1 : kBigCap];
+    int rs_off[33];
+    int rs_first[32];
+    int rs_end[32];
+};
+
+// Gradient of the loss through one particle term (kb, kap, Dp) at offset w
+// for upstream gradient (g1, g2): adds G.alpha_t (to be divided by m) and
+// -J^T G.
+template <typename T>
+LENS_DEV void term_grad(T wx, T wy, T kb, T kap, T Dp, T g1, T g2, T& gm, T& gx, T& gy)
+{
+    T a1 = kb * wx, a2 = kb * wy;
+    T c2 = fma(wx, wx, -wy * wy), s2 = (wx + wx) * wy;
+    T gg1 = -Dp * c2, gg2 = -Dp * s2;
+    gm = fma(g1, a1, fma(g2, a2, gm));
+    gx -= fma(g1, kap + gg1, g2 * gg2);
+    gy -= fma(g1, gg2, g2 * (kap - gg1));
+}
+
+// Term values of the forward's leaf records and big-list corrections.
+template <int KIND, typename T>
+LENS_DEV void leaf_term(const BackParams<T>& P, const vec4_t<T>& q, const vec4_t<T>& q1, T r2, T& kb, T& kap,
+                        T& Dp)
+{
+    kap = T(0);
+    if constexpr (KIND == LENS_POINT) {
+        point_terms(q.z, r2, kb, Dp);
+    } else if constexpr (KIND == LENS_GAUSS) {
+        if (q.w > T(0)) gauss_terms(q.z, q.w, r2, P.Uq, P.invNq, kb, kap, Dp);
+        else point_terms(q.z, fmax(r2, -q.w), kb, Dp);
+    } else {
+        if (q.w > T(0)) nfw_terms(q.z, q.w, q1.x, q1.y, r2, kb, kap, Dp);
+        else point_terms(q.z, fmax(r2, -q.w), kb, Dp);
+    }
+}
+
+template <int KIND, typename T>
+LENS_DEV void big_term(const BackParams<T>& P, const vec4_t<T>& q, const vec4_t<T>& q1, T r2, T& kb, T& kap,
+                       T& Dp)
+{
+    if constexpr (KIND == LENS_GAUSS) {
+        const double L = 0.69314718055994530942;
+        if (q.w < T(0)) {
+            // no ray inside the softening radius: closed form of (full - point)
+            T inv = rcp(r2);
+            T t = r2 * q1.y;
+            T e = (T)exp2(-(double)fmin(t, P.Uq2));
+            kb = (q1.x * inv) * (P.eU - e);
+            kap = t < P.Uq2 ? q1.z * e : T(0);
+            Dp = (kb - kap) * inv;
+        } else {
+            T inv = r2 > T(0) ? rcp(r2) : T(0);
+            T inv_s = fmin(inv, q.w);
+            T kbp = (q1.x * P.Nq) * inv_s;
+            T t = r2 * q1.y;
+            if (t < P.Uq2) {
+                T u = (T)((double)t * L);
+                T e = (T)exp(-(double)u), h1, g;
+                gauss_h1_g(u, e, h1, g);
+                kb = q1.z * h1 - kbp;
+                kap = q1.z * e;
+                Dp = (q1.z * g) * inv - kbp * inv_s;
+            } else {
+                kb = T(0);
+                kap = T(0);
+                Dp = T(0);
+            }
+        }
+    } else {
+        T inv = r2 > T(0) ? rcp(r2) : T(0);
+        T inv_s = fmin(inv, q.w);
+        T kbp = q1.x * inv_s;
+        T kbe, kape, Dpe;
+        nfw_terms(q1.x, q.z, q1.y, q1.z, r2, kbe, kape, Dpe);
+        kb = kbe - kbp;
+        kap = kape;
+        Dp = Dpe - kbp * inv_s;
+    }
+}
+
+template <int KIND, typename T> struct BackCtx {
+    const BackParams<T>& P;
+    BackShared<KIND, T>& S;
+    int nr;  // rays in the group
+    v2_t<T> H;
+    vec4_t<T> box;
+
+    LENS_DEV BackCtx(const BackParams<T>& p, BackShared<KIND, T>& s) : P(p), S(s) {}
+
+    // lane c owns far cell c: dL/dM, dL/dQ2, dL/dz_cm over the group's rays
+    LENS_DEV void flush_far(int nf)
+    {
+        int lane = threadIdx.x & 31;
+        __syncwarp();
+        if (lane < nf) {
+            T dx = S.fdx[lane], dy = S.fdy[lane], M = S.fM[lane], qr = S.fqr[lane], qi = S.fqi[lane];
+            T aM = T(0), cr = T(0), ci = T(0), br = T(0), bi = T(0);
+            for (int j = 0; j < nr; ++j) {
+                T wx = S.rx[j] - dx, wy = S.ry[j] - dy;
+                T g1 = S.rg1[j], g2 = S.rg2[j];
+                T inv = rcp(fma(wx, wx, wy * wy));
+                T ux = wx * inv, uy = -wy * inv;
+                T u2x = fma(ux, ux, -uy * uy), u2y = (ux + ux) * uy;
+                T u3x = fma(u2x, ux, -u2y * uy), u3y = fma(u2x, uy, u2y * ux);
+                T u4x = fma(u2x, u2x, -u2y * u2y), u4y = (u2x + u2x) * u2y;
+                // G = g1 + i g2 multiplies dA (A = conj(alpha)); dL = Re(G dA)
+                aM += g1 * ux - g2 * uy;
+                cr += g1 * u3x - g2 * u3y;
+                ci += g1 * u3y + g2 * u3x;
+                T tx = M * u2x + T(3) * (qr * u4x - qi * u4y), ty = M * u2y + T(3) * (qr * u4y + qi * u4x);
+                br += g1 * tx - g2 * ty;
+                bi += g1 * ty + g2 * tx;
+            }
+            float* a = P.adj + 5 * (int64_t)S.fnode[lane];
+            atomicAdd(a + 0, (float)aM);
+            atomicAdd(a + 1, (float)cr);
+            atomicAdd(a + 2, (float)ci);
+            atomicAdd(a + 3, (float)br);
+            atomicAdd(a + 4, (float)bi);
+        }
+        __syncwarp();
+    }
+
+    LENS_DEV void add_particle(int pid, T m, T gm, T gx, T gy)
+    {
+        float* g = P.gpart + 3 * (int64_t)pid;
+        if (m != T(0)) atomicAdd(g + 0, (float)(gm / m));
+        atomicAdd(g + 1, (float)gx);
+        atomicAdd(g + 2, (float)gy);
+    }
+
+    LENS_DEV void flush_near(int nn)
+    {
+        int lane = threadIdx.x & 31;
+        __syncwarp();
+        for (int i = lane; i < nn; i += 32) {
+            vec4_t<T> q = S.n0[i], q1;
+            if constexpr (KIND == LENS_NFW) q1 = S.n1[i];
+            T gm = T(0), gx = T(0), gy = T(0);
+            for (int j = 0; j < nr; ++j) {
+                T wx = S.rx[j] - q.x, wy = S.ry[j] - q.y;
+                T r2 = fma(wx, wx, wy * wy), kb, kap, Dp;
+                leaf_term<KIND, T>(P, q, q1, r2, kb, kap, Dp);
+                term_grad(wx, wy, kb, kap, Dp, S.rg1[j], S.rg2[j], gm, gx, gy);
+            }
+            add_particle(S.npid[i], q.z, gm, gx, gy);
+        }
+        __syncwarp();
+    }
+
+    LENS_DEV void flush_big(int nb)
+    {
+        int lane = threadIdx.x & 31;
+        __syncwarp();
+        for (int i = lane; i < nb; i += 32) {
+            vec4_t<T> q = S.b0[i], q1 = S.b1[i];
+            T gm = T(0), gx = T(0), gy = T(0);
+            for (int j = 0; j < nr; ++j) {
+                T wx = S.rx[j] - q.x, wy = S.ry[j] - q.y;
+                T r2 = fma(wx, wx, wy * wy), kb, kap, Dp;
+                big_term<KIND, T>(P, q, q1, r2, kb, kap, Dp);
+                term_grad(wx, wy, kb, kap, Dp, S.rg1[j], S.rg2[j], gm, gx, gy);
+            }
+            T m = KIND == LENS_GAUSS ? q1.x * P.Nq : q1.x;
+            add_particle(S.bpid[i], m, gm, gx, gy);
+        }
+        __syncwarp();
+    }
+};
+
+// Same selection as the forward's leaf append, recording tree positions.
+template <int KIND, typename T>
+LENS_DEV void back_append_near(BackCtx<KIND, T>& C, int cnt, int first, int& nbuf, const vec4_t<T>* src0,
+                               const vec4_t<T>* src1)
+{
+    const unsigned full = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    int tot;
+    int off = warp_exclusive_scan(cnt, &tot);
+    if (tot == 0) return;
+    BackShared<KIND, T>& S = C.S;
+    S.rs_off[lane] = off;
+    S.rs_first[lane] = first;
+    if (lane == 31) S.rs_off[32] = tot;
+    __syncwarp();
+    for (int base = 0; base < tot; base += 32) {
+        if (nbuf + 32 > kNearCap) {
+            C.flush_near(nbuf);
+            nbuf = 0;
+        }
+        int i = base + lane;
+        if (i < tot) {
+            int lo = 0, hi = 32;
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (S.rs_off[mid] <= i) lo = mid;
+                else hi = mid;
+            }
+            int p = S.rs_first[lo] + (i - S.rs_off[lo]);
+            vec4_t<T> q0 = src0[p];
+            q0.x -= C.H.x;
+            q0.y -= C.H.y;
+            S.n0[nbuf + lane] = q0;
+            if constexpr (KIND == LENS_NFW) S.n1[nbuf + lane] = src1[p];
+            S.npid[nbuf + lane] = p;
+        }
+        nbuf += tot - base < 32 ? tot - base : 32;
+        __syncwarp();
+    }
+    (void)full;
+}
+
+// Same selection as the forward's big-list append (two-level support boxes,
+// per-entry support test, fast-path flag), recording tree positions.
+template <int KIND, typename T>
+LENS_DEV void back_append_big(BackCtx<KIND, T>& C, bool has, int v, int z, int w, int& nbuf)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const BackParams<T>& P = C.P;
+    BackShared<KIND, T>& S = C.S;
+    int cnt = 0;
+    if (has) {
+        vec4_t<T> nb4 = P.node_bigbox[v];
+        if (box_reaches_group<T>(nb4, C.H, C.box)) cnt = ((z + w - 1) >> 5) - (z >> 5) + 1;
+    }
+    int tot;
+    int off = warp_exclusive_scan(cnt, &tot);
+    if (tot == 0) return;
+    S.rs_off[lane] = off;
+    S.rs_first[lane] = z;
+    S.rs_end[lane] = z + w;
+    if (lane == 31) S.rs_off[32] = tot;
+    __syncwarp();
+    for (int base = 0; base < tot; base += 32) {
+        int i = base + lane;
+        int cid = -1, own = 0;
+        bool pass = false;
+        if (i < tot) {
+            int lo = 0, hi = 32;
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (S.rs_off[mid] <= i) lo = mid;
+                else hi = mid;
+            }
+            own = lo;
+            cid = (S.rs_first[lo] >> 5) + (i - S.rs_off[lo]);
+            pass = box_reaches_group<T>(P.big_chunk[cid], C.H, C.box);
+        }
+        unsigned ball = __ballot_sync(full, pass);
+        while (ball) {
+            int src = __ffs(ball) - 1;
+            ball &= ball - 1;
+            int c = __shfl_sync(full, cid, src);
+            int o = __shfl_sync(full, own, src);
+            if (nbuf + 32 > kBigCap) {
+                C.flush_big(nbuf);
+                nbuf = 0;
+            }
+            int e = 32 * c + lane;
+            bool keep = false;
+            vec4_t<T> q0;
+            if (e >= S.rs_first[o] && e < S.rs_end[o]) {
+                q0 = P.big0[e];
+                q0.x -= C.H.x;
+                q0.y -= C.H.y;
+                T ex = fmax(fabs(q0.x - C.box.x) - C.box.z, T(0));
+                T ey = fmax(fabs(q0.y - C.box.y) - C.box.w, T(0));
+                T near2 = fma(ex, ex, ey * ey);
+                keep = near2 < q0.z;
+                if constexpr (KIND == LENS_GAUSS) {
+                    if (keep && near2 > T(0) && near2 * q0.w >= T(1.000001)) q0.w = T(-1);
+                }
+            }
+            unsigned kb = __ballot_sync(full, keep);
+            if (keep) {
+                int slot = nbuf + __popc(kb & ((1u << lane) - 1u));
+                S.b0[slot] = q0;
+                S.b1[slot] = P.big1[e];
+                S.bpid[slot] = (int)P.big_pid[e];
+            }
+            nbuf += __popc(kb);
+            __syncwarp();
+        }
+    }
+}
+
+template <int KIND, typename T, bool DIRECT>
+__global__ void __launch_bounds__(kWalkWarps * 32)
+back_kernel(BackParams<T> P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned full = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    BackShared<KIND, T>& S = reinterpret_cast<BackShared<KIND, T>*>(smem_raw)[warp];
+    int* stack = P.stack + ((int64_t)blockIdx.x * kWalkWarps + warp) * kStackCap;
+    BackCtx<KIND, T> C(P, S);
+
+    for (;;) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(P.counter, 1u);
+        g = __shfl_sync(full, g, 0);
+        if ((int64_t)g >= P.n_groups) break;
+        C.H = P.gH[g];
+        C.box = P.gbox[g];
+        uint2 rg = P.grange[g];
+        C.nr = (int)rg.y;
+        for (int k = lane; k < (int)rg.y; k += 32) {
+            v2_t<T> l = P.ray_l[rg.x + k];
+            uint32_t i = P.ray_idx[rg.x + k];
+            S.rx[k] = l.x;
+            S.ry[k] = l.y;
+            S.rg1[k] = P.ga1[i];
+            S.rg2[k] = P.ga2[i];
+        }
+        __syncwarp();
+
+        if (P.n_part > 0) {
+            int nn = 0, nb = 0;
+            if (DIRECT) {
+                for (int64_t base = 0; base < P.n_part; base += 0x40000000) {
+                    int64_t rem = P.n_part - base;
+                    int c = (int)(rem < 0x40000000 ? rem : 0x40000000);
+                    back_append_near<KIND, T>(C, lane == 0 ? c : 0, (int)base, nn, P.leaf0, P.leaf1);
+                }
+                C.flush_near(nn);
+            } else {
+                int nf = 0, sp = 1;
+                if (lane == 0) stack[0] = 0;
+                __syncwarp();
+                while (sp > 0) {
+                    int k = sp < 32 ? sp : 32;
+                    sp -= k;
+                    int v = lane < k ? stack[sp + lane] : -1;
+                    __syncwarp();
+                    bool valid = v >= 0, acc = false, leaf = false, open = false;
+                    vec4_t<T> A;
+                    int4 Lk = make_int4(0, 0, 0, 0);
+                    T dxv = T(0), dyv = T(0);
+                    if (valid) {
+                        A = P.nodeA[v];
+                        Lk = P.link[v];
+                        dxv = A.x - C.H.x;
+                        dyv = A.y - C.H.y;
+                        T ex = fmax(fabs(dxv - C.box.x) - C.box.z, T(0));
+                        T ey = fmax(fabs(dyv - C.box.y) - C.box.w, T(0));
+                        acc = fma(ex, ex, ey * ey) > A.w;
+                        leaf = !acc && (Lk.y & kLeafBit);
+                        open = !acc && !leaf;
+                    }
+                    unsigned ball = __ballot_sync(full, acc);
+                    if (acc) {
+                        int pos = nf + __popc(ball & ((1u << lane) - 1u));
+                        v2_t<T> Q = P.nodeB[v];
+                        S.fdx[pos] = dxv;
+                        S.fdy[pos] = dyv;
+                        S.fM[pos] = A.z;
+                        S.fqr[pos] = Q.x;
+                        S.fqi[pos] = Q.y;
+                        S.fnode[pos] = v;
+                    }
+                    nf += __popc(ball);
+                    int nc = open ? Lk.y : 0;
+                    int totc;
+                    int offc = warp_exclusive_scan(nc, &totc);
+                    if (sp + totc > kStackCap) {
+                        if (lane == 0) atomicOr(P.err, DERR_STACK_OVERFLOW);
+                        break;
+                    }
+                    for (int c = 0; c < nc; ++c) stack[sp + offc + c] = Lk.x + c;
+                    sp += totc;
+                    back_append_near<KIND, T>(C, leaf ? (Lk.y & kCountMask) : 0, Lk.x, nn, P.leaf0, P.leaf1);
+                    if constexpr (KIND != LENS_POINT) back_append_big<KIND, T>(C, valid && Lk.w > 0, v, Lk.z, Lk.w, nb);
+                    __syncwarp();
+                    if (nf >= 32) {
+                        C.flush_far(nf);
+                        nf = 0;
+                    }
+                }
+                C.flush_far(nf);
+                C.flush_near(nn);
+                if constexpr (KIND != LENS_POINT) C.flush_big(nb);
+            }
+        }
+
+        // analytic halos: lanes own rays; reduce each halo's gradient over the warp
+        if (P.n_halos > 0 && P.ghalo) {
+            for (int h = 0; h < P.n_halos; ++h) {
+                const HaloDev& hd = P.halos[h];
+                T hx = (T)((double)C.H.x - hd.x), hy = (T)((double)C.H.y - hd.y);
+                T m = (T)hd.m;
+                T gm = T(0), gx = T(0), gy = T(0);
+                for (int k = lane; k < C.nr; k += 32) {
+                    T wx = S.rx[k] + hx, wy = S.ry[k] + hy;
+                    T r2 = fma(wx, wx, wy * wy);
+                    T kb = T(0), kap = T(0), Dp = T(0);
+                    if (hd.kind == LENS_POINT) {
+                        point_terms(m, r2, kb, Dp);
+                    } else if (hd.kind == LENS_GAUSS) {
+                        gauss_terms(m, (T)hd.c0, r2, (T)hd.c1, (T)hd.c2, kb, kap, Dp);
+                    } else if (hd.kind == LENS_NFW) {
+                        nfw_terms(m, (T)hd.c2, (T)hd.c0, (T)hd.c1, r2, kb, kap, Dp);
+                    } else if (hd.kind == LENS_SIS) {
+                        if (r2 > T(0)) {
+                            T rr = sqrt(r2), re = (T)hd.p0;
+                            kb = re / rr;
+                            kap = T(0.5) * kb;
+                            Dp = kap / r2;
+                        }
+                    } else {
+                        T R2 = (T)hd.c2;
+                        if (r2 < R2) {
+                            kb = m / R2;
+                            kap = kb;
+                        } else {
+                            point_terms(m, r2, kb, Dp);
+                        }
+                    }
+                    term_grad(wx, wy, kb, kap, Dp, S.rg1[k], S.rg2[k], gm, gx, gy);
+                }
+                for (int o = 16; o; o >>= 1) {
+                    gm += __shfl_xor_sync(full, gm, o);
+                    gx += __shfl_xor_sync(full, gx, o);
+                    gy += __shfl_xor_sync(full, gy, o);
+                }
+                if (lane == 0) {
+                    // the strength parameter: m, or r_E for the SIS
+                    double strength = hd.kind == LENS_SIS ? hd.p0 : hd.m;
+                    if (strength != 0.0) atomicAdd(P.ghalo + 3 * h, (double)gm / strength);
+                    atomicAdd(P.ghalo + 3 * h + 1, (double)gx);
+                    atomicAdd(P.ghalo + 3 * h + 2, (double)gy);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------- polynomial push-down
+
+// P_v(z) = a + b (z - z_v) + c (z - z_v)^2 (a real, b and c complex) for node v:
+// its own cell adjoint plus its parent's polynomial re-centred at v's centre
+// of mass.  One launch per level, root first.
+template <typename T>
+__global__ void k_push(uint32_t b0, uint32_t b1, const int* parent, const vec4_t<T>* nodeA, const float* adj,
+                       dbl4* polyA, double2* polyC)
+{
+    uint32_t v = b0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= b1) return;
+    vec4_t<T> A = nodeA[v];
+    const float* a = adj + 5 * (int64_t)v;
+    double M = (double)A.z;
+    double pa = a[0], pbr = 0, pbi = 0, pcr = a[1], pci = a[2];
+    if (M != 0.0) {
+        pbr = a[3] / M;
+        pbi = a[4] / M;
+    }
+    int p = parent[v];
+    if (p >= 0) {
+        dbl4 PA = polyA[p];        // {a, b_re, b_im, unused}
+        double2 PC = polyC[p];     // c
+        vec4_t<T> Ap = nodeA[p];
+        double dx = (double)A.x - (double)Ap.x, dy = (double)A.y - (double)Ap.y;  // delta = z_v - z_p
+        // a + b delta + c delta^2 (real part), b + 2 c delta, c
+        double d2x = dx * dx - dy * dy, d2y = 2.0 * dx * dy;
+        pa += PA.x + (PA.y * dx - PA.z * dy) + (PC.x * d2x - PC.y * d2y);
+        pbr += PA.y + 2.0 * (PC.x * dx - PC.y * dy);
+        pbi += PA.z + 2.0 * (PC.x * dy + PC.y * dx);
+        pcr += PC.x;
+        pci += PC.y;
+    }
+    polyA[v] = make_dbl4(pa, pbr, pbi, 0.0);
+    polyC[v] = make_double2(pcr, pci);
+}
+
+// Every particle of every leaf: dL/dm += Re P(d), dL/dz += m P'(d), then
+// scatter (with the direct terms) to the caller's input order.
+template <typename T>
+__global__ void k_leafgrad(uint32_t n_nodes, const int4* link, const vec4_t<T>* nodeA, const vec4_t<T>* exact0,
+                           const dbl4* polyA, const double2* polyC, const float* gpart, const uint32_t* perm,
+                           T* out)
+{
+    uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_nodes) return;
+    int4 L = link[v];
+    if (!(L.y & kLeafBit)) return;
+    vec4_t<T> A = nodeA[v];
+    dbl4 PA = polyA[v];
+    double2 PC = polyC[v];
+    int cnt = L.y & kCountMask;
+    for (int k = 0; k < cnt; ++k) {
+        int j = L.x + k;
+        vec4_t<T> q = exact0[j];
+        double dx = (double)q.x - (double)A.x, dy = (double)q.y - (double)A.y;
+        double d2x = dx * dx - dy * dy, d2y = 2.0 * dx * dy;
+        double gm = PA.x + (PA.y * dx - PA.z * dy) + (PC.x * d2x - PC.y * d2y);
+        double kr = PA.y + 2.0 * (PC.x * dx - PC.y * dy), ki = PA.z + 2.0 * (PC.x * dy + PC.y * dx);
+        double m = (double)q.z;
+        // dL = Re(m P'(d) dz): dL/dx = m Re P', dL/dy = -m Im P'
+        gm += gpart[3 * (int64_t)j];
+        double gx = m * kr + gpart[3 * (int64_t)j + 1];
+        double gy = -m * ki + gpart[3 * (int64_t)j + 2];
+        uint32_t i = perm[j];
+        out[3 * (int64_t)i] += (T)gm;
+        out[3 * (int64_t)i + 1] += (T)gx;
+        out[3 * (int64_t)i + 2] += (T)gy;
+    }
+}
+
+// ------------------------------------------------------------- host
+
+template <int KIND, typename T, bool DIRECT>
+static void back_launch(const BackParams<T>& P, int num_sms, cudaStream_t s)
+{
+    size_t smem = kWalkWarps * sizeof(BackShared<KIND, T>);
+    static int bps = -1;
+    if (bps < 0) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(back_kernel<KIND, T, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, back_kernel<KIND, T, DIRECT>, kWalkWarps * 32, smem);
+        if (bps < 1) bps = 1;
+        if (bps > 16) bps = 16;  // stack slots are allocated for 16 blocks per SM
+    }
+    { back_kernel<KIND, T, DIRECT><<<num_sms * bps, kWalkWarps * 32, smem, s>>>(P); note_launch(); }
+}
+
+template <typename T, bool DIRECT>
+static void back_dispatch(int kind, const BackParams<T>& P, int num_sms, cudaStream_t s)
+{
+    if (kind == LENS_POINT) back_launch<LENS_POINT, T, DIRECT>(P, num_sms, s);
+    else if (kind == LENS_GAUSS) back_launch<LENS_GAUSS, T, DIRECT>(P, num_sms, s);
+    else back_launch<LENS_NFW, T, DIRECT>(P, num_sms, s);
+}
+
+template <typename T>
+static lens_status backward_typed(lens_tree* t, double ox, double oy, const void* dx, const void* dy, int dtype,
+                                  int64_t n, const void* const g[5], void* const* g_species, void* g_halos,
+                                  int flags, cudaStream_t s)
+{
+    using T4 = vec4_t<T>;
+    using T2 = v2_t<T>;
+    int64_t off[2] = {0, n};
+    double orig[2] = {ox, oy};
+    ShootPlan plan;
+    LENS_TRY(upload_batches(t, 1, off, orig, s, &plan));
+    if (32 * plan.R > kMaxGroup) return lens_set_error(LENS_ERR_INTERNAL, "group larger than the adjoint buffer");
+    LENS_TRY(enqueue_groups<T>(t, plan, dx, dy, dtype, s));
+    Layout Lay = make_layout(t->ray_cap, t->batch_cap, max_slots(t));
+    char* base = (char*)t->ray_scratch.ptr;
+    BackParams<T> P{};
+    P.gH = (const T2*)(base + Lay.gH);
+    P.gbox = (const T4*)(base + Lay.gbox);
+    P.grange = (const uint2*)(base + Lay.grange);
+    P.ray_l = (const T2*)(base + Lay.rl);
+    P.ray_idx = (const uint32_t*)(base + Lay.ridx);
+    P.n_groups = (int64_t)plan.ng;
+    P.stack = (int*)(base + Lay.stack);
+    P.err = t->d_err;
+    P.ga1 = (const T*)g[0];
+    P.ga2 = (const T*)g[1];
+    uint32_t* counter = (uint32_t*)(base + Lay.counter);
+    const bool direct = (flags & LENS_DIRECT) != 0;
+    bool first = true;
+    int launches = 0;
+    for (size_t si = 0; si < t->sp.size(); ++si) {
+        const SpeciesTree& st = t->sp[si];
+        bool want = st.n > 0 && g_species && g_species[si];
+        bool halos_here = first && t->n_halos > 0 && g_halos;
+        if (!want && !halos_here) continue;
+        float* adj = nullptr;
+        float* gpart = nullptr;
+        dbl4* polyA = nullptr;
+        double2* polyC = nullptr;
+        if (st.n > 0) {
+            LENS_CUDA(cudaMallocAsync((void**)&adj, st.n_nodes * 5 * sizeof(float), s));
+            LENS_CUDA(cudaMallocAsync((void**)&gpart, st.n * 3 * sizeof(float), s));
+            LENS_CUDA(cudaMallocAsync((void**)&polyA, st.n_nodes * sizeof(dbl4), s));
+            LENS_CUDA(cudaMallocAsync((void**)&polyC, st.n_nodes * sizeof(double2), s));
+            LENS_CUDA(cudaMemsetAsync(adj, 0, st.n_nodes * 5 * sizeof(float), s));
+            LENS_CUDA(cudaMemsetAsync(gpart, 0, st.n * 3 * sizeof(float), s));
+        }
+        P.nodeA = (const T4*)st.nodeA;
+        P.nodeB = (const T2*)st.nodeB;
+        P.link = st.link;
+        P.leaf0 = (const T4*)((direct || st.kind == LENS_POINT) ? st.exact0 : st.leaf0);
+        P.leaf1 = (const T4*)st.exact1;
+        P.big0 = (const T4*)st.big0;
+        P.big1 = (const T4*)st.big1;
+        P.big_chunk = (const T4*)st.big_chunk;
+        P.node_bigbox = (const T4*)st.node_bigbox;
+        P.big_pid = st.big_pid;
+        P.n_part = want ? st.n : 0;
+        P.Uq = (T)st.Uq;
+        P.invNq = (T)st.invNq;
+        P.Uq2 = (T)(st.Uq * 1.4426950408889634074);
+        P.Nq = (T)(st.invNq > 0 ? 1.0 / st.invNq : 0.0);
+        P.eU = (T)std::exp(-st.Uq);
+        P.halos = t->halos;
+        P.n_halos = halos_here ? (int)t->n_halos : 0;
+        P.ghalo = (double*)g_halos;
+        P.adj = adj;
+        P.gpart = gpart;
+        P.counter = counter + 2 * launches;
+        LENS_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(uint32_t), s));
+        int kind = st.n > 0 ? st.kind : LENS_POINT;
+        if (direct) back_dispatch<T, true>(kind, P, t->num_sms, s);
+        else back_dispatch<T, false>(kind, P, t->num_sms, s);
+        if (want) {
+            const int TB = 256;
+            if (!direct) {
+                for (int l = 0; l <= st.depth; ++l) {
+                    uint32_t b0 = (uint32_t)st.level_start[l], b1 = (uint32_t)st.level_start[l + 1];
+                    if (b1 > b0)
+                        { k_push<T><<<grid_for(b1 - b0, TB), TB, 0, s>>>(b0, b1, st.parent, (const T4*)st.nodeA, adj,
+                                                                      polyA, polyC); note_launch(); }
+                }
+            } else {
+                LENS_CUDA(cudaMemsetAsync(polyA, 0, st.n_nodes * sizeof(dbl4), s));
+                LENS_CUDA(cudaMemsetAsync(polyC, 0, st.n_nodes * sizeof(double2), s));
+            }
+            { k_leafgrad<T><<<grid_for(st.n_nodes, TB), TB, 0, s>>>((uint32_t)st.n_nodes, st.link, (const T4*)st.nodeA,
+                                                                    (const T4*)st.exact0, polyA, polyC, gpart, st.perm,
+                                                                    (T*)g_species[si]); note_launch(); }
+        }
+        if (adj) {
+            cudaFreeAsync(adj, s);
+            cudaFreeAsync(gpart, s);
+            cudaFreeAsync(polyA, s);
+            cudaFreeAsync(polyC, s);
+        }
+        first = false;
+        ++launches;
+    }
+    if (first && t->n_halos > 0 && g_halos) {
+        // no species: halos only
+        P.n_part = 0;
+        P.halos = t->halos;
+        P.n_halos = (int)t->n_halos;
+        P.ghalo = (double*)g_halos;
+        P.counter = counter;
+        LENS_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(uint32_t), s));
+        back_dispatch<T, true>(LENS_POINT, P, t->num_sms, s);
+    }
+    LENS_CUDA(cudaGetLastError());
+    return LENS_OK;
+}
 
 lens_status shoot_backward(lens_tree* t, double ox, double oy, const void* dx, const void* dy, int dtype,
                            int64_t n, const void* const g[5], void* const* g_species, void* g_halos,
                            int flags, cudaStream_t s)
 {
-    (void)t; (void)ox; (void)oy; (void)dx; (void)dy; (void)dtype; (void)n; (void)g; (void)g_species;
-    (void)g_halos; (void)flags; (void)s;
-    return lens_set_error(LENS_ERR_UNSUPPORTED, "backward walk not built yet");
+    if (t->precision == LENS_PREC_FP64)
+        return backward_typed<double>(t, ox, oy, dx, dy, dtype, n, g, g_species, g_halos, flags, s);
+    return backward_typed<float>(t, ox, oy, dx, dy, dtype, n, g, g_species, g_halos, flags, s);
 }
 
 }  // namespace lens

@@ -3,17 +3,10 @@
 // call is captured once per (sizes, pointers, flags) key and replayed.
 #include <vector>
 
-#include "tree.cuh"
+#include "walk_shared.cuh"
 
 namespace lens {
 
-struct ShootPlan {
-    int64_t n = 0, nb = 0;
-    uint64_t ng = 0;
-    int R = 1;
-};
-lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig,
-                           cudaStream_t s, ShootPlan* plan);
 lens_status enqueue_shoot(lens_tree* t, const ShootPlan& plan, const void* dx, const void* dy, int dtype,
                           void* const out[5], int flags, cudaStream_t s);
 

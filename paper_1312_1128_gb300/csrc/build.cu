@@ -261,7 +261,7 @@ __global__ void k_level_bounds(const uint32_t* lvl_sorted, uint32_t n_nodes, uin
 __global__ void k_links(uint32_t n_nodes, const uint32_t* bfs2pre, const uint32_t* pre2bfs,
                         const uint32_t* lvl, const uint32_t* first, const uint32_t* count,
                         const uint8_t* isleaf, const uint8_t* nchild, int4* link, uint8_t* node_level,
-                        uint32_t* n_leaves)
+                        uint32_t* n_leaves, int* parent)
 {
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_nodes) return;
@@ -274,7 +274,9 @@ __global__ void k_links(uint32_t n_nodes, const uint32_t* bfs2pre, const uint32_
     } else {
         L.x = (int)pre2bfs[v + 1];
         L.y = (int)nchild[v];
+        for (int c = 0; c < L.y; ++c) parent[L.x + c] = (int)b;
     }
+    if (b == 0) parent[0] = -1;
     L.z = 0;
     L.w = 0;
     link[b] = L;
@@ -681,6 +683,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     LENS_CUDA(cudaMallocAsync((void**)&st.link, n_nodes * sizeof(int4), s));
     LENS_CUDA(cudaMallocAsync((void**)&st.node_rcm, n_nodes * sizeof(float), s));
     LENS_CUDA(cudaMallocAsync((void**)&st.node_level, n_nodes, s));
+    LENS_CUDA(cudaMallocAsync((void**)&st.parent, n_nodes * sizeof(int), s));
     LENS_CUDA(cudaMallocAsync((void**)&st.perm, n * sizeof(uint32_t), s));
     LENS_CUDA(cudaMallocAsync(&st.exact0, n * sizeof(T4), s));
     if (in.kind == LENS_NFW) LENS_CUDA(cudaMallocAsync(&st.exact1, n * sizeof(T4), s));
@@ -692,7 +695,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     LENS_CUDA(cudaMemcpyAsync(st.perm, P, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
 
     { k_links<<<GN, TB, 0, s>>>(n_nodes, bfs2pre, pre2bfs, lvl, first, count, isleaf, nchild, st.link,
-                              st.node_level, counters); note_launch(); }
+                              st.node_level, counters, st.parent); note_launch(); }
     LENS_CUDA(cudaStreamSynchronize(s));  // level table on the host
     lap(1);
     int depth = (int)ls[kMaxDepth + 1];
@@ -821,7 +824,7 @@ void free_species(SpeciesTree& st)
 {
     void* ptrs[] = {st.nodeA, st.nodeB, st.link, st.node_rcm, st.node_level, st.exact0, st.exact1,
                     st.leaf0, st.big0, st.big1, st.perm, st.big_pid, st.listed, st.big_chunk,
-                    st.node_bigbox};
+                    st.node_bigbox, st.parent};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, 0);
     st = SpeciesTree();

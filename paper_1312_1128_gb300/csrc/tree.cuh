@@ -31,6 +31,7 @@ struct SpeciesTree {
     void* nodeB = nullptr;     // T2 {Re Q2, Im Q2}
     int4* link = nullptr;      // {first child | first particle, count | leaf bit, big start, big count}
     float* node_rcm = nullptr; // r_cm (distance from the centre of mass to the farthest corner)
+    int* parent = nullptr;     // parent node (-1 at the root), for the adjoint push-down
     uint8_t* node_level = nullptr;
     // particles (Morton order)
     void* exact0 = nullptr;    // T4 full-profile records (see walk)

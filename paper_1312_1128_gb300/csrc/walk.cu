@@ -27,32 +27,11 @@
 
 #include "profiles.cuh"
 #include "sort.cuh"
-#include "walk.cuh"
+#include "walk_shared.cuh"
 
 namespace lens {
 
-template <typename T> struct V2;
-template <> struct V2<float> { using type = float2; };
-template <> struct V2<double> { using type = double2; };
-template <typename T> using v2_t = typename V2<T>::type;
-
 // ------------------------------------------------------------ grouping
-
-__device__ __forceinline__ int batch_of(const int64_t* boff, int nb, int64_t i)
-{
-    int lo = 0, hi = nb;  // boff[lo] <= i < boff[hi]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (boff[mid] <= i) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ double ray_offset(const void* p, int dtype, int64_t i)
-{
-    return dtype == LENS_F32 ? (double)((const float*)p)[i] : ((const double*)p)[i];
-}
 
 __global__ void k_ray_bbox(const int64_t* boff, int nb, const double* borig, const void* dx,
                            const void* dy, int dtype, int64_t n, unsigned long long* bbox)
@@ -500,18 +479,6 @@ LENS_DEV void append_ranges(WalkCtx<KIND, T, R, AO>& C, int cnt, int first, int&
     }
 }
 
-// Does the box {x0, y0, x1, y1} (frame coordinates) reach the group's ray
-// box?  The subtraction of H is rounded; a relative margin keeps the test
-// conservative.
-template <typename T>
-LENS_DEV bool box_reaches_group(const vec4_t<T>& b, const v2_t<T>& H, const vec4_t<T>& g)
-{
-    const T eps = sizeof(T) == 4 ? T(4.8e-7) : T(8.9e-16);
-    T x0 = b.x - H.x, x1 = b.z - H.x, y0 = b.y - H.y, y1 = b.w - H.y;
-    T tx = eps * (fabs(b.x) + fabs(b.z) + T(2) * fabs(H.x)), ty = eps * (fabs(b.y) + fabs(b.w) + T(2) * fabs(H.y));
-    return x0 - tx <= g.x + g.z && x1 + tx >= g.x - g.z && y0 - ty <= g.y + g.w && y1 + ty >= g.y - g.w;
-}
-
 // Big lists of the visited boxes (one list per lane: entries [z, z + w) of
 // the big arrays).  A list whose support box misses the group is skipped;
 // otherwise its 32-entry chunks are tested by their support boxes and the
@@ -739,37 +706,6 @@ walk_kernel(WalkParams<T> P)
 
 // ------------------------------------------------------------- host side
 
-struct Layout {
-    size_t boff, borig, gfirst, bbox, k0, k1, v0, v1, tmp, rl, ridx, gH, gbox, grange, counter,
-        stack, total;
-};
-
-static Layout make_layout(int64_t n, int64_t nb, int64_t slots)
-{
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    Layout L{};
-    int64_t ng = n / 32 + nb + 1;
-    size_t o = 0;
-    L.boff = o; o += al((nb + 1) * sizeof(int64_t));
-    L.borig = o; o += al(nb * 2 * sizeof(double));
-    L.gfirst = o; o += al((nb + 1) * sizeof(uint32_t));
-    L.bbox = o; o += al(nb * 4 * sizeof(unsigned long long));
-    L.k0 = o; o += al(n * sizeof(uint64_t));
-    L.k1 = o; o += al(n * sizeof(uint64_t));
-    L.v0 = o; o += al(n * sizeof(uint32_t));
-    L.v1 = o; o += al(n * sizeof(uint32_t));
-    L.tmp = o; o += al(radix_sort_temp_bytes<uint64_t>(n));
-    L.rl = o; o += al(n * 2 * sizeof(double));
-    L.ridx = o; o += al(n * sizeof(uint32_t));
-    L.gH = o; o += al(ng * 2 * sizeof(double));
-    L.gbox = o; o += al(ng * 4 * sizeof(double));
-    L.grange = o; o += al(ng * sizeof(uint2));
-    L.counter = o; o += al(64 * sizeof(uint32_t));
-    L.stack = o; o += al((size_t)slots * kStackCap * sizeof(int));
-    L.total = o;
-    return L;
-}
-
 template <int KIND, typename T, int R, bool AO, bool DIRECT>
 static int walk_blocks_per_sm()
 {
@@ -792,8 +728,6 @@ static int walk_blocks_per_sm()
 }
 
 void free_graphs(lens_tree* t);
-
-static int max_slots(lens_tree* t) { return t->num_sms * 16 * kWalkWarps; }
 
 lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s)
 {
@@ -846,13 +780,6 @@ static void launch_dispatch(int kind, bool ao, bool direct, const WalkParams<T>&
     }
 }
 
-// Host-side plan of one shoot call: sizes fixed by the batch table.
-struct ShootPlan {
-    int64_t n = 0, nb = 0;
-    uint64_t ng = 0;
-    int R = 1;
-};
-
 static int rays_per_lane(const lens_tree* t)
 {
     return (t->precision == LENS_PREC_FP64 || t->group_rays <= 32) ? 1 : 2;
@@ -887,6 +814,55 @@ lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const
     return LENS_OK;
 }
 
+template <typename T>
+lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, const void* dy, int dtype,
+                           cudaStream_t s)
+{
+    using T4 = vec4_t<T>;
+    using T2 = v2_t<T>;
+    const int64_t n = plan.n, nb = plan.nb;
+    const uint64_t ng = plan.ng;
+    const int R = plan.R;
+    Layout L = make_layout(t->ray_cap, t->batch_cap, max_slots(t));
+    char* base = (char*)t->ray_scratch.ptr;
+    int64_t* d_boff = (int64_t*)(base + L.boff);
+    double* d_borig = (double*)(base + L.borig);
+    uint32_t* d_gfirst = (uint32_t*)(base + L.gfirst);
+    unsigned long long* d_bbox = (unsigned long long*)(base + L.bbox);
+    T2* ray_l = (T2*)(base + L.rl);
+    uint32_t* ray_idx = (uint32_t*)(base + L.ridx);
+    T2* gH = (T2*)(base + L.gH);
+    T4* gbox = (T4*)(base + L.gbox);
+    uint2* grange = (uint2*)(base + L.grange);
+    {
+        const int TB = 256;
+        { k_bbox_init<<<grid_for(nb, 128), 128, 0, s>>>(d_bbox, nb); note_launch(); }
+        { k_ray_bbox<<<grid_for(n, TB), TB, 0, s>>>(d_boff, (int)nb, d_borig, dx, dy, dtype, n, d_bbox); note_launch(); }
+        uint64_t* k0 = (uint64_t*)(base + L.k0);
+        uint64_t* k1 = (uint64_t*)(base + L.k1);
+        uint32_t* v0 = (uint32_t*)(base + L.v0);
+        uint32_t* v1 = (uint32_t*)(base + L.v1);
+        { k_ray_keys<<<grid_for(n, TB), TB, 0, s>>>(d_boff, (int)nb, d_borig, dx, dy, dtype, n, d_bbox, k0, v0); note_launch(); }
+        int bbits = 0;
+        while ((1ll << bbits) < nb) ++bbits;
+        int end_bit = (32 + bbits + 7) & ~7;
+        uint64_t* sk;
+        uint32_t* sv;
+        radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, end_bit, base + L.tmp, s, &sk, &sv);
+        unsigned gg = grid_for((int64_t)ng * 32, TB);
+        if (R == 1)
+            { k_groups<T, 1><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
+                                             sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
+        else
+            { k_groups<T, 2><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
+                                             sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
+    }
+
+    return LENS_OK;
+}
+template lens_status enqueue_groups<float>(lens_tree*, const ShootPlan&, const void*, const void*, int, cudaStream_t);
+template lens_status enqueue_groups<double>(lens_tree*, const ShootPlan&, const void*, const void*, int, cudaStream_t);
+
 // Enqueue the kernels of one shoot call (no allocation, no host sync: safe
 // to capture into a CUDA graph).
 template <typename T>
@@ -917,29 +893,7 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
             if (!t->ev[i]) LENS_CUDA(cudaEventCreate(&t->ev[i]));
         LENS_CUDA(cudaEventRecord(t->ev[0], s));
     }
-    if (n > 0) {
-        const int TB = 256;
-        { k_bbox_init<<<grid_for(nb, 128), 128, 0, s>>>(d_bbox, nb); note_launch(); }
-        { k_ray_bbox<<<grid_for(n, TB), TB, 0, s>>>(d_boff, (int)nb, d_borig, dx, dy, dtype, n, d_bbox); note_launch(); }
-        uint64_t* k0 = (uint64_t*)(base + L.k0);
-        uint64_t* k1 = (uint64_t*)(base + L.k1);
-        uint32_t* v0 = (uint32_t*)(base + L.v0);
-        uint32_t* v1 = (uint32_t*)(base + L.v1);
-        { k_ray_keys<<<grid_for(n, TB), TB, 0, s>>>(d_boff, (int)nb, d_borig, dx, dy, dtype, n, d_bbox, k0, v0); note_launch(); }
-        int bbits = 0;
-        while ((1ll << bbits) < nb) ++bbits;
-        int end_bit = (32 + bbits + 7) & ~7;
-        uint64_t* sk;
-        uint32_t* sv;
-        radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, end_bit, base + L.tmp, s, &sk, &sv);
-        unsigned gg = grid_for((int64_t)ng * 32, TB);
-        if (R == 1)
-            { k_groups<T, 1><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
-                                             sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
-        else
-            { k_groups<T, 2><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
-                                             sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
-    }
+    if (n > 0) LENS_TRY(enqueue_groups<T>(t, plan, dx, dy, dtype, s));
 
     if (timing) LENS_CUDA(cudaEventRecord(t->ev[1], s));
     WalkParams<T> P{};

@@ -1,0 +1,94 @@
+// walk_shared.cuh -- definitions shared by the forward walk (walk.cu), the
+// adjoint walk (backward.cu) and graph replay (batch.cu).
+#pragma once
+
+#include "sort.cuh"
+#include "tree.cuh"
+
+namespace lens {
+
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+template <typename T> using v2_t = typename V2<T>::type;
+
+__device__ __forceinline__ int batch_of(const int64_t* boff, int nb, int64_t i)
+{
+    int lo = 0, hi = nb;  // boff[lo] <= i < boff[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (boff[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double ray_offset(const void* p, int dtype, int64_t i)
+{
+    return dtype == LENS_F32 ? (double)((const float*)p)[i] : ((const double*)p)[i];
+}
+
+// Does the box {x0, y0, x1, y1} (frame coordinates) reach the group's ray
+// box?  The subtraction of H is rounded; a relative margin keeps the test
+// conservative.
+template <typename T>
+LENS_DEV bool box_reaches_group(const vec4_t<T>& b, const v2_t<T>& H, const vec4_t<T>& g)
+{
+    const T eps = sizeof(T) == 4 ? T(4.8e-7) : T(8.9e-16);
+    T x0 = b.x - H.x, x1 = b.z - H.x, y0 = b.y - H.y, y1 = b.w - H.y;
+    T tx = eps * (fabs(b.x) + fabs(b.z) + T(2) * fabs(H.x)), ty = eps * (fabs(b.y) + fabs(b.w) + T(2) * fabs(H.y));
+    return x0 - tx <= g.x + g.z && x1 + tx >= g.x - g.z && y0 - ty <= g.y + g.w && y1 + ty >= g.y - g.w;
+}
+
+// ------------------------------------------------------- shoot scratch
+
+struct Layout {
+    size_t boff, borig, gfirst, bbox, k0, k1, v0, v1, tmp, rl, ridx, gH, gbox, grange, counter,
+        stack, total;
+};
+
+inline Layout make_layout(int64_t n, int64_t nb, int64_t slots)
+{
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    Layout L{};
+    int64_t ng = n / 32 + nb + 1;
+    size_t o = 0;
+    L.boff = o; o += al((nb + 1) * sizeof(int64_t));
+    L.borig = o; o += al(nb * 2 * sizeof(double));
+    L.gfirst = o; o += al((nb + 1) * sizeof(uint32_t));
+    L.bbox = o; o += al(nb * 4 * sizeof(unsigned long long));
+    L.k0 = o; o += al(n * sizeof(uint64_t));
+    L.k1 = o; o += al(n * sizeof(uint64_t));
+    L.v0 = o; o += al(n * sizeof(uint32_t));
+    L.v1 = o; o += al(n * sizeof(uint32_t));
+    L.tmp = o; o += al(radix_sort_temp_bytes<uint64_t>(n));
+    L.rl = o; o += al(n * 2 * sizeof(double));
+    L.ridx = o; o += al(n * sizeof(uint32_t));
+    L.gH = o; o += al(ng * 2 * sizeof(double));
+    L.gbox = o; o += al(ng * 4 * sizeof(double));
+    L.grange = o; o += al(ng * sizeof(uint2));
+    L.counter = o; o += al(64 * sizeof(uint32_t));
+    L.stack = o; o += al((size_t)slots * kStackCap * sizeof(int));
+    L.total = o;
+    return L;
+}
+
+inline int max_slots(lens_tree* t) { return t->num_sms * 16 * kWalkWarps; }
+
+
+// Host-side plan of one shoot call: sizes fixed by the batch table.
+struct ShootPlan {
+    int64_t n = 0, nb = 0;
+    uint64_t ng = 0;
+    int R = 1;
+};
+
+lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s);
+lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig,
+                           cudaStream_t s, ShootPlan* plan);
+// Ray grouping of one shoot call (sort + groups) into the tree's scratch.
+template <typename T>
+lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, const void* dy, int dtype,
+                           cudaStream_t s);
+
+}  // namespace lens
