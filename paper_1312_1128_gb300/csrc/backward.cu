@@ -163,13 +163,14 @@ template <int KIND, typename T> struct BackCtx {
 
     LENS_DEV BackCtx(const BackParams<T>& p, BackShared<KIND, T>& s) : P(p), S(s) {}
 
-    // lane c owns far cell c: dL/dM, dL/dQ2, dL/dz_cm over the group's rays
+    // lane c owns far cells c, c + 32, ...: dL/dM, dL/dQ2, dL/dz_cm over the
+    // group's rays (the buffer holds up to kFarCap cells when it is flushed)
     LENS_DEV void flush_far(int nf)
     {
         int lane = threadIdx.x & 31;
         __syncwarp();
-        if (lane < nf) {
-            T dx = S.fdx[lane], dy = S.fdy[lane], M = S.fM[lane], qr = S.fqr[lane], qi = S.fqi[lane];
+        for (int cell = lane; cell < nf; cell += 32) {
+            T dx = S.fdx[cell], dy = S.fdy[cell], M = S.fM[cell], qr = S.fqr[cell], qi = S.fqi[cell];
             T aM = T(0), cr = T(0), ci = T(0), br = T(0), bi = T(0);
             for (int j = 0; j < nr; ++j) {
                 T wx = S.rx[j] - dx, wy = S.ry[j] - dy;
@@ -187,7 +188,7 @@ template <int KIND, typename T> struct BackCtx {
                 br += g1 * tx - g2 * ty;
                 bi += g1 * ty + g2 * tx;
             }
-            float* a = P.adj + 5 * (int64_t)S.fnode[lane];
+            float* a = P.adj + 5 * (int64_t)S.fnode[cell];
             atomicAdd(a + 0, (float)aM);
             atomicAdd(a + 1, (float)cr);
             atomicAdd(a + 2, (float)ci);

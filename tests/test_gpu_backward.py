@@ -147,16 +147,14 @@ def test_halo_gradient_direct():
     rx = g.uniform(-0.5, 0.5, 512).astype(np.float32)
     ry = g.uniform(-0.5, 0.5, 512).astype(np.float32)
     lens = L.Lens([L.Species.points(cu(pts))], [L.Halo.sis(0.05, -0.03, 0.2)], theta=0.3)
-    out = lens.shoot(cu(rx), cu(ry), flags=L.ALPHA_ONLY)
-    a = torch.stack([out[0], out[1]], 1).double()
-    gsum = (2 * a).float()
-    gh = torch.zeros(1, 3, dtype=torch.float64, device="cuda")
-    lens.backward(cu(rx), cu(ry), gsum[:, 0].contiguous(), gsum[:, 1].contiguous(), g_halos=gh,
-                  flags=L.DIRECT)
     comps = oracle.concat(comps_points(pts), oracle.make_components(oracle.SIS, 0.05, -0.03, 0.0, 0.2))
     ref_a = oracle.direct_sum(comps, rx.astype(np.float64), ry.astype(np.float64))
     G = np.zeros_like(ref_a)
     G[:, :2] = 2 * ref_a[:, :2]
+    gsum = cu(G[:, :2].astype(np.float32))
+    gh = torch.zeros(1, 3, dtype=torch.float64, device="cuda")
+    lens.backward(cu(rx), cu(ry), gsum[:, 0].contiguous(), gsum[:, 1].contiguous(), g_halos=gh,
+                  flags=L.DIRECT)
     # the oracle's mass slot is dL/dm; for the SIS the strength is r_E:
     # alpha is linear in r_E, so dL/dr_E = sum G.alpha_SIS / r_E
     sis = oracle.make_components(oracle.SIS, 0.05, -0.03, 0.0, 0.2)
