@@ -55,8 +55,10 @@ template <typename T> struct BackParams {
     const HaloDev* halos;
     int n_halos;
     double* ghalo;  // n_halos x 3, or null
-    float* adj;     // n_nodes x 5: dL/dM, dL/dQ2 (re, im), dL/dz_cm (re, im)
-    float* gpart;   // n x 3 in tree order: dL/dm, dL/dx, dL/dy
+    double* adj;    // n_nodes x 5: dL/dM, dL/dQ2 (re, im), dL/dz_cm (re, im)
+    double* gpart;  // n x 3 in tree order: dL/dm, dL/dx, dL/dy
+    // (FP64 accumulators: these sums run over up to millions of rays with
+    // strong cancellation)
     uint32_t* counter;
     int* stack;
     uint32_t* err;
@@ -188,22 +190,22 @@ template <int KIND, typename T> struct BackCtx {
                 br += g1 * tx - g2 * ty;
                 bi += g1 * ty + g2 * tx;
             }
-            float* a = P.adj + 5 * (int64_t)S.fnode[cell];
-            atomicAdd(a + 0, (float)aM);
-            atomicAdd(a + 1, (float)cr);
-            atomicAdd(a + 2, (float)ci);
-            atomicAdd(a + 3, (float)br);
-            atomicAdd(a + 4, (float)bi);
+            double* a = P.adj + 5 * (int64_t)S.fnode[cell];
+            atomicAdd(a + 0, (double)aM);
+            atomicAdd(a + 1, (double)cr);
+            atomicAdd(a + 2, (double)ci);
+            atomicAdd(a + 3, (double)br);
+            atomicAdd(a + 4, (double)bi);
         }
         __syncwarp();
     }
 
     LENS_DEV void add_particle(int pid, T m, T gm, T gx, T gy)
     {
-        float* g = P.gpart + 3 * (int64_t)pid;
-        if (m != T(0)) atomicAdd(g + 0, (float)(gm / m));
-        atomicAdd(g + 1, (float)gx);
-        atomicAdd(g + 2, (float)gy);
+        double* g = P.gpart + 3 * (int64_t)pid;
+        if (m != T(0)) atomicAdd(g + 0, (double)gm / (double)m);
+        atomicAdd(g + 1, (double)gx);
+        atomicAdd(g + 2, (double)gy);
     }
 
     LENS_DEV void flush_near(int nn)
@@ -519,13 +521,13 @@ back_kernel(BackParams<T> P)
 // its own cell adjoint plus its parent's polynomial re-centred at v's centre
 // of mass.  One launch per level, root first.
 template <typename T>
-__global__ void k_push(uint32_t b0, uint32_t b1, const int* parent, const vec4_t<T>* nodeA, const float* adj,
+__global__ void k_push(uint32_t b0, uint32_t b1, const int* parent, const vec4_t<T>* nodeA, const double* adj,
                        dbl4* polyA, double2* polyC)
 {
     uint32_t v = b0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= b1) return;
     vec4_t<T> A = nodeA[v];
-    const float* a = adj + 5 * (int64_t)v;
+    const double* a = adj + 5 * (int64_t)v;
     double M = (double)A.z;
     double pa = a[0], pbr = 0, pbi = 0, pcr = a[1], pci = a[2];
     if (M != 0.0) {
@@ -554,7 +556,7 @@ __global__ void k_push(uint32_t b0, uint32_t b1, const int* parent, const vec4_t
 // scatter (with the direct terms) to the caller's input order.
 template <typename T>
 __global__ void k_leafgrad(uint32_t n_nodes, const int4* link, const vec4_t<T>* nodeA, const vec4_t<T>* exact0,
-                           const dbl4* polyA, const double2* polyC, const float* gpart, const uint32_t* perm,
+                           const dbl4* polyA, const double2* polyC, const double* gpart, const uint32_t* perm,
                            T* out)
 {
     uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -645,17 +647,17 @@ static lens_status backward_typed(lens_tree* t, double ox, double oy, const void
         bool want = st.n > 0 && g_species && g_species[si];
         bool halos_here = first && t->n_halos > 0 && g_halos;
         if (!want && !halos_here) continue;
-        float* adj = nullptr;
-        float* gpart = nullptr;
+        double* adj = nullptr;
+        double* gpart = nullptr;
         dbl4* polyA = nullptr;
         double2* polyC = nullptr;
         if (st.n > 0) {
-            LENS_CUDA(cudaMallocAsync((void**)&adj, st.n_nodes * 5 * sizeof(float), s));
-            LENS_CUDA(cudaMallocAsync((void**)&gpart, st.n * 3 * sizeof(float), s));
+            LENS_CUDA(cudaMallocAsync((void**)&adj, st.n_nodes * 5 * sizeof(double), s));
+            LENS_CUDA(cudaMallocAsync((void**)&gpart, st.n * 3 * sizeof(double), s));
             LENS_CUDA(cudaMallocAsync((void**)&polyA, st.n_nodes * sizeof(dbl4), s));
             LENS_CUDA(cudaMallocAsync((void**)&polyC, st.n_nodes * sizeof(double2), s));
-            LENS_CUDA(cudaMemsetAsync(adj, 0, st.n_nodes * 5 * sizeof(float), s));
-            LENS_CUDA(cudaMemsetAsync(gpart, 0, st.n * 3 * sizeof(float), s));
+            LENS_CUDA(cudaMemsetAsync(adj, 0, st.n_nodes * 5 * sizeof(double), s));
+            LENS_CUDA(cudaMemsetAsync(gpart, 0, st.n * 3 * sizeof(double), s));
         }
         P.nodeA = (const T4*)st.nodeA;
         P.nodeB = (const T2*)st.nodeB;
