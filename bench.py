@@ -314,6 +314,22 @@ def run_gpu(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_once(args):
+    """One build + shoot of the workload (profiling: `ncu ... python bench.py --once`)."""
+    import torch
+
+    import paper_1312_1128_gb300 as L
+    w = lensgen.workload_nfw_sph(n_grid=args.grid)
+    parts = torch.from_numpy(w["gauss"]).cuda()
+    rx, ry = torch.from_numpy(w["rx"]).cuda(), torch.from_numpy(w["ry"]).cuda()
+    lens = L.Lens([L.Species.gauss(parts, w["q"])], theta=THETA, group_rays=64)
+    lens.shoot(rx, ry, flags=L.TIMING | L.COUNT)
+    lens.sync()
+    print(json.dumps({"grid": args.grid, "timing_ms": lens.last_timing(), "counters": lens.counters(),
+                      "build_ms": lens.info()["build_ms"][0]}))
+    lens.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,7 +338,14 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--grid", type=int, default=2048,
+                    help="ray grid side (profiling runs use a smaller grid; the metric is quoted at 2048)")
+    ap.add_argument("--once", action="store_true",
+                    help="one build + shoot of the workload and exit (for profiler captures)")
     args = ap.parse_args()
+    if args.once:
+        run_once(args)
+        return
     if args.warmup < 3 and args.impl == "gpu":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

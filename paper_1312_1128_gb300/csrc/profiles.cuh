@@ -244,6 +244,26 @@ LENS_DEV void gauss_correction_fast(Acc5<float>& acc, float wx, float wy, const 
     float kap = t < Uq2 ? q1.z * e : 0.0f;
     acc.template radial<AO>(wx, wy, dkb, kap, (dkb - kap) * inv);
 }
+// The same when, in addition, the support contains every ray of the group:
+// no select for the support edge, and kappa accumulates with one FMA.
+template <bool AO>
+LENS_DEV void gauss_correction_inside(Acc5<float>& acc, float wx, float wy, const float4& q1, float eU)
+{
+    float wy2 = wy * wy;
+    float r2 = fmaf(wx, wx, wy2);
+    float inv = rcp(r2);
+    float e = exp2neg(r2 * q1.y);
+    float dkb = (q1.x * inv) * (eU - e);
+    acc.a1 = fmaf(dkb, wx, acc.a1);
+    acc.a2 = fmaf(dkb, wy, acc.a2);
+    if (!AO) {
+        acc.k = fmaf(q1.z, e, acc.k);
+        float Dp = fmaf(-q1.z, e, dkb) * inv;
+        float c2 = fmaf(wx, wx, -wy2), s2 = (wx + wx) * wy;
+        acc.g1 = fmaf(-Dp, c2, acc.g1);
+        acc.g2 = fmaf(-Dp, s2, acc.g2);
+    }
+}
 template <bool AO>
 LENS_DEV void gauss_correction_fast(Acc5<double>& acc, double wx, double wy, const dbl4& q1, double Uq2,
                                     double eU)
@@ -256,6 +276,12 @@ LENS_DEV void gauss_correction_fast(Acc5<double>& acc, double wx, double wy, con
     double dkb = (q1.x * inv) * (eU - e);
     double kap = t < Uq2 ? q1.z * e : 0.0;
     acc.template radial<AO>(wx, wy, dkb, kap, (dkb - kap) * inv);
+}
+
+template <bool AO>
+LENS_DEV void gauss_correction_inside(Acc5<double>& acc, double wx, double wy, const dbl4& q1, double eU)
+{
+    gauss_correction_fast<AO>(acc, wx, wy, q1, INFINITY, eU);
 }
 
 // FP64 form of the same correction (q1.y holds c log2 e as well).

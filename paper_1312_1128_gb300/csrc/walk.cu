@@ -328,10 +328,17 @@ template <int KIND, typename T, int R, bool AO> struct WalkCtx {
         int i = 0;
         if constexpr (KIND == LENS_GAUSS) {
             // b0.w < 0 marks an entry whose softening radius no ray of the
-            // group reaches (the common case)
+            // group reaches (the common case); b0.w = -2 also that its
+            // support contains every ray of the group
             for (; i + 1 < nb; i += 2) {
                 vec4_t<T> q = S.b0[i], q1 = S.b1[i], p = S.b0[i + 1], p1 = S.b1[i + 1];
-                if (q.w < T(0) && p.w < T(0)) {
+                if (q.w < T(-1.5) && p.w < T(-1.5)) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        gauss_correction_inside<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1, P.eU);
+                        gauss_correction_inside<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p1, P.eU);
+                    }
+                } else if (q.w < T(0) && p.w < T(0)) {
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         gauss_correction_fast<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1, P.Uq2, P.eU);
@@ -545,8 +552,13 @@ LENS_DEV void append_big(WalkCtx<KIND, T, R, AO>& C, bool has, int v, int z, int
                 T near2 = fma(ex, ex, ey * ey);
                 keep = near2 < q0.z;
                 if constexpr (KIND == LENS_GAUSS) {
-                    // every ray of the group beyond the softening radius?
-                    if (keep && near2 > T(0) && near2 * q0.w >= T(1.000001)) q0.w = T(-1);
+                    // every ray of the group beyond the softening radius?  and
+                    // all inside the support?
+                    if (keep && near2 > T(0) && near2 * q0.w >= T(1.000001)) {
+                        T fx = fabs(q0.x - C.box.x) + C.box.z, fy = fabs(q0.y - C.box.y) + C.box.w;
+                        T far2 = fma(fx, fx, fy * fy) * T(1.000001);
+                        q0.w = far2 < q0.z ? T(-2) : T(-1);
+                    }
                 }
             }
             unsigned kb = __ballot_sync(full, keep);
