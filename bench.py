@@ -47,14 +47,6 @@ THETA = 0.3
 FLOPS = {"far_cells": 50, "near_point": 22, "near_full": 33, "big_corrections": 38}
 
 
-def useful_flops_per_ray(theta: float) -> float:
-    """Paper-tree (per-ray MAC, leaf < 5) interaction counts of this workload
-    (tests/golden/useful_counts.json, written from the oracle) x FLOPS."""
-    with open(os.path.join(ROOT, "tests", "golden", "useful_counts.json")) as f:
-        c = json.load(f)[WORKLOAD][str(theta)]
-    return sum(FLOPS[k] * c[k] for k in FLOPS)
-
-
 def walk_traffic():
     """DRAM bytes per walk launch from the committed ncu capture, if the walk
     source is unchanged since it was taken."""
@@ -141,50 +133,321 @@ def bench_config(ws: int) -> dict:
             "parallelism": f"independent replicas x{ws}"}
 
 
-def oracle_rays_per_sec(w, budget_s: float, seed: int = 7):
-    """FP64 direct sum over all particles (the oracle as it stands) on a
-    time-bounded random sample of the grid rays."""
-    import oracle
-    p = w["gauss"].astype(np.float64)
-    comps = oracle.make_components(oracle.GAUSS, p[:, 0], p[:, 1], p[:, 2], p[:, 3], w["q"])
-    g = lensgen.rng(seed)
-    order = g.permutation(w["rx"].size)
-    done, t0, chunk = 0, time.perf_counter(), 64
-    while time.perf_counter() - t0 < budget_s and done < order.size:
-        idx = order[done:done + chunk]
-        oracle.direct_sum(comps, w["rx"][idx].astype(np.float64), w["ry"][idx].astype(np.float64))
-        done += idx.size
-    dt = time.perf_counter() - t0
-    return done / dt, done, dt, oracle.max_threads()
-
-
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    w = lensgen.workload_nfw_sph()
-    n_rays = w["rx"].size
+    wl = WORKLOADS[args.workload]()
+    n_rays = wl.n_rays
     per_step = 2.0  # seconds of oracle work per step
     for _ in range(args.warmup):
-        oracle_rays_per_sec(w, 0.5)
-    rates, samples = [], 0
-    cores = None
-    t_all = 0.0
+        wl.oracle_rate(0.5)
+    samples, t_all, cores = 0, 0.0, None
     for k in range(args.steps):
-        r, done, dt, cores = oracle_rays_per_sec(w, per_step, seed=100 + k)
-        rates.append(r)
+        r, done, dt, cores = wl.oracle_rate(per_step, seed=100 + k)
         samples += done
         t_all += dt
     value = samples / t_all
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_rays / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": bench_config(ws),
+            "data": "synthetic", "config": wl.config(ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{samples} random grid rays of the workload, FP64 direct "
-                                       f"sum over all 1e6 particles (the tree's theta -> 0 limit), "
+                             "sample": f"{samples} random rays of the workload, FP64 direct sum over "
+                                       f"every lens component (the tree's theta -> 0 limit), "
                                        f"{per_step:.0f} s per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- workloads
+
+class Workload:
+    """One benchmark workload: inputs, one timed step, its end-to-end form."""
+    name = ""
+    theta = THETA
+    dtype = "f32"
+
+    def flops_per_ray(self):
+        with open(os.path.join(ROOT, "tests", "golden", "useful_counts.json")) as f:
+            c = json.load(f)[self.name][str(self.theta)]
+        return sum(self.FLOPS[k] * c[k] for k in self.FLOPS)
+
+
+class NfwSph(Workload):
+    """Headline: 1e6 smoothed NFW particles, 2048^2 grid, theta 0.3; step =
+    tree build + ray grouping + walk."""
+    name = WORKLOAD
+    FLOPS = FLOPS
+
+    def __init__(self, grid=2048):
+        self.w = lensgen.workload_nfw_sph(n_grid=grid)
+        self.n_rays = self.w["rx"].size
+
+    def config(self, ws):
+        return bench_config(ws)
+
+    def prepare(self, L, torch, dev):
+        w = self.w
+        self.L = L
+        self.parts = torch.from_numpy(w["gauss"]).to(dev)
+        self.rx, self.ry = torch.from_numpy(w["rx"]).to(dev), torch.from_numpy(w["ry"]).to(dev)
+        self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
+        self.group = 32
+
+    def tune(self):
+        lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta)
+        self.group = lens.autotune(self.rx, self.ry)
+        lens.close()
+
+    def step(self, flags):
+        lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta,
+                           group_rays=self.group)
+        lens.shoot(self.rx, self.ry, flags=flags, out=self.outs)
+        return lens
+
+    def e2e(self, torch, dev):
+        """Host buffers: H2D of particles and rays, D2H of the five outputs."""
+        w, L = self.w, self.L
+        if not hasattr(self, "h"):
+            self.h = [torch.from_numpy(w["gauss"]).pin_memory(), torch.from_numpy(w["rx"]).pin_memory(),
+                      torch.from_numpy(w["ry"]).pin_memory()]
+            self.d = [torch.empty_like(x, device=dev) for x in self.h]
+            self.hout = [torch.empty(self.n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
+        for d, h in zip(self.d, self.h):
+            d.copy_(h, non_blocking=True)
+        lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group)
+        lens.shoot(self.d[1], self.d[2], out=self.outs)
+        for h, o in zip(self.hout, self.outs):
+            h.copy_(o, non_blocking=True)
+        return lens, sum(x.numel() * 4 for x in self.h), 5 * self.n_rays * 4
+
+    def oracle_rate(self, budget, seed=7):
+        import oracle
+        w = self.w
+        p = w["gauss"].astype(np.float64)
+        comps = oracle.make_components(oracle.GAUSS, p[:, 0], p[:, 1], p[:, 2], p[:, 3], w["q"])
+        return _oracle_loop(oracle, comps, w["rx"], w["ry"], None, budget, seed)
+
+
+class MixedBatches(Workload):
+    """1,000 NFW halos + 1e6 stars; 256 uneven refinement batches (3.7e7
+    rays) in one persistent launch replayed as a CUDA graph; the lens is
+    built once (an adaptive-refinement loop reuses it), so a step is one
+    pass over all batches."""
+    name = "mixed_batches_256"
+    FLOPS = {"far_cells": 50, "near_point": 22, "near_full": 60, "big_corrections": 70}
+
+    def __init__(self):
+        self.w = lensgen.workload_mixed_batches()
+        self.n_rays = int(self.w["offsets"][-1])
+
+    def config(self, ws):
+        return {"workload": self.name, "n_halos": 1000, "n_stars": 1_000_000, "n_batches": 256,
+                "rays": self.n_rays, "theta": self.theta, "leaf_max": 5,
+                "l2": "flushed between timed steps (256 MB write)", "graph": "CUDA graph replay",
+                "parallelism": f"independent replicas x{ws}"}
+
+    def prepare(self, L, torch, dev):
+        w = self.w
+        self.L = L
+        self.sp = [torch.from_numpy(w["points"]).to(dev), torch.from_numpy(w["nfw"]).to(dev)]
+        self.dx, self.dy = torch.from_numpy(w["dx"]).to(dev), torch.from_numpy(w["dy"]).to(dev)
+        self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
+        self.lens = L.Lens([L.Species.points(self.sp[0]), L.Species.nfw(self.sp[1], w["conc"])],
+                           theta=self.theta)
+        self.lens.reserve(self.n_rays, 256)
+        self.group = 32
+
+    def tune(self):
+        pass
+
+    def step(self, flags):
+        self.lens.shoot_batches(self.w["offsets"], self.w["origins"], self.dx, self.dy,
+                                flags=flags | self.L.USE_GRAPH, out=self.outs)
+        return None
+
+    def e2e(self, torch, dev):
+        w = self.w
+        if not hasattr(self, "h"):
+            self.h = [torch.from_numpy(w["dx"]).pin_memory(), torch.from_numpy(w["dy"]).pin_memory()]
+            self.hout = [torch.empty(self.n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
+        self.dx.copy_(self.h[0], non_blocking=True)
+        self.dy.copy_(self.h[1], non_blocking=True)
+        self.lens.shoot_batches(w["offsets"], w["origins"], self.dx, self.dy, flags=self.L.USE_GRAPH,
+                                out=self.outs)
+        for h, o in zip(self.hout, self.outs):
+            h.copy_(o, non_blocking=True)
+        return None, 2 * self.n_rays * 4, 5 * self.n_rays * 4
+
+    def oracle_rate(self, budget, seed=7):
+        import oracle
+        w = self.w
+        s, h = w["points"].astype(np.float64), w["nfw"].astype(np.float64)
+        comps = oracle.concat(oracle.make_components(oracle.POINT, s[:, 0], s[:, 1], s[:, 2]),
+                              oracle.make_components(oracle.NFW, h[:, 0], h[:, 1], h[:, 2], h[:, 3],
+                                                     w["conc"] * h[:, 3]))
+        b = np.repeat(np.arange(len(w["offsets"]) - 1), np.diff(w["offsets"]))
+        rx = w["origins"][b, 0] + w["dx"].astype(np.float64)
+        ry = w["origins"][b, 1] + w["dy"].astype(np.float64)
+        return _oracle_loop(oracle, comps, rx, ry, None, budget, seed)
+
+
+class Microlensing(Workload):
+    """1e7 stars + SIS; 4096^2 rays over a 1e-6 patch at (0.5, 0) as FP64
+    origin + FP32 offsets; theta 0.1; step = build + grouping + walk."""
+    name = "microlensing_1e7_4096sq"
+    theta = 0.1
+    FLOPS = {"far_cells": 50, "near_point": 22}
+    SIS_FLOPS = 20
+
+    def __init__(self):
+        self.w = lensgen.workload_microlensing()
+        self.n_rays = self.w["dx"].size
+
+    def flops_per_ray(self):
+        return super().flops_per_ray() + self.SIS_FLOPS
+
+    def config(self, ws):
+        return {"workload": self.name, "n_stars": 10_000_000, "sis_r_e": 0.5, "grid": 4096,
+                "patch": "1e-6 at (0.5, 0)", "theta": self.theta, "leaf_max": 5,
+                "l2": "flushed between timed steps (256 MB write)",
+                "parallelism": f"independent replicas x{ws}"}
+
+    def prepare(self, L, torch, dev):
+        w = self.w
+        self.L = L
+        self.sp = torch.from_numpy(w["points"]).to(dev)
+        self.dx, self.dy = torch.from_numpy(w["dx"]).to(dev), torch.from_numpy(w["dy"]).to(dev)
+        self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
+        self.group = 32
+
+    def tune(self):
+        lens = self.L.Lens([self.L.Species.points(self.sp)], [self.L.Halo.sis(0.0, 0.0, self.w["sis_re"])],
+                           theta=self.theta)
+        self.group = lens.autotune(self.dx, self.dy, origin=self.w["origin"])
+        lens.close()
+
+    def step(self, flags):
+        L = self.L
+        lens = L.Lens([L.Species.points(self.sp)], [L.Halo.sis(0.0, 0.0, self.w["sis_re"])], theta=self.theta,
+                      group_rays=self.group)
+        lens.shoot(self.dx, self.dy, origin=self.w["origin"], flags=flags, out=self.outs)
+        return lens
+
+    def e2e(self, torch, dev):
+        w, L = self.w, self.L
+        if not hasattr(self, "h"):
+            self.h = [torch.from_numpy(w["points"]).pin_memory(), torch.from_numpy(w["dx"]).pin_memory(),
+                      torch.from_numpy(w["dy"]).pin_memory()]
+            self.d = [torch.empty_like(x, device=dev) for x in self.h]
+            self.hout = [torch.empty(self.n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
+        for d, h in zip(self.d, self.h):
+            d.copy_(h, non_blocking=True)
+        lens = L.Lens([L.Species.points(self.d[0])], [L.Halo.sis(0.0, 0.0, w["sis_re"])], theta=self.theta,
+                      group_rays=self.group)
+        lens.shoot(self.d[1], self.d[2], origin=w["origin"], out=self.outs)
+        for h, o in zip(self.hout, self.outs):
+            h.copy_(o, non_blocking=True)
+        return lens, sum(x.numel() * 4 for x in self.h), 5 * self.n_rays * 4
+
+    def oracle_rate(self, budget, seed=7):
+        import oracle
+        w = self.w
+        s = w["points"].astype(np.float64)
+        comps = oracle.concat(oracle.make_components(oracle.POINT, s[:, 0], s[:, 1], s[:, 2]),
+                              oracle.make_components(oracle.SIS, 0.0, 0.0, 0.0, w["sis_re"]))
+        rx = w["origin"][0] + w["dx"].astype(np.float64)
+        ry = w["origin"][1] + w["dy"].astype(np.float64)
+        return _oracle_loop(oracle, comps, rx, ry, None, budget, seed)
+
+
+class Fit(Workload):
+    """Lens fit: 1e5 Gaussians (r_sm 0.01), 1000^2 grid, theta 0.3; step =
+    build + forward alpha + adjoint of L = sum |alpha - alpha_t|^2."""
+    name = "fit_1e5_1000sq"
+    FLOPS = FLOPS
+
+    def __init__(self):
+        self.w = lensgen.workload_fit()
+        self.n_rays = self.w["rx"].size
+
+    def config(self, ws):
+        return {"workload": self.name, "n_particles": 100_000, "grid": 1000, "theta": self.theta,
+                "loss": "sum |alpha - alpha_t|^2, target masses m exp(0.05 N(0,1))",
+                "l2": "flushed between timed steps (256 MB write)",
+                "parallelism": f"independent replicas x{ws}"}
+
+    def prepare(self, L, torch, dev):
+        w = self.w
+        self.L = L
+        self.torch = torch
+        self.parts = torch.from_numpy(w["gauss"]).to(dev)
+        self.rx, self.ry = torch.from_numpy(w["rx"]).to(dev), torch.from_numpy(w["ry"]).to(dev)
+        tl = L.Lens([L.Species.gauss(torch.from_numpy(w["target"]).to(dev), w["q"])], theta=self.theta)
+        at = tl.shoot(self.rx, self.ry, flags=L.ALPHA_ONLY)
+        self.at = [a.clone() for a in at[:2]]
+        tl.close()
+        self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
+        self.grad = torch.zeros(self.parts.shape[0], 3, dtype=torch.float32, device=dev)
+        self.group = 32
+
+    def tune(self):
+        lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta)
+        self.group = lens.autotune(self.rx, self.ry)
+        lens.close()
+
+    def step(self, flags):
+        L = self.L
+        lens = L.Lens([L.Species.gauss(self.parts, self.w["q"])], theta=self.theta, group_rays=self.group)
+        lens.shoot(self.rx, self.ry, flags=flags | L.ALPHA_ONLY, out=self.outs)
+        g1 = 2 * (self.outs[0] - self.at[0])
+        g2 = 2 * (self.outs[1] - self.at[1])
+        self.grad.zero_()
+        lens.backward(self.rx, self.ry, g1, g2, grads=[self.grad])
+        return lens
+
+    def e2e(self, torch, dev):
+        w, L = self.w, self.L
+        if not hasattr(self, "h"):
+            self.h = [torch.from_numpy(w["gauss"]).pin_memory(), torch.from_numpy(w["rx"]).pin_memory(),
+                      torch.from_numpy(w["ry"]).pin_memory()]
+            self.d = [torch.empty_like(x, device=dev) for x in self.h]
+            self.hgrad = torch.empty(self.parts.shape[0], 3, dtype=torch.float32).pin_memory()
+            self.hloss = torch.empty(1, dtype=torch.float32).pin_memory()
+        for d, h in zip(self.d, self.h):
+            d.copy_(h, non_blocking=True)
+        lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group)
+        lens.shoot(self.d[1], self.d[2], flags=L.ALPHA_ONLY, out=self.outs)
+        r1, r2 = self.outs[0] - self.at[0], self.outs[1] - self.at[1]
+        self.grad.zero_()
+        lens.backward(self.d[1], self.d[2], (2 * r1).contiguous(), (2 * r2).contiguous(), grads=[self.grad])
+        self.hloss.copy_((r1 * r1 + r2 * r2).sum().reshape(1), non_blocking=True)
+        self.hgrad.copy_(self.grad, non_blocking=True)
+        return lens, sum(x.numel() * 4 for x in self.h), self.hgrad.numel() * 4 + 4
+
+    def oracle_rate(self, budget, seed=7):
+        import oracle
+        w = self.w
+        p = w["gauss"].astype(np.float64)
+        comps = oracle.make_components(oracle.GAUSS, p[:, 0], p[:, 1], p[:, 2], p[:, 3], w["q"])
+        return _oracle_loop(oracle, comps, w["rx"], w["ry"], None, budget, seed)
+
+
+WORKLOADS = {"nfw_sph": NfwSph, "mixed_batches": MixedBatches, "microlensing": Microlensing, "fit": Fit}
+
+
+def _oracle_loop(oracle, comps, rx, ry, _, budget_s, seed):
+    """The oracle's FP64 direct sum (as it stands) over a time-bounded random
+    sample of the workload's rays."""
+    g = lensgen.rng(seed)
+    order = g.permutation(rx.size)
+    done, t0, chunk = 0, time.perf_counter(), 64
+    while time.perf_counter() - t0 < budget_s and done < order.size:
+        idx = order[done:done + chunk]
+        oracle.direct_sum(comps, np.asarray(rx[idx], np.float64), np.asarray(ry[idx], np.float64))
+        done += idx.size
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, oracle.max_threads()
 
 
 # ------------------------------------------------------------- GPU path
@@ -195,39 +458,30 @@ def run_gpu(args, ws, rank, local):
     import paper_1312_1128_gb300 as L
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = lensgen.workload_nfw_sph()
-    n_rays = w["rx"].size
-    parts = torch.from_numpy(w["gauss"]).to(dev)
-    rx = torch.from_numpy(w["rx"]).to(dev)
-    ry = torch.from_numpy(w["ry"]).to(dev)
-    outs = [torch.empty(n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
+    wl = WORKLOADS[args.workload]()
+    wl.prepare(L, torch, dev)
+    n_rays = wl.n_rays
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    species = [L.Species.gauss(parts, w["q"])]
     lib = L.lib()
 
-    tuned = {"group_rays": 32}
+    def done(lens):
+        if lens is not None:
+            lens.close()
 
-    def step(flags=L.TIMING):
-        lens = L.Lens(species, theta=THETA, group_rays=tuned["group_rays"])
-        lens.shoot(rx, ry, flags=flags, out=outs)
-        return lens
-
-    # autotune the ray-group size once on this lens and these rays (warm-up)
-    lens = L.Lens(species, theta=THETA)
-    tuned["group_rays"] = lens.autotune(rx, ry)
-    lens.close()
+    wl.tune()   # autotune the ray-group size once (warm-up)
     for _ in range(args.warmup):
-        step().close()
+        done(wl.step(L.TIMING))
     torch.cuda.synchronize()
     # interaction counters of one step (outside the timed region)
-    lens = step(L.COUNT)
-    lens.sync()
-    cnt = lens.counters()
-    lens.close()
+    lens = wl.step(L.COUNT)
+    tgt = lens if lens is not None else getattr(wl, "lens", None)
+    tgt.sync()
+    cnt = tgt.counters()
+    done(lens)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    walk_ms, group_ms = [], []
+    walk_ms, group_ms, build_phases = [], [], None
     clocks = ClockSampler(local)
     launches0 = lib.lens_kernel_launches()
     for k in range(args.steps):
@@ -235,14 +489,16 @@ def run_gpu(args, ws, rank, local):
         torch.cuda.synchronize()
         barrier(ws)
         ev[k][0].record()
-        lens = step()
+        lens = wl.step(L.TIMING)
         ev[k][1].record()
         torch.cuda.synchronize()
-        g_ms, w_ms = lens.last_timing()
+        tl = lens if lens is not None else wl.lens
+        g_ms, w_ms = tl.last_timing()
         group_ms.append(g_ms)
         walk_ms.append(w_ms)
-        build_phases = [round(x, 3) for x in lens.info()["build_ms"][0]]
-        lens.close()
+        if lens is not None:
+            build_phases = [round(x, 3) for x in lens.info()["build_ms"][0]]
+        done(lens)
     barrier(ws)
     launches = lib.lens_kernel_launches() - launches0
     clk = clocks.stop()
@@ -251,12 +507,6 @@ def run_gpu(args, ws, rank, local):
     value = ws * n_rays / (ms * 1e-3)
 
     # end to end through the public API with host buffers
-    h_parts = torch.from_numpy(w["gauss"]).pin_memory()
-    h_rx = torch.from_numpy(w["rx"]).pin_memory()
-    h_ry = torch.from_numpy(w["ry"]).pin_memory()
-    h_out = [torch.empty(n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
-    d_parts = torch.empty_like(parts)
-    d_rx, d_ry = torch.empty_like(rx), torch.empty_like(ry)
     e2e_ms = []
     for k in range(max(3, args.steps // 2)):
         flush.fill_(k & 0xff)
@@ -264,23 +514,15 @@ def run_gpu(args, ws, rank, local):
         barrier(ws)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        d_parts.copy_(h_parts, non_blocking=True)
-        d_rx.copy_(h_rx, non_blocking=True)
-        d_ry.copy_(h_ry, non_blocking=True)
-        lens = L.Lens([L.Species.gauss(d_parts, w["q"])], theta=THETA)
-        lens.shoot(d_rx, d_ry, out=outs)
-        for h, o in zip(h_out, outs):
-            h.copy_(o, non_blocking=True)
+        lens, h2d, d2h = wl.e2e(torch, dev)
         b.record()
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-        lens.close()
+        done(lens)
     e2e = max_over_ranks(ws, float(np.mean(e2e_ms)), dev)
-    h2d = h_parts.numel() * 4 + 2 * n_rays * 4
-    d2h = 5 * n_rays * 4
 
-    # roofline of the dominant kernel (the walk): useful flops / its duration
-    fpr = useful_flops_per_ray(THETA)
+    # roofline of the dominant kernel (the forward walk): useful flops / its duration
+    fpr = wl.flops_per_ray()
     w_ms = float(np.mean(walk_ms))
     achieved = fpr * n_rays / (w_ms * 1e-3) / 1e12
     props = torch.cuda.get_device_properties(dev)
@@ -290,12 +532,13 @@ def run_gpu(args, ws, rank, local):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": bench_config(ws), "tuning": {"group_rays": tuned["group_rays"]},
+            "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
+            "config": wl.config(ws), "tuning": {"group_rays": wl.group},
             "e2e": {"value": ws * n_rays / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": walk_traffic(),
+                         "frac": achieved / peak,
+                         "traffic": walk_traffic() if args.workload == "nfw_sph" else None,
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                                        f"{sm_max:.0f} MHz (max SM clock)",
                          "fp32_ffma_measured": measured_peak,
@@ -306,10 +549,10 @@ def run_gpu(args, ws, rank, local):
                                                  "big_scanned", "big_kept", "ray_interactions"]},
             "clocks": clk, "gpu_launches": int(launches)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        r, done, dt, cores = oracle_rays_per_sec(w, args.cpu_seconds)
+        r, done_n, dt, cores = wl.oracle_rate(args.cpu_seconds)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{done} random grid rays of the workload, FP64 direct sum "
-                                          f"over all 1e6 particles, {dt:.1f} s"}
+                                "sample": f"{done_n} random rays of the workload, FP64 direct sum over "
+                                          f"every lens component, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -336,6 +579,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", choices=["nfw_sph", "mixed_batches", "microlensing", "fit"], default="nfw_sph",
+                    help="nfw_sph (default) is the headline; the others measure the batched, "
+                         "microlensing and differentiable paths")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--grid", type=int, default=2048,
