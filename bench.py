@@ -166,6 +166,10 @@ class Workload:
     name = ""
     theta = THETA
     dtype = "f32"
+    graph = False
+
+    def extra(self):
+        return {}
 
     def flops_per_ray(self):
         with open(os.path.join(ROOT, "tests", "golden", "useful_counts.json")) as f:
@@ -193,6 +197,11 @@ class NfwSph(Workload):
         self.rx, self.ry = torch.from_numpy(w["rx"]).to(dev), torch.from_numpy(w["ry"]).to(dev)
         self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
         self.group = 32
+        # pinned host buffers of the end-to-end form, allocated outside any timing
+        self.h = [torch.from_numpy(w["gauss"]).pin_memory(), torch.from_numpy(w["rx"]).pin_memory(),
+                  torch.from_numpy(w["ry"]).pin_memory()]
+        self.d = [torch.empty_like(x, device=dev) for x in self.h]
+        self.hout = [torch.empty(self.n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
 
     def tune(self):
         lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta)
@@ -208,11 +217,6 @@ class NfwSph(Workload):
     def e2e(self, torch, dev):
         """Host buffers: H2D of particles and rays, D2H of the five outputs."""
         w, L = self.w, self.L
-        if not hasattr(self, "h"):
-            self.h = [torch.from_numpy(w["gauss"]).pin_memory(), torch.from_numpy(w["rx"]).pin_memory(),
-                      torch.from_numpy(w["ry"]).pin_memory()]
-            self.d = [torch.empty_like(x, device=dev) for x in self.h]
-            self.hout = [torch.empty(self.n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
         for d, h in zip(self.d, self.h):
             d.copy_(h, non_blocking=True)
         lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group)
@@ -257,20 +261,22 @@ class MixedBatches(Workload):
                            theta=self.theta)
         self.lens.reserve(self.n_rays, 256)
         self.group = 32
+        self.h = [torch.from_numpy(w["dx"]).pin_memory(), torch.from_numpy(w["dy"]).pin_memory()]
+        self.hout = [torch.empty(self.n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
+
+    graph = True  # timed by the caller's events (a replayed graph records no internal events)
 
     def tune(self):
         pass
 
     def step(self, flags):
+        # LENS_TIMING does not combine with graph replay; COUNT does (own graph)
         self.lens.shoot_batches(self.w["offsets"], self.w["origins"], self.dx, self.dy,
-                                flags=flags | self.L.USE_GRAPH, out=self.outs)
+                                flags=(flags & ~self.L.TIMING) | self.L.USE_GRAPH, out=self.outs)
         return None
 
     def e2e(self, torch, dev):
         w = self.w
-        if not hasattr(self, "h"):
-            self.h = [torch.from_numpy(w["dx"]).pin_memory(), torch.from_numpy(w["dy"]).pin_memory()]
-            self.hout = [torch.empty(self.n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
         self.dx.copy_(self.h[0], non_blocking=True)
         self.dy.copy_(self.h[1], non_blocking=True)
         self.lens.shoot_batches(w["offsets"], w["origins"], self.dx, self.dy, flags=self.L.USE_GRAPH,
@@ -320,6 +326,10 @@ class Microlensing(Workload):
         self.dx, self.dy = torch.from_numpy(w["dx"]).to(dev), torch.from_numpy(w["dy"]).to(dev)
         self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
         self.group = 32
+        self.h = [torch.from_numpy(w["points"]).pin_memory(), torch.from_numpy(w["dx"]).pin_memory(),
+                  torch.from_numpy(w["dy"]).pin_memory()]
+        self.d = [torch.empty_like(x, device=dev) for x in self.h]
+        self.hout = [torch.empty(self.n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
 
     def tune(self):
         lens = self.L.Lens([self.L.Species.points(self.sp)], [self.L.Halo.sis(0.0, 0.0, self.w["sis_re"])],
@@ -336,11 +346,6 @@ class Microlensing(Workload):
 
     def e2e(self, torch, dev):
         w, L = self.w, self.L
-        if not hasattr(self, "h"):
-            self.h = [torch.from_numpy(w["points"]).pin_memory(), torch.from_numpy(w["dx"]).pin_memory(),
-                      torch.from_numpy(w["dy"]).pin_memory()]
-            self.d = [torch.empty_like(x, device=dev) for x in self.h]
-            self.hout = [torch.empty(self.n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
         for d, h in zip(self.d, self.h):
             d.copy_(h, non_blocking=True)
         lens = L.Lens([L.Species.points(self.d[0])], [L.Halo.sis(0.0, 0.0, w["sis_re"])], theta=self.theta,
@@ -390,6 +395,12 @@ class Fit(Workload):
         self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
         self.grad = torch.zeros(self.parts.shape[0], 3, dtype=torch.float32, device=dev)
         self.group = 32
+        self.h = [torch.from_numpy(w["gauss"]).pin_memory(), torch.from_numpy(w["rx"]).pin_memory(),
+                  torch.from_numpy(w["ry"]).pin_memory()]
+        self.d = [torch.empty_like(x, device=dev) for x in self.h]
+        self.hgrad = torch.empty(self.parts.shape[0], 3, dtype=torch.float32).pin_memory()
+        self.hloss = torch.empty(1, dtype=torch.float32).pin_memory()
+        self.back_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
 
     def tune(self):
         lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta)
@@ -403,17 +414,16 @@ class Fit(Workload):
         g1 = 2 * (self.outs[0] - self.at[0])
         g2 = 2 * (self.outs[1] - self.at[1])
         self.grad.zero_()
+        self.back_ev[0].record()
         lens.backward(self.rx, self.ry, g1, g2, grads=[self.grad])
+        self.back_ev[1].record()
         return lens
+
+    def extra(self):
+        return {"backward_ms": self.back_ev[0].elapsed_time(self.back_ev[1])}
 
     def e2e(self, torch, dev):
         w, L = self.w, self.L
-        if not hasattr(self, "h"):
-            self.h = [torch.from_numpy(w["gauss"]).pin_memory(), torch.from_numpy(w["rx"]).pin_memory(),
-                      torch.from_numpy(w["ry"]).pin_memory()]
-            self.d = [torch.empty_like(x, device=dev) for x in self.h]
-            self.hgrad = torch.empty(self.parts.shape[0], 3, dtype=torch.float32).pin_memory()
-            self.hloss = torch.empty(1, dtype=torch.float32).pin_memory()
         for d, h in zip(self.d, self.h):
             d.copy_(h, non_blocking=True)
         lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group)
@@ -481,7 +491,7 @@ def run_gpu(args, ws, rank, local):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    walk_ms, group_ms, build_phases = [], [], None
+    walk_ms, group_ms, build_phases, extras = [], [], None, []
     clocks = ClockSampler(local)
     launches0 = lib.lens_kernel_launches()
     for k in range(args.steps):
@@ -492,10 +502,13 @@ def run_gpu(args, ws, rank, local):
         lens = wl.step(L.TIMING)
         ev[k][1].record()
         torch.cuda.synchronize()
-        tl = lens if lens is not None else wl.lens
-        g_ms, w_ms = tl.last_timing()
+        if wl.graph:
+            g_ms, w_ms = 0.0, ev[k][0].elapsed_time(ev[k][1])  # grouping + walk, one graph
+        else:
+            g_ms, w_ms = lens.last_timing()
         group_ms.append(g_ms)
         walk_ms.append(w_ms)
+        extras.append(wl.extra())
         if lens is not None:
             build_phases = [round(x, 3) for x in lens.info()["build_ms"][0]]
         done(lens)
@@ -545,6 +558,7 @@ def run_gpu(args, ws, rank, local):
                          "useful_flops_per_ray": fpr, "walk_ms": w_ms,
                          "group_ms": float(np.mean(group_ms))},
             "build_ms_phases": build_phases,
+            **({k: float(np.mean([e[k] for e in extras])) for k in extras[0]} if extras and extras[0] else {}),
             "interactions": {k: cnt[k] for k in ["groups", "visited", "cells", "leaf_particles",
                                                  "big_scanned", "big_kept", "ray_interactions"]},
             "clocks": clk, "gpu_launches": int(launches)}

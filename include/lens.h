@@ -84,7 +84,8 @@ enum {
     LENS_ACCUMULATE = 4,  /* add to the output arrays instead of overwriting them           */
     LENS_USE_GRAPH = 8,   /* lens_shoot_batches: replay a cached CUDA graph of the launch    */
     LENS_COUNT = 16,      /* accumulate walk interaction counters (lens_tree_counters)     */
-    LENS_TIMING = 32      /* time the grouping and walk kernels (lens_last_timing)          */
+    LENS_TIMING = 32      /* time the grouping and walk kernels (lens_last_timing); not with *
+                           * LENS_USE_GRAPH (time a replay with events on the caller's stream) */
 };
 
 /* One particle species: a homogeneous set of particles of one kind (Sec. 3.1

@@ -280,6 +280,9 @@ lens_status lens_shoot_batches(lens_tree* tree, int64_t n_batches, const int64_t
     if (n == 0) return LENS_OK;
     if (!ray_dx || !ray_dy) return lens_set_error(LENS_ERR_INVALID_ARG, "ray arrays are NULL");
     void* out[5] = {alpha1, alpha2, kappa, gamma1, gamma2};
+    if ((flags & LENS_USE_GRAPH) && (flags & LENS_TIMING))
+        return lens_set_error(LENS_ERR_INVALID_ARG, "LENS_TIMING cannot be combined with LENS_USE_GRAPH; "
+                                                    "time a replay with events on the caller's stream");
     if (flags & LENS_USE_GRAPH)
         return graph_shoot_batches(tree, n_batches, offsets, origins, ray_dx, ray_dy, ray_dtype, out,
                                    flags & ~LENS_USE_GRAPH, (cudaStream_t)stream);

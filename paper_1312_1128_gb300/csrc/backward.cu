@@ -117,12 +117,12 @@ LENS_DEV void big_term(const BackParams<T>& P, const vec4_t<T>& q, const vec4_t<
                        T& Dp)
 {
     if constexpr (KIND == LENS_GAUSS) {
-        const double L = 0.69314718055994530942;
+        const T L = T(0.69314718055994530942);
         if (q.w < T(0)) {
             // no ray inside the softening radius: closed form of (full - point)
             T inv = rcp(r2);
             T t = r2 * q1.y;
-            T e = (T)exp2(-(double)fmin(t, P.Uq2));
+            T e = exp2neg(fmin(t, P.Uq2));
             kb = (q1.x * inv) * (P.eU - e);
             kap = t < P.Uq2 ? q1.z * e : T(0);
             Dp = (kb - kap) * inv;
@@ -132,8 +132,8 @@ LENS_DEV void big_term(const BackParams<T>& P, const vec4_t<T>& q, const vec4_t<
             T kbp = (q1.x * P.Nq) * inv_s;
             T t = r2 * q1.y;
             if (t < P.Uq2) {
-                T u = (T)((double)t * L);
-                T e = (T)exp(-(double)u), h1, g;
+                T u = t * L;
+                T e = expneg(u), h1, g;
                 gauss_h1_g(u, e, h1, g);
                 kb = q1.z * h1 - kbp;
                 kap = q1.z * e;

@@ -192,6 +192,7 @@ LENS_DEV float exp2neg(float t)
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-t));
     return r;
 }
+LENS_DEV double exp2neg(double t) { return exp2(-t); }
 
 // Correction (full truncated Gaussian - softened point) at offset w, for an
 // entry that some ray of the group approaches within its softening radius.
