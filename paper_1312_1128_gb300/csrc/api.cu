@@ -26,6 +26,7 @@ static thread_local char g_msg[512] = "";
 static std::atomic<long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 lens_status lens_set_error(lens_status s, const char* fmt, ...)
 {

@@ -17,8 +17,24 @@ struct GraphEntry {
     int dtype, flags;
     void* out[5];
     void* scratch;
+    int64_t kernels;  // kernel nodes in the graph, added to the launch counter per replay
     cudaGraphExec_t exec;
 };
+
+// Number of kernel nodes in a captured graph.
+static int64_t count_kernel_nodes(cudaGraph_t graph)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(graph, nodes.data(), &n) != cudaSuccess) return 0;
+    int64_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
 
 void free_graphs(lens_tree* t)
 {
@@ -41,6 +57,7 @@ lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, co
         for (int q = 0; q < 5 && same; ++q) same = g->out[q] == out[q];
         if (same) {
             LENS_CUDA(cudaGraphLaunch(g->exec, s));
+            note_launches(g->kernels);
             return LENS_OK;
         }
     }
@@ -54,7 +71,9 @@ lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, co
         cudaStreamDestroy(cs);
         return lens_cuda_check(e, "cudaStreamBeginCapture");
     }
+    const int64_t before = lens_kernel_launches();
     lens_status st = enqueue_shoot(t, plan, dx, dy, dtype, out, flags, cs);
+    note_launches(before - lens_kernel_launches());  // capture records kernels without running them
     e = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
     if (st != LENS_OK) {
@@ -62,11 +81,12 @@ lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, co
         return st;
     }
     if (e != cudaSuccess) return lens_cuda_check(e, "cudaStreamEndCapture");
+    const int64_t kernels = count_kernel_nodes(graph);
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return lens_cuda_check(e, "cudaGraphInstantiate");
-    GraphEntry* g = new GraphEntry{plan.n, plan.nb, plan.ng, dx, dy, dtype, flags, {}, t->ray_scratch.ptr, exec};
+    GraphEntry* g = new GraphEntry{plan.n, plan.nb, plan.ng, dx, dy, dtype, flags, {}, t->ray_scratch.ptr, kernels, exec};
     for (int q = 0; q < 5; ++q) g->out[q] = out[q];
     t->graphs.push_back(g);
     return LENS_OK;

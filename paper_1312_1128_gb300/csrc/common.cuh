@@ -69,6 +69,7 @@ LENS_HD double ordered_to_dbl(unsigned long long u)
 
 // Host-side helpers (defined in api.cu).
 void note_launch();  // counts every kernel launch made by the library
+void note_launches(int64_t n);  // adds n launches (a graph replay), or takes back -n
 lens_status lens_set_error(lens_status s, const char* fmt, ...);
 lens_status lens_cuda_check(cudaError_t e, const char* what);
 

@@ -174,13 +174,20 @@ def test_batches_and_graph_replay():
     w = lensgen.workload_mixed_batches(n_halos=100, n_stars=20000, n_batches=12, nmin=50, nmax=3000)
     lens = L.Lens([L.Species.points(cu(w["points"])), L.Species.nfw(cu(w["nfw"]), 3.0)], theta=0.3)
     dx, dy = cu(w["dx"]), cu(w["dy"])
+    lib = L.lib()
+    k0 = lib.lens_kernel_launches()
     eager = to_np(lens.shoot_batches(w["offsets"], w["origins"], dx, dy))
+    per_call = lib.lens_kernel_launches() - k0
+    assert per_call > 0
     outs = [torch.empty(dx.numel(), device="cuda") for _ in range(5)]
-    for _ in range(3):
+    for it in range(3):
         for o in outs:
             o.fill_(float("nan"))
+        k0 = lib.lens_kernel_launches()
         lens.shoot_batches(w["offsets"], w["origins"], dx, dy, flags=L.USE_GRAPH, out=outs)
         lens.sync()
+        # the first call runs eagerly and captures; a replay counts the graph's kernels
+        assert lib.lens_kernel_launches() - k0 == per_call, it
         np.testing.assert_array_equal(to_np(outs), eager)
     comps = oracle.concat(comps_points(w["points"]), comps_nfw(w["nfw"], 3.0))
     b = np.repeat(np.arange(len(w["offsets"]) - 1), np.diff(w["offsets"]))
