@@ -285,6 +285,69 @@ LENS_DEV void gauss_correction_inside(Acc5<double>& acc, double wx, double wy, c
     gauss_correction_fast<AO>(acc, wx, wy, q1, INFINITY, eU);
 }
 
+// Two big-list entries of the same ray at once, in packed FP32x2 arithmetic
+// (one instruction issues both halves).  The closed form above, for entries
+// that no ray of the group reaches inside the softening radius; EDGE selects
+// the form with the support edge (clamped exponent, kappa 0 outside), else
+// every ray lies inside both supports.  Operands are pairs over the two
+// entries: nx, ny = minus the entry positions, cl = -c log2 e, kz = m c/N_q,
+// mN = m/N_q, nmE = -(m/N_q) e^-q^2/2; lx, ly = the ray's position in both
+// halves; nUq2 = -q^2/2 log2 e.  With P = kappa - dkb (= -dD r^2):
+//   -dkb = ((m/N_q) e - (m/N_q) eU)/r^2,   -dD = P/r^2,
+//   -alpha += -dkb w,  gamma1 = sum P - 2 sum (-dD) wy^2 (= sum -dD (wx^2 - wy^2)),
+//   gamma2/2 = sum -dD wx wy,
+// so every update is one FMA or add; the halves are summed when the buffer
+// is folded.  Accumulators: na1, na2 = -alpha; k = kappa; g1p = sum P;
+// g1y = sum -dD wy^2; hg2 = gamma2/2.
+struct Acc5x2 {
+    float2 na1, na2, k, g1p, g1y, hg2;
+    LENS_DEV void zero()
+    {
+        na1 = na2 = k = g1p = g1y = hg2 = make_float2(0.0f, 0.0f);
+    }
+};
+
+LENS_DEV float exp2_approx(float t)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
+    return r;
+}
+
+template <bool AO, bool EDGE>
+LENS_DEV void gauss_correction_x2(Acc5x2& acc, float2 lx, float2 ly, float2 nx, float2 ny, float2 cl, float2 mN,
+                                  float2 nmE, float2 kz, float nUq2)
+{
+    float2 wx = __fadd2_rn(lx, nx);
+    float2 wy = __fadd2_rn(ly, ny);
+    float2 wyy = __fmul2_rn(wy, wy);
+    float2 r2 = __ffma2_rn(wx, wx, wyy);
+    float2 t = __fmul2_rn(r2, cl);
+    float2 tc = t;
+    if (EDGE) {
+        tc.x = fmaxf(t.x, nUq2);
+        tc.y = fmaxf(t.y, nUq2);
+    }
+    float2 e = make_float2(exp2_approx(tc.x), exp2_approx(tc.y));
+    float2 inv = make_float2(rcp(r2.x), rcp(r2.y));
+    float2 ndkb = __fmul2_rn(__ffma2_rn(mN, e, nmE), inv);
+    acc.na1 = __ffma2_rn(ndkb, wx, acc.na1);
+    acc.na2 = __ffma2_rn(ndkb, wy, acc.na2);
+    if (!AO) {
+        float2 ek = e;
+        if (EDGE) {
+            ek.x = t.x > nUq2 ? e.x : 0.0f;
+            ek.y = t.y > nUq2 ? e.y : 0.0f;
+        }
+        acc.k = __ffma2_rn(kz, ek, acc.k);
+        float2 P = __ffma2_rn(kz, ek, ndkb);
+        acc.g1p = __fadd2_rn(acc.g1p, P);
+        float2 ndD = __fmul2_rn(P, inv);
+        acc.g1y = __ffma2_rn(ndD, wyy, acc.g1y);
+        acc.hg2 = __ffma2_rn(ndD, __fmul2_rn(wx, wy), acc.hg2);
+    }
+}
+
 // FP64 form of the same correction (q1.y holds c log2 e as well).
 template <bool AO>
 LENS_DEV void gauss_correction(Acc5<double>& acc, double wx, double wy, const dbl4& q, const dbl4& q1,

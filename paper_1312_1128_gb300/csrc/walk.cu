@@ -251,11 +251,21 @@ template <typename T> struct WalkParams {
 };
 
 template <int KIND, typename T> struct WalkShared {
+    // FP32 Gaussian big entries are stored one array per field, so that two
+    // consecutive entries load as one float2 operand of the packed form
+    static constexpr bool kPackedBig = KIND == LENS_GAUSS && sizeof(T) == 4;
+    static constexpr int kB = kPackedBig ? kBigCap : 1;
     T fdx[kFarCap], fdy[kFarCap], fM[kFarCap], fqr[kFarCap], fqi[kFarCap];
     vec4_t<T> n0[kNearCap];
     vec4_t<T> n1[KIND == LENS_NFW ? kNearCap : 1];
-    vec4_t<T> b0[KIND == LENS_POINT ? 1 : kBigCap];
-    vec4_t<T> b1[KIND == LENS_POINT ? 1 : kBigCap];
+    vec4_t<T> b0[KIND == LENS_POINT || kPackedBig ? 1 : kBigCap];
+    vec4_t<T> b1[KIND == LENS_POINT || kPackedBig ? 1 : kBigCap];
+    // -x, -y (from the group anchor), -c log2 e, m/N_q, -(m/N_q) e^-q^2/2,
+    // m c/N_q, the flag or 1/r0^2 (b0.w of the generic layout) and 1/c.
+    // Entries whose support contains every ray of the group fill slots
+    // [0, n_in) from the bottom; the others fill [kBigCap - n_out, kBigCap)
+    // from the top (the buffer count packs n_in | n_out << 16).
+    float bnx[kB], bny[kB], bcl[kB], bm[kB], bme[kB], bk[kB], bw[kB], bic[kB];
     int rs_off[33];
     int rs_first[32];
     int rs_end[32];
@@ -323,8 +333,98 @@ template <int KIND, typename T, int R, bool AO> struct WalkCtx {
     // b0 = {x - H.x, y - H.y, s^2, 1/r0^2}; b1 = {m/N_q, c log2 e, m c / N_q,
     // 1/c} (GAUSS) or {m, A, B, 0} (NFW).  1/max(r^2, r0^2) = min(1/r^2, 1/r0^2).
     // Two entries per iteration for instruction-level parallelism.
+    // One packed-layout entry for every ray, in scalar arithmetic (entries
+    // with a ray inside the softening radius, and unpaired entries).
+    LENS_DEV void big_entry_scalar(int i, Acc5x2 (&pa)[R])
+    {
+        const float nx = S.bnx[i], ny = S.bny[i], w = S.bw[i];
+        const float4 q = make_float4(0.0f, 0.0f, 0.0f, w);
+        const float4 q1 = make_float4(S.bm[i], -S.bcl[i], S.bk[i], S.bic[i]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            Acc5<float> a;
+            a.zero();
+            if (w < 0.0f) gauss_correction_fast<AO>(a, lx[r] + nx, ly[r] + ny, q1, P.Uq2, P.eU);
+            else gauss_correction<AO>(a, lx[r] + nx, ly[r] + ny, q, q1, P.Uq2, P.Nq);
+            pa[r].na1.x -= a.a1;
+            pa[r].na2.x -= a.a2;
+            if (!AO) {
+                pa[r].k.x += a.k;
+                pa[r].g1p.x += a.g1;
+                pa[r].hg2.x = fmaf(0.5f, a.g2, pa[r].hg2.x);
+            }
+        }
+    }
+
+    template <bool EDGE>
+    LENS_DEV void big_pair_packed(int i, Acc5x2 (&pa)[R], const float2 (&LX)[R], const float2 (&LY)[R])
+    {
+        const float2 nx = *reinterpret_cast<const float2*>(&S.bnx[i]);
+        const float2 ny = *reinterpret_cast<const float2*>(&S.bny[i]);
+        const float2 cl = *reinterpret_cast<const float2*>(&S.bcl[i]);
+        const float2 mN = *reinterpret_cast<const float2*>(&S.bm[i]);
+        const float2 nmE = *reinterpret_cast<const float2*>(&S.bme[i]);
+        const float2 kz = *reinterpret_cast<const float2*>(&S.bk[i]);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            gauss_correction_x2<AO, EDGE>(pa[r], LX[r], LY[r], nx, ny, cl, mN, nmE, kz, -P.Uq2);
+    }
+
+    // FP32 Gaussian big buffer in packed arithmetic: the whole-group-inside
+    // region four entries at a time without tests, then the other region
+    // pair by pair (packed closed form with the support edge, or scalar where
+    // a ray may be inside the softening radius).
+    LENS_DEV void flush_big_packed(int nbuf)
+    {
+        const int n_in = nbuf & 0xffff, n_out = nbuf >> 16;
+        Acc5x2 pa[R];
+        float2 LX[R], LY[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            pa[r].zero();
+            LX[r] = make_float2(lx[r], lx[r]);
+            LY[r] = make_float2(ly[r], ly[r]);
+        }
+        int i = 0;
+        for (; i + 3 < n_in; i += 4) {
+            big_pair_packed<false>(i, pa, LX, LY);
+            big_pair_packed<false>(i + 2, pa, LX, LY);
+        }
+        if (i + 1 < n_in) {
+            big_pair_packed<false>(i, pa, LX, LY);
+            i += 2;
+        }
+        if (i < n_in) big_entry_scalar(i, pa);
+        i = kBigCap - n_out;
+        if ((i & 1) && i < kBigCap) big_entry_scalar(i++, pa);
+        for (; i + 1 < kBigCap; i += 2) {
+            const float2 w = *reinterpret_cast<const float2*>(&S.bw[i]);
+            if (w.x < 0.0f && w.y < 0.0f) {
+                big_pair_packed<true>(i, pa, LX, LY);
+            } else {
+                big_entry_scalar(i, pa);
+                big_entry_scalar(i + 1, pa);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            part[r].a1 -= pa[r].na1.x + pa[r].na1.y;
+            part[r].a2 -= pa[r].na2.x + pa[r].na2.y;
+            if (!AO) {
+                part[r].k += pa[r].k.x + pa[r].k.y;
+                part[r].g1 += (pa[r].g1p.x + pa[r].g1p.y) - 2.0f * (pa[r].g1y.x + pa[r].g1y.y);
+                part[r].g2 += 2.0f * (pa[r].hg2.x + pa[r].hg2.y);
+            }
+        }
+        fold();
+    }
+
     LENS_DEV void flush_big(int nb)
     {
+        if constexpr (WalkShared<KIND, T>::kPackedBig) {
+            flush_big_packed(nb);
+            return;
+        }
         int i = 0;
         if constexpr (KIND == LENS_GAUSS) {
             // b0.w < 0 marks an entry whose softening radius no ray of the
@@ -420,9 +520,9 @@ template <int KIND, typename T, int R, bool AO> struct WalkCtx {
     }
 };
 
-// Append, in order, the items of up to 32 index ranges (one per lane) to a
-// shared buffer, flushing it whenever fewer than 32 slots remain.
-template <int KIND, typename T, int R, bool AO, bool BIG>
+// Append, in order, the leaf particles of up to 32 index ranges (one per
+// lane) to the near buffer, flushing it whenever fewer than 32 slots remain.
+template <int KIND, typename T, int R, bool AO>
 LENS_DEV void append_ranges(WalkCtx<KIND, T, R, AO>& C, int cnt, int first, int& nbuf,
                             const vec4_t<T>* src0, const vec4_t<T>* src1, int& n_seen, int& n_kept)
 {
@@ -437,11 +537,9 @@ LENS_DEV void append_ranges(WalkCtx<KIND, T, R, AO>& C, int cnt, int first, int&
     S.rs_first[lane] = first;
     if (lane == 31) S.rs_off[32] = tot;
     __syncwarp();
-    const int cap = BIG ? kBigCap : kNearCap;
     for (int base = 0; base < tot; base += 32) {
-        if (nbuf + 32 > cap) {
-            if constexpr (BIG) C.flush_big(nbuf);
-            else C.flush_near(nbuf);
+        if (nbuf + 32 > kNearCap) {
+            C.flush_near(nbuf);
             nbuf = 0;
             __syncwarp();
         }
@@ -458,32 +556,28 @@ LENS_DEV void append_ranges(WalkCtx<KIND, T, R, AO>& C, int cnt, int first, int&
             }
             int p = S.rs_first[lo] + (i - S.rs_off[lo]);
             q0 = src0[p];
-            if constexpr (BIG || KIND == LENS_NFW) q1 = src1[p];
+            if constexpr (KIND == LENS_NFW) q1 = src1[p];
             q0.x -= C.H.x;
             q0.y -= C.H.y;
             keep = true;
-            if constexpr (BIG) {
-                // does the support reach the group's bounding box?
-                T ex = fmax(fabs(q0.x - C.box.x) - C.box.z, T(0));
-                T ey = fmax(fabs(q0.y - C.box.y) - C.box.w, T(0));
-                keep = fma(ex, ex, ey * ey) < q1.y;
-            }
         }
         unsigned ball = __ballot_sync(full, keep);
         if (keep) {
             int slot = nbuf + __popc(ball & ((1u << lane) - 1u));
-            if constexpr (BIG) {
-                S.b0[slot] = q0;
-                S.b1[slot] = q1;
-            } else {
-                S.n0[slot] = q0;
-                if constexpr (KIND == LENS_NFW) S.n1[slot] = q1;
-            }
+            S.n0[slot] = q0;
+            if constexpr (KIND == LENS_NFW) S.n1[slot] = q1;
         }
         nbuf += __popc(ball);
         n_kept += __popc(ball);
         __syncwarp();
     }
+}
+
+// Slots in use in the big buffer (the packed layout counts both regions).
+template <int KIND, typename T> LENS_DEV int big_used(int nbuf)
+{
+    if constexpr (WalkShared<KIND, T>::kPackedBig) return (nbuf & 0xffff) + (nbuf >> 16);
+    else return nbuf;
 }
 
 // Big lists of the visited boxes (one list per lane: entries [z, z + w) of
@@ -533,7 +627,7 @@ LENS_DEV void append_big(WalkCtx<KIND, T, R, AO>& C, bool has, int v, int z, int
             ball &= ball - 1;
             int c = __shfl_sync(full, cid, src);
             int o = __shfl_sync(full, own, src);
-            if (nbuf + 32 > kBigCap) {
+            if (big_used<KIND, T>(nbuf) + 32 > kBigCap) {
                 C.flush_big(nbuf);
                 nbuf = 0;
                 __syncwarp();
@@ -562,13 +656,32 @@ LENS_DEV void append_big(WalkCtx<KIND, T, R, AO>& C, bool has, int v, int z, int
                 }
             }
             unsigned kb = __ballot_sync(full, keep);
-            if (keep) {
-                q1 = P.big1[e];
-                int slot = nbuf + __popc(kb & ((1u << lane) - 1u));
-                S.b0[slot] = q0;
-                S.b1[slot] = q1;
+            if constexpr (WalkShared<KIND, T>::kPackedBig) {
+                const bool in = keep && q0.w < T(-1.5);
+                const unsigned bi = __ballot_sync(full, in), lt = (1u << lane) - 1u;
+                if (keep) {
+                    q1 = P.big1[e];
+                    int slot = in ? (nbuf & 0xffff) + __popc(bi & lt)
+                                  : kBigCap - 1 - ((nbuf >> 16) + __popc(kb & ~bi & lt));
+                    S.bnx[slot] = -q0.x;
+                    S.bny[slot] = -q0.y;
+                    S.bcl[slot] = -q1.y;
+                    S.bm[slot] = q1.x;
+                    S.bme[slot] = -q1.x * P.eU;
+                    S.bk[slot] = q1.z;
+                    S.bw[slot] = q0.w;
+                    S.bic[slot] = q1.w;
+                }
+                nbuf += __popc(bi) + (__popc(kb & ~bi) << 16);
+            } else {
+                if (keep) {
+                    q1 = P.big1[e];
+                    int slot = nbuf + __popc(kb & ((1u << lane) - 1u));
+                    S.b0[slot] = q0;
+                    S.b1[slot] = q1;
+                }
+                nbuf += __popc(kb);
             }
-            nbuf += __popc(kb);
             n_kept += __popc(kb);
             __syncwarp();
         }
@@ -576,7 +689,7 @@ LENS_DEV void append_big(WalkCtx<KIND, T, R, AO>& C, bool has, int v, int z, int
 }
 
 template <int KIND, typename T, int R, bool AO, bool DIRECT>
-__global__ void __launch_bounds__(kWalkWarps * 32, sizeof(T) == 4 ? 6 : 2)
+__global__ void __launch_bounds__(kWalkWarps * 32, sizeof(T) == 4 ? (R == 2 ? 5 : 6) : 2)
 walk_kernel(WalkParams<T> P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -622,7 +735,7 @@ walk_kernel(WalkParams<T> P)
                 for (int64_t base = 0; base < P.n_part; base += 0x40000000) {
                     int64_t rem = P.n_part - base;
                     int c = (int)(rem < 0x40000000 ? rem : 0x40000000);
-                    append_ranges<KIND, T, R, AO, false>(C, lane == 0 ? c : 0, (int)base, nn, P.leaf0,
+                    append_ranges<KIND, T, R, AO>(C, lane == 0 ? c : 0, (int)base, nn, P.leaf0,
                                                           P.leaf1, c_near, c_dummy);
                 }
                 C.flush_near(nn);
@@ -672,7 +785,7 @@ walk_kernel(WalkParams<T> P)
                     }
                     for (int c = 0; c < nc; ++c) stack[sp + offc + c] = Lk.x + c;
                     sp += totc;
-                    append_ranges<KIND, T, R, AO, false>(C, leaf ? (Lk.y & kCountMask) : 0, Lk.x, nn,
+                    append_ranges<KIND, T, R, AO>(C, leaf ? (Lk.y & kCountMask) : 0, Lk.x, nn,
                                                           P.leaf0, P.leaf1, c_near, c_dummy);
                     if constexpr (KIND != LENS_POINT)
                         append_big<KIND, T, R, AO>(C, valid && Lk.w > 0, v, Lk.z, Lk.w, nb, c_bigs, c_bigk);
