@@ -269,24 +269,52 @@ template <int KIND, typename T> struct WalkShared {
     int rs_off[33];
     int rs_first[32];
     int rs_end[32];
+    // Neumaier-compensated totals of each lane's rays ([component][ray][lane]):
+    // touched once per buffer flush, so they live here rather than in registers
+    T tot_s[5][kMaxRaysPerLane][32], tot_c[5][kMaxRaysPerLane][32];
 };
 
 template <int KIND, typename T, int R, bool AO> struct WalkCtx {
+    static_assert(R <= kMaxRaysPerLane, "rays per lane");
+    static constexpr int kQ = AO ? 2 : 5;  // components accumulated
     const WalkParams<T>& P;
     WalkShared<KIND, T>& S;
     T lx[R], ly[R];
     Acc5<T> part[R];
-    Comp5<T> tot[R];
     v2_t<T> H;
     vec4_t<T> box;
 
     LENS_DEV WalkCtx(const WalkParams<T>& p, WalkShared<KIND, T>& s) : P(p), S(s) {}
 
+    LENS_DEV void tot_zero()
+    {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) S.tot_s[q][r][lane] = S.tot_c[q][r][lane] = T(0);
+    }
+
+    LENS_DEV T tot_get(int r, int q) const
+    {
+        const int lane = threadIdx.x & 31;
+        return S.tot_s[q][r][lane] + S.tot_c[q][r][lane];
+    }
+
+    // Add the partial sums of the last flush to the compensated totals.
     LENS_DEV void fold()
     {
+        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            tot[r].add(part[r]);
+            const T v[5] = {part[r].a1, part[r].a2, part[r].k, part[r].g1, part[r].g2};
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                T ts = S.tot_s[q][r][lane], tc = S.tot_c[q][r][lane];
+                Comp5<T>::add1(ts, tc, v[q]);
+                S.tot_s[q][r][lane] = ts;
+                S.tot_c[q][r][lane] = tc;
+            }
             part[r].zero();
         }
     }
@@ -724,8 +752,8 @@ walk_kernel(WalkParams<T> P)
                 ridx[r] = 0;
             }
             C.part[r].zero();
-            C.tot[r].zero();
         }
+        C.tot_zero();
 
         int c_vis = 0, c_acc = 0, c_near = 0, c_bigs = 0, c_bigk = 0, c_dummy = 0;
         if (KIND >= 0 && P.n_part > 0) {
@@ -820,7 +848,7 @@ walk_kernel(WalkParams<T> P)
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
                 if (AO && q >= 2) break;
-                T val = C.tot[r].get(q);
+                T val = C.tot_get(r, q);
                 if (P.accumulate) val += P.out[q][i];
                 P.out[q][i] = val;
             }
