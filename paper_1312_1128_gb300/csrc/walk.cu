@@ -948,7 +948,7 @@ lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const
     LENS_TRY(reserve_rays(t, n, nb, s));
     Layout L = make_layout(t->ray_cap, t->batch_cap, max_slots(t));
     char* base = (char*)t->ray_scratch.ptr;
-    // pageable host copies: the driver stages them before returning
+    // pageable host copies: the CUDA driver stages them before returning
     std::vector<uint32_t> gf(nb + 1);
     uint64_t ng = 0;
     for (int64_t b = 0; b < nb; ++b) {
