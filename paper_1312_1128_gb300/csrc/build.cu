@@ -486,12 +486,23 @@ __global__ void k_bigrecords(const uint32_t* sval, int64_t nbig, const vec4_t<T>
     listed[j] = 1;
 }
 
-template <typename T> __device__ __forceinline__ T round_dn(double x);
-template <> __device__ __forceinline__ float round_dn<float>(double x) { return __double2float_rd(x); }
-template <> __device__ __forceinline__ double round_dn<double>(double x) { return x; }
-template <typename T> __device__ __forceinline__ T round_upx(double x);
-template <> __device__ __forceinline__ float round_upx<float>(double x) { return __double2float_ru(x); }
-template <> __device__ __forceinline__ double round_upx<double>(double x) { return x; }
+// Support extent of one big entry {x, y, s^2, .}, rounded outwards.
+__device__ __forceinline__ void entry_extent(const float4& q, float& x0, float& y0, float& x1, float& y1)
+{
+    const float r = __fsqrt_ru(q.z);
+    x0 = fminf(x0, __fsub_rd(q.x, r));
+    y0 = fminf(y0, __fsub_rd(q.y, r));
+    x1 = fmaxf(x1, __fadd_ru(q.x, r));
+    y1 = fmaxf(y1, __fadd_ru(q.y, r));
+}
+__device__ __forceinline__ void entry_extent(const dbl4& q, double& x0, double& y0, double& x1, double& y1)
+{
+    const double r = sqrt(q.z);
+    x0 = fmin(x0, q.x - r);
+    y0 = fmin(y0, q.y - r);
+    x1 = fmax(x1, q.x + r);
+    y1 = fmax(y1, q.y + r);
+}
 
 // Bounding box of the support squares [x - s, x + s] x [y - s, y + s] of big
 // entries [b, e): per 32-entry chunk and per node list (conservative bounds
@@ -499,15 +510,10 @@ template <> __device__ __forceinline__ double round_upx<double>(double x) { retu
 template <typename T>
 __device__ __forceinline__ vec4_t<T> support_box(const vec4_t<T>* big0, int64_t b, int64_t e)
 {
-    double x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
-    for (int64_t i = b; i < e; ++i) {
-        vec4_t<T> q = big0[i];
-        double s = sqrt((double)q.z);
-        x0 = fmin(x0, (double)q.x - s); x1 = fmax(x1, (double)q.x + s);
-        y0 = fmin(y0, (double)q.y - s); y1 = fmax(y1, (double)q.y + s);
-    }
+    T x0 = T(INFINITY), y0 = T(INFINITY), x1 = T(-INFINITY), y1 = T(-INFINITY);
+    for (int64_t i = b; i < e; ++i) entry_extent(big0[i], x0, y0, x1, y1);
     vec4_t<T> r;
-    r.x = round_dn<T>(x0); r.y = round_dn<T>(y0); r.z = round_upx<T>(x1); r.w = round_upx<T>(y1);
+    r.x = x0; r.y = y0; r.z = x1; r.w = y1;
     return r;
 }
 
@@ -522,7 +528,10 @@ __global__ void k_chunkbox(const vec4_t<T>* big0, int64_t nbig, int64_t nchunks,
 
 // One warp per node: the node's list [z, z + w) is covered by the boxes of
 // its whole 32-entry chunks plus the single entries of the partial chunks at
-// its two ends; lanes stride over both and reduce.
+// its two ends; lanes stride over both and reduce in the tree's precision
+// (chunk boxes are already rounded outwards; min and max do not round).  A
+// node without a list gets the empty box (+inf, +inf, -inf, -inf), which no
+// reader looks at.
 template <typename T>
 __global__ void k_nodebox(const int4* link, uint32_t n_nodes, const vec4_t<T>* big0,
                           const vec4_t<T>* chunk, vec4_t<T>* out)
@@ -531,38 +540,28 @@ __global__ void k_nodebox(const int4* link, uint32_t n_nodes, const vec4_t<T>* b
     int lane = threadIdx.x & 31;
     if (v >= n_nodes) return;
     int4 L = link[v];
-    int64_t z = L.z, e = (int64_t)L.z + L.w;
-    int64_t c0 = (z + 31) >> 5, c1 = e >> 5;  // whole chunks [c0, c1)
-    double x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
-    if (c0 < c1) {
+    T x0 = T(INFINITY), y0 = T(INFINITY), x1 = T(-INFINITY), y1 = T(-INFINITY);
+    if (L.w > 0) {
+        int64_t z = L.z, e = (int64_t)L.z + L.w;
+        int64_t c0 = (z + 31) >> 5, c1 = e >> 5;  // whole chunks [c0, c1)
         for (int64_t c = c0 + lane; c < c1; c += 32) {
             vec4_t<T> b = chunk[c];
-            x0 = fmin(x0, (double)b.x); y0 = fmin(y0, (double)b.y);
-            x1 = fmax(x1, (double)b.z); y1 = fmax(y1, (double)b.w);
+            x0 = fmin(x0, b.x); y0 = fmin(y0, b.y);
+            x1 = fmax(x1, b.z); y1 = fmax(y1, b.w);
         }
-    }
-    int64_t head_end = c0 < c1 ? 32 * c0 : e, tail_begin = c0 < c1 ? 32 * c1 : e;
-    for (int64_t i = z + lane; i < head_end; i += 32) {
-        vec4_t<T> q = big0[i];
-        double s = sqrt((double)q.z);
-        x0 = fmin(x0, (double)q.x - s); x1 = fmax(x1, (double)q.x + s);
-        y0 = fmin(y0, (double)q.y - s); y1 = fmax(y1, (double)q.y + s);
-    }
-    for (int64_t i = tail_begin + lane; i < e; i += 32) {
-        vec4_t<T> q = big0[i];
-        double s = sqrt((double)q.z);
-        x0 = fmin(x0, (double)q.x - s); x1 = fmax(x1, (double)q.x + s);
-        y0 = fmin(y0, (double)q.y - s); y1 = fmax(y1, (double)q.y + s);
-    }
-    for (int o = 16; o; o >>= 1) {
-        x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, o));
-        x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, o));
-        y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, o));
-        y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+        int64_t head_end = c0 < c1 ? 32 * c0 : e, tail_begin = c0 < c1 ? 32 * c1 : e;
+        for (int64_t i = z + lane; i < head_end; i += 32) entry_extent(big0[i], x0, y0, x1, y1);
+        for (int64_t i = tail_begin + lane; i < e; i += 32) entry_extent(big0[i], x0, y0, x1, y1);
+        for (int o = 16; o; o >>= 1) {
+            x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+            x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+            y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+            y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+        }
     }
     if (lane == 0) {
         vec4_t<T> r;
-        r.x = round_dn<T>(x0); r.y = round_dn<T>(y0); r.z = round_upx<T>(x1); r.w = round_upx<T>(y1);
+        r.x = x0; r.y = y0; r.z = x1; r.w = y1;
         out[v] = r;
     }
 }
