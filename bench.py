@@ -197,6 +197,7 @@ class NfwSph(Workload):
         self.rx, self.ry = torch.from_numpy(w["rx"]).to(dev), torch.from_numpy(w["ry"]).to(dev)
         self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
         self.group = 32
+        self.walk = "default"
         # pinned host buffers of the end-to-end form, allocated outside any timing
         self.h = [torch.from_numpy(w["gauss"]).pin_memory(), torch.from_numpy(w["rx"]).pin_memory(),
                   torch.from_numpy(w["ry"]).pin_memory()]
@@ -206,11 +207,12 @@ class NfwSph(Workload):
     def tune(self):
         lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta)
         self.group = lens.autotune(self.rx, self.ry)
+        self.walk = lens.info()["walk"]
         lens.close()
 
     def step(self, flags):
         lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta,
-                           group_rays=self.group)
+                           group_rays=self.group, walk=self.walk)
         lens.shoot(self.rx, self.ry, flags=flags, out=self.outs)
         return lens
 
@@ -219,7 +221,8 @@ class NfwSph(Workload):
         w, L = self.w, self.L
         for d, h in zip(self.d, self.h):
             d.copy_(h, non_blocking=True)
-        lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group)
+        lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group,
+                      walk=self.walk)
         lens.shoot(self.d[1], self.d[2], out=self.outs)
         for h, o in zip(self.hout, self.outs):
             h.copy_(o, non_blocking=True)
@@ -261,12 +264,15 @@ class MixedBatches(Workload):
                            theta=self.theta)
         self.lens.reserve(self.n_rays, 256)
         self.group = 32
+        self.walk = "default"
         self.h = [torch.from_numpy(w["dx"]).pin_memory(), torch.from_numpy(w["dy"]).pin_memory()]
         self.hout = [torch.empty(self.n_rays, dtype=torch.float32).pin_memory() for _ in range(5)]
 
     graph = True  # timed by the caller's events (a replayed graph records no internal events)
 
     def tune(self):
+        # the library's defaults: lens_autotune times one batch, which does
+        # not represent 256 uneven batches in one launch
         pass
 
     def step(self, flags):
@@ -326,6 +332,7 @@ class Microlensing(Workload):
         self.dx, self.dy = torch.from_numpy(w["dx"]).to(dev), torch.from_numpy(w["dy"]).to(dev)
         self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
         self.group = 32
+        self.walk = "default"
         self.h = [torch.from_numpy(w["points"]).pin_memory(), torch.from_numpy(w["dx"]).pin_memory(),
                   torch.from_numpy(w["dy"]).pin_memory()]
         self.d = [torch.empty_like(x, device=dev) for x in self.h]
@@ -335,12 +342,13 @@ class Microlensing(Workload):
         lens = self.L.Lens([self.L.Species.points(self.sp)], [self.L.Halo.sis(0.0, 0.0, self.w["sis_re"])],
                            theta=self.theta)
         self.group = lens.autotune(self.dx, self.dy, origin=self.w["origin"])
+        self.walk = lens.info()["walk"]
         lens.close()
 
     def step(self, flags):
         L = self.L
         lens = L.Lens([L.Species.points(self.sp)], [L.Halo.sis(0.0, 0.0, self.w["sis_re"])], theta=self.theta,
-                      group_rays=self.group)
+                      group_rays=self.group, walk=self.walk)
         lens.shoot(self.dx, self.dy, origin=self.w["origin"], flags=flags, out=self.outs)
         return lens
 
@@ -349,7 +357,7 @@ class Microlensing(Workload):
         for d, h in zip(self.d, self.h):
             d.copy_(h, non_blocking=True)
         lens = L.Lens([L.Species.points(self.d[0])], [L.Halo.sis(0.0, 0.0, w["sis_re"])], theta=self.theta,
-                      group_rays=self.group)
+                      group_rays=self.group, walk=self.walk)
         lens.shoot(self.d[1], self.d[2], origin=w["origin"], out=self.outs)
         for h, o in zip(self.hout, self.outs):
             h.copy_(o, non_blocking=True)
@@ -395,6 +403,7 @@ class Fit(Workload):
         self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
         self.grad = torch.zeros(self.parts.shape[0], 3, dtype=torch.float32, device=dev)
         self.group = 32
+        self.walk = "default"
         self.h = [torch.from_numpy(w["gauss"]).pin_memory(), torch.from_numpy(w["rx"]).pin_memory(),
                   torch.from_numpy(w["ry"]).pin_memory()]
         self.d = [torch.empty_like(x, device=dev) for x in self.h]
@@ -405,11 +414,13 @@ class Fit(Workload):
     def tune(self):
         lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta)
         self.group = lens.autotune(self.rx, self.ry)
+        self.walk = lens.info()["walk"]
         lens.close()
 
     def step(self, flags):
         L = self.L
-        lens = L.Lens([L.Species.gauss(self.parts, self.w["q"])], theta=self.theta, group_rays=self.group)
+        lens = L.Lens([L.Species.gauss(self.parts, self.w["q"])], theta=self.theta, group_rays=self.group,
+                      walk=self.walk)
         lens.shoot(self.rx, self.ry, flags=flags | L.ALPHA_ONLY, out=self.outs)
         g1 = 2 * (self.outs[0] - self.at[0])
         g2 = 2 * (self.outs[1] - self.at[1])
@@ -426,7 +437,8 @@ class Fit(Workload):
         w, L = self.w, self.L
         for d, h in zip(self.d, self.h):
             d.copy_(h, non_blocking=True)
-        lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group)
+        lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group,
+                      walk=self.walk)
         lens.shoot(self.d[1], self.d[2], flags=L.ALPHA_ONLY, out=self.outs)
         r1, r2 = self.outs[0] - self.at[0], self.outs[1] - self.at[1]
         self.grad.zero_()
@@ -546,7 +558,7 @@ def run_gpu(args, ws, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
-            "config": wl.config(ws), "tuning": {"group_rays": wl.group},
+            "config": wl.config(ws), "tuning": {"group_rays": wl.group, "walk": wl.walk},
             "e2e": {"value": ws * n_rays / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

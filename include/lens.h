@@ -117,8 +117,16 @@ typedef struct lens_params {
     int32_t leaf_max;    /* a box holding fewer than leaf_max particles is a leaf (>= 1; paper: 5)  */
     int32_t precision;   /* LENS_PREC_FP32 or LENS_PREC_FP64                                          */
     int32_t group_rays;  /* rays sharing one interaction list: 0 = autotuned/default, else 32 or 64   */
-    int32_t reserved;    /* must be 0 */
+    int32_t walk;        /* LENS_WALK_*: how warps share a group's walk (0 = default, autotuned)      */
 } lens_params;
+
+/* lens_params.walk.  LENS_WALK_WARP: one warp walks the tree for its group
+ * and evaluates every full buffer itself.  LENS_WALK_PAIRS: a producer warp
+ * walks and fills shared-memory buffers that a consumer warp, holding the
+ * group's rays, evaluates (the latency-bound walk overlaps the arithmetic).
+ * Same results up to the order of summation.  LENS_WALK_DEFAULT = WARP until
+ * lens_autotune picks one. */
+enum { LENS_WALK_DEFAULT = 0, LENS_WALK_WARP = 1, LENS_WALK_PAIRS = 2 };
 
 typedef struct lens_tree lens_tree;  /* opaque, library-owned */
 
@@ -135,6 +143,8 @@ typedef struct lens_tree_info {
     double root[8][3];        /* root box centre x, y and half side */
     double build_ms[8][4];    /* host wall time of the build phases: sort + topology
                                  count, node layout, moments + big lists, finish */
+    int32_t group_rays;       /* current ray-group size (32 or 64) */
+    int32_t walk;             /* current walk form: LENS_WALK_WARP or LENS_WALK_PAIRS */
 } lens_tree_info;
 
 /*
@@ -221,10 +231,13 @@ lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double or
 
 /*
  * lens_autotune -- pick the ray-group size (rays sharing one interaction
- * list: 32 or 64) for this tree by timing the walk on the given rays (at most
- * the first 8,388,608; same arguments as lens_shoot_rays) with CUDA events,
- * and keep the faster one for later calls.  *group_rays receives the choice.
- * Synchronous; allocates temporary outputs on the device.
+ * list: 32 or 64) and, unless the tree was built with a fixed
+ * lens_params.walk, the walk form (LENS_WALK_WARP or LENS_WALK_PAIRS) for
+ * this tree by timing the walk on the given rays (at most the first
+ * 8,388,608; same arguments as lens_shoot_rays) with CUDA events, and keep
+ * the fastest for later calls.  *group_rays receives the group size;
+ * lens_tree_get_info reports both.  Synchronous; allocates temporary outputs
+ * on the device.
  */
 lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, const void* ray_dx,
                           const void* ray_dy, int32_t ray_dtype, int64_t n, void* stream,

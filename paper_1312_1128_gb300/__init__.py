@@ -30,6 +30,7 @@ POINT, GAUSS, NFW, SIS, DISK = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 PREC_FP32, PREC_FP64 = 0, 1
 ALPHA_ONLY, DIRECT, ACCUMULATE, USE_GRAPH, COUNT, TIMING = 1, 2, 4, 8, 16, 32
+WALK_DEFAULT, WALK_WARP, WALK_PAIRS = 0, 1, 2
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "liblens.so")
@@ -56,7 +57,7 @@ class _Halo(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("leaf_max", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("group_rays", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("walk", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -64,7 +65,8 @@ class _Info(ctypes.Structure):
                 ("n_halos", ctypes.c_int64), ("n_particles", ctypes.c_int64 * 8),
                 ("n_nodes", ctypes.c_int64 * 8), ("n_leaves", ctypes.c_int64 * 8),
                 ("n_big", ctypes.c_int64 * 8), ("depth", ctypes.c_int32 * 8),
-                ("root", (ctypes.c_double * 3) * 8), ("build_ms", (ctypes.c_double * 4) * 8)]
+                ("root", (ctypes.c_double * 3) * 8), ("build_ms", (ctypes.c_double * 4) * 8),
+                ("group_rays", ctypes.c_int32), ("walk", ctypes.c_int32)]
 
 
 def lib():
@@ -189,7 +191,7 @@ class Lens:
     """A built lens: one quadtree per species plus analytic halos."""
 
     def __init__(self, species=(), halos=(), theta: float = 0.1, leaf_max: int = 5,
-                 precision: str = "fp32", group_rays: int = 0, stream=None):
+                 precision: str = "fp32", group_rays: int = 0, walk: str = "default", stream=None):
         L = lib()
         self._keep = []
         sp = (_Species * max(1, len(species)))()
@@ -207,7 +209,8 @@ class Lens:
         for i, h in enumerate(halos):
             hs[i] = _Halo(h.kind, 0, h.x, h.y, h.m, h.p0, h.p1)
         prec = {"fp32": PREC_FP32, "fp64": PREC_FP64}[precision]
-        params = _Params(float(theta), int(leaf_max), prec, int(group_rays), 0)
+        wk = {"default": WALK_DEFAULT, "warp": WALK_WARP, "pairs": WALK_PAIRS}[walk]
+        params = _Params(float(theta), int(leaf_max), prec, int(group_rays), wk)
         h = ctypes.c_void_p()
         _check(L.lens_build_tree(sp, len(species), hs, len(halos), ctypes.byref(params),
                                  _stream_ptr(stream), ctypes.byref(h)))
@@ -233,7 +236,8 @@ class Lens:
                     n_particles=list(inf.n_particles[:k]), n_nodes=list(inf.n_nodes[:k]),
                     n_leaves=list(inf.n_leaves[:k]), n_big=list(inf.n_big[:k]),
                     depth=list(inf.depth[:k]), root=[tuple(inf.root[i]) for i in range(k)],
-                    build_ms=[tuple(inf.build_ms[i]) for i in range(k)])
+                    build_ms=[tuple(inf.build_ms[i]) for i in range(k)], group_rays=inf.group_rays,
+                    walk={WALK_WARP: "warp", WALK_PAIRS: "pairs"}.get(inf.walk, "default"))
 
     def export(self, species: int = 0):
         """Host copies of one species' tree: nodes (n_nodes, 8), links

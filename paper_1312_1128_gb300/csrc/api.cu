@@ -151,7 +151,8 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
         return lens_set_error(LENS_ERR_INVALID_ARG, "unknown precision %d", params->precision);
     if (params->group_rays != 0 && params->group_rays != 32 && params->group_rays != 64)
         return lens_set_error(LENS_ERR_INVALID_ARG, "group_rays must be 0, 32 or 64");
-    if (params->reserved != 0) return lens_set_error(LENS_ERR_INVALID_ARG, "reserved must be 0");
+    if (params->walk < LENS_WALK_DEFAULT || params->walk > LENS_WALK_PAIRS)
+        return lens_set_error(LENS_ERR_INVALID_ARG, "walk must be LENS_WALK_DEFAULT, _WARP or _PAIRS");
     for (int i = 0; i < n_species; ++i) {
         const lens_species& s = species[i];
         if (s.kind != LENS_POINT && s.kind != LENS_GAUSS && s.kind != LENS_NFW)
@@ -172,6 +173,8 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
     t->theta = params->theta;
     t->leaf_max = params->leaf_max;
     t->group_rays = params->group_rays == 0 ? 32 : params->group_rays;
+    t->walk_mode = params->walk == LENS_WALK_DEFAULT ? LENS_WALK_WARP : params->walk;
+    t->walk_fixed = params->walk != LENS_WALK_DEFAULT;
     cudaStream_t s = (cudaStream_t)stream;
     auto fail = [&](lens_status st) {
         lens_free_tree(t);
@@ -326,13 +329,18 @@ lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, con
     for (int q = 0; q < 5; ++q) out[q] = (char*)buf + q * m * es;
     int64_t off[2] = {0, m};
     double orig[2] = {origin_x, origin_y};
-    const int cand[2] = {32, 64};
+    // candidates: group size x walk form (the walk only if the caller left it open)
+    const int cand_g[4] = {32, 64, 32, 64};
+    const int cand_w[4] = {LENS_WALK_WARP, LENS_WALK_WARP, LENS_WALK_PAIRS, LENS_WALK_PAIRS};
     double best = 1e300;
-    int best_g = tree->group_rays;
+    int best_g = tree->group_rays, best_w = tree->walk_mode;
+    const int user_w = tree->walk_mode;
     lens_status st = LENS_OK;
-    for (int c = 0; c < 2 && st == LENS_OK; ++c) {
-        if (tree->precision == LENS_PREC_FP64 && cand[c] != 32) continue;
-        tree->group_rays = cand[c];
+    for (int c = 0; c < 4 && st == LENS_OK; ++c) {
+        if (tree->precision == LENS_PREC_FP64 && cand_g[c] != 32) continue;
+        if (tree->walk_fixed && cand_w[c] != user_w) continue;
+        tree->group_rays = cand_g[c];
+        tree->walk_mode = cand_w[c];
         double ms = 0;
         for (int rep = 0; rep < 2 && st == LENS_OK; ++rep) {  // first run warms up
             st = shoot(tree, 1, off, orig, ray_dx, ray_dy, ray_dtype, out, LENS_TIMING, s);
@@ -343,11 +351,13 @@ lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, con
         }
         if (st == LENS_OK && ms < best) {
             best = ms;
-            best_g = cand[c];
+            best_g = cand_g[c];
+            best_w = cand_w[c];
         }
     }
     cudaFreeAsync(buf, s);
     tree->group_rays = best_g;
+    tree->walk_mode = best_w;
     *group_rays = best_g;
     return st;
 }
@@ -371,6 +381,8 @@ lens_status lens_sync_status(lens_tree* tree, void* stream)
     if (herr) {
         LENS_CUDA(cudaMemset(tree->d_err, 0, sizeof(uint32_t)));
         if (herr & DERR_BAD_INPUT) return lens_set_error(LENS_ERR_INVALID_ARG, "bad input found on the device");
+        if (herr & DERR_WAIT_TIMEOUT)
+            return lens_set_error(LENS_ERR_INTERNAL, "a hand-over wait between walk warps timed out (code %u)", herr);
         return lens_set_error(LENS_ERR_INTERNAL, "device check failed (code %u)", herr);
     }
     return LENS_OK;
@@ -420,6 +432,8 @@ lens_status lens_tree_get_info(const lens_tree* t, lens_tree_info* info)
         info->root[i][2] = s.root_half;
         for (int k = 0; k < 4; ++k) info->build_ms[i][k] = s.phase_ms[k];
     }
+    info->group_rays = t->group_rays;
+    info->walk = t->walk_mode;
     return LENS_OK;
 }
 

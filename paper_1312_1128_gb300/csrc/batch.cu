@@ -15,6 +15,7 @@ struct GraphEntry {
     uint64_t ng;
     const void *dx, *dy;
     int dtype, flags;
+    int group_rays, walk;  // the tree's settings when captured
     void* out[5];
     void* scratch;
     int64_t kernels;  // kernel nodes in the graph, added to the launch counter per replay
@@ -53,7 +54,8 @@ lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, co
     LENS_TRY(upload_batches(t, nb, off, orig, s, &plan));
     for (GraphEntry* g : t->graphs) {
         bool same = g->n == plan.n && g->nb == plan.nb && g->ng == plan.ng && g->dx == dx && g->dy == dy &&
-                    g->dtype == dtype && g->flags == flags && g->scratch == t->ray_scratch.ptr;
+                    g->dtype == dtype && g->flags == flags && g->scratch == t->ray_scratch.ptr &&
+                    g->group_rays == t->group_rays && g->walk == t->walk_mode;
         for (int q = 0; q < 5 && same; ++q) same = g->out[q] == out[q];
         if (same) {
             LENS_CUDA(cudaGraphLaunch(g->exec, s));
@@ -86,7 +88,8 @@ lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, co
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return lens_cuda_check(e, "cudaGraphInstantiate");
-    GraphEntry* g = new GraphEntry{plan.n, plan.nb, plan.ng, dx, dy, dtype, flags, {}, t->ray_scratch.ptr, kernels, exec};
+    GraphEntry* g = new GraphEntry{plan.n, plan.nb, plan.ng, dx, dy, dtype, flags, t->group_rays, t->walk_mode, {},
+                                  t->ray_scratch.ptr, kernels, exec};
     for (int q = 0; q < 5; ++q) g->out[q] = out[q];
     t->graphs.push_back(g);
     return LENS_OK;

@@ -14,7 +14,8 @@ enum : uint32_t {
     DERR_STACK_OVERFLOW = 1u,   // walk stack capacity exceeded (cannot happen by construction)
     DERR_BAD_INPUT = 2u,        // negative / non-finite mass or size in the input
     DERR_INDEX = 4u,            // an index check in a kernel failed
-    DERR_BUFFER = 8u            // an interaction buffer check failed
+    DERR_BUFFER = 8u,           // an interaction buffer check failed
+    DERR_WAIT_TIMEOUT = 16u     // a bounded wait between cooperating warps gave up
 };
 
 // Morton keys: 24 levels of 2 bits below the root.

@@ -67,6 +67,8 @@ struct lens_tree {
     double theta = 0.1;
     int leaf_max = 5;
     int group_rays = 32;
+    int walk_mode = LENS_WALK_WARP;
+    bool walk_fixed = false;  // chosen by the caller at build time (not autotuned)
     std::vector<lens::SpeciesTree> sp;
     std::vector<lens_halo> halos_host;
     lens::HaloDev* halos = nullptr;  // device copy

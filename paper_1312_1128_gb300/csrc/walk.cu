@@ -28,6 +28,7 @@
 #include "profiles.cuh"
 #include "sort.cuh"
 #include "walk_shared.cuh"
+#include "walk_dev.cuh"
 
 namespace lens {
 
@@ -222,500 +223,6 @@ __global__ void k_groups(int64_t n_groups, const int64_t* boff, const uint32_t* 
 
 // ---------------------------------------------------------------- walk
 
-template <typename T> struct WalkParams {
-    const vec4_t<T>* nodeA;
-    const v2_t<T>* nodeB;
-    const int4* link;
-    const vec4_t<T>* leaf0;   // near records (listed particles marked)
-    const vec4_t<T>* leaf1;   // NFW second record
-    const vec4_t<T>* big0;       // {x, y, s^2, r0^2}
-    const vec4_t<T>* big1;       // {m, c | A, B, 0}
-    const vec4_t<T>* big_chunk;  // support bounding box per 32 entries
-    const vec4_t<T>* node_bigbox;
-    int64_t n_part;
-    T Uq, invNq, Uq2, Nq, eU;
-    const v2_t<T>* gH;
-    const vec4_t<T>* gbox;
-    const uint2* grange;
-    const v2_t<T>* ray_l;
-    const uint32_t* ray_idx;
-    int64_t n_groups;
-    const HaloDev* halos;
-    int n_halos;
-    T* out[5];
-    int accumulate;
-    uint32_t* counter;
-    int* stack;
-    uint32_t* err;
-    unsigned long long* stats;  // optional walk counters
-};
-
-template <int KIND, typename T> struct WalkShared {
-    // FP32 Gaussian big entries are stored one array per field, so that two
-    // consecutive entries load as one float2 operand of the packed form
-    static constexpr bool kPackedBig = KIND == LENS_GAUSS && sizeof(T) == 4;
-    static constexpr int kB = kPackedBig ? kBigCap : 1;
-    T fdx[kFarCap], fdy[kFarCap], fM[kFarCap], fqr[kFarCap], fqi[kFarCap];
-    vec4_t<T> n0[kNearCap];
-    vec4_t<T> n1[KIND == LENS_NFW ? kNearCap : 1];
-    vec4_t<T> b0[KIND == LENS_POINT || kPackedBig ? 1 : kBigCap];
-    vec4_t<T> b1[KIND == LENS_POINT || kPackedBig ? 1 : kBigCap];
-    // -x, -y (from the group anchor), -c log2 e, m/N_q, -(m/N_q) e^-q^2/2,
-    // m c/N_q, the flag or 1/r0^2 (b0.w of the generic layout) and 1/c.
-    // Entries whose support contains every ray of the group fill slots
-    // [0, n_in) from the bottom; the others fill [kBigCap - n_out, kBigCap)
-    // from the top (the buffer count packs n_in | n_out << 16).
-    float bnx[kB], bny[kB], bcl[kB], bm[kB], bme[kB], bk[kB], bw[kB], bic[kB];
-    int rs_off[33];
-    int rs_first[32];
-    int rs_end[32];
-    // Neumaier-compensated totals of each lane's rays ([component][ray][lane]):
-    // touched once per buffer flush, so they live here rather than in registers
-    T tot_s[5][kMaxRaysPerLane][32], tot_c[5][kMaxRaysPerLane][32];
-};
-
-template <int KIND, typename T, int R, bool AO> struct WalkCtx {
-    static_assert(R <= kMaxRaysPerLane, "rays per lane");
-    static constexpr int kQ = AO ? 2 : 5;  // components accumulated
-    const WalkParams<T>& P;
-    WalkShared<KIND, T>& S;
-    T lx[R], ly[R];
-    Acc5<T> part[R];
-    v2_t<T> H;
-    vec4_t<T> box;
-
-    LENS_DEV WalkCtx(const WalkParams<T>& p, WalkShared<KIND, T>& s) : P(p), S(s) {}
-
-    LENS_DEV void tot_zero()
-    {
-        const int lane = threadIdx.x & 31;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int q = 0; q < kQ; ++q) S.tot_s[q][r][lane] = S.tot_c[q][r][lane] = T(0);
-    }
-
-    LENS_DEV T tot_get(int r, int q) const
-    {
-        const int lane = threadIdx.x & 31;
-        return S.tot_s[q][r][lane] + S.tot_c[q][r][lane];
-    }
-
-    // Add the partial sums of the last flush to the compensated totals.
-    LENS_DEV void fold()
-    {
-        const int lane = threadIdx.x & 31;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const T v[5] = {part[r].a1, part[r].a2, part[r].k, part[r].g1, part[r].g2};
-#pragma unroll
-            for (int q = 0; q < kQ; ++q) {
-                T ts = S.tot_s[q][r][lane], tc = S.tot_c[q][r][lane];
-                Comp5<T>::add1(ts, tc, v[q]);
-                S.tot_s[q][r][lane] = ts;
-                S.tot_c[q][r][lane] = tc;
-            }
-            part[r].zero();
-        }
-    }
-
-    LENS_DEV void flush_far(int nf)
-    {
-        for (int c = 0; c < nf; ++c) {
-            T dx = S.fdx[c], dy = S.fdy[c], M = S.fM[c], qr = S.fqr[c], qi = S.fqi[c];
-#pragma unroll
-            for (int r = 0; r < R; ++r) cell_terms<T, AO>(part[r], lx[r] - dx, ly[r] - dy, M, qr, qi);
-        }
-        fold();
-    }
-
-    // Leaf particles: full profile unless marked as a listed (softened) point.
-    LENS_DEV void flush_near(int nn)
-    {
-        for (int i = 0; i < nn; ++i) {
-            vec4_t<T> q = S.n0[i];
-            vec4_t<T> q1;
-            if constexpr (KIND == LENS_NFW) q1 = S.n1[i];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                T wx = lx[r] - q.x, wy = ly[r] - q.y;
-                T r2 = fma(wx, wx, wy * wy);
-                T kb, kap = T(0), Dp;
-                if (KIND == LENS_POINT) {
-                    point_terms(q.z, r2, kb, Dp);
-                } else if (KIND == LENS_GAUSS) {
-                    if (q.w > T(0)) gauss_terms(q.z, q.w, r2, P.Uq, P.invNq, kb, kap, Dp);
-                    else point_terms(q.z, fmax(r2, -q.w), kb, Dp);
-                } else {
-                    if (q.w > T(0)) nfw_terms(q.z, q.w, q1.x, q1.y, r2, kb, kap, Dp);
-                    else point_terms(q.z, fmax(r2, -q.w), kb, Dp);
-                }
-                part[r].template radial<AO>(wx, wy, kb, kap, Dp);
-            }
-        }
-        fold();
-    }
-
-    // Big-list corrections: (full profile - softened point); zero outside the
-    // support, where both are the same point mass.
-    // b0 = {x - H.x, y - H.y, s^2, 1/r0^2}; b1 = {m/N_q, c log2 e, m c / N_q,
-    // 1/c} (GAUSS) or {m, A, B, 0} (NFW).  1/max(r^2, r0^2) = min(1/r^2, 1/r0^2).
-    // Two entries per iteration for instruction-level parallelism.
-    // One packed-layout entry for every ray, in scalar arithmetic (entries
-    // with a ray inside the softening radius, and unpaired entries).
-    LENS_DEV void big_entry_scalar(int i, Acc5x2 (&pa)[R])
-    {
-        const float nx = S.bnx[i], ny = S.bny[i], w = S.bw[i];
-        const float4 q = make_float4(0.0f, 0.0f, 0.0f, w);
-        const float4 q1 = make_float4(S.bm[i], -S.bcl[i], S.bk[i], S.bic[i]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            Acc5<float> a;
-            a.zero();
-            if (w < 0.0f) gauss_correction_fast<AO>(a, lx[r] + nx, ly[r] + ny, q1, P.Uq2, P.eU);
-            else gauss_correction<AO>(a, lx[r] + nx, ly[r] + ny, q, q1, P.Uq2, P.Nq);
-            pa[r].na1.x -= a.a1;
-            pa[r].na2.x -= a.a2;
-            if (!AO) {
-                pa[r].k.x += a.k;
-                pa[r].g1p.x += a.g1;
-                pa[r].hg2.x = fmaf(0.5f, a.g2, pa[r].hg2.x);
-            }
-        }
-    }
-
-    template <bool EDGE>
-    LENS_DEV void big_pair_packed(int i, Acc5x2 (&pa)[R], const float2 (&LX)[R], const float2 (&LY)[R])
-    {
-        const float2 nx = *reinterpret_cast<const float2*>(&S.bnx[i]);
-        const float2 ny = *reinterpret_cast<const float2*>(&S.bny[i]);
-        const float2 cl = *reinterpret_cast<const float2*>(&S.bcl[i]);
-        const float2 mN = *reinterpret_cast<const float2*>(&S.bm[i]);
-        const float2 nmE = *reinterpret_cast<const float2*>(&S.bme[i]);
-        const float2 kz = *reinterpret_cast<const float2*>(&S.bk[i]);
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-            gauss_correction_x2<AO, EDGE>(pa[r], LX[r], LY[r], nx, ny, cl, mN, nmE, kz, -P.Uq2);
-    }
-
-    // FP32 Gaussian big buffer in packed arithmetic: the whole-group-inside
-    // region four entries at a time without tests, then the other region
-    // pair by pair (packed closed form with the support edge, or scalar where
-    // a ray may be inside the softening radius).
-    LENS_DEV void flush_big_packed(int nbuf)
-    {
-        const int n_in = nbuf & 0xffff, n_out = nbuf >> 16;
-        Acc5x2 pa[R];
-        float2 LX[R], LY[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            pa[r].zero();
-            LX[r] = make_float2(lx[r], lx[r]);
-            LY[r] = make_float2(ly[r], ly[r]);
-        }
-        int i = 0;
-        for (; i + 3 < n_in; i += 4) {
-            big_pair_packed<false>(i, pa, LX, LY);
-            big_pair_packed<false>(i + 2, pa, LX, LY);
-        }
-        if (i + 1 < n_in) {
-            big_pair_packed<false>(i, pa, LX, LY);
-            i += 2;
-        }
-        if (i < n_in) big_entry_scalar(i, pa);
-        i = kBigCap - n_out;
-        if ((i & 1) && i < kBigCap) big_entry_scalar(i++, pa);
-        for (; i + 1 < kBigCap; i += 2) {
-            const float2 w = *reinterpret_cast<const float2*>(&S.bw[i]);
-            if (w.x < 0.0f && w.y < 0.0f) {
-                big_pair_packed<true>(i, pa, LX, LY);
-            } else {
-                big_entry_scalar(i, pa);
-                big_entry_scalar(i + 1, pa);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            part[r].a1 -= pa[r].na1.x + pa[r].na1.y;
-            part[r].a2 -= pa[r].na2.x + pa[r].na2.y;
-            if (!AO) {
-                part[r].k += pa[r].k.x + pa[r].k.y;
-                part[r].g1 += (pa[r].g1p.x + pa[r].g1p.y) - 2.0f * (pa[r].g1y.x + pa[r].g1y.y);
-                part[r].g2 += 2.0f * (pa[r].hg2.x + pa[r].hg2.y);
-            }
-        }
-        fold();
-    }
-
-    LENS_DEV void flush_big(int nb)
-    {
-        if constexpr (WalkShared<KIND, T>::kPackedBig) {
-            flush_big_packed(nb);
-            return;
-        }
-        int i = 0;
-        if constexpr (KIND == LENS_GAUSS) {
-            // b0.w < 0 marks an entry whose softening radius no ray of the
-            // group reaches (the common case); b0.w = -2 also that its
-            // support contains every ray of the group
-            for (; i + 1 < nb; i += 2) {
-                vec4_t<T> q = S.b0[i], q1 = S.b1[i], p = S.b0[i + 1], p1 = S.b1[i + 1];
-                if (q.w < T(-1.5) && p.w < T(-1.5)) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        gauss_correction_inside<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1, P.eU);
-                        gauss_correction_inside<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p1, P.eU);
-                    }
-                } else if (q.w < T(0) && p.w < T(0)) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        gauss_correction_fast<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1, P.Uq2, P.eU);
-                        gauss_correction_fast<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p1, P.Uq2, P.eU);
-                    }
-                } else {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if (q.w < T(0)) gauss_correction_fast<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q1, P.Uq2, P.eU);
-                        else gauss_correction<AO>(part[r], lx[r] - q.x, ly[r] - q.y, q, q1, P.Uq2, P.Nq);
-                        if (p.w < T(0)) gauss_correction_fast<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p1, P.Uq2, P.eU);
-                        else gauss_correction<AO>(part[r], lx[r] - p.x, ly[r] - p.y, p, p1, P.Uq2, P.Nq);
-                    }
-                }
-            }
-        }
-        for (; i < nb; ++i) {
-            vec4_t<T> q = S.b0[i], q1 = S.b1[i];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                T wx = lx[r] - q.x, wy = ly[r] - q.y;
-                if constexpr (KIND == LENS_GAUSS) {
-                    if (q.w < T(0)) gauss_correction_fast<AO>(part[r], wx, wy, q1, P.Uq2, P.eU);
-                    else gauss_correction<AO>(part[r], wx, wy, q, q1, P.Uq2, P.Nq);
-                } else {
-                    T r2 = fma(wx, wx, wy * wy);
-                    T inv = r2 > T(0) ? rcp(r2) : T(0);
-                    T inv_s = fmin(inv, q.w);
-                    T kbp = q1.x * inv_s;
-                    T kb, kap, Dp;
-                    nfw_terms(q1.x, q.z, q1.y, q1.z, r2, kb, kap, Dp);
-                    part[r].template radial<AO>(wx, wy, kb - kbp, kap, Dp - kbp * inv_s);
-                }
-            }
-        }
-        fold();
-    }
-
-    // Analytic components for every ray (Sec. 3.2 analytic models, App. B).
-    LENS_DEV void halos()
-    {
-        for (int h = 0; h < P.n_halos; ++h) {
-            const HaloDev& hd = P.halos[h];
-            T hx = (T)((double)H.x - hd.x), hy = (T)((double)H.y - hd.y);
-            int kind = hd.kind;
-            T m = (T)hd.m;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                T wx = lx[r] + hx, wy = ly[r] + hy;
-                T r2 = fma(wx, wx, wy * wy);
-                T kb = T(0), kap = T(0), Dp = T(0);
-                if (kind == LENS_POINT) {
-                    point_terms(m, r2, kb, Dp);
-                } else if (kind == LENS_GAUSS) {
-                    gauss_terms(m, (T)hd.c0, r2, (T)hd.c1, (T)hd.c2, kb, kap, Dp);
-                } else if (kind == LENS_NFW) {
-                    nfw_terms(m, (T)hd.c2, (T)hd.c0, (T)hd.c1, r2, kb, kap, Dp);
-                } else if (kind == LENS_SIS) {
-                    if (r2 > T(0)) {
-                        T rr = sqrt(r2), re = (T)hd.p0;
-                        kb = re / rr;
-                        kap = T(0.5) * kb;
-                        Dp = kap / r2;
-                    }
-                } else {  // uniform disk
-                    T R2 = (T)hd.c2;
-                    if (r2 < R2) {
-                        kb = m / R2;
-                        kap = kb;
-                        Dp = T(0);
-                    } else {
-                        point_terms(m, r2, kb, Dp);
-                    }
-                }
-                part[r].template radial<AO>(wx, wy, kb, kap, Dp);
-            }
-        }
-        fold();
-    }
-};
-
-// Append, in order, the leaf particles of up to 32 index ranges (one per
-// lane) to the near buffer, flushing it whenever fewer than 32 slots remain.
-template <int KIND, typename T, int R, bool AO>
-LENS_DEV void append_ranges(WalkCtx<KIND, T, R, AO>& C, int cnt, int first, int& nbuf,
-                            const vec4_t<T>* src0, const vec4_t<T>* src1, int& n_seen, int& n_kept)
-{
-    const unsigned full = 0xffffffffu;
-    int lane = threadIdx.x & 31;
-    int tot;
-    int off = warp_exclusive_scan(cnt, &tot);
-    if (tot == 0) return;
-    n_seen += tot;
-    WalkShared<KIND, T>& S = C.S;
-    S.rs_off[lane] = off;
-    S.rs_first[lane] = first;
-    if (lane == 31) S.rs_off[32] = tot;
-    __syncwarp();
-    for (int base = 0; base < tot; base += 32) {
-        if (nbuf + 32 > kNearCap) {
-            C.flush_near(nbuf);
-            nbuf = 0;
-            __syncwarp();
-        }
-        int i = base + lane;
-        bool have = i < tot;
-        vec4_t<T> q0, q1;
-        bool keep = false;
-        if (have) {
-            int lo = 0, hi = 32;  // last lane o with rs_off[o] <= i
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (S.rs_off[mid] <= i) lo = mid;
-                else hi = mid;
-            }
-            int p = S.rs_first[lo] + (i - S.rs_off[lo]);
-            q0 = src0[p];
-            if constexpr (KIND == LENS_NFW) q1 = src1[p];
-            q0.x -= C.H.x;
-            q0.y -= C.H.y;
-            keep = true;
-        }
-        unsigned ball = __ballot_sync(full, keep);
-        if (keep) {
-            int slot = nbuf + __popc(ball & ((1u << lane) - 1u));
-            S.n0[slot] = q0;
-            if constexpr (KIND == LENS_NFW) S.n1[slot] = q1;
-        }
-        nbuf += __popc(ball);
-        n_kept += __popc(ball);
-        __syncwarp();
-    }
-}
-
-// Slots in use in the big buffer (the packed layout counts both regions).
-template <int KIND, typename T> LENS_DEV int big_used(int nbuf)
-{
-    if constexpr (WalkShared<KIND, T>::kPackedBig) return (nbuf & 0xffff) + (nbuf >> 16);
-    else return nbuf;
-}
-
-// Big lists of the visited boxes (one list per lane: entries [z, z + w) of
-// the big arrays).  A list whose support box misses the group is skipped;
-// otherwise its 32-entry chunks are tested by their support boxes and the
-// entries of the chunks that pass are tested one by one; entries whose
-// support reaches the group's box are appended to the big buffer.
-template <int KIND, typename T, int R, bool AO>
-LENS_DEV void append_big(WalkCtx<KIND, T, R, AO>& C, bool has, int v, int z, int w, int& nbuf,
-                         int& n_seen, int& n_kept)
-{
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const WalkParams<T>& P = C.P;
-    WalkShared<KIND, T>& S = C.S;
-    int cnt = 0;
-    if (has) {
-        vec4_t<T> nb4 = P.node_bigbox[v];
-        if (box_reaches_group<T>(nb4, C.H, C.box)) cnt = ((z + w - 1) >> 5) - (z >> 5) + 1;
-    }
-    int tot;
-    int off = warp_exclusive_scan(cnt, &tot);
-    if (tot == 0) return;
-    S.rs_off[lane] = off;
-    S.rs_first[lane] = z;
-    S.rs_end[lane] = z + w;
-    if (lane == 31) S.rs_off[32] = tot;
-    __syncwarp();
-    for (int base = 0; base < tot; base += 32) {
-        int i = base + lane;
-        int cid = -1, own = 0;
-        bool pass = false;
-        if (i < tot) {
-            int lo = 0, hi = 32;
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (S.rs_off[mid] <= i) lo = mid;
-                else hi = mid;
-            }
-            own = lo;
-            cid = (S.rs_first[lo] >> 5) + (i - S.rs_off[lo]);
-            pass = box_reaches_group<T>(P.big_chunk[cid], C.H, C.box);
-        }
-        unsigned ball = __ballot_sync(full, pass);
-        while (ball) {
-            int src = __ffs(ball) - 1;
-            ball &= ball - 1;
-            int c = __shfl_sync(full, cid, src);
-            int o = __shfl_sync(full, own, src);
-            if (big_used<KIND, T>(nbuf) + 32 > kBigCap) {
-                C.flush_big(nbuf);
-                nbuf = 0;
-                __syncwarp();
-            }
-            int e = 32 * c + lane;
-            bool keep = false;
-            vec4_t<T> q0, q1;
-            bool inr = e >= S.rs_first[o] && e < S.rs_end[o];
-            n_seen += __popc(__ballot_sync(full, inr));
-            if (inr) {
-                q0 = P.big0[e];
-                q0.x -= C.H.x;
-                q0.y -= C.H.y;
-                T ex = fmax(fabs(q0.x - C.box.x) - C.box.z, T(0));
-                T ey = fmax(fabs(q0.y - C.box.y) - C.box.w, T(0));
-                T near2 = fma(ex, ex, ey * ey);
-                keep = near2 < q0.z;
-                if constexpr (KIND == LENS_GAUSS) {
-                    // every ray of the group beyond the softening radius?  and
-                    // all inside the support?
-                    if (keep && near2 > T(0) && near2 * q0.w >= T(1.000001)) {
-                        T fx = fabs(q0.x - C.box.x) + C.box.z, fy = fabs(q0.y - C.box.y) + C.box.w;
-                        T far2 = fma(fx, fx, fy * fy) * T(1.000001);
-                        q0.w = far2 < q0.z ? T(-2) : T(-1);
-                    }
-                }
-            }
-            unsigned kb = __ballot_sync(full, keep);
-            if constexpr (WalkShared<KIND, T>::kPackedBig) {
-                const bool in = keep && q0.w < T(-1.5);
-                const unsigned bi = __ballot_sync(full, in), lt = (1u << lane) - 1u;
-                if (keep) {
-                    q1 = P.big1[e];
-                    int slot = in ? (nbuf & 0xffff) + __popc(bi & lt)
-                                  : kBigCap - 1 - ((nbuf >> 16) + __popc(kb & ~bi & lt));
-                    S.bnx[slot] = -q0.x;
-                    S.bny[slot] = -q0.y;
-                    S.bcl[slot] = -q1.y;
-                    S.bm[slot] = q1.x;
-                    S.bme[slot] = -q1.x * P.eU;
-                    S.bk[slot] = q1.z;
-                    S.bw[slot] = q0.w;
-                    S.bic[slot] = q1.w;
-                }
-                nbuf += __popc(bi) + (__popc(kb & ~bi) << 16);
-            } else {
-                if (keep) {
-                    q1 = P.big1[e];
-                    int slot = nbuf + __popc(kb & ((1u << lane) - 1u));
-                    S.b0[slot] = q0;
-                    S.b1[slot] = q1;
-                }
-                nbuf += __popc(kb);
-            }
-            n_kept += __popc(kb);
-            __syncwarp();
-        }
-    }
-}
-
 template <int KIND, typename T, int R, bool AO, bool DIRECT>
 __global__ void __launch_bounds__(kWalkWarps * 32, sizeof(T) == 4 ? (R == 2 ? 5 : 6) : 2)
 walk_kernel(WalkParams<T> P)
@@ -756,77 +263,21 @@ walk_kernel(WalkParams<T> P)
         C.tot_zero();
 
         int c_vis = 0, c_acc = 0, c_near = 0, c_bigs = 0, c_bigk = 0, c_dummy = 0;
+        C.nf = C.nn = C.nb = 0;
         if (KIND >= 0 && P.n_part > 0) {
-            int nn = 0, nb = 0;
             if (DIRECT) {
                 // every particle with its full profile
                 for (int64_t base = 0; base < P.n_part; base += 0x40000000) {
                     int64_t rem = P.n_part - base;
                     int c = (int)(rem < 0x40000000 ? rem : 0x40000000);
-                    append_ranges<KIND, T, R, AO>(C, lane == 0 ? c : 0, (int)base, nn, P.leaf0,
-                                                          P.leaf1, c_near, c_dummy);
+                    append_ranges(C, lane == 0 ? c : 0, (int)base, P.leaf0, P.leaf1, c_near, c_dummy);
                 }
-                C.flush_near(nn);
+                C.flush_near();
             } else {
-                int nf = 0, sp = 1;
-                if (lane == 0) stack[0] = 0;
-                __syncwarp();
-                while (sp > 0) {
-                    int k = sp < 32 ? sp : 32;
-                    sp -= k;
-                    int v = lane < k ? stack[sp + lane] : -1;
-                    __syncwarp();
-                    bool valid = v >= 0, acc = false, leaf = false, open = false;
-                    vec4_t<T> A;
-                    int4 Lk = make_int4(0, 0, 0, 0);
-                    T dxv = T(0), dyv = T(0);
-                    if (valid) {
-                        A = P.nodeA[v];
-                        Lk = P.link[v];
-                        dxv = A.x - C.H.x;
-                        dyv = A.y - C.H.y;
-                        T ex = fmax(fabs(dxv - C.box.x) - C.box.z, T(0));
-                        T ey = fmax(fabs(dyv - C.box.y) - C.box.w, T(0));
-                        acc = fma(ex, ex, ey * ey) > A.w;
-                        leaf = !acc && (Lk.y & kLeafBit);
-                        open = !acc && !leaf;
-                    }
-                    unsigned ball = __ballot_sync(full, acc);
-                    if (acc) {
-                        int pos = nf + __popc(ball & ((1u << lane) - 1u));
-                        v2_t<T> Q = P.nodeB[v];
-                        S.fdx[pos] = dxv;
-                        S.fdy[pos] = dyv;
-                        S.fM[pos] = A.z;
-                        S.fqr[pos] = Q.x;
-                        S.fqi[pos] = Q.y;
-                    }
-                    nf += __popc(ball);
-                    c_vis += k;
-                    c_acc += __popc(ball);
-                    int nc = open ? Lk.y : 0;
-                    int totc;
-                    int offc = warp_exclusive_scan(nc, &totc);
-                    if (sp + totc > kStackCap) {
-                        if (lane == 0) atomicOr(P.err, DERR_STACK_OVERFLOW);
-                        break;
-                    }
-                    for (int c = 0; c < nc; ++c) stack[sp + offc + c] = Lk.x + c;
-                    sp += totc;
-                    append_ranges<KIND, T, R, AO>(C, leaf ? (Lk.y & kCountMask) : 0, Lk.x, nn,
-                                                          P.leaf0, P.leaf1, c_near, c_dummy);
-                    if constexpr (KIND != LENS_POINT)
-                        append_big<KIND, T, R, AO>(C, valid && Lk.w > 0, v, Lk.z, Lk.w, nb, c_bigs, c_bigk);
-                    __syncwarp();
-                    if (nf >= 32) {
-                        C.flush_far(nf);
-                        nf = 0;
-                        __syncwarp();
-                    }
-                }
-                C.flush_far(nf);
-                C.flush_near(nn);
-                if constexpr (KIND != LENS_POINT) C.flush_big(nb);
+                traverse(C, stack, c_vis, c_acc, c_near, c_bigs, c_bigk);
+                C.flush_far();
+                C.flush_near();
+                if constexpr (KIND != LENS_POINT) C.flush_big();
             }
         }
         if (P.n_halos > 0) C.halos();
@@ -1084,8 +535,14 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
         P.counter = counter + 2 * launches;
         LENS_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(uint32_t), s));
         if (n > 0) {
-            if (R == 1) launch_dispatch<T, 1>(st.kind, ao, direct, P, t->num_sms, s);
-            else launch_dispatch<T, 2>(st.kind, ao, direct, P, t->num_sms, s);
+            bool done = false;
+            if (!direct && t->walk_mode == LENS_WALK_PAIRS)
+                done = R == 1 ? launch_ws<T, 1>(st.kind, ao, P, t->num_sms, s)
+                              : launch_ws<T, 2>(st.kind, ao, P, t->num_sms, s);
+            if (!done) {
+                if (R == 1) launch_dispatch<T, 1>(st.kind, ao, direct, P, t->num_sms, s);
+                else launch_dispatch<T, 2>(st.kind, ao, direct, P, t->num_sms, s);
+            }
         }
         first_launch = false;
         ++launches;

@@ -116,6 +116,56 @@ def test_tree_gauss_nfw_sph(theta, bar):
     assert ek[~amb].max() <= 1e-5, ek[~amb].max()
 
 
+def _counters(lens):
+    c = lens.counters(reset=True)
+    return [int(c[k]) for k in ("groups", "visited", "cells", "leaf_particles", "big_scanned", "big_kept",
+                                "ray_interactions")]
+
+
+@pytest.mark.parametrize("group_rays", [32, 64])
+@pytest.mark.parametrize("case", ["gauss", "nfw_halo_ao", "points_fp64"])
+def test_walk_pairs_matches_warp(case, group_rays):
+    """The producer/consumer walk visits the same boxes and keeps the same
+    entries as the one-warp walk (interaction counters equal), and its totals
+    agree up to the order of summation; both meet the oracle's bar."""
+    g = lensgen.rng(31)
+    rx = g.uniform(-1, 1, 3000).astype(np.float64)
+    ry = g.uniform(-1, 1, 3000).astype(np.float64)
+    flags, prec, halos = 0, "fp32", []
+    if case == "gauss":
+        parts = lensgen.nfw_particles(20000, 7, nsph=32)
+        species, comps = [L.Species.gauss(cu(parts), 3.0)], comps_gauss(parts, 3.0)
+    elif case == "nfw_halo_ao":
+        h = lensgen.nfw_test_halos(3000, 22, 0.3)
+        species, comps = [L.Species.nfw(cu(h), 3.0)], comps_nfw(h, 3.0)
+        halos = [L.Halo.sis(0.1, -0.2, 0.05)]
+        comps = oracle.concat(comps, oracle.make_components(oracle.SIS, 0.1, -0.2, 0, 0.05))
+        flags = L.ALPHA_ONLY
+    else:
+        p = lensgen.point_disk(5000, 33)
+        species, comps, prec = [L.Species.points(cu(p))], comps_points(p), "fp64"
+    dtype = np.float64 if prec == "fp64" else np.float32
+    dx, dy = cu(rx.astype(dtype)), cu(ry.astype(dtype))
+    res, cnt = {}, {}
+    ncomp = 2 if flags & L.ALPHA_ONLY else 5
+    for walk in ("warp", "pairs"):
+        lens = L.Lens(species, halos, theta=0.3, precision=prec, group_rays=group_rays, walk=walk)
+        out = lens.shoot(dx, dy, flags=flags | L.COUNT)
+        res[walk] = np.stack([o.double().cpu().numpy() for o in out[:ncomp]], axis=1)
+        lens.sync()
+        cnt[walk] = _counters(lens)
+        lens.close()
+    assert cnt["warp"] == cnt["pairs"], cnt
+    ref, absum = oracle.direct_sum(comps, rx, ry, with_absum=True)
+    a, b = res["warp"], res["pairs"]
+    # same terms, summed in another order: a few roundings of the sum of |terms|
+    eps = 1e-14 if prec == "fp64" else 1e-6
+    d = np.abs(a - b) / (absum[:, :ncomp] + 1e-300)
+    assert d.max() <= eps, d.max(axis=0)
+    ea, _, _ = rel_errors(b, ref) if ncomp == 5 else rel_errors(np.c_[b, ref[:, 2:]], ref)
+    assert np.median(ea) <= 1e-3
+
+
 def test_tree_points_fp64_theta01():
     w = lensgen.workload_point_disk()
     p = w["points"]
