@@ -47,6 +47,9 @@ THETA = 0.3
 FLOPS = {"far_cells": 50, "near_point": 22, "near_full": 33, "big_corrections": 38}
 
 
+WALK_SOURCES = ("walk.cu", "walk_dev.cuh", "profiles.cuh")
+
+
 def walk_traffic():
     """DRAM bytes per walk launch from the committed ncu capture, if the walk
     source is unchanged since it was taken."""
@@ -55,10 +58,16 @@ def walk_traffic():
         return None
     with open(p) as f:
         d = json.load(f)
-    src = os.path.join(ROOT, "paper_1312_1128_gb300", "csrc", "walk.cu")
-    with open(src, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()[:16]
-    return d.get("bytes_per_launch") if d.get("walk_cu_sha256_16") == h else None
+    return d.get("bytes_per_launch") if d.get("walk_src_sha256_16") == walk_src_hash() else None
+
+
+def walk_src_hash():
+    """First 16 hex digits of the SHA-256 of the walk kernel's sources."""
+    h = hashlib.sha256()
+    for name in WALK_SOURCES:
+        with open(os.path.join(ROOT, "paper_1312_1128_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -591,7 +600,7 @@ def run_once(args):
     w = lensgen.workload_nfw_sph(n_grid=args.grid)
     parts = torch.from_numpy(w["gauss"]).cuda()
     rx, ry = torch.from_numpy(w["rx"]).cuda(), torch.from_numpy(w["ry"]).cuda()
-    lens = L.Lens([L.Species.gauss(parts, w["q"])], theta=THETA, group_rays=64)
+    lens = L.Lens([L.Species.gauss(parts, w["q"])], theta=THETA, group_rays=64, walk=args.walk)
     lens.shoot(rx, ry, flags=L.TIMING | L.COUNT)
     lens.sync()
     print(json.dumps({"grid": args.grid, "timing_ms": lens.last_timing(), "counters": lens.counters(),
@@ -614,7 +623,14 @@ def main():
                     help="ray grid side (profiling runs use a smaller grid; the metric is quoted at 2048)")
     ap.add_argument("--once", action="store_true",
                     help="one build + shoot of the workload and exit (for profiler captures)")
+    ap.add_argument("--walk", choices=["warp", "pairs"], default="warp",
+                    help="walk form of --once (the headline's autotuned choice is warp)")
+    ap.add_argument("--print-walk-hash", action="store_true",
+                    help="print the hash of the walk sources that profiles/walk_traffic.json is keyed by")
     args = ap.parse_args()
+    if args.print_walk_hash:
+        print(walk_src_hash())
+        return
     if args.once:
         run_once(args)
         return
