@@ -123,6 +123,14 @@ def barrier(ws):
         dist.barrier()
 
 
+def replica_rate(ws, units_per_rank: int, ms_local: float, device=None):
+    """Whole-job rate of independent replicas: every rank processes
+    units_per_rank units; the job takes as long as the slowest rank.
+    Returns (max ms over ranks, units of all ranks per second)."""
+    ms = max_over_ranks(ws, ms_local, device)
+    return ms, ws * units_per_rank / (ms * 1e-3)
+
+
 def max_over_ranks(ws, v: float, device=None) -> float:
     if ws == 1:
         return v
@@ -243,6 +251,27 @@ class NfwSph(Workload):
         p = w["gauss"].astype(np.float64)
         comps = oracle.make_components(oracle.GAUSS, p[:, 0], p[:, 1], p[:, 2], p[:, 3], w["q"])
         return _oracle_loop(oracle, comps, w["rx"], w["ry"], None, budget, seed)
+
+    def cpu_other(self, budget=4.0):
+        """The oracle's direct sum on one core, and the oracle's paper tree
+        (Sec. 3.2, per-ray walk, OpenMP) on all cores, on bounded samples."""
+        import oracle
+        w = self.w
+        p = w["gauss"].astype(np.float64)
+        comps = oracle.make_components(oracle.GAUSS, p[:, 0], p[:, 1], p[:, 2], p[:, 3], w["q"])
+        r1, n1, dt1, _ = _oracle_loop(oracle, comps, w["rx"], w["ry"], None, budget, 11, nthreads=1)
+        t0 = time.perf_counter()
+        tree = oracle.PaperTree(comps, 5, self.theta)
+        tb = time.perf_counter() - t0
+        idx = lensgen.rng(12).permutation(w["rx"].size)[:max(64, int(budget * 1500))]
+        t0 = time.perf_counter()
+        tree.eval(w["rx"][idx].astype(np.float64), w["ry"][idx].astype(np.float64))
+        te = time.perf_counter() - t0
+        return {"oracle_direct_1core": {"value": r1, "unit": UNIT, "cores": 1,
+                                        "sample": f"{n1} random rays, {dt1:.1f} s"},
+                "oracle_paper_tree": {"value": idx.size / te, "unit": UNIT, "cores": oracle.max_threads(),
+                                      "build_s": tb, "theta": self.theta,
+                                      "sample": f"{idx.size} random rays, {te:.1f} s (build excluded)"}}
 
 
 class MixedBatches(Workload):
@@ -463,22 +492,66 @@ class Fit(Workload):
         comps = oracle.make_components(oracle.GAUSS, p[:, 0], p[:, 1], p[:, 2], p[:, 3], w["q"])
         return _oracle_loop(oracle, comps, w["rx"], w["ry"], None, budget, seed)
 
+    def cpu_other(self, budget=4.0):
+        """The oracle's direct sum on one core, and the oracle's paper tree
+        (Sec. 3.2, per-ray walk, OpenMP) on all cores, on bounded samples."""
+        import oracle
+        w = self.w
+        p = w["gauss"].astype(np.float64)
+        comps = oracle.make_components(oracle.GAUSS, p[:, 0], p[:, 1], p[:, 2], p[:, 3], w["q"])
+        r1, n1, dt1, _ = _oracle_loop(oracle, comps, w["rx"], w["ry"], None, budget, 11, nthreads=1)
+        t0 = time.perf_counter()
+        tree = oracle.PaperTree(comps, 5, self.theta)
+        tb = time.perf_counter() - t0
+        idx = lensgen.rng(12).permutation(w["rx"].size)[:max(64, int(budget * 1500))]
+        t0 = time.perf_counter()
+        tree.eval(w["rx"][idx].astype(np.float64), w["ry"][idx].astype(np.float64))
+        te = time.perf_counter() - t0
+        return {"oracle_direct_1core": {"value": r1, "unit": UNIT, "cores": 1,
+                                        "sample": f"{n1} random rays, {dt1:.1f} s"},
+                "oracle_paper_tree": {"value": idx.size / te, "unit": UNIT, "cores": oracle.max_threads(),
+                                      "build_s": tb, "theta": self.theta,
+                                      "sample": f"{idx.size} random rays, {te:.1f} s (build excluded)"}}
+
 
 WORKLOADS = {"nfw_sph": NfwSph, "mixed_batches": MixedBatches, "microlensing": Microlensing, "fit": Fit}
 
 
-def _oracle_loop(oracle, comps, rx, ry, _, budget_s, seed):
+def _oracle_loop(oracle, comps, rx, ry, _, budget_s, seed, nthreads=0):
     """The oracle's FP64 direct sum (as it stands) over a time-bounded random
-    sample of the workload's rays."""
+    sample of the workload's rays (nthreads = 0: all host cores)."""
     g = lensgen.rng(seed)
     order = g.permutation(rx.size)
-    done, t0, chunk = 0, time.perf_counter(), 64
+    done, t0, chunk = 0, time.perf_counter(), 64 if nthreads != 1 else 8
     while time.perf_counter() - t0 < budget_s and done < order.size:
         idx = order[done:done + chunk]
-        oracle.direct_sum(comps, np.asarray(rx[idx], np.float64), np.asarray(ry[idx], np.float64))
+        oracle.direct_sum(comps, np.asarray(rx[idx], np.float64), np.asarray(ry[idx], np.float64),
+                          nthreads=nthreads)
         done += idx.size
     dt = time.perf_counter() - t0
-    return done / dt, done, dt, oracle.max_threads()
+    return done / dt, done, dt, (oracle.max_threads() if nthreads == 0 else nthreads)
+
+
+def measured_hbm_gbs():
+    """(peak GB/s, basis) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def build_roofline(n, n_nodes, build_ms):
+    """Achieved bandwidth of the tree build against the algorithmic bytes:
+    per particle 16 B read + 16 B written, 24 B per radix pass (key and index
+    read and written; 6 passes of 8 bits over the 48-bit keys), and 48 B per
+    node."""
+    nbytes = n * (32 + 24 * 6) + n_nodes * 48
+    peak, basis = measured_hbm_gbs()
+    gbs = nbytes / (build_ms * 1e-3) / 1e9
+    return {"ms": build_ms, "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "peak_gbs": peak,
+            "frac": gbs / peak, "peak_basis": basis,
+            "note": "host wall time of the build phases (includes the syncs that read counts)"}
 
 
 # ------------------------------------------------------------- GPU path
@@ -512,7 +585,7 @@ def run_gpu(args, ws, rank, local):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    walk_ms, group_ms, build_phases, extras = [], [], None, []
+    walk_ms, group_ms, build_phases, build_sizes, extras = [], [], None, None, []
     clocks = ClockSampler(local)
     launches0 = lib.lens_kernel_launches()
     for k in range(args.steps):
@@ -531,14 +604,15 @@ def run_gpu(args, ws, rank, local):
         walk_ms.append(w_ms)
         extras.append(wl.extra())
         if lens is not None:
-            build_phases = [round(x, 3) for x in lens.info()["build_ms"][0]]
+            info = lens.info()
+            build_phases = [round(x, 3) for x in info["build_ms"][0]]
+            build_sizes = (info["n_particles"][0], info["n_nodes"][0])
         done(lens)
     barrier(ws)
     launches = lib.lens_kernel_launches() - launches0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = max_over_ranks(ws, float(np.mean(step_ms)), dev)
-    value = ws * n_rays / (ms * 1e-3)
+    ms, value = replica_rate(ws, n_rays, float(np.mean(step_ms)), dev)
 
     # end to end through the public API with host buffers
     e2e_ms = []
@@ -553,7 +627,7 @@ def run_gpu(args, ws, rank, local):
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
         done(lens)
-    e2e = max_over_ranks(ws, float(np.mean(e2e_ms)), dev)
+    e2e, e2e_value = replica_rate(ws, n_rays, float(np.mean(e2e_ms)), dev)
 
     # roofline of the dominant kernel (the forward walk): useful flops / its duration
     fpr = wl.flops_per_ray()
@@ -568,7 +642,7 @@ def run_gpu(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
             "config": wl.config(ws), "tuning": {"group_rays": wl.group, "walk": wl.walk},
-            "e2e": {"value": ws * n_rays / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
@@ -579,6 +653,9 @@ def run_gpu(args, ws, rank, local):
                          "useful_flops_per_ray": fpr, "walk_ms": w_ms,
                          "group_ms": float(np.mean(group_ms))},
             "build_ms_phases": build_phases,
+            **({"build": build_roofline(build_sizes[0], build_sizes[1], sum(build_phases))}
+               if build_phases and build_sizes else {}),
+            "walk_interactions_per_s": cnt["ray_interactions"] / (w_ms * 1e-3),
             **({k: float(np.mean([e[k] for e in extras])) for k in extras[0]} if extras and extras[0] else {}),
             "interactions": {k: cnt[k] for k in ["groups", "visited", "cells", "leaf_particles",
                                                  "big_scanned", "big_kept", "ray_interactions"]},
@@ -588,6 +665,8 @@ def run_gpu(args, ws, rank, local):
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{done_n} random rays of the workload, FP64 direct sum over "
                                           f"every lens component, {dt:.1f} s"}
+        if hasattr(wl, "cpu_other"):
+            line["cpu_other"] = wl.cpu_other()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
