@@ -187,9 +187,9 @@ int or_direct_sum(const or_comp* comps, int64_t nc, const double* rx, const doub
                   int64_t nr, double* out, double* absum, int nthreads)
 {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #endif
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
     for (int64_t i = 0; i < nr; ++i) {
         nsum acc[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
         double ab[5] = {0, 0, 0, 0, 0};
@@ -220,9 +220,9 @@ int or_direct_vjp(const or_comp* comps, int64_t nc, const double* rx, const doub
     for (int64_t i = 0; i < nr; ++i)
         if (G[5 * i + 2] != 0.0 || G[5 * i + 3] != 0.0 || G[5 * i + 4] != 0.0) return -1;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #endif
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int64_t j = 0; j < nc; ++j) {
         nsum gm = {0, 0}, gx = {0, 0}, gy = {0, 0};
         double t[5];
@@ -482,9 +482,9 @@ int or_tree_eval(const or_tree* t, const double* rx, const double* ry, int64_t n
 {
     if (!t) return -1;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #endif
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
     for (int64_t i = 0; i < nr; ++i) {
         nsum acc[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
         or_counts cn = {0, 0, 0, 0, 0};
