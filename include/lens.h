@@ -271,6 +271,53 @@ lens_status lens_shoot_rays_direct_noalloc(lens_tree* tree, double origin_x, dou
                                            int64_t n, void* alpha1, void* alpha2, void* kappa,
                                            void* gamma1, void* gamma2, int32_t flags, void* stream);
 
+/* lens_refine_cells modes (see below). */
+enum { LENS_REFINE_KAPPA_GAMMA = 0, LENS_REFINE_DEFLECTION = 1 };
+
+/*
+ * lens_refine_cells -- refine cells of a uniform grid of already-shot rays by
+ * the linear lens equation y = y_c + A (x - x_c) (Sec. 3.4 interpolation,
+ * Eq. linear_lens_equation), where the magnification matrix A is uniform over
+ * the cell.  Needs no tree: it reads the outputs of an earlier shot.
+ *   x0, y0, h, nx, ny: ray (i, j) sits at (x0 + i h, y0 + j h), flat index
+ *       i + nx j (nx, ny >= 3, h > 0).  Each ray is the centre of a cell of
+ *       side h; its neighbours are the rays E (i+1, j), N (i, j+1),
+ *       W (i-1, j), S (i, j-1).
+ *   alpha1, alpha2: device, nx*ny deflections, alpha_dtype LENS_F32 or
+ *       LENS_F64 (the deflection mode differences neighbouring deflections:
+ *       with FP32 deflections the rounding of alpha over h limits A to about
+ *       ulp(alpha)/h, so FP64 deflections are what it is for; Sec. 3.4).
+ *   kappa, gamma1, gamma2: device, nx*ny float; required by
+ *       LENS_REFINE_KAPPA_GAMMA, ignored (may be NULL) by LENS_REFINE_DEFLECTION.
+ *   cells, n_cells: device int64, flat indices of the cells' centre rays.
+ *   k: sub-cells per side, odd, 1..15; sub-cell (a, b) is centred at
+ *       x_c + ((a - (k-1)/2) h/k, (b - (k-1)/2) h/k).
+ *   tol: uniformity tolerance (the paper uses 1e-4).
+ *   mode: LENS_REFINE_KAPPA_GAMMA -- uniform if kappa, gamma1, gamma2 of every
+ *       neighbour are within tol of the centre's (compared in FP32); A is
+ *       Eq. magmatrix at the centre.  LENS_REFINE_DEFLECTION -- A from the
+ *       three points centre + each neighbour pair not colinear with it
+ *       (E-N, N-W, W-S, S-E) by the App. A solve with y = x - alpha; uniform if
+ *       no element differs by more than tol between the pairs (compared in
+ *       the precision of alpha); A = the pairs' average.
+ *   Outputs (device, caller-owned): uniform[n_cells] uint8 (1 uniform, 0 not,
+ *       2 = the index is not an interior cell of the grid); amat[4 n_cells]
+ *       float (a11, a21, a12, a22 with dy1 = a11 dx1 + a21 dx2,
+ *       dy2 = a12 dx1 + a22 dx2; NaN for index 2); y_sub[2 k k n_cells]
+ *       double, [cell][b][a][x, y] source positions of the sub-cell centres,
+ *       NaN unless uniform (the caller shoots those rays instead);
+ *       n_nonuniform: optional device counter, incremented once per cell with
+ *       uniform == 0.
+ * Asynchronous on `stream`; allocates nothing; n_cells == 0 is a no-op.
+ * Errors: LENS_ERR_INVALID_ARG for bad sizes, k, tol, mode, dtype or NULL
+ * arrays; launch failures as LENS_ERR_CUDA.
+ */
+lens_status lens_refine_cells(double x0, double y0, double h, int64_t nx, int64_t ny, const void* alpha1,
+                              const void* alpha2, int32_t alpha_dtype, const float* kappa,
+                              const float* gamma1, const float* gamma2, const int64_t* cells,
+                              int64_t n_cells, int32_t k, double tol, int32_t mode, uint8_t* uniform,
+                              float* amat, double* y_sub, unsigned long long* n_nonuniform, void* stream);
+
 /* lens_reserve -- grow the tree's scratch for up to max_rays rays in up to
  * max_batches batches, so that later calls of that size allocate nothing. */
 lens_status lens_reserve(lens_tree* tree, int64_t max_rays, int64_t max_batches);
@@ -323,8 +370,8 @@ lens_status lens_last_timing(lens_tree* tree, double* group_ms, double* walk_ms)
 lens_status lens_fp32_peak(int64_t iters, double* flops, void* stream);
 
 /* lens_kernel_launches -- number of CUDA kernels this library has launched
- * in the process so far (all trees, all threads); a graph replay counts the
- * kernels it contains once per replay only when they are enqueued eagerly. */
+ * in the process so far (all trees, all threads); a CUDA-graph replay adds
+ * the number of kernels the graph contains. */
 int64_t lens_kernel_launches(void);
 
 void lens_free_tree(lens_tree* tree);

@@ -22,15 +22,16 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["Lens", "Species", "Halo", "LensError", "shoot", "lib", "fp32_peak",
+__all__ = ["Lens", "Species", "Halo", "LensError", "shoot", "lib", "fp32_peak", "refine_cells",
            "POINT", "GAUSS", "NFW", "SIS", "DISK", "ALPHA_ONLY", "DIRECT", "ACCUMULATE", "USE_GRAPH",
-           "COUNT", "TIMING"]
+           "COUNT", "TIMING", "REFINE_KAPPA_GAMMA", "REFINE_DEFLECTION"]
 
 POINT, GAUSS, NFW, SIS, DISK = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 PREC_FP32, PREC_FP64 = 0, 1
 ALPHA_ONLY, DIRECT, ACCUMULATE, USE_GRAPH, COUNT, TIMING = 1, 2, 4, 8, 16, 32
 WALK_DEFAULT, WALK_WARP, WALK_PAIRS = 0, 1, 2
+REFINE_KAPPA_GAMMA, REFINE_DEFLECTION = 0, 1
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "liblens.so")
@@ -95,6 +96,8 @@ def lib():
     L.lens_fp32_peak.argtypes = [i64, ctypes.POINTER(ctypes.c_double), vp]
     L.lens_tree_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), i32]
     L.lens_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.lens_refine_cells.argtypes = [d, d, d, i64, i64, vp, vp, i32, vp, vp, vp, vp, i64, i32, d, i32, vp, vp,
+                                    vp, vp, vp]
     L.lens_kernel_launches.argtypes = []
     L.lens_kernel_launches.restype = ctypes.c_int64
     L.lens_free_tree.argtypes = [vp]
@@ -105,7 +108,7 @@ def lib():
                  "lens_shoot_rays_backward", "lens_reserve", "lens_sync_status",
                  "lens_tree_get_info", "lens_tree_export", "lens_fp32_peak", "lens_api_version",
                  "lens_tree_counters", "lens_last_timing", "lens_autotune",
-                 "lens_shoot_rays_direct_noalloc"]:
+                 "lens_shoot_rays_direct_noalloc", "lens_refine_cells"]:
         getattr(L, name).restype = ctypes.c_int32
     _lib = L
     return L
@@ -360,6 +363,36 @@ def fp32_peak(iters: int = 4096, stream=None) -> float:
     v = ctypes.c_double()
     _check(lib().lens_fp32_peak(int(iters), ctypes.byref(v), _stream_ptr(stream)))
     return v.value
+
+
+def refine_cells(x0, y0, h, nx, ny, alpha1, alpha2, kappa=None, gamma1=None, gamma2=None, cells=None,
+                 k: int = 3, tol: float = 1e-4, mode: int = REFINE_KAPPA_GAMMA, n_nonuniform=None,
+                 stream=None):
+    """lens_refine_cells on device tensors (grid arrays of nx*ny; cells: int64
+    flat indices, default every interior ray).  Returns (uniform uint8 (n,),
+    amat float32 (n, 4): a11, a21, a12, a22, y_sub float64 (n, k, k, 2))."""
+    torch = _torch()
+    dev = alpha1.device
+    if cells is None:
+        j, i = torch.meshgrid(torch.arange(1, ny - 1, device=dev), torch.arange(1, nx - 1, device=dev),
+                              indexing="ij")
+        cells = (i + nx * j).reshape(-1).to(torch.int64)
+    n = cells.numel()
+    uniform = torch.empty(n, dtype=torch.uint8, device=dev)
+    amat = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    y_sub = torch.empty(n, k, k, 2, dtype=torch.float64, device=dev)
+    ad = F32 if alpha1.dtype == torch.float32 else F64
+    for t in (kappa, gamma1, gamma2):
+        if t is not None and t.dtype != torch.float32:
+            raise ValueError("kappa and gamma must be float32")
+    _check(lib().lens_refine_cells(float(x0), float(y0), float(h), int(nx), int(ny), _dev_ptr(alpha1),
+                                   _dev_ptr(alpha2), ad, _dev_ptr(kappa) if kappa is not None else None,
+                                   _dev_ptr(gamma1) if gamma1 is not None else None,
+                                   _dev_ptr(gamma2) if gamma2 is not None else None, _dev_ptr(cells), n,
+                                   int(k), float(tol), int(mode), _dev_ptr(uniform), _dev_ptr(amat),
+                                   _dev_ptr(y_sub), _dev_ptr(n_nonuniform) if n_nonuniform is not None
+                                   else None, _stream_ptr(stream)))
+    return uniform, amat, y_sub
 
 
 def shoot(lens: Lens, dx, dy, origin=(0.0, 0.0), species_data=None):

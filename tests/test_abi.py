@@ -72,3 +72,24 @@ def test_bad_arguments_return_status(lib):
     # backward: kappa/gamma gradients are declared unsupported in this version
     assert lt.lens_shoot_rays_backward(None, 0.0, 0.0, None, None, 0, 1, None, None, None, None, None,
                                        None, None, 0, None) == 1
+
+
+def test_refine_cells_argument_checks():
+    """lens_refine_cells rejects bad arguments before touching the device;
+    n_cells == 0 is a no-op (no device call)."""
+    import paper_1312_1128_gb300 as L
+    lt = L.lib()
+    fake = ctypes.c_void_p(16)  # never dereferenced: every case fails or returns first
+
+    def call(h=0.01, nx=8, ny=8, dtype=0, n=4, k=3, tol=1e-4, mode=0, arrays=True, kg=True):
+        a = fake if arrays else None
+        g = fake if kg else None
+        return lt.lens_refine_cells(0.0, 0.0, h, nx, ny, a, a, dtype, g, g, g, a, n, k, tol, mode, a, a, a,
+                                    None, None)
+
+    assert call(n=0) == 0
+    for kw in [dict(n=-1), dict(nx=2), dict(ny=2), dict(h=0.0), dict(h=float("nan")), dict(k=2), dict(k=0),
+               dict(k=17), dict(tol=-1.0), dict(mode=5), dict(dtype=3), dict(arrays=False),
+               dict(kg=False, mode=0)]:
+        assert call(**kw) == 1, kw
+    assert b"kappa" in lt.lens_last_error()
