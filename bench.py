@@ -61,13 +61,25 @@ def walk_traffic():
     return d.get("bytes_per_launch") if d.get("walk_src_sha256_16") == walk_src_hash() else None
 
 
-def walk_src_hash():
-    """First 16 hex digits of the SHA-256 of the walk kernel's sources."""
+def walk_src_hash(names=None):
+    """First 16 hex digits of the SHA-256 of a kernel's sources (default: the
+    walk's)."""
     h = hashlib.sha256()
-    for name in WALK_SOURCES:
+    for name in names or WALK_SOURCES:
         with open(os.path.join(ROOT, "paper_1312_1128_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def refine_traffic():
+    """DRAM bytes per refinement step (the k_refine launch) from the committed ncu
+    capture, if refine.cu is unchanged since it was taken."""
+    p = os.path.join(ROOT, "profiles", "refine_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    return d.get("bytes_per_step") if d.get("refine_src_sha256_16") == walk_src_hash(("refine.cu",)) else None
 
 
 class ClockSampler:
@@ -164,14 +176,14 @@ def run_reference(args, ws, rank):
         samples += done
         t_all += dt
     value = samples / t_all
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+    line = {"impl": "reference", "metric": getattr(wl, "metric", METRIC), "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_rays / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": wl.config(ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{samples} random rays of the workload, FP64 direct sum over "
-                                       f"every lens component (the tree's theta -> 0 limit), "
-                                       f"{per_step:.0f} s per step"},
+                             "sample": f"{samples} " + getattr(wl, "oracle_desc",
+                                       "random rays of the workload, FP64 direct sum over every lens "
+                                       "component (the tree's theta -> 0 limit)") + f", {per_step:.0f} s per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -514,7 +526,172 @@ class Fit(Workload):
                                       "sample": f"{idx.size} random rays, {te:.1f} s (build excluded)"}}
 
 
-WORKLOADS = {"nfw_sph": NfwSph, "mixed_batches": MixedBatches, "microlensing": Microlensing, "fit": Fit}
+class Refine:
+    """Sec. 3.4 cell refinement: the 2048^2 grid of a lens of 1,000 NFW halos
+    (the batched workload's halo field, smooth at the cell scale away from
+    the halo centres) is shot once; a step refines every interior cell into
+    3x3 sub-cells with the kappa/gamma uniformity test (tol 1e-4, Eq.
+    magmatrix) = lens_refine_cells."""
+    name = "refine_2048sq_k3"
+    metric = "refined sub-cell rays/sec (Sec. 3.4 linear lens equation)"
+    k, tol = 3, 1e-4
+    # algorithmic bytes per cell: kappa, gamma1, gamma2, alpha1, alpha2 (FP32,
+    # each grid value read once) and the outputs: the flag, A (4 floats) and
+    # k^2 source positions (2 doubles each); every interior cell, so the
+    # cell list is implicit
+    BYTES_PER_CELL = 5 * 4 + 1 + 16 + 3 * 3 * 16
+
+    def __init__(self, grid=2048):
+        self.w = lensgen.workload_refine(n_grid=grid)
+        self.n = grid
+        self.h = self.w["h"]
+        self.x0, self.y0 = self.w["x0"], self.w["y0"]
+        self.n_cells = (grid - 2) ** 2
+        self.n_rays = self.n_cells * self.k * self.k  # sub-cell rays produced per step
+
+    def config(self, ws):
+        return {"workload": self.name, "grid": self.n, "cells": self.n_cells, "k": self.k, "tol": self.tol,
+                "mode": "kappa/gamma", "patch": "0.03 x 0.03 at (0.3, 0.2)",
+                "lens": "1,000 NFW halos (batched workload's field), tree theta 0.3",
+                "l2": "flushed between timed steps (256 MB write)",
+                "parallelism": f"independent replicas x{ws}"}
+
+    def prepare(self, L, torch, dev):
+        w = self.w
+        self.L, self.torch = L, torch
+        halos = torch.from_numpy(w["nfw"]).to(dev)
+        dx, dy = torch.from_numpy(w["dx"]).to(dev), torch.from_numpy(w["dy"]).to(dev)
+        lens = L.Lens([L.Species.nfw(halos, w["conc"])], theta=THETA, group_rays=64)
+        self.grid = lens.shoot(dx, dy, origin=tuple(w["origin"]))
+        lens.sync()
+        lens.close()
+        j, i = torch.meshgrid(torch.arange(1, self.n - 1, device=dev), torch.arange(1, self.n - 1, device=dev),
+                              indexing="ij")
+        self.cells = (i + self.n * j).reshape(-1).to(torch.int64).contiguous()
+        self.out = (torch.empty(self.n_cells, dtype=torch.uint8, device=dev),
+                    torch.empty(self.n_cells, 4, dtype=torch.float32, device=dev),
+                    torch.empty(self.n_cells, self.k, self.k, 2, dtype=torch.float64, device=dev))
+        self.h_grid = [g.cpu().pin_memory() for g in self.grid]
+        self.d_grid = [torch.empty_like(g) for g in self.grid]
+        self.h_y = torch.empty(self.out[2].shape, dtype=torch.float64).pin_memory()
+        self.h_u = torch.empty(self.n_cells, dtype=torch.uint8).pin_memory()
+
+    def step(self, grid=None):
+        g = grid if grid is not None else self.grid
+        self.L.refine_cells(self.x0, self.y0, self.h, self.n, self.n, g[0], g[1], g[2], g[3], g[4],
+                            cells=None, k=self.k, tol=self.tol, out=self.out)
+
+    def e2e(self):
+        for d, hg in zip(self.d_grid, self.h_grid):
+            d.copy_(hg, non_blocking=True)
+        self.step(self.d_grid)
+        self.h_u.copy_(self.out[0], non_blocking=True)
+        self.h_y.copy_(self.out[2], non_blocking=True)
+        return 5 * self.n * self.n * 4, self.n_cells * (1 + self.k * self.k * 16)
+
+    def oracle_rate(self, budget, seed=7):
+        """The refinement oracle (numpy, FP64) on 256 random cells, repeated
+        for `budget` seconds; its grid inputs at those cells and their
+        neighbours come from the oracle's own direct sum of the lens (input
+        preparation, not timed)."""
+        import oracle
+        import oracle.refine as R
+        w = self.w
+        n = self.n
+        if getattr(self, "_oracle_inputs", None) is None:
+            g = lensgen.rng(seed)
+            i = g.integers(1, n - 1, 256)
+            j = g.integers(1, n - 1, 256)
+            cells = (i + n * j).astype(np.int64)
+            need = np.unique(np.concatenate([cells, cells + 1, cells - 1, cells + n, cells - n]))
+            p = w["nfw"].astype(np.float64)
+            comps = oracle.make_components(oracle.NFW, p[:, 0], p[:, 1], p[:, 2], p[:, 3], w["conc"] * p[:, 3])
+            vals = oracle.direct_sum(comps, w["origin"][0] + w["dx"][need], w["origin"][1] + w["dy"][need])
+            grid = [np.full(n * n, np.nan, np.float32) for _ in range(5)]
+            for q in range(5):
+                grid[q][need] = vals[:, q]
+            self._oracle_inputs = (cells, grid)
+        cells, grid = self._oracle_inputs
+        done, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget:
+            R.refine_cells(self.x0, self.y0, self.h, n, n, *grid, cells, self.k, self.tol, R.KAPPA_GAMMA)
+            done += cells.size
+        dt = time.perf_counter() - t0
+        return done * self.k * self.k / dt, done * self.k * self.k, dt, 1
+
+    oracle_desc = ("sub-cell rays of 256 random cells (repeated), FP64 numpy refinement oracle on "
+                   "oracle-computed grid values")
+
+
+def run_gpu_refine(args, ws, rank, local):
+    """The refinement workload: same timing rules as run_gpu (warm-up, L2
+    flush between timed steps, CUDA events, max over ranks, clocks)."""
+    import torch
+
+    import paper_1312_1128_gb300 as L
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = Refine()
+    wl.prepare(L, torch, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lib = L.lib()
+    for _ in range(args.warmup):
+        wl.step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    launches0 = lib.lens_kernel_launches()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ev[k][0].record()
+        wl.step()
+        ev[k][1].record()
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = lib.lens_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms, value = replica_rate(ws, wl.n_rays, float(np.mean(step_ms)), dev)
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2)):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        barrier(ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        h2d, d2h = wl.e2e()
+        b.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e, e2e_value = replica_rate(ws, wl.n_rays, float(np.mean(e2e_ms)), dev)
+    peak, basis = measured_hbm_gbs()
+    nbytes = wl.BYTES_PER_CELL * wl.n_cells
+    achieved = nbytes / (float(np.mean(step_ms)) * 1e-3) / 1e9
+    uni = wl.out[0]
+    line = {"metric": wl.metric, "value": value,
+            "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": wl.config(ws),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": refine_traffic(), "peak_basis": basis,
+                         "algorithmic_bytes_per_cell": wl.BYTES_PER_CELL,
+                         "kernels": "k_refine (one launch per step)"},
+            "uniform_fraction": float((uni == 1).float().mean().item()),
+            "clocks": clk, "gpu_launches": int(launches)}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r, done_n, dt, cores = wl.oracle_rate(min(args.cpu_seconds, 10.0))
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{done_n} {wl.oracle_desc}, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+WORKLOADS = {"nfw_sph": NfwSph, "mixed_batches": MixedBatches, "microlensing": Microlensing, "fit": Fit,
+             "refine": Refine}
 
 
 def _oracle_loop(oracle, comps, rx, ry, _, budget_s, seed, nthreads=0):
@@ -539,6 +716,18 @@ def measured_hbm_gbs():
             return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback 6.8 TB/s"
+
+
+def grouping_roofline(n_rays, group_ms):
+    """Achieved bandwidth of the ray grouping (bounding box, Morton keys, a
+    4-pass radix sort of 32-bit keys, group records) against its algorithmic
+    bytes per ray: 8 B read for the box, 8 B read + 12 B written for the
+    keys, 24 B per sort pass, 12 B read + 12 B written for the sorted rays."""
+    nbytes = n_rays * (8 + 20 + 24 * 4 + 24)
+    peak, basis = measured_hbm_gbs()
+    gbs = nbytes / (group_ms * 1e-3) / 1e9
+    return {"ms": group_ms, "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "peak_gbs": peak,
+            "frac": gbs / peak, "peak_basis": basis}
 
 
 def build_roofline(n, n_nodes, build_ms):
@@ -656,6 +845,8 @@ def run_gpu(args, ws, rank, local):
             **({"build": build_roofline(build_sizes[0], build_sizes[1], sum(build_phases))}
                if build_phases and build_sizes else {}),
             "walk_interactions_per_s": cnt["ray_interactions"] / (w_ms * 1e-3),
+            **({"grouping": grouping_roofline(n_rays, float(np.mean(group_ms)))}
+               if not wl.graph and float(np.mean(group_ms)) > 0 else {}),
             **({k: float(np.mean([e[k] for e in extras])) for k in extras[0]} if extras and extras[0] else {}),
             "interactions": {k: cnt[k] for k in ["groups", "visited", "cells", "leaf_particles",
                                                  "big_scanned", "big_kept", "ray_interactions"]},
@@ -693,7 +884,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["nfw_sph", "mixed_batches", "microlensing", "fit"], default="nfw_sph",
+    ap.add_argument("--workload", choices=["nfw_sph", "mixed_batches", "microlensing", "fit", "refine"],
+                    default="nfw_sph",
                     help="nfw_sph (default) is the headline; the others measure the batched, "
                          "microlensing and differentiable paths")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -720,7 +912,10 @@ def main():
         run_reference(args, ws, rank)
     else:
         ws, rank, local = dist_setup("nccl")
-        run_gpu(args, ws, rank, local)
+        if args.workload == "refine":
+            run_gpu_refine(args, ws, rank, local)
+        else:
+            run_gpu(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

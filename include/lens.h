@@ -289,7 +289,10 @@ enum { LENS_REFINE_KAPPA_GAMMA = 0, LENS_REFINE_DEFLECTION = 1 };
  *       ulp(alpha)/h, so FP64 deflections are what it is for; Sec. 3.4).
  *   kappa, gamma1, gamma2: device, nx*ny float; required by
  *       LENS_REFINE_KAPPA_GAMMA, ignored (may be NULL) by LENS_REFINE_DEFLECTION.
- *   cells, n_cells: device int64, flat indices of the cells' centre rays.
+ *   cells, n_cells: device int64, flat indices of the cells' centre rays;
+ *       cells == NULL means every interior cell in row-major order
+ *       (i = 1..nx-2 fastest, then j = 1..ny-2; n_cells must be
+ *       (nx - 2)(ny - 2)).
  *   k: sub-cells per side, odd, 1..15; sub-cell (a, b) is centred at
  *       x_c + ((a - (k-1)/2) h/k, (b - (k-1)/2) h/k).
  *   tol: uniformity tolerance (the paper uses 1e-4).

@@ -231,6 +231,19 @@ def workload_nfw_sph(n_part=1_000_000, n_grid=2048, seed=2, nsph=32, q=3.0):
     return dict(gauss=parts, q=q, rx=rx, ry=ry)
 
 
+def workload_refine(n_halos=1000, n_grid=2048, seed=3, conc=3.0, centre=(0.3, 0.2), width=0.03):
+    """The batched workload's NFW halo field (same seed, so the same halos)
+    and an n_grid^2 cell-centred grid of rays over a width-wide square at
+    `centre` (an FP64 origin plus FP64 offsets, so ray (i, j) sits exactly at
+    x0 + i h, y0 + j h): the input of the cell-refinement workload."""
+    halos = nfw_halo_field(n_halos, seed, g=rng(seed))
+    h = width / n_grid
+    c = (np.arange(n_grid) + 0.5) * h - 0.5 * width
+    X, Y = np.meshgrid(c, c)
+    return dict(nfw=halos, conc=conc, origin=np.array(centre, np.float64), dx=X.reshape(-1), dy=Y.reshape(-1),
+                n_grid=n_grid, h=h, x0=centre[0] + c[0], y0=centre[1] + c[0])
+
+
 def workload_mixed_batches(n_halos=1000, n_stars=1_000_000, n_batches=256, nmin=1e3,
                            nmax=1e6, seed=3, kappa_star=0.5):
     """NFW halo field plus Salpeter stars in a 0.01-wide patch at (0.3, 0.2);

@@ -367,20 +367,22 @@ def fp32_peak(iters: int = 4096, stream=None) -> float:
 
 def refine_cells(x0, y0, h, nx, ny, alpha1, alpha2, kappa=None, gamma1=None, gamma2=None, cells=None,
                  k: int = 3, tol: float = 1e-4, mode: int = REFINE_KAPPA_GAMMA, n_nonuniform=None,
-                 stream=None):
+                 out=None, stream=None):
     """lens_refine_cells on device tensors (grid arrays of nx*ny; cells: int64
     flat indices, default every interior ray).  Returns (uniform uint8 (n,),
-    amat float32 (n, 4): a11, a21, a12, a22, y_sub float64 (n, k, k, 2))."""
+    amat float32 (n, 4): a11, a21, a12, a22, y_sub float64 (n, k, k, 2)),
+    written into `out` (that triple) when given."""
     torch = _torch()
     dev = alpha1.device
-    if cells is None:
-        j, i = torch.meshgrid(torch.arange(1, ny - 1, device=dev), torch.arange(1, nx - 1, device=dev),
-                              indexing="ij")
-        cells = (i + nx * j).reshape(-1).to(torch.int64)
-    n = cells.numel()
-    uniform = torch.empty(n, dtype=torch.uint8, device=dev)
-    amat = torch.empty(n, 4, dtype=torch.float32, device=dev)
-    y_sub = torch.empty(n, k, k, 2, dtype=torch.float64, device=dev)
+    n = cells.numel() if cells is not None else (nx - 2) * (ny - 2)  # None: every interior cell, row-major
+    if out is not None:
+        uniform, amat, y_sub = out
+        if uniform.numel() < n or amat.numel() < 4 * n or y_sub.numel() < 2 * k * k * n:
+            raise ValueError("refine outputs too small")
+    else:
+        uniform = torch.empty(n, dtype=torch.uint8, device=dev)
+        amat = torch.empty(n, 4, dtype=torch.float32, device=dev)
+        y_sub = torch.empty(n, k, k, 2, dtype=torch.float64, device=dev)
     ad = F32 if alpha1.dtype == torch.float32 else F64
     for t in (kappa, gamma1, gamma2):
         if t is not None and t.dtype != torch.float32:
@@ -388,7 +390,8 @@ def refine_cells(x0, y0, h, nx, ny, alpha1, alpha2, kappa=None, gamma1=None, gam
     _check(lib().lens_refine_cells(float(x0), float(y0), float(h), int(nx), int(ny), _dev_ptr(alpha1),
                                    _dev_ptr(alpha2), ad, _dev_ptr(kappa) if kappa is not None else None,
                                    _dev_ptr(gamma1) if gamma1 is not None else None,
-                                   _dev_ptr(gamma2) if gamma2 is not None else None, _dev_ptr(cells), n,
+                                   _dev_ptr(gamma2) if gamma2 is not None else None,
+                                   _dev_ptr(cells) if cells is not None else None, n,
                                    int(k), float(tol), int(mode), _dev_ptr(uniform), _dev_ptr(amat),
                                    _dev_ptr(y_sub), _dev_ptr(n_nonuniform) if n_nonuniform is not None
                                    else None, _stream_ptr(stream)))

@@ -104,9 +104,13 @@ def test_refine_fullsize_sampled():
     for mode in (R.KAPPA_GAMMA, R.DEFLECTION):
         a = [cu(out[:, q].astype(np.float32)) for q in range(5)]
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-        uni, A, ys = L.refine_cells(x0, y0, h, nx, ny, *a, k=3, mode=mode, n_nonuniform=cnt)
+        uni, A, ys = L.refine_cells(x0, y0, h, nx, ny, *a, k=3, mode=mode, n_nonuniform=cnt)  # implicit cells
         torch.cuda.synchronize()
         assert uni.numel() == allc.size and int(cnt.item()) == int((uni == 0).sum().item())
+        # the implicit list is every interior cell in row-major order
+        u2, A2, y2 = L.refine_cells(x0, y0, h, nx, ny, *a, cells=cu(allc[:70000]), k=3, mode=mode)
+        assert torch.equal(u2, uni[:70000]) and torch.equal(A2, A[:70000])
+        assert torch.equal(torch.nan_to_num(y2), torch.nan_to_num(ys[:70000]))
         idx = torch.from_numpy(sample).cuda()
         got_u, got_A, got_y = uni[idx].cpu().numpy(), A[idx].cpu().numpy(), ys[idx].cpu().numpy()
         kg = [out[:, q].astype(np.float32) for q in (2, 3, 4)]
