@@ -45,6 +45,12 @@ THETA = 0.3
 # FP32 flops per interaction as the kernels write them (FADD/FMUL = 1,
 # FFMA = 2, MUFU = 1), frozen before tuning.
 FLOPS = {"far_cells": 50, "near_point": 22, "near_full": 33, "big_corrections": 38}
+# the same interactions when only alpha is accumulated (LENS_ALPHA_ONLY)
+FLOPS_ALPHA = {"far_cells": 31, "near_point": 11, "near_full": 20, "big_corrections": 16}
+# the adjoint's per-interaction work for alpha gradients, as backward.cu
+# writes it: the forward term plus the gradient update (23 flops), and for a
+# far cell the cell adjoints dL/dM, dL/dQ2, dL/dz_cm
+FLOPS_ADJOINT = {"far_cells": 56, "near_point": 31, "near_full": 42, "big_corrections": 37}
 
 
 WALK_SOURCES = ("walk.cu", "walk_dev.cuh", "profiles.cuh")
@@ -426,9 +432,16 @@ class Microlensing(Workload):
 
 class Fit(Workload):
     """Lens fit: 1e5 Gaussians (r_sm 0.01), 1000^2 grid, theta 0.3; step =
-    build + forward alpha + adjoint of L = sum |alpha - alpha_t|^2."""
+    build + forward alpha + adjoint of L = sum |alpha - alpha_t|^2.  The
+    adjoint is the dominant kernel: the line's roofline describes it, the
+    forward walk's is reported beside it."""
     name = "fit_1e5_1000sq"
-    FLOPS = FLOPS
+    FLOPS = FLOPS_ALPHA
+
+    def adjoint_flops_per_ray(self):
+        with open(os.path.join(ROOT, "tests", "golden", "useful_counts.json")) as f:
+            c = json.load(f)[self.name][str(self.theta)]
+        return sum(FLOPS_ADJOINT[k] * c[k] for k in FLOPS_ADJOINT)
 
     def __init__(self):
         self.w = lensgen.workload_fit()
@@ -851,6 +864,18 @@ def run_gpu(args, ws, rank, local):
             "interactions": {k: cnt[k] for k in ["groups", "visited", "cells", "leaf_particles",
                                                  "big_scanned", "big_kept", "ray_interactions"]},
             "clocks": clk, "gpu_launches": int(launches)}
+    if hasattr(wl, "adjoint_flops_per_ray"):
+        # the adjoint dominates this step: its roofline is the line's
+        b_ms = line["backward_ms"]
+        afpr = wl.adjoint_flops_per_ray()
+        a_ach = afpr * n_rays / (b_ms * 1e-3) / 1e12
+        line["roofline_forward"] = line["roofline"]
+        line["roofline"] = {"bound": "alu", "achieved": a_ach, "peak": peak, "unit": "TFLOP/s",
+                            "frac": a_ach / peak, "traffic": None,
+                            "peak_basis": line["roofline_forward"]["peak_basis"],
+                            "kernel": "lens_shoot_rays_backward (back_kernel + push-down + leaf gradients), "
+                                      "timed as a whole",
+                            "useful_flops_per_ray": afpr, "backward_ms": b_ms}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         r, done_n, dt, cores = wl.oracle_rate(args.cpu_seconds)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
