@@ -116,6 +116,15 @@ def nfw_particles(n: int, seed: int, rs: float = 0.1, rmax: float = 1.0,
     return p
 
 
+def nfw_positions_3d(n: int, seed: int, rs: float = 0.1, rmax: float = 1.0):
+    """The 3D positions nfw_particles(n, seed) projects (same draws), as
+    float32 (n, 3) {x, y, z}: the input of the smoothing-length search."""
+    g = rng(seed)
+    r = nfw_radii(g, n, rs, rmax)
+    x, y, z = isotropic(g, r)
+    return np.stack([f32(x), f32(y), f32(z)], axis=1)
+
+
 def nfw_halo_field(n: int, seed: int, log10_m_mean: float = -4.0, log10_m_sigma: float = 1.0,
                    rs_at_1e4: float = 0.02, box: float = 1.0, g=None):
     """NFW halos: log10 m ~ N(mean, sigma); positions uniform in [-box, box]^2;

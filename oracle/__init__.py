@@ -13,6 +13,7 @@ direct_sum(comps, rx, ry)       Sec. 5.1 theta=0 limit: sum over all components
 direct_vjp(comps, rx, ry, G)    gradient of a loss of alpha w.r.t. (m, x, y)
 PaperTree(comps, leaf_max, th)  Sec. 3.2 tree, evaluated ray by ray, with counts
 refine.refine_cells(...)        Sec. 3.4 cell interpolation with A from App. A (numpy)
+knn.kth_neighbour_distance(...)  Sec. 3.1 3D smoothing lengths (brute force / cKDTree)
 
 Components are a numpy structured array of ``COMP_DTYPE`` (see
 ``make_components``); types follow ``POINT, GAUSS, NFW, SIS, DISK``.
