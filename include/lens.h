@@ -321,6 +321,24 @@ lens_status lens_refine_cells(double x0, double y0, double h, int64_t nx, int64_
                               int64_t n_cells, int32_t k, double tol, int32_t mode, uint8_t* uniform,
                               float* amat, double* y_sub, unsigned long long* n_nonuniform, void* stream);
 
+/*
+ * lens_smoothing_lengths -- the smoothing length of every particle (Sec.
+ * 3.1): the distance in 3D to its k-th nearest other particle (the paper
+ * prefers the 3D neighbour distance; its workloads use k = 32).  Exact
+ * k-nearest search: particles are sorted by 3D Morton keys, the k nearest of
+ * each particle's 2k key-order neighbours bound the distance, and the 3x3x3
+ * octree cells at least that large around the particle are scanned.
+ * Distances are computed in FP32.
+ *   xyz: device float32, n x 3 row-major {x, y, z}; r_sm: device float32,
+ *       n outputs (caller-owned; may not alias xyz).
+ *   k: 1..64; n = 0 is a no-op, otherwise n > k and n < 2^32.
+ * Synchronous on `stream` (reads the particles' bounding box); allocates its
+ * scratch (about 40 B per particle) from the stream-ordered pool.
+ * Errors: LENS_ERR_INVALID_ARG for bad k or n, NULL arrays or non-finite
+ * positions; LENS_ERR_CUDA / LENS_ERR_OOM from the device.
+ */
+lens_status lens_smoothing_lengths(const float* xyz, int64_t n, int32_t k, float* r_sm, void* stream);
+
 /* lens_reserve -- grow the tree's scratch for up to max_rays rays in up to
  * max_batches batches, so that later calls of that size allocate nothing. */
 lens_status lens_reserve(lens_tree* tree, int64_t max_rays, int64_t max_batches);

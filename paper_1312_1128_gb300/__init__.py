@@ -22,7 +22,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["Lens", "Species", "Halo", "LensError", "shoot", "lib", "fp32_peak", "refine_cells",
+__all__ = ["Lens", "Species", "Halo", "LensError", "shoot", "lib", "fp32_peak", "refine_cells", "smoothing_lengths",
            "POINT", "GAUSS", "NFW", "SIS", "DISK", "ALPHA_ONLY", "DIRECT", "ACCUMULATE", "USE_GRAPH",
            "COUNT", "TIMING", "REFINE_KAPPA_GAMMA", "REFINE_DEFLECTION"]
 
@@ -98,6 +98,7 @@ def lib():
     L.lens_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.lens_refine_cells.argtypes = [d, d, d, i64, i64, vp, vp, i32, vp, vp, vp, vp, i64, i32, d, i32, vp, vp,
                                     vp, vp, vp]
+    L.lens_smoothing_lengths.argtypes = [vp, i64, i32, vp, vp]
     L.lens_kernel_launches.argtypes = []
     L.lens_kernel_launches.restype = ctypes.c_int64
     L.lens_free_tree.argtypes = [vp]
@@ -108,7 +109,7 @@ def lib():
                  "lens_shoot_rays_backward", "lens_reserve", "lens_sync_status",
                  "lens_tree_get_info", "lens_tree_export", "lens_fp32_peak", "lens_api_version",
                  "lens_tree_counters", "lens_last_timing", "lens_autotune",
-                 "lens_shoot_rays_direct_noalloc", "lens_refine_cells"]:
+                 "lens_shoot_rays_direct_noalloc", "lens_refine_cells", "lens_smoothing_lengths"]:
         getattr(L, name).restype = ctypes.c_int32
     _lib = L
     return L
@@ -396,6 +397,19 @@ def refine_cells(x0, y0, h, nx, ny, alpha1, alpha2, kappa=None, gamma1=None, gam
                                    _dev_ptr(y_sub), _dev_ptr(n_nonuniform) if n_nonuniform is not None
                                    else None, _stream_ptr(stream)))
     return uniform, amat, y_sub
+
+
+def smoothing_lengths(xyz, k: int = 32, out=None, stream=None):
+    """Distance from every particle to its k-th nearest other particle in 3D
+    (lens_smoothing_lengths): xyz a (n, 3) float32 CUDA tensor; returns (n,)
+    float32 (written into `out` when given)."""
+    torch = _torch()
+    if xyz.dim() != 2 or xyz.shape[1] != 3 or xyz.dtype != torch.float32:
+        raise ValueError("xyz must be (n, 3) float32")
+    n = xyz.shape[0]
+    r = out if out is not None else torch.empty(n, dtype=torch.float32, device=xyz.device)
+    _check(lib().lens_smoothing_lengths(_dev_ptr(xyz), n, int(k), _dev_ptr(r), _stream_ptr(stream)))
+    return r
 
 
 def shoot(lens: Lens, dx, dy, origin=(0.0, 0.0), species_data=None):

@@ -1,0 +1,269 @@
+// knn.cu -- smoothing lengths on the GPU (Sec. 3.1): for every particle the
+// distance to its k-th nearest other particle in 3D, the size the smoothed
+// particles of the lens are given (the paper prefers the 3D neighbour
+// distance).
+//
+// Particles are sorted by 63-bit 3D Morton keys of a cube around them.  A
+// query first takes the k nearest among its 2k neighbours in key order: an
+// upper bound R on the k-th distance.  With the octree level whose cell side
+// is at least R (plus a margin for the quantisation), every particle within R
+// lies in the 3 x 3 x 3 cells around the query's cell; each cell is one run of
+// the sorted keys, found by binary search, and scanning them gives the exact
+// k nearest.  One thread per particle keeps its k smallest squared distances.
+#include <cmath>
+
+#include "common.cuh"
+#include "sort.cuh"
+
+namespace lens {
+
+constexpr int kKnnMax = 64;   // largest k
+constexpr int kKnnBits = 21;  // key bits per axis
+
+// Spread the 21 bits of v to every third bit.
+LENS_DEV uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffull;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+LENS_DEV uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) { return spread3(x) | spread3(y) << 1 | spread3(z) << 2; }
+
+struct KnnCube {
+    float ox, oy, oz;  // lower corner
+    float inv_q;       // quanta per unit length (2^21 / side)
+    float side;
+};
+
+LENS_DEV uint32_t quantise(float v, float o, float inv_q)
+{
+    float t = (v - o) * inv_q;
+    t = fminf(fmaxf(t, 0.0f), (float)((1u << kKnnBits) - 1));
+    return (uint32_t)t;
+}
+
+__global__ void k_knn_bbox(const float* xyz, int64_t n, unsigned long long* bb)
+{
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            const float v = xyz[3 * i + a];
+            lo[a] = fminf(lo[a], v);
+            hi[a] = fmaxf(hi[a], v);
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&bb[a], dbl_to_ordered((double)lo[a]));
+            atomicMax(&bb[3 + a], dbl_to_ordered((double)hi[a]));
+        }
+}
+
+__global__ void k_knn_bbox_init(unsigned long long* bb)
+{
+    if (threadIdx.x < 3) {
+        bb[threadIdx.x] = dbl_to_ordered(INFINITY);
+        bb[3 + threadIdx.x] = dbl_to_ordered(-INFINITY);
+    }
+}
+
+__global__ void k_knn_keys(const float* xyz, int64_t n, KnnCube c, uint64_t* keys, uint32_t* idx, uint32_t* err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) atomicOr(err, 1u);
+    keys[i] = morton3(quantise(x, c.ox, c.inv_q), quantise(y, c.oy, c.inv_q), quantise(z, c.oz, c.inv_q));
+    idx[i] = (uint32_t)i;
+}
+
+__global__ void k_knn_gather(const float* xyz, int64_t n, const uint32_t* idx, float4* sp)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = idx[i];
+    sp[i] = make_float4(xyz[3 * (int64_t)j], xyz[3 * (int64_t)j + 1], xyz[3 * (int64_t)j + 2], __uint_as_float(j));
+}
+
+// The k smallest values seen, unordered, with the largest tracked.
+struct KSmallest {
+    float v[kKnnMax];
+    int k, cnt, iw;
+    float worst;
+    LENS_DEV void reset(int kk, float bound)
+    {
+        k = kk;
+        cnt = 0;
+        iw = 0;
+        worst = bound;  // values above the bound are not kept
+    }
+    LENS_DEV void offer(float d2)
+    {
+        if (cnt < k) {
+            if (d2 > worst) return;
+            v[cnt++] = d2;
+            if (cnt == k) rescan();
+        } else if (d2 < worst) {
+            v[iw] = d2;
+            rescan();
+        }
+    }
+    LENS_DEV void rescan()
+    {
+        iw = 0;
+        worst = v[0];
+        for (int q = 1; q < k; ++q)
+            if (v[q] > worst) {
+                worst = v[q];
+                iw = q;
+            }
+    }
+};
+
+LENS_DEV int64_t lower_bound_u64(const uint64_t* a, int64_t n, uint64_t key)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(128)
+k_knn_query(const float4* sp, const uint64_t* keys, int64_t n, int k, KnnCube c, float* r_out, uint32_t* err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 p = sp[i];
+    KSmallest S;
+    // upper bound: the k nearest among the 2k neighbours in key order
+    S.reset(k, INFINITY);
+    const int64_t w0 = i - k > 0 ? i - k : 0, w1 = i + k + 1 < n ? i + k + 1 : n;
+    for (int64_t j = w0; j < w1; ++j) {
+        if (j == i) continue;
+        const float4 q = sp[j];
+        const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+        S.offer(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    }
+    // rounding of the bound and of the quantisation: inflate R by both
+    const float q1 = 1.0f / c.inv_q;
+    const float R = sqrtf(S.worst) * 1.000001f + 2.0f * q1;
+    const float R2 = R * R;
+    int level = 0;
+    if (R < c.side) {
+        level = (int)floorf(log2f(c.side / R));
+        level = level < 0 ? 0 : (level > kKnnBits ? kKnnBits : level);
+        while (level > 0 && c.side / (float)(1u << level) < R) --level;  // cell side >= R
+    }
+    const int shift = kKnnBits - level;
+    const int64_t ncell = (int64_t)1 << level;
+    const int64_t cx = quantise(p.x, c.ox, c.inv_q) >> shift, cy = quantise(p.y, c.oy, c.inv_q) >> shift,
+                  cz = quantise(p.z, c.oz, c.inv_q) >> shift;
+    S.reset(k, R2);
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int64_t ax = cx + dx, ay = cy + dy, az = cz + dz;
+                if (ax < 0 || ay < 0 || az < 0 || ax >= ncell || ay >= ncell || az >= ncell) continue;
+                const uint64_t prefix = morton3((uint32_t)ax, (uint32_t)ay, (uint32_t)az);
+                const uint64_t kmin = prefix << (3 * shift);
+                const uint64_t kmax = (prefix + 1) << (3 * shift);
+                const int64_t a = lower_bound_u64(keys, n, kmin), b = lower_bound_u64(keys, n, kmax);
+                for (int64_t j = a; j < b; ++j) {
+                    if (j == i) continue;
+                    const float4 q = sp[j];
+                    const float ddx = q.x - p.x, ddy = q.y - p.y, ddz = q.z - p.z;
+                    S.offer(fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz)));
+                }
+            }
+    if (S.cnt < k) {
+        atomicOr(err, 2u);  // cannot happen: the bound's k particles lie in these cells
+        r_out[__float_as_uint(p.w)] = NAN;
+        return;
+    }
+    r_out[__float_as_uint(p.w)] = sqrtf(S.worst);
+}
+
+}  // namespace lens
+
+using namespace lens;
+
+extern "C" lens_status lens_smoothing_lengths(const float* xyz, int64_t n, int32_t k, float* r_sm, void* stream)
+{
+    if (k < 1 || k > kKnnMax) return lens_set_error(LENS_ERR_INVALID_ARG, "k must be 1..%d", kKnnMax);
+    if (n < 0 || n > 0xffffffffll) return lens_set_error(LENS_ERR_INVALID_ARG, "bad particle count");
+    if (n == 0) return LENS_OK;
+    if (n <= k) return lens_set_error(LENS_ERR_INVALID_ARG, "need more than k particles");
+    if (!xyz || !r_sm) return lens_set_error(LENS_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int TB = 256;
+    const int64_t G = (n + TB - 1) / TB;
+    // scratch: bbox + error word, keys x 2, indices x 2, sorted points, sort temp
+    const size_t tmp_bytes = radix_sort_temp_bytes<uint64_t>(n);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_bb = 0, o_err = o_bb + al(6 * 8), o_k0 = o_err + al(8), o_k1 = o_k0 + al(n * 8),
+                 o_v0 = o_k1 + al(n * 8), o_v1 = o_v0 + al(n * 4), o_sp = o_v1 + al(n * 4),
+                 o_tmp = o_sp + al(n * 16), total = o_tmp + al(tmp_bytes);
+    char* base = nullptr;
+    LENS_CUDA(cudaMallocAsync((void**)&base, total, s));
+    unsigned long long* bb = (unsigned long long*)(base + o_bb);
+    uint32_t* err = (uint32_t*)(base + o_err);
+    uint64_t *k0 = (uint64_t*)(base + o_k0), *k1 = (uint64_t*)(base + o_k1);
+    uint32_t *v0 = (uint32_t*)(base + o_v0), *v1 = (uint32_t*)(base + o_v1);
+    float4* sp = (float4*)(base + o_sp);
+    lens_status st = LENS_OK;
+    unsigned long long hbb[6];
+    uint32_t herr = 0;
+    do {
+        cudaError_t e = cudaMemsetAsync(err, 0, 4, s);
+        if (e != cudaSuccess) { st = lens_cuda_check(e, "memset"); break; }
+        k_knn_bbox_init<<<1, 32, 0, s>>>(bb);
+        note_launch();
+        k_knn_bbox<<<(unsigned)(G < 1024 ? G : 1024), TB, 0, s>>>(xyz, n, bb);
+        note_launch();
+        e = cudaMemcpyAsync(hbb, bb, sizeof(hbb), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { st = lens_cuda_check(e, "bbox"); break; }
+        double lo[3], hi[3], side = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = ordered_to_dbl(hbb[a]);
+            hi[a] = ordered_to_dbl(hbb[3 + a]);
+            side = std::max(side, hi[a] - lo[a]);
+        }
+        if (!std::isfinite(side)) { st = lens_set_error(LENS_ERR_INVALID_ARG, "non-finite particle position"); break; }
+        side = side > 0.0 ? side * (1.0 + 1e-5) : 1.0;
+        KnnCube c;
+        c.ox = (float)lo[0];
+        c.oy = (float)lo[1];
+        c.oz = (float)lo[2];
+        c.side = (float)side;
+        c.inv_q = (float)((double)(1u << kKnnBits) / side);
+        k_knn_keys<<<(unsigned)G, TB, 0, s>>>(xyz, n, c, k0, v0, err);
+        note_launch();
+        uint64_t* sk;
+        uint32_t* sv;
+        radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, 3 * kKnnBits, base + o_tmp, s, &sk, &sv);
+        k_knn_gather<<<(unsigned)G, TB, 0, s>>>(xyz, n, sv, sp);
+        note_launch();
+        k_knn_query<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(sp, sk, n, k, c, r_sm, err);
+        note_launch();
+        e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { st = lens_cuda_check(e, "smoothing lengths"); break; }
+        if (herr & 1u) st = lens_set_error(LENS_ERR_INVALID_ARG, "non-finite particle position");
+        else if (herr) st = lens_set_error(LENS_ERR_INTERNAL, "neighbour search check failed (code %u)", herr);
+    } while (false);
+    cudaFreeAsync(base, s);
+    return st;
+}

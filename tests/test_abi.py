@@ -93,3 +93,13 @@ def test_refine_cells_argument_checks():
                dict(kg=False, mode=0)]:
         assert call(**kw) == 1, kw
     assert b"kappa" in lt.lens_last_error()
+
+
+def test_smoothing_lengths_argument_checks():
+    import paper_1312_1128_gb300 as L
+    lt = L.lib()
+    fake = ctypes.c_void_p(16)  # never dereferenced: every case fails or returns first
+    assert lt.lens_smoothing_lengths(fake, 0, 32, fake, None) == 0
+    for n, k, arr in [(100, 0, fake), (100, 65, fake), (-1, 8, fake), (32, 32, fake), (5, 32, fake),
+                      (100, 8, None), (1 << 33, 8, fake)]:
+        assert lt.lens_smoothing_lengths(arr, n, k, arr, None) == 1, (n, k)
