@@ -173,6 +173,7 @@ def run_reference(args, ws, rank):
         return
     wl = WORKLOADS[args.workload]()
     n_rays = wl.n_rays
+    unit = getattr(wl, "unit", UNIT)
     per_step = 2.0  # seconds of oracle work per step
     for _ in range(args.warmup):
         wl.oracle_rate(0.5)
@@ -182,15 +183,16 @@ def run_reference(args, ws, rank):
         samples += done
         t_all += dt
     value = samples / t_all
-    line = {"impl": "reference", "metric": getattr(wl, "metric", METRIC), "value": value, "unit": UNIT, "n_gpus": ws,
+    line = {"impl": "reference", "metric": getattr(wl, "metric", METRIC), "value": value,
+            "unit": unit, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_rays / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": wl.config(ws),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
                              "sample": f"{samples} " + getattr(wl, "oracle_desc",
                                        "random rays of the workload, FP64 direct sum over every lens "
                                        "component (the tree's theta -> 0 limit)") + f", {per_step:.0f} s per step"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -636,6 +638,122 @@ class Refine:
                    "oracle-computed grid values")
 
 
+class Knn:
+    """Sec. 3.1 smoothing lengths: the 3D distance to the 32nd nearest
+    neighbour of each of the headline's 1e6 NFW particles (the input
+    preparation of the smoothed-particle lens, on the device); step =
+    lens_smoothing_lengths."""
+    name = "smoothing_1e6_k32"
+    metric = "smoothing lengths/sec (Sec. 3.1, 3D k = 32 nearest neighbour)"
+    unit = "particles/s"
+    k = 32
+    # algorithmic bytes per particle of this sort-based search: positions in
+    # (12) and lengths out (4), keys and indices written (12), 8 radix passes
+    # over (key, index) read and written (24 each), the sorted copy (16 in,
+    # 16 out)
+    BYTES_PER_PARTICLE = 12 + 4 + 12 + 8 * 24 + 32
+
+    def __init__(self, n=1_000_000):
+        self.xyz = lensgen.nfw_positions_3d(n, 2)
+        self.n_rays = n  # units of the line: particles
+
+    def config(self, ws):
+        return {"workload": self.name, "n_particles": self.n_rays, "k": self.k,
+                "particles": "3D NFW, r_s = 0.1, r < 1 (the headline's, seed 2)",
+                "l2": "flushed between timed steps (256 MB write)",
+                "parallelism": f"independent replicas x{ws}"}
+
+    def prepare(self, L, torch, dev):
+        self.L = L
+        self.d_xyz = torch.from_numpy(self.xyz).to(dev)
+        self.r = torch.empty(self.n_rays, dtype=torch.float32, device=dev)
+        self.h_xyz = torch.from_numpy(self.xyz).pin_memory()
+        self.d2 = torch.empty_like(self.d_xyz)
+        self.h_r = torch.empty(self.n_rays, dtype=torch.float32).pin_memory()
+
+    def step(self):
+        self.L.smoothing_lengths(self.d_xyz, self.k, out=self.r)
+
+    def e2e(self):
+        self.d2.copy_(self.h_xyz, non_blocking=True)
+        self.L.smoothing_lengths(self.d2, self.k, out=self.r)
+        self.h_r.copy_(self.r, non_blocking=True)
+        return self.xyz.nbytes, self.n_rays * 4
+
+    oracle_desc = "particles (every particle of the workload), the oracle's k-d tree search on all host cores"
+
+    def oracle_rate(self, budget, seed=7):
+        from oracle import knn
+        t0 = time.perf_counter()
+        knn.kth_neighbour_distance_tree(self.xyz, self.k)
+        dt = time.perf_counter() - t0
+        import os as _os
+        return self.n_rays / dt, self.n_rays, dt, _os.cpu_count()
+
+
+def run_gpu_knn(args, ws, rank, local):
+    """The smoothing-length workload: same timing rules as run_gpu."""
+    import torch
+
+    import paper_1312_1128_gb300 as L
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = Knn()
+    wl.prepare(L, torch, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lib = L.lib()
+    for _ in range(args.warmup):
+        wl.step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    launches0 = lib.lens_kernel_launches()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ev[k][0].record()
+        wl.step()
+        ev[k][1].record()
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = lib.lens_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms, value = replica_rate(ws, wl.n_rays, float(np.mean(step_ms)), dev)
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2)):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        barrier(ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        h2d, d2h = wl.e2e()
+        b.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e, e2e_value = replica_rate(ws, wl.n_rays, float(np.mean(e2e_ms)), dev)
+    peak, basis = measured_hbm_gbs()
+    achieved = wl.BYTES_PER_PARTICLE * wl.n_rays / (float(np.mean(step_ms)) * 1e-3) / 1e9
+    line = {"metric": wl.metric, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": wl.config(ws),
+            "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_basis": basis,
+                         "algorithmic_bytes_per_particle": wl.BYTES_PER_PARTICLE,
+                         "kernels": "bbox, keys, radix sort, gather, query (one call per step)"},
+            "clocks": clk, "gpu_launches": int(launches)}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r, done_n, dt, cores = wl.oracle_rate(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": r, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{done_n} {wl.oracle_desc}, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_gpu_refine(args, ws, rank, local):
     """The refinement workload: same timing rules as run_gpu (warm-up, L2
     flush between timed steps, CUDA events, max over ranks, clocks)."""
@@ -704,7 +822,7 @@ def run_gpu_refine(args, ws, rank, local):
 
 
 WORKLOADS = {"nfw_sph": NfwSph, "mixed_batches": MixedBatches, "microlensing": Microlensing, "fit": Fit,
-             "refine": Refine}
+             "refine": Refine, "knn": Knn}
 
 
 def _oracle_loop(oracle, comps, rx, ry, _, budget_s, seed, nthreads=0):
@@ -909,7 +1027,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["nfw_sph", "mixed_batches", "microlensing", "fit", "refine"],
+    ap.add_argument("--workload", choices=["nfw_sph", "mixed_batches", "microlensing", "fit", "refine", "knn"],
                     default="nfw_sph",
                     help="nfw_sph (default) is the headline; the others measure the batched, "
                          "microlensing and differentiable paths")
@@ -939,6 +1057,8 @@ def main():
         ws, rank, local = dist_setup("nccl")
         if args.workload == "refine":
             run_gpu_refine(args, ws, rank, local)
+        elif args.workload == "knn":
+            run_gpu_knn(args, ws, rank, local)
         else:
             run_gpu(args, ws, rank, local)
     if ws > 1:

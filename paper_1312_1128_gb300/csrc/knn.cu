@@ -3,13 +3,15 @@
 // particles of the lens are given (the paper prefers the 3D neighbour
 // distance).
 //
-// Particles are sorted by 63-bit 3D Morton keys of a cube around them.  A
-// query first takes the k nearest among its 2k neighbours in key order: an
-// upper bound R on the k-th distance.  With the octree level whose cell side
-// is at least R (plus a margin for the quantisation), every particle within R
-// lies in the 3 x 3 x 3 cells around the query's cell; each cell is one run of
-// the sorted keys, found by binary search, and scanning them gives the exact
-// k nearest.  One thread per particle keeps its k smallest squared distances.
+// Particles are sorted by 63-bit 3D Morton keys of a cube around them, which
+// makes every octree cell one run of the sorted keys.  A query first takes
+// the k nearest among its 2k neighbours in key order (an upper bound on the
+// k-th distance), then descends the implicit octree from the root: a cell's
+// run splits into its children's runs by binary search within it, children
+// whose box lies farther than the current k-th distance are skipped, the
+// nearest child is visited first, and cells of at most kKnnLeaf particles
+// are scanned.  One thread per particle keeps its k smallest squared
+// distances; the search is exact.
 #include <cmath>
 
 #include "common.cuh"
@@ -17,8 +19,10 @@
 
 namespace lens {
 
-constexpr int kKnnMax = 64;   // largest k
-constexpr int kKnnBits = 21;  // key bits per axis
+constexpr int kKnnMax = 64;    // largest k
+constexpr int kKnnBits = 21;   // key bits per axis
+constexpr int kKnnLeaf = 16;   // a cell with at most this many particles is scanned
+constexpr int kKnnStack = 8 * kKnnBits + 8;  // depth-first: at most 7 siblings pending per level
 
 // Spread the 21 bits of v to every third bit.
 LENS_DEV uint64_t spread3(uint32_t v)
@@ -33,6 +37,18 @@ LENS_DEV uint64_t spread3(uint32_t v)
 }
 
 LENS_DEV uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) { return spread3(x) | spread3(y) << 1 | spread3(z) << 2; }
+
+// Inverse of spread3: every third bit back to 21 contiguous bits.
+LENS_DEV uint32_t compact3(uint64_t x)
+{
+    x &= 0x1249249249249249ull;
+    x = (x | x >> 2) & 0x10c30c30c30c30c3ull;
+    x = (x | x >> 4) & 0x100f00f00f00f00full;
+    x = (x | x >> 8) & 0x1f0000ff0000ffull;
+    x = (x | x >> 16) & 0x1f00000000ffffull;
+    x = (x | x >> 32) & 0x1fffffull;
+    return (uint32_t)x;
+}
 
 struct KnnCube {
     float ox, oy, oz;  // lower corner
@@ -129,66 +145,105 @@ struct KSmallest {
     }
 };
 
-LENS_DEV int64_t lower_bound_u64(const uint64_t* a, int64_t n, uint64_t key)
+LENS_DEV uint32_t lower_bound_u64(const uint64_t* a, uint32_t lo, uint32_t hi, uint64_t key)
 {
-    int64_t lo = 0, hi = n;
     while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
+        const uint32_t mid = lo + ((hi - lo) >> 1);
         if (a[mid] < key) lo = mid + 1;
         else hi = mid;
     }
     return lo;
 }
 
+// A pending octree cell: key prefix (3 level bits), level, run [a, b).
+struct KnnNode {
+    uint64_t prefix;
+    uint32_t a, b;
+    int level;
+};
+
 __global__ void __launch_bounds__(128)
-k_knn_query(const float4* sp, const uint64_t* keys, int64_t n, int k, KnnCube c, float* r_out, uint32_t* err)
+k_knn_query(const float4* sp4, const uint64_t* keys, int64_t n, int k, KnnCube c, float* r_out, uint32_t* err)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float4 p = sp[i];
+    const float4 p = sp4[i];
     KSmallest S;
     // upper bound: the k nearest among the 2k neighbours in key order
     S.reset(k, INFINITY);
     const int64_t w0 = i - k > 0 ? i - k : 0, w1 = i + k + 1 < n ? i + k + 1 : n;
     for (int64_t j = w0; j < w1; ++j) {
         if (j == i) continue;
-        const float4 q = sp[j];
+        const float4 q = sp4[j];
         const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
         S.offer(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
     }
-    // rounding of the bound and of the quantisation: inflate R by both
-    const float q1 = 1.0f / c.inv_q;
-    const float R = sqrtf(S.worst) * 1.000001f + 2.0f * q1;
-    const float R2 = R * R;
-    int level = 0;
-    if (R < c.side) {
-        level = (int)floorf(log2f(c.side / R));
-        level = level < 0 ? 0 : (level > kKnnBits ? kKnnBits : level);
-        while (level > 0 && c.side / (float)(1u << level) < R) --level;  // cell side >= R
-    }
-    const int shift = kKnnBits - level;
-    const int64_t ncell = (int64_t)1 << level;
-    const int64_t cx = quantise(p.x, c.ox, c.inv_q) >> shift, cy = quantise(p.y, c.oy, c.inv_q) >> shift,
-                  cz = quantise(p.z, c.oz, c.inv_q) >> shift;
+    // descend the octree with the bound as the initial search radius
+    // (inflated for the rounding of the squared distances)
+    const float R2 = S.worst * 1.000002f;
     S.reset(k, R2);
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int64_t ax = cx + dx, ay = cy + dy, az = cz + dz;
-                if (ax < 0 || ay < 0 || az < 0 || ax >= ncell || ay >= ncell || az >= ncell) continue;
-                const uint64_t prefix = morton3((uint32_t)ax, (uint32_t)ay, (uint32_t)az);
-                const uint64_t kmin = prefix << (3 * shift);
-                const uint64_t kmax = (prefix + 1) << (3 * shift);
-                const int64_t a = lower_bound_u64(keys, n, kmin), b = lower_bound_u64(keys, n, kmax);
-                for (int64_t j = a; j < b; ++j) {
-                    if (j == i) continue;
-                    const float4 q = sp[j];
-                    const float ddx = q.x - p.x, ddy = q.y - p.y, ddz = q.z - p.z;
-                    S.offer(fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz)));
+    const float qlen = 1.0f / c.inv_q;  // length of one quantum
+    KnnNode stack[kKnnStack];
+    int sp = 0;
+    stack[sp++] = KnnNode{0ull, 0u, (uint32_t)n, 0};
+    while (sp > 0) {
+        const KnnNode nd = stack[--sp];
+        if (nd.b - nd.a <= (uint32_t)kKnnLeaf || nd.level == kKnnBits) {
+            for (uint32_t j = nd.a; j < nd.b; ++j) {
+                if ((int64_t)j == i) continue;
+                const float4 q = sp4[j];
+                const float ddx = q.x - p.x, ddy = q.y - p.y, ddz = q.z - p.z;
+                S.offer(fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz)));
+            }
+            continue;
+        }
+        // children, nearest first: pushed in decreasing distance
+        const int cl = nd.level + 1, shift = kKnnBits - cl;
+        const float side = qlen * (float)(1u << shift);
+        float cd[8];
+        uint32_t ca[8], cb[8];
+        int order[8], m = 0;
+        uint32_t lo = nd.a;
+        for (int ch = 0; ch < 8; ++ch) {
+            const uint64_t pre = nd.prefix * 8 + ch;
+            const uint32_t hi = ch == 7 ? nd.b : lower_bound_u64(keys, lo, nd.b, (pre + 1) << (3 * shift));
+            if (hi > lo) {
+                // the child's box, with a quantum of margin on every side
+                const float bx = c.ox + qlen * (float)(compact3(pre) << shift) - qlen;
+                const float by = c.oy + qlen * (float)(compact3(pre >> 1) << shift) - qlen;
+                const float bz = c.oz + qlen * (float)(compact3(pre >> 2) << shift) - qlen;
+                const float ex = fmaxf(fmaxf(bx - p.x, p.x - (bx + side + 2.0f * qlen)), 0.0f);
+                const float ey = fmaxf(fmaxf(by - p.y, p.y - (by + side + 2.0f * qlen)), 0.0f);
+                const float ez = fmaxf(fmaxf(bz - p.z, p.z - (bz + side + 2.0f * qlen)), 0.0f);
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                if (d2 <= S.worst) {
+                    cd[m] = d2;
+                    ca[m] = lo;
+                    cb[m] = hi;
+                    order[m] = ch;
+                    ++m;
                 }
             }
+            lo = hi;
+        }
+        // insertion sort by decreasing distance, then push (nearest on top)
+        for (int u = 1; u < m; ++u)
+            for (int v = u; v > 0 && cd[v] > cd[v - 1]; --v) {
+                float td = cd[v]; cd[v] = cd[v - 1]; cd[v - 1] = td;
+                uint32_t ta = ca[v]; ca[v] = ca[v - 1]; ca[v - 1] = ta;
+                uint32_t tb = cb[v]; cb[v] = cb[v - 1]; cb[v - 1] = tb;
+                int to = order[v]; order[v] = order[v - 1]; order[v - 1] = to;
+            }
+        for (int u = 0; u < m; ++u) {
+            if (sp >= kKnnStack) {
+                atomicOr(err, 4u);  // cannot happen: at most 7 pending siblings per level
+                break;
+            }
+            stack[sp++] = KnnNode{nd.prefix * 8 + order[u], ca[u], cb[u], cl};
+        }
+    }
     if (S.cnt < k) {
-        atomicOr(err, 2u);  // cannot happen: the bound's k particles lie in these cells
+        atomicOr(err, 2u);  // cannot happen: the bound's k particles are within the radius
         r_out[__float_as_uint(p.w)] = NAN;
         return;
     }
