@@ -11,6 +11,7 @@ Functions
 eval_component(comp, x, y)      one component's (a1, a2, kappa, g1, g2)
 direct_sum(comps, rx, ry)       Sec. 5.1 theta=0 limit: sum over all components
 direct_vjp(comps, rx, ry, G)    gradient of a loss of alpha w.r.t. (m, x, y)
+potential_component / direct_potential   lensing potential psi (Eq. alpha, Eq. timedelay)
 PaperTree(comps, leaf_max, th)  Sec. 3.2 tree, evaluated ray by ray, with counts
 refine.refine_cells(...)        Sec. 3.4 cell interpolation with A from App. A (numpy)
 knn.kth_neighbour_distance(...)  Sec. 3.1 3D smoothing lengths (brute force / cKDTree)
@@ -64,6 +65,10 @@ def _load():
         lib.or_eval_component.restype = None
         lib.or_direct_sum.argtypes = [vp, i64, vp, vp, i64, vp, vp, i32]
         lib.or_direct_sum.restype = i32
+        lib.or_potential_component.argtypes = [vp, d, d]
+        lib.or_potential_component.restype = d
+        lib.or_direct_potential.argtypes = [vp, i64, vp, vp, i64, vp, vp, i32]
+        lib.or_direct_potential.restype = i32
         lib.or_direct_vjp.argtypes = [vp, i64, vp, vp, i64, vp, vp, i32]
         lib.or_direct_vjp.restype = i32
         lib.or_tree_build.argtypes = [vp, i64, i32, d]
@@ -123,6 +128,27 @@ def direct_sum(comps, rx, ry, nthreads: int = 0, with_absum: bool = False):
     ab = np.zeros((rx.size, 5)) if with_absum else None
     lib.or_direct_sum(_ptr(c), c.size, _ptr(rx), _ptr(ry), rx.size, _ptr(out),
                       _ptr(ab) if ab is not None else None, int(nthreads))
+    return (out, ab) if with_absum else out
+
+
+def potential_component(comp, x: float, y: float) -> float:
+    """One component's lensing potential psi at (x, y) (alpha = grad psi)."""
+    lib = _load()
+    c = np.ascontiguousarray(np.asarray(comp, COMP_DTYPE).reshape(-1)[:1])
+    return lib.or_potential_component(_ptr(c), float(x), float(y))
+
+
+def direct_potential(comps, rx, ry, nthreads: int = 0, with_absum: bool = False):
+    """Direct FP64 sum of the lensing potential over all components (Eq.
+    alpha, Eq. timedelay); optionally also sum |term| per ray."""
+    lib = _load()
+    c = np.ascontiguousarray(np.asarray(comps, COMP_DTYPE).reshape(-1))
+    rx = np.ascontiguousarray(rx, dtype=np.float64).reshape(-1)
+    ry = np.ascontiguousarray(ry, dtype=np.float64).reshape(-1)
+    out = np.zeros(rx.size)
+    ab = np.zeros(rx.size) if with_absum else None
+    lib.or_direct_potential(_ptr(c), c.size, _ptr(rx), _ptr(ry), rx.size, _ptr(out),
+                            _ptr(ab) if ab is not None else None, int(nthreads))
     return (out, ab) if with_absum else out
 
 

@@ -170,6 +170,93 @@ void or_eval_component(const or_comp* c, double x, double y, double out[5])
     out[4] = -(kb - kap) * s2;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Lensing potential (Eq. alpha: alpha = grad psi; Eq. timedelay uses psi).  */
+/* For an axisymmetric component psi(r) = psi(r_e) - int_r^{r_e} Mt(r')/r' dr'*/
+/* with Mt the enclosed m-unit mass above; outside its support every finite  */
+/* component is a point mass, psi = m ln r.  The additive constant is fixed   */
+/* by that choice (SIS: psi = r_E r).                                         */
+/* ------------------------------------------------------------------------ */
+
+/* Ein(u) = int_0^u (1 - e^-t)/t dt: its alternating series for u < 8, and
+ * Ein = E1(u) + ln u + gamma_E with the continued fraction of E1 beyond. */
+static double or_ein(double u)
+{
+    if (u < 8.0) {
+        double s = 0.0, term = 1.0;  /* term = u^k / k! */
+        for (int k = 1; k < 200; ++k) {
+            term *= u / k;
+            double add = ((k & 1) ? term : -term) / k;
+            s += add;
+            if (fabs(add) < 1e-18 * fabs(s)) break;
+        }
+        return s;
+    }
+    /* E1(u) = e^-u / (u + 1 - 1/(u + 3 - 4/(u + 5 - 9/(u + 7 - ...)))) (modified Lentz) */
+    double b = u + 1.0, cc = 1e300, d = 1.0 / b, h = d;
+    for (int i = 1; i < 300; ++i) {
+        double an = -(double)i * i;
+        b += 2.0;
+        d = 1.0 / (an * d + b);
+        cc = b + an / cc;
+        double del = cc * d;
+        h *= del;
+        if (fabs(del - 1.0) < 1e-16) break;
+    }
+    return h * exp(-u) + log(u) + 0.57721566490153286061;
+}
+
+/* NFW potential shape H(x) = int g(x)/x dx = ln^2(x/2)/2 - (1 - x^2) F(x)^2/2
+ * (H(0) = 0).  For x < 1/2 the two squares nearly cancel; there
+ * arccosh(1/x) = L + e with L = ln(2/x), e = log1p(-x^2 / (2 (1 + t))),
+ * t = sqrt(1 - x^2), and H = -e (2L + e)/2. */
+static double nfw_H(double x)
+{
+    if (x <= 0.0) return 0.0;
+    if (x < 0.5) {
+        double t = sqrt(1.0 - x * x), L = log(2.0 / x);
+        double e = log1p(-x * x / (2.0 * (1.0 + t)));
+        return -0.5 * e * (2.0 * L + e);
+    }
+    double lx = log(0.5 * x), F = nfw_F(x);
+    return 0.5 * lx * lx - 0.5 * (1.0 - x * x) * F * F;
+}
+
+/* psi(r) of one component (r >= 0; a point mass and an SIS give 0 at r = 0). */
+static double or_potential_profile(const or_comp* c, double r)
+{
+    switch (c->type) {
+    case OR_POINT:
+        return r > 0.0 ? c->m * log(r) : 0.0;
+    case OR_GAUSS: {
+        double sig = c->p0, q = c->p1, re = q * sig;
+        if (r >= re) return c->m * log(r);
+        double Nq = -expm1(-0.5 * q * q), u = r * r / (2.0 * sig * sig);
+        return c->m * log(re) - c->m / (2.0 * Nq) * (or_ein(0.5 * q * q) - or_ein(u));
+    }
+    case OR_NFW: {
+        double rs = c->p0, Rmax = c->p1;
+        if (r >= Rmax) return c->m * log(r);
+        double X = Rmax / rs;
+        return c->m * log(Rmax) - c->m / nfw_g(X) * (nfw_H(X) - nfw_H(r / rs));
+    }
+    case OR_SIS:
+        return c->p0 * r;
+    case OR_DISK: {
+        double R = c->p0;
+        if (r >= R) return c->m * log(r);
+        return c->m * (log(R) + 0.5 * (r * r / (R * R) - 1.0));
+    }
+    }
+    return 0.0;
+}
+
+double or_potential_component(const or_comp* c, double x, double y)
+{
+    double dx = x - c->x, dy = y - c->y;
+    return or_potential_profile(c, sqrt(dx * dx + dy * dy));
+}
+
 /* Neumaier compensated accumulator. */
 typedef struct { double s, c; } nsum;
 static inline void nadd(nsum* a, double v)
@@ -202,6 +289,28 @@ int or_direct_sum(const or_comp* comps, int64_t nc, const double* rx, const doub
             out[5 * i + q] = acc[q].s + acc[q].c;
             if (absum) absum[5 * i + q] = ab[q];
         }
+    }
+    return 0;
+}
+
+/* Direct sum of the potential (Neumaier), with sum |term| (optional). */
+int or_direct_potential(const or_comp* comps, int64_t nc, const double* rx, const double* ry,
+                        int64_t nr, double* psi, double* absum, int nthreads)
+{
+#ifdef _OPENMP
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
+    for (int64_t i = 0; i < nr; ++i) {
+        nsum acc = {0, 0};
+        double ab = 0.0;
+        for (int64_t j = 0; j < nc; ++j) {
+            double t = or_potential_component(&comps[j], rx[i], ry[i]);
+            nadd(&acc, t);
+            ab += fabs(t);
+        }
+        psi[i] = acc.s + acc.c;
+        if (absum) absum[i] = ab;
     }
     return 0;
 }
