@@ -271,6 +271,24 @@ lens_status lens_shoot_rays_direct_noalloc(lens_tree* tree, double origin_x, dou
                                            int64_t n, void* alpha1, void* alpha2, void* kappa,
                                            void* gamma1, void* gamma2, int32_t flags, void* stream);
 
+/*
+ * lens_shoot_potential -- the lensing potential psi (Eq. alpha: alpha =
+ * grad psi), with the deflection, for the time delay of Eq. timedelay
+ * (delta t = |alpha|^2 / 2 - psi on a single plane), by the tree walk of
+ * lens_shoot_rays: far cells add the monopole + quadrupole potential
+ * M ln|w| - Re(Q2 / (2 w^2)) about their centre of mass; particles and halos
+ * their own potentials; big lists (full - softened point).  Each component's
+ * additive constant is fixed by psi = m ln r outside its support (SIS:
+ * r_E r).  LENS_DIRECT sums every particle's potential instead of walking.
+ *   Same ray arguments as lens_shoot_rays; psi (required), alpha1, alpha2
+ *   (may be NULL): device arrays of n values in the tree's precision.
+ *   flags: LENS_DIRECT, LENS_ACCUMULATE only.
+ * Asynchronous; errors as lens_shoot_rays.
+ */
+lens_status lens_shoot_potential(lens_tree* tree, double origin_x, double origin_y, const void* ray_dx,
+                                 const void* ray_dy, int32_t ray_dtype, int64_t n, void* psi, void* alpha1,
+                                 void* alpha2, int32_t flags, void* stream);
+
 /* lens_refine_cells modes (see below). */
 enum { LENS_REFINE_KAPPA_GAMMA = 0, LENS_REFINE_DEFLECTION = 1 };
 

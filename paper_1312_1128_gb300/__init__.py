@@ -99,6 +99,7 @@ def lib():
     L.lens_refine_cells.argtypes = [d, d, d, i64, i64, vp, vp, i32, vp, vp, vp, vp, i64, i32, d, i32, vp, vp,
                                     vp, vp, vp]
     L.lens_smoothing_lengths.argtypes = [vp, i64, i32, vp, vp]
+    L.lens_shoot_potential.argtypes = [vp, d, d, vp, vp, i32, i64, vp, vp, vp, i32, vp]
     L.lens_kernel_launches.argtypes = []
     L.lens_kernel_launches.restype = ctypes.c_int64
     L.lens_free_tree.argtypes = [vp]
@@ -109,7 +110,8 @@ def lib():
                  "lens_shoot_rays_backward", "lens_reserve", "lens_sync_status",
                  "lens_tree_get_info", "lens_tree_export", "lens_fp32_peak", "lens_api_version",
                  "lens_tree_counters", "lens_last_timing", "lens_autotune",
-                 "lens_shoot_rays_direct_noalloc", "lens_refine_cells", "lens_smoothing_lengths"]:
+                 "lens_shoot_rays_direct_noalloc", "lens_refine_cells", "lens_smoothing_lengths",
+                 "lens_shoot_potential"]:
         getattr(L, name).restype = ctypes.c_int32
     _lib = L
     return L
@@ -305,6 +307,22 @@ class Lens:
         _check(lib().lens_shoot_rays(self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx),
                                      _dev_ptr(dy), rd, n, *[_dev_ptr(o) for o in out], int(flags),
                                      _stream_ptr(stream)))
+        return out
+
+    def potential(self, dx, dy, origin=(0.0, 0.0), flags: int = 0, out=None, stream=None):
+        """Lensing potential psi and alpha1, alpha2 at rays origin + (dx, dy)
+        (lens_shoot_potential; the time delay is |alpha|^2/2 - psi)."""
+        torch = _torch()
+        n = dx.numel()
+        if dy.numel() != n or dx.dtype != dy.dtype:
+            raise ValueError("dx, dy must match in size and dtype")
+        dt = torch.float64 if self.precision == "fp64" else torch.float32
+        if out is None:
+            out = [torch.empty(n, dtype=dt, device=dx.device) for _ in range(3)]
+        rd = F32 if dx.dtype == torch.float32 else F64
+        _check(lib().lens_shoot_potential(self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx), _dev_ptr(dy),
+                                          rd, n, *[_dev_ptr(o) if o is not None else None for o in out],
+                                          int(flags), _stream_ptr(stream)))
         return out
 
     def shoot_direct_noalloc(self, dx, dy, out, origin=(0.0, 0.0), flags: int = 0, stream=None):

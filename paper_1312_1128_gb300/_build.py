@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(PKG, "liblens.so")
 
-SOURCES = ["walk.cu", "walk_ws.cu", "build.cu", "backward.cu", "sort.cu", "batch.cu", "refine.cu", "knn.cu", "api.cu"]
+SOURCES = ["walk.cu", "walk_ws.cu", "build.cu", "backward.cu", "sort.cu", "batch.cu", "refine.cu", "knn.cu", "psi.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

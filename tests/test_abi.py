@@ -103,3 +103,13 @@ def test_smoothing_lengths_argument_checks():
     for n, k, arr in [(100, 0, fake), (100, 65, fake), (-1, 8, fake), (32, 32, fake), (5, 32, fake),
                       (100, 8, None), (1 << 33, 8, fake)]:
         assert lt.lens_smoothing_lengths(arr, n, k, arr, None) == 1, (n, k)
+
+
+def test_shoot_potential_argument_checks():
+    """lens_shoot_potential rejects a NULL tree before anything else."""
+    import paper_1312_1128_gb300 as L
+    lt = L.lib()
+    fake = ctypes.c_void_p(16)  # never dereferenced: every case fails first
+    for flags in (0, 1, 8):
+        assert lt.lens_shoot_potential(None, 0.0, 0.0, fake, fake, 0, 10, fake, None, None, flags, None) == 1
+    assert b"tree" in lt.lens_last_error()
