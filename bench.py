@@ -53,6 +53,14 @@ FLOPS_ALPHA = {"far_cells": 31, "near_point": 11, "near_full": 20, "big_correcti
 FLOPS_ADJOINT = {"far_cells": 56, "near_point": 31, "near_full": 42, "big_corrections": 37}
 
 
+# the potential walk's interactions (psi.cu, potential.cuh) counted the same
+# way, frozen before tuning: a far cell's M ln|w| - Re(Q2/2w^2) with its
+# deflection (46), a point's m ln r with its deflection (15), a truncated
+# Gaussian's potential inside its support with the Ein series as a 20-term
+# Horner polynomial (68), a big-list entry's (full - softened point) (77)
+FLOPS_PSI = {"far_cells": 46, "near_point": 15, "near_full": 68, "big_corrections": 77}
+
+
 WALK_SOURCES = ("walk.cu", "walk_dev.cuh", "profiles.cuh")
 
 
@@ -292,6 +300,74 @@ class NfwSph(Workload):
                 "oracle_paper_tree": {"value": idx.size / te, "unit": UNIT, "cores": oracle.max_threads(),
                                       "build_s": tb, "theta": self.theta,
                                       "sample": f"{idx.size} random rays, {te:.1f} s (build excluded)"}}
+
+
+class Potential(NfwSph):
+    """The headline's lens (1e6 smoothed NFW particles, 2048^2 grid, theta
+    0.3) shooting the lensing potential with the deflection (Eq. alpha, Eq.
+    timedelay); step = tree build + ray grouping + potential walk."""
+    name = "potential_nfw_sph_1e6_2048sq"
+    FLOPS = FLOPS_PSI
+    metric = "rays/sec (psi + alpha) at stated error"
+    oracle_desc = ("random rays of the workload, FP64 direct potential and deflection over every lens "
+                   "component (the tree's theta -> 0 limit)")
+
+    def flops_per_ray(self):
+        # the potential walk visits the same cells, leaves and big lists as
+        # the headline's walk over the same tree
+        with open(os.path.join(ROOT, "tests", "golden", "useful_counts.json")) as f:
+            c = json.load(f)[WORKLOAD][str(self.theta)]
+        return sum(self.FLOPS[k] * c[k] for k in self.FLOPS)
+
+    def config(self, ws):
+        return {**bench_config(ws), "workload": self.name, "outputs": "psi, alpha1, alpha2"}
+
+    def prepare(self, L, torch, dev):
+        super().prepare(L, torch, dev)
+        self.outs = self.outs[:3]
+        self.hout = self.hout[:3]
+
+    def tune(self):
+        """Group size by the potential walk's own time (32 or 64 rays)."""
+        best = None
+        for g in (32, 64):
+            lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta, group_rays=g)
+            t = []
+            for _ in range(3):
+                lens.potential(self.rx, self.ry, flags=self.L.TIMING, out=self.outs)
+                t.append(lens.last_timing()[1])
+            lens.close()
+            if best is None or min(t) < best[0]:
+                best = (min(t), g)
+        self.group = best[1]
+        self.walk = "warp"
+
+    def step(self, flags):
+        lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta,
+                           group_rays=self.group)
+        lens.potential(self.rx, self.ry, flags=flags, out=self.outs)
+        return lens
+
+    def e2e(self, torch, dev):
+        """Host buffers: H2D of particles and rays, D2H of psi, alpha1, alpha2."""
+        w, L = self.w, self.L
+        for d, h in zip(self.d, self.h):
+            d.copy_(h, non_blocking=True)
+        lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group)
+        lens.potential(self.d[1], self.d[2], out=self.outs)
+        for h, o in zip(self.hout, self.outs):
+            h.copy_(o, non_blocking=True)
+        return lens, sum(x.numel() * 4 for x in self.h), 3 * self.n_rays * 4
+
+    def oracle_rate(self, budget, seed=7):
+        import oracle
+        w = self.w
+        p = w["gauss"].astype(np.float64)
+        comps = oracle.make_components(oracle.GAUSS, p[:, 0], p[:, 1], p[:, 2], p[:, 3], w["q"])
+        return _oracle_loop(oracle, comps, w["rx"], w["ry"], None, budget, seed, potential=True)
+
+    def cpu_other(self, budget=4.0):
+        return {}
 
 
 class MixedBatches(Workload):
@@ -822,19 +898,22 @@ def run_gpu_refine(args, ws, rank, local):
 
 
 WORKLOADS = {"nfw_sph": NfwSph, "mixed_batches": MixedBatches, "microlensing": Microlensing, "fit": Fit,
-             "refine": Refine, "knn": Knn}
+             "refine": Refine, "knn": Knn, "potential": Potential}
 
 
-def _oracle_loop(oracle, comps, rx, ry, _, budget_s, seed, nthreads=0):
+def _oracle_loop(oracle, comps, rx, ry, _, budget_s, seed, nthreads=0, potential=False):
     """The oracle's FP64 direct sum (as it stands) over a time-bounded random
-    sample of the workload's rays (nthreads = 0: all host cores)."""
+    sample of the workload's rays (nthreads = 0: all host cores); with
+    potential, its direct potential and the direct deflection."""
     g = lensgen.rng(seed)
     order = g.permutation(rx.size)
     done, t0, chunk = 0, time.perf_counter(), 64 if nthreads != 1 else 8
     while time.perf_counter() - t0 < budget_s and done < order.size:
         idx = order[done:done + chunk]
-        oracle.direct_sum(comps, np.asarray(rx[idx], np.float64), np.asarray(ry[idx], np.float64),
-                          nthreads=nthreads)
+        x, y = np.asarray(rx[idx], np.float64), np.asarray(ry[idx], np.float64)
+        oracle.direct_sum(comps, x, y, nthreads=nthreads)
+        if potential:
+            oracle.direct_potential(comps, x, y, nthreads=nthreads)
         done += idx.size
     dt = time.perf_counter() - t0
     return done / dt, done, dt, (oracle.max_threads() if nthreads == 0 else nthreads)
@@ -958,7 +1037,8 @@ def run_gpu(args, ws, rank, local):
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     measured_peak = L.fp32_peak(20000) / 1e12
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+    line = {"metric": getattr(wl, "metric", METRIC), "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
             "config": wl.config(ws), "tuning": {"group_rays": wl.group, "walk": wl.walk},
@@ -997,16 +1077,20 @@ def run_gpu(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         r, done_n, dt, cores = wl.oracle_rate(args.cpu_seconds)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{done_n} random rays of the workload, FP64 direct sum over "
-                                          f"every lens component, {dt:.1f} s"}
-        if hasattr(wl, "cpu_other"):
-            line["cpu_other"] = wl.cpu_other()
+                                "sample": f"{done_n} " + getattr(wl, "oracle_desc",
+                                          "random rays of the workload, FP64 direct sum over every lens "
+                                          "component") + f", {dt:.1f} s"}
+        if hasattr(wl, "cpu_other") and wl.cpu_other is not None:
+            other = wl.cpu_other()
+            if other:
+                line["cpu_other"] = other
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
 def run_once(args):
-    """One build + shoot of the workload (profiling: `ncu ... python bench.py --once`)."""
+    """One build + shoot of the headline's lens (profiling: `ncu ... python
+    bench.py --once`); with --workload potential, one potential shot."""
     import torch
 
     import paper_1312_1128_gb300 as L
@@ -1014,7 +1098,10 @@ def run_once(args):
     parts = torch.from_numpy(w["gauss"]).cuda()
     rx, ry = torch.from_numpy(w["rx"]).cuda(), torch.from_numpy(w["ry"]).cuda()
     lens = L.Lens([L.Species.gauss(parts, w["q"])], theta=THETA, group_rays=64, walk=args.walk)
-    lens.shoot(rx, ry, flags=L.TIMING | L.COUNT)
+    if args.workload == "potential":
+        lens.potential(rx, ry, flags=L.TIMING | L.COUNT)
+    else:
+        lens.shoot(rx, ry, flags=L.TIMING | L.COUNT)
     lens.sync()
     print(json.dumps({"grid": args.grid, "timing_ms": lens.last_timing(), "counters": lens.counters(),
                       "build_ms": lens.info()["build_ms"][0]}))
@@ -1027,7 +1114,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["nfw_sph", "mixed_batches", "microlensing", "fit", "refine", "knn"],
+    ap.add_argument("--workload", choices=["nfw_sph", "mixed_batches", "microlensing", "fit", "refine", "knn",
+                                           "potential"],
                     default="nfw_sph",
                     help="nfw_sph (default) is the headline; the others measure the batched, "
                          "microlensing and differentiable paths")

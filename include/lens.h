@@ -282,7 +282,9 @@ lens_status lens_shoot_rays_direct_noalloc(lens_tree* tree, double origin_x, dou
  * r_E r).  LENS_DIRECT sums every particle's potential instead of walking.
  *   Same ray arguments as lens_shoot_rays; psi (required), alpha1, alpha2
  *   (may be NULL): device arrays of n values in the tree's precision.
- *   flags: LENS_DIRECT, LENS_ACCUMULATE only.
+ *   flags: LENS_DIRECT, LENS_ACCUMULATE, LENS_TIMING (lens_last_timing then
+ *   reports this call's grouping and potential-walk times) and LENS_COUNT
+ *   (the walk counters of lens_tree_counters) only.
  * Asynchronous; errors as lens_shoot_rays.
  */
 lens_status lens_shoot_potential(lens_tree* tree, double origin_x, double origin_y, const void* ray_dx,

@@ -17,7 +17,33 @@ namespace lens {
 template <typename T> struct PsiConsts {
     T EinU;  // Ein(q^2/2) of the species (Gaussian)
     T HX;    // H(R_max / r_s) of the species (NFW)
+    T A0;    // N_q ln U_q - Ein(U_q) (Gaussian)
+    int series;  // U_q <= 5: Ein inside every support by the 20-term series
 };
+
+LENS_DEV float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <int k> LENS_DEV float2 ein_horner2(float2 u, float2 s)
+{
+    if constexpr (k < 0) {
+        return s;
+    } else {
+        constexpr float c = float(ein_coef(k));
+        return ein_horner2<k - 1>(u, __ffma2_rn(s, u, make_float2(c, c)));
+    }
+}
+
+// Ein(u) for u < 5 on a pair, the 20-term series of ein<float>
+LENS_DEV float2 ein_series2(float2 u)
+{
+    constexpr float top = float(ein_coef(19));
+    return __fmul2_rn(ein_horner2<18>(u, make_float2(top, top)), u);
+}
 
 template <int KIND, typename T, int R> struct PsiCtx {
     using value_type = T;
@@ -121,18 +147,130 @@ template <int KIND, typename T, int R> struct PsiCtx {
         }
     }
 
+    // One packed FP32 Gaussian entry (m' = m/N_q, c, w) for every ray, in the
+    // closed form of (full - point) inside the support, u = c r^2 < U_q:
+    //   psi: m'/2 (A0 + Ein(u) - N_q ln u),  kb: m' (e^-U_q - e^-u) / r^2;
+    // a ray inside the softening radius (s = r^2 w < 1) adds the difference
+    // of the softened point from the plain one: m'N_q/2 (ln s - s + 1) to psi
+    // and m'N_q (1/r^2 - w) to kb.  Zero outside the support.
+    LENS_DEV void big_packed(int i, float Nq)
+    {
+        const float nx = B->bnx[i], ny = B->bny[i], cl = B->bcl[i], mp = B->bm[i], nme = B->bme[i];
+        const float w = B->bw[i];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float wx = lx[r] + nx, wy = ly[r] + ny, r2 = fmaf(wx, wx, wy * wy);
+            const float t = r2 * cl;  // -u log2 e
+            if (!(t > -P.Uq2)) continue;
+            const float e = exp2_approx(t), u = t * -0.69314718055994530942f;
+            const float E = ein(u);
+            const float inv = r2 > 0.0f ? rcp(r2) : 0.0f;
+            float kb = -fmaf(mp, e, nme) * inv;
+            float psi = 0.5f * mp * fmaf(-Nq, __logf(u), K.A0 + E);
+            const float sw = r2 * w;
+            if (w > 0.0f && sw < 1.0f) {
+                const float mq = mp * Nq;
+                psi = 0.5f * mp * (K.A0 + E + Nq * (logf(w * B->bic[i]) - sw + 1.0f));
+                kb = fmaf(mp, (1.0f - e) * inv, -mq * w);
+            }
+            part[r][0] += psi;
+            part[r][1] = fmaf(kb, wx, part[r][1]);
+            part[r][2] = fmaf(kb, wy, part[r][2]);
+        }
+    }
+
+    // The same closed form on two entries (i, i+1) at once in FP32x2, every
+    // ray beyond both softening radii (needs U_q <= 5).  P2 accumulates psi,
+    // -alpha1, -alpha2 per entry slot.  EDGE: a ray may be outside a support,
+    // where its terms are set to 0.
+    template <bool EDGE>
+    LENS_DEV void big_pair(int i, float2 (&P2)[R][3], const float2 (&LX)[R], const float2 (&LY)[R])
+    {
+        const float2 nx = *reinterpret_cast<const float2*>(&B->bnx[i]);
+        const float2 ny = *reinterpret_cast<const float2*>(&B->bny[i]);
+        const float2 cl = *reinterpret_cast<const float2*>(&B->bcl[i]);
+        const float2 mp = *reinterpret_cast<const float2*>(&B->bm[i]);
+        const float2 nme = *reinterpret_cast<const float2*>(&B->bme[i]);
+        const float2 hmp = __fmul2_rn(mp, make_float2(0.5f, 0.5f));
+        const float nUq2 = -P.Uq2, nNqL = -P.Nq * 0.69314718055994530942f;
+        const float2 A0 = make_float2(K.A0, K.A0);
+        constexpr float nL = -0.69314718055994530942f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 wx = __fadd2_rn(LX[r], nx), wy = __fadd2_rn(LY[r], ny);
+            const float2 r2 = __ffma2_rn(wx, wx, __fmul2_rn(wy, wy));
+            const float2 t = __fmul2_rn(r2, cl);
+            float2 tc = t;
+            if (EDGE) {
+                tc.x = fmaxf(t.x, nUq2);
+                tc.y = fmaxf(t.y, nUq2);
+            }
+            const float2 e = make_float2(exp2_approx(tc.x), exp2_approx(tc.y));
+            const float2 u = __fmul2_rn(tc, make_float2(nL, nL));
+            const float2 E = ein_series2(u);
+            const float2 inv = make_float2(rcp(r2.x), rcp(r2.y));
+            float2 nkb = __fmul2_rn(__ffma2_rn(mp, e, nme), inv);
+            const float2 lg = make_float2(lg2_approx(u.x), lg2_approx(u.y));
+            float2 psi = __fmul2_rn(hmp, __ffma2_rn(make_float2(nNqL, nNqL), lg, __fadd2_rn(A0, E)));
+            if (EDGE) {
+                const bool ix = t.x > nUq2, iy = t.y > nUq2;
+                psi = make_float2(ix ? psi.x : 0.0f, iy ? psi.y : 0.0f);
+                nkb = make_float2(ix ? nkb.x : 0.0f, iy ? nkb.y : 0.0f);
+            }
+            P2[r][0] = __fadd2_rn(P2[r][0], psi);
+            P2[r][1] = __ffma2_rn(nkb, wx, P2[r][1]);
+            P2[r][2] = __ffma2_rn(nkb, wy, P2[r][2]);
+        }
+    }
+
+    // Packed FP32 Gaussian buffer: the whole-group-inside region pair by pair
+    // without tests, then the edge region pair by pair where both entries
+    // have every ray beyond their softening radii, else entry by entry.
+    LENS_DEV void flush_big_pairs(int nbuf, float Nq)
+    {
+        const int n_in = nbuf & 0xffff, n_out = nbuf >> 16;
+        float2 P2[R][3], LX[R], LY[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            LX[r] = make_float2(lx[r], lx[r]);
+            LY[r] = make_float2(ly[r], ly[r]);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) P2[r][q] = make_float2(0.0f, 0.0f);
+        }
+        int i = 0;
+        for (; i + 1 < n_in; i += 2) big_pair<false>(i, P2, LX, LY);
+        if (i < n_in) big_packed(i, Nq);
+        i = kBigCap - n_out;
+        if ((i & 1) && i < kBigCap) big_packed(i++, Nq);
+        for (; i + 1 < kBigCap; i += 2) {
+            const float2 w = *reinterpret_cast<const float2*>(&B->bw[i]);
+            if (w.x < 0.0f && w.y < 0.0f) {
+                big_pair<true>(i, P2, LX, LY);
+            } else {
+                big_packed(i, Nq);
+                big_packed(i + 1, Nq);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            part[r][0] += P2[r][0].x + P2[r][0].y;
+            part[r][1] -= P2[r][1].x + P2[r][1].y;
+            part[r][2] -= P2[r][2].x + P2[r][2].y;
+        }
+    }
+
     LENS_DEV void flush_big()
     {
         if constexpr (KIND != LENS_POINT) {
             const T Nq = P.invNq > T(0) ? T(1) / P.invNq : T(0);
             if constexpr (WalkBuf<KIND, T>::kPackedBig) {
-                const int n_in = nb & 0xffff, n_out = nb >> 16;
-                auto one = [&](int i) {
-                    const float c = -B->bcl[i] * 0.69314718055994530942f;  // bcl = -c log2 e
-                    big_one(-B->bnx[i], -B->bny[i], B->bm[i] * Nq, B->bw[i], c, T(0), T(0), T(0));
-                };
-                for (int i = 0; i < n_in; ++i) one(i);
-                for (int i = kBigCap - n_out; i < kBigCap; ++i) one(i);
+                if (K.series) {
+                    flush_big_pairs(nb, Nq);
+                } else {
+                    const int n_in = nb & 0xffff, n_out = nb >> 16;
+                    for (int i = 0; i < n_in; ++i) big_packed(i, Nq);
+                    for (int i = kBigCap - n_out; i < kBigCap; ++i) big_packed(i, Nq);
+                }
             } else {
                 for (int i = 0; i < nb; ++i) {
                     const vec4_t<T> q = B->b0[i], q1 = B->b1[i];
@@ -230,6 +368,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32) psi_kernel(WalkParams<T> P, P
             }
         }
         if (P.n_halos > 0) C.halos();
+        if (P.stats && lane == 0) {
+            const unsigned long long nr = rg.y;
+            atomicAdd(&P.stats[0], 1ull);
+            atomicAdd(&P.stats[1], (unsigned long long)c_vis);
+            atomicAdd(&P.stats[2], (unsigned long long)c_acc);
+            atomicAdd(&P.stats[3], (unsigned long long)c_near);
+            atomicAdd(&P.stats[4], (unsigned long long)c_bigs);
+            atomicAdd(&P.stats[5], (unsigned long long)c_bigk);
+            atomicAdd(&P.stats[6], nr * (unsigned long long)(c_acc + c_near + c_bigk));
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!rv[r]) continue;
@@ -304,7 +452,14 @@ static lens_status psi_typed(lens_tree* t, const ShootPlan& plan, const void* dx
     using T2 = v2_t<T>;
     Layout L = make_layout(t->ray_cap, t->batch_cap, max_slots(t));
     char* base = (char*)t->ray_scratch.ptr;
+    const bool timing = (flags & LENS_TIMING) != 0;
+    if (timing) {
+        for (int i = 0; i < 3; ++i)
+            if (!t->ev[i]) LENS_CUDA(cudaEventCreate(&t->ev[i]));
+        LENS_CUDA(cudaEventRecord(t->ev[0], s));
+    }
     if (plan.n > 0) LENS_TRY(enqueue_groups<T>(t, plan, dx, dy, dtype, s));
+    if (timing) LENS_CUDA(cudaEventRecord(t->ev[1], s));
     WalkParams<T> P{};
     P.gH = (T2*)(base + L.gH);
     P.gbox = (T4*)(base + L.gbox);
@@ -314,6 +469,7 @@ static lens_status psi_typed(lens_tree* t, const ShootPlan& plan, const void* dx
     P.n_groups = (int64_t)plan.ng;
     P.stack = (int*)(base + L.stack);
     P.err = t->d_err;
+    P.stats = (flags & LENS_COUNT) ? t->d_stats : nullptr;
     for (int q = 0; q < 3; ++q) P.out[q] = (T*)out[q];
     P.out[3] = P.out[4] = nullptr;
     uint32_t* counter = (uint32_t*)(base + L.counter);
@@ -353,7 +509,11 @@ static lens_status psi_typed(lens_tree* t, const ShootPlan& plan, const void* dx
         P.n_halos = first ? (int)t->n_halos : 0;
         P.accumulate = first ? ((flags & LENS_ACCUMULATE) ? 1 : 0) : 1;
         PsiConsts<T> K{};
-        if (st.kind == LENS_GAUSS) K.EinU = (T)ein<double>(st.Uq);
+        if (st.kind == LENS_GAUSS) {
+            K.EinU = (T)ein<double>(st.Uq);
+            K.A0 = (T)((1.0 - std::exp(-st.Uq)) * std::log(st.Uq) - ein<double>(st.Uq));
+            K.series = st.Uq <= 5.0 ? 1 : 0;
+        }
         if (st.kind == LENS_NFW) K.HX = (T)host_nfw_H(st.shape);
         launch(st.kind, K);
         first = false;
@@ -365,6 +525,10 @@ static lens_status psi_typed(lens_tree* t, const ShootPlan& plan, const void* dx
         P.n_halos = (int)t->n_halos;
         P.accumulate = (flags & LENS_ACCUMULATE) ? 1 : 0;
         launch(LENS_POINT, PsiConsts<T>{});
+    }
+    if (timing) {
+        LENS_CUDA(cudaEventRecord(t->ev[2], s));
+        t->timed = true;
     }
     LENS_CUDA(cudaGetLastError());
     return LENS_OK;
@@ -381,8 +545,9 @@ extern "C" lens_status lens_shoot_potential(lens_tree* tree, double origin_x, do
     if (!tree) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
     if (n < 0) return lens_set_error(LENS_ERR_INVALID_ARG, "n < 0");
     if (ray_dtype != LENS_F32 && ray_dtype != LENS_F64) return lens_set_error(LENS_ERR_INVALID_ARG, "bad ray dtype");
-    if (flags & ~(LENS_DIRECT | LENS_ACCUMULATE))
-        return lens_set_error(LENS_ERR_INVALID_ARG, "lens_shoot_potential takes LENS_DIRECT and LENS_ACCUMULATE only");
+    if (flags & ~(LENS_DIRECT | LENS_ACCUMULATE | LENS_TIMING | LENS_COUNT))
+        return lens_set_error(LENS_ERR_INVALID_ARG, "lens_shoot_potential takes LENS_DIRECT, LENS_ACCUMULATE, "
+                                                    "LENS_TIMING and LENS_COUNT only");
     if (n == 0) return LENS_OK;
     if (!ray_dx || !ray_dy || !psi) return lens_set_error(LENS_ERR_INVALID_ARG, "NULL ray or psi array");
     if (!std::isfinite(origin_x) || !std::isfinite(origin_y))

@@ -120,3 +120,42 @@ def test_potential_edges():
     psi, a1, a2 = lens.potential(x, x, out=[torch.empty(8, device="cuda"), None, None])
     assert a1 is None and torch.isfinite(psi).all()
     lens.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_direct_gauss_q5_both_ein_branches(prec):
+    """q = 5 puts u = r^2 / (2 sigma^2) up to 12.5: both the series (u < 5)
+    and the continued fraction (u >= 5) of Ein are taken."""
+    gp = lensgen.nfw_particles(1500, 67, fixed_sigma=0.03)
+    g = lensgen.rng(68)
+    rx = g.uniform(-0.5, 0.5, 1024)
+    ry = g.uniform(-0.5, 0.5, 1024)
+    dt = np.float64 if prec == "fp64" else np.float32
+    lens = L.Lens([L.Species.gauss(cu(gp.astype(dt)), 5.0)], theta=0.3, precision=prec)
+    psi, _, _ = lens.potential(cu(rx.astype(dt)), cu(ry.astype(dt)), flags=L.DIRECT)
+    ref, ab = oracle.direct_potential(comps_gauss(gp, 5.0), rx.astype(dt).astype(np.float64),
+                                      ry.astype(dt).astype(np.float64), with_absum=True)
+    d = np.abs(psi.cpu().numpy().astype(np.float64) - ref)
+    bar = 1e-12 * ab if prec == "fp64" else 8 * EPS32 * ab + 1e-7 * np.abs(ref)
+    assert np.all(d <= bar), (d / ab).max()
+    lens.close()
+
+
+def test_potential_timing_and_counters():
+    """LENS_TIMING and LENS_COUNT on the potential walk: positive times, and
+    the same interaction counts as the deflection walk over the same tree."""
+    parts = lensgen.nfw_particles(20000, 7, nsph=32)
+    g = lensgen.rng(9)
+    rx = cu(g.uniform(-1, 1, 8192).astype(np.float32))
+    ry = cu(g.uniform(-1, 1, 8192).astype(np.float32))
+    lens = L.Lens([L.Species.gauss(cu(parts), 3.0)], theta=0.3, group_rays=32, walk="warp")
+    lens.potential(rx, ry, flags=L.TIMING | L.COUNT)
+    gm, wm = lens.last_timing()
+    assert gm > 0 and wm > 0
+    c_psi = lens.counters()
+    lens.shoot(rx, ry, flags=L.COUNT)
+    lens.sync()
+    c_fwd = lens.counters()
+    for k in ("groups", "visited", "cells", "leaf_particles", "big_kept", "ray_interactions"):
+        assert c_psi[k] == c_fwd[k], k
+    lens.close()
