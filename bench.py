@@ -85,6 +85,20 @@ def walk_src_hash(names=None):
     return h.hexdigest()[:16]
 
 
+PSI_SOURCES = ("psi.cu", "potential.cuh", "walk_dev.cuh", "profiles.cuh")
+
+
+def psi_traffic():
+    """DRAM bytes per potential-walk launch from the committed ncu capture, if
+    its sources are unchanged since it was taken."""
+    p = os.path.join(ROOT, "profiles", "psi_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    return d.get("bytes_per_launch") if d.get("psi_src_sha256_16") == walk_src_hash(PSI_SOURCES) else None
+
+
 def refine_traffic():
     """DRAM bytes per refinement step (the k_refine launch) from the committed ncu
     capture, if refine.cu is unchanged since it was taken."""
@@ -1046,7 +1060,8 @@ def run_gpu(args, ws, rank, local):
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": walk_traffic() if args.workload == "nfw_sph" else None,
+                         "traffic": {"nfw_sph": walk_traffic, "potential": psi_traffic}.get(
+                             args.workload, lambda: None)(),
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                                        f"{sm_max:.0f} MHz (max SM clock)",
                          "fp32_ffma_measured": measured_peak,
@@ -1128,10 +1143,11 @@ def main():
     ap.add_argument("--walk", choices=["warp", "pairs"], default="warp",
                     help="walk form of --once (the headline's autotuned choice is warp)")
     ap.add_argument("--print-walk-hash", action="store_true",
-                    help="print the hash of the walk sources that profiles/walk_traffic.json is keyed by")
+                    help="print the hash of the walk sources that profiles/walk_traffic.json is keyed by "
+                         "(with --workload potential: of the potential walk's, profiles/psi_traffic.json)")
     args = ap.parse_args()
     if args.print_walk_hash:
-        print(walk_src_hash())
+        print(walk_src_hash(PSI_SOURCES if args.workload == "potential" else None))
         return
     if args.once:
         run_once(args)
