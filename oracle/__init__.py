@@ -15,6 +15,8 @@ potential_component / direct_potential   lensing potential psi (Eq. alpha, Eq. t
 PaperTree(comps, leaf_max, th)  Sec. 3.2 tree, evaluated ray by ray, with counts
 refine.refine_cells(...)        Sec. 3.4 cell interpolation with A from App. A (numpy)
 knn.kth_neighbour_distance(...)  Sec. 3.1 3D smoothing lengths (brute force / cKDTree)
+images.find_images(...)         Sec. 4 image finding by grid refinement (pure Python)
+images.sis_finite_source_mu     App. B finite-source SIS magnification (quadrature)
 
 Components are a numpy structured array of ``COMP_DTYPE`` (see
 ``make_components``); types follow ``POINT, GAUSS, NFW, SIS, DISK``.
