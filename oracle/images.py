@@ -22,10 +22,12 @@ The readings (where the paper leaves a choice):
   I1 a cell (L, i, j) has side h_L = S / (N 3^L) and centre
      (x0 + (i + 1/2) h_L, y0 + (j + 1/2) h_L); refining makes its 9 children
      (L+1, 3i+a, 3j+b); the middle child keeps the parent's ray (same centre).
-  I2 "source size" of a circle is its diameter D: telescoping starts at
-     D_0 = h_0 / sqrt(mu_min) and divides by 3 while above 2R, then uses 2R;
-     at each size, cells with a source point inside (|y - y_c| < D/2) and
-     h_L > D sqrt(mu_min) / 3 are refined, repeatedly, until none remain.
+  I2 the "source size" of a circle is its radius: telescoping starts at
+     r_0 = h_0 / sqrt(mu_min) (an image of magnification mu_min then has the
+     radius of a coarse cell and always holds a grid point) and divides by 3
+     while above R, then uses R; at each size r, cells with a source point
+     inside (|y - y_c| < r) and h_L > r sqrt(mu_min) / 3 are refined,
+     repeatedly, until none remain.
   I3 neighbours share an edge; an image is a connected set of image cells.
   I4 inner border: image cells with a non-image neighbour; outer border:
      non-image cells with an image neighbour (of each image they touch).
@@ -248,22 +250,21 @@ def find_images(alpha, sources, prm: AmrParams, with_cells=False):
         yc = (ycx, ycy)
         g = _Grid(prm, alpha)
         # telescoping (I2)
-        d_target = 2.0 * R
-        d = h0 / smu
-        if d < d_target:
-            d = d_target
+        r = h0 / smu
+        if r < R:
+            r = R
         while True:
-            thr = d * smu / 3.0
+            thr = r * smu / 3.0
             while True:
-                sel = [c for c in g.inside(yc, 0.5 * d)
+                sel = [c for c in g.inside(yc, r)
                        if cell_size(prm, c[0]) > thr and c[0] < prm.l_max]
                 if not sel or g.refine(sel) == 0:
                     break
-            if d <= d_target:
+            if r <= R:
                 break
-            d = d / 3.0
-            if d < d_target:
-                d = d_target
+            r = r / 3.0
+            if r < R:
+                r = R
         # uniform step (I5)
         while True:
             imgs, inner, outer = _images(g, yc, R)

@@ -103,7 +103,7 @@ def test_neighbours_match_geometry():
 
 # ------------------------------------------------------------ the images
 
-CASES = [(0.5, 0.1), (1.5, 0.1), (0.0, 0.1), (1.9, 0.05), (0.5, 0.01)]
+CASES = [(0.5, 0.1), (1.5, 0.1), (0.1, 0.9), (1.9, 0.05)]
 
 
 @pytest.fixture(scope="module")
