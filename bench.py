@@ -781,6 +781,143 @@ class Knn:
         return self.n_rays / dt, self.n_rays, dt, _os.cpu_count()
 
 
+class Images:
+    """Sec. 4 / Sec. 5.2 image finding: the paper's SIS test -- an SIS of
+    r_e = 1, a 64 x 64 initial grid over 20 r_e x 20 r_e, mu_min = 0.01,
+    uniform circular sources of radius 0.1, 0.01 and 1e-4 r_e with their
+    centres at 0, 0.1, ..., 2 r_e (62 sources: the smallest from 0.1 r_e),
+    all images of every source refined until their largest border cell is
+    5e-4 of their area; step = one lens_find_images call for all sources."""
+    name = "images_sis_62src"
+    metric = "sources/sec (all images and magnifications of uniform sources, Sec. 4; SIS test of Sec. 5.2)"
+    unit = "sources/s"
+    # algorithmic bytes per cell of one image-labelling pass (the dominant
+    # kernels): neighbours (leaf fields 21 in, 4 neighbour keys 32, 16 out),
+    # union-find (init 9, unite 41, roots 12), the rank scan (8), labels (13),
+    # borders (37)
+    BYTES_PER_LABEL_CELL = 69 + 9 + 41 + 12 + 8 + 13 + 37
+    GRID = dict(x0=-10.0, y0=-10.0, side=20.0, n=64, l_max=12, mu_min=0.01, f_area=5e-4, n_min=50)
+
+    def __init__(self):
+        src = []
+        for R in (0.1, 0.01, 1e-4):
+            for b in np.round(np.linspace(0.0, 2.0, 21), 6):
+                if R < 1e-3 and b == 0.0:
+                    continue
+                src.append((float(b), 0.0, R))
+        self.src = np.array(src)
+        self.n_rays = len(src)  # units of the line: sources
+
+    def config(self, ws):
+        return {"workload": self.name, "lens": "SIS, r_e = 1", "sources": self.n_rays,
+                "radii": [0.1, 0.01, 1e-4], "centres": "0 .. 2 r_e in steps of 0.1 (R = 1e-4 from 0.1)",
+                "grid": "64 x 64 over 20 r_e x 20 r_e", "mu_min": 0.01, "f_area": 5e-4, "n_min": 50,
+                "l_max": 12, "precision": "fp64 deflections",
+                "l2": "flushed between timed steps (256 MB write)",
+                "parallelism": f"independent replicas x{ws}"}
+
+    def prepare(self, L, torch, dev):
+        self.L = L
+        self.lens = L.Lens([], [L.Halo.sis(0.0, 0.0, 1.0)], theta=0.3, precision="fp64")
+        self.stats = None
+
+    def step(self):
+        imgs, self.stats = self.lens.find_images(self.src, max_cells=1 << 26, max_images=1024, **self.GRID)
+        self.n_images = len(imgs)
+        return imgs
+
+    oracle_desc = ("sources of the workload (R = 0.1 at 1.1, 1.5 and 1.9 r_e, the oracle's fastest: one image "
+                   "each), the oracle's pure-Python grid refinement with FP64 deflections from its C direct sum, "
+                   "one core")
+
+    def oracle_rate(self, budget, seed=7):
+        import oracle
+        from oracle import images as I
+        comps = oracle.make_components(oracle.SIS, 0.0, 0.0, 0.0, 1.0)
+
+        def alpha(x, y):
+            o = oracle.direct_sum(comps, x, y, nthreads=1)
+            return o[:, 0], o[:, 1]
+        prm = I.AmrParams(**{k: v for k, v in self.GRID.items()})
+        sample = [(1.1, 0.0, 0.1), (1.5, 0.0, 0.1), (1.9, 0.0, 0.1)]
+        t0 = time.perf_counter()
+        done = 0
+        while done < 1 or time.perf_counter() - t0 < budget:
+            I.find_images(alpha, [sample[done % len(sample)]], prm)
+            done += 1
+            if done >= 3 * len(sample):
+                break
+        dt = time.perf_counter() - t0
+        return done / dt, done, dt, 1
+
+
+def run_gpu_images(args, ws, rank, local):
+    """The image-finding workload: same timing rules as run_gpu."""
+    import torch
+
+    import paper_1312_1128_gb300 as L
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = Images()
+    wl.prepare(L, torch, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lib = L.lib()
+    for _ in range(args.warmup):
+        wl.step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    launches0 = lib.lens_kernel_launches()
+    label_ms, label_cells, shoot_ms, wall = [], [], [], []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        ev[k][0].record()
+        wl.step()
+        ev[k][1].record()
+        torch.cuda.synchronize()
+        wall.append(1e3 * (time.perf_counter() - t0))
+        label_ms.append(wl.stats["label_ms"])
+        label_cells.append(wl.stats["label_cells"])
+        shoot_ms.append(wl.stats["shoot_ms"])
+    barrier(ws)
+    launches = lib.lens_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms, value = replica_rate(ws, wl.n_rays, float(np.mean(step_ms)), dev)
+    # the call takes host sources and returns host images: its wall time is
+    # the end-to-end figure
+    e2e, e2e_value = replica_rate(ws, wl.n_rays, float(np.mean(wall)), dev)
+    peak, basis = measured_hbm_gbs()
+    achieved = wl.BYTES_PER_LABEL_CELL * float(np.mean(label_cells)) / (float(np.mean(label_ms)) * 1e-3) / 1e9
+    st = wl.stats
+    line = {"metric": wl.metric, "value": value, "unit": wl.unit, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": wl.config(ws),
+            "e2e": {"value": e2e_value, "unit": wl.unit, "h2d_bytes_per_step": int(wl.src.nbytes),
+                    "d2h_bytes_per_step": int(wl.n_images * 32)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_basis": basis,
+                         "algorithmic_bytes_per_cell": wl.BYTES_PER_LABEL_CELL,
+                         "kernel": "image labelling pass (neighbours, union-find, labels, borders), timed per "
+                                   "pass with CUDA events inside the call",
+                         "label_ms_per_step": float(np.mean(label_ms)),
+                         "label_cells_per_step": float(np.mean(label_cells))},
+            "shooting": {"ms_per_step": float(np.mean(shoot_ms)), "rays_per_step": int(st["rays"]),
+                         "rays_per_s": st["rays"] / (float(np.mean(shoot_ms)) * 1e-3)},
+            "images": wl.n_images, "final_cells": int(st["cells"]), "rounds": int(st["rounds"]),
+            "clocks": clk, "gpu_launches": int(launches)}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r, done_n, dt, cores = wl.oracle_rate(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": r, "unit": wl.unit, "cores": cores, "kind": "oracle",
+                                "sample": f"{done_n} {wl.oracle_desc}, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_gpu_knn(args, ws, rank, local):
     """The smoothing-length workload: same timing rules as run_gpu."""
     import torch
@@ -912,7 +1049,7 @@ def run_gpu_refine(args, ws, rank, local):
 
 
 WORKLOADS = {"nfw_sph": NfwSph, "mixed_batches": MixedBatches, "microlensing": Microlensing, "fit": Fit,
-             "refine": Refine, "knn": Knn, "potential": Potential}
+             "refine": Refine, "knn": Knn, "potential": Potential, "images": Images}
 
 
 def _oracle_loop(oracle, comps, rx, ry, _, budget_s, seed, nthreads=0, potential=False):
@@ -1130,7 +1267,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", choices=["nfw_sph", "mixed_batches", "microlensing", "fit", "refine", "knn",
-                                           "potential"],
+                                           "potential", "images"],
                     default="nfw_sph",
                     help="nfw_sph (default) is the headline; the others measure the batched, "
                          "microlensing and differentiable paths")
@@ -1163,6 +1300,8 @@ def main():
             run_gpu_refine(args, ws, rank, local)
         elif args.workload == "knn":
             run_gpu_knn(args, ws, rank, local)
+        elif args.workload == "images":
+            run_gpu_images(args, ws, rank, local)
         else:
             run_gpu(args, ws, rank, local)
     if ws > 1:

@@ -420,6 +420,70 @@ const char* lens_status_string(lens_status s);
 const char* lens_last_error(void);
 int32_t lens_api_version(void);
 
+
+/*
+ * Image finding by adaptive grid refinement (Sec. 4) for uniform circular
+ * sources, many at once.  Each source gets its own grid of n x n cells over
+ * [x0, x0 + side] x [y0, y0 + side]; a cell (L, i, j) has side
+ * h_L = side / (n 3^L) and is refined into its 9 thirds.  Per source:
+ *   telescoping -- source radius r = h_0 / sqrt(mu_min), divided by 3 down
+ *     to the source's R; at each r, cells whose source point
+ *     y = x - alpha(x) lies within r of the source centre and whose side
+ *     exceeds r sqrt(mu_min) / 3 are refined until none remain;
+ *   images -- connected sets (cells sharing an edge) of cells whose point lies
+ *     inside the source; inner border: image cells with a non-image
+ *     neighbour, outer border: non-image cells with an image neighbour;
+ *   uniform step -- while an image has fewer than n_min cells, its cells and
+ *     its outer border are refined;
+ *   border step -- until an image's largest border cell has area below
+ *     f_area times the image's area and its outer border is as fine as its
+ *     inner border, its border cells of the largest size are refined;
+ * cells at level l_max are never refined (the minimum grid size).
+ */
+typedef struct lens_amr_params {
+    double x0, y0, side;  /* the initial grid                                  */
+    int32_t n;            /* initial cells per side, 1..4096                    */
+    int32_t l_max;        /* level cap, 0..19                                   */
+    double mu_min;        /* smallest |magnification| to find, (0, 1]          */
+    double f_area;        /* stopping fraction of the border step (paper 5e-4)  */
+    int32_t n_min;        /* cells per image after the uniform step (paper 50)  */
+    int32_t max_rounds;   /* refinement rounds before giving up, 0: 10000       */
+    int64_t max_cells;    /* leaf-cell capacity of the call, 0: 2^23            */
+} lens_amr_params;
+
+/* One image found by lens_find_images. */
+typedef struct lens_image {
+    int32_t source;   /* index of its source                                   */
+    int32_t n_cells;  /* cells of the image                                    */
+    double area;      /* sum of its cells' areas (per-level counts x h_L^2)    */
+    double mu;        /* area / (pi R^2): its magnification                    */
+    int64_t first;    /* smallest cell key of the image within its source:     */
+                      /* (i0 n + j0) 9^l_max + the base-9 digits 3a + b of the  */
+                      /* cell's refinements, padded to level l_max              */
+} lens_image;
+
+/*
+ * lens_find_images -- the images and magnifications of n_sources uniform
+ * circular sources through the tree's lens (deflections by lens_shoot_rays
+ * in the tree's precision, ray positions in FP64).
+ *   sources: host, 3 doubles per source {y_c1, y_c2, R}, R > 0.
+ *   images: host, max_images records (caller-owned), ordered by source and
+ *     then by first; *n_images receives the count.
+ *   stats: host, 6 int64 or NULL: rays shot, final leaf cells, rounds, cells
+ *     visited by the image-labelling passes (neighbours, union-find, labels,
+ *     borders), their device time in ns, the shooting's device time in ns.
+ * Limits: n_sources n^2 9^l_max < 2^63, n 3^l_max < 2^32.  Device memory:
+ * about 150 bytes per cell of max_cells, kept with the tree for later calls
+ * (grown when a call needs more) and freed by lens_free_tree.
+ * Synchronous on stream (the refinement reads small counts back each round).
+ * Errors: LENS_ERR_INVALID_ARG for bad parameters, more images than
+ * max_images or more cells than max_cells; LENS_ERR_INTERNAL when max_rounds
+ * runs out; LENS_ERR_OOM; shooting errors as lens_shoot_rays.
+ */
+lens_status lens_find_images(lens_tree* tree, const lens_amr_params* params, int32_t n_sources,
+                             const double* sources, int32_t max_images, lens_image* images, int32_t* n_images,
+                             int64_t* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,18 @@ class _Halo(ctypes.Structure):
                 ("p1", ctypes.c_double)]
 
 
+class _AmrParams(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("side", ctypes.c_double),
+                ("n", ctypes.c_int32), ("l_max", ctypes.c_int32), ("mu_min", ctypes.c_double),
+                ("f_area", ctypes.c_double), ("n_min", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
+                ("max_cells", ctypes.c_int64)]
+
+
+class _Image(ctypes.Structure):
+    _fields_ = [("source", ctypes.c_int32), ("n_cells", ctypes.c_int32), ("area", ctypes.c_double),
+                ("mu", ctypes.c_double), ("first", ctypes.c_int64)]
+
+
 class _Params(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("leaf_max", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("group_rays", ctypes.c_int32),
@@ -100,6 +112,7 @@ def lib():
                                     vp, vp, vp]
     L.lens_smoothing_lengths.argtypes = [vp, i64, i32, vp, vp]
     L.lens_shoot_potential.argtypes = [vp, d, d, vp, vp, i32, i64, vp, vp, vp, i32, vp]
+    L.lens_find_images.argtypes = [vp, vp, i32, vp, i32, vp, vp, vp, vp]
     L.lens_kernel_launches.argtypes = []
     L.lens_kernel_launches.restype = ctypes.c_int64
     L.lens_free_tree.argtypes = [vp]
@@ -111,7 +124,7 @@ def lib():
                  "lens_tree_get_info", "lens_tree_export", "lens_fp32_peak", "lens_api_version",
                  "lens_tree_counters", "lens_last_timing", "lens_autotune",
                  "lens_shoot_rays_direct_noalloc", "lens_refine_cells", "lens_smoothing_lengths",
-                 "lens_shoot_potential"]:
+                 "lens_shoot_potential", "lens_find_images"]:
         getattr(L, name).restype = ctypes.c_int32
     _lib = L
     return L
@@ -324,6 +337,27 @@ class Lens:
                                           rd, n, *[_dev_ptr(o) if o is not None else None for o in out],
                                           int(flags), _stream_ptr(stream)))
         return out
+
+    def find_images(self, sources, x0, y0, side, n=64, l_max=12, mu_min=0.01, f_area=5e-4, n_min=50,
+                    max_cells=0, max_rounds=0, max_images=4096, stream=None):
+        """Images of uniform circular sources (lens_find_images, Sec. 4).
+        sources: (k, 3) array-like of {y_c1, y_c2, R}.  Returns (images,
+        stats): images a list of dicts (source, n_cells, area, mu, first)
+        ordered by source, stats {rays, cells, rounds, label_cells, label_ms,
+        shoot_ms}: rays shot, final cells, refinement rounds, cells visited by
+        the image-labelling passes and their device time, the shooting's."""
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.float64).reshape(-1, 3))
+        prm = _AmrParams(float(x0), float(y0), float(side), int(n), int(l_max), float(mu_min), float(f_area),
+                         int(n_min), int(max_rounds), int(max_cells))
+        out = (_Image * max(1, int(max_images)))()
+        cnt = ctypes.c_int32()
+        st = (ctypes.c_int64 * 6)()
+        _check(lib().lens_find_images(self._h, ctypes.byref(prm), src.shape[0], src.ctypes.data_as(ctypes.c_void_p),
+                                      int(max_images), out, ctypes.byref(cnt), st, _stream_ptr(stream)))
+        imgs = [{"source": out[k].source, "n_cells": out[k].n_cells, "area": out[k].area, "mu": out[k].mu,
+                 "first": out[k].first} for k in range(cnt.value)]
+        return imgs, {"rays": st[0], "cells": st[1], "rounds": st[2], "label_cells": st[3],
+                      "label_ms": st[4] * 1e-6, "shoot_ms": st[5] * 1e-6}
 
     def shoot_direct_noalloc(self, dx, dy, out, origin=(0.0, 0.0), flags: int = 0, stream=None):
         """Direct sum into caller-provided outputs without any device

@@ -18,10 +18,14 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(PKG, "liblens.so")
 
-SOURCES = ["walk.cu", "walk_ws.cu", "build.cu", "backward.cu", "sort.cu", "batch.cu", "refine.cu", "knn.cu", "psi.cu", "api.cu"]
+SOURCES = ["walk.cu", "walk_ws.cu", "build.cu", "backward.cu", "sort.cu", "batch.cu", "refine.cu", "knn.cu", "psi.cu",
+           "amr.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code rounds every operation (no contraction into fused multiply-adds,
+# which GCC does by default on Arm): the image finder's host-side decisions
+# follow their FP64 definitions operation by operation
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
+              "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
 
 
 def _nvcc() -> str:

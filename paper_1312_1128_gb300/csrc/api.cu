@@ -129,6 +129,7 @@ void lens_free_tree(lens_tree* t)
     if (t->d_err) cudaFree(t->d_err);
     if (t->ray_scratch.ptr) cudaFreeAsync(t->ray_scratch.ptr, 0);
     if (t->d_stats) cudaFree(t->d_stats);
+    if (t->amr_ws && t->amr_free) t->amr_free(t->amr_ws);
     for (int i = 0; i < 3; ++i)
         if (t->ev[i]) cudaEventDestroy(t->ev[i]);
     delete t;

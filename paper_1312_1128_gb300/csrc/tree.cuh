@@ -83,6 +83,8 @@ struct lens_tree {
     unsigned long long* d_stats = nullptr;  // 8 walk counters (LENS_COUNT)
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // LENS_TIMING: start, grouped, walked
     bool timed = false;
+    void* amr_ws = nullptr;                 // image-finding workspace (amr.cu), kept between calls
+    void (*amr_free)(void*) = nullptr;
 };
 
 namespace lens {

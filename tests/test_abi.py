@@ -113,3 +113,31 @@ def test_shoot_potential_argument_checks():
     for flags in (0, 1, 8):
         assert lt.lens_shoot_potential(None, 0.0, 0.0, fake, fake, 0, 10, fake, None, None, flags, None) == 1
     assert b"tree" in lt.lens_last_error()
+
+
+def test_find_images_argument_checks():
+    """lens_find_images rejects bad parameters before touching the tree or the
+    device."""
+    import paper_1312_1128_gb300 as L
+    lt = L.lib()
+    cnt = ctypes.c_int32(7)
+    assert lt.lens_find_images(None, None, 0, None, 0, None, ctypes.byref(cnt), None, None) == 1
+    fake = ctypes.c_void_p(16)  # never dereferenced: every case fails first
+    src = (ctypes.c_double * 3)(0.5, 0.0, 0.1)
+    imgs = (L._Image * 4)()
+
+    def call(n_src=1, s=src, **kw):
+        p = dict(x0=-10.0, y0=-10.0, side=20.0, n=64, l_max=12, mu_min=0.01, f_area=5e-4, n_min=50,
+                 max_rounds=0, max_cells=0)
+        p.update(kw)
+        prm = L._AmrParams(**p)
+        return lt.lens_find_images(fake, ctypes.byref(prm), n_src, s, 4, imgs, ctypes.byref(cnt), None, None)
+
+    assert call(n_src=0) == 0 and cnt.value == 0
+    for kw in [dict(n=0), dict(n=5000), dict(l_max=-1), dict(l_max=20), dict(side=0.0), dict(side=float("nan")),
+               dict(mu_min=0.0), dict(mu_min=1.5), dict(f_area=0.0), dict(n_min=-1), dict(n_src=-1),
+               dict(n=4096, l_max=19), dict(max_cells=100)]:
+        assert call(**kw) == 1, kw
+    bad = (ctypes.c_double * 3)(0.5, 0.0, -1.0)
+    assert call(s=bad) == 1
+    assert b"radius" in lt.lens_last_error()
