@@ -75,12 +75,16 @@ inline unsigned blocks(int64_t n) { return (unsigned)((n + kAmrThreads - 1) / kA
 
 __device__ __forceinline__ uint64_t make_key(const AmrConst& C, int s, int lv, uint32_t i, uint32_t j)
 {
-    const uint32_t s3 = C.pow3[lv];
-    uint64_t c = (uint64_t)(i / s3) * (uint64_t)C.n + (j / s3);
-    for (int l = 1; l <= lv; ++l) {
-        const uint32_t d = C.pow3[lv - l];
-        c = c * 9ull + 3u * ((i / d) % 3u) + ((j / d) % 3u);
+    // base-9 digits from the finest level up (constant divisions by 3), then
+    // the level-0 cell
+    uint64_t c = 0, m = 1;
+    for (int l = 0; l < lv; ++l) {
+        c += (uint64_t)(3u * (i % 3u) + (j % 3u)) * m;
+        i /= 3u;
+        j /= 3u;
+        m *= 9ull;
     }
+    c += ((uint64_t)i * (uint64_t)C.n + j) * m;
     return (uint64_t)s * C.src_span + c * C.pow9[C.l_max - lv];
 }
 
@@ -151,13 +155,35 @@ __global__ void k_neighbours(Leaves L, int64_t n, AmrConst C, const uint8_t* wan
         const int64_t ni = (int64_t)i + di[d], nj = (int64_t)j + dj[d];
         if (want[s] && ni >= 0 && nj >= 0 && ni < lim && nj < lim) {
             const uint64_t q = make_key(C, s, lv, (uint32_t)ni, (uint32_t)nj);
-            int64_t lo = 0, hi = n;  // first index with key > q
-            while (lo < hi) {
+            // the last leaf with key <= q, galloping out from k (a +x / +y
+            // neighbour has a larger key, a -x / -y one a smaller) to
+            // key[lo] <= q < key[hi], then bisecting
+            int64_t lo, hi, step = 1;
+            if (L.key[k] <= q) {
+                lo = k;
+                hi = k + 1;
+                while (hi < n && L.key[hi] <= q) {
+                    lo = hi;
+                    step *= 2;
+                    hi = k + step;
+                }
+                if (hi > n) hi = n;
+            } else {
+                hi = k;
+                lo = k - 1;
+                while (lo >= 0 && L.key[lo] > q) {
+                    hi = lo;
+                    step *= 2;
+                    lo = k - step;
+                }
+                if (lo < 0) lo = -1;
+            }
+            while (hi - lo > 1) {
                 const int64_t mid = (lo + hi) >> 1;
-                if (L.key[mid] <= q) lo = mid + 1;
+                if (L.key[mid] <= q) lo = mid;
                 else hi = mid;
             }
-            const int64_t c = lo - 1;
+            const int64_t c = lo;
             if (c >= 0) {
                 const int lc = L.lv[c];
                 if (lc <= lv && q < L.key[c] + C.pow9[C.l_max - lc]) res = (int32_t)c;
@@ -180,20 +206,57 @@ __device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t u)
     }
 }
 
-__global__ void k_uf_init(Leaves L, int64_t n, const uint8_t* in, const uint8_t* want, int32_t* parent)
+// Union-find, first inside each block of kAmrThreads consecutive leaves (in
+// shared memory: the pairs whose both cells lie in the block), then across
+// blocks.  Every hook points to a smaller index, so a root is its
+// component's smallest index.  Equal-level pairs are taken once (from the
+// +x / +y side); a cell of another source or outside an image is -1.
+__device__ __forceinline__ int32_t uf_find_shared(volatile int32_t* p, int32_t u)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    parent[k] = (in[k] && want[L.src[k]]) ? (int32_t)k : -1;
+    for (;;) {
+        const int32_t q = p[u];
+        if (q == u) return u;
+        u = q;
+    }
+}
+
+__global__ void __launch_bounds__(kAmrThreads) k_uf_local(Leaves L, int64_t n, const uint8_t* in, const uint8_t* want,
+                                                        const int32_t* nb, int32_t* parent)
+{
+    __shared__ int32_t sp[kAmrThreads];
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * kAmrThreads, k = base + t;
+    const bool mine = k < n && in[k] && want[L.src[k]];
+    sp[t] = mine ? t : -1;
+    __syncthreads();
+    if (mine) {
+        for (int d = 0; d < 4; ++d) {
+            const int32_t c = nb[4 * k + d];
+            if (c < base || c >= base + kAmrThreads || sp[c - base] < 0) continue;
+            if ((d & 1) && L.lv[c] == L.lv[k]) continue;
+            int32_t a = t, b = (int32_t)(c - base);
+            for (;;) {
+                a = uf_find_shared(sp, a);
+                b = uf_find_shared(sp, b);
+                if (a == b) break;
+                const int32_t hi = a > b ? a : b, lo = a > b ? b : a;
+                if (atomicCAS(&sp[hi], hi, lo) == hi) break;
+            }
+        }
+    }
+    __syncthreads();
+    if (k < n) parent[k] = mine ? (int32_t)(base + uf_find_shared(sp, t)) : -1;
 }
 
 __global__ void k_uf_unite(Leaves L, int64_t n, const int32_t* nb, int32_t* parent)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || parent[k] < 0) return;
+    const int64_t base = (int64_t)blockIdx.x * kAmrThreads;
     for (int d = 0; d < 4; ++d) {
         const int32_t c = nb[4 * k + d];
         if (c < 0 || parent[c] < 0) continue;
+        if (c >= base && c < base + kAmrThreads) continue;  // united inside the block
         if ((d & 1) && L.lv[c] == L.lv[k]) continue;  // an equal-level pair is also found from c's +x / +y side
         int32_t a = (int32_t)k, b = c;
         for (;;) {
@@ -557,7 +620,7 @@ extern "C" lens_status lens_find_images(lens_tree* tree, const lens_amr_params* 
         LENS_CUDA(cudaEventRecord(W.ev[0], st));
         k_neighbours<<<blocks(n), kAmrThreads, 0, st>>>(cur->view(), n, C, W.want.p, W.nb.p);
         note_launch();
-        k_uf_init<<<blocks(n), kAmrThreads, 0, st>>>(cur->view(), n, W.in.p, W.want.p, W.parent.p);
+        k_uf_local<<<blocks(n), kAmrThreads, 0, st>>>(cur->view(), n, W.in.p, W.want.p, W.nb.p, W.parent.p);
         note_launch();
         k_uf_unite<<<blocks(n), kAmrThreads, 0, st>>>(cur->view(), n, W.nb.p, W.parent.p);
         note_launch();
