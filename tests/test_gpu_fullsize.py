@@ -193,3 +193,59 @@ def test_fit_fullsize_mass_finite_differences_fp64(fit):
         assert grad[j, 0] == pytest.approx(fd, rel=1e-6, abs=1e-9 * np.abs(grad[:, 0]).max())
     lens.close()
     tl.close()
+
+
+def test_potential_fullsize_tree(sph):
+    """The potential workload as bench.py times it (1e6 smoothed NFW particles,
+    2048^2 rays, theta = 0.3, 32- and 64-ray groups): psi on 512 sampled rays
+    against the oracle's direct potential at the deflection's bar (1e-3 of
+    |psi| at the median ray), and the call's alpha equal to shoot()'s."""
+    w = sph
+    parts = cu(w["gauss"])
+    rx, ry = cu(w["rx"]), cu(w["ry"])
+    g = lensgen.rng(93)
+    idx = lensgen.sample_indices(g, w["rx"].size, 512)
+    ti = torch.from_numpy(idx).cuda()
+    comps = comps_gauss(w["gauss"], w["q"])
+    ref = oracle.direct_potential(comps, w["rx"][idx].astype(np.float64), w["ry"][idx].astype(np.float64))
+    for gr in (32, 64):
+        lens = L.Lens([L.Species.gauss(parts, w["q"])], theta=0.3, group_rays=gr)
+        psi, a1, a2 = lens.potential(rx, ry)
+        e = np.abs(psi[ti].double().cpu().numpy() - ref) / np.abs(ref)
+        assert np.median(e) <= 1e-3, (gr, np.median(e))
+        s = lens.shoot(rx, ry, flags=L.ALPHA_ONLY)
+        lens.sync()
+        d = (a1 - s[0]).abs().max().item()
+        assert d <= 1e-4 * s[0].abs().max().item(), (gr, d)
+        lens.close()
+
+
+def test_images_fullsize_sis_test():
+    """The image-finding workload as bench.py times it: the 62 sources of the
+    Sec. 5.2 SIS test in one call; every image above mu_min found, none
+    spurious, all magnifications within 0.7 % of App. B (median below 0.05 %),
+    and the same result on a second call (the workspace is reused)."""
+    from oracle import images as I
+    src = []
+    for R in (0.1, 0.01, 1e-4):
+        for b in np.round(np.linspace(0.0, 2.0, 21), 6):
+            if R < 1e-3 and b == 0.0:
+                continue
+            src.append((float(b), 0.0, R))
+    lens = L.Lens([], [L.Halo.sis(0.0, 0.0, 1.0)], theta=0.3, precision="fp64")
+    kw = dict(x0=-10.0, y0=-10.0, side=20.0, n=64, l_max=12, mu_min=0.01, f_area=5e-4, n_min=50,
+              max_cells=1 << 26, max_images=1024)
+    imgs, st = lens.find_images(src, **kw)
+    errs = []
+    for k, (b, _, R) in enumerate(src):
+        mp, mm, ring = I.sis_finite_source_mu(b, R)
+        exp = [mp + mm] if ring else ([mp, mm] if mm > 0 else [mp])
+        got = sorted((im["mu"] for im in imgs if im["source"] == k), reverse=True)
+        assert len(got) <= len(exp), (b, R, got)
+        assert all(m < 0.01 for m in exp[len(got):]), (b, R, got, exp)
+        errs += [abs(a / e - 1.0) for a, e in zip(got, exp)]
+    errs = np.array(errs)
+    assert errs.max() < 7e-3 and np.median(errs) < 5e-4, (errs.max(), np.median(errs))
+    again, st2 = lens.find_images(src, **kw)
+    assert again == imgs and st2["cells"] == st["cells"]
+    lens.close()
