@@ -351,21 +351,33 @@ __global__ void k_mark_images(Leaves L, int64_t n, AmrConst C, const int32_t* nb
     }
 }
 
-__global__ void k_count_marks(Leaves L, int64_t n, const uint8_t* mark, uint32_t* cnt9, uint32_t* nmark)
+__global__ void k_count_marks(Leaves L, int64_t n, const uint8_t* mark, uint32_t* cnt9, uint32_t* rmark,
+                              uint32_t* nmark)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const bool m = mark[k] != 0;
     cnt9[k] = m ? 9u : 1u;
+    rmark[k] = m ? 1u : 0u;
     if (m) atomicAdd(&nmark[L.src[k]], 1u);
 }
 
-// children of marked leaves in digit order where the parent stood
-__global__ void k_refine(Leaves A, int64_t n, AmrConst C, const uint8_t* mark, const uint32_t* pos, Leaves B,
-                         double* rx, double* ry, uint32_t* rslot)
+// the leaves of sources that have just finished leave the working array
+// (their images are recorded): output count 0
+__global__ void k_drop(Leaves L, int64_t n, const uint8_t* drop, uint32_t* cnt9)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    if (drop[L.src[k]]) cnt9[k] = 0u;
+}
+
+// children of marked leaves in digit order where the parent stood
+__global__ void k_refine(Leaves A, int64_t n, AmrConst C, const uint8_t* mark, const uint8_t* drop,
+                         const uint32_t* pos, const uint32_t* rpos, Leaves B, double* rx, double* ry,
+                         uint32_t* rslot)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || drop[A.src[k]]) return;
     const int64_t p = pos[k];
     const uint64_t key = A.key[k];
     const int lv = A.lv[k];
@@ -383,7 +395,7 @@ __global__ void k_refine(Leaves A, int64_t n, AmrConst C, const uint8_t* mark, c
     }
     const uint64_t step = C.pow9[C.l_max - lv - 1];
     const double h = C.h[lv + 1];
-    const int64_t rbase = p - k;  // 8 rays per marked leaf before k
+    const int64_t rbase = 8 * (int64_t)rpos[k];  // 8 rays per marked leaf before k
     for (int t = 0; t < 9; ++t) {
         const uint32_t ci = 3u * i + (uint32_t)(t / 3), cj = 3u * j + (uint32_t)(t % 3);
         const int64_t o = p + t;
@@ -446,9 +458,9 @@ struct LeafBufs {
 // Device memory of one call, kept with the tree and grown when a call needs more.
 struct AmrWorkspace {
     LeafBufs A, B;
-    DevBuf<uint8_t> in, mark, want;
+    DevBuf<uint8_t> in, mark, want, drop;
     DevBuf<int32_t> nb, parent, img, mode, lin, lout, isrc, act;
-    DevBuf<uint32_t> is_root, cnt9, rslot, icnt, nmark, total;
+    DevBuf<uint32_t> is_root, cnt9, rmark, rslot, icnt, nmark, total;
     DevBuf<unsigned long long> ifirst;
     DevBuf<double> rx, ry, a1, a2, scx, scy, sr2, thr;
     DevBuf<char> tmp;
@@ -462,9 +474,9 @@ struct AmrWorkspace {
     {
         cudaError_t e;
         if ((e = A.alloc(cap)) || (e = B.alloc(cap)) || (e = in.alloc(cap)) || (e = mark.alloc(cap)) ||
-            (e = want.alloc(ns)) || (e = nb.alloc(4 * cap)) || (e = parent.alloc(cap)) || (e = img.alloc(cap)) ||
+            (e = want.alloc(ns)) || (e = drop.alloc(ns)) || (e = nb.alloc(4 * cap)) || (e = parent.alloc(cap)) || (e = img.alloc(cap)) ||
             (e = mode.alloc(ns)) || (e = lin.alloc(M)) || (e = lout.alloc(M)) || (e = isrc.alloc(M)) ||
-            (e = act.alloc(M)) || (e = is_root.alloc(cap)) || (e = cnt9.alloc(cap)) || (e = rslot.alloc(cap)) ||
+            (e = act.alloc(M)) || (e = is_root.alloc(cap)) || (e = cnt9.alloc(cap)) || (e = rmark.alloc(cap)) || (e = rslot.alloc(cap)) ||
             (e = icnt.alloc(M * (LM + 1))) || (e = nmark.alloc(ns)) || (e = total.alloc(1)) ||
             (e = ifirst.alloc(M)) || (e = rx.alloc(cap)) || (e = ry.alloc(cap)) || (e = a1.alloc(cap)) ||
             (e = a2.alloc(cap)) || (e = scx.alloc(ns)) || (e = scy.alloc(ns)) || (e = sr2.alloc(ns)) ||
@@ -592,7 +604,9 @@ extern "C" lens_status lens_find_images(lens_tree* tree, const lens_amr_params* 
     std::vector<int> mode(n_sources, MODE_TELE);
     std::vector<double> rcur(n_sources), rad(n_sources), h_cx(n_sources), h_cy(n_sources), h_r2(n_sources),
         h_thr(n_sources);
-    std::vector<uint8_t> h_want(n_sources);
+    std::vector<uint8_t> h_want(n_sources), h_drop(n_sources, 0);
+    std::vector<std::vector<lens_image>> done_images(n_sources);
+    int64_t final_cells = 0;
     for (int s = 0; s < n_sources; ++s) {
         h_cx[s] = sources[3 * s];
         h_cy[s] = sources[3 * s + 1];
@@ -601,6 +615,7 @@ extern "C" lens_status lens_find_images(lens_tree* tree, const lens_amr_params* 
         if (r < rad[s]) r = rad[s];
         rcur[s] = r;
     }
+    LENS_CUDA(cudaMemsetAsync(W.drop.p, 0, n_sources, st));
     LENS_CUDA(cudaMemcpyAsync(W.scx.p, h_cx.data(), n_sources * sizeof(double), cudaMemcpyHostToDevice, st));
     LENS_CUDA(cudaMemcpyAsync(W.scy.p, h_cy.data(), n_sources * sizeof(double), cudaMemcpyHostToDevice, st));
     const std::vector<int32_t> sentinel(M, LM + 1);
@@ -718,12 +733,15 @@ extern "C" lens_status lens_find_images(lens_tree* tree, const lens_amr_params* 
             }
         }
         LENS_CUDA(cudaMemsetAsync(W.nmark.p, 0, n_sources * sizeof(uint32_t), st));
-        k_count_marks<<<blocks(n), kAmrThreads, 0, st>>>(cur->view(), n, W.mark.p, W.cnt9.p, W.nmark.p);
+        k_count_marks<<<blocks(n), kAmrThreads, 0, st>>>(cur->view(), n, W.mark.p, W.cnt9.p, W.rmark.p,
+                                                         W.nmark.p);
         note_launch();
         LENS_CUDA(cudaMemcpyAsync(h_nmark.data(), W.nmark.p, n_sources * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                   st));
         LENS_CUDA(cudaStreamSynchronize(st));
         int64_t marks = 0;
+        bool any_drop = false;
+        std::fill(h_drop.begin(), h_drop.end(), (uint8_t)0);
         for (int s = 0; s < n_sources; ++s) {
             marks += h_nmark[s];
             if (h_nmark[s] != 0) continue;
@@ -738,52 +756,65 @@ extern "C" lens_status lens_find_images(lens_tree* tree, const lens_amr_params* 
             } else if (mode[s] == MODE_UNIFORM) {
                 mode[s] = MODE_BORDER;
             } else if (mode[s] == MODE_BORDER) {
+                // this round's images are final (its cells no longer change)
                 mode[s] = MODE_DONE;
+                h_drop[s] = 1;
+                any_drop = true;
             }
         }
-        if (marks == 0) continue;
-        const int64_t n2 = n + 8 * marks;
-        if (n2 > cap)
+        if (any_drop) {
+            for (int id = 0; id < n_img; ++id) {
+                const int s = h_isrc[id];
+                if (!h_drop[s]) continue;
+                lens_image o{};
+                o.source = s;
+                uint32_t cells = 0;
+                for (int l = 0; l <= LM; ++l) cells += h_icnt[(size_t)id * (LM + 1) + l];
+                o.n_cells = (int32_t)cells;
+                o.area = area_of(id);
+                o.mu = o.area / (M_PI * rad[s] * rad[s]);
+                o.first = (int64_t)(h_ifirst[id] - (unsigned long long)s * C.src_span);
+                done_images[s].push_back(o);
+            }
+            LENS_CUDA(cudaMemcpyAsync(W.drop.p, h_drop.data(), n_sources, cudaMemcpyHostToDevice, st));
+            k_drop<<<blocks(n), kAmrThreads, 0, st>>>(cur->view(), n, W.drop.p, W.cnt9.p);
+            note_launch();
+        }
+        if (marks == 0 && !any_drop) continue;
+        if (n + 8 * marks > cap)
             return lens_set_error(LENS_ERR_INVALID_ARG, "image finding needs more than max_cells = %lld cells",
                                   (long long)cap);
-        scan_exclusive_u32(W.cnt9.p, W.cnt9.p, n, nullptr, W.tmp.p, st);
-        k_refine<<<blocks(n), kAmrThreads, 0, st>>>(cur->view(), n, C, W.mark.p, W.cnt9.p, nxt->view(), W.rx.p,
-                                                    W.ry.p, W.rslot.p);
+        scan_exclusive_u32(W.cnt9.p, W.cnt9.p, n, W.total.p, W.tmp.p, st);
+        scan_exclusive_u32(W.rmark.p, W.rmark.p, n, nullptr, W.tmp.p, st);
+        k_refine<<<blocks(n), kAmrThreads, 0, st>>>(cur->view(), n, C, W.mark.p, W.drop.p, W.cnt9.p, W.rmark.p,
+                                                    nxt->view(), W.rx.p, W.ry.p, W.rslot.p);
         note_launch();
+        uint32_t n2 = 0;
+        LENS_CUDA(cudaMemcpyAsync(&n2, W.total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        if (any_drop) {
+            std::fill(h_drop.begin(), h_drop.end(), (uint8_t)0);
+            LENS_CUDA(cudaMemcpyAsync(W.drop.p, h_drop.data(), n_sources, cudaMemcpyHostToDevice, st));
+        }
         std::swap(cur, nxt);
-        n = n2;
         LENS_TRY(shoot(8 * marks));
         LENS_CUDA(cudaStreamSynchronize(st));
         LENS_TRY(shoot_time());
+        final_cells += n + 8 * marks - (int64_t)n2;  // the dropped leaves
+        n = n2;
     }
 
-    // final images of every source
-    for (int s = 0; s < n_sources; ++s) {
-        h_want[s] = 1;
-        h_r2[s] = rad[s] * rad[s];
-    }
-    LENS_CUDA(cudaMemcpyAsync(W.sr2.p, h_r2.data(), n_sources * sizeof(double), cudaMemcpyHostToDevice, st));
-    LENS_CUDA(cudaMemcpyAsync(W.want.p, h_want.data(), n_sources, cudaMemcpyHostToDevice, st));
-    k_inside<<<blocks(n), kAmrThreads, 0, st>>>(cur->view(), n, W.scx.p, W.scy.p, W.sr2.p, W.in.p);
-    note_launch();
-    LENS_TRY(find());
-    if (n_img > max_images)
-        return lens_set_error(LENS_ERR_INVALID_ARG, "%d images exceed max_images = %d", n_img, max_images);
-    for (int id = 0; id < n_img; ++id) {
-        const int s = h_isrc[id];
-        lens_image& o = images[id];
-        o.source = s;
-        uint32_t cells = 0;
-        for (int l = 0; l <= LM; ++l) cells += h_icnt[(size_t)id * (LM + 1) + l];
-        o.n_cells = (int32_t)cells;
-        o.area = area_of(id);
-        o.mu = o.area / (M_PI * rad[s] * rad[s]);
-        o.first = (int64_t)(h_ifirst[id] - (unsigned long long)s * C.src_span);
-    }
-    *n_images = n_img;
+    // every source's images, recorded as it finished, by source and key
+    int32_t total_img = 0;
+    for (int s = 0; s < n_sources; ++s) total_img += (int32_t)done_images[s].size();
+    if (total_img > max_images)
+        return lens_set_error(LENS_ERR_INVALID_ARG, "%d images exceed max_images = %d", total_img, max_images);
+    int32_t o = 0;
+    for (int s = 0; s < n_sources; ++s)
+        for (const lens_image& im : done_images[s]) images[o++] = im;
+    *n_images = total_img;
     if (stats) {
         stats[0] = rays_total;
-        stats[1] = n;
+        stats[1] = final_cells;
         stats[2] = rounds;
         stats[3] = find_cells;
         stats[4] = (int64_t)std::llround(find_ms * 1e6);
