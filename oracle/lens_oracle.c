@@ -56,14 +56,15 @@ typedef struct {
 
 /* Projected NFW helper F(x) (SEF92-style closed form, Sec. 3.2 "analytic
  * models"): arccosh(1/x)/sqrt(1-x^2) for x<1, arccos(1/x)/sqrt(x^2-1) for x>1,
- * F(1) = 1.  Near x = 1 both forms are 0/0; there the Taylor series in
- * u = 1 - x^2, F = sum_k u^k/(2k+1), is used. */
+ * F(1) = 1.  Near x = 1 both forms are 0/0 and arccosh(1/x) is
+ * ill-conditioned; for |u| < 0.1, u = 1 - x^2, the series
+ * F = sum_k u^k/(2k+1) is used instead (40 terms: below 1e-40 there). */
 static double nfw_F(double x)
 {
     double u = 1.0 - x * x;
-    if (fabs(u) < 2e-4) {
+    if (fabs(u) < 0.1) {
         double s = 0.0, p = 1.0;
-        for (int k = 0; k < 8; ++k) { s += p / (2 * k + 1); p *= u; }
+        for (int k = 0; k < 40; ++k) { s += p / (2 * k + 1); p *= u; }
         return s;
     }
     if (x < 1.0) return acosh(1.0 / x) / sqrt(u);
@@ -71,13 +72,13 @@ static double nfw_F(double x)
 }
 
 /* Projected NFW surface-density shape f(x) = (1 - F)/(x^2 - 1), f(1) = 1/3;
- * near x = 1 its series f = sum_k u^k/(2k+3). */
+ * for |u| < 0.1 its series f = sum_k u^k/(2k+3) (the quotient cancels). */
 static double nfw_f(double x)
 {
     double u = 1.0 - x * x;
-    if (fabs(u) < 2e-4) {
+    if (fabs(u) < 0.1) {
         double s = 0.0, p = 1.0;
-        for (int k = 0; k < 8; ++k) { s += p / (2 * k + 3); p *= u; }
+        for (int k = 0; k < 40; ++k) { s += p / (2 * k + 3); p *= u; }
         return s;
     }
     return (1.0 - nfw_F(x)) / (x * x - 1.0);

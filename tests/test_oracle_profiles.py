@@ -124,6 +124,27 @@ def test_nfw_enclosed_mass_series_regions_vs_high_precision(x):
     assert M_or == pytest.approx(ref, rel=1e-12)
 
 
+@pytest.mark.parametrize("x", [0.9, 0.95, 0.97, 0.999, 0.99963, 0.9999, 1.0, 1.0003, 1.001, 1.02, 1.05, 1.1])
+def test_nfw_convergence_near_x1_vs_high_precision(x):
+    """kappa = m f(x) / (2 r_s^2 g(X)), f = (1 - F)/(x^2 - 1), near x = 1,
+    where the closed forms cancel (arccosh(1/x) is ill-conditioned there):
+    against 50-digit mpmath at 1e-14."""
+    mpmath.mp.dps = 50
+    rs, X, m = 1.0, 20.0, 1.0
+    c = comp(NFW, 0.0, 0.0, m, rs, X * rs)
+    kap = oracle.eval_component(c, x * rs, 0.0)[2]
+    xm = mpmath.mpf(x)
+    if x < 1:
+        F = mpmath.acosh(1 / xm) / mpmath.sqrt(1 - xm * xm)
+    elif x > 1:
+        F = mpmath.acos(1 / xm) / mpmath.sqrt(xm * xm - 1)
+    else:
+        F = mpmath.mpf(1)
+    f = (1 - F) / (xm * xm - 1) if x != 1.0 else mpmath.mpf(1) / 3
+    ref = float(m * f / (2 * rs * rs * _g_mp(X)))
+    assert kap == pytest.approx(ref, rel=1e-14)
+
+
 # ----------------------------------------------------------------------- SIS
 
 def test_sis_appendix_b_images_and_magnifications():
