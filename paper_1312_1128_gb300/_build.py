@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(PKG, "liblens.so")
 
 SOURCES = ["walk.cu", "walk_ws.cu", "build.cu", "backward.cu", "sort.cu", "batch.cu", "refine.cu", "knn.cu", "psi.cu",
-           "amr.cu", "api.cu"]
+           "amr.cu", "halo_rays.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code rounds every operation (no contraction into fused multiply-adds,
 # which GCC does by default on Arm): the image finder's host-side decisions

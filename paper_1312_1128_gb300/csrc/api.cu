@@ -20,6 +20,9 @@ lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, co
                                 const void* dx, const void* dy, int dtype, void* const out[5],
                                 int flags, cudaStream_t s);
 void free_graphs(lens_tree* t);
+bool halos_only(const lens_tree* t);
+lens_status shoot_halos_only(lens_tree* t, double ox, double oy, const void* dx, const void* dy, int dtype,
+                             int64_t n, void* const out[5], int flags, cudaStream_t s);
 }  // namespace lens
 
 static thread_local char g_msg[512] = "";
@@ -256,6 +259,10 @@ lens_status lens_shoot_rays(lens_tree* tree, double origin_x, double origin_y, c
     int64_t off[2] = {0, n};
     double orig[2] = {origin_x, origin_y};
     void* out[5] = {alpha1, alpha2, kappa, gamma1, gamma2};
+    // analytic components only: one thread per ray, no grouping or walk
+    if (!(flags & (LENS_TIMING | LENS_COUNT)) && halos_only(tree))
+        return shoot_halos_only(tree, origin_x, origin_y, ray_dx, ray_dy, ray_dtype, n, out, flags,
+                                (cudaStream_t)stream);
     return shoot(tree, 1, off, orig, ray_dx, ray_dy, ray_dtype, out, flags, (cudaStream_t)stream);
 }
 

@@ -306,3 +306,57 @@ def test_forward_is_bitwise_deterministic(walk):
                     assert torch.equal(a, b)
                 assert torch.equal(psi, first[1])
         lens.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_halos_only_per_ray_path(prec):
+    """A lens of analytic components only is shot one thread per ray (no
+    grouping, no walk): all five halo kinds against the oracle's direct sum,
+    FP32 and FP64 ray offsets about an FP64 origin, ALPHA_ONLY and ACCUMULATE,
+    and the same values as the grouped path (taken with TIMING)."""
+    halos = [L.Halo.sis(0.1, -0.05, 0.15), L.Halo.disk(-0.2, 0.1, -0.02, 0.3),
+             L.Halo.gauss(0.3, 0.3, 0.01, 0.05, 3.0), L.Halo.nfw(-0.4, -0.3, 0.02, 0.05, 0.2),
+             L.Halo.point(0.5, -0.5, 0.003)]
+    comps = oracle.concat(
+        oracle.make_components(oracle.SIS, 0.1, -0.05, 0.0, 0.15),
+        oracle.make_components(oracle.DISK, -0.2, 0.1, -0.02, 0.3),
+        oracle.make_components(oracle.GAUSS, 0.3, 0.3, 0.01, 0.05, 3.0),
+        oracle.make_components(oracle.NFW, -0.4, -0.3, 0.02, 0.05, 0.2),
+        oracle.make_components(oracle.POINT, 0.5, -0.5, 0.003))
+    lens = L.Lens([], halos, theta=0.3, precision=prec)
+    g = lensgen.rng(71)
+    origin = (0.25, -0.125)
+    dx = g.uniform(-0.9, 0.9, 30000)
+    dy = g.uniform(-0.9, 0.9, 30000)
+    ref = oracle.direct_sum(comps, origin[0] + dx, origin[1] + dy)
+    for rdt in (np.float64, np.float32):
+        rx, ry = cu(dx.astype(rdt)), cu(dy.astype(rdt))
+        got = to_np(lens.shoot(rx, ry, origin=origin))
+        rr = oracle.direct_sum(comps, origin[0] + dx.astype(rdt).astype(np.float64),
+                               origin[1] + dy.astype(rdt).astype(np.float64))
+        mask = ~edge_mask(comps, origin[0] + dx.astype(rdt), origin[1] + dy.astype(rdt))
+        # the halos' kappa and gamma cancel at some rays (a negative-mass
+        # disk among them): bars on the conditioning, sum |term|
+        _, absum = oracle.direct_sum(comps, origin[0] + dx.astype(rdt).astype(np.float64),
+                                     origin[1] + dy.astype(rdt).astype(np.float64), with_absum=True)
+        if prec == "fp64":
+            d = np.abs(got - rr)
+            ok = d <= 1e-12 * np.abs(rr) + 64 * 2.0 ** -53 * absum
+            bad = np.nonzero(~ok.all(axis=1) & mask)[0]
+            assert ok[:, :2].all() and bad.size == 0, [
+                (origin[0] + dx[b], origin[1] + dy[b], got[b].tolist(), rr[b].tolist(), absum[b].tolist())
+                for b in bad[:3]]
+        else:
+            ok, _ = within_fp32_bar(got, rr, absum)
+            assert ok[:, 0].all() and ok[mask].all(), (rdt, (~ok[mask]).sum(axis=0))
+        grouped = to_np(lens.shoot(rx, ry, origin=origin, flags=L.TIMING))
+        np.testing.assert_allclose(got, grouped, rtol=1e-12 if prec == "fp64" else 1e-5,
+                                   atol=1e-14 if prec == "fp64" else 1e-6)
+        ao = lens.shoot(rx, ry, origin=origin, flags=L.ALPHA_ONLY)
+        np.testing.assert_array_equal(to_np(ao[:2]), got[:, :2])
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        acc = [torch.full((dx.size,), 2.0, dtype=dt, device="cuda") for _ in range(5)]
+        lens.shoot(rx, ry, origin=origin, flags=L.ACCUMULATE, out=acc)
+        np.testing.assert_allclose(to_np(acc), got + 2.0, rtol=1e-12 if prec == "fp64" else 1e-6, atol=1e-6)
+    assert ref.shape[0] == dx.size
+    lens.close()
