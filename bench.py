@@ -54,11 +54,12 @@ FLOPS_ADJOINT = {"far_cells": 56, "near_point": 31, "near_full": 42, "big_correc
 
 
 # the potential walk's interactions (psi.cu, potential.cuh) counted the same
-# way, frozen before tuning: a far cell's M ln|w| - Re(Q2/2w^2) with its
-# deflection (46), a point's m ln r with its deflection (15), a truncated
-# Gaussian's potential inside its support with the Ein series as a 20-term
-# Horner polynomial (68), a big-list entry's (full - softened point) (77)
-FLOPS_PSI = {"far_cells": 46, "near_point": 15, "near_full": 68, "big_corrections": 77}
+# way: a far cell's M ln|w| - Re(Q2/2w^2) with its deflection (46), a
+# point's m ln r with its deflection (15), a truncated Gaussian's potential
+# inside its support with the Ein series as a 20-term Horner polynomial (68),
+# a big-list entry's (full - softened point) with Ein as u p(u - 9/4), p of
+# degree 9 (q <= 3) (56; 77 with the 20-term series it replaced)
+FLOPS_PSI = {"far_cells": 46, "near_point": 15, "near_full": 68, "big_corrections": 56}
 
 
 WALK_SOURCES = ("walk.cu", "walk_dev.cuh", "profiles.cuh")

@@ -18,7 +18,7 @@ template <typename T> struct PsiConsts {
     T EinU;  // Ein(q^2/2) of the species (Gaussian)
     T HX;    // H(R_max / r_s) of the species (NFW)
     T A0;    // N_q ln U_q - Ein(U_q) (Gaussian)
-    int series;  // U_q <= 5: Ein inside every support by the 20-term series
+    int series;  // 2: U_q <= 4.5, Ein by the degree-9 polynomial; 1: U_q <= 5, by the 20-term series
 };
 
 LENS_DEV float lg2_approx(float x)
@@ -43,6 +43,24 @@ LENS_DEV float2 ein_series2(float2 u)
 {
     constexpr float top = float(ein_coef(19));
     return __fmul2_rn(ein_horner2<18>(u, make_float2(top, top)), u);
+}
+
+template <int k> LENS_DEV float2 ein_cheb2(float2 t, float2 s)
+{
+    if constexpr (k < 0) {
+        return s;
+    } else {
+        constexpr float c = float(ein_cheb_coef(k));
+        return ein_cheb2<k - 1>(t, __ffma2_rn(s, t, make_float2(c, c)));
+    }
+}
+
+// Ein(u) for u <= 4.5 on a pair: u p(u - 9/4)
+LENS_DEV float2 ein_poly2(float2 u)
+{
+    constexpr float top = float(ein_cheb_coef(9)), mid = float(0.5 * kEinChebMax);
+    const float2 t = __fadd2_rn(u, make_float2(-mid, -mid));
+    return __fmul2_rn(ein_cheb2<8>(t, make_float2(top, top)), u);
 }
 
 template <int KIND, typename T, int R> struct PsiCtx {
@@ -183,7 +201,7 @@ template <int KIND, typename T, int R> struct PsiCtx {
     // ray beyond both softening radii (needs U_q <= 5).  P2 accumulates psi,
     // -alpha1, -alpha2 per entry slot.  EDGE: a ray may be outside a support,
     // where its terms are set to 0.
-    template <bool EDGE>
+    template <bool EDGE, bool POLY>
     LENS_DEV void big_pair(int i, float2 (&P2)[R][3], const float2 (&LX)[R], const float2 (&LY)[R])
     {
         const float2 nx = *reinterpret_cast<const float2*>(&B->bnx[i]);
@@ -207,7 +225,7 @@ template <int KIND, typename T, int R> struct PsiCtx {
             }
             const float2 e = make_float2(exp2_approx(tc.x), exp2_approx(tc.y));
             const float2 u = __fmul2_rn(tc, make_float2(nL, nL));
-            const float2 E = ein_series2(u);
+            const float2 E = POLY ? ein_poly2(u) : ein_series2(u);
             const float2 inv = make_float2(rcp(r2.x), rcp(r2.y));
             float2 nkb = __fmul2_rn(__ffma2_rn(mp, e, nme), inv);
             const float2 lg = make_float2(lg2_approx(u.x), lg2_approx(u.y));
@@ -226,7 +244,7 @@ template <int KIND, typename T, int R> struct PsiCtx {
     // Packed FP32 Gaussian buffer: the whole-group-inside region pair by pair
     // without tests, then the edge region pair by pair where both entries
     // have every ray beyond their softening radii, else entry by entry.
-    LENS_DEV void flush_big_pairs(int nbuf, float Nq)
+    template <bool POLY> LENS_DEV void flush_big_pairs(int nbuf, float Nq)
     {
         const int n_in = nbuf & 0xffff, n_out = nbuf >> 16;
         float2 P2[R][3], LX[R], LY[R];
@@ -238,14 +256,14 @@ template <int KIND, typename T, int R> struct PsiCtx {
             for (int q = 0; q < 3; ++q) P2[r][q] = make_float2(0.0f, 0.0f);
         }
         int i = 0;
-        for (; i + 1 < n_in; i += 2) big_pair<false>(i, P2, LX, LY);
+        for (; i + 1 < n_in; i += 2) big_pair<false, POLY>(i, P2, LX, LY);
         if (i < n_in) big_packed(i, Nq);
         i = kBigCap - n_out;
         if ((i & 1) && i < kBigCap) big_packed(i++, Nq);
         for (; i + 1 < kBigCap; i += 2) {
             const float2 w = *reinterpret_cast<const float2*>(&B->bw[i]);
             if (w.x < 0.0f && w.y < 0.0f) {
-                big_pair<true>(i, P2, LX, LY);
+                big_pair<true, POLY>(i, P2, LX, LY);
             } else {
                 big_packed(i, Nq);
                 big_packed(i + 1, Nq);
@@ -264,8 +282,10 @@ template <int KIND, typename T, int R> struct PsiCtx {
         if constexpr (KIND != LENS_POINT) {
             const T Nq = P.invNq > T(0) ? T(1) / P.invNq : T(0);
             if constexpr (WalkBuf<KIND, T>::kPackedBig) {
-                if (K.series) {
-                    flush_big_pairs(nb, Nq);
+                if (K.series == 2) {
+                    flush_big_pairs<true>(nb, Nq);
+                } else if (K.series == 1) {
+                    flush_big_pairs<false>(nb, Nq);
                 } else {
                     const int n_in = nb & 0xffff, n_out = nb >> 16;
                     for (int i = 0; i < n_in; ++i) big_packed(i, Nq);
@@ -512,7 +532,7 @@ static lens_status psi_typed(lens_tree* t, const ShootPlan& plan, const void* dx
         if (st.kind == LENS_GAUSS) {
             K.EinU = (T)ein<double>(st.Uq);
             K.A0 = (T)((1.0 - std::exp(-st.Uq)) * std::log(st.Uq) - ein<double>(st.Uq));
-            K.series = st.Uq <= 5.0 ? 1 : 0;
+            K.series = st.Uq <= kEinChebMax ? 2 : (st.Uq <= 5.0 ? 1 : 0);
         }
         if (st.kind == LENS_NFW) K.HX = (T)host_nfw_H(st.shape);
         launch(st.kind, K);

@@ -159,3 +159,21 @@ def test_potential_timing_and_counters():
     for k in ("groups", "visited", "cells", "leaf_particles", "big_kept", "ray_interactions"):
         assert c_psi[k] == c_fwd[k], k
     lens.close()
+
+
+@pytest.mark.parametrize("q", [3.0, 3.1, 3.5])
+def test_tree_ein_branches(q):
+    """The packed big-list potential takes Ein by the degree-9 polynomial for
+    q <= 3 (U_q <= 4.5), by the 20-term series up to U_q = 5, and the generic
+    per-entry form beyond: each against the oracle's direct potential at the
+    theta = 0.1 bar."""
+    parts = lensgen.nfw_particles(20000, 7, nsph=32)
+    g = lensgen.rng(81)
+    rx = g.uniform(-1, 1, 4096).astype(np.float32)
+    ry = g.uniform(-1, 1, 4096).astype(np.float32)
+    lens = L.Lens([L.Species.gauss(cu(parts), q)], theta=0.1, group_rays=64)
+    psi, _, _ = lens.potential(cu(rx), cu(ry))
+    ref = oracle.direct_potential(comps_gauss(parts, q), rx.astype(np.float64), ry.astype(np.float64))
+    e = np.abs(psi.cpu().numpy() - ref) / np.abs(ref)
+    assert np.median(e) <= 1e-4 and np.quantile(e, 0.99) <= 1e-3, (q, np.median(e), np.quantile(e, 0.99))
+    lens.close()
