@@ -110,9 +110,11 @@ __global__ void k_knn_gather(const float* xyz, int64_t n, const uint32_t* idx, f
     sp[i] = make_float4(xyz[3 * (int64_t)j], xyz[3 * (int64_t)j + 1], xyz[3 * (int64_t)j + 2], __uint_as_float(j));
 }
 
-// The k smallest values seen, unordered, with the largest tracked.
-struct KSmallest {
-    float v[kKnnMax];
+// The k smallest values seen (k <= K), unordered, with the largest tracked;
+// K fixed at compile time and every index a compile-time constant (selects),
+// so the values stay in registers.
+template <int K> struct KSmallest {
+    float v[K];
     int k, cnt, iw;
     float worst;
     LENS_DEV void reset(int kk, float bound)
@@ -121,23 +123,33 @@ struct KSmallest {
         cnt = 0;
         iw = 0;
         worst = bound;  // values above the bound are not kept
+#pragma unroll
+        for (int q = 0; q < K; ++q) v[q] = -INFINITY;
+    }
+    LENS_DEV void put(int at, float d2)
+    {
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            if (q == at) v[q] = d2;
     }
     LENS_DEV void offer(float d2)
     {
         if (cnt < k) {
             if (d2 > worst) return;
-            v[cnt++] = d2;
+            put(cnt++, d2);
             if (cnt == k) rescan();
         } else if (d2 < worst) {
-            v[iw] = d2;
+            put(iw, d2);
             rescan();
         }
     }
+    // slots at or beyond k hold -inf and are never the largest
     LENS_DEV void rescan()
     {
         iw = 0;
         worst = v[0];
-        for (int q = 1; q < k; ++q)
+#pragma unroll
+        for (int q = 1; q < K; ++q)
             if (v[q] > worst) {
                 worst = v[q];
                 iw = q;
@@ -162,13 +174,14 @@ struct KnnNode {
     int level;
 };
 
+template <int K>
 __global__ void __launch_bounds__(128)
 k_knn_query(const float4* sp4, const uint64_t* keys, int64_t n, int k, KnnCube c, float* r_out, uint32_t* err)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 p = sp4[i];
-    KSmallest S;
+    KSmallest<K> S;
     // upper bound: the k nearest among the 2k neighbours in key order
     S.reset(k, INFINITY);
     const int64_t w0 = i - k > 0 ? i - k : 0, w1 = i + k + 1 < n ? i + k + 1 : n;
@@ -311,7 +324,8 @@ extern "C" lens_status lens_smoothing_lengths(const float* xyz, int64_t n, int32
         radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, 3 * kKnnBits, base + o_tmp, s, &sk, &sv);
         k_knn_gather<<<(unsigned)G, TB, 0, s>>>(xyz, n, sv, sp);
         note_launch();
-        k_knn_query<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(sp, sk, n, k, c, r_sm, err);
+        if (k <= 32) k_knn_query<32><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(sp, sk, n, k, c, r_sm, err);
+        else k_knn_query<kKnnMax><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(sp, sk, n, k, c, r_sm, err);
         note_launch();
         e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
