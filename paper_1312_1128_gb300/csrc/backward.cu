@@ -203,7 +203,9 @@ template <int KIND, typename T> struct BackCtx {
     LENS_DEV void add_particle(int pid, T m, T gm, T gx, T gy)
     {
         double* g = P.gpart + 3 * (int64_t)pid;
-        if (m != T(0)) atomicAdd(g + 0, (double)gm / (double)m);
+        // dL/dm = gm / m in the working precision (an FP64 division is slow on
+        // this GPU's FP64 pipe); accumulated in FP64
+        if (m != T(0)) atomicAdd(g + 0, (double)(gm / m));
         atomicAdd(g + 1, (double)gx);
         atomicAdd(g + 2, (double)gy);
     }
