@@ -420,9 +420,32 @@ class MixedBatches(Workload):
     graph = True  # timed by the caller's events (a replayed graph records no internal events)
 
     def tune(self):
-        # the library's defaults: lens_autotune times one batch, which does
-        # not represent 256 uneven batches in one launch
-        pass
+        """Group size and walk form by the time of one replay of all 256
+        batches (lens_autotune times one batch, which does not represent
+        uneven batches in one launch)."""
+        import torch
+        L, w = self.L, self.w
+        best = None
+        for g, walk in [(32, "warp"), (64, "warp"), (32, "pairs"), (64, "pairs")]:
+            lens = L.Lens([L.Species.points(self.sp[0]), L.Species.nfw(self.sp[1], w["conc"])], theta=self.theta,
+                          group_rays=g, walk=walk)
+            lens.reserve(self.n_rays, 256)
+            t = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                lens.shoot_batches(w["offsets"], w["origins"], self.dx, self.dy, flags=L.USE_GRAPH, out=self.outs)
+                b.record()
+                torch.cuda.synchronize()
+                t.append(a.elapsed_time(b))
+            lens.close()
+            if best is None or min(t[1:]) < best[0]:
+                best = (min(t[1:]), g, walk)
+        _, self.group, self.walk = best
+        self.lens.close()
+        self.lens = L.Lens([L.Species.points(self.sp[0]), L.Species.nfw(self.sp[1], w["conc"])], theta=self.theta,
+                           group_rays=self.group, walk=self.walk)
+        self.lens.reserve(self.n_rays, 256)
 
     def step(self, flags):
         # LENS_TIMING does not combine with graph replay; COUNT does (own graph)
