@@ -135,36 +135,75 @@ __global__ void radix_hist_kernel(const K* keys, int64_t n, int shift, uint32_t*
 }
 
 // Stable scatter: element (block, r, t) precedes (block, r', t') iff
-// (r, t) < (r', t'), i.e. global index order, and equal digits keep it.
+// (r, t) < (r', t'), i.e. global index order, and equal digits keep it.  The
+// tile is first ordered by digit in shared memory (each element at its
+// digit's start in the tile plus its stable rank among the tile's equal
+// digits), then written out in that order: a digit's run of the tile goes to
+// consecutive output positions, so the stores coalesce.
 template <typename K>
-__global__ void radix_scatter_kernel(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
-                                     int64_t n, int shift, const uint32_t* offs, int64_t nblocks)
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const K* kin, const uint32_t* vin, K* kout,
+                                                                     uint32_t* vout, int64_t n, int shift,
+                                                                     const uint32_t* offs, int64_t nblocks)
 {
+    __shared__ K sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
     __shared__ uint32_t wcnt[kSortThreads / 32][kRadix];
     __shared__ uint32_t run[kRadix];
+    __shared__ uint32_t tstart[kRadix];
     __shared__ uint32_t base_off[kRadix];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const int tile_n = (int)(n - base < kSortTile ? n - base : kSortTile);
+    // the tile's digit counts, then their exclusive scan (one digit per thread)
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
         run[d] = 0;
+        tstart[d] = 0;
         base_off[d] = offs[(int64_t)d * nblocks + blockIdx.x];
     }
-    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    __syncthreads();
+    for (int e = threadIdx.x; e < tile_n; e += kSortThreads)
+        atomicAdd(&tstart[(uint32_t)(kin[base + e] >> shift) & 0xffu], 1u);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // 256 digits: each lane scans its 8 consecutive counts, then the lanes' totals
+        constexpr int per = kRadix / 32;
+        uint32_t c[per], tot = 0;
+#pragma unroll
+        for (int q = 0; q < per; ++q) {
+            c[q] = tstart[lane * per + q];
+            tot += c[q];
+        }
+        uint32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        uint32_t acc = incl - tot;
+#pragma unroll
+        for (int q = 0; q < per; ++q) {
+            tstart[lane * per + q] = acc;
+            acc += c[q];
+        }
+    }
+    __syncthreads();
+    // stable ranks, 256 elements at a time, placed in shared memory
     for (int r = 0; r < kSortItems; ++r) {
         for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads)
             (&wcnt[0][0])[i] = 0;
         __syncthreads();
-        int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
-        bool valid = idx < n;
-        K key = valid ? kin[idx] : K(0);
-        uint32_t d = valid ? ((uint32_t)(key >> shift) & 0xffu) : 0xffffffffu;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        const int e = r * kSortThreads + threadIdx.x;
+        const bool valid = e < tile_n;
+        const K key = valid ? kin[base + e] : K(0);
+        const uint32_t d = valid ? ((uint32_t)(key >> shift) & 0xffu) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
         if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
         __syncthreads();
         for (int dd = threadIdx.x; dd < kRadix; dd += kSortThreads) {
             uint32_t s = run[dd];
             for (int w = 0; w < kSortThreads / 32; ++w) {
-                uint32_t t = wcnt[w][dd];
+                const uint32_t t = wcnt[w][dd];
                 wcnt[w][dd] = s;
                 s += t;
             }
@@ -172,11 +211,20 @@ __global__ void radix_scatter_kernel(const K* kin, const uint32_t* vin, K* kout,
         }
         __syncthreads();
         if (valid) {
-            uint32_t pos = base_off[d] + wcnt[wid][d] + rank;
-            kout[pos] = key;
-            vout[pos] = vin[idx];
+            const uint32_t tp = tstart[d] + wcnt[wid][d] + rank;
+            sk[tp] = key;
+            sv[tp] = vin[base + e];
         }
         __syncthreads();
+    }
+    // out in digit order: element e of the ordered tile has digit d and goes to
+    // base_off[d] + (e - tstart[d])
+    for (int e = threadIdx.x; e < tile_n; e += kSortThreads) {
+        const K key = sk[e];
+        const uint32_t d = (uint32_t)(key >> shift) & 0xffu;
+        const uint32_t pos = base_off[d] + (uint32_t)e - tstart[d];
+        kout[pos] = key;
+        vout[pos] = sv[e];
     }
 }
 
