@@ -31,7 +31,11 @@
 //   border: until its largest border cell has area < f_area x its area and
 //     its outer border is as fine as its inner border, an image's border
 //     cells of the largest size are refined;
-// cells at level L_max are never refined.  Every decision compares FP64
+// cells at level L_max are never refined.  A source's images are final in
+// the border round that marks none of its cells: they are recorded then, and
+// its cells leave the working array in the same refinement pass (a count of
+// 0 in the scan), so later rounds touch only unfinished sources.  Every
+// decision compares FP64
 // values formed by the same operations on the host (exact per-level cell
 // counts for the areas) and on the device (explicit round-to-nearest
 // operations, no contraction), so that the cell sets follow the method's
