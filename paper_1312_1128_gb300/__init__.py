@@ -7,8 +7,14 @@ missing or CUDA is unavailable, the calls raise.
 
     lens = Lens(species=[Species.gauss(parts, q=3.0)], halos=[Halo.sis(0, 0, 0.5)],
                 theta=0.3)
-    a1, a2, kappa, g1, g2 = lens.shoot(rx, ry)              # device tensors
-    alpha, kappa, gamma = shoot(lens, rx, ry, masses=...)  # differentiable
+    a1, a2, kappa, g1, g2 = lens.shoot(rx, ry)          # device tensors (Sec. 3.2)
+    lens.shoot_batches(offsets, origins, rx, ry)          # uneven batches, one launch
+    psi, a1, a2 = lens.potential(rx, ry)                  # lensing potential (time delay)
+    grads = lens.backward(rx, ry, g_alpha1, g_alpha2)     # adjoint w.r.t. (m, x, y)
+    alpha = shoot(lens, rx, ry, species_data=parts)       # differentiable (autograd)
+    images, stats = lens.find_images(sources, x0, y0, side, n)   # Sec. 4 image finding
+    refine_cells(...)                                      # Sec. 3.4 cell interpolation
+    r_sm = smoothing_lengths(xyz, 32)                      # Sec. 3.1 smoothing lengths
 
 Ray positions are an FP64 origin plus offsets (float32 or float64 tensors), so
 microlensing-scale patches keep their resolution (the paper stores alpha in
