@@ -171,3 +171,19 @@ def test_telescoping_finds_the_faint_image():
     assert len(mus) == 2 and abs(mus[0] / mm - 1) < 7e-3 and abs(mus[1] / mp - 1) < 7e-3
     g = I._Grid(prm, alpha_sis)
     assert not any(c for c in g.inside((0.95, 0.0), 0.1) if I.cell_centre(prm, *c)[0] < 0)
+
+
+@pytest.mark.parametrize("n_min", [1000, 3000])
+def test_uniform_step_brings_every_image_to_n_min(n_min):
+    """I5 on its own: with a coarse telescoping (mu_min = 1) and a loose border
+    rule (f_area = 0.5) the images keep a few hundred cells, so every image
+    reaches n_min cells only through the uniform step; without it (n_min = 0)
+    they stay below."""
+    cases = [(0.5, 0.0, 0.1), (1.5, 0.0, 0.1)]
+    loose = dict(f_area=0.5, l_max=10, mu_min=1.0)
+    with_u = I.find_images(alpha_sis, cases, sis_params(n_min=n_min, **loose))
+    without = I.find_images(alpha_sis, cases, sis_params(n_min=0, **loose))
+    for a, b in zip(with_u, without):
+        assert len(a["images"]) == len(b["images"]) > 0
+        assert all(im["n_cells"] >= n_min for im in a["images"])
+        assert max(im["n_cells"] for im in b["images"]) < n_min
