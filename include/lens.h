@@ -178,7 +178,11 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species,
  *   alpha1 .. gamma2: DEVICE output arrays of n elements, float for an FP32
  *       tree, double for an FP64 tree.  kappa, gamma1, gamma2 may be NULL
  *       only with LENS_ALPHA_ONLY.
- *   flags: LENS_ALPHA_ONLY, LENS_DIRECT, LENS_ACCUMULATE.
+ *   flags: LENS_ALPHA_ONLY, LENS_DIRECT, LENS_ACCUMULATE, LENS_COUNT,
+ *       LENS_TIMING.
+ * A tree without particles (analytic components only) is shot one thread
+ * per ray with no ray grouping, except with LENS_COUNT or LENS_TIMING, whose
+ * counters and times refer to the grouped walk (the same terms either way).
  * Scratch buffers grow on demand (cudaMalloc, outside any graph capture).
  */
 lens_status lens_shoot_rays(lens_tree* tree, double origin_x, double origin_y,
