@@ -101,3 +101,44 @@ def test_closed_forms_continuity_and_sum():
     each = np.array([[psi_at(comps[j], x, y) for j in range(comps.size)] for x, y in zip(rx, ry)])
     np.testing.assert_allclose(tot, each.sum(axis=1), rtol=1e-13, atol=1e-15)
     np.testing.assert_allclose(ab, np.abs(each).sum(axis=1), rtol=1e-13)
+
+
+def arrival_time(comps, x, y, src):
+    """Eq. timedelay on one plane: tau(x) = |x - y_s|^2 / 2 - psi(x)."""
+    psi = oracle.direct_potential(comps, np.array([x]), np.array([y]))[0]
+    return 0.5 * ((x - src[0]) ** 2 + (y - src[1]) ** 2) - psi
+
+
+@pytest.mark.parametrize("b", [0.1, 0.35, 0.8])
+def test_sis_time_delay_between_images(b):
+    """SIS of Einstein radius r_E: images at x+- = b +- r_E along the source
+    direction (App. B); the arrival-time difference is 2 r_E b, and both
+    images are stationary points of tau (the lens equation)."""
+    rE = 0.7
+    sis = oracle.make_components(oracle.SIS, 0.0, 0.0, 0.0, rE)
+    src = (b * rE * np.cos(0.4), b * rE * np.sin(0.4))
+    u = np.array([np.cos(0.4), np.sin(0.4)])
+    yb = b * rE
+    xp, xm = (yb + rE) * u, (yb - rE) * u
+    dt = arrival_time(sis, *xm, src) - arrival_time(sis, *xp, src)
+    assert dt == pytest.approx(2 * rE * yb, rel=1e-12)
+    h = 1e-6
+    for xi in (xp, xm):
+        g = [(arrival_time(sis, *(xi + h * e), src) - arrival_time(sis, *(xi - h * e), src)) / (2 * h)
+             for e in (np.array([1.0, 0.0]), np.array([0.0, 1.0]))]
+        assert np.hypot(*g) < 1e-8
+
+
+@pytest.mark.parametrize("y", [0.2, 1.0, 2.5])
+def test_point_mass_time_delay_between_images(y):
+    """Point mass m (r_E^2 = m in m-units): images at x+- = (y +- sqrt(y^2 + 4))
+    / 2 in units of r_E; the arrival-time difference is r_E^2 [y sqrt(y^2 + 4)
+    / 2 + ln((sqrt(y^2 + 4) + y) / (sqrt(y^2 + 4) - y))]."""
+    m = 0.09
+    rE = np.sqrt(m)
+    pm = oracle.make_components(oracle.POINT, 0.0, 0.0, m)
+    s = np.sqrt(y * y + 4)
+    src = (y * rE, 0.0)
+    xp, xm = 0.5 * (y + s) * rE, 0.5 * (y - s) * rE
+    dt = arrival_time(pm, xm, 0.0, src) - arrival_time(pm, xp, 0.0, src)
+    assert dt == pytest.approx(m * (0.5 * y * s + np.log((s + y) / (s - y))), rel=1e-12)
