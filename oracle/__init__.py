@@ -10,7 +10,7 @@ Functions
 ---------
 eval_component(comp, x, y)      one component's (a1, a2, kappa, g1, g2)
 direct_sum(comps, rx, ry)       Sec. 5.1 theta=0 limit: sum over all components
-direct_vjp(comps, rx, ry, G)    gradient of a loss of alpha w.r.t. (m, x, y)
+direct_vjp(comps, rx, ry, G)    gradient of a loss of alpha w.r.t. (m, x, y[, p0, p1])
 potential_component / direct_potential   lensing potential psi (Eq. alpha, Eq. timedelay)
 PaperTree(comps, leaf_max, th)  Sec. 3.2 tree, evaluated ray by ray, with counts
 refine.refine_cells(...)        Sec. 3.4 cell interpolation with A from App. A (numpy)
@@ -71,7 +71,7 @@ def _load():
         lib.or_potential_component.restype = d
         lib.or_direct_potential.argtypes = [vp, i64, vp, vp, i64, vp, vp, i32]
         lib.or_direct_potential.restype = i32
-        lib.or_direct_vjp.argtypes = [vp, i64, vp, vp, i64, vp, vp, i32]
+        lib.or_direct_vjp.argtypes = [vp, i64, vp, vp, i64, vp, vp, i32, i32]
         lib.or_direct_vjp.restype = i32
         lib.or_tree_build.argtypes = [vp, i64, i32, d]
         lib.or_tree_build.restype = vp
@@ -154,17 +154,19 @@ def direct_potential(comps, rx, ry, nthreads: int = 0, with_absum: bool = False)
     return (out, ab) if with_absum else out
 
 
-def direct_vjp(comps, rx, ry, G, nthreads: int = 0) -> np.ndarray:
+def direct_vjp(comps, rx, ry, G, nthreads: int = 0, params: bool = False) -> np.ndarray:
     """dL/d(m, x, y) for every component, given G = dL/d(outputs) (nr, 5);
-    only the alpha columns of G may be non-zero."""
+    only the alpha columns of G may be non-zero.  With params, (nc, 5):
+    also dL/d(p0, p1), the component's shape parameters (GAUSS r_sm, q; NFW
+    r_s, R_max; SIS r_E; DISK R)."""
     lib = _load()
     c = np.ascontiguousarray(np.asarray(comps, COMP_DTYPE).reshape(-1))
     rx = np.ascontiguousarray(rx, dtype=np.float64).reshape(-1)
     ry = np.ascontiguousarray(ry, dtype=np.float64).reshape(-1)
     G = np.ascontiguousarray(G, dtype=np.float64).reshape(rx.size, 5)
-    grad = np.zeros((c.size, 3))
+    grad = np.zeros((c.size, 5 if params else 3))
     rc = lib.or_direct_vjp(_ptr(c), c.size, _ptr(rx), _ptr(ry), rx.size, _ptr(G), _ptr(grad),
-                           int(nthreads))
+                           1 if params else 0, int(nthreads))
     if rc != 0:
         raise ValueError("direct_vjp supports gradients of alpha only")
     return grad

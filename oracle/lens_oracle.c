@@ -22,7 +22,8 @@
  *     r_cut = r_cm / theta_force (Eq. r_cut), the 2D MAC, big-particle lists;
  *     evaluated ray by ray with per-ray interaction counts;
  *   - the vector-Jacobian product of the direct sum (gradient of a loss with
- *     respect to particle masses and positions) for the differentiable fit.
+ *     respect to particle masses, positions and shape parameters) for the
+ *     differentiable fit.
  *
  * Units: masses are in "m-units", m = M / (pi Sigma_crit), so a point mass has
  * alpha = m x / |x|^2 (Sec. 3.5) and kappa = pi * (m-unit surface density).
@@ -316,25 +317,80 @@ int or_direct_potential(const or_comp* comps, int64_t nc, const double* rx, cons
     return 0;
 }
 
+/* Derivatives of the enclosed mass Mt(<r) with respect to the component's
+ * shape parameters p0 and p1 at radius r > 0 (the profiles of or_profile
+ * above, differentiated at fixed r and m).  alpha = Mt w / r^2, so
+ * d alpha / d p = (d Mt / d p) w / r^2.
+ *   GAUSS (p0 = r_sm, p1 = q), inside r < q r_sm, u = r^2 / (2 r_sm^2):
+ *     Mt = m (1 - e^-u) / N_q,  du/dr_sm = -2u / r_sm,
+ *     dN_q/dq = q e^{-q^2/2}; the support edge moves with both but Mt is
+ *     continuous there (= m), so nothing is added at the edge.
+ *   NFW (p0 = r_s, p1 = R_max), inside r < R_max, x = r/r_s, X = R_max/r_s:
+ *     Mt = m g(x) / g(X) with g' = x f (Sec. 3.2 projected NFW).
+ *   SIS (p0 = r_E): Mt = r_E r.
+ *   DISK (p0 = R), inside r < R: Mt = m r^2 / R^2.
+ *   Outside a truncated profile Mt = m does not depend on p0, p1. */
+static void or_profile_dparams(const or_comp* c, double r, double* d0, double* d1)
+{
+    *d0 = 0.0;
+    *d1 = 0.0;
+    switch (c->type) {
+    case OR_GAUSS: {
+        double sig = c->p0, q = c->p1;
+        if (r < q * sig) {
+            double Nq = -expm1(-0.5 * q * q), u = r * r / (2.0 * sig * sig);
+            double Mt = c->m * (-expm1(-u)) / Nq;
+            *d0 = c->m * exp(-u) * (-2.0 * u / sig) / Nq;
+            *d1 = -Mt * q * exp(-0.5 * q * q) / Nq;
+        }
+        return;
+    }
+    case OR_NFW: {
+        double rs = c->p0, Rmax = c->p1;
+        if (r < Rmax) {
+            double x = r / rs, X = Rmax / rs, gx = nfw_g(x), gX = nfw_g(X);
+            double dgx = x * nfw_f(x), dgX = X * nfw_f(X);   /* g'(x), g'(X) */
+            /* dx/dr_s = -x/r_s, dX/dr_s = -X/r_s, dX/dR_max = 1/r_s */
+            *d0 = c->m * (dgx * (-x / rs) * gX - gx * dgX * (-X / rs)) / (gX * gX);
+            *d1 = -c->m * gx * dgX / (rs * gX * gX);
+        }
+        return;
+    }
+    case OR_SIS:
+        *d0 = r;
+        return;
+    case OR_DISK: {
+        double R = c->p0;
+        if (r < R) *d0 = -2.0 * c->m * r * r / (R * R * R);
+        return;
+    }
+    default:
+        return;
+    }
+}
+
 /* Vector-Jacobian product of the direct sum: given upstream gradients
  * G (nr x 5, for alpha1, alpha2, kappa, gamma1, gamma2 at each ray), returns
- * grad (nc x 3) = dL/d(m, x, y) of every component.  Only the alpha part of G
- * may be non-zero (the loss of the differentiable fit is a function of alpha);
- * a non-zero kappa/gamma gradient returns -1.
+ * grad (nc x 3, or nc x 5 with with_params) = dL/d(m, x, y[, p0, p1]) of every
+ * component.  Only the alpha part of G may be non-zero (the loss of the
+ * differentiable fit is a function of alpha); a non-zero kappa/gamma gradient
+ * returns -1.
  *   d alpha / d m = alpha / m (every profile is linear in m at fixed shape);
  *   d alpha / d x_p = -(Jacobian of alpha at the ray), with the Jacobian
- *   [[kappa+gamma1, gamma2], [gamma2, kappa-gamma1]] from Eqs. kappa-gamma_2. */
+ *   [[kappa+gamma1, gamma2], [gamma2, kappa-gamma1]] from Eqs. kappa-gamma_2;
+ *   d alpha / d p0, p1 = (d Mt / d p) w / r^2 (or_profile_dparams). */
 int or_direct_vjp(const or_comp* comps, int64_t nc, const double* rx, const double* ry,
-                  int64_t nr, const double* G, double* grad, int nthreads)
+                  int64_t nr, const double* G, double* grad, int with_params, int nthreads)
 {
     for (int64_t i = 0; i < nr; ++i)
         if (G[5 * i + 2] != 0.0 || G[5 * i + 3] != 0.0 || G[5 * i + 4] != 0.0) return -1;
+    const int st = with_params ? 5 : 3;
 #ifdef _OPENMP
     const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #endif
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int64_t j = 0; j < nc; ++j) {
-        nsum gm = {0, 0}, gx = {0, 0}, gy = {0, 0};
+        nsum gm = {0, 0}, gx = {0, 0}, gy = {0, 0}, g0 = {0, 0}, g1s = {0, 0};
         double t[5];
         for (int64_t i = 0; i < nr; ++i) {
             double g1 = G[5 * i], g2 = G[5 * i + 1];
@@ -345,10 +401,24 @@ int or_direct_vjp(const or_comp* comps, int64_t nc, const double* rx, const doub
             double a11 = t[2] + t[3], a22 = t[2] - t[3], a12 = t[4];
             nadd(&gx, -(g1 * a11 + g2 * a12));
             nadd(&gy, -(g1 * a12 + g2 * a22));
+            if (with_params) {
+                double dx = rx[i] - comps[j].x, dy = ry[i] - comps[j].y, r2 = dx * dx + dy * dy;
+                if (r2 > 0.0) {
+                    double d0, d1;
+                    or_profile_dparams(&comps[j], sqrt(r2), &d0, &d1);
+                    double gw = (g1 * dx + g2 * dy) / r2;
+                    nadd(&g0, d0 * gw);
+                    nadd(&g1s, d1 * gw);
+                }
+            }
         }
-        grad[3 * j] = gm.s + gm.c;
-        grad[3 * j + 1] = gx.s + gx.c;
-        grad[3 * j + 2] = gy.s + gy.c;
+        grad[st * j] = gm.s + gm.c;
+        grad[st * j + 1] = gx.s + gx.c;
+        grad[st * j + 2] = gy.s + gy.c;
+        if (with_params) {
+            grad[st * j + 3] = g0.s + g0.c;
+            grad[st * j + 4] = g1s.s + g1s.c;
+        }
     }
     return 0;
 }
