@@ -42,15 +42,32 @@ UNIT = "rays/s"
 WORKLOAD = "nfw_sph_1e6_2048sq"
 THETA = 0.3
 
-# FP32 flops per interaction as the kernels write them (FADD/FMUL = 1,
-# FFMA = 2, MUFU = 1), frozen before tuning.
-FLOPS = {"far_cells": 50, "near_point": 22, "near_full": 33, "big_corrections": 38}
+# FP32 flops per interaction as the kernels evaluate them now (FADD/FMUL =
+# 1, FFMA = 2, MUFU = 1; comparisons and selects 0; a packed FFMA2 counts as
+# its two FFMAs), term by term:
+#   far cell (cell_terms): w 2, r^2 3, 1/r^2 1, u = 1/w 2, u^2 5, u^3 6,
+#     alpha 12, u^4 5, 3 Q2 2, gamma 12 = 50 (alpha only: 31);
+#   leaf point (point_terms + radial): w 2, r^2 3, 1/r^2, kb, D 3, radial 14
+#     = 22 (alpha only: 11);
+#   leaf Gaussian inside its support (gauss_terms + radial): w 2, r^2 3, u 1,
+#     1/r^2 1, e^-u 2, h1 and g 4, m c / N_q 2, kb, kappa, D 4, radial 14 = 33
+#     (alpha only: 19);
+#   big-list correction (gauss_correction_x2, per entry and ray): w 2, w_y^2
+#     1, r^2 2, t 1, 2^-t 1, 1/r^2 1, -dkb 3, alpha 4, kappa 2, P 2, gamma1 3,
+#     w_x w_y 1, gamma2 2 = 26 (alpha only: 15).
+FLOPS = {"far_cells": 50, "near_point": 22, "near_full": 33, "big_corrections": 26}
 # the same interactions when only alpha is accumulated (LENS_ALPHA_ONLY)
-FLOPS_ALPHA = {"far_cells": 31, "near_point": 11, "near_full": 20, "big_corrections": 16}
+FLOPS_ALPHA = {"far_cells": 31, "near_point": 11, "near_full": 19, "big_corrections": 15}
 # the adjoint's per-interaction work for alpha gradients, as backward.cu
-# writes it: the forward term plus the gradient update (23 flops), and for a
-# far cell the cell adjoints dL/dM, dL/dQ2, dL/dz_cm
-FLOPS_ADJOINT = {"far_cells": 56, "near_point": 31, "near_full": 42, "big_corrections": 37}
+# writes it: a far cell's dL/dM, dL/dQ2, dL/dz_cm over the group's rays (w 2,
+# 1/r^2 4, u 2, u^2 5, u^3 6, u^4 5, dL/dM 4, dL/dQ2 8, dL/dz_cm 20 = 56);
+# a particle term's forward value plus its gradient update (term_grad: G.w
+# 3, c2 s2 5, gamma 2, m 2, size 2, position 10 = 24): point 8 + 24,
+# Gaussian 19 + 24, big-list correction 14 + 24
+FLOPS_ADJOINT = {"far_cells": 56, "near_point": 32, "near_full": 43, "big_corrections": 38}
+# the survey's nominal table (written before the kernels existed), reported
+# beside the kernel's own counts for the headline workload
+FLOPS_NOMINAL = {"far_cells": 46, "near_point": 20, "near_full": 32, "big_corrections": 35}
 
 
 # the potential walk's interactions (psi.cu, potential.cuh) counted the same
@@ -242,6 +259,7 @@ class NfwSph(Workload):
     tree build + ray grouping + walk."""
     name = WORKLOAD
     FLOPS = FLOPS
+    FLOPS_NOMINAL = FLOPS_NOMINAL
 
     def __init__(self, grid=2048):
         self.w = lensgen.workload_nfw_sph(n_grid=grid)
@@ -294,6 +312,41 @@ class NfwSph(Workload):
         p = w["gauss"].astype(np.float64)
         comps = oracle.make_components(oracle.GAUSS, p[:, 0], p[:, 1], p[:, 2], p[:, 3], w["q"])
         return _oracle_loop(oracle, comps, w["rx"], w["ry"], None, budget, seed)
+
+    def direct_forms(self, torch, dev, fp64_peak):
+        """The plain direct-sum forms of this lens on the GPU, FP64 and FP32,
+        on 4,096 sampled grid rays (every particle for every ray, the tree's
+        theta -> 0 limit): rays/s beside the tree's, and the FP64 form's
+        fraction of the measured FP64 peak.  Direct flops per ray: a
+        Gaussian inside its support 33, a point mass outside 22 (the walk's
+        table), with the support count per ray from the paper tree's big-list
+        corrections (every particle whose support covers the ray)."""
+        L, w = self.L, self.w
+        idx = lensgen.sample_indices(lensgen.rng(4246), self.n_rays, 4096)
+        with open(os.path.join(ROOT, "tests", "golden", "useful_counts.json")) as f:
+            inside = json.load(f)[WORKLOAD][str(self.theta)]["big_corrections"]
+        n = w["gauss"].shape[0]
+        fpr = inside * FLOPS["near_full"] + (n - inside) * FLOPS["near_point"]
+        out = {}
+        for prec, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+            lens = L.Lens([L.Species.gauss(self.parts.to(dt), w["q"])], theta=self.theta, precision=prec)
+            dx = torch.from_numpy(w["rx"][idx]).to(dev).to(dt)
+            dy = torch.from_numpy(w["ry"][idx]).to(dev).to(dt)
+            ms = []
+            for _ in range(4):
+                lens.shoot(dx, dy, flags=L.DIRECT | L.TIMING)
+                ms.append(lens.last_timing()[1])
+            lens.close()
+            t = float(np.median(ms[1:]))
+            peak = fp64_peak if prec == "fp64" else None
+            out[prec] = {"rays_per_s": 4096 / (t * 1e-3), "walk_ms": t, "rays": 4096,
+                         "interactions_per_s": 4096 * n / (t * 1e-3),
+                         "achieved_tflops": fpr * 4096 / (t * 1e-3) / 1e12,
+                         **({"fp64_peak_tflops": peak / 1e12, "frac_of_fp64_peak": fpr * 4096 / (t * 1e-3) / peak}
+                            if peak else {}),
+                         "error": "exact sum: FP64 within 1e-12, FP32 within 1e-5 or 8 roundings of sum |term|"}
+        out["flops_per_ray"] = fpr
+        return out
 
     def cpu_other(self, budget=4.0):
         """The oracle's direct sum on one core, and the oracle's paper tree
@@ -391,7 +444,10 @@ class MixedBatches(Workload):
     built once (an adaptive-refinement loop reuses it), so a step is one
     pass over all batches."""
     name = "mixed_batches_256"
-    FLOPS = {"far_cells": 50, "near_point": 22, "near_full": 60, "big_corrections": 70}
+    # NFW leaf inside R_max (nfw_terms: F, f, g with sqrt, log, log1p counted
+    # as one operation each, 29, + w, r^2 5 + radial 14 = 48); an NFW big-list
+    # correction (the same minus the softened point: 52)
+    FLOPS = {"far_cells": 50, "near_point": 22, "near_full": 48, "big_corrections": 52}
 
     def __init__(self):
         self.w = lensgen.workload_mixed_batches()
@@ -482,7 +538,7 @@ class Microlensing(Workload):
     name = "microlensing_1e7_4096sq"
     theta = 0.1
     FLOPS = {"far_cells": 50, "near_point": 22}
-    SIS_FLOPS = 20
+    SIS_FLOPS = 23  # w 2, r^2 3, sqrt 1, kb 1, kappa 1, D 1, radial 14
 
     def __init__(self):
         self.w = lensgen.workload_microlensing()
@@ -580,13 +636,13 @@ class Fit(Workload):
         self.at = [a.clone() for a in at[:2]]
         tl.close()
         self.outs = [torch.empty(self.n_rays, dtype=torch.float32, device=dev) for _ in range(5)]
-        self.grad = torch.zeros(self.parts.shape[0], 3, dtype=torch.float32, device=dev)
+        self.grad = torch.zeros(self.parts.shape[0], 4, dtype=torch.float32, device=dev)
         self.group = 32
         self.walk = "default"
         self.h = [torch.from_numpy(w["gauss"]).pin_memory(), torch.from_numpy(w["rx"]).pin_memory(),
                   torch.from_numpy(w["ry"]).pin_memory()]
         self.d = [torch.empty_like(x, device=dev) for x in self.h]
-        self.hgrad = torch.empty(self.parts.shape[0], 3, dtype=torch.float32).pin_memory()
+        self.hgrad = torch.empty(self.parts.shape[0], 4, dtype=torch.float32).pin_memory()
         self.hloss = torch.empty(1, dtype=torch.float32).pin_memory()
         self.back_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
 
@@ -1076,8 +1132,156 @@ def run_gpu_refine(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+class PointDiskFp64:
+    """The FP64 form (Sec. 5.1's direct-summation comparison; alpha kept in
+    higher precision, Sec. 3.4): 2,000 equal point masses in the unit disk,
+    a 64 x 64 FP64 grid over [-1.2, 1.2]^2; step = FP64 tree build + the FP64
+    direct sum + the FP64 tree walk at theta = 0.1, both for every ray."""
+    name = "point_disk_2000_64sq_fp64"
+    metric = "rays/sec (alpha+kappa+gamma), FP64 direct sum and FP64 tree at theta = 0.1"
+    unit = "rays/s"
+    theta = 0.1
+    FLOPS_DIRECT = 22     # a point mass's alpha + kappa + gamma (the FP32 table's count)
+    FLOPS = {"far_cells": 50, "near_point": 22}
+
+    def __init__(self):
+        self.w = lensgen.workload_point_disk()
+        self.n_rays = self.w["rx"].size
+        self.n = self.w["points"].shape[0]
+
+    def config(self, ws):
+        return {"workload": self.name, "n_points": self.n, "grid": 64, "extent": "[-1.2, 1.2]^2",
+                "theta": self.theta, "leaf_max": 5, "precision": "fp64 throughout",
+                "error": "direct sum within 1e-12 of the FP64 oracle; tree median alpha error <= 1e-4",
+                "l2": "flushed between timed steps (256 MB write)",
+                "parallelism": f"independent replicas x{ws}"}
+
+    def tree_flops_per_ray(self):
+        with open(os.path.join(ROOT, "tests", "golden", "useful_counts.json")) as f:
+            c = json.load(f)["point_disk_2000_64sq"][str(self.theta)]
+        return sum(self.FLOPS[k] * c[k] for k in self.FLOPS)
+
+    def prepare(self, L, torch, dev):
+        w = self.w
+        self.L = L
+        self.parts = torch.from_numpy(w["points"]).to(dev)
+        self.rx, self.ry = torch.from_numpy(w["rx"]).to(dev), torch.from_numpy(w["ry"]).to(dev)
+        self.od = [torch.empty(self.n_rays, dtype=torch.float64, device=dev) for _ in range(5)]
+        self.ot = [torch.empty(self.n_rays, dtype=torch.float64, device=dev) for _ in range(5)]
+        self.h = [torch.from_numpy(w["points"]).pin_memory(), torch.from_numpy(w["rx"]).pin_memory(),
+                  torch.from_numpy(w["ry"]).pin_memory()]
+        self.d = [torch.empty_like(x, device=dev) for x in self.h]
+        self.hout = [torch.empty(self.n_rays, dtype=torch.float64).pin_memory() for _ in range(10)]
+
+    def step(self, flags=0, inputs=None):
+        L = self.L
+        parts, rx, ry = inputs if inputs is not None else (self.parts, self.rx, self.ry)
+        lens = L.Lens([L.Species.points(parts)], theta=self.theta, precision="fp64")
+        lens.shoot(rx, ry, flags=flags | L.DIRECT, out=self.od)
+        t_direct = lens.last_timing()[1] if flags & L.TIMING else None
+        lens.shoot(rx, ry, flags=flags, out=self.ot)
+        t_tree = lens.last_timing()[1] if flags & L.TIMING else None
+        return lens, t_direct, t_tree
+
+    def e2e(self):
+        for d, h in zip(self.d, self.h):
+            d.copy_(h, non_blocking=True)
+        lens, _, _ = self.step(0, self.d)
+        for h, o in zip(self.hout, self.od + self.ot):
+            h.copy_(o, non_blocking=True)
+        return lens, sum(x.numel() * 8 for x in self.h), 10 * self.n_rays * 8
+
+    oracle_desc = "rays of the grid, FP64 direct sum over every point mass (the oracle), all host cores"
+
+    def oracle_rate(self, budget, seed=7):
+        import oracle
+        p = self.w["points"]
+        comps = oracle.make_components(oracle.POINT, p[:, 0], p[:, 1], p[:, 2])
+        return _oracle_loop(oracle, comps, self.w["rx"], self.w["ry"], None, budget, seed)
+
+
+def run_gpu_fp64(args, ws, rank, local):
+    """The FP64 workload: same timing rules as run_gpu (warm-up, L2 flush
+    between timed steps, CUDA events, max over ranks, clocks)."""
+    import torch
+
+    import paper_1312_1128_gb300 as L
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = PointDiskFp64()
+    wl.prepare(L, torch, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lib = L.lib()
+    for _ in range(args.warmup):
+        wl.step(L.TIMING)[0].close()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    launches0 = lib.lens_kernel_launches()
+    t_dir, t_tree = [], []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ev[k][0].record()
+        lens, a, b = wl.step(L.TIMING)
+        ev[k][1].record()
+        torch.cuda.synchronize()
+        t_dir.append(a)
+        t_tree.append(b)
+        lens.close()
+    barrier(ws)
+    launches = lib.lens_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms, value = replica_rate(ws, wl.n_rays, float(np.mean(step_ms)), dev)
+    wl.e2e()[0].close()  # one untimed call first, like the warm-up steps
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2)):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        barrier(ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lens, h2d, d2h = wl.e2e()
+        b.record()
+        torch.cuda.synchronize()
+        lens.close()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e, e2e_value = replica_rate(ws, wl.n_rays, float(np.mean(e2e_ms)), dev)
+    peak64 = L.fp64_peak(256)
+    d_ms, tr_ms = float(np.median(t_dir)), float(np.median(t_tree))
+    d_flops = wl.n_rays * wl.n * wl.FLOPS_DIRECT
+    achieved = d_flops / (d_ms * 1e-3) / 1e12
+    tree_fpr = wl.tree_flops_per_ray()
+    line = {"metric": wl.metric, "value": value, "unit": wl.unit, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": wl.config(ws),
+            "e2e": {"value": e2e_value, "unit": wl.unit, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved * 1e12 / peak64, "traffic": None,
+                         "peak_basis": "measured FP64 DFMA rate (lens_fp64_peak, every SM)",
+                         "kernel": "FP64 direct sum (walk_kernel, LENS_DIRECT), CUDA events on its stream",
+                         "useful_flops": d_flops, "direct_ms": d_ms},
+            "direct": {"ms": d_ms, "rays_per_s": wl.n_rays / (d_ms * 1e-3),
+                       "interactions_per_s": wl.n_rays * wl.n / (d_ms * 1e-3)},
+            "tree": {"ms": tr_ms, "rays_per_s": wl.n_rays / (tr_ms * 1e-3), "theta": wl.theta,
+                     "useful_flops_per_ray": tree_fpr,
+                     "achieved_tflops": tree_fpr * wl.n_rays / (tr_ms * 1e-3) / 1e12,
+                     "frac_of_fp64_peak": tree_fpr * wl.n_rays / (tr_ms * 1e-3) / peak64},
+            "clocks": clk, "gpu_launches": int(launches)}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r, done_n, dt, cores = wl.oracle_rate(min(args.cpu_seconds, 10.0))
+        line["cpu_baseline"] = {"value": r, "unit": wl.unit, "cores": cores, "kind": "oracle",
+                                "sample": f"{done_n} {wl.oracle_desc}, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 WORKLOADS = {"nfw_sph": NfwSph, "mixed_batches": MixedBatches, "microlensing": Microlensing, "fit": Fit,
-             "refine": Refine, "knn": Knn, "potential": Potential, "images": Images}
+             "refine": Refine, "knn": Knn, "potential": Potential, "images": Images, "point_disk_fp64": PointDiskFp64}
 
 
 def _oracle_loop(oracle, comps, rx, ry, _, budget_s, seed, nthreads=0, potential=False):
@@ -1211,8 +1415,18 @@ def run_gpu(args, ws, rank, local):
         done(lens)
     e2e, e2e_value = replica_rate(ws, n_rays, float(np.mean(e2e_ms)), dev)
 
+    direct = None
+    if hasattr(wl, "direct_forms"):
+        direct = wl.direct_forms(torch, dev, L.fp64_peak(256))
+
     # roofline of the dominant kernel (the forward walk): useful flops / its duration
     fpr = wl.flops_per_ray()
+    nominal_fpr = None
+    if getattr(wl, "FLOPS_NOMINAL", None):
+        saved = wl.FLOPS
+        wl.FLOPS = wl.FLOPS_NOMINAL
+        nominal_fpr = wl.flops_per_ray()
+        wl.FLOPS = saved
     w_ms = float(np.mean(walk_ms))
     achieved = fpr * n_rays / (w_ms * 1e-3) / 1e12
     props = torch.cuda.get_device_properties(dev)
@@ -1235,6 +1449,8 @@ def run_gpu(args, ws, rank, local):
                                        f"{sm_max:.0f} MHz (max SM clock)",
                          "fp32_ffma_measured": measured_peak,
                          "useful_flops_per_ray": fpr, "walk_ms": w_ms,
+                         **({"frac_nominal_table": nominal_fpr * n_rays / (w_ms * 1e-3) / 1e12 / peak,
+                             "useful_flops_per_ray_nominal_table": nominal_fpr} if nominal_fpr else {}),
                          "group_ms": float(np.mean(group_ms))},
             "build_ms_phases": build_phases,
             **({"build": build_roofline(build_sizes[0], build_sizes[1], sum(build_phases))}
@@ -1245,6 +1461,7 @@ def run_gpu(args, ws, rank, local):
             **({k: float(np.mean([e[k] for e in extras])) for k in extras[0]} if extras and extras[0] else {}),
             "interactions": {k: cnt[k] for k in ["groups", "visited", "cells", "leaf_particles",
                                                  "big_scanned", "big_kept", "ray_interactions"]},
+            **({"direct_sum_forms": direct} if direct else {}),
             "clocks": clk, "gpu_launches": int(launches)}
     if hasattr(wl, "adjoint_flops_per_ray"):
         # the adjoint dominates this step: its roofline is the line's
@@ -1299,7 +1516,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", choices=["nfw_sph", "mixed_batches", "microlensing", "fit", "refine", "knn",
-                                           "potential", "images"],
+                                           "potential", "images", "point_disk_fp64"],
                     default="nfw_sph",
                     help="nfw_sph (default) is the headline; the others measure the batched, "
                          "microlensing and differentiable paths")
@@ -1334,6 +1551,8 @@ def main():
             run_gpu_knn(args, ws, rank, local)
         elif args.workload == "images":
             run_gpu_images(args, ws, rank, local)
+        elif args.workload == "point_disk_fp64":
+            run_gpu_fp64(args, ws, rank, local)
         else:
             run_gpu(args, ws, rank, local)
     if ws > 1:

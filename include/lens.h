@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define LENS_API_VERSION 1
+#define LENS_API_VERSION 2
 
 typedef enum lens_status {
     LENS_OK = 0,
@@ -211,20 +211,31 @@ lens_status lens_shoot_batches(lens_tree* tree, int64_t n_batches, const int64_t
 
 /*
  * lens_shoot_rays_backward -- vector-Jacobian product of lens_shoot_rays:
- * given dL/d(outputs) at n rays, accumulates dL/d(particle mass, x, y) and
- * dL/d(halo parameters).  No counterpart in the paper: it differentiates the
- * tree approximation the forward computes (cells' monopole and quadrupole
- * moments as functions of their particles), for lens-model fitting.
+ * given dL/d(outputs) at n rays, accumulates dL/d(particle mass, position,
+ * size) and dL/d(halo parameters).  No counterpart in the paper: it
+ * differentiates the tree approximation the forward computes (cells'
+ * monopole and quadrupole moments as functions of their particles; each
+ * profile's enclosed mass as a function of its size and shape, Sec. 3.1 and
+ * Sec. 3.2), for lens-model fitting.
  *   ray arguments: exactly those of the forward call.
  *   g_alpha1, g_alpha2: DEVICE arrays of n gradients (output dtype); g_kappa,
  *       g_gamma1, g_gamma2 must be NULL in this version (LENS_ERR_UNSUPPORTED
  *       otherwise).
  *   g_species: HOST array of n_species DEVICE pointers (NULL entries skip a
- *       species); each receives n x 3 {dL/dm, dL/dx, dL/dy} in the tree's
- *       precision, ADDED to its contents.
- *   g_halos: DEVICE array n_halos x 3 doubles {dL/dm (dL/dr_E for SIS),
- *       dL/dx, dL/dy}, added to, or NULL.
+ *       species); each receives n x 4 {dL/dm, dL/dx, dL/dy, dL/dp} in the
+ *       tree's precision, ADDED to its contents, in the species' input order;
+ *       p is the species' fourth column (GAUSS r_sm, NFW r_s at the fixed
+ *       ratio R_max / r_s; 0 for POINT).
+ *   g_halos: DEVICE array n_halos x 5 doubles, added to, or NULL:
+ *       {dL/dm (dL/dr_E for the SIS), dL/dx, dL/dy, dL/dp0, dL/dp1} with p0, p1
+ *       the lens_halo fields (GAUSS r_sm, q; NFW r_s, R_max; SIS r_E again,
+ *       0; DISK R, 0; POINT 0, 0).
  *   flags: LENS_DIRECT differentiates the direct sum instead of the tree.
+ * Tree gradients with respect to masses and positions follow the tree's
+ * moments (so they carry the tree's own approximation error); size and halo
+ * parameter gradients equal the direct sum's, since every ray inside a
+ * particle's support meets its full profile.  Scratch: about 32 B per
+ * particle and 88 B per tree node, from the stream-ordered pool.
  */
 lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double origin_y,
                                      const void* ray_dx, const void* ray_dy, int32_t ray_dtype,
@@ -255,20 +266,26 @@ lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, con
  * cudaMalloc may cause, or deployments that reserve a fixed device budget up
  * front.  The paper has no counterpart; it is a deployment variant only.
  *   Arguments, output layout and results are those of lens_shoot_rays with
- *   LENS_DIRECT (rays are grouped 32 at a time in their input order instead
- *   of being sorted, so results can differ from it by FP32 rounding).
+ *   LENS_DIRECT, except that rays are grouped 32 at a time in their input
+ *   order instead of being sorted: give them in a spatially coherent order
+ *   (rows of a grid, Morton order).  An FP32 tree forms each ray's offset
+ *   from its group's anchor in FP32 (exactly when the positions are FP32
+ *   values), so a group that spans a large extent rounds its rays' positions
+ *   more coarsely than the sorting call does.
  *   flags: LENS_ALPHA_ONLY and LENS_ACCUMULATE only.
  *   n: at most 262,144 rays per call; larger n returns LENS_ERR_INVALID_ARG
  *   and launches nothing.
- * Scratch: a fixed 5.4 MiB device array defined in the library, present on
- * every GPU that loads the library until the process exits.  The first call
- * on a device looks up that array's device address (with the device
- * current); make that first call before any stream capture.  The call makes
- * no cudaMalloc, cudaFree or other allocating call.  All calls share the one
- * array, which keeps the last call's contents (the call clears what must
- * start at zero): calls that overlap on the GPU, on any streams, race, so
- * order them (one stream, or events).  The tree must have been built on the
- * current device.
+ * Scratch: a fixed 5.4 MiB device array defined in the library.  Each GPU
+ * holds its copy from the first lens_build_tree on it until the process
+ * exits; lens_build_tree looks up the array's device address (with the
+ * tree's device current) and keeps it in the tree, so this call makes no
+ * cudaMalloc, cudaFree, other allocating call or symbol lookup.  A tree built
+ * before a cudaDeviceReset of its device is invalid afterwards (like all its
+ * device buffers); build a new one.  All calls share the one array, which
+ * keeps the last call's contents (the call clears what must start at zero):
+ * calls that overlap on the GPU, on any streams and through any trees, race,
+ * so order them (one stream, or events).  The tree must have been built on
+ * the current device.
  */
 lens_status lens_shoot_rays_direct_noalloc(lens_tree* tree, double origin_x, double origin_y,
                                            const void* ray_dx, const void* ray_dy, int32_t ray_dtype,
@@ -368,8 +385,22 @@ lens_status lens_smoothing_lengths(const float* xyz, int64_t n, int32_t k, float
 lens_status lens_reserve(lens_tree* tree, int64_t max_rays, int64_t max_batches);
 
 /* lens_sync_status -- synchronise `stream` and report (then clear) any error
- * latched by a kernel of this tree. */
+ * latched by a kernel of this tree: LENS_ERR_TIMEOUT when a bounded wait
+ * between cooperating warps ran out (see lens_set_wait_limit),
+ * LENS_ERR_INVALID_ARG for bad values found on the device, LENS_ERR_INTERNAL
+ * for a failed consistency check. */
 lens_status lens_sync_status(lens_tree* tree, void* stream);
+
+/* lens_set_wait_limit -- the bound, in SM clock cycles, of every wait
+ * between the cooperating warps of the LENS_WALK_PAIRS walk (a consumer
+ * waiting for a filled buffer, a producer for an empty one); 0 restores the
+ * default of 4e9 cycles (about 2 s at the maximum SM clock).  A wait that
+ * runs out latches an error, both warps of the pair return, and the next
+ * lens_sync_status reports LENS_ERR_TIMEOUT; the outputs of that call are
+ * then incomplete, and the tree and the CUDA context stay usable.  Applies
+ * to calls made after it (a CUDA graph that lens_shoot_batches cached
+ * earlier keeps the limit it was captured with).  Host-only, cheap. */
+lens_status lens_set_wait_limit(lens_tree* tree, int64_t cycles);
 
 /* lens_tree_get_info -- fill *info (host).  Synchronous, cheap. */
 lens_status lens_tree_get_info(const lens_tree* tree, lens_tree_info* info);
@@ -413,6 +444,19 @@ lens_status lens_last_timing(lens_tree* tree, double* group_ms, double* walk_ms)
  * current device for about `iters` FMAs per thread and return the achieved
  * FP32 rate in FLOP/s (FFMA = 2 flops) in *flops.  Synchronous. */
 lens_status lens_fp32_peak(int64_t iters, double* flops, void* stream);
+
+/* lens_fp64_peak -- the same microbenchmark with dependent FP64 DFMAs: the
+ * achieved FP64 rate in FLOP/s (DFMA = 2 flops) in *flops.  Synchronous. */
+lens_status lens_fp64_peak(int64_t iters, double* flops, void* stream);
+
+/* lens_fail_allocations -- failure-injection hook for tests of the error
+ * paths: the library's next `after` device allocations succeed and the one
+ * after them fails as if the device were out of memory (the call that makes
+ * it returns LENS_ERR_OOM and releases what it had allocated); after < 0
+ * (the default) turns the hook off.  The hook then turns itself off.  It
+ * affects every tree and thread of the process; it changes no setting of the
+ * GPU. */
+void lens_fail_allocations(int64_t after);
 
 /* lens_kernel_launches -- number of CUDA kernels this library has launched
  * in the process so far (all trees, all threads); a CUDA-graph replay adds

@@ -10,7 +10,7 @@ missing or CUDA is unavailable, the calls raise.
     a1, a2, kappa, g1, g2 = lens.shoot(rx, ry)          # device tensors (Sec. 3.2)
     lens.shoot_batches(offsets, origins, rx, ry)          # uneven batches, one launch
     psi, a1, a2 = lens.potential(rx, ry)                  # lensing potential (time delay)
-    grads = lens.backward(rx, ry, g_alpha1, g_alpha2)     # adjoint w.r.t. (m, x, y)
+    grads = lens.backward(rx, ry, g_alpha1, g_alpha2)     # adjoint w.r.t. (m, x, y, size)
     alpha = shoot(lens, rx, ry, species_data=parts)       # differentiable (autograd)
     images, stats = lens.find_images(sources, x0, y0, side, n)   # Sec. 4 image finding
     refine_cells(...)                                      # Sec. 3.4 cell interpolation
@@ -28,7 +28,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["Lens", "Species", "Halo", "LensError", "shoot", "lib", "fp32_peak", "refine_cells", "smoothing_lengths",
+__all__ = ["Lens", "Species", "Halo", "LensError", "shoot", "lib", "fp32_peak", "fp64_peak", "fail_allocations",
+           "refine_cells", "smoothing_lengths",
            "POINT", "GAUSS", "NFW", "SIS", "DISK", "ALPHA_ONLY", "DIRECT", "ACCUMULATE", "USE_GRAPH",
            "COUNT", "TIMING", "REFINE_KAPPA_GAMMA", "REFINE_DEFLECTION"]
 
@@ -109,9 +110,13 @@ def lib():
     L.lens_shoot_rays_direct_noalloc.argtypes = [vp, d, d, vp, vp, i32, i64, vp, vp, vp, vp, vp, i32, vp]
     L.lens_autotune.argtypes = [vp, d, d, vp, vp, i32, i64, vp, ctypes.POINTER(ctypes.c_int32)]
     L.lens_sync_status.argtypes = [vp, vp]
+    L.lens_set_wait_limit.argtypes = [vp, i64]
     L.lens_tree_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
     L.lens_tree_export.argtypes = [vp, i32, vp, vp, vp, vp]
     L.lens_fp32_peak.argtypes = [i64, ctypes.POINTER(ctypes.c_double), vp]
+    L.lens_fp64_peak.argtypes = [i64, ctypes.POINTER(ctypes.c_double), vp]
+    L.lens_fail_allocations.argtypes = [i64]
+    L.lens_fail_allocations.restype = None
     L.lens_tree_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), i32]
     L.lens_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.lens_refine_cells.argtypes = [d, d, d, i64, i64, vp, vp, i32, vp, vp, vp, vp, i64, i32, d, i32, vp, vp,
@@ -127,10 +132,10 @@ def lib():
     L.lens_last_error.restype = ctypes.c_char_p
     for name in ["lens_build_tree", "lens_shoot_rays", "lens_shoot_batches",
                  "lens_shoot_rays_backward", "lens_reserve", "lens_sync_status",
-                 "lens_tree_get_info", "lens_tree_export", "lens_fp32_peak", "lens_api_version",
+                 "lens_tree_get_info", "lens_tree_export", "lens_fp32_peak", "lens_fp64_peak", "lens_api_version",
                  "lens_tree_counters", "lens_last_timing", "lens_autotune",
                  "lens_shoot_rays_direct_noalloc", "lens_refine_cells", "lens_smoothing_lengths",
-                 "lens_shoot_potential", "lens_find_images"]:
+                 "lens_shoot_potential", "lens_find_images", "lens_set_wait_limit"]:
         getattr(L, name).restype = ctypes.c_int32
     _lib = L
     return L
@@ -246,6 +251,30 @@ class Lens:
         self.species = list(species)
         self.halos = list(halos)
         self.theta = theta
+        self._build_args = dict(theta=theta, leaf_max=leaf_max, precision=precision)
+        # what the tree was built from: storage and in-place version of every
+        # species tensor (a differentiable shoot rebuilds when they change)
+        self._built_from = [(s.data.data_ptr(), s.data._version) for s in self.species]
+
+    def built_from(self, species_data) -> bool:
+        """True if the tree was built from these tensors' current values."""
+        if len(species_data) != len(self._built_from):
+            return False
+        return all(t.data_ptr() == p and t._version == v for t, (p, v) in zip(species_data, self._built_from))
+
+    def rebuild(self, species_data, stream=None):
+        """Rebuild the tree from new values of the species tensors (same
+        kinds, shapes, halos and parameters; the tuned group size and walk
+        form are kept)."""
+        if len(species_data) != len(self.species):
+            raise ValueError("rebuild takes one tensor per species")
+        inf = self.info()
+        walk = inf["walk"] if inf["walk"] != "default" else "default"
+        new = Lens([Species(s.kind, t.detach(), s.shape) for s, t in zip(self.species, species_data)],
+                   self.halos, group_rays=inf["group_rays"], walk=walk, stream=stream, **self._build_args)
+        self.close()
+        self._h, new._h = new._h, None
+        self._keep, self.species, self._built_from = new._keep, new.species, new._built_from
 
     # ------------------------------------------------------------------
     @property
@@ -294,6 +323,11 @@ class Lens:
     def sync(self, stream=None):
         _check(lib().lens_sync_status(self._h, _stream_ptr(stream)))
 
+    def set_wait_limit(self, cycles: int = 0):
+        """Bound of the pairs walk's waits between warps, in SM clock cycles
+        (0: the default, about 2 s)."""
+        _check(lib().lens_set_wait_limit(self._h, int(cycles)))
+
     def autotune(self, dx, dy, origin=(0.0, 0.0), stream=None) -> int:
         """Time the walk with 32- and 64-ray groups on these rays; keep and
         return the faster group size."""
@@ -309,18 +343,26 @@ class Lens:
 
     def _outs(self, n, alpha_only, out):
         torch = _torch()
+        k = 2 if alpha_only else 5
         if out is None:
-            k = 2 if alpha_only else 5
             out = [torch.empty(n, dtype=self.out_dtype, device="cuda") for _ in range(k)]
             out += [None] * (5 - k)
+            return out
+        out = list(out) + [None] * (5 - len(out))
+        for q, o in enumerate(out):
+            if o is None:
+                if q < k:
+                    raise ValueError("alpha outputs (and kappa, gamma without ALPHA_ONLY) are required")
+            elif o.dtype != self.out_dtype or o.numel() < n:
+                raise ValueError(f"outputs must be {self.out_dtype} with at least {n} elements")
         return out
 
     def shoot(self, dx, dy, origin=(0.0, 0.0), flags: int = 0, out=None, stream=None):
         """alpha1, alpha2, kappa, gamma1, gamma2 at rays origin + (dx, dy)."""
         torch = _torch()
         n = dx.numel()
-        if dy.numel() != n or dx.dtype != dy.dtype:
-            raise ValueError("dx, dy must match in size and dtype")
+        if dy.numel() != n or dx.dtype != dy.dtype or dx.dtype not in (torch.float32, torch.float64):
+            raise ValueError("dx, dy must be float32 or float64 of the same size")
         out = self._outs(n, bool(flags & ALPHA_ONLY), out)
         rd = F32 if dx.dtype == torch.float32 else F64
         _check(lib().lens_shoot_rays(self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx),
@@ -367,11 +409,26 @@ class Lens:
 
     def shoot_direct_noalloc(self, dx, dy, out, origin=(0.0, 0.0), flags: int = 0, stream=None):
         """Direct sum into caller-provided outputs without any device
-        allocation (at most 262,144 rays per call; see lens.h)."""
+        allocation (lens_shoot_rays_direct_noalloc: at most 262,144 rays per
+        call, calls must not overlap on the GPU).  out: five tensors (kappa,
+        gamma1, gamma2 may be None with ALPHA_ONLY) of the tree's output dtype
+        and at least n elements each."""
         torch = _torch()
+        n = dx.numel()
+        if dy.numel() != n or dx.dtype != dy.dtype or dx.dtype not in (torch.float32, torch.float64):
+            raise ValueError("dx, dy must be float32 or float64 of the same size")
+        out = list(out) + [None] * (5 - len(out))
+        need = 2 if flags & ALPHA_ONLY else 5
+        for k, o in enumerate(out):
+            if o is None:
+                if k < need:
+                    raise ValueError("alpha outputs (and kappa, gamma without ALPHA_ONLY) are required")
+                continue
+            if o.dtype != self.out_dtype or o.numel() < n:
+                raise ValueError(f"outputs must be {self.out_dtype} with at least {n} elements")
         rd = F32 if dx.dtype == torch.float32 else F64
         _check(lib().lens_shoot_rays_direct_noalloc(
-            self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx), _dev_ptr(dy), rd, dx.numel(),
+            self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx), _dev_ptr(dy), rd, n,
             *[_dev_ptr(o) for o in out], int(flags), _stream_ptr(stream)))
         return out
 
@@ -391,15 +448,28 @@ class Lens:
 
     def backward(self, dx, dy, g_alpha1, g_alpha2, origin=(0.0, 0.0), flags: int = 0,
                  grads=None, g_halos=None, stream=None):
-        """Accumulate dL/d(m, x, y) of every particle (and halo parameters)."""
+        """Accumulate dL/d(m, x, y, size) of every particle ((n, 4) per
+        species, input order) and, when g_halos is an (n_halos, 5) float64
+        CUDA tensor, dL/d(m or r_E, x, y, p0, p1) of every halo."""
         torch = _torch()
+        n = dx.numel()
+        if dy.numel() != n or dx.dtype != dy.dtype or dx.dtype not in (torch.float32, torch.float64):
+            raise ValueError("dx, dy must be float32 or float64 of the same size")
+        for g in (g_alpha1, g_alpha2):
+            if g.dtype != self.out_dtype or g.numel() < n:
+                raise ValueError(f"upstream gradients must be {self.out_dtype} with n elements")
         if grads is None:
-            grads = [torch.zeros(s.data.shape[0], 3, dtype=self.out_dtype, device="cuda")
+            grads = [torch.zeros(s.data.shape[0], 4, dtype=self.out_dtype, device="cuda")
                      for s in self.species]
+        for s, g in zip(self.species, grads):
+            if g.dtype != self.out_dtype or g.numel() < 4 * s.data.shape[0]:
+                raise ValueError(f"species gradients must be ({s.data.shape[0]}, 4) {self.out_dtype}")
+        if g_halos is not None and (g_halos.dtype != torch.float64 or g_halos.numel() < 5 * self.n_halos):
+            raise ValueError(f"g_halos must be ({self.n_halos}, 5) float64")
         arr = (ctypes.c_void_p * max(1, len(grads)))(*[g.data_ptr() for g in grads])
         rd = F32 if dx.dtype == torch.float32 else F64
         _check(lib().lens_shoot_rays_backward(
-            self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx), _dev_ptr(dy), rd, dx.numel(),
+            self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx), _dev_ptr(dy), rd, n,
             _dev_ptr(g_alpha1), _dev_ptr(g_alpha2), None, None, None, arr,
             _dev_ptr(g_halos) if g_halos is not None else None, int(flags), _stream_ptr(stream)))
         return grads
@@ -422,6 +492,20 @@ def fp32_peak(iters: int = 4096, stream=None) -> float:
     v = ctypes.c_double()
     _check(lib().lens_fp32_peak(int(iters), ctypes.byref(v), _stream_ptr(stream)))
     return v.value
+
+
+def fp64_peak(iters: int = 1024, stream=None) -> float:
+    """Measured FP64 DFMA rate of the current GPU (FLOP/s)."""
+    v = ctypes.c_double()
+    _check(lib().lens_fp64_peak(int(iters), ctypes.byref(v), _stream_ptr(stream)))
+    return v.value
+
+
+def fail_allocations(after: int):
+    """Failure injection for error-path tests (lens_fail_allocations): the
+    library's next `after` device allocations succeed and the following one
+    fails as out of memory; a negative value turns the hook off."""
+    lib().lens_fail_allocations(int(after))
 
 
 def refine_cells(x0, y0, h, nx, ny, alpha1, alpha2, kappa=None, gamma1=None, gamma2=None, cells=None,
@@ -472,7 +556,9 @@ def smoothing_lengths(xyz, k: int = 32, out=None, stream=None):
 
 def shoot(lens: Lens, dx, dy, origin=(0.0, 0.0), species_data=None):
     """Differentiable alpha (n, 2) through lens_shoot_rays / _backward: the
-    gradient flows to the (n, 4) species tensors' (x, y, m) columns.  The lens
-    must have been built from ``species_data`` (its current values)."""
+    gradient flows to the (n, 4) species tensors' columns (x, y, m and the
+    size r_sm or r_s).  If ``species_data`` is not what the tree was built
+    from, or was changed in place since, the tree is rebuilt from its current
+    values first."""
     from ._autograd import shoot_alpha
     return shoot_alpha(lens, dx, dy, origin, species_data)

@@ -9,6 +9,8 @@ class _ShootAlpha(torch.autograd.Function):
     @staticmethod
     def forward(ctx, lens, dx, dy, origin, *species_data):
         from . import ALPHA_ONLY
+        if not lens.built_from(species_data):
+            lens.rebuild(species_data)   # new values: the old tree's moments are stale
         out = lens.shoot(dx, dy, origin=origin, flags=ALPHA_ONLY)
         ctx.lens = lens
         ctx.origin = origin
@@ -28,12 +30,14 @@ class _ShootAlpha(torch.autograd.Function):
             gd[:, 0] = gr[:, 1].to(gd.dtype)   # x
             gd[:, 1] = gr[:, 2].to(gd.dtype)   # y
             gd[:, 2] = gr[:, 0].to(gd.dtype)   # m
+            gd[:, 3] = gr[:, 3].to(gd.dtype)   # size (r_sm or r_s; 0 for points)
             out.append(gd)
         return (None, None, None, None, *out)
 
 
 def shoot_alpha(lens, dx, dy, origin=(0.0, 0.0), species_data=None):
     """alpha (n, 2) at rays origin + (dx, dy); differentiable w.r.t. the
-    species tensors the lens was built from (columns x, y, m)."""
+    species tensors (columns x, y, m, size); the lens is rebuilt from them
+    when they are not its current data."""
     data = species_data if species_data is not None else [s.data for s in lens.species]
     return _ShootAlpha.apply(lens, dx, dy, tuple(origin), *data)

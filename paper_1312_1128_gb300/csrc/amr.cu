@@ -435,7 +435,7 @@ template <typename T> struct DevBuf {
         want = std::max<size_t>(want, 1);
         if (want <= n) return cudaSuccess;
         release();
-        cudaError_t e = cudaMalloc((void**)&p, want * sizeof(T));
+        cudaError_t e = lens_malloc((void**)&p, want * sizeof(T));
         if (e == cudaSuccess) n = want;
         else p = nullptr;
         return e;

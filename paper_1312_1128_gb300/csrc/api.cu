@@ -1,5 +1,5 @@
 // api.cu -- the C ABI of liblens (include/lens.h): argument checking, tree
-// ownership, error reporting and the FP32 peak microbenchmark.
+// ownership, error reporting and the FP32 / FP64 peak microbenchmarks.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -23,10 +23,43 @@ void free_graphs(lens_tree* t);
 bool halos_only(const lens_tree* t);
 lens_status shoot_halos_only(lens_tree* t, double ox, double oy, const void* dx, const void* dy, int dtype,
                              int64_t n, void* const out[5], int flags, cudaStream_t s);
+lens_status noalloc_scratch_address(void** out);
 }  // namespace lens
 
 static thread_local char g_msg[512] = "";
 static std::atomic<long long> g_launches{0};
+
+static std::atomic<long long> g_fail_after{-1};
+
+// The failure-injection hook: true if this allocation is the one to fail.
+static bool alloc_should_fail()
+{
+    long long c = g_fail_after.load();
+    while (c >= 0) {
+        if (g_fail_after.compare_exchange_weak(c, c - 1)) return c == 0;
+    }
+    return false;
+}
+
+cudaError_t lens_malloc(void** p, size_t bytes)
+{
+    if (alloc_should_fail()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t lens_malloc_async(void** p, size_t bytes, cudaStream_t s)
+{
+    if (alloc_should_fail()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, s);
+}
+
+extern "C" void lens_fail_allocations(int64_t after) { g_fail_after.store(after < 0 ? -1 : (long long)after); }
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -51,19 +84,27 @@ lens_status lens_cuda_check(cudaError_t e, const char* what)
 
 using namespace lens;
 
-static double nfw_gX(double X)
+// Projected NFW shape functions at X = R_max / r_s (Sec. 3.2): F, the
+// surface-density shape f = (1 - F)/(X^2 - 1) and the enclosed-mass shape
+// g = ln(X/2) + F; near X = 1 both F and f are power series in u = 1 - X^2.
+static void nfw_host(double X, double* Fo, double* fo, double* go)
 {
-    double u = 1.0 - X * X, F;
-    if (std::fabs(u) < 1e-4) {
-        double s = 0.0;
-        for (int k = 12; k >= 0; --k) s = s * u + 1.0 / (2 * k + 1);
+    double u = 1.0 - X * X, F, f;
+    if (std::fabs(u) < 1e-2) {
+        double s = 0.0, t = 0.0;
+        for (int k = 16; k >= 0; --k) {
+            s = s * u + 1.0 / (2 * k + 1);
+            t = t * u + 1.0 / (2 * k + 3);
+        }
         F = s;
-    } else if (X < 1.0) {
-        F = std::acosh(1.0 / X) / std::sqrt(u);
+        f = t;
     } else {
-        F = std::acos(1.0 / X) / std::sqrt(-u);
+        F = X < 1.0 ? std::acosh(1.0 / X) / std::sqrt(u) : std::acos(1.0 / X) / std::sqrt(-u);
+        f = (1.0 - F) / (X * X - 1.0);
     }
-    return std::log(0.5 * X) + F;
+    *Fo = F;
+    *fo = f;
+    *go = std::log(0.5 * X) + F;
 }
 
 static lens_status check_halo(const lens_halo& h, HaloDev& d)
@@ -85,10 +126,15 @@ static lens_status check_halo(const lens_halo& h, HaloDev& d)
         return LENS_OK;
     case LENS_NFW:
         if (!(h.p0 > 0 && h.p1 > 0)) return lens_set_error(LENS_ERR_INVALID_ARG, "NFW halo needs r_s > 0, R_max > 0");
-        d.c0 = h.m / nfw_gX(h.p1 / h.p0);
+    {
+        double X = h.p1 / h.p0, F, f, g;
+        nfw_host(X, &F, &f, &g);
+        d.c0 = h.m / g;
         d.c1 = 1.0 / h.p0;
         d.c2 = h.p1 * h.p1;
+        d.c3 = X * f / g;
         return LENS_OK;
+    }
     case LENS_SIS:
         if (!(h.p0 >= 0)) return lens_set_error(LENS_ERR_INVALID_ARG, "SIS halo needs r_E >= 0");
         return LENS_OK;
@@ -198,18 +244,18 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
     }
     e = cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaDeviceGetAttribute"));
-    e = cudaMalloc((void**)&t->d_err, sizeof(uint32_t));
+    e = lens_malloc((void**)&t->d_err, sizeof(uint32_t));
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMalloc(err)"));
     e = cudaMemsetAsync(t->d_err, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMemsetAsync"));
-    e = cudaMalloc((void**)&t->d_stats, 8 * sizeof(unsigned long long));
+    e = lens_malloc((void**)&t->d_stats, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMalloc(stats)"));
     e = cudaMemsetAsync(t->d_stats, 0, 8 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMemsetAsync"));
     t->halos_host.assign(halos, halos + n_halos);
     t->n_halos = n_halos;
     if (n_halos > 0) {
-        e = cudaMalloc((void**)&t->halos, n_halos * sizeof(HaloDev));
+        e = lens_malloc((void**)&t->halos, n_halos * sizeof(HaloDev));
         if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMalloc(halos)"));
         e = cudaMemcpy(t->halos, hd.data(), n_halos * sizeof(HaloDev), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMemcpy(halos)"));
@@ -227,6 +273,13 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
     if (herr & DERR_BAD_INPUT)
         return fail(lens_set_error(LENS_ERR_INVALID_ARG, "negative or non-finite particle mass or size"));
     if (herr) return fail(lens_set_error(LENS_ERR_INTERNAL, "tree build check failed (code %u)", herr));
+    // the allocation-free shoot's scratch: its address on this device, taken
+    // here (the first lookup on a device loads the array) so that the shoot
+    // call itself makes no runtime lookup
+    {
+        lens_status st = noalloc_scratch_address(&t->noalloc_scratch);
+        if (st != LENS_OK) return fail(st);
+    }
     *out = t;
     return LENS_OK;
 }
@@ -332,7 +385,7 @@ lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, con
     int64_t m = n < (1 << 23) ? n : (1 << 23);
     size_t es = tree->precision == LENS_PREC_FP64 ? 8 : 4;
     void* buf = nullptr;
-    LENS_CUDA(cudaMallocAsync(&buf, 5 * m * es, s));
+    LENS_CUDA(lens_malloc_async(&buf, 5 * m * es, s));
     void* out[5];
     for (int q = 0; q < 5; ++q) out[q] = (char*)buf + q * m * es;
     int64_t off[2] = {0, m};
@@ -390,9 +443,17 @@ lens_status lens_sync_status(lens_tree* tree, void* stream)
         LENS_CUDA(cudaMemset(tree->d_err, 0, sizeof(uint32_t)));
         if (herr & DERR_BAD_INPUT) return lens_set_error(LENS_ERR_INVALID_ARG, "bad input found on the device");
         if (herr & DERR_WAIT_TIMEOUT)
-            return lens_set_error(LENS_ERR_INTERNAL, "a hand-over wait between walk warps timed out (code %u)", herr);
+            return lens_set_error(LENS_ERR_TIMEOUT, "a hand-over wait between walk warps timed out (code %u)", herr);
         return lens_set_error(LENS_ERR_INTERNAL, "device check failed (code %u)", herr);
     }
+    return LENS_OK;
+}
+
+lens_status lens_set_wait_limit(lens_tree* tree, int64_t cycles)
+{
+    if (!tree) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
+    if (cycles < 0) return lens_set_error(LENS_ERR_INVALID_ARG, "cycles must be >= 0");
+    tree->wait_cycles = cycles == 0 ? 4000000000ll : cycles;
     return LENS_OK;
 }
 
@@ -499,41 +560,40 @@ lens_status lens_tree_export(const lens_tree* t, int32_t si, void* nodes, int32_
 
 }  // extern "C"
 
-// ------------------------------------------------- FP32 peak microbenchmark
+// ------------------------------------------- FP32 / FP64 peak microbenchmarks
 
-// Eight independent dependent-FFMA chains per thread (enough ILP to keep the
-// FP32 pipes busy), written to memory at the end so nothing is eliminated.
-__global__ void k_ffma_peak(float* sink, int64_t iters, float a, float b)
+// Eight independent dependent-FMA chains per thread (enough ILP to keep the
+// FMA pipes busy), written to memory at the end so nothing is eliminated.
+template <typename T>
+__global__ void k_fma_peak(T* sink, int64_t iters, T a, T b)
 {
-    float x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6,
-          x7 = x0 + 7;
+    T x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
     for (int64_t i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            x0 = fmaf(x0, a, b); x1 = fmaf(x1, a, b); x2 = fmaf(x2, a, b); x3 = fmaf(x3, a, b);
-            x4 = fmaf(x4, a, b); x5 = fmaf(x5, a, b); x6 = fmaf(x6, a, b); x7 = fmaf(x7, a, b);
+            x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+            x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
         }
     }
-    float r = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
-    if (r == 1234.5f) sink[0] = r;
+    T r = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+    if (r == T(1234.5)) sink[0] = r;
 }
 
-extern "C" lens_status lens_fp32_peak(int64_t iters, double* flops, void* stream)
+template <typename T>
+static lens_status fma_peak(int64_t iters, double* flops, cudaStream_t s)
 {
-    if (!flops || iters < 1) return lens_set_error(LENS_ERR_INVALID_ARG, "bad arguments");
-    cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 0;
     LENS_CUDA(cudaGetDevice(&dev));
     LENS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    float* sink = nullptr;
-    LENS_CUDA(cudaMalloc(&sink, sizeof(float)));
+    T* sink = nullptr;
+    LENS_CUDA(lens_malloc((void**)&sink, sizeof(T)));
     const int threads = 256, blocks = sms * 8;
     cudaEvent_t e0, e1;
     LENS_CUDA(cudaEventCreate(&e0));
     LENS_CUDA(cudaEventCreate(&e1));
-    { k_ffma_peak<<<blocks, threads, 0, s>>>(sink, iters / 8 + 1, 0.999f, 0.001f); note_launch(); }  // warm up
+    { k_fma_peak<T><<<blocks, threads, 0, s>>>(sink, iters / 8 + 1, T(0.999), T(0.001)); note_launch(); }  // warm up
     LENS_CUDA(cudaEventRecord(e0, s));
-    { k_ffma_peak<<<blocks, threads, 0, s>>>(sink, iters, 0.999f, 0.001f); note_launch(); }
+    { k_fma_peak<T><<<blocks, threads, 0, s>>>(sink, iters, T(0.999), T(0.001)); note_launch(); }
     LENS_CUDA(cudaEventRecord(e1, s));
     LENS_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
@@ -544,4 +604,16 @@ extern "C" lens_status lens_fp32_peak(int64_t iters, double* flops, void* stream
     double total = 2.0 * 8.0 * 16.0 * (double)iters * (double)threads * (double)blocks;
     *flops = total / (ms * 1e-3);
     return LENS_OK;
+}
+
+extern "C" lens_status lens_fp32_peak(int64_t iters, double* flops, void* stream)
+{
+    if (!flops || iters < 1) return lens_set_error(LENS_ERR_INVALID_ARG, "bad arguments");
+    return fma_peak<float>(iters, flops, (cudaStream_t)stream);
+}
+
+extern "C" lens_status lens_fp64_peak(int64_t iters, double* flops, void* stream)
+{
+    if (!flops || iters < 1) return lens_set_error(LENS_ERR_INVALID_ARG, "bad arguments");
+    return fma_peak<double>(iters, flops, (cudaStream_t)stream);
 }

@@ -15,6 +15,14 @@
 //   linear in the mass, so dalpha/dm = alpha/m, and dalpha/dx_p = -J with J
 //   the term's own Jacobian [[kappa+g1, g2], [g2, kappa-g1]] (Eqs. kappa,
 //   gamma_1, gamma_2);
+//   sizes: a profile of size s and fixed shape encloses Mt = m F(r/s), and
+//   dMt/dr = 2 r kappa (m-units), so dMt/ds = -2 r^2 kappa / s and
+//   dalpha/ds = -(2 kappa / s) w: a particle's size gradient is
+//   -(2/s) sum kappa (G.w) over the rays inside its support (kappa = 0
+//   outside).  Every such ray meets the particle's full profile in the walk
+//   (a leaf, or the big list of a visited box), so the tree's size gradient
+//   is the direct sum's.  Analytic halos add the derivatives of their other
+//   shape parameters (q, R_max) through the enclosed mass the same way;
 //   far cells, conj(alpha) = M/w + Q2/w^3 with w = x - x_cm: per cell the
 //   adjoints a = dL/dM, C = dL/dQ2 and B = dL/dz_cm (dL = Re(G dA) with
 //   A = conj(alpha)).  Since dM = dm_i, dz_cm = (dm_i d_i + m_i dz_i)/M and
@@ -54,9 +62,9 @@ template <typename T> struct BackParams {
     const T* ga2;
     const HaloDev* halos;
     int n_halos;
-    double* ghalo;  // n_halos x 3, or null
+    double* ghalo;  // n_halos x 5 {dL/dm (dL/dr_E for the SIS), dL/dx, dL/dy, dL/dp0, dL/dp1}, or null
     double* adj;    // n_nodes x 5: dL/dM, dL/dQ2 (re, im), dL/dz_cm (re, im)
-    double* gpart;  // n x 3 in tree order: dL/dm, dL/dx, dL/dy
+    double* gpart;  // n x 4 in tree order: dL/dm, dL/dx, dL/dy, sum kappa (G.w)
     // (FP64 accumulators: these sums run over up to millions of rays with
     // strong cancellation)
     uint32_t* counter;
@@ -82,15 +90,16 @@ template <int KIND, typename T> struct BackShared {
 };
 
 // Gradient of the loss through one particle term (kb, kap, Dp) at offset w
-// for upstream gradient (g1, g2): adds G.alpha_t (to be divided by m) and
-// -J^T G.
+// for upstream gradient (g1, g2): adds G.alpha_t (to be divided by m),
+// -J^T G and kappa (G.w) (the size gradient's sum).
 template <typename T>
-LENS_DEV void term_grad(T wx, T wy, T kb, T kap, T Dp, T g1, T g2, T& gm, T& gx, T& gy)
+LENS_DEV void term_grad(T wx, T wy, T kb, T kap, T Dp, T g1, T g2, T& gm, T& gx, T& gy, T& gk)
 {
-    T a1 = kb * wx, a2 = kb * wy;
+    T gw = fma(g1, wx, g2 * wy);
     T c2 = fma(wx, wx, -wy * wy), s2 = (wx + wx) * wy;
     T gg1 = -Dp * c2, gg2 = -Dp * s2;
-    gm = fma(g1, a1, fma(g2, a2, gm));
+    gm = fma(kb, gw, gm);
+    gk = fma(kap, gw, gk);
     gx -= fma(g1, kap + gg1, g2 * gg2);
     gy -= fma(g1, gg2, g2 * (kap - gg1));
 }
@@ -200,14 +209,15 @@ template <int KIND, typename T> struct BackCtx {
         __syncwarp();
     }
 
-    LENS_DEV void add_particle(int pid, T m, T gm, T gx, T gy)
+    LENS_DEV void add_particle(int pid, T m, T gm, T gx, T gy, T gk)
     {
-        double* g = P.gpart + 3 * (int64_t)pid;
+        double* g = P.gpart + 4 * (int64_t)pid;
         // dL/dm = gm / m in the working precision (an FP64 division is slow on
         // this GPU's FP64 pipe); accumulated in FP64
         if (m != T(0)) atomicAdd(g + 0, (double)(gm / m));
         atomicAdd(g + 1, (double)gx);
         atomicAdd(g + 2, (double)gy);
+        if (gk != T(0)) atomicAdd(g + 3, (double)gk);
     }
 
     LENS_DEV void flush_near(int nn)
@@ -217,14 +227,14 @@ template <int KIND, typename T> struct BackCtx {
         for (int i = lane; i < nn; i += 32) {
             vec4_t<T> q = S.n0[i], q1;
             if constexpr (KIND == LENS_NFW) q1 = S.n1[i];
-            T gm = T(0), gx = T(0), gy = T(0);
+            T gm = T(0), gx = T(0), gy = T(0), gk = T(0);
             for (int j = 0; j < nr; ++j) {
                 T wx = S.rx[j] - q.x, wy = S.ry[j] - q.y;
                 T r2 = fma(wx, wx, wy * wy), kb, kap, Dp;
                 leaf_term<KIND, T>(P, q, q1, r2, kb, kap, Dp);
-                term_grad(wx, wy, kb, kap, Dp, S.rg1[j], S.rg2[j], gm, gx, gy);
+                term_grad(wx, wy, kb, kap, Dp, S.rg1[j], S.rg2[j], gm, gx, gy, gk);
             }
-            add_particle(S.npid[i], q.z, gm, gx, gy);
+            add_particle(S.npid[i], q.z, gm, gx, gy, gk);
         }
         __syncwarp();
     }
@@ -235,15 +245,15 @@ template <int KIND, typename T> struct BackCtx {
         __syncwarp();
         for (int i = lane; i < nb; i += 32) {
             vec4_t<T> q = S.b0[i], q1 = S.b1[i];
-            T gm = T(0), gx = T(0), gy = T(0);
+            T gm = T(0), gx = T(0), gy = T(0), gk = T(0);
             for (int j = 0; j < nr; ++j) {
                 T wx = S.rx[j] - q.x, wy = S.ry[j] - q.y;
                 T r2 = fma(wx, wx, wy * wy), kb, kap, Dp;
                 big_term<KIND, T>(P, q, q1, r2, kb, kap, Dp);
-                term_grad(wx, wy, kb, kap, Dp, S.rg1[j], S.rg2[j], gm, gx, gy);
+                term_grad(wx, wy, kb, kap, Dp, S.rg1[j], S.rg2[j], gm, gx, gy, gk);
             }
             T m = KIND == LENS_GAUSS ? q1.x * P.Nq : q1.x;
-            add_particle(S.bpid[i], m, gm, gx, gy);
+            add_particle(S.bpid[i], m, gm, gx, gy, gk);
         }
         __syncwarp();
     }
@@ -470,17 +480,22 @@ back_kernel(BackParams<T> P)
                 const HaloDev& hd = P.halos[h];
                 T hx = (T)((double)C.H.x - hd.x), hy = (T)((double)C.H.y - hd.y);
                 T m = (T)hd.m;
-                T gm = T(0), gx = T(0), gy = T(0);
+                // gk = sum kappa (G.w); gin = sum kb (G.w) over the rays inside
+                // the support (the enclosed mass depends on q, R_max only there)
+                T gm = T(0), gx = T(0), gy = T(0), gk = T(0), gin = T(0);
                 for (int k = lane; k < C.nr; k += 32) {
                     T wx = S.rx[k] + hx, wy = S.ry[k] + hy;
                     T r2 = fma(wx, wx, wy * wy);
                     T kb = T(0), kap = T(0), Dp = T(0);
+                    bool inside = false;
                     if (hd.kind == LENS_POINT) {
                         point_terms(m, r2, kb, Dp);
                     } else if (hd.kind == LENS_GAUSS) {
                         gauss_terms(m, (T)hd.c0, r2, (T)hd.c1, (T)hd.c2, kb, kap, Dp);
+                        inside = r2 * (T)hd.c0 < (T)hd.c1;
                     } else if (hd.kind == LENS_NFW) {
                         nfw_terms(m, (T)hd.c2, (T)hd.c0, (T)hd.c1, r2, kb, kap, Dp);
+                        inside = r2 < (T)hd.c2 && r2 > T(0);
                     } else if (hd.kind == LENS_SIS) {
                         if (r2 > T(0)) {
                             T rr = sqrt(r2), re = (T)hd.p0;
@@ -497,19 +512,44 @@ back_kernel(BackParams<T> P)
                             point_terms(m, r2, kb, Dp);
                         }
                     }
-                    term_grad(wx, wy, kb, kap, Dp, S.rg1[k], S.rg2[k], gm, gx, gy);
+                    T gm0 = gm;
+                    term_grad(wx, wy, kb, kap, Dp, S.rg1[k], S.rg2[k], gm, gx, gy, gk);
+                    if (inside) gin += gm - gm0;
                 }
                 for (int o = 16; o; o >>= 1) {
                     gm += __shfl_xor_sync(full, gm, o);
                     gx += __shfl_xor_sync(full, gx, o);
                     gy += __shfl_xor_sync(full, gy, o);
+                    gk += __shfl_xor_sync(full, gk, o);
+                    gin += __shfl_xor_sync(full, gin, o);
                 }
                 if (lane == 0) {
                     // the strength parameter: m, or r_E for the SIS
                     double strength = hd.kind == LENS_SIS ? hd.p0 : hd.m;
-                    if (strength != 0.0) atomicAdd(P.ghalo + 3 * h, (double)gm / strength);
-                    atomicAdd(P.ghalo + 3 * h + 1, (double)gx);
-                    atomicAdd(P.ghalo + 3 * h + 2, (double)gy);
+                    double gs = strength != 0.0 ? (double)gm / strength : 0.0;
+                    // shape parameters p0, p1 (d alpha / d p = (d kb / d p) w)
+                    double g0 = 0.0, g1 = 0.0;
+                    if (hd.kind == LENS_GAUSS) {
+                        // p0 = r_sm: dkb = -2 kappa / r_sm; p1 = q: dkb = -kb N_q'(q) / N_q
+                        g0 = -2.0 * (double)gk / hd.p0;
+                        g1 = -hd.p1 * exp(-hd.c1) * hd.c2 * (double)gin;
+                    } else if (hd.kind == LENS_NFW) {
+                        // p0 = r_s: dkb = (-2 kappa + X c3 kb) / r_s; p1 = R_max:
+                        // dkb = -c3 kb / r_s (X = R_max / r_s, c3 = X f(X) / g(X))
+                        double X = hd.p1 / hd.p0;
+                        g0 = (-2.0 * (double)gk + X * hd.c3 * (double)gin) * hd.c1;
+                        g1 = -hd.c3 * (double)gin * hd.c1;
+                    } else if (hd.kind == LENS_DISK) {
+                        g0 = -2.0 * (double)gk / hd.p0;  // p0 = R
+                    } else if (hd.kind == LENS_SIS) {
+                        g0 = gs;                          // p0 = r_E
+                    }
+                    double* out = P.ghalo + 5 * h;
+                    if (gs != 0.0) atomicAdd(out, gs);
+                    atomicAdd(out + 1, (double)gx);
+                    atomicAdd(out + 2, (double)gy);
+                    if (g0 != 0.0) atomicAdd(out + 3, g0);
+                    if (g1 != 0.0) atomicAdd(out + 4, g1);
                 }
             }
         }
@@ -555,11 +595,13 @@ __global__ void k_push(uint32_t b0, uint32_t b1, const int* parent, const vec4_t
 }
 
 // Every particle of every leaf: dL/dm += Re P(d), dL/dz += m P'(d), then
-// scatter (with the direct terms) to the caller's input order.
+// scatter (with the direct terms) to the caller's input order; the size
+// gradient is -(2/s) sum kappa (G.w) with s the particle's size (r_sm from
+// c = 1/(2 r_sm^2) of a Gaussian record, r_s = 1/B of an NFW record).
 template <typename T>
 __global__ void k_leafgrad(uint32_t n_nodes, const int4* link, const vec4_t<T>* nodeA, const vec4_t<T>* exact0,
-                           const dbl4* polyA, const double2* polyC, const double* gpart, const uint32_t* perm,
-                           T* out)
+                           const vec4_t<T>* exact1, int kind, const dbl4* polyA, const double2* polyC,
+                           const double* gpart, const uint32_t* perm, T* out)
 {
     uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_nodes) return;
@@ -577,14 +619,20 @@ __global__ void k_leafgrad(uint32_t n_nodes, const int4* link, const vec4_t<T>* 
         double gm = PA.x + (PA.y * dx - PA.z * dy) + (PC.x * d2x - PC.y * d2y);
         double kr = PA.y + 2.0 * (PC.x * dx - PC.y * dy), ki = PA.z + 2.0 * (PC.x * dy + PC.y * dx);
         double m = (double)q.z;
+        const double* gp = gpart + 4 * (int64_t)j;
         // dL = Re(m P'(d) dz): dL/dx = m Re P', dL/dy = -m Im P'
-        gm += gpart[3 * (int64_t)j];
-        double gx = m * kr + gpart[3 * (int64_t)j + 1];
-        double gy = -m * ki + gpart[3 * (int64_t)j + 2];
+        gm += gp[0];
+        double gx = m * kr + gp[1];
+        double gy = -m * ki + gp[2];
+        double inv_s = 0.0;  // 1/s
+        if (kind == LENS_GAUSS) inv_s = sqrt(2.0 * (double)q.w);
+        else if (kind == LENS_NFW) inv_s = (double)exact1[j].y;
+        double gs = -2.0 * inv_s * gp[3];
         uint32_t i = perm[j];
-        out[3 * (int64_t)i] += (T)gm;
-        out[3 * (int64_t)i + 1] += (T)gx;
-        out[3 * (int64_t)i + 2] += (T)gy;
+        out[4 * (int64_t)i] += (T)gm;
+        out[4 * (int64_t)i + 1] += (T)gx;
+        out[4 * (int64_t)i + 2] += (T)gy;
+        out[4 * (int64_t)i + 3] += (T)gs;
     }
 }
 
@@ -653,13 +701,14 @@ static lens_status backward_typed(lens_tree* t, double ox, double oy, const void
         double* gpart = nullptr;
         dbl4* polyA = nullptr;
         double2* polyC = nullptr;
+        StreamTemps tmps(s);  // this species' accumulators, released on every return path
         if (st.n > 0) {
-            LENS_CUDA(cudaMallocAsync((void**)&adj, st.n_nodes * 5 * sizeof(double), s));
-            LENS_CUDA(cudaMallocAsync((void**)&gpart, st.n * 3 * sizeof(double), s));
-            LENS_CUDA(cudaMallocAsync((void**)&polyA, st.n_nodes * sizeof(dbl4), s));
-            LENS_CUDA(cudaMallocAsync((void**)&polyC, st.n_nodes * sizeof(double2), s));
+            LENS_CUDA(tmps.get(&adj, st.n_nodes * 5 * sizeof(double)));
+            LENS_CUDA(tmps.get(&gpart, st.n * 4 * sizeof(double)));
+            LENS_CUDA(tmps.get(&polyA, st.n_nodes * sizeof(dbl4)));
+            LENS_CUDA(tmps.get(&polyC, st.n_nodes * sizeof(double2)));
             LENS_CUDA(cudaMemsetAsync(adj, 0, st.n_nodes * 5 * sizeof(double), s));
-            LENS_CUDA(cudaMemsetAsync(gpart, 0, st.n * 3 * sizeof(double), s));
+            LENS_CUDA(cudaMemsetAsync(gpart, 0, st.n * 4 * sizeof(double), s));
         }
         P.nodeA = (const T4*)st.nodeA;
         P.nodeB = (const T2*)st.nodeB;
@@ -701,14 +750,9 @@ static lens_status backward_typed(lens_tree* t, double ox, double oy, const void
                 LENS_CUDA(cudaMemsetAsync(polyC, 0, st.n_nodes * sizeof(double2), s));
             }
             { k_leafgrad<T><<<grid_for(st.n_nodes, TB), TB, 0, s>>>((uint32_t)st.n_nodes, st.link, (const T4*)st.nodeA,
-                                                                    (const T4*)st.exact0, polyA, polyC, gpart, st.perm,
+                                                                    (const T4*)st.exact0, (const T4*)st.exact1, st.kind,
+                                                                    polyA, polyC, gpart, st.perm,
                                                                     (T*)g_species[si]); note_launch(); }
-        }
-        if (adj) {
-            cudaFreeAsync(adj, s);
-            cudaFreeAsync(gpart, s);
-            cudaFreeAsync(polyA, s);
-            cudaFreeAsync(polyC, s);
         }
         first = false;
         ++launches;

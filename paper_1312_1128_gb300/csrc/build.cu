@@ -589,7 +589,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     const int64_t n = in.n;
     const int TB = 256;
     const unsigned G = grid_for(n, TB);
-    // temporaries (stream ordered)
+    StreamTemps tmps(s);  // temporaries (stream ordered), released on every return path
     T4* staged = nullptr;
     T4* sorted = nullptr;
     unsigned long long* bbox = nullptr;
@@ -598,15 +598,15 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     uint32_t *v0 = nullptr, *v1 = nullptr;
     void* tmp = nullptr;
     size_t tmp_bytes = std::max(radix_sort_temp_bytes<uint64_t>(n), scan_temp_bytes(n + 1));
-    LENS_CUDA(cudaMallocAsync((void**)&staged, n * sizeof(T4), s));
-    LENS_CUDA(cudaMallocAsync((void**)&sorted, n * sizeof(T4), s));
-    LENS_CUDA(cudaMallocAsync((void**)&bbox, 4 * sizeof(unsigned long long), s));
-    LENS_CUDA(cudaMallocAsync((void**)&rb, sizeof(RootBox), s));
-    LENS_CUDA(cudaMallocAsync((void**)&k0, n * sizeof(uint64_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&k1, n * sizeof(uint64_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&v0, (n + 1) * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&v1, (n + 1) * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync(&tmp, tmp_bytes, s));
+    LENS_CUDA(tmps.get(&staged, n * sizeof(T4)));
+    LENS_CUDA(tmps.get(&sorted, n * sizeof(T4)));
+    LENS_CUDA(tmps.get(&bbox, 4 * sizeof(unsigned long long)));
+    LENS_CUDA(tmps.get(&rb, sizeof(RootBox)));
+    LENS_CUDA(tmps.get(&k0, n * sizeof(uint64_t)));
+    LENS_CUDA(tmps.get(&k1, n * sizeof(uint64_t)));
+    LENS_CUDA(tmps.get(&v0, (n + 1) * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&v1, (n + 1) * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&tmp, tmp_bytes));
 
     unsigned long long init[4] = {~0ull, 0ull, ~0ull, 0ull};
     LENS_CUDA(cudaMemcpyAsync(bbox, init, sizeof(init), cudaMemcpyHostToDevice, s));
@@ -621,8 +621,8 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     // topology
     uint8_t* Lp = nullptr;
     uint32_t* off = nullptr;   // n + 1: owned-box offsets, last = n_nodes
-    LENS_CUDA(cudaMallocAsync((void**)&Lp, n, s));
-    LENS_CUDA(cudaMallocAsync((void**)&off, (n + 1) * sizeof(uint32_t), s));
+    LENS_CUDA(tmps.get(&Lp, n));
+    LENS_CUDA(tmps.get(&off, (n + 1) * sizeof(uint32_t)));
     { k_levels<<<G, TB, 0, s>>>(K, n, t->leaf_max, Lp, off); note_launch(); }
     scan_exclusive_u32(off, off, n, off + n, tmp, s);
     uint32_t n_nodes = 0;
@@ -637,9 +637,9 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
         // the level sort and scans below run over n_nodes elements
         size_t need = std::max(radix_sort_temp_bytes<uint32_t>(n_nodes), scan_temp_bytes((int64_t)n_nodes + 1));
         if (need > tmp_bytes) {
-            cudaFreeAsync(tmp, s);
+            tmps.release(tmp);
             tmp_bytes = need;
-            LENS_CUDA(cudaMallocAsync(&tmp, tmp_bytes, s));
+            LENS_CUDA(tmps.get(&tmp, tmp_bytes));
         }
     }
 
@@ -647,18 +647,18 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     uint32_t *lk1 = nullptr, *lv0 = nullptr, *lv1 = nullptr, *pre2bfs = nullptr;
     uint32_t *level_start = nullptr, *counters = nullptr;
     uint8_t *isleaf = nullptr, *nchild = nullptr;
-    LENS_CUDA(cudaMallocAsync((void**)&lvl, n_nodes * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&first, n_nodes * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&count, n_nodes * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&skip, n_nodes * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&lk1, n_nodes * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&lv0, n_nodes * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&lv1, n_nodes * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&pre2bfs, n_nodes * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&level_start, (kMaxDepth + 2) * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&counters, 4 * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync((void**)&isleaf, n_nodes, s));
-    LENS_CUDA(cudaMallocAsync((void**)&nchild, n_nodes, s));
+    LENS_CUDA(tmps.get(&lvl, n_nodes * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&first, n_nodes * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&count, n_nodes * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&skip, n_nodes * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&lk1, n_nodes * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&lv0, n_nodes * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&lv1, n_nodes * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&pre2bfs, n_nodes * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&level_start, (kMaxDepth + 2) * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&counters, 4 * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&isleaf, n_nodes));
+    LENS_CUDA(tmps.get(&nchild, n_nodes));
     LENS_CUDA(cudaMemsetAsync(counters, 0, 4 * sizeof(uint32_t), s));
     LENS_CUDA(cudaMemsetAsync(level_start, 0xff, (kMaxDepth + 2) * sizeof(uint32_t), s));
     { k_nodes<<<G, TB, 0, s>>>(K, n, Lp, off, n_nodes, lvl, first, count, skip, isleaf); note_launch(); }
@@ -666,7 +666,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     // breadth-first order: stable sort of preorder ids by level
     LENS_CUDA(cudaMemcpyAsync(lv0, lvl, n_nodes * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     uint32_t* ids = nullptr;  // values of the level sort: preorder ids
-    LENS_CUDA(cudaMallocAsync((void**)&ids, n_nodes * sizeof(uint32_t), s));
+    LENS_CUDA(tmps.get(&ids, n_nodes * sizeof(uint32_t)));
     { k_iota_u32<<<GN, TB, 0, s>>>(ids, n_nodes); note_launch(); }
     uint32_t *lvl_sorted, *bfs2pre;
     radix_sort_pairs<uint32_t>(lv0, ids, lv1, lk1, n_nodes, 0, 8, tmp, s, &lvl_sorted, &bfs2pre);
@@ -677,18 +677,18 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
                               cudaMemcpyDeviceToHost, s));
 
     // persistent node arrays
-    LENS_CUDA(cudaMallocAsync(&st.nodeA, n_nodes * sizeof(T4), s));
-    LENS_CUDA(cudaMallocAsync(&st.nodeB, n_nodes * sizeof(T2), s));
-    LENS_CUDA(cudaMallocAsync((void**)&st.link, n_nodes * sizeof(int4), s));
-    LENS_CUDA(cudaMallocAsync((void**)&st.node_rcm, n_nodes * sizeof(float), s));
-    LENS_CUDA(cudaMallocAsync((void**)&st.node_level, n_nodes, s));
-    LENS_CUDA(cudaMallocAsync((void**)&st.parent, n_nodes * sizeof(int), s));
-    LENS_CUDA(cudaMallocAsync((void**)&st.perm, n * sizeof(uint32_t), s));
-    LENS_CUDA(cudaMallocAsync(&st.exact0, n * sizeof(T4), s));
-    if (in.kind == LENS_NFW) LENS_CUDA(cudaMallocAsync(&st.exact1, n * sizeof(T4), s));
+    LENS_CUDA(lens_malloc_async((void**)&st.nodeA, n_nodes * sizeof(T4), s));
+    LENS_CUDA(lens_malloc_async((void**)&st.nodeB, n_nodes * sizeof(T2), s));
+    LENS_CUDA(lens_malloc_async((void**)&st.link, n_nodes * sizeof(int4), s));
+    LENS_CUDA(lens_malloc_async((void**)&st.node_rcm, n_nodes * sizeof(float), s));
+    LENS_CUDA(lens_malloc_async((void**)&st.node_level, n_nodes, s));
+    LENS_CUDA(lens_malloc_async((void**)&st.parent, n_nodes * sizeof(int), s));
+    LENS_CUDA(lens_malloc_async((void**)&st.perm, n * sizeof(uint32_t), s));
+    LENS_CUDA(lens_malloc_async((void**)&st.exact0, n * sizeof(T4), s));
+    if (in.kind == LENS_NFW) LENS_CUDA(lens_malloc_async((void**)&st.exact1, n * sizeof(T4), s));
     if (in.kind != LENS_POINT) {
-        LENS_CUDA(cudaMallocAsync(&st.leaf0, n * sizeof(T4), s));
-        LENS_CUDA(cudaMallocAsync((void**)&st.listed, n, s));
+        LENS_CUDA(lens_malloc_async((void**)&st.leaf0, n * sizeof(T4), s));
+        LENS_CUDA(lens_malloc_async((void**)&st.listed, n, s));
         LENS_CUDA(cudaMemsetAsync(st.listed, 0, n, s));
     }
     LENS_CUDA(cudaMemcpyAsync(st.perm, P, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
@@ -707,8 +707,8 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
 
     dbl4* mom = nullptr;
     double2* q2 = nullptr;
-    LENS_CUDA(cudaMallocAsync((void**)&mom, n_nodes * sizeof(dbl4), s));
-    LENS_CUDA(cudaMallocAsync((void**)&q2, n_nodes * sizeof(double2), s));
+    LENS_CUDA(tmps.get(&mom, n_nodes * sizeof(dbl4)));
+    LENS_CUDA(tmps.get(&q2, n_nodes * sizeof(double2)));
     for (int l = depth; l >= 0; --l) {
         uint32_t b0 = (uint32_t)st.level_start[l], b1 = (uint32_t)st.level_start[l + 1];
         if (b1 > b0)
@@ -744,12 +744,12 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
         if (t->theta > 0.0) lambda = std::min(0.5, std::max(0.0, (1.0 / t->theta - 1.0) / std::sqrt(2.0)));
         double* r0sq = nullptr;
         uint32_t *bk0 = nullptr, *bk1 = nullptr, *bv0 = nullptr, *bv1 = nullptr, *end = nullptr;
-        LENS_CUDA(cudaMallocAsync((void**)&r0sq, n * sizeof(double), s));
-        LENS_CUDA(cudaMallocAsync((void**)&bk0, n * sizeof(uint32_t), s));
-        LENS_CUDA(cudaMallocAsync((void**)&bk1, n * sizeof(uint32_t), s));
-        LENS_CUDA(cudaMallocAsync((void**)&bv0, n * sizeof(uint32_t), s));
-        LENS_CUDA(cudaMallocAsync((void**)&bv1, n * sizeof(uint32_t), s));
-        LENS_CUDA(cudaMallocAsync((void**)&end, n_nodes * sizeof(uint32_t), s));
+        LENS_CUDA(tmps.get(&r0sq, n * sizeof(double)));
+        LENS_CUDA(tmps.get(&bk0, n * sizeof(uint32_t)));
+        LENS_CUDA(tmps.get(&bk1, n * sizeof(uint32_t)));
+        LENS_CUDA(tmps.get(&bv0, n * sizeof(uint32_t)));
+        LENS_CUDA(tmps.get(&bv1, n * sizeof(uint32_t)));
+        LENS_CUDA(tmps.get(&end, n_nodes * sizeof(uint32_t)));
         LENS_CUDA(cudaMemsetAsync(end, 0, n_nodes * sizeof(uint32_t), s));
         { k_biglevel<T><<<G, TB, 0, s>>>(sorted, K, n, Lp, off, pre2bfs, st.node_rcm, rb, in.kind, in.shape,
                                        t->theta, lambda, n_nodes, bk0, bv0, r0sq, counters + 1); note_launch(); }
@@ -766,35 +766,27 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
         lap(2);
         st.n_big = nbig;
         if (nbig > 0) {
-            LENS_CUDA(cudaMallocAsync(&st.big0, nbig * sizeof(T4), s));
-            LENS_CUDA(cudaMallocAsync(&st.big1, nbig * sizeof(T4), s));
-            LENS_CUDA(cudaMallocAsync((void**)&st.big_pid, nbig * sizeof(uint32_t), s));
+            LENS_CUDA(lens_malloc_async((void**)&st.big0, nbig * sizeof(T4), s));
+            LENS_CUDA(lens_malloc_async((void**)&st.big1, nbig * sizeof(T4), s));
+            LENS_CUDA(lens_malloc_async((void**)&st.big_pid, nbig * sizeof(uint32_t), s));
             { k_bigrecords<T><<<grid_for(nbig, TB), TB, 0, s>>>(
                 sval, nbig, (T4*)st.exact0, (T4*)st.exact1, sorted, r0sq, in.kind, in.shape, st.invNq, (T4*)st.big0,
                 (T4*)st.big1, st.big_pid, (T4*)st.leaf0, st.listed); note_launch(); }
             st.n_chunks = ((int64_t)nbig + 31) / 32;
-            LENS_CUDA(cudaMallocAsync(&st.big_chunk, st.n_chunks * sizeof(T4), s));
-            LENS_CUDA(cudaMallocAsync(&st.node_bigbox, (size_t)n_nodes * sizeof(T4), s));
+            LENS_CUDA(lens_malloc_async((void**)&st.big_chunk, st.n_chunks * sizeof(T4), s));
+            LENS_CUDA(lens_malloc_async((void**)&st.node_bigbox, (size_t)n_nodes * sizeof(T4), s));
             { k_chunkbox<T><<<grid_for(st.n_chunks, TB), TB, 0, s>>>((T4*)st.big0, nbig, st.n_chunks,
                                                                    (T4*)st.big_chunk); note_launch(); }
             { k_nodebox<T><<<grid_for((int64_t)n_nodes * 32, TB), TB, 0, s>>>(st.link, n_nodes, (T4*)st.big0,
                                                                           (T4*)st.big_chunk, (T4*)st.node_bigbox); note_launch(); }
         }
-        cudaFreeAsync(r0sq, s); cudaFreeAsync(bk0, s); cudaFreeAsync(bk1, s);
-        cudaFreeAsync(bv0, s); cudaFreeAsync(bv1, s); cudaFreeAsync(end, s);
     }
 
     uint32_t nleaves = 0;
     LENS_CUDA(cudaMemcpyAsync(&nleaves, counters, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     RootBox hrb;
     LENS_CUDA(cudaMemcpyAsync(&hrb, rb, sizeof(RootBox), cudaMemcpyDeviceToHost, s));
-    cudaFreeAsync(staged, s); cudaFreeAsync(sorted, s); cudaFreeAsync(bbox, s); cudaFreeAsync(rb, s);
-    cudaFreeAsync(k0, s); cudaFreeAsync(k1, s); cudaFreeAsync(v0, s); cudaFreeAsync(v1, s);
-    cudaFreeAsync(tmp, s); cudaFreeAsync(Lp, s); cudaFreeAsync(off, s); cudaFreeAsync(lvl, s);
-    cudaFreeAsync(first, s); cudaFreeAsync(count, s); cudaFreeAsync(skip, s); cudaFreeAsync(lk1, s);
-    cudaFreeAsync(lv0, s); cudaFreeAsync(lv1, s); cudaFreeAsync(pre2bfs, s);
-    cudaFreeAsync(level_start, s); cudaFreeAsync(counters, s); cudaFreeAsync(isleaf, s);
-    cudaFreeAsync(nchild, s); cudaFreeAsync(ids, s); cudaFreeAsync(mom, s); cudaFreeAsync(q2, s);
+    tmps.release_all();
     LENS_CUDA(cudaStreamSynchronize(s));
     lap(3);
     st.n_leaves = nleaves;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lens.h"
 
 #define LENS_DEV __device__ __forceinline__
@@ -70,6 +72,10 @@ LENS_HD double ordered_to_dbl(unsigned long long u)
 }
 
 // Host-side helpers (defined in api.cu).
+// Every device allocation of the library goes through these two, so that the
+// failure-injection hook (lens_fail_allocations) can fail the n-th one.
+cudaError_t lens_malloc(void** p, size_t bytes);
+cudaError_t lens_malloc_async(void** p, size_t bytes, cudaStream_t s);
 void note_launch();  // counts every kernel launch made by the library
 void note_launches(int64_t n);  // adds n launches (a graph replay), or takes back -n
 lens_status lens_set_error(lens_status s, const char* fmt, ...);
@@ -88,3 +94,37 @@ lens_status lens_cuda_check(cudaError_t e, const char* what);
     } while (0)
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+// Stream-ordered temporaries of one call, released on every return path
+// (an allocation that fails part-way through leaves nothing behind).
+struct StreamTemps {
+    cudaStream_t s;
+    std::vector<void*> p;
+    explicit StreamTemps(cudaStream_t st) : s(st) {}
+    StreamTemps(const StreamTemps&) = delete;
+    StreamTemps& operator=(const StreamTemps&) = delete;
+    ~StreamTemps() { release_all(); }
+    template <typename P> cudaError_t get(P** out, size_t bytes)
+    {
+        void* q = nullptr;
+        cudaError_t e = lens_malloc_async(&q, bytes, s);
+        if (e == cudaSuccess) p.push_back(q);
+        *out = (P*)q;
+        return e;
+    }
+    void release(void* q)
+    {
+        for (auto& x : p)
+            if (x == q && x) {
+                cudaFreeAsync(x, s);
+                x = nullptr;
+            }
+    }
+    void release_all()
+    {
+        for (auto& x : p)
+            if (x) cudaFreeAsync(x, s);
+        p.clear();
+    }
+};
+

@@ -284,7 +284,7 @@ extern "C" lens_status lens_smoothing_lengths(const float* xyz, int64_t n, int32
                  o_v0 = o_k1 + al(n * 8), o_v1 = o_v0 + al(n * 4), o_sp = o_v1 + al(n * 4),
                  o_tmp = o_sp + al(n * 16), total = o_tmp + al(tmp_bytes);
     char* base = nullptr;
-    LENS_CUDA(cudaMallocAsync((void**)&base, total, s));
+    LENS_CUDA(lens_malloc_async((void**)&base, total, s));
     unsigned long long* bb = (unsigned long long*)(base + o_bb);
     uint32_t* err = (uint32_t*)(base + o_err);
     uint64_t *k0 = (uint64_t*)(base + o_k0), *k1 = (uint64_t*)(base + o_k1);

@@ -51,6 +51,7 @@ struct HaloDev {
     int32_t kind, pad;
     double x, y, m, p0, p1;
     double c0, c1, c2;  // derived constants (GAUSS: c, Uq, invNq; NFW: A, B, R^2)
+    double c3;          // NFW: X f(X) / g(X), X = R_max / r_s (the adjoint's d/dR_max)
 };
 
 struct DevScratch {
@@ -79,10 +80,12 @@ struct lens_tree {
     int64_t ray_cap = 0, batch_cap = 0;
     int num_sms = 0;
     int device = 0;
+    long long wait_cycles = 4000000000ll;   // bound of a wait between cooperating warps (~2 s at 2 GHz)
     std::vector<lens::GraphEntry*> graphs;
     unsigned long long* d_stats = nullptr;  // 8 walk counters (LENS_COUNT)
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // LENS_TIMING: start, grouped, walked
     bool timed = false;
+    void* noalloc_scratch = nullptr;        // device address of the no-alloc scratch array (walk.cu)
     void* amr_ws = nullptr;                 // image-finding workspace (amr.cu), kept between calls
     void (*amr_free)(void*) = nullptr;
 };

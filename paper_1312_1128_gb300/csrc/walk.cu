@@ -22,7 +22,6 @@
 // support s.  The softening removes the cancellation of a huge point term
 // against its correction when a ray passes close to a listed particle.
 #include <algorithm>
-#include <mutex>
 #include <cmath>
 
 #include "profiles.cuh"
@@ -342,7 +341,7 @@ lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s)
     if (t->ray_scratch.ptr) cudaFreeAsync(t->ray_scratch.ptr, s);
     t->ray_scratch.ptr = nullptr;
     t->ray_cap = t->batch_cap = 0;
-    cudaError_t e = cudaMallocAsync(&t->ray_scratch.ptr, L.total, s);
+    cudaError_t e = lens_malloc_async(&t->ray_scratch.ptr, L.total, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return lens_set_error(LENS_ERR_OOM, "cannot allocate %zu bytes of ray scratch", L.total);
@@ -506,6 +505,7 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
     P.n_groups = (int64_t)ng;
     P.stack = stack;
     P.err = t->d_err;
+    P.wait_cycles = t->wait_cycles;
     for (int q = 0; q < 5; ++q) P.out[q] = (T*)out[q];
     const bool ao = (flags & LENS_ALPHA_ONLY) != 0;
     const bool direct = (flags & LENS_DIRECT) != 0;
@@ -666,28 +666,21 @@ __global__ void k_groups_inorder(int64_t n, double ox, double oy, const void* dx
     }
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the host-side name of a __device__ array is only a handle).
-static unsigned char* noalloc_scratch_ptr(int dev, lens_status* st)
+// Device address of the scratch array on the current device (the host-side
+// name of a __device__ array is only a handle, not a device address).
+// lens_build_tree looks it up with the tree's device current and keeps it in
+// the tree, so the allocation-free call itself makes no runtime lookup, and a
+// tree built after a device reset holds the new address.
+lens_status noalloc_scratch_address(void** out)
 {
-    static std::mutex mu;
-    static unsigned char* ptrs[256] = {nullptr};
-    if (dev < 0 || dev >= 256) {
-        *st = lens_set_error(LENS_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
-        return nullptr;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        *out = nullptr;
+        return lens_cuda_check(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress(no-alloc scratch)");
     }
-    std::lock_guard<std::mutex> lock(mu);
-    if (!ptrs[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            *st = lens_cuda_check(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress");
-            return nullptr;
-        }
-        ptrs[dev] = (unsigned char*)p;
-    }
-    *st = LENS_OK;
-    return ptrs[dev];
+    *out = p;
+    return LENS_OK;
 }
 
 template <typename T>
@@ -696,9 +689,8 @@ static lens_status noalloc_typed(lens_tree* t, double ox, double oy, const void*
 {
     using T4 = vec4_t<T>;
     using T2 = v2_t<T>;
-    lens_status st;
-    unsigned char* base = noalloc_scratch_ptr(t->device, &st);
-    if (!base) return st;
+    unsigned char* base = (unsigned char*)t->noalloc_scratch;
+    if (!base) return lens_set_error(LENS_ERR_INTERNAL, "tree holds no address of the no-alloc scratch");
     uint32_t* counters = (uint32_t*)(base + kNaCounters);
     T2* ray_l = (T2*)(base + kNaRayL);
     uint32_t* ray_idx = (uint32_t*)(base + kNaRayIdx);

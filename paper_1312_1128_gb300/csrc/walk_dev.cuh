@@ -37,6 +37,7 @@ template <typename T> struct WalkParams {
     int* stack;
     uint32_t* err;
     unsigned long long* stats;  // optional walk counters
+    long long wait_cycles;      // bound of every wait between cooperating warps (SM clock cycles)
 };
 
 template <int KIND, typename T> struct WalkBuf {

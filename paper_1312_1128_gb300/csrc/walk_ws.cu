@@ -11,8 +11,10 @@
 // slot.  The consumer holds the group's rays and evaluates every slot it
 // receives; at the group's last slot it adds the analytic halos and stores the
 // totals.  Each hand-over is an mbarrier phase (all 32 lanes arrive; every
-// lane acquires before reading), and every wait is bounded: a wait that gives
-// up latches DERR_WAIT_TIMEOUT and both warps return.
+// lane acquires before reading), and every wait is bounded (the tree's wait
+// limit, about 2 s of SM clock by default): a wait that gives up latches
+// DERR_WAIT_TIMEOUT and both warps return -- the consumer at once, the
+// producer at its next hand-over, which then waits for nobody.
 #include "walk_dev.cuh"
 
 namespace lens {
@@ -25,7 +27,6 @@ constexpr int kWsThreads = 2 * kWsPairs * 32;
 // block's 256 x kWsLaunchRegs, checked on the host before every launch.
 constexpr int kWsLaunchRegs = 80, kWsProdRegs = 64, kWsConsRegs = 96;
 static_assert(kWsProdRegs + kWsConsRegs == 2 * kWsLaunchRegs, "register split must use the launch budget");
-constexpr long long kWsWaitCycles = 4000000000ll;  // ~2 s at the maximum SM clock
 enum : int { kWsLast = 1, kWsStop = 2 };
 
 template <int KIND, typename T> struct WsSlot {
@@ -68,13 +69,13 @@ LENS_DEV bool mbar_try_wait(unsigned long long* b, uint32_t parity)
 
 // Wait, warp-uniformly, for the completion of the barrier phase of the given
 // parity: every lane polls (each acquiring the phase for itself) for at most
-// kWsWaitCycles.  Returns false (error latched) if any lane gave up.
-LENS_DEV bool mbar_wait(unsigned long long* b, uint32_t parity, uint32_t* err)
+// `limit` SM clock cycles.  Returns false (error latched) if any lane gave up.
+LENS_DEV bool mbar_wait(unsigned long long* b, uint32_t parity, uint32_t* err, long long limit)
 {
     bool ok = true;
     const long long t0 = clock64();
     while (!mbar_try_wait(b, parity)) {
-        if (clock64() - t0 > kWsWaitCycles) {
+        if (clock64() - t0 > limit) {
             ok = false;
             break;
         }
@@ -106,7 +107,7 @@ template <int KIND, typename T> struct WsProducer {
     LENS_DEV void acquire()
     {
         const int s = use & 1;
-        if (use >= 2 && alive) alive = mbar_wait(&W.empty[s], ((use >> 1) - 1) & 1, P.err);
+        if (use >= 2 && alive) alive = mbar_wait(&W.empty[s], ((use >> 1) - 1) & 1, P.err, P.wait_cycles);
         B = &W.slot[s].buf;
         nf = nn = nb = 0;
     }
@@ -188,7 +189,7 @@ LENS_DEV void ws_consume(const WalkParams<T>& P, WsPair<KIND, T>& W)
     uint2 rg = make_uint2(0, 0);
     for (uint32_t use = 0;; ++use) {
         const int s = use & 1;
-        if (!mbar_wait(&W.full[s], (use >> 1) & 1, P.err)) return;
+        if (!mbar_wait(&W.full[s], (use >> 1) & 1, P.err, P.wait_cycles)) return;
         const WsSlot<KIND, T>& sl = W.slot[s];
         const int flags = sl.flags, g = sl.g;
         if (flags & kWsStop) return;

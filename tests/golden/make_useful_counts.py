@@ -73,6 +73,14 @@ def main():
     rx, ry = w["rx"][idx].astype(np.float64), w["ry"][idx].astype(np.float64)
     out["fit_1e5_1000sq"] = {th: counts_for(comps, rx, ry, float(th)) for th in ["0.3", "0.1"]}
     out["fit_1e5_1000sq"]["sample"] = "4096 grid rays drawn with PCG64 seed 4245"
+
+    # equal point masses in the unit disk, FP64 64^2 grid over [-1.2, 1.2]^2
+    # (the FP64 workload): every ray of the grid
+    w = lensgen.workload_point_disk()
+    p = w["points"]
+    comps = oracle.make_components(oracle.POINT, p[:, 0], p[:, 1], p[:, 2])
+    out["point_disk_2000_64sq"] = {"0.1": counts_for(comps, w["rx"], w["ry"], 0.1)}
+    out["point_disk_2000_64sq"]["sample"] = "all 4096 grid rays"
     with open(os.path.join(HERE, "useful_counts.json"), "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
 

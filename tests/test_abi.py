@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_version_and_status_strings(lib):
     lib.lens_api_version.restype = ctypes.c_int32
-    assert lib.lens_api_version() == 1
+    assert lib.lens_api_version() == 2
     lib.lens_status_string.restype = ctypes.c_char_p
     lib.lens_status_string.argtypes = [ctypes.c_int]
     assert lib.lens_status_string(0) == b"ok"
@@ -69,6 +69,9 @@ def test_bad_arguments_return_status(lib):
     assert lt.lens_shoot_batches(None, 2, off, org, None, None, 0, None, None, None, None, None, 0, None) == 1
     off = (ctypes.c_int64 * 3)(0, 5, 3)
     assert lt.lens_shoot_batches(None, 2, off, org, None, None, 0, None, None, None, None, None, 0, None) == 1
+    # the wait limit needs a tree
+    lt.lens_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert lt.lens_set_wait_limit(None, 0) == 1
     # backward: kappa/gamma gradients are declared unsupported in this version
     assert lt.lens_shoot_rays_backward(None, 0.0, 0.0, None, None, 0, 1, None, None, None, None, None,
                                        None, None, 0, None) == 1

@@ -146,9 +146,10 @@ def test_fit_fullsize_adjoint_vs_oracle_vjp(fit):
     G[:, 1] = G2.double().cpu().numpy()
     ref = oracle.direct_vjp(comps_gauss(parts[sel], w["q"]), w["rx"].astype(np.float64),
                             w["ry"].astype(np.float64), G)
+    errs = [np.linalg.norm(grad[sel, k] - ref[:, k]) / np.linalg.norm(ref[:, k]) for k in range(3)]
+    print("full-size fit: tree adjoint vs oracle VJP, rel L2 m, x, y =", errs)
     for k in range(3):
-        err = np.linalg.norm(grad[sel, k] - ref[:, k]) / np.linalg.norm(ref[:, k])
-        assert err <= 5e-3, (k, err)
+        assert errs[k] <= 5e-3, (k, errs[k])
     lens.close()
     tl.close()
 
