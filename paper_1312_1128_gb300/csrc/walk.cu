@@ -235,11 +235,13 @@ walk_kernel(WalkParams<T> P)
     uint32_t ridx[R];
     bool rv[R];
 
+    const int NS = DIRECT && P.n_slices > 1 ? P.n_slices : 1;
     for (;;) {
-        uint32_t g = 0;
-        if (lane == 0) g = atomicAdd(P.counter, 1u);
-        g = __shfl_sync(full, g, 0);
-        if ((int64_t)g >= P.n_groups) break;
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(P.counter, 1u);
+        item = __shfl_sync(full, item, 0);
+        if ((int64_t)item >= P.n_groups * NS) break;
+        const uint32_t g = item / (uint32_t)NS, slice = item % (uint32_t)NS;
         C.H = P.gH[g];
         C.box = P.gbox[g];
         uint2 rg = P.grange[g];
@@ -265,9 +267,10 @@ walk_kernel(WalkParams<T> P)
         C.nf = C.nn = C.nb = 0;
         if (KIND >= 0 && P.n_part > 0) {
             if (DIRECT) {
-                // every particle with its full profile
-                for (int64_t base = 0; base < P.n_part; base += 0x40000000) {
-                    int64_t rem = P.n_part - base;
+                // every particle of this item's slice with its full profile
+                const int64_t p0 = P.n_part * slice / NS, p1 = P.n_part * (slice + 1) / NS;
+                for (int64_t base = p0; base < p1; base += 0x40000000) {
+                    int64_t rem = p1 - base;
                     int c = (int)(rem < 0x40000000 ? rem : 0x40000000);
                     append_ranges(C, lane == 0 ? c : 0, (int)base, P.leaf0, P.leaf1, c_near, c_dummy);
                 }
@@ -279,10 +282,10 @@ walk_kernel(WalkParams<T> P)
                 if constexpr (KIND != LENS_POINT) C.flush_big();
             }
         }
-        if (P.n_halos > 0) C.halos();
+        if (P.n_halos > 0 && slice == 0) C.halos();
         if (P.stats && lane == 0) {
             unsigned long long nr = rg.y;
-            atomicAdd(&P.stats[0], 1ull);
+            if (slice == 0) atomicAdd(&P.stats[0], 1ull);
             atomicAdd(&P.stats[1], (unsigned long long)c_vis);
             atomicAdd(&P.stats[2], (unsigned long long)c_acc);
             atomicAdd(&P.stats[3], (unsigned long long)c_near);
@@ -299,12 +302,49 @@ walk_kernel(WalkParams<T> P)
             for (int q = 0; q < 5; ++q) {
                 if (AO && q >= 2) break;
                 T val = C.tot_get(r, q);
+                if (NS > 1) {
+                    P.split[((int64_t)slice * 5 + q) * P.split_n + i] = val;
+                    continue;
+                }
                 if (P.accumulate) val += P.out[q][i];
                 P.out[q][i] = val;
             }
         }
         __syncwarp();
     }
+}
+
+// The slices of a split direct sum, added per ray in slice order with
+// Neumaier compensation (deterministic), into the outputs.
+template <typename T>
+__global__ void k_split_sum(int64_t n, int S, int nq, const T* split, T* o0, T* o1, T* o2, T* o3, T* o4,
+                            int accumulate)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T* out[5] = {o0, o1, o2, o3, o4};
+    for (int q = 0; q < nq; ++q) {
+        T s = T(0), c = T(0);
+        for (int k = 0; k < S; ++k) Comp5<T>::add1(s, c, split[((int64_t)k * 5 + q) * n + i]);
+        T v = s + c;
+        if (accumulate) v += out[q][i];
+        out[q][i] = v;
+    }
+}
+
+// Particle slices for a direct sum of ng ray groups over n_part particles:
+// enough work items (group x slice) for about 16 warps per SM when the rays
+// alone give fewer, each slice at least 128 particles, the partial sums
+// within the scratch of the split region.
+static int split_slices(const lens_tree* t, int64_t ng, int64_t n_rays, int64_t n_part)
+{
+    const int64_t target = (int64_t)t->num_sms * 16;
+    if (ng <= 0 || ng >= target) return 1;
+    int64_t S = (target + ng - 1) / ng;
+    S = std::min<int64_t>(S, std::max<int64_t>(1, n_part / 128));
+    S = std::min<int64_t>(S, 64);
+    S = std::min<int64_t>(S, (int64_t)split_values(max_slots(const_cast<lens_tree*>(t))) / std::max<int64_t>(1, n_rays));
+    return S < 2 ? 1 : (int)S;
 }
 
 // ------------------------------------------------------------- host side
@@ -534,6 +574,10 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
         P.accumulate = first_launch ? ((flags & LENS_ACCUMULATE) ? 1 : 0) : 1;
         P.counter = counter + 2 * launches;
         LENS_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(uint32_t), s));
+        // few ray groups in a direct sum: split the particles over slices too
+        P.n_slices = direct ? split_slices(t, (int64_t)ng, n, st.n) : 1;
+        P.split_n = n;
+        P.split = (T*)(base + L.split);
         if (n > 0) {
             bool done = false;
             if (!direct && t->walk_mode == LENS_WALK_PAIRS)
@@ -542,6 +586,11 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
             if (!done) {
                 if (R == 1) launch_dispatch<T, 1>(st.kind, ao, direct, P, t->num_sms, s);
                 else launch_dispatch<T, 2>(st.kind, ao, direct, P, t->num_sms, s);
+            }
+            if (P.n_slices > 1) {
+                k_split_sum<T><<<grid_for(n, 256), 256, 0, s>>>(n, P.n_slices, ao ? 2 : 5, P.split, P.out[0], P.out[1],
+                                                              P.out[2], P.out[3], P.out[4], P.accumulate);
+                note_launch();
             }
         }
         first_launch = false;

@@ -38,6 +38,12 @@ template <typename T> struct WalkParams {
     uint32_t* err;
     unsigned long long* stats;  // optional walk counters
     long long wait_cycles;      // bound of every wait between cooperating warps (SM clock cycles)
+    // direct sum split over particle slices (n_slices > 1): work item
+    // g * n_slices + k sums slice k of the particles for group g's rays into
+    // split[(k * 5 + q) * split_n + ray]; k_split_sum adds the slices
+    int n_slices;
+    int64_t split_n;
+    T* split;
 };
 
 template <int KIND, typename T> struct WalkBuf {

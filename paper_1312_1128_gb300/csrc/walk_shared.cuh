@@ -44,8 +44,12 @@ LENS_DEV bool box_reaches_group(const vec4_t<T>& b, const v2_t<T>& H, const vec4
 
 struct Layout {
     size_t boff, borig, gfirst, bbox, k0, k1, v0, v1, tmp, rl, ridx, gH, gbox, grange, counter,
-        stack, total;
+        stack, split, total;
 };
+
+// Partial sums of a direct sum split over particle slices: room for 32 rays
+// per warp slot of the device, five outputs, FP64 (see split_slices).
+inline size_t split_values(int64_t slots) { return (size_t)slots * 32; }
 
 inline Layout make_layout(int64_t n, int64_t nb, int64_t slots)
 {
@@ -69,6 +73,7 @@ inline Layout make_layout(int64_t n, int64_t nb, int64_t slots)
     L.grange = o; o += al(ng * sizeof(uint2));
     L.counter = o; o += al(64 * sizeof(uint32_t));
     L.stack = o; o += al((size_t)slots * kStackCap * sizeof(int));
+    L.split = o; o += al(split_values(slots) * 5 * sizeof(double));
     L.total = o;
     return L;
 }
