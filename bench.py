@@ -1323,17 +1323,23 @@ def grouping_roofline(n_rays, group_ms):
             "frac": gbs / peak, "peak_basis": basis}
 
 
-def build_roofline(n, n_nodes, build_ms):
+def build_roofline(n, n_nodes, phases):
     """Achieved bandwidth of the tree build against the algorithmic bytes:
     per particle 16 B read + 16 B written, 24 B per radix pass (key and index
     read and written; 6 passes of 8 bits over the 48-bit keys), and 48 B per
-    node."""
+    node; and of its first phase (staging 32 B, Morton keys 28 B, the six
+    sort passes 144 B, the gather 36 B per particle)."""
+    build_ms = sum(phases)
     nbytes = n * (32 + 24 * 6) + n_nodes * 48
+    sort_bytes = n * (32 + 28 + 24 * 6 + 36)
     peak, basis = measured_hbm_gbs()
     gbs = nbytes / (build_ms * 1e-3) / 1e9
+    sgbs = sort_bytes / (phases[0] * 1e-3) / 1e9 if phases[0] > 0 else None
     return {"ms": build_ms, "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "peak_gbs": peak,
             "frac": gbs / peak, "peak_basis": basis,
-            "note": "host wall time of the build phases (includes the syncs that read counts)"}
+            "stage_sort": {"ms": phases[0], "algorithmic_bytes": sort_bytes, "achieved_gbs": sgbs,
+                           "frac": sgbs / peak if sgbs else None},
+            "note": "device time of the build phases (CUDA events on the build's stream)"}
 
 
 # ------------------------------------------------------------- GPU path
@@ -1453,7 +1459,7 @@ def run_gpu(args, ws, rank, local):
                              "useful_flops_per_ray_nominal_table": nominal_fpr} if nominal_fpr else {}),
                          "group_ms": float(np.mean(group_ms))},
             "build_ms_phases": build_phases,
-            **({"build": build_roofline(build_sizes[0], build_sizes[1], sum(build_phases))}
+            **({"build": build_roofline(build_sizes[0], build_sizes[1], build_phases)}
                if build_phases and build_sizes else {}),
             "walk_interactions_per_s": cnt["ray_interactions"] / (w_ms * 1e-3),
             **({"grouping": grouping_roofline(n_rays, float(np.mean(group_ms)))}
@@ -1491,10 +1497,22 @@ def run_gpu(args, ws, rank, local):
 
 def run_once(args):
     """One build + shoot of the headline's lens (profiling: `ncu ... python
-    bench.py --once`); with --workload potential, one potential shot."""
+    bench.py --once`); with --workload potential, one potential shot; with
+    --workload microlensing, one build of the 1e7-star tree (inputs larger
+    than L2) and a shot of a --grid^2 patch."""
     import torch
 
     import paper_1312_1128_gb300 as L
+    if args.workload == "microlensing":
+        w = lensgen.workload_microlensing(n_grid=args.grid)
+        stars = torch.from_numpy(w["points"]).cuda()
+        dx, dy = torch.from_numpy(w["dx"]).cuda(), torch.from_numpy(w["dy"]).cuda()
+        lens = L.Lens([L.Species.points(stars)], [L.Halo.sis(0.0, 0.0, w["sis_re"])], theta=0.1, group_rays=64)
+        lens.shoot(dx, dy, origin=w["origin"], flags=L.TIMING)
+        lens.sync()
+        print(json.dumps({"grid": args.grid, "timing_ms": lens.last_timing(), "build_ms": lens.info()["build_ms"][0]}))
+        lens.close()
+        return
     w = lensgen.workload_nfw_sph(n_grid=args.grid)
     parts = torch.from_numpy(w["gauss"]).cuda()
     rx, ry = torch.from_numpy(w["rx"]).cuda(), torch.from_numpy(w["ry"]).cuda()

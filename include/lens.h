@@ -141,8 +141,9 @@ typedef struct lens_tree_info {
     int64_t n_big[8];         /* big-list entries (Sec. 3.2) */
     int32_t depth[8];         /* deepest level (root = 0) */
     double root[8][3];        /* root box centre x, y and half side */
-    double build_ms[8][4];    /* host wall time of the build phases: sort + topology
-                                 count, node layout, moments + big lists, finish */
+    double build_ms[8][4];    /* device time (CUDA events) of the build phases: stage +
+                                 Morton sort, topology + node layout, moments + big
+                                 lists, finish */
     int32_t group_rays;       /* current ray-group size (32 or 64) */
     int32_t walk;             /* current walk form: LENS_WALK_WARP or LENS_WALK_PAIRS */
 } lens_tree_info;
@@ -159,10 +160,17 @@ typedef struct lens_tree_info {
  *   params: host pointer; theta >= 0, leaf_max >= 1.
  *   stream: cudaStream_t to build on (NULL = default stream).
  *   out: receives the new tree on LENS_OK, NULL otherwise.
- * The call synchronises on `stream` once to size the node arrays.
+ * The call synchronises on `stream` once per species, to size the node
+ * arrays (and read the input check); the rest of the build is enqueued on
+ * `stream` and finishes in stream order, so use the tree on that stream or
+ * synchronise first, and keep the species data valid until then.  Counts the
+ * host reports (lens_tree_get_info) are read from the device when first
+ * asked for.
  * Errors: LENS_ERR_INVALID_ARG for NULL pointers, negative sizes, unknown
  * kinds or dtypes, theta < 0, leaf_max < 1 or a negative / non-finite mass or
- * size found on the device; LENS_ERR_OOM; LENS_ERR_CUDA.
+ * size found on the device; LENS_ERR_OOM (nothing is kept); LENS_ERR_CUDA; a
+ * consistency check that fails on the device after the call returned is
+ * reported by lens_sync_status.
  */
 lens_status lens_build_tree(const lens_species* species, int32_t n_species,
                             const lens_halo* halos, int64_t n_halos,
@@ -402,7 +410,8 @@ lens_status lens_sync_status(lens_tree* tree, void* stream);
  * earlier keeps the limit it was captured with).  Host-only, cheap. */
 lens_status lens_set_wait_limit(lens_tree* tree, int64_t cycles);
 
-/* lens_tree_get_info -- fill *info (host).  Synchronous, cheap. */
+/* lens_tree_get_info -- fill *info (host).  Synchronous (waits for the
+ * build), cheap. */
 lens_status lens_tree_get_info(const lens_tree* tree, lens_tree_info* info);
 
 /*

@@ -265,14 +265,11 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
         lens_status st = build_species(t, t->sp[i], species[i], s);
         if (st != LENS_OK) return fail(st);
     }
-    e = cudaStreamSynchronize(s);
+    // no synchronisation here: each species' build waited once for its node
+    // count (and its input check); the rest runs on in stream order, and a
+    // device-side check that fails later is reported by lens_sync_status
+    e = cudaGetLastError();
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "tree build"));
-    uint32_t herr = 0;
-    e = cudaMemcpy(&herr, t->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMemcpy(err)"));
-    if (herr & DERR_BAD_INPUT)
-        return fail(lens_set_error(LENS_ERR_INVALID_ARG, "negative or non-finite particle mass or size"));
-    if (herr) return fail(lens_set_error(LENS_ERR_INTERNAL, "tree build check failed (code %u)", herr));
     // the allocation-free shoot's scratch: its address on this device, taken
     // here (the first lookup on a device loads the array) so that the shoot
     // call itself makes no runtime lookup
@@ -486,6 +483,7 @@ lens_status lens_tree_get_info(const lens_tree* t, lens_tree_info* info)
 {
     if (!t || !info) return lens_set_error(LENS_ERR_INVALID_ARG, "NULL argument");
     std::memset(info, 0, sizeof(*info));
+    for (auto& st : const_cast<lens_tree*>(t)->sp) LENS_TRY(finish_species(st));
     info->n_species = (int32_t)t->sp.size();
     info->precision = t->precision;
     info->n_halos = t->n_halos;
@@ -511,6 +509,7 @@ lens_status lens_tree_export(const lens_tree* t, int32_t si, void* nodes, int32_
 {
     if (!t) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
     if (si < 0 || si >= (int32_t)t->sp.size()) return lens_set_error(LENS_ERR_INVALID_ARG, "bad species index");
+    LENS_TRY(finish_species(const_cast<lens_tree*>(t)->sp[si]));
     const SpeciesTree& s = t->sp[si];
     int64_t nn = s.n_nodes, n = s.n;
     LENS_CUDA(cudaDeviceSynchronize());

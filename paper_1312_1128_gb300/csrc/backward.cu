@@ -739,6 +739,7 @@ static lens_status backward_typed(lens_tree* t, double ox, double oy, const void
         if (want) {
             const int TB = 256;
             if (!direct) {
+                LENS_TRY(finish_species(const_cast<SpeciesTree&>(st)));  // the level table
                 for (int l = 0; l <= st.depth; ++l) {
                     uint32_t b0 = (uint32_t)st.level_start[l], b1 = (uint32_t)st.level_start[l + 1];
                     if (b1 > b0)

@@ -13,13 +13,13 @@
 //      lcp(K[j-1], K[j]) + 1 down to its leaf level), so a scan of the owned
 //      counts numbers every box in depth-first preorder;
 //   4. a stable sort by level gives breadth-first order (children contiguous);
-//   5. moments bottom-up, one launch per level, in FP64, stored in FP32 (or
-//      FP64) with r_cut^2 rounded up;
+//   5. moments bottom-up in one launch (the last child of a box to finish
+//      computes the box), in FP64 at the top levels (FP32 below them in an
+//      FP32 tree), stored in FP32 (or FP64) with r_cut^2 rounded up;
 //   6. big lists: a particle whose support radius s exceeds lambda times the
 //      side of a box on its path is listed at the shallowest such box; lists
 //      are grouped per box by a stable sort (deterministic order).
 #include <algorithm>
-#include <chrono>
 #include <cmath>
 
 #include "profiles.cuh"
@@ -30,6 +30,7 @@ namespace lens {
 
 struct RootBox {
     double cx, cy, half, x0, y0;
+    double inv;  // 2^24 / (2 half): Morton quantisation scale
 };
 
 template <typename T> struct V2;
@@ -67,48 +68,70 @@ __device__ __forceinline__ uint32_t compact24(uint64_t x)
 
 // ------------------------------------------------------------- 1. stage
 
+// Staging: the input rows as the tree's records {x, y, m, p}, checked
+// (finite, m >= 0, p > 0 for profiles); the bounding box of the stored
+// positions.  FP32 input into an FP32 tree stays in FP32 (the FP64 pipe of
+// this GPU has 1/64 of the FP32 rate); the box is reduced in the stored
+// precision and only the block's result goes through FP64.
 template <typename T>
 __global__ void k_stage(const void* data, int dtype, int64_t n, int kind, vec4_t<T>* staged,
                         unsigned long long* bbox, uint32_t* err)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = i < n;
-    double x = 0, y = 0, m = 0, p = 0;
+    T x = 0, y = 0;
     if (valid) {
+        vec4_t<T> r;
+        bool ok;
         if (dtype == LENS_F32) {
-            const float* d = (const float*)data + 4 * i;
-            x = d[0]; y = d[1]; m = d[2]; p = d[3];
+            const float* d = (const float*)data + 4 * i;  // the caller's rows need only 4-byte alignment
+            const float4 v = make_float4(d[0], d[1], d[2], d[3]);
+            ok = isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && v.z >= 0.0f;
+            if (kind != LENS_POINT) ok = ok && isfinite(v.w) && v.w > 0.0f;
+            r.x = (T)v.x; r.y = (T)v.y; r.z = (T)v.z; r.w = (T)v.w;
         } else {
             const double* d = (const double*)data + 4 * i;
-            x = d[0]; y = d[1]; m = d[2]; p = d[3];
+            const double dx = d[0], dy = d[1], dm = d[2], dp = d[3];
+            ok = isfinite(dx) && isfinite(dy) && isfinite(dm) && dm >= 0.0;
+            if (kind != LENS_POINT) ok = ok && isfinite(dp) && dp > 0.0;
+            r.x = (T)dx; r.y = (T)dy; r.z = (T)dm; r.w = (T)dp;
         }
-        bool ok = isfinite(x) && isfinite(y) && isfinite(m) && m >= 0.0;
-        if (kind != LENS_POINT) ok = ok && isfinite(p) && p > 0.0;
         if (!ok) {
             atomicOr(err, DERR_BAD_INPUT);
-            x = y = m = 0.0;
-            p = 1.0;
+            r.x = r.y = r.z = T(0);
+            r.w = T(1);
         }
-        vec4_t<T> r;
-        r.x = (T)x; r.y = (T)y; r.z = (T)m; r.w = (T)p;
         staged[i] = r;
-        x = (double)r.x;
-        y = (double)r.y;
+        x = r.x;
+        y = r.y;
     }
-    // warp-aggregated bounding box of the stored (rounded) positions
-    unsigned long long xmin = valid ? dbl_to_ordered(x) : ~0ull, xmax = valid ? dbl_to_ordered(x) : 0ull;
-    unsigned long long ymin = valid ? dbl_to_ordered(y) : ~0ull, ymax = valid ? dbl_to_ordered(y) : 0ull;
+    // bounding box of the stored (rounded) positions: warp, then block, then
+    // four atomics per block
+    __shared__ T red[4][32];
+    T xmin = valid ? x : T(INFINITY), xmax = valid ? x : T(-INFINITY);
+    T ymin = valid ? y : T(INFINITY), ymax = valid ? y : T(-INFINITY);
     for (int o = 16; o; o >>= 1) {
-        xmin = min(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
-        xmax = max(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-        ymin = min(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
-        ymax = max(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+        xmin = fmin(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
+        xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        ymin = fmin(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+        ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
     }
-    if ((threadIdx.x & 31) == 0 && xmax != 0ull) {
-        atomicMin(&bbox[0], xmin);
-        atomicMax(&bbox[1], xmax);
-        atomicMin(&bbox[2], ymin);
-        atomicMax(&bbox[3], ymax);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = xmin; red[1][w] = xmax; red[2][w] = ymin; red[3][w] = ymax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; ++k) {
+            xmin = fmin(xmin, red[0][k]); xmax = fmax(xmax, red[1][k]);
+            ymin = fmin(ymin, red[2][k]); ymax = fmax(ymax, red[3][k]);
+        }
+        if (xmin <= xmax) {
+            atomicMin(&bbox[0], dbl_to_ordered((double)xmin));
+            atomicMax(&bbox[1], dbl_to_ordered((double)xmax));
+            atomicMin(&bbox[2], dbl_to_ordered((double)ymin));
+            atomicMax(&bbox[3], dbl_to_ordered((double)ymax));
+        }
     }
 }
 
@@ -126,6 +149,7 @@ __global__ void k_root(const unsigned long long* bbox, RootBox* rb)
     rb->half = half;
     rb->x0 = cx - half;
     rb->y0 = cy - half;
+    rb->inv = 16777216.0 / (2.0 * half);
 }
 
 // ----------------------------------------------------------- 2. Morton
@@ -137,10 +161,12 @@ __global__ void k_morton(const vec4_t<T>* staged, int64_t n, const RootBox* rb, 
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     vec4_t<T> r = staged[i];
-    double inv = 16777216.0 / (2.0 * rb->half);
-    double fx = ((double)r.x - rb->x0) * inv, fy = ((double)r.y - rb->y0) * inv;
-    uint32_t qx = (uint32_t)fmin(fmax(floor(fx), 0.0), 16777215.0);
-    uint32_t qy = (uint32_t)fmin(fmax(floor(fy), 0.0), 16777215.0);
+    const double inv = rb->inv;
+    // FP64 differences and scaling (exact cell of the stored position), the
+    // floor and the clamp in integer arithmetic
+    long long ix = __double2ll_rd(((double)r.x - rb->x0) * inv), iy = __double2ll_rd(((double)r.y - rb->y0) * inv);
+    uint32_t qx = (uint32_t)min(max(ix, 0ll), 16777215ll);
+    uint32_t qy = (uint32_t)min(max(iy, 0ll), 16777215ll);
     keys[i] = spread24(qx) | (spread24(qy) << 1);
     vals[i] = (uint32_t)i;
 }
@@ -186,30 +212,9 @@ __device__ __forceinline__ int64_t run_end(const uint64_t* K, int64_t n, int64_t
     return hi;
 }
 
-// First index f <= j that shares j's box at level l.
-__device__ __forceinline__ int64_t run_start(const uint64_t* K, int64_t j, int l)
-{
-    if (l == 0) return 0;
-    uint64_t kj = K[j];
-    int64_t lo = -1, hi = j;  // hi shares; lo is a failing candidate
-    while (hi - lo > 1) {
-        int64_t mid = lo + ((hi - lo) >> 1);
-        if (lcp_digits(kj, K[mid]) >= l) hi = mid;
-        else lo = mid;
-    }
-    return hi;
-}
-
 __device__ __forceinline__ int first_level(const uint64_t* K, int64_t j)
 {
     return j == 0 ? 0 : lcp_digits(K[j - 1], K[j]) + 1;
-}
-
-// Preorder id of the box at level l containing particle j (l <= L_j).
-__device__ __forceinline__ uint32_t node_at(const uint64_t* K, const uint32_t* off, int64_t j, int l)
-{
-    int64_t f = run_start(K, j, l);
-    return off[f] + (uint32_t)(l - first_level(K, f));
 }
 
 __global__ void k_nodes(const uint64_t* K, int64_t n, const uint8_t* Lp, const uint32_t* off,
@@ -261,16 +266,18 @@ __global__ void k_level_bounds(const uint32_t* lvl_sorted, uint32_t n_nodes, uin
 __global__ void k_links(uint32_t n_nodes, const uint32_t* bfs2pre, const uint32_t* pre2bfs,
                         const uint32_t* lvl, const uint32_t* first, const uint32_t* count,
                         const uint8_t* isleaf, const uint8_t* nchild, int4* link, uint8_t* node_level,
-                        uint32_t* n_leaves, int* parent)
+                        uint32_t* n_leaves, int* parent, uint32_t* first_bfs, uint32_t* leaf_of)
 {
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_nodes) return;
     uint32_t v = bfs2pre[b];
+    first_bfs[b] = first[v];
     int4 L;
     if (isleaf[v]) {
         L.x = (int)first[v];
         L.y = (int)count[v] | kLeafBit;
         atomicAdd(n_leaves, 1u);
+        for (uint32_t k = 0; k < count[v]; ++k) leaf_of[first[v] + k] = b;
     } else {
         L.x = (int)pre2bfs[v + 1];
         L.y = (int)nchild[v];
@@ -291,73 +298,122 @@ template <typename T> __device__ __forceinline__ T round_up(double x);
 template <> __device__ __forceinline__ float round_up<float>(double x) { return __double2float_ru(x); }
 template <> __device__ __forceinline__ double round_up<double>(double x) { return x * (1.0 + 4e-16); }
 
-template <typename T>
-__global__ void k_moments(uint32_t b0, uint32_t b1, const uint32_t* bfs2pre, const uint32_t* lvl,
-                          const uint32_t* first, const int4* link, const vec4_t<T>* sorted,
-                          const uint64_t* K, const RootBox* rb, double theta, dbl4* mom,
-                          double2* q2, vec4_t<T>* nodeA, typename V2<T>::type* nodeB, float* rcm_out)
+// Monopole, centre of mass, quadrupole, r_cm and r_cut^2 of box b (BFS
+// index) from its particles (a leaf) or its children (children in order),
+// about the box centre, in the arithmetic type A: FP64 for the FP64 tree and
+// for the top kFp64Levels levels of the FP32 tree, FP32 below (a box there
+// holds few particles, and its moments are stored in FP32 anyway; GB300's
+// FP64 pipe has 1/64 of the FP32 rate).  r_cm and r_cut^2 are formed in FP64
+// from the stored centre of mass in every case (r_cm rounded down, r_cut^2
+// up).  Level and first particle come in BFS order.  Children are read
+// through L2 (__ldcg): other threads of the launch wrote them, and a line
+// cached in L1 before one of them was written would be stale.
+// inv_theta2 = 1/theta^2 (infinite r_cut when theta = 0).
+constexpr int kFp64Levels = 8;
+
+template <typename T, typename A>
+__device__ __forceinline__ void node_moments(uint32_t b, int l, const uint32_t* first_bfs, const int4* link,
+                                             const vec4_t<T>* sorted, const uint64_t* K, const RootBox* rb,
+                                             double inv_theta2, dbl4* mom, double2* q2, vec4_t<T>* nodeA,
+                                             typename V2<T>::type* nodeB, float* rcm_out)
 {
-    uint32_t b = b0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= b1) return;
-    uint32_t v = bfs2pre[b];
-    int l = (int)lvl[v];
-    double side = 2.0 * rb->half / (double)(1u << l);
-    uint64_t key = K[first[v]];
-    uint32_t ix = compact24(key) >> (kMaxDepth - l), iy = compact24(key >> 1) >> (kMaxDepth - l);
-    double cx = rb->x0 + (ix + 0.5) * side, cy = rb->y0 + (iy + 0.5) * side;
-    int4 L = link[b];
-    double M = 0, sx = 0, sy = 0, qr = 0, qi = 0;
+    const double side = 2.0 * rb->half / (double)(1u << l);
+    const uint64_t key = K[first_bfs[b]];
+    const uint32_t ix = compact24(key) >> (kMaxDepth - l), iy = compact24(key >> 1) >> (kMaxDepth - l);
+    const double cxd = rb->x0 + (ix + 0.5) * side, cyd = rb->y0 + (iy + 0.5) * side;
+    const A cx = (A)cxd, cy = (A)cyd;   // the moments are taken about this point
+    const int4 L = link[b];
+    A M = 0, sx = 0, sy = 0, qr = 0, qi = 0;
     if (L.y & kLeafBit) {
-        int cnt = L.y & kCountMask;
+        const int cnt = L.y & kCountMask;
         for (int k = 0; k < cnt; ++k) {
             vec4_t<T> r = sorted[L.x + k];
-            double m = (double)r.z;
+            A m = (A)r.z;
             M += m;
-            sx += m * ((double)r.x - cx);
-            sy += m * ((double)r.y - cy);
+            sx += m * ((A)r.x - cx);
+            sy += m * ((A)r.y - cy);
         }
-        double dx = M > 0 ? sx / M : 0.0, dy = M > 0 ? sy / M : 0.0;
+        const A inv = M > A(0) ? A(1) / M : A(0);
+        const A dx = sx * inv, dy = sy * inv;
         for (int k = 0; k < cnt; ++k) {
             vec4_t<T> r = sorted[L.x + k];
-            double m = (double)r.z;
-            double ax = (double)r.x - cx - dx, ay = (double)r.y - cy - dy;
+            A m = (A)r.z;
+            A ax = (A)r.x - cx - dx, ay = (A)r.y - cy - dy;
             qr += m * (ax * ax - ay * ay);
-            qi += m * 2.0 * ax * ay;
+            qi += m * A(2) * ax * ay;
         }
         sx = dx;
         sy = dy;
     } else {
+        A cm[4], cxk[4], cyk[4], cqr[4], cqi[4];
         for (int k = 0; k < L.y; ++k) {
-            dbl4 c = mom[L.x + k];
-            M += c.x;
-            sx += c.x * (c.y - cx);
-            sy += c.x * (c.z - cy);
+            const double* pm = reinterpret_cast<const double*>(mom + L.x + k);
+            const double2 cq = __ldcg(q2 + L.x + k);
+            cm[k] = (A)__ldcg(pm);
+            cxk[k] = (A)__ldcg(pm + 1) - cx;
+            cyk[k] = (A)__ldcg(pm + 2) - cy;
+            cqr[k] = (A)cq.x;
+            cqi[k] = (A)cq.y;
         }
-        double dx = M > 0 ? sx / M : 0.0, dy = M > 0 ? sy / M : 0.0;
         for (int k = 0; k < L.y; ++k) {
-            dbl4 c = mom[L.x + k];
-            double2 cq = q2[L.x + k];
-            double ax = c.y - cx - dx, ay = c.z - cy - dy;
-            qr += cq.x + c.x * (ax * ax - ay * ay);
-            qi += cq.y + c.x * 2.0 * ax * ay;
+            M += cm[k];
+            sx += cm[k] * cxk[k];
+            sy += cm[k] * cyk[k];
+        }
+        const A inv = M > A(0) ? A(1) / M : A(0);
+        const A dx = sx * inv, dy = sy * inv;
+        for (int k = 0; k < L.y; ++k) {
+            A ax = cxk[k] - dx, ay = cyk[k] - dy;
+            qr += cqr[k] + cm[k] * (ax * ax - ay * ay);
+            qi += cqi[k] + cm[k] * A(2) * ax * ay;
         }
         sx = dx;
         sy = dy;
     }
-    double cmx = cx + sx, cmy = cy + sy;
-    mom[b] = make_dbl4(M, cmx, cmy, side);
-    q2[b] = make_double2(qr, qi);
+    const A cmx = cx + sx, cmy = cy + sy;
+    mom[b] = make_dbl4((double)M, (double)cmx, (double)cmy, side);
+    q2[b] = make_double2((double)qr, (double)qi);
     // r_cm: distance from the centre of mass to the farthest corner of the box
-    double ex = fabs(sx) + 0.5 * side, ey = fabs(sy) + 0.5 * side;
-    double rcm = sqrt(ex * ex + ey * ey);
-    double rc2 = theta > 0.0 ? (rcm / theta) * (rcm / theta) : INFINITY;
-    vec4_t<T> A;
-    A.x = (T)cmx; A.y = (T)cmy; A.z = (T)M; A.w = round_up<T>(rc2);
-    nodeA[b] = A;
+    const double ex = fabs((double)cmx - cxd) + 0.5 * side, ey = fabs((double)cmy - cyd) + 0.5 * side;
+    const double rcm2 = ex * ex + ey * ey;
+    vec4_t<T> Av;
+    Av.x = (T)cmx; Av.y = (T)cmy; Av.z = (T)M; Av.w = round_up<T>(rcm2 * inv_theta2);
+    nodeA[b] = Av;
     typename V2<T>::type B;
     B.x = (T)qr; B.y = (T)qi;
     nodeB[b] = B;
-    rcm_out[b] = __double2float_rd(rcm);
+    rcm_out[b] = __fsqrt_rd(__double2float_rd(rcm2));
+}
+
+// The moments of every box in one launch, bottom-up.  One thread per box;
+// a leaf's thread computes the leaf, then counts it at its parent (one
+// atomic per box), and the child that completes the count computes the
+// parent from its children and climbs on.  Every box is computed once, by
+// whichever child finishes last; no thread ever waits for another.  A fence
+// before each count publishes the box; a fence after the completing count
+// orders the reads of its siblings.
+template <typename T>
+__global__ void k_moments_up(uint32_t n_nodes, const uint8_t* node_level, const uint32_t* first_bfs,
+                             const int4* link, const int* parent, const vec4_t<T>* sorted, const uint64_t* K,
+                             const RootBox* rb, double inv_theta2, dbl4* mom, double2* q2, vec4_t<T>* nodeA,
+                             typename V2<T>::type* nodeB, float* rcm_out, uint32_t* ready)
+{
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_nodes || !(link[b].y & kLeafBit)) return;
+    for (;;) {
+        const int l = node_level[b];
+        if (sizeof(T) == 4 && l >= kFp64Levels)
+            node_moments<T, float>(b, l, first_bfs, link, sorted, K, rb, inv_theta2, mom, q2, nodeA, nodeB, rcm_out);
+        else
+            node_moments<T, double>(b, l, first_bfs, link, sorted, K, rb, inv_theta2, mom, q2, nodeA, nodeB, rcm_out);
+        int p = parent[b];
+        if (p < 0) return;
+        __threadfence();
+        uint32_t done = atomicAdd(&ready[p], 1u) + 1u;
+        if (done < (uint32_t)link[p].y) return;   // a box's y is its child count
+        __threadfence();
+        b = (uint32_t)p;
+    }
 }
 
 // ------------------------------------------- 6. records and big lists
@@ -395,42 +451,48 @@ __device__ __forceinline__ double support_radius(int kind, double shape, double 
     return kind == LENS_POINT ? 0.0 : shape * p;
 }
 
+// Listing box of every particle: the shallowest box on its path whose side
+// times lambda its support radius s exceeds (found by climbing the parent
+// links from its leaf), and the softening radius r0 of a listed particle.
 template <typename T>
-__global__ void k_biglevel(const vec4_t<T>* sorted, const uint64_t* K, int64_t n, const uint8_t* Lp,
-                           const uint32_t* off, const uint32_t* pre2bfs, const float* rcm,
-                           const RootBox* rb, int kind, double shape, double theta, double lambda,
-                           uint32_t n_nodes, uint32_t* bkey, uint32_t* bval, double* r0sq,
-                           uint32_t* n_big)
+__global__ void k_biglevel(const vec4_t<T>* sorted, int64_t n, const uint8_t* node_level, const uint32_t* leaf_of,
+                           const int* parent, const float* rcm, const RootBox* rb, int kind, double shape,
+                           double theta, double lambda, uint32_t n_nodes, uint32_t* bkey, uint32_t* bval,
+                           double* r0sq, uint32_t* n_big)
 {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    double s = support_radius(kind, shape, (double)sorted[j].w);
-    int L = Lp[j];
-    int lp = -1;
-    double side0 = 2.0 * rb->half;
-    for (int l = 0; l <= L; ++l) {
-        if (s > lambda * side0 / (double)(1u << l)) { lp = l; break; }
+    bool listed = false;
+    if (j < n) {
+        double s = support_radius(kind, shape, (double)sorted[j].w);
+        const uint32_t leaf = leaf_of[j];
+        const int L = node_level[leaf];
+        int lp = -1;
+        double side0 = 2.0 * rb->half;
+        for (int l = 0; l <= L; ++l) {
+            if (s > lambda * side0 / (double)(1u << l)) { lp = l; break; }
+        }
+        bval[j] = (uint32_t)j;
+        if (lp < 0) {
+            bkey[j] = n_nodes;
+            r0sq[j] = 0.0;
+        } else {
+            uint32_t v = leaf;
+            for (int l = L; l > lp; --l) v = (uint32_t)parent[v];
+            bkey[j] = v;
+            // softening radius of the listed particle inside its leaf: any cell
+            // whose multipole contains the particle and is accepted lies farther
+            // than r_cm(leaf) (1/theta - 1) from the ray (r_cm grows towards the root)
+            double r0;
+            if (theta <= 0.0) r0 = s;
+            else if (theta >= 1.0) r0 = 0.0;
+            else r0 = fmin(s, (double)rcm[leaf] * (1.0 / theta - 1.0));
+            r0 *= 0.999;
+            r0sq[j] = r0 * r0;
+            listed = true;
+        }
     }
-    bval[j] = (uint32_t)j;
-    if (lp < 0) {
-        bkey[j] = n_nodes;
-        r0sq[j] = 0.0;
-        return;
-    }
-    bkey[j] = pre2bfs[node_at(K, off, j, lp)];
-    // softening radius of the listed particle inside its leaf: any cell whose
-    // multipole contains the particle and is accepted lies farther than
-    // r_cm(leaf) (1/theta - 1) from the ray (r_cm grows towards the root)
-    double r0;
-    if (theta <= 0.0) r0 = s;
-    else if (theta >= 1.0) r0 = 0.0;
-    else {
-        double rl = (double)rcm[pre2bfs[node_at(K, off, j, L)]];
-        r0 = fmin(s, rl * (1.0 / theta - 1.0));
-    }
-    r0 *= 0.999;
-    r0sq[j] = r0 * r0;
-    atomicAdd(n_big, 1u);
+    const unsigned ball = __ballot_sync(0xffffffffu, listed);
+    if ((threadIdx.x & 31) == 0 && ball) atomicAdd(n_big, (uint32_t)__popc(ball));
 }
 
 __global__ void k_bigcsr(const uint32_t* skey, int64_t n, uint32_t n_nodes, int4* link, uint32_t* end)
@@ -452,13 +514,13 @@ __global__ void k_bigcount(uint32_t n_nodes, int4* link, const uint32_t* end)
 }
 
 template <typename T>
-__global__ void k_bigrecords(const uint32_t* sval, int64_t nbig, const vec4_t<T>* e0,
+__global__ void k_bigrecords(const uint32_t* sval, const uint32_t* d_nbig, const vec4_t<T>* e0,
                              const vec4_t<T>* e1, const vec4_t<T>* sorted, const double* r0sq,
                              int kind, double shape, double invNq, vec4_t<T>* big0, vec4_t<T>* big1,
                              uint32_t* big_pid, vec4_t<T>* leaf0, uint8_t* listed)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nbig) return;
+    if (i >= (int64_t)*d_nbig) return;
     uint32_t j = sval[i];
     vec4_t<T> q = e0[j];
     double s = support_radius(kind, shape, (double)sorted[j].w);
@@ -518,10 +580,11 @@ __device__ __forceinline__ vec4_t<T> support_box(const vec4_t<T>* big0, int64_t 
 }
 
 template <typename T>
-__global__ void k_chunkbox(const vec4_t<T>* big0, int64_t nbig, int64_t nchunks, vec4_t<T>* out)
+__global__ void k_chunkbox(const vec4_t<T>* big0, const uint32_t* d_nbig, int64_t max_chunks, vec4_t<T>* out)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nchunks) return;
+    const int64_t nbig = *d_nbig;
+    if (c >= max_chunks || 32 * c >= nbig) return;
     int64_t b = 32 * c, e = b + 32 < nbig ? b + 32 : nbig;
     out[c] = support_box<T>(big0, b, e);
 }
@@ -574,18 +637,51 @@ __global__ void k_iota_u32(uint32_t* a, uint32_t n)
 
 // ================================================================ host
 
+// What the host learns of a build only when it asks (lens_tree_get_info,
+// lens_tree_export, the adjoint): written on the device at the end of the
+// build, so the build itself synchronises once (to size the node arrays).
+struct BuildMeta {
+    uint32_t level_start[kMaxDepth + 2];  // BFS start of each level; [kMaxDepth + 1] = deepest level
+    uint32_t nbig, nleaves, pad[2];
+    RootBox rb;
+};
+
+lens_status finish_species(SpeciesTree& st)
+{
+    if (st.meta_ready || st.n == 0) return LENS_OK;
+    LENS_CUDA(cudaEventSynchronize(st.ev[4]));
+    BuildMeta m;
+    LENS_CUDA(cudaMemcpy(&m, st.d_meta, sizeof(m), cudaMemcpyDeviceToHost));
+    int depth = (int)m.level_start[kMaxDepth + 1];
+    if (depth < 0 || depth > kMaxDepth) return lens_set_error(LENS_ERR_INTERNAL, "tree build: bad depth %d", depth);
+    st.depth = depth;
+    st.level_start.assign(depth + 2, 0);
+    for (int l = 0; l <= depth; ++l) st.level_start[l] = m.level_start[l];
+    st.level_start[depth + 1] = st.n_nodes;
+    st.n_big = m.nbig;
+    st.n_chunks = ((int64_t)m.nbig + 31) / 32;
+    st.n_leaves = m.nleaves;
+    st.root_cx = m.rb.cx;
+    st.root_cy = m.rb.cy;
+    st.root_half = m.rb.half;
+    for (int k = 0; k < 4; ++k) {
+        float ms = 0;
+        LENS_CUDA(cudaEventElapsedTime(&ms, st.ev[k], st.ev[k + 1]));
+        st.phase_ms[k] = ms;
+    }
+    st.meta_ready = true;
+    return LENS_OK;
+}
+
 template <typename T>
 static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species& in, cudaStream_t s)
 {
     using T4 = vec4_t<T>;
     using T2 = typename V2<T>::type;
-    using clk = std::chrono::steady_clock;
-    auto t_start = clk::now();
-    auto lap = [&](int k) {
-        auto now = clk::now();
-        st.phase_ms[k] = std::chrono::duration<double, std::milli>(now - t_start).count();
-        t_start = now;
-    };
+    // device time of the phases: events 0..4 around sort, layout, moments +
+    // big lists, finish
+    for (int k = 0; k < 5; ++k) LENS_CUDA(cudaEventCreate(&st.ev[k]));
+    LENS_CUDA(cudaEventRecord(st.ev[0], s));
     const int64_t n = in.n;
     const int TB = 256;
     const unsigned G = grid_for(n, TB);
@@ -617,6 +713,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     uint32_t* P;
     radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, kKeyBits, tmp, s, &K, &P);
     { k_gather<T><<<G, TB, 0, s>>>(staged, P, n, sorted); note_launch(); }
+    LENS_CUDA(cudaEventRecord(st.ev[1], s));
 
     // topology
     uint8_t* Lp = nullptr;
@@ -625,12 +722,16 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     LENS_CUDA(tmps.get(&off, (n + 1) * sizeof(uint32_t)));
     { k_levels<<<G, TB, 0, s>>>(K, n, t->leaf_max, Lp, off); note_launch(); }
     scan_exclusive_u32(off, off, n, off + n, tmp, s);
-    uint32_t n_nodes = 0;
+    // the one synchronisation of the build: the node count sizes the node
+    // arrays; the staging kernel's input check is read with it
+    uint32_t n_nodes = 0, herr = 0;
     LENS_CUDA(cudaMemcpyAsync(&n_nodes, off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    LENS_CUDA(cudaMemcpyAsync(&herr, t->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     LENS_CUDA(cudaStreamSynchronize(s));
+    if (herr & DERR_BAD_INPUT)
+        return lens_set_error(LENS_ERR_INVALID_ARG, "negative or non-finite particle mass or size");
     if (n_nodes == 0 || n_nodes > (uint32_t)kCountMask)
         return lens_set_error(LENS_ERR_INTERNAL, "tree build: bad node count %u", n_nodes);
-    lap(0);
     st.n_nodes = n_nodes;
     const unsigned GN = grid_for(n_nodes, TB);
     {
@@ -672,9 +773,9 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     radix_sort_pairs<uint32_t>(lv0, ids, lv1, lk1, n_nodes, 0, 8, tmp, s, &lvl_sorted, &bfs2pre);
     { k_invert<<<GN, TB, 0, s>>>(bfs2pre, n_nodes, pre2bfs); note_launch(); }
     { k_level_bounds<<<GN, TB, 0, s>>>(lvl_sorted, n_nodes, level_start); note_launch(); }
-    std::vector<uint32_t> ls(kMaxDepth + 2);
-    LENS_CUDA(cudaMemcpyAsync(ls.data(), level_start, ls.size() * sizeof(uint32_t),
-                              cudaMemcpyDeviceToHost, s));
+    LENS_CUDA(lens_malloc_async(&st.d_meta, sizeof(BuildMeta), s));
+    LENS_CUDA(cudaMemcpyAsync(((BuildMeta*)st.d_meta)->level_start, level_start, (kMaxDepth + 2) * sizeof(uint32_t),
+                              cudaMemcpyDeviceToDevice, s));
 
     // persistent node arrays
     LENS_CUDA(lens_malloc_async((void**)&st.nodeA, n_nodes * sizeof(T4), s));
@@ -693,29 +794,25 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     }
     LENS_CUDA(cudaMemcpyAsync(st.perm, P, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
 
+    uint32_t* first_bfs = nullptr;  // first particle of every node, BFS order
+    uint32_t* leaf_of = nullptr;    // leaf (BFS) of every particle
+    LENS_CUDA(tmps.get(&first_bfs, n_nodes * sizeof(uint32_t)));
+    LENS_CUDA(tmps.get(&leaf_of, n * sizeof(uint32_t)));
     { k_links<<<GN, TB, 0, s>>>(n_nodes, bfs2pre, pre2bfs, lvl, first, count, isleaf, nchild, st.link,
-                              st.node_level, counters, st.parent); note_launch(); }
-    LENS_CUDA(cudaStreamSynchronize(s));  // level table on the host
-    lap(1);
-    int depth = (int)ls[kMaxDepth + 1];
-    if (depth < 0 || depth > kMaxDepth)
-        return lens_set_error(LENS_ERR_INTERNAL, "tree build: bad depth %d", depth);
-    st.depth = depth;
-    st.level_start.assign(depth + 2, 0);
-    for (int l = 0; l <= depth; ++l) st.level_start[l] = ls[l];
-    st.level_start[depth + 1] = n_nodes;
+                              st.node_level, counters, st.parent, first_bfs, leaf_of); note_launch(); }
+    LENS_CUDA(cudaEventRecord(st.ev[2], s));
 
     dbl4* mom = nullptr;
     double2* q2 = nullptr;
+    uint32_t* ready = nullptr;
     LENS_CUDA(tmps.get(&mom, n_nodes * sizeof(dbl4)));
     LENS_CUDA(tmps.get(&q2, n_nodes * sizeof(double2)));
-    for (int l = depth; l >= 0; --l) {
-        uint32_t b0 = (uint32_t)st.level_start[l], b1 = (uint32_t)st.level_start[l + 1];
-        if (b1 > b0)
-            { k_moments<T><<<grid_for(b1 - b0, TB), TB, 0, s>>>(
-                b0, b1, bfs2pre, lvl, first, st.link, sorted, K, rb, t->theta, mom, q2, (T4*)st.nodeA,
-                (T2*)st.nodeB, st.node_rcm); note_launch(); }
-    }
+    LENS_CUDA(tmps.get(&ready, n_nodes * sizeof(uint32_t)));
+    LENS_CUDA(cudaMemsetAsync(ready, 0, n_nodes * sizeof(uint32_t), s));
+    const double inv_theta2 = t->theta > 0.0 ? 1.0 / (t->theta * t->theta) : INFINITY;
+    { k_moments_up<T><<<GN, TB, 0, s>>>(n_nodes, st.node_level, first_bfs, st.link, st.parent, sorted, K, rb,
+                                      inv_theta2, mom, q2, (T4*)st.nodeA, (T2*)st.nodeB, st.node_rcm, ready);
+      note_launch(); }
 
     // records
     double gX = 1.0;
@@ -751,7 +848,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
         LENS_CUDA(tmps.get(&bv1, n * sizeof(uint32_t)));
         LENS_CUDA(tmps.get(&end, n_nodes * sizeof(uint32_t)));
         LENS_CUDA(cudaMemsetAsync(end, 0, n_nodes * sizeof(uint32_t), s));
-        { k_biglevel<T><<<G, TB, 0, s>>>(sorted, K, n, Lp, off, pre2bfs, st.node_rcm, rb, in.kind, in.shape,
+        { k_biglevel<T><<<G, TB, 0, s>>>(sorted, n, st.node_level, leaf_of, st.parent, st.node_rcm, rb, in.kind, in.shape,
                                        t->theta, lambda, n_nodes, bk0, bv0, r0sq, counters + 1); note_launch(); }
         int bits = 1;
         while (bits < 32 && ((1ull << bits) <= (uint64_t)n_nodes)) ++bits;
@@ -760,39 +857,32 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
         radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, n, 0, bits, tmp, s, &skey, &sval);
         { k_bigcsr<<<G, TB, 0, s>>>(skey, n, n_nodes, st.link, end); note_launch(); }
         { k_bigcount<<<GN, TB, 0, s>>>(n_nodes, st.link, end); note_launch(); }
-        uint32_t nbig = 0;
-        LENS_CUDA(cudaMemcpyAsync(&nbig, counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        LENS_CUDA(cudaStreamSynchronize(s));
-        lap(2);
-        st.n_big = nbig;
-        if (nbig > 0) {
-            LENS_CUDA(lens_malloc_async((void**)&st.big0, nbig * sizeof(T4), s));
-            LENS_CUDA(lens_malloc_async((void**)&st.big1, nbig * sizeof(T4), s));
-            LENS_CUDA(lens_malloc_async((void**)&st.big_pid, nbig * sizeof(uint32_t), s));
-            { k_bigrecords<T><<<grid_for(nbig, TB), TB, 0, s>>>(
-                sval, nbig, (T4*)st.exact0, (T4*)st.exact1, sorted, r0sq, in.kind, in.shape, st.invNq, (T4*)st.big0,
-                (T4*)st.big1, st.big_pid, (T4*)st.leaf0, st.listed); note_launch(); }
-            st.n_chunks = ((int64_t)nbig + 31) / 32;
-            LENS_CUDA(lens_malloc_async((void**)&st.big_chunk, st.n_chunks * sizeof(T4), s));
-            LENS_CUDA(lens_malloc_async((void**)&st.node_bigbox, (size_t)n_nodes * sizeof(T4), s));
-            { k_chunkbox<T><<<grid_for(st.n_chunks, TB), TB, 0, s>>>((T4*)st.big0, nbig, st.n_chunks,
-                                                                   (T4*)st.big_chunk); note_launch(); }
-            { k_nodebox<T><<<grid_for((int64_t)n_nodes * 32, TB), TB, 0, s>>>(st.link, n_nodes, (T4*)st.big0,
-                                                                          (T4*)st.big_chunk, (T4*)st.node_bigbox); note_launch(); }
-        }
+        // the big arrays hold up to one entry per particle (the count is read
+        // on the device), so the build does not wait for it
+        const uint32_t* d_nbig = counters + 1;
+        const int64_t max_chunks = (n + 31) / 32;
+        LENS_CUDA(lens_malloc_async((void**)&st.big0, n * sizeof(T4), s));
+        LENS_CUDA(lens_malloc_async((void**)&st.big1, n * sizeof(T4), s));
+        LENS_CUDA(lens_malloc_async((void**)&st.big_pid, n * sizeof(uint32_t), s));
+        { k_bigrecords<T><<<G, TB, 0, s>>>(
+            sval, d_nbig, (T4*)st.exact0, (T4*)st.exact1, sorted, r0sq, in.kind, in.shape, st.invNq, (T4*)st.big0,
+            (T4*)st.big1, st.big_pid, (T4*)st.leaf0, st.listed); note_launch(); }
+        LENS_CUDA(lens_malloc_async((void**)&st.big_chunk, max_chunks * sizeof(T4), s));
+        LENS_CUDA(lens_malloc_async((void**)&st.node_bigbox, (size_t)n_nodes * sizeof(T4), s));
+        { k_chunkbox<T><<<grid_for(max_chunks, TB), TB, 0, s>>>((T4*)st.big0, d_nbig, max_chunks,
+                                                              (T4*)st.big_chunk); note_launch(); }
+        { k_nodebox<T><<<grid_for((int64_t)n_nodes * 32, TB), TB, 0, s>>>(st.link, n_nodes, (T4*)st.big0,
+                                                                      (T4*)st.big_chunk, (T4*)st.node_bigbox); note_launch(); }
     }
+    LENS_CUDA(cudaEventRecord(st.ev[3], s));
 
-    uint32_t nleaves = 0;
-    LENS_CUDA(cudaMemcpyAsync(&nleaves, counters, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    RootBox hrb;
-    LENS_CUDA(cudaMemcpyAsync(&hrb, rb, sizeof(RootBox), cudaMemcpyDeviceToHost, s));
+    BuildMeta* dm = (BuildMeta*)st.d_meta;
+    LENS_CUDA(cudaMemcpyAsync(&dm->nleaves, counters, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    LENS_CUDA(cudaMemcpyAsync(&dm->nbig, counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    LENS_CUDA(cudaMemcpyAsync(&dm->rb, rb, sizeof(RootBox), cudaMemcpyDeviceToDevice, s));
     tmps.release_all();
-    LENS_CUDA(cudaStreamSynchronize(s));
-    lap(3);
-    st.n_leaves = nleaves;
-    st.root_cx = hrb.cx;
-    st.root_cy = hrb.cy;
-    st.root_half = hrb.half;
+    LENS_CUDA(cudaEventRecord(st.ev[4], s));
+    LENS_CUDA(cudaGetLastError());
     return LENS_OK;
 }
 
@@ -815,9 +905,11 @@ void free_species(SpeciesTree& st)
 {
     void* ptrs[] = {st.nodeA, st.nodeB, st.link, st.node_rcm, st.node_level, st.exact0, st.exact1,
                     st.leaf0, st.big0, st.big1, st.perm, st.big_pid, st.listed, st.big_chunk,
-                    st.node_bigbox, st.parent};
+                    st.node_bigbox, st.parent, st.d_meta};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, 0);
+    for (cudaEvent_t& e : st.ev)
+        if (e) cudaEventDestroy(e);
     st = SpeciesTree();
 }
 

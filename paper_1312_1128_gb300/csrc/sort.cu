@@ -134,6 +134,25 @@ __global__ void radix_hist_kernel(const K* keys, int64_t n, int shift, uint32_t*
         hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
 }
 
+// Exclusive scan of one digit's counts over the tiles (block d scans
+// hist[d * nblocks ...]), in place; the digit's total goes to digit_tot[d].
+__global__ void __launch_bounds__(kScanThreads) radix_colscan_kernel(uint32_t* hist, int64_t nblocks,
+                                                                       uint32_t* digit_tot)
+{
+    uint32_t* col = hist + (int64_t)blockIdx.x * nblocks;
+    __shared__ uint32_t tot;
+    uint32_t run = 0;
+    for (int64_t base = 0; base < nblocks; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = i < nblocks ? col[i] : 0u;
+        const uint32_t ex = block_exclusive_scan(v, &tot);
+        if (i < nblocks) col[i] = run + ex;
+        run += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) digit_tot[blockIdx.x] = run;
+}
+
 // Stable scatter: element (block, r, t) precedes (block, r', t') iff
 // (r, t) < (r', t'), i.e. global index order, and equal digits keep it.  The
 // tile is first ordered by digit in shared memory (each element at its
@@ -143,7 +162,8 @@ __global__ void radix_hist_kernel(const K* keys, int64_t n, int shift, uint32_t*
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const K* kin, const uint32_t* vin, K* kout,
                                                                      uint32_t* vout, int64_t n, int shift,
-                                                                     const uint32_t* offs, int64_t nblocks)
+                                                                     const uint32_t* offs, const uint32_t* digit_tot,
+                                                                     int64_t nblocks)
 {
     __shared__ K sk[kSortTile];
     __shared__ uint32_t sv[kSortTile];
@@ -154,11 +174,34 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const K* ki
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
     const int tile_n = (int)(n - base < kSortTile ? n - base : kSortTile);
-    // the tile's digit counts, then their exclusive scan (one digit per thread)
+    // the digits' global starts (an exclusive scan of the digit totals, by one
+    // warp) plus this tile's place among the tiles of each digit
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
         run[d] = 0;
         tstart[d] = 0;
-        base_off[d] = offs[(int64_t)d * nblocks + blockIdx.x];
+        base_off[d] = digit_tot[d];
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        constexpr int per = kRadix / 32;
+        uint32_t c[per], tot = 0;
+#pragma unroll
+        for (int q = 0; q < per; ++q) {
+            c[q] = base_off[lane * per + q];
+            tot += c[q];
+        }
+        uint32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        uint32_t acc = incl - tot;
+#pragma unroll
+        for (int q = 0; q < per; ++q) {
+            base_off[lane * per + q] = acc + offs[(int64_t)(lane * per + q) * nblocks + blockIdx.x];
+            acc += c[q];
+        }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < tile_n; e += kSortThreads)
@@ -233,7 +276,7 @@ size_t radix_sort_temp_bytes(int64_t n)
 {
     int64_t nb = (n + kSortTile - 1) / kSortTile;
     size_t hist = ((size_t)nb * kRadix * sizeof(uint32_t) + 255) & ~(size_t)255;
-    return hist + scan_temp_bytes(nb * kRadix) + 256;
+    return hist + kRadix * sizeof(uint32_t) + 256;
 }
 
 // Sort (keys, vals) by bits [begin_bit, end_bit) of the key.  Uses the
@@ -248,11 +291,12 @@ void radix_sort_pairs(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int b
     if (n > 1) {
         int64_t nb = (n + kSortTile - 1) / kSortTile;
         uint32_t* hist = (uint32_t*)tmp;
-        void* stmp = (char*)tmp + (((size_t)nb * kRadix * sizeof(uint32_t) + 255) & ~(size_t)255);
+        uint32_t* dtot = (uint32_t*)((char*)tmp + (((size_t)nb * kRadix * sizeof(uint32_t) + 255) & ~(size_t)255));
         for (int b = begin_bit; b < end_bit; b += 8) {
             { radix_hist_kernel<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ki, n, b, hist, nb); note_launch(); }
-            scan_exclusive_u32(hist, hist, nb * kRadix, nullptr, stmp, s);
-            { radix_scatter_kernel<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, b, hist, nb); note_launch(); }
+            { radix_colscan_kernel<<<kRadix, kScanThreads, 0, s>>>(hist, nb, dtot); note_launch(); }
+            { radix_scatter_kernel<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, b, hist, dtot, nb);
+              note_launch(); }
             K* tk = ki; ki = ko; ko = tk;
             uint32_t* tv = vi; vi = vo; vo = tv;
         }

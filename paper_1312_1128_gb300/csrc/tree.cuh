@@ -24,7 +24,12 @@ struct SpeciesTree {
     double shape = 0;          // q (GAUSS) or R_max / r_s (NFW)
     double Uq = 0, invNq = 0;  // GAUSS: q^2/2 and 1/(1 - e^{-q^2/2})
     std::vector<int64_t> level_start;  // BFS offset of each level, depth + 2 entries
-    double phase_ms[4] = {0, 0, 0, 0};   // host wall time of the build phases
+    double phase_ms[4] = {0, 0, 0, 0};   // device time of the build phases (CUDA events)
+    // depth, level_start, n_big, n_chunks, n_leaves, root_* and phase_ms are
+    // filled from the device by finish_species when first needed
+    bool meta_ready = false;
+    void* d_meta = nullptr;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
     // node data (BFS order); element type T = float or double by prec
     void* nodeA = nullptr;     // T4 {x_cm, y_cm, M, r_cut^2}
@@ -93,6 +98,7 @@ struct lens_tree {
 namespace lens {
 
 lens_status build_species(lens_tree* t, SpeciesTree& st, const lens_species& in, cudaStream_t s);
+lens_status finish_species(SpeciesTree& st);  // host copies of the build's counts (synchronises once)
 void free_species(SpeciesTree& st);
 
 }  // namespace lens

@@ -24,10 +24,14 @@ from paper_1312_1128_gb300 import shard  # noqa: E402
 
 
 def test_two_range_split_on_one_gpu():
-    parts = lensgen.nfw_particles(20000, 51, nsph=16)
+    """327,680 rays: each range still gives every SM enough ray groups, so no
+    call splits its direct sum over particle slices (a split sums in another
+    order)."""
+    parts = lensgen.nfw_particles(3000, 51, nsph=16)
     g = lensgen.rng(52)
-    rx = g.uniform(-0.8, 0.8, 20000).astype(np.float32)
-    ry = g.uniform(-0.8, 0.8, 20000).astype(np.float32)
+    n = 327680
+    rx = g.uniform(-0.8, 0.8, n).astype(np.float32)
+    ry = g.uniform(-0.8, 0.8, n).astype(np.float32)
     dx, dy = torch.from_numpy(rx).cuda(), torch.from_numpy(ry).cuda()
     lens = L.Lens([L.Species.gauss(torch.from_numpy(parts).cuda(), 3.0)], theta=0.3)
     order, bounds = shard.ray_ranges(rx, ry, 2)
@@ -39,7 +43,7 @@ def test_two_range_split_on_one_gpu():
         split_d[idx] = to_np(shard.shoot_rank(lens, dx, dy, idx, flags=L.DIRECT))
         split_t[idx] = to_np(shard.shoot_rank(lens, dx, dy, idx))
     np.testing.assert_array_equal(split_d, full_d)
-    sel = np.arange(0, rx.size, 10)
+    sel = np.arange(0, rx.size, 100)
     ref = oracle.direct_sum(comps_gauss(parts, 3.0), rx[sel].astype(np.float64), ry[sel].astype(np.float64))
     ea, _, eg = rel_errors(split_t[sel], ref)
     assert np.median(ea) <= 1e-3 and np.median(eg) <= 1e-3
