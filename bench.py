@@ -244,6 +244,7 @@ class Workload:
     theta = THETA
     dtype = "f32"
     graph = False
+    tile = "default"
 
     def extra(self):
         return {}
@@ -286,11 +287,12 @@ class NfwSph(Workload):
         lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta)
         self.group = lens.autotune(self.rx, self.ry)
         self.walk = lens.info()["walk"]
+        self.tile = lens.info()["tile"]
         lens.close()
 
     def step(self, flags):
         lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta,
-                           group_rays=self.group, walk=self.walk)
+                           group_rays=self.group, walk=self.walk, tile=self.tile)
         lens.shoot(self.rx, self.ry, flags=flags, out=self.outs)
         return lens
 
@@ -300,7 +302,7 @@ class NfwSph(Workload):
         for d, h in zip(self.d, self.h):
             d.copy_(h, non_blocking=True)
         lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group,
-                      walk=self.walk)
+                      walk=self.walk, tile=self.tile)
         lens.shoot(self.d[1], self.d[2], out=self.outs)
         for h, o in zip(self.hout, self.outs):
             h.copy_(o, non_blocking=True)
@@ -482,9 +484,10 @@ class MixedBatches(Workload):
         import torch
         L, w = self.L, self.w
         best = None
-        for g, walk in [(32, "warp"), (64, "warp"), (32, "pairs"), (64, "pairs")]:
+        for g, walk, tile in [(32, "warp", "standard"), (64, "warp", "standard"), (32, "pairs", "standard"),
+                              (64, "pairs", "standard"), (32, "warp", "large"), (64, "warp", "large")]:
             lens = L.Lens([L.Species.points(self.sp[0]), L.Species.nfw(self.sp[1], w["conc"])], theta=self.theta,
-                          group_rays=g, walk=walk)
+                          group_rays=g, walk=walk, tile=tile)
             lens.reserve(self.n_rays, 256)
             t = []
             for _ in range(3):
@@ -496,11 +499,11 @@ class MixedBatches(Workload):
                 t.append(a.elapsed_time(b))
             lens.close()
             if best is None or min(t[1:]) < best[0]:
-                best = (min(t[1:]), g, walk)
-        _, self.group, self.walk = best
+                best = (min(t[1:]), g, walk, tile)
+        _, self.group, self.walk, self.tile = best
         self.lens.close()
         self.lens = L.Lens([L.Species.points(self.sp[0]), L.Species.nfw(self.sp[1], w["conc"])], theta=self.theta,
-                           group_rays=self.group, walk=self.walk)
+                           group_rays=self.group, walk=self.walk, tile=self.tile)
         self.lens.reserve(self.n_rays, 256)
 
     def step(self, flags):
@@ -571,12 +574,13 @@ class Microlensing(Workload):
                            theta=self.theta)
         self.group = lens.autotune(self.dx, self.dy, origin=self.w["origin"])
         self.walk = lens.info()["walk"]
+        self.tile = lens.info()["tile"]
         lens.close()
 
     def step(self, flags):
         L = self.L
         lens = L.Lens([L.Species.points(self.sp)], [L.Halo.sis(0.0, 0.0, self.w["sis_re"])], theta=self.theta,
-                      group_rays=self.group, walk=self.walk)
+                      group_rays=self.group, walk=self.walk, tile=self.tile)
         lens.shoot(self.dx, self.dy, origin=self.w["origin"], flags=flags, out=self.outs)
         return lens
 
@@ -585,7 +589,7 @@ class Microlensing(Workload):
         for d, h in zip(self.d, self.h):
             d.copy_(h, non_blocking=True)
         lens = L.Lens([L.Species.points(self.d[0])], [L.Halo.sis(0.0, 0.0, w["sis_re"])], theta=self.theta,
-                      group_rays=self.group, walk=self.walk)
+                      group_rays=self.group, walk=self.walk, tile=self.tile)
         lens.shoot(self.d[1], self.d[2], origin=w["origin"], out=self.outs)
         for h, o in zip(self.hout, self.outs):
             h.copy_(o, non_blocking=True)
@@ -650,12 +654,13 @@ class Fit(Workload):
         lens = self.L.Lens([self.L.Species.gauss(self.parts, self.w["q"])], theta=self.theta)
         self.group = lens.autotune(self.rx, self.ry)
         self.walk = lens.info()["walk"]
+        self.tile = lens.info()["tile"]
         lens.close()
 
     def step(self, flags):
         L = self.L
         lens = L.Lens([L.Species.gauss(self.parts, self.w["q"])], theta=self.theta, group_rays=self.group,
-                      walk=self.walk)
+                      walk=self.walk, tile=self.tile)
         lens.shoot(self.rx, self.ry, flags=flags | L.ALPHA_ONLY, out=self.outs)
         g1 = 2 * (self.outs[0] - self.at[0])
         g2 = 2 * (self.outs[1] - self.at[1])
@@ -673,7 +678,7 @@ class Fit(Workload):
         for d, h in zip(self.d, self.h):
             d.copy_(h, non_blocking=True)
         lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group,
-                      walk=self.walk)
+                      walk=self.walk, tile=self.tile)
         lens.shoot(self.d[1], self.d[2], flags=L.ALPHA_ONLY, out=self.outs)
         r1, r2 = self.outs[0] - self.at[0], self.outs[1] - self.at[1]
         self.grad.zero_()
@@ -1444,7 +1449,7 @@ def run_gpu(args, ws, rank, local):
             "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
-            "config": wl.config(ws), "tuning": {"group_rays": wl.group, "walk": wl.walk},
+            "config": wl.config(ws), "tuning": {"group_rays": wl.group, "walk": wl.walk, "tile": getattr(wl, "tile", "default")},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

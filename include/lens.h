@@ -118,7 +118,17 @@ typedef struct lens_params {
     int32_t precision;   /* LENS_PREC_FP32 or LENS_PREC_FP64                                          */
     int32_t group_rays;  /* rays sharing one interaction list: 0 = autotuned/default, else 32 or 64   */
     int32_t walk;        /* LENS_WALK_*: how warps share a group's walk (0 = default, autotuned)      */
+    int32_t tile;        /* LENS_TILE_*: near-field tile of the walk (0 = default, autotuned)         */
+    int32_t reserved;    /* 0                                                                         */
 } lens_params;
+
+/* lens_params.tile: the shared-memory tiles in which a warp stages leaf
+ * particles and big-list entries before evaluating them for its rays
+ * (Sec. 3.2 near field).  LENS_TILE_STANDARD: 128 of each per warp;
+ * LENS_TILE_LARGE: 256 (fewer flushes, twice the shared memory; FP32 trees,
+ * one-warp walk).  LENS_TILE_DEFAULT = STANDARD until lens_autotune picks
+ * one.  Same results up to the order of summation. */
+enum { LENS_TILE_DEFAULT = 0, LENS_TILE_STANDARD = 1, LENS_TILE_LARGE = 2 };
 
 /* lens_params.walk.  LENS_WALK_WARP: one warp walks the tree for its group
  * and evaluates every full buffer itself.  LENS_WALK_PAIRS: a producer warp
@@ -146,6 +156,8 @@ typedef struct lens_tree_info {
                                  lists, finish */
     int32_t group_rays;       /* current ray-group size (32 or 64) */
     int32_t walk;             /* current walk form: LENS_WALK_WARP or LENS_WALK_PAIRS */
+    int32_t tile;             /* current near-field tile: LENS_TILE_STANDARD or LENS_TILE_LARGE */
+    int32_t reserved;
 } lens_tree_info;
 
 /*
@@ -254,13 +266,14 @@ lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double or
 
 /*
  * lens_autotune -- pick the ray-group size (rays sharing one interaction
- * list: 32 or 64) and, unless the tree was built with a fixed
- * lens_params.walk, the walk form (LENS_WALK_WARP or LENS_WALK_PAIRS) for
- * this tree by timing the walk on the given rays (at most the first
- * 8,388,608; same arguments as lens_shoot_rays) with CUDA events, and keep
- * the fastest for later calls.  *group_rays receives the group size;
- * lens_tree_get_info reports both.  Synchronous; allocates temporary outputs
- * on the device.
+ * list: 32 or 64) and, unless the tree was built with them fixed in
+ * lens_params, the walk form (LENS_WALK_WARP or LENS_WALK_PAIRS) and the
+ * near-field tile (LENS_TILE_STANDARD or LENS_TILE_LARGE) for this tree by
+ * timing the walk on the given rays (at most the first 8,388,608; same
+ * arguments as lens_shoot_rays) with CUDA events, and keep the fastest for
+ * later calls.  *group_rays receives the group size; lens_tree_get_info
+ * reports all three.  Synchronous; allocates temporary outputs on the
+ * device.
  */
 lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, const void* ray_dx,
                           const void* ray_dy, int32_t ray_dtype, int64_t n, void* stream,

@@ -38,6 +38,7 @@ F32, F64 = 0, 1
 PREC_FP32, PREC_FP64 = 0, 1
 ALPHA_ONLY, DIRECT, ACCUMULATE, USE_GRAPH, COUNT, TIMING = 1, 2, 4, 8, 16, 32
 WALK_DEFAULT, WALK_WARP, WALK_PAIRS = 0, 1, 2
+TILE_DEFAULT, TILE_STANDARD, TILE_LARGE = 0, 1, 2
 REFINE_KAPPA_GAMMA, REFINE_DEFLECTION = 0, 1
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -77,7 +78,7 @@ class _Image(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("leaf_max", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("group_rays", ctypes.c_int32),
-                ("walk", ctypes.c_int32)]
+                ("walk", ctypes.c_int32), ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -86,7 +87,8 @@ class _Info(ctypes.Structure):
                 ("n_nodes", ctypes.c_int64 * 8), ("n_leaves", ctypes.c_int64 * 8),
                 ("n_big", ctypes.c_int64 * 8), ("depth", ctypes.c_int32 * 8),
                 ("root", (ctypes.c_double * 3) * 8), ("build_ms", (ctypes.c_double * 4) * 8),
-                ("group_rays", ctypes.c_int32), ("walk", ctypes.c_int32)]
+                ("group_rays", ctypes.c_int32), ("walk", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 def lib():
@@ -221,7 +223,8 @@ class Lens:
     """A built lens: one quadtree per species plus analytic halos."""
 
     def __init__(self, species=(), halos=(), theta: float = 0.1, leaf_max: int = 5,
-                 precision: str = "fp32", group_rays: int = 0, walk: str = "default", stream=None):
+                 precision: str = "fp32", group_rays: int = 0, walk: str = "default", tile: str = "default",
+                 stream=None):
         L = lib()
         self._keep = []
         sp = (_Species * max(1, len(species)))()
@@ -240,7 +243,8 @@ class Lens:
             hs[i] = _Halo(h.kind, 0, h.x, h.y, h.m, h.p0, h.p1)
         prec = {"fp32": PREC_FP32, "fp64": PREC_FP64}[precision]
         wk = {"default": WALK_DEFAULT, "warp": WALK_WARP, "pairs": WALK_PAIRS}[walk]
-        params = _Params(float(theta), int(leaf_max), prec, int(group_rays), wk)
+        tl = {"default": TILE_DEFAULT, "standard": TILE_STANDARD, "large": TILE_LARGE}[tile]
+        params = _Params(float(theta), int(leaf_max), prec, int(group_rays), wk, tl, 0)
         h = ctypes.c_void_p()
         _check(L.lens_build_tree(sp, len(species), hs, len(halos), ctypes.byref(params),
                                  _stream_ptr(stream), ctypes.byref(h)))
@@ -269,9 +273,9 @@ class Lens:
         if len(species_data) != len(self.species):
             raise ValueError("rebuild takes one tensor per species")
         inf = self.info()
-        walk = inf["walk"] if inf["walk"] != "default" else "default"
         new = Lens([Species(s.kind, t.detach(), s.shape) for s, t in zip(self.species, species_data)],
-                   self.halos, group_rays=inf["group_rays"], walk=walk, stream=stream, **self._build_args)
+                   self.halos, group_rays=inf["group_rays"], walk=inf["walk"], tile=inf["tile"], stream=stream,
+                   **self._build_args)
         self.close()
         self._h, new._h = new._h, None
         self._keep, self.species, self._built_from = new._keep, new.species, new._built_from
@@ -291,7 +295,8 @@ class Lens:
                     n_leaves=list(inf.n_leaves[:k]), n_big=list(inf.n_big[:k]),
                     depth=list(inf.depth[:k]), root=[tuple(inf.root[i]) for i in range(k)],
                     build_ms=[tuple(inf.build_ms[i]) for i in range(k)], group_rays=inf.group_rays,
-                    walk={WALK_WARP: "warp", WALK_PAIRS: "pairs"}.get(inf.walk, "default"))
+                    walk={WALK_WARP: "warp", WALK_PAIRS: "pairs"}.get(inf.walk, "default"),
+                    tile={TILE_STANDARD: "standard", TILE_LARGE: "large"}.get(inf.tile, "default"))
 
     def export(self, species: int = 0):
         """Host copies of one species' tree: nodes (n_nodes, 8), links

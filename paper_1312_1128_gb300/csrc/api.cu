@@ -203,6 +203,8 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
         return lens_set_error(LENS_ERR_INVALID_ARG, "group_rays must be 0, 32 or 64");
     if (params->walk < LENS_WALK_DEFAULT || params->walk > LENS_WALK_PAIRS)
         return lens_set_error(LENS_ERR_INVALID_ARG, "walk must be LENS_WALK_DEFAULT, _WARP or _PAIRS");
+    if (params->tile < LENS_TILE_DEFAULT || params->tile > LENS_TILE_LARGE)
+        return lens_set_error(LENS_ERR_INVALID_ARG, "tile must be LENS_TILE_DEFAULT, _STANDARD or _LARGE");
     for (int i = 0; i < n_species; ++i) {
         const lens_species& s = species[i];
         if (s.kind != LENS_POINT && s.kind != LENS_GAUSS && s.kind != LENS_NFW)
@@ -225,6 +227,8 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
     t->group_rays = params->group_rays == 0 ? 32 : params->group_rays;
     t->walk_mode = params->walk == LENS_WALK_DEFAULT ? LENS_WALK_WARP : params->walk;
     t->walk_fixed = params->walk != LENS_WALK_DEFAULT;
+    t->tile = params->tile == LENS_TILE_LARGE && params->precision == LENS_PREC_FP32 ? 1 : 0;
+    t->tile_fixed = params->tile != LENS_TILE_DEFAULT;
     cudaStream_t s = (cudaStream_t)stream;
     auto fail = [&](lens_status st) {
         lens_free_tree(t);
@@ -387,18 +391,24 @@ lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, con
     for (int q = 0; q < 5; ++q) out[q] = (char*)buf + q * m * es;
     int64_t off[2] = {0, m};
     double orig[2] = {origin_x, origin_y};
-    // candidates: group size x walk form (the walk only if the caller left it open)
-    const int cand_g[4] = {32, 64, 32, 64};
-    const int cand_w[4] = {LENS_WALK_WARP, LENS_WALK_WARP, LENS_WALK_PAIRS, LENS_WALK_PAIRS};
+    // candidates: group size x walk form x near-field tile (the walk form and
+    // the tile only if the caller left them open; the large tile serves the
+    // one-warp FP32 walk)
+    const int cand_g[6] = {32, 64, 32, 64, 32, 64};
+    const int cand_w[6] = {LENS_WALK_WARP, LENS_WALK_WARP, LENS_WALK_PAIRS, LENS_WALK_PAIRS, LENS_WALK_WARP,
+                           LENS_WALK_WARP};
+    const int cand_t[6] = {0, 0, 0, 0, 1, 1};
     double best = 1e300;
-    int best_g = tree->group_rays, best_w = tree->walk_mode;
-    const int user_w = tree->walk_mode;
+    int best_g = tree->group_rays, best_w = tree->walk_mode, best_t = tree->tile;
+    const int user_w = tree->walk_mode, user_t = tree->tile;
     lens_status st = LENS_OK;
-    for (int c = 0; c < 4 && st == LENS_OK; ++c) {
-        if (tree->precision == LENS_PREC_FP64 && cand_g[c] != 32) continue;
+    for (int c = 0; c < 6 && st == LENS_OK; ++c) {
+        if (tree->precision == LENS_PREC_FP64 && (cand_g[c] != 32 || cand_t[c] != 0)) continue;
         if (tree->walk_fixed && cand_w[c] != user_w) continue;
+        if (tree->tile_fixed && cand_t[c] != user_t) continue;
         tree->group_rays = cand_g[c];
         tree->walk_mode = cand_w[c];
+        tree->tile = cand_t[c];
         double ms = 0;
         for (int rep = 0; rep < 2 && st == LENS_OK; ++rep) {  // first run warms up
             st = shoot(tree, 1, off, orig, ray_dx, ray_dy, ray_dtype, out, LENS_TIMING, s);
@@ -411,11 +421,13 @@ lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, con
             best = ms;
             best_g = cand_g[c];
             best_w = cand_w[c];
+            best_t = cand_t[c];
         }
     }
     cudaFreeAsync(buf, s);
     tree->group_rays = best_g;
     tree->walk_mode = best_w;
+    tree->tile = best_t;
     *group_rays = best_g;
     return st;
 }
@@ -501,6 +513,7 @@ lens_status lens_tree_get_info(const lens_tree* t, lens_tree_info* info)
     }
     info->group_rays = t->group_rays;
     info->walk = t->walk_mode;
+    info->tile = t->tile ? LENS_TILE_LARGE : LENS_TILE_STANDARD;
     return LENS_OK;
 }
 

@@ -65,7 +65,9 @@ LENS_DEV float2 ein_poly2(float2 u)
 
 template <int KIND, typename T, int R> struct PsiCtx {
     using value_type = T;
+    using Buf = WalkBuf<KIND, T>;
     static constexpr int kKind = KIND;
+    static constexpr int kNear = Buf::kNear, kBig = Buf::kBig;
     const WalkParams<T>& P;
     const PsiConsts<T> K;
     WalkBuf<KIND, T>* B;

@@ -74,6 +74,8 @@ struct lens_tree {
     int leaf_max = 5;
     int group_rays = 32;
     int walk_mode = LENS_WALK_WARP;
+    int tile = 0;             // near-field tile of the one-warp FP32 tree walk: 0 standard, 1 doubled
+    bool tile_fixed = false;  // chosen by the caller at build time (not autotuned)
     bool walk_fixed = false;  // chosen by the caller at build time (not autotuned)
     std::vector<lens::SpeciesTree> sp;
     std::vector<lens_halo> halos_host;

@@ -222,16 +222,16 @@ __global__ void k_groups(int64_t n_groups, const int64_t* boff, const uint32_t* 
 
 // ---------------------------------------------------------------- walk
 
-template <int KIND, typename T, int R, bool AO, bool DIRECT>
+template <int KIND, typename T, int R, bool AO, bool DIRECT, int TILE>
 __global__ void __launch_bounds__(kWalkWarps * 32, sizeof(T) == 4 ? (R == 2 ? 5 : 6) : 2)
 walk_kernel(WalkParams<T> P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const unsigned full = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WalkShared<KIND, T>& S = reinterpret_cast<WalkShared<KIND, T>*>(smem_raw)[warp];
+    WalkShared<KIND, T, TILE>& S = reinterpret_cast<WalkShared<KIND, T, TILE>*>(smem_raw)[warp];
     int* stack = P.stack + ((int64_t)blockIdx.x * kWalkWarps + warp) * kStackCap;
-    WalkCtx<KIND, T, R, AO> C(P, S);
+    WalkCtx<KIND, T, R, AO, TILE> C(P, S);
     uint32_t ridx[R];
     bool rv[R];
 
@@ -349,21 +349,21 @@ static int split_slices(const lens_tree* t, int64_t ng, int64_t n_rays, int64_t 
 
 // ------------------------------------------------------------- host side
 
-template <int KIND, typename T, int R, bool AO, bool DIRECT>
+template <int KIND, typename T, int R, bool AO, bool DIRECT, int TILE>
 static int walk_blocks_per_sm()
 {
     static int cached = -1;
     if (cached < 0) {
-        size_t smem = kWalkWarps * sizeof(WalkShared<KIND, T>);
+        size_t smem = kWalkWarps * sizeof(WalkShared<KIND, T, TILE>);
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(walk_kernel<KIND, T, R, AO, DIRECT>,
+            cudaFuncSetAttribute(walk_kernel<KIND, T, R, AO, DIRECT, TILE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         // the walk keeps its working set in shared memory and registers:
         // prefer the largest shared-memory carveout
-        cudaFuncSetAttribute(walk_kernel<KIND, T, R, AO, DIRECT>,
+        cudaFuncSetAttribute(walk_kernel<KIND, T, R, AO, DIRECT, TILE>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<KIND, T, R, AO, DIRECT>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<KIND, T, R, AO, DIRECT, TILE>,
                                                       kWalkWarps * 32, smem);
         cached = nb > 0 ? nb : 1;
     }
@@ -392,34 +392,44 @@ lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s)
     return LENS_OK;
 }
 
-template <int KIND, typename T, int R, bool AO, bool DIRECT>
+template <int KIND, typename T, int R, bool AO, bool DIRECT, int TILE>
 static void launch_one(const WalkParams<T>& P, int num_sms, cudaStream_t s)
 {
-    size_t smem = kWalkWarps * sizeof(WalkShared<KIND, T>);
-    int bps = walk_blocks_per_sm<KIND, T, R, AO, DIRECT>();
+    size_t smem = kWalkWarps * sizeof(WalkShared<KIND, T, TILE>);
+    int bps = walk_blocks_per_sm<KIND, T, R, AO, DIRECT, TILE>();
     if (bps > 16) bps = 16;  // stack slots are allocated for 16 blocks per SM
     int grid = num_sms * bps;
-    { walk_kernel<KIND, T, R, AO, DIRECT><<<grid, kWalkWarps * 32, smem, s>>>(P); note_launch(); }
+    { walk_kernel<KIND, T, R, AO, DIRECT, TILE><<<grid, kWalkWarps * 32, smem, s>>>(P); note_launch(); }
 }
 
-template <typename T, int R, bool AO, bool DIRECT>
+template <typename T, int R, bool AO, bool DIRECT, int TILE>
 static void launch_kind(int kind, const WalkParams<T>& P, int num_sms, cudaStream_t s)
 {
-    if (kind == LENS_POINT) launch_one<LENS_POINT, T, R, AO, DIRECT>(P, num_sms, s);
-    else if (kind == LENS_GAUSS) launch_one<LENS_GAUSS, T, R, AO, DIRECT>(P, num_sms, s);
-    else launch_one<LENS_NFW, T, R, AO, DIRECT>(P, num_sms, s);
+    if (kind == LENS_POINT) launch_one<LENS_POINT, T, R, AO, DIRECT, TILE>(P, num_sms, s);
+    else if (kind == LENS_GAUSS) launch_one<LENS_GAUSS, T, R, AO, DIRECT, TILE>(P, num_sms, s);
+    else launch_one<LENS_NFW, T, R, AO, DIRECT, TILE>(P, num_sms, s);
 }
 
+// tile: the near-field tile size of the tree walk (WalkBuf); the larger tile
+// is built for FP32 tree walks only (the direct sum and the FP64 tree keep
+// the standard one).
 template <typename T, int R>
 static void launch_dispatch(int kind, bool ao, bool direct, const WalkParams<T>& P, int num_sms,
-                            cudaStream_t s)
+                            cudaStream_t s, int tile = 0)
 {
     if (direct) {
-        if (ao) launch_kind<T, R, true, true>(kind, P, num_sms, s);
-        else launch_kind<T, R, false, true>(kind, P, num_sms, s);
+        if (ao) launch_kind<T, R, true, true, 0>(kind, P, num_sms, s);
+        else launch_kind<T, R, false, true, 0>(kind, P, num_sms, s);
     } else {
-        if (ao) launch_kind<T, R, true, false>(kind, P, num_sms, s);
-        else launch_kind<T, R, false, false>(kind, P, num_sms, s);
+        if constexpr (sizeof(T) == 4) {
+            if (tile == 1) {
+                if (ao) launch_kind<T, R, true, false, 1>(kind, P, num_sms, s);
+                else launch_kind<T, R, false, false, 1>(kind, P, num_sms, s);
+                return;
+            }
+        }
+        if (ao) launch_kind<T, R, true, false, 0>(kind, P, num_sms, s);
+        else launch_kind<T, R, false, false, 0>(kind, P, num_sms, s);
     }
 }
 
@@ -584,8 +594,8 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
                 done = R == 1 ? launch_ws<T, 1>(st.kind, ao, P, t->num_sms, s)
                               : launch_ws<T, 2>(st.kind, ao, P, t->num_sms, s);
             if (!done) {
-                if (R == 1) launch_dispatch<T, 1>(st.kind, ao, direct, P, t->num_sms, s);
-                else launch_dispatch<T, 2>(st.kind, ao, direct, P, t->num_sms, s);
+                if (R == 1) launch_dispatch<T, 1>(st.kind, ao, direct, P, t->num_sms, s, t->tile);
+                else launch_dispatch<T, 2>(st.kind, ao, direct, P, t->num_sms, s, t->tile);
             }
             if (P.n_slices > 1) {
                 k_split_sum<T><<<grid_for(n, 256), 256, 0, s>>>(n, P.n_slices, ao ? 2 : 5, P.split, P.out[0], P.out[1],

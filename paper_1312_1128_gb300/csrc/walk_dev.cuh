@@ -46,20 +46,26 @@ template <typename T> struct WalkParams {
     T* split;
 };
 
-template <int KIND, typename T> struct WalkBuf {
+// The shared-memory tiles of the near field: TILE 0 holds kNearCap leaf
+// particles and kBigCap big-list entries per warp, TILE 1 twice as many
+// (fewer flushes and folds, more shared memory per warp); the autotuner
+// times both.
+template <int KIND, typename T, int TILE = 0> struct WalkBuf {
+    static constexpr int kNear = TILE ? 2 * kNearCap : kNearCap;
+    static constexpr int kBig = TILE ? 2 * kBigCap : kBigCap;
     // FP32 Gaussian big entries are stored one array per field, so that two
     // consecutive entries load as one float2 operand of the packed form
     static constexpr bool kPackedBig = KIND == LENS_GAUSS && sizeof(T) == 4;
-    static constexpr int kB = kPackedBig ? kBigCap : 1;
+    static constexpr int kB = kPackedBig ? kBig : 1;
     T fdx[kFarCap], fdy[kFarCap], fM[kFarCap], fqr[kFarCap], fqi[kFarCap];
-    vec4_t<T> n0[kNearCap];
-    vec4_t<T> n1[KIND == LENS_NFW ? kNearCap : 1];
-    vec4_t<T> b0[KIND == LENS_POINT || kPackedBig ? 1 : kBigCap];
-    vec4_t<T> b1[KIND == LENS_POINT || kPackedBig ? 1 : kBigCap];
+    vec4_t<T> n0[kNear];
+    vec4_t<T> n1[KIND == LENS_NFW ? kNear : 1];
+    vec4_t<T> b0[KIND == LENS_POINT || kPackedBig ? 1 : kBig];
+    vec4_t<T> b1[KIND == LENS_POINT || kPackedBig ? 1 : kBig];
     // -x, -y (from the group anchor), -c log2 e, m/N_q, -(m/N_q) e^-q^2/2,
     // m c/N_q, the flag or 1/r0^2 (b0.w of the generic layout) and 1/c.
     // Entries whose support contains every ray of the group fill slots
-    // [0, n_in) from the bottom; the others fill [kBigCap - n_out, kBigCap)
+    // [0, n_in) from the bottom; the others fill [kBig - n_out, kBig)
     // from the top (the buffer count packs n_in | n_out << 16).
     float bnx[kB], bny[kB], bcl[kB], bm[kB], bme[kB], bk[kB], bw[kB], bic[kB];
 };
@@ -78,24 +84,25 @@ template <typename T> struct WalkTot {
 };
 
 // Shared memory of one warp of the walk kernel.
-template <int KIND, typename T> struct WalkShared {
-    WalkBuf<KIND, T> buf;
+template <int KIND, typename T, int TILE = 0> struct WalkShared {
+    WalkBuf<KIND, T, TILE> buf;
     WalkRanges rng;
     WalkTot<T> tot;
 };
 
-template <int KIND, typename T, int R, bool AO> struct WalkEval {
+template <int KIND, typename T, int R, bool AO, int TILE = 0> struct WalkEval {
     static_assert(R <= kMaxRaysPerLane, "rays per lane");
     static constexpr int kQ = AO ? 2 : 5;  // components accumulated
+    using Buf = WalkBuf<KIND, T, TILE>;
     const WalkParams<T>& P;
-    WalkBuf<KIND, T>* B;   // the buffers being evaluated
+    Buf* B;                // the buffers being evaluated
     WalkTot<T>* Tt;        // compensated totals of the lane's rays
     T lx[R], ly[R];
     Acc5<T> part[R];
     v2_t<T> H;
     vec4_t<T> box;
 
-    LENS_DEV WalkEval(const WalkParams<T>& p, WalkBuf<KIND, T>* b, WalkTot<T>* t) : P(p), B(b), Tt(t) {}
+    LENS_DEV WalkEval(const WalkParams<T>& p, Buf* b, WalkTot<T>* t) : P(p), B(b), Tt(t) {}
 
     LENS_DEV void tot_zero()
     {
@@ -229,9 +236,9 @@ template <int KIND, typename T, int R, bool AO> struct WalkEval {
             i += 2;
         }
         if (i < n_in) big_entry_scalar(i, pa);
-        i = kBigCap - n_out;
-        if ((i & 1) && i < kBigCap) big_entry_scalar(i++, pa);
-        for (; i + 1 < kBigCap; i += 2) {
+        i = Buf::kBig - n_out;
+        if ((i & 1) && i < Buf::kBig) big_entry_scalar(i++, pa);
+        for (; i + 1 < Buf::kBig; i += 2) {
             const float2 w = *reinterpret_cast<const float2*>(&B->bw[i]);
             if (w.x < 0.0f && w.y < 0.0f) {
                 big_pair_packed<true>(i, pa, LX, LY);
@@ -261,7 +268,7 @@ template <int KIND, typename T, int R, bool AO> struct WalkEval {
     // parallelism.
     LENS_DEV void eval_big(int nb)
     {
-        if constexpr (WalkBuf<KIND, T>::kPackedBig) {
+        if constexpr (Buf::kPackedBig) {
             eval_big_packed(nb);
             return;
         }
@@ -362,13 +369,16 @@ template <int KIND, typename T, int R, bool AO> struct WalkEval {
 
 // The walk kernel's context: evaluation plus the buffer counts, where a full
 // buffer is evaluated on the spot.
-template <int KIND, typename T, int R, bool AO> struct WalkCtx : WalkEval<KIND, T, R, AO> {
+template <int KIND, typename T, int R, bool AO, int TILE = 0> struct WalkCtx : WalkEval<KIND, T, R, AO, TILE> {
     using value_type = T;
+    using Buf = WalkBuf<KIND, T, TILE>;
     static constexpr int kKind = KIND;
+    static constexpr int kNear = Buf::kNear, kBig = Buf::kBig;
     WalkRanges* Rg;
     int nf = 0, nn = 0, nb = 0;  // entries in the far, near and big buffers
 
-    LENS_DEV WalkCtx(const WalkParams<T>& p, WalkShared<KIND, T>& s) : WalkEval<KIND, T, R, AO>(p, &s.buf, &s.tot), Rg(&s.rng) {}
+    LENS_DEV WalkCtx(const WalkParams<T>& p, WalkShared<KIND, T, TILE>& s)
+        : WalkEval<KIND, T, R, AO, TILE>(p, &s.buf, &s.tot), Rg(&s.rng) {}
     LENS_DEV void flush_far()
     {
         this->eval_far(nf);
@@ -404,7 +414,7 @@ LENS_DEV void append_ranges(Ctx& C, int cnt, int first, const vec4_t<T>* src0, c
     if (lane == 31) C.Rg->rs_off[32] = tot;
     __syncwarp();
     for (int base = 0; base < tot; base += 32) {
-        if (C.nn + 32 > kNearCap) {
+        if (C.nn + 32 > Ctx::kNear) {
             C.flush_near();
             __syncwarp();
         }
@@ -491,7 +501,7 @@ LENS_DEV void append_big(Ctx& C, bool has, int v, int z, int w, int& n_seen, int
             ball &= ball - 1;
             int c = __shfl_sync(full, cid, src);
             int o = __shfl_sync(full, own, src);
-            if (big_used<KIND, T>(C.nb) + 32 > kBigCap) {
+            if (big_used<KIND, T>(C.nb) + 32 > Ctx::kBig) {
                 C.flush_big();
                 __syncwarp();
             }
@@ -519,13 +529,13 @@ LENS_DEV void append_big(Ctx& C, bool has, int v, int z, int w, int& n_seen, int
                 }
             }
             unsigned kb = __ballot_sync(full, keep);
-            if constexpr (WalkBuf<KIND, T>::kPackedBig) {
+            if constexpr (Ctx::Buf::kPackedBig) {
                 const bool in = keep && q0.w < T(-1.5);
                 const unsigned bi = __ballot_sync(full, in), lt = (1u << lane) - 1u;
                 if (keep) {
                     q1 = P.big1[e];
                     int slot = in ? (C.nb & 0xffff) + __popc(bi & lt)
-                                  : kBigCap - 1 - ((C.nb >> 16) + __popc(kb & ~bi & lt));
+                                  : Ctx::kBig - 1 - ((C.nb >> 16) + __popc(kb & ~bi & lt));
                     C.B->bnx[slot] = -q0.x;
                     C.B->bny[slot] = -q0.y;
                     C.B->bcl[slot] = -q1.y;

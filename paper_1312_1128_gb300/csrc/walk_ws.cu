@@ -89,7 +89,9 @@ LENS_DEV bool mbar_wait(unsigned long long* b, uint32_t parity, uint32_t* err, l
 // into the current slot; a full buffer hands the slot over.
 template <int KIND, typename T> struct WsProducer {
     using value_type = T;
+    using Buf = WalkBuf<KIND, T>;
     static constexpr int kKind = KIND;
+    static constexpr int kNear = Buf::kNear, kBig = Buf::kBig;
     const WalkParams<T>& P;
     WsPair<KIND, T>& W;
     WalkBuf<KIND, T>* B = nullptr;

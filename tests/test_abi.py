@@ -53,6 +53,9 @@ def test_bad_arguments_return_status(lib):
     for th, leaf, prec, res in [(-1.0, 5, 0, 0), (0.1, 0, 0, 0), (0.1, 5, 7, 0), (0.1, 5, 0, 3), (0.1, 5, 0, -1)]:
         p = L._Params(th, leaf, prec, 0, res)
         assert lt.lens_build_tree(None, 0, None, 0, ctypes.byref(p), None, ctypes.byref(h)) == 1
+    # unknown near-field tile
+    p = L._Params(0.1, 5, 0, 0, 0, 3)
+    assert lt.lens_build_tree(None, 0, None, 0, ctypes.byref(p), None, ctypes.byref(h)) == 1
     # unknown species kind
     sp = (L._Species * 1)(L._Species(9, 0, 10, 1, 3.0))
     p = L._Params(0.1, 5, 0, 0, 0)

@@ -125,9 +125,11 @@ def _counters(lens):
 @pytest.mark.parametrize("group_rays", [32, 64])
 @pytest.mark.parametrize("case", ["gauss", "nfw_halo_ao", "points_fp64"])
 def test_walk_pairs_matches_warp(case, group_rays):
-    """The producer/consumer walk visits the same boxes and keeps the same
-    entries as the one-warp walk (interaction counters equal), and its totals
-    agree up to the order of summation; both meet the oracle's bar."""
+    """The producer/consumer walk and the one-warp walk with the large
+    near-field tile visit the same boxes and keep the same entries as the
+    one-warp walk with the standard tile (interaction counters equal), and
+    their totals agree up to the order of summation; all meet the oracle's
+    bar."""
     g = lensgen.rng(31)
     rx = g.uniform(-1, 1, 3000).astype(np.float64)
     ry = g.uniform(-1, 1, 3000).astype(np.float64)
@@ -148,22 +150,26 @@ def test_walk_pairs_matches_warp(case, group_rays):
     dx, dy = cu(rx.astype(dtype)), cu(ry.astype(dtype))
     res, cnt = {}, {}
     ncomp = 2 if flags & L.ALPHA_ONLY else 5
-    for walk in ("warp", "pairs"):
-        lens = L.Lens(species, halos, theta=0.3, precision=prec, group_rays=group_rays, walk=walk)
+    for form, walk, tile in (("warp", "warp", "standard"), ("pairs", "pairs", "standard"),
+                             ("large", "warp", "large")):
+        lens = L.Lens(species, halos, theta=0.3, precision=prec, group_rays=group_rays, walk=walk, tile=tile)
+        assert lens.info()["tile"] == (tile if prec == "fp32" else "standard")
         out = lens.shoot(dx, dy, flags=flags | L.COUNT)
-        res[walk] = np.stack([o.double().cpu().numpy() for o in out[:ncomp]], axis=1)
+        res[form] = np.stack([o.double().cpu().numpy() for o in out[:ncomp]], axis=1)
         lens.sync()
-        cnt[walk] = _counters(lens)
+        cnt[form] = _counters(lens)
         lens.close()
-    assert cnt["warp"] == cnt["pairs"], cnt
+    assert cnt["warp"] == cnt["pairs"] == cnt["large"], cnt
     ref, absum = oracle.direct_sum(comps, rx, ry, with_absum=True)
-    a, b = res["warp"], res["pairs"]
-    # same terms, summed in another order: a few roundings of the sum of |terms|
-    eps = 1e-14 if prec == "fp64" else 1e-6
-    d = np.abs(a - b) / (absum[:, :ncomp] + 1e-300)
-    assert d.max() <= eps, d.max(axis=0)
-    ea, _, _ = rel_errors(b, ref) if ncomp == 5 else rel_errors(np.c_[b, ref[:, 2:]], ref)
-    assert np.median(ea) <= 1e-3
+    a = res["warp"]
+    for form in ("pairs", "large"):
+        b = res[form]
+        # same terms, summed in another order: a few roundings of the sum of |terms|
+        eps = 1e-14 if prec == "fp64" else 1e-6
+        d = np.abs(a - b) / (absum[:, :ncomp] + 1e-300)
+        assert d.max() <= eps, (form, d.max(axis=0))
+        ea, _, _ = rel_errors(b, ref) if ncomp == 5 else rel_errors(np.c_[b, ref[:, 2:]], ref)
+        assert np.median(ea) <= 1e-3
 
 
 def test_tree_points_fp64_theta01():
