@@ -485,7 +485,8 @@ class MixedBatches(Workload):
         L, w = self.L, self.w
         best = None
         for g, walk, tile in [(32, "warp", "standard"), (64, "warp", "standard"), (32, "pairs", "standard"),
-                              (64, "pairs", "standard"), (32, "warp", "large"), (64, "warp", "large")]:
+                              (64, "pairs", "standard"), (64, "trios", "standard"), (32, "warp", "large"),
+                              (64, "warp", "large")]:
             lens = L.Lens([L.Species.points(self.sp[0]), L.Species.nfw(self.sp[1], w["conc"])], theta=self.theta,
                           group_rays=g, walk=walk, tile=tile)
             lens.reserve(self.n_rays, 256)
@@ -1549,7 +1550,7 @@ def main():
                     help="ray grid side (profiling runs use a smaller grid; the metric is quoted at 2048)")
     ap.add_argument("--once", action="store_true",
                     help="one build + shoot of the workload and exit (for profiler captures)")
-    ap.add_argument("--walk", choices=["warp", "pairs"], default="warp",
+    ap.add_argument("--walk", choices=["warp", "pairs", "trios"], default="warp",
                     help="walk form of --once (the headline's autotuned choice is warp)")
     ap.add_argument("--print-walk-hash", action="store_true",
                     help="print the hash of the walk sources that profiles/walk_traffic.json is keyed by "

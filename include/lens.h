@@ -134,9 +134,11 @@ enum { LENS_TILE_DEFAULT = 0, LENS_TILE_STANDARD = 1, LENS_TILE_LARGE = 2 };
  * and evaluates every full buffer itself.  LENS_WALK_PAIRS: a producer warp
  * walks and fills shared-memory buffers that a consumer warp, holding the
  * group's rays, evaluates (the latency-bound walk overlaps the arithmetic).
- * Same results up to the order of summation.  LENS_WALK_DEFAULT = WARP until
- * lens_autotune picks one. */
-enum { LENS_WALK_DEFAULT = 0, LENS_WALK_WARP = 1, LENS_WALK_PAIRS = 2 };
+ * LENS_WALK_TRIOS: a producer warp feeds two consumer warps that split the
+ * 64 rays of its group (32 each), so that two warps of three do arithmetic;
+ * with 32-ray groups it is the pairs form.  Same results up to the order of
+ * summation.  LENS_WALK_DEFAULT = WARP until lens_autotune picks one. */
+enum { LENS_WALK_DEFAULT = 0, LENS_WALK_WARP = 1, LENS_WALK_PAIRS = 2, LENS_WALK_TRIOS = 3 };
 
 typedef struct lens_tree lens_tree;  /* opaque, library-owned */
 
@@ -155,7 +157,7 @@ typedef struct lens_tree_info {
                                  Morton sort, topology + node layout, moments + big
                                  lists, finish */
     int32_t group_rays;       /* current ray-group size (32 or 64) */
-    int32_t walk;             /* current walk form: LENS_WALK_WARP or LENS_WALK_PAIRS */
+    int32_t walk;             /* current walk form: LENS_WALK_WARP, _PAIRS or _TRIOS */
     int32_t tile;             /* current near-field tile: LENS_TILE_STANDARD or LENS_TILE_LARGE */
     int32_t reserved;
 } lens_tree_info;
@@ -267,7 +269,7 @@ lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double or
 /*
  * lens_autotune -- pick the ray-group size (rays sharing one interaction
  * list: 32 or 64) and, unless the tree was built with them fixed in
- * lens_params, the walk form (LENS_WALK_WARP or LENS_WALK_PAIRS) and the
+ * lens_params, the walk form (LENS_WALK_WARP, _PAIRS or _TRIOS) and the
  * near-field tile (LENS_TILE_STANDARD or LENS_TILE_LARGE) for this tree by
  * timing the walk on the given rays (at most the first 8,388,608; same
  * arguments as lens_shoot_rays) with CUDA events, and keep the fastest for

@@ -37,7 +37,7 @@ POINT, GAUSS, NFW, SIS, DISK = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 PREC_FP32, PREC_FP64 = 0, 1
 ALPHA_ONLY, DIRECT, ACCUMULATE, USE_GRAPH, COUNT, TIMING = 1, 2, 4, 8, 16, 32
-WALK_DEFAULT, WALK_WARP, WALK_PAIRS = 0, 1, 2
+WALK_DEFAULT, WALK_WARP, WALK_PAIRS, WALK_TRIOS = 0, 1, 2, 3
 TILE_DEFAULT, TILE_STANDARD, TILE_LARGE = 0, 1, 2
 REFINE_KAPPA_GAMMA, REFINE_DEFLECTION = 0, 1
 
@@ -242,7 +242,7 @@ class Lens:
         for i, h in enumerate(halos):
             hs[i] = _Halo(h.kind, 0, h.x, h.y, h.m, h.p0, h.p1)
         prec = {"fp32": PREC_FP32, "fp64": PREC_FP64}[precision]
-        wk = {"default": WALK_DEFAULT, "warp": WALK_WARP, "pairs": WALK_PAIRS}[walk]
+        wk = {"default": WALK_DEFAULT, "warp": WALK_WARP, "pairs": WALK_PAIRS, "trios": WALK_TRIOS}[walk]
         tl = {"default": TILE_DEFAULT, "standard": TILE_STANDARD, "large": TILE_LARGE}[tile]
         params = _Params(float(theta), int(leaf_max), prec, int(group_rays), wk, tl, 0)
         h = ctypes.c_void_p()
@@ -295,7 +295,7 @@ class Lens:
                     n_leaves=list(inf.n_leaves[:k]), n_big=list(inf.n_big[:k]),
                     depth=list(inf.depth[:k]), root=[tuple(inf.root[i]) for i in range(k)],
                     build_ms=[tuple(inf.build_ms[i]) for i in range(k)], group_rays=inf.group_rays,
-                    walk={WALK_WARP: "warp", WALK_PAIRS: "pairs"}.get(inf.walk, "default"),
+                    walk={WALK_WARP: "warp", WALK_PAIRS: "pairs", WALK_TRIOS: "trios"}.get(inf.walk, "default"),
                     tile={TILE_STANDARD: "standard", TILE_LARGE: "large"}.get(inf.tile, "default"))
 
     def export(self, species: int = 0):

@@ -73,17 +73,21 @@ template <typename T> struct BackParams {
 };
 
 constexpr int kMaxGroup = 64;
+// The adjoint's leaf and big-list buffers (entries per warp).  Halving them
+// raises the occupancy from five to seven blocks per SM but did not speed
+// the lens-fit adjoint up (4.0 against 3.9 ms): it is not occupancy-bound.
+constexpr int kBackNear = kNearCap, kBackBig = kBigCap;
 
 template <int KIND, typename T> struct BackShared {
     T rx[kMaxGroup], ry[kMaxGroup], rg1[kMaxGroup], rg2[kMaxGroup];
     T fdx[kFarCap], fdy[kFarCap], fM[kFarCap], fqr[kFarCap], fqi[kFarCap];
     int fnode[kFarCap];
-    vec4_t<T> n0[kNearCap];
-    vec4_t<T> n1[KIND == LENS_NFW ? kNearCap : 1];
-    int npid[kNearCap];
-    vec4_t<T> b0[KIND == LENS_POINT ? 1 : kBigCap];
-    vec4_t<T> b1[KIND == LENS_POINT ? 1 : kBigCap];
-    int bpid[KIND == LENS_POINT ? 1 : kBigCap];
+    vec4_t<T> n0[kBackNear];
+    vec4_t<T> n1[KIND == LENS_NFW ? kBackNear : 1];
+    int npid[kBackNear];
+    vec4_t<T> b0[KIND == LENS_POINT ? 1 : kBackBig];
+    vec4_t<T> b1[KIND == LENS_POINT ? 1 : kBackBig];
+    int bpid[KIND == LENS_POINT ? 1 : kBackBig];
     int rs_off[33];
     int rs_first[32];
     int rs_end[32];
@@ -275,7 +279,7 @@ LENS_DEV void back_append_near(BackCtx<KIND, T>& C, int cnt, int first, int& nbu
     if (lane == 31) S.rs_off[32] = tot;
     __syncwarp();
     for (int base = 0; base < tot; base += 32) {
-        if (nbuf + 32 > kNearCap) {
+        if (nbuf + 32 > kBackNear) {
             C.flush_near(nbuf);
             nbuf = 0;
         }
@@ -344,7 +348,7 @@ LENS_DEV void back_append_big(BackCtx<KIND, T>& C, bool has, int v, int z, int w
             ball &= ball - 1;
             int c = __shfl_sync(full, cid, src);
             int o = __shfl_sync(full, own, src);
-            if (nbuf + 32 > kBigCap) {
+            if (nbuf + 32 > kBackBig) {
                 C.flush_big(nbuf);
                 nbuf = 0;
             }

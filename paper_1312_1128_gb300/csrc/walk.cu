@@ -590,9 +590,11 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
         P.split = (T*)(base + L.split);
         if (n > 0) {
             bool done = false;
-            if (!direct && t->walk_mode == LENS_WALK_PAIRS)
-                done = R == 1 ? launch_ws<T, 1>(st.kind, ao, P, t->num_sms, s)
-                              : launch_ws<T, 2>(st.kind, ao, P, t->num_sms, s);
+            if (!direct && (t->walk_mode == LENS_WALK_PAIRS || t->walk_mode == LENS_WALK_TRIOS)) {
+                const int consumers = t->walk_mode == LENS_WALK_TRIOS ? 2 : 1;
+                done = R == 1 ? launch_ws<T, 1>(st.kind, ao, P, t->num_sms, s, consumers)
+                              : launch_ws<T, 2>(st.kind, ao, P, t->num_sms, s, consumers);
+            }
             if (!done) {
                 if (R == 1) launch_dispatch<T, 1>(st.kind, ao, direct, P, t->num_sms, s, t->tile);
                 else launch_dispatch<T, 2>(st.kind, ao, direct, P, t->num_sms, s, t->tile);

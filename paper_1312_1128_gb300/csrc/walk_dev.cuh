@@ -635,6 +635,6 @@ LENS_DEV bool traverse(Ctx& C, int* stack, int& c_vis, int& c_acc, int& c_near, 
 // Launch the producer/consumer form of the walk (walk_ws.cu); false if it
 // cannot run here (the caller then launches the one-warp walk).
 template <typename T, int R>
-bool launch_ws(int kind, bool ao, const WalkParams<T>& P, int num_sms, cudaStream_t s);
+bool launch_ws(int kind, bool ao, const WalkParams<T>& P, int num_sms, cudaStream_t s, int consumers);
 
 }  // namespace lens

@@ -19,14 +19,22 @@
 
 namespace lens {
 
-constexpr int kWsPairs = 4;                  // producer/consumer pairs per block
-constexpr int kWsThreads = 2 * kWsPairs * 32;
-// Registers per thread: the kernel is compiled for kWsLaunchRegs (three
-// blocks per SM); the producer warpgroup then gives registers back and the
-// consumer warpgroup takes them: 128 x (kWsProdRegs + kWsConsRegs) equals the
-// block's 256 x kWsLaunchRegs, checked on the host before every launch.
-constexpr int kWsLaunchRegs = 80, kWsProdRegs = 64, kWsConsRegs = 96;
-static_assert(kWsProdRegs + kWsConsRegs == 2 * kWsLaunchRegs, "register split must use the launch budget");
+constexpr int kWsPairs = 4;                  // producers (one per team) per block
+// A team is one producer warp and CONS consumer warps: CONS = 1 (pairs; the
+// consumer holds the whole group, R rays per lane) or CONS = 2 (trios: a
+// 64-ray group split between two consumers, 32 rays each).  The block's
+// warps are the producers (warpgroup 0) and then each consumer rank's
+// warpgroup.
+template <int CONS> struct WsShape {
+    static constexpr int kThreads = (1 + CONS) * kWsPairs * 32;
+    static constexpr int kBlocksPerSm = CONS == 1 ? 3 : 2;
+    // Registers per thread: the kernel is compiled for kLaunchRegs; the
+    // producer warpgroup then gives registers back and each consumer
+    // warpgroup takes them: 128 (kProdRegs + CONS kConsRegs) equals the
+    // block's kThreads x kLaunchRegs, checked on the host before every launch.
+    static constexpr int kLaunchRegs = 80, kProdRegs = 64, kConsRegs = CONS == 1 ? 96 : 88;
+    static_assert(kProdRegs + CONS * kConsRegs == (1 + CONS) * kLaunchRegs, "register split must use the launch budget");
+};
 enum : int { kWsLast = 1, kWsStop = 2 };
 
 template <int KIND, typename T> struct WsSlot {
@@ -36,11 +44,11 @@ template <int KIND, typename T> struct WsSlot {
     int flags;       // kWsLast: the group's last slot; kWsStop: no more groups
 };
 
-template <int KIND, typename T> struct WsPair {
+template <int KIND, typename T, int CONS> struct WsPair {
     WsSlot<KIND, T> slot[2];
-    unsigned long long full[2], empty[2];  // mbarriers, 32 arrivals each
+    unsigned long long full[2], empty[2];  // mbarriers: 32 and 32 CONS arrivals
     WalkRanges rng;                        // the producer's list ranges
-    WalkTot<T> tot;                        // the consumer's compensated totals
+    WalkTot<T> tot[CONS];                  // each consumer's compensated totals
 };
 
 LENS_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -87,13 +95,13 @@ LENS_DEV bool mbar_wait(unsigned long long* b, uint32_t parity, uint32_t* err, l
 
 // The producer's context: the traversal and the appends of walk_dev.cuh write
 // into the current slot; a full buffer hands the slot over.
-template <int KIND, typename T> struct WsProducer {
+template <int KIND, typename T, int CONS> struct WsProducer {
     using value_type = T;
     using Buf = WalkBuf<KIND, T>;
     static constexpr int kKind = KIND;
     static constexpr int kNear = Buf::kNear, kBig = Buf::kBig;
     const WalkParams<T>& P;
-    WsPair<KIND, T>& W;
+    WsPair<KIND, T, CONS>& W;
     WalkBuf<KIND, T>* B = nullptr;
     WalkRanges* Rg;
     v2_t<T> H;
@@ -103,7 +111,7 @@ template <int KIND, typename T> struct WsProducer {
     uint32_t use = 0;  // slots handed over so far
     bool alive = true;
 
-    LENS_DEV WsProducer(const WalkParams<T>& p, WsPair<KIND, T>& w) : P(p), W(w), Rg(&w.rng) {}
+    LENS_DEV WsProducer(const WalkParams<T>& p, WsPair<KIND, T, CONS>& w) : P(p), W(w), Rg(&w.rng) {}
 
     // Take the next slot, waiting until the consumer has released it.
     LENS_DEV void acquire()
@@ -144,12 +152,12 @@ template <int KIND, typename T> struct WsProducer {
     LENS_DEV void flush_big() { flush(); }
 };
 
-template <int KIND, typename T>
-LENS_DEV void ws_produce(const WalkParams<T>& P, WsPair<KIND, T>& W, int* stack)
+template <int KIND, typename T, int CONS>
+LENS_DEV void ws_produce(const WalkParams<T>& P, WsPair<KIND, T, CONS>& W, int* stack)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    WsProducer<KIND, T> C(P, W);
+    WsProducer<KIND, T, CONS> C(P, W);
     for (;;) {
         uint32_t g = 0;
         if (lane == 0) g = atomicAdd(P.counter, 1u);
@@ -180,11 +188,12 @@ LENS_DEV void ws_produce(const WalkParams<T>& P, WsPair<KIND, T>& W, int* stack)
     }
 }
 
-template <int KIND, typename T, int R, bool AO>
-LENS_DEV void ws_consume(const WalkParams<T>& P, WsPair<KIND, T>& W)
+// Consumer rank c of its team: rays c * 32 + [0, 32 R) of every group.
+template <int KIND, typename T, int R, bool AO, int CONS>
+LENS_DEV void ws_consume(const WalkParams<T>& P, WsPair<KIND, T, CONS>& W, int c)
 {
     const int lane = threadIdx.x & 31;
-    WalkEval<KIND, T, R, AO> E(P, &W.slot[0].buf, &W.tot);
+    WalkEval<KIND, T, R, AO> E(P, &W.slot[0].buf, &W.tot[c]);
     uint32_t ridx[R];
     bool rv[R];
     int cur = -1;
@@ -203,7 +212,7 @@ LENS_DEV void ws_consume(const WalkParams<T>& P, WsPair<KIND, T>& W)
             rg = P.grange[g];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                int k = r * 32 + lane;
+                int k = c * 32 + r * 32 + lane;
                 rv[r] = k < (int)rg.y;
                 if (rv[r]) {
                     v2_t<T> l = P.ray_l[rg.x + k];
@@ -247,85 +256,102 @@ LENS_DEV void ws_consume(const WalkParams<T>& P, WsPair<KIND, T>& W)
     }
 }
 
-template <int KIND, typename T, int R, bool AO>
-__global__ void __launch_bounds__(kWsThreads, 3) walk_ws_kernel(WalkParams<T> P)
+template <int KIND, typename T, int R, bool AO, int CONS>
+__global__ void __launch_bounds__(WsShape<CONS>::kThreads, WsShape<CONS>::kBlocksPerSm)
+walk_ws_kernel(WalkParams<T> P)
 {
+    using Sh = WsShape<CONS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pair = warp % kWsPairs;
-    WsPair<KIND, T>& W = reinterpret_cast<WsPair<KIND, T>*>(smem_raw)[pair];
-    if (warp < kWsPairs && lane == 0) {
+    const int team = warp % kWsPairs, role = warp / kWsPairs;  // role 0: producer; 1..CONS: consumers
+    WsPair<KIND, T, CONS>& W = reinterpret_cast<WsPair<KIND, T, CONS>*>(smem_raw)[team];
+    if (role == 0 && lane == 0) {
         mbar_init(&W.full[0], 32);
         mbar_init(&W.full[1], 32);
-        mbar_init(&W.empty[0], 32);
-        mbar_init(&W.empty[1], 32);
+        mbar_init(&W.empty[0], 32 * CONS);
+        mbar_init(&W.empty[1], 32 * CONS);
     }
     __syncthreads();
-    if (warp < kWsPairs) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kWsProdRegs));
-        int* stack = P.stack + ((int64_t)blockIdx.x * kWsPairs + pair) * kStackCap;
-        ws_produce<KIND, T>(P, W, stack);
+    if (role == 0) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(Sh::kProdRegs));
+        int* stack = P.stack + ((int64_t)blockIdx.x * kWsPairs + team) * kStackCap;
+        ws_produce<KIND, T, CONS>(P, W, stack);
     } else {
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kWsConsRegs));
-        ws_consume<KIND, T, R, AO>(P, W);
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(Sh::kConsRegs));
+        ws_consume<KIND, T, R, AO, CONS>(P, W, role - 1);
     }
 }
 
-template <int KIND, typename T, int R, bool AO>
+template <int KIND, typename T, int R, bool AO, int CONS>
 static int ws_blocks_per_sm()
 {
     static int cached = -1;
     if (cached < 0) {
-        size_t smem = kWsPairs * sizeof(WsPair<KIND, T>);
-        cudaFuncSetAttribute(walk_ws_kernel<KIND, T, R, AO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        size_t smem = kWsPairs * sizeof(WsPair<KIND, T, CONS>);
+        cudaFuncSetAttribute(walk_ws_kernel<KIND, T, R, AO, CONS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        cudaFuncSetAttribute(walk_ws_kernel<KIND, T, R, AO>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(walk_ws_kernel<KIND, T, R, AO, CONS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              100);
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_ws_kernel<KIND, T, R, AO>, kWsThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_ws_kernel<KIND, T, R, AO, CONS>,
+                                                      WsShape<CONS>::kThreads, smem);
         cached = nb > 0 ? nb : 1;
     }
     return cached;
 }
 
 // Compiled registers per thread of the kernel (the register split is only
-// valid if the launch holds exactly kWsLaunchRegs per thread).
-template <int KIND, typename T, int R, bool AO>
+// valid if the launch holds exactly kLaunchRegs per thread).
+template <int KIND, typename T, int R, bool AO, int CONS>
 static int ws_kernel_regs()
 {
     static int cached = -1;
     if (cached < 0) {
         cudaFuncAttributes a{};
-        cached = cudaFuncGetAttributes(&a, walk_ws_kernel<KIND, T, R, AO>) == cudaSuccess ? a.numRegs : 0;
+        cached = cudaFuncGetAttributes(&a, walk_ws_kernel<KIND, T, R, AO, CONS>) == cudaSuccess ? a.numRegs : 0;
     }
     return cached;
 }
 
-template <int KIND, typename T, int R, bool AO>
+template <int KIND, typename T, int R, bool AO, int CONS>
 static bool ws_launch_one(const WalkParams<T>& P, int num_sms, cudaStream_t s)
 {
-    if (ws_kernel_regs<KIND, T, R, AO>() != kWsLaunchRegs) return false;
-    size_t smem = kWsPairs * sizeof(WsPair<KIND, T>);
-    int bps = ws_blocks_per_sm<KIND, T, R, AO>();
+    if (ws_kernel_regs<KIND, T, R, AO, CONS>() != WsShape<CONS>::kLaunchRegs) return false;
+    size_t smem = kWsPairs * sizeof(WsPair<KIND, T, CONS>);
+    int bps = ws_blocks_per_sm<KIND, T, R, AO, CONS>();
     // stacks are allocated for 16 blocks x kWalkWarps warps per SM
     if (bps > 16 * kWalkWarps / kWsPairs) bps = 16 * kWalkWarps / kWsPairs;
-    { walk_ws_kernel<KIND, T, R, AO><<<num_sms * bps, kWsThreads, smem, s>>>(P); note_launch(); }
+    { walk_ws_kernel<KIND, T, R, AO, CONS><<<num_sms * bps, WsShape<CONS>::kThreads, smem, s>>>(P); note_launch(); }
     return true;
 }
 
-template <typename T, int R>
-bool launch_ws(int kind, bool ao, const WalkParams<T>& P, int num_sms, cudaStream_t s)
+template <typename T, int R, int CONS>
+static bool launch_kind_ws(int kind, bool ao, const WalkParams<T>& P, int num_sms, cudaStream_t s)
 {
     if (kind == LENS_POINT)
-        return ao ? ws_launch_one<LENS_POINT, T, R, true>(P, num_sms, s) : ws_launch_one<LENS_POINT, T, R, false>(P, num_sms, s);
+        return ao ? ws_launch_one<LENS_POINT, T, R, true, CONS>(P, num_sms, s)
+                  : ws_launch_one<LENS_POINT, T, R, false, CONS>(P, num_sms, s);
     if (kind == LENS_GAUSS)
-        return ao ? ws_launch_one<LENS_GAUSS, T, R, true>(P, num_sms, s) : ws_launch_one<LENS_GAUSS, T, R, false>(P, num_sms, s);
-    return ao ? ws_launch_one<LENS_NFW, T, R, true>(P, num_sms, s) : ws_launch_one<LENS_NFW, T, R, false>(P, num_sms, s);
+        return ao ? ws_launch_one<LENS_GAUSS, T, R, true, CONS>(P, num_sms, s)
+                  : ws_launch_one<LENS_GAUSS, T, R, false, CONS>(P, num_sms, s);
+    return ao ? ws_launch_one<LENS_NFW, T, R, true, CONS>(P, num_sms, s)
+              : ws_launch_one<LENS_NFW, T, R, false, CONS>(P, num_sms, s);
 }
 
-template bool launch_ws<float, 1>(int, bool, const WalkParams<float>&, int, cudaStream_t);
-template bool launch_ws<float, 2>(int, bool, const WalkParams<float>&, int, cudaStream_t);
-template bool launch_ws<double, 1>(int, bool, const WalkParams<double>&, int, cudaStream_t);
-template bool launch_ws<double, 2>(int, bool, const WalkParams<double>&, int, cudaStream_t);
+// R: rays per lane of the group (32 R rays).  consumers = 2 splits a 64-ray
+// group between two consumer warps (R = 2 only).
+template <typename T, int R>
+bool launch_ws(int kind, bool ao, const WalkParams<T>& P, int num_sms, cudaStream_t s, int consumers)
+{
+    if constexpr (R == 2) {
+        if (consumers == 2) return launch_kind_ws<T, 1, 2>(kind, ao, P, num_sms, s);
+    }
+    return launch_kind_ws<T, R, 1>(kind, ao, P, num_sms, s);
+}
+
+template bool launch_ws<float, 1>(int, bool, const WalkParams<float>&, int, cudaStream_t, int);
+template bool launch_ws<float, 2>(int, bool, const WalkParams<float>&, int, cudaStream_t, int);
+template bool launch_ws<double, 1>(int, bool, const WalkParams<double>&, int, cudaStream_t, int);
+template bool launch_ws<double, 2>(int, bool, const WalkParams<double>&, int, cudaStream_t, int);
 
 }  // namespace lens

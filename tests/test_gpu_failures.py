@@ -28,16 +28,17 @@ def cu(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def test_pairs_walk_wait_runs_out_and_reports_timeout():
+@pytest.mark.parametrize("walk", ["pairs", "trios"])
+def test_pairs_walk_wait_runs_out_and_reports_timeout(walk):
     parts = lensgen.nfw_particles(20000, 91, nsph=16)
     g = lensgen.rng(92)
     dx = cu(g.uniform(-0.8, 0.8, 40000).astype(np.float32))
     dy = cu(g.uniform(-0.8, 0.8, 40000).astype(np.float32))
-    ref_lens = L.Lens([L.Species.gauss(cu(parts), 3.0)], theta=0.3, walk="warp")
+    ref_lens = L.Lens([L.Species.gauss(cu(parts), 3.0)], theta=0.3, walk="warp", group_rays=64)
     ref = ref_lens.shoot(dx, dy)
     ref_lens.sync()
-    lens = L.Lens([L.Species.gauss(cu(parts), 3.0)], theta=0.3, walk="pairs")
-    assert lens.info()["walk"] == "pairs"
+    lens = L.Lens([L.Species.gauss(cu(parts), 3.0)], theta=0.3, walk=walk, group_rays=64)
+    assert lens.info()["walk"] == walk
     lens.set_wait_limit(200)
     lens.shoot(dx, dy)
     with pytest.raises(L.LensError) as e:

@@ -125,7 +125,8 @@ def _counters(lens):
 @pytest.mark.parametrize("group_rays", [32, 64])
 @pytest.mark.parametrize("case", ["gauss", "nfw_halo_ao", "points_fp64"])
 def test_walk_pairs_matches_warp(case, group_rays):
-    """The producer/consumer walk and the one-warp walk with the large
+    """The producer/consumer walks (one consumer, or two sharing a 64-ray
+    group) and the one-warp walk with the large
     near-field tile visit the same boxes and keep the same entries as the
     one-warp walk with the standard tile (interaction counters equal), and
     their totals agree up to the order of summation; all meet the oracle's
@@ -151,7 +152,7 @@ def test_walk_pairs_matches_warp(case, group_rays):
     res, cnt = {}, {}
     ncomp = 2 if flags & L.ALPHA_ONLY else 5
     for form, walk, tile in (("warp", "warp", "standard"), ("pairs", "pairs", "standard"),
-                             ("large", "warp", "large")):
+                             ("trios", "trios", "standard"), ("large", "warp", "large")):
         lens = L.Lens(species, halos, theta=0.3, precision=prec, group_rays=group_rays, walk=walk, tile=tile)
         assert lens.info()["tile"] == (tile if prec == "fp32" else "standard")
         out = lens.shoot(dx, dy, flags=flags | L.COUNT)
@@ -159,10 +160,10 @@ def test_walk_pairs_matches_warp(case, group_rays):
         lens.sync()
         cnt[form] = _counters(lens)
         lens.close()
-    assert cnt["warp"] == cnt["pairs"] == cnt["large"], cnt
+    assert cnt["warp"] == cnt["pairs"] == cnt["trios"] == cnt["large"], cnt
     ref, absum = oracle.direct_sum(comps, rx, ry, with_absum=True)
     a = res["warp"]
-    for form in ("pairs", "large"):
+    for form in ("pairs", "trios", "large"):
         b = res[form]
         # same terms, summed in another order: a few roundings of the sum of |terms|
         eps = 1e-14 if prec == "fp64" else 1e-6
@@ -290,7 +291,7 @@ def test_invalid_inputs_are_rejected():
         L.Lens([], theta=-1.0)
 
 
-@pytest.mark.parametrize("walk", ["warp", "pairs"])
+@pytest.mark.parametrize("walk", ["warp", "pairs", "trios"])
 def test_forward_is_bitwise_deterministic(walk):
     """Each ray's sum is taken by one warp in a fixed order whatever warp takes
     its group (the work counter only changes who): repeated shots and a fresh
