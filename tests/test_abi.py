@@ -50,7 +50,7 @@ def test_bad_arguments_return_status(lib):
     assert lt.lens_build_tree(None, 0, None, 0, None, None, ctypes.byref(h)) == 1
     assert h.value is None
     # negative theta, bad leaf size, unknown precision, unknown walk
-    for th, leaf, prec, res in [(-1.0, 5, 0, 0), (0.1, 0, 0, 0), (0.1, 5, 7, 0), (0.1, 5, 0, 3), (0.1, 5, 0, -1)]:
+    for th, leaf, prec, res in [(-1.0, 5, 0, 0), (0.1, 0, 0, 0), (0.1, 5, 7, 0), (0.1, 5, 0, 4), (0.1, 5, 0, -1)]:
         p = L._Params(th, leaf, prec, 0, res)
         assert lt.lens_build_tree(None, 0, None, 0, ctypes.byref(p), None, ctypes.byref(h)) == 1
     # unknown near-field tile
