@@ -10,8 +10,9 @@
 // run splits into its children's runs by binary search within it, children
 // whose box lies farther than the current k-th distance are skipped, the
 // nearest child is visited first, and cells of at most kKnnLeaf particles
-// are scanned.  One thread per particle keeps its k smallest squared
-// distances; the search is exact.
+// are scanned.  32 consecutive particles share one warp and one descent
+// (the union of what their queries need); each lane keeps its own k
+// smallest squared distances; the search is exact.
 #include <cmath>
 
 #include "common.cuh"
@@ -174,70 +175,95 @@ struct KnnNode {
     int level;
 };
 
+constexpr int kKnnWarps = 4;   // warps per block of the query
+
+// One warp per 32 consecutive particles of the key order (spatially close
+// queries, one per lane), sharing one descent of the octree: a child cell is
+// visited if any lane's query may have a neighbour in it (its box within
+// that lane's current k-th distance), the 8 children's runs are found by 8
+// lanes' binary searches at once, children are pushed nearest-first by the
+// smallest of the lanes' distances, and a scanned cell's particles are
+// broadcast to every lane, each keeping its own k smallest.  The stack is
+// the warp's, in shared memory.  Exact: a lane never prunes a cell that
+// could hold one of its k nearest.
 template <int K>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kKnnWarps * 32)
 k_knn_query(const float4* sp4, const uint64_t* keys, int64_t n, int k, KnnCube c, float* r_out, uint32_t* err)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float4 p = sp4[i];
+    __shared__ KnnNode stacks[kKnnWarps][kKnnStack];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    KnnNode* stack = stacks[warp];
+    const int64_t i0 = ((int64_t)blockIdx.x * kKnnWarps + warp) * 32;
+    if (i0 >= n) return;
+    const int64_t i = i0 + lane;
+    const bool valid = i < n;
+    const float4 p = valid ? sp4[i] : sp4[i0];
     KSmallest<K> S;
     // upper bound: the k nearest among the 2k neighbours in key order
     S.reset(k, INFINITY);
-    const int64_t w0 = i - k > 0 ? i - k : 0, w1 = i + k + 1 < n ? i + k + 1 : n;
-    for (int64_t j = w0; j < w1; ++j) {
-        if (j == i) continue;
-        const float4 q = sp4[j];
-        const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
-        S.offer(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    if (valid) {
+        const int64_t w0 = i - k > 0 ? i - k : 0, w1 = i + k + 1 < n ? i + k + 1 : n;
+        for (int64_t j = w0; j < w1; ++j) {
+            if (j == i) continue;
+            const float4 q = sp4[j];
+            const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+            S.offer(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        }
     }
-    // descend the octree with the bound as the initial search radius
-    // (inflated for the rounding of the squared distances)
-    const float R2 = S.worst * 1.000002f;
+    // descend with the bound as the initial search radius (inflated for the
+    // rounding of the squared distances); an invalid lane needs nothing
+    const float R2 = valid ? S.worst * 1.000002f : -1.0f;
     S.reset(k, R2);
     const float qlen = 1.0f / c.inv_q;  // length of one quantum
-    KnnNode stack[kKnnStack];
     int sp = 0;
-    stack[sp++] = KnnNode{0ull, 0u, (uint32_t)n, 0};
+    if (lane == 0) stack[0] = KnnNode{0ull, 0u, (uint32_t)n, 0};
+    sp = 1;
+    __syncwarp();
     while (sp > 0) {
         const KnnNode nd = stack[--sp];
+        __syncwarp();
         if (nd.b - nd.a <= (uint32_t)kKnnLeaf || nd.level == kKnnBits) {
             for (uint32_t j = nd.a; j < nd.b; ++j) {
-                if ((int64_t)j == i) continue;
-                const float4 q = sp4[j];
-                const float ddx = q.x - p.x, ddy = q.y - p.y, ddz = q.z - p.z;
-                S.offer(fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz)));
+                const float4 q = sp4[j];   // the same record for every lane
+                if (valid && (int64_t)j != i) {
+                    const float ddx = q.x - p.x, ddy = q.y - p.y, ddz = q.z - p.z;
+                    S.offer(fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz)));
+                }
             }
             continue;
         }
-        // children, nearest first: pushed in decreasing distance
         const int cl = nd.level + 1, shift = kKnnBits - cl;
         const float side = qlen * (float)(1u << shift);
+        // lane ch < 8 finds where child ch's run starts
+        uint32_t start = nd.a;
+        if (lane > 0 && lane < 8) start = lower_bound_u64(keys, nd.a, nd.b, (nd.prefix * 8 + lane) << (3 * shift));
+        // children in order, each with the smallest of the lanes' distances to
+        // its box (a quantum of margin on every side); kept if any lane needs it
         float cd[8];
         uint32_t ca[8], cb[8];
         int order[8], m = 0;
-        uint32_t lo = nd.a;
         for (int ch = 0; ch < 8; ++ch) {
+            const uint32_t lo = __shfl_sync(full, start, ch);
+            const uint32_t hi = ch == 7 ? nd.b : __shfl_sync(full, start, ch + 1);
+            if (hi <= lo) continue;
             const uint64_t pre = nd.prefix * 8 + ch;
-            const uint32_t hi = ch == 7 ? nd.b : lower_bound_u64(keys, lo, nd.b, (pre + 1) << (3 * shift));
-            if (hi > lo) {
-                // the child's box, with a quantum of margin on every side
-                const float bx = c.ox + qlen * (float)(compact3(pre) << shift) - qlen;
-                const float by = c.oy + qlen * (float)(compact3(pre >> 1) << shift) - qlen;
-                const float bz = c.oz + qlen * (float)(compact3(pre >> 2) << shift) - qlen;
-                const float ex = fmaxf(fmaxf(bx - p.x, p.x - (bx + side + 2.0f * qlen)), 0.0f);
-                const float ey = fmaxf(fmaxf(by - p.y, p.y - (by + side + 2.0f * qlen)), 0.0f);
-                const float ez = fmaxf(fmaxf(bz - p.z, p.z - (bz + side + 2.0f * qlen)), 0.0f);
-                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                if (d2 <= S.worst) {
-                    cd[m] = d2;
-                    ca[m] = lo;
-                    cb[m] = hi;
-                    order[m] = ch;
-                    ++m;
-                }
-            }
-            lo = hi;
+            const float bx = c.ox + qlen * (float)(compact3(pre) << shift) - qlen;
+            const float by = c.oy + qlen * (float)(compact3(pre >> 1) << shift) - qlen;
+            const float bz = c.oz + qlen * (float)(compact3(pre >> 2) << shift) - qlen;
+            const float ex = fmaxf(fmaxf(bx - p.x, p.x - (bx + side + 2.0f * qlen)), 0.0f);
+            const float ey = fmaxf(fmaxf(by - p.y, p.y - (by + side + 2.0f * qlen)), 0.0f);
+            const float ez = fmaxf(fmaxf(bz - p.z, p.z - (bz + side + 2.0f * qlen)), 0.0f);
+            const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            const bool need = valid && d2 <= S.worst;
+            if (!__any_sync(full, need)) continue;
+            float dmin = need ? d2 : INFINITY;
+            for (int o = 16; o; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(full, dmin, o));
+            cd[m] = dmin;
+            ca[m] = lo;
+            cb[m] = hi;
+            order[m] = ch;
+            ++m;
         }
         // insertion sort by decreasing distance, then push (nearest on top)
         for (int u = 1; u < m; ++u)
@@ -247,14 +273,16 @@ k_knn_query(const float4* sp4, const uint64_t* keys, int64_t n, int k, KnnCube c
                 uint32_t tb = cb[v]; cb[v] = cb[v - 1]; cb[v - 1] = tb;
                 int to = order[v]; order[v] = order[v - 1]; order[v - 1] = to;
             }
-        for (int u = 0; u < m; ++u) {
-            if (sp >= kKnnStack) {
-                atomicOr(err, 4u);  // cannot happen: at most 7 pending siblings per level
-                break;
-            }
-            stack[sp++] = KnnNode{nd.prefix * 8 + order[u], ca[u], cb[u], cl};
+        if (sp + m > kKnnStack) {
+            if (lane == 0) atomicOr(err, 4u);  // cannot happen: at most 7 pending siblings per level
+            break;
         }
+        if (lane == 0)
+            for (int u = 0; u < m; ++u) stack[sp + u] = KnnNode{nd.prefix * 8 + order[u], ca[u], cb[u], cl};
+        sp += m;
+        __syncwarp();
     }
+    if (!valid) return;
     if (S.cnt < k) {
         atomicOr(err, 2u);  // cannot happen: the bound's k particles are within the radius
         r_out[__float_as_uint(p.w)] = NAN;
@@ -324,8 +352,9 @@ extern "C" lens_status lens_smoothing_lengths(const float* xyz, int64_t n, int32
         radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, 3 * kKnnBits, base + o_tmp, s, &sk, &sv);
         k_knn_gather<<<(unsigned)G, TB, 0, s>>>(xyz, n, sv, sp);
         note_launch();
-        if (k <= 32) k_knn_query<32><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(sp, sk, n, k, c, r_sm, err);
-        else k_knn_query<kKnnMax><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(sp, sk, n, k, c, r_sm, err);
+        const unsigned qb = (unsigned)((n + 32 * kKnnWarps - 1) / (32 * kKnnWarps));
+        if (k <= 32) k_knn_query<32><<<qb, kKnnWarps * 32, 0, s>>>(sp, sk, n, k, c, r_sm, err);
+        else k_knn_query<kKnnMax><<<qb, kKnnWarps * 32, 0, s>>>(sp, sk, n, k, c, r_sm, err);
         note_launch();
         e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
