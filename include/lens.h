@@ -159,7 +159,9 @@ typedef struct lens_tree_info {
     int32_t group_rays;       /* current ray-group size (32 or 64) */
     int32_t walk;             /* current walk form: LENS_WALK_WARP, _PAIRS or _TRIOS */
     int32_t tile;             /* current near-field tile: LENS_TILE_STANDARD or LENS_TILE_LARGE */
-    int32_t reserved;
+    int32_t split_groups;     /* ray groups the last lens_shoot_rays_backward split into
+                                 slices (the heaviest groups of a recorded walk), 0 if none;
+                                 reading it synchronises the device */
 } lens_tree_info;
 
 /*

@@ -88,7 +88,7 @@ class _Info(ctypes.Structure):
                 ("n_big", ctypes.c_int64 * 8), ("depth", ctypes.c_int32 * 8),
                 ("root", (ctypes.c_double * 3) * 8), ("build_ms", (ctypes.c_double * 4) * 8),
                 ("group_rays", ctypes.c_int32), ("walk", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("split_groups", ctypes.c_int32)]
 
 
 def lib():
@@ -296,7 +296,8 @@ class Lens:
                     depth=list(inf.depth[:k]), root=[tuple(inf.root[i]) for i in range(k)],
                     build_ms=[tuple(inf.build_ms[i]) for i in range(k)], group_rays=inf.group_rays,
                     walk={WALK_WARP: "warp", WALK_PAIRS: "pairs", WALK_TRIOS: "trios"}.get(inf.walk, "default"),
-                    tile={TILE_STANDARD: "standard", TILE_LARGE: "large"}.get(inf.tile, "default"))
+                    tile={TILE_STANDARD: "standard", TILE_LARGE: "large"}.get(inf.tile, "default"),
+                    split_groups=inf.split_groups)
 
     def export(self, species: int = 0):
         """Host copies of one species' tree: nodes (n_nodes, 8), links

@@ -252,9 +252,9 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMalloc(err)"));
     e = cudaMemsetAsync(t->d_err, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMemsetAsync"));
-    e = lens_malloc((void**)&t->d_stats, 8 * sizeof(unsigned long long));
+    e = lens_malloc((void**)&t->d_stats, 9 * sizeof(unsigned long long));
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMalloc(stats)"));
-    e = cudaMemsetAsync(t->d_stats, 0, 8 * sizeof(unsigned long long), s);
+    e = cudaMemsetAsync(t->d_stats, 0, 9 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaMemsetAsync"));
     t->halos_host.assign(halos, halos + n_halos);
     t->n_halos = n_halos;
@@ -514,6 +514,10 @@ lens_status lens_tree_get_info(const lens_tree* t, lens_tree_info* info)
     info->group_rays = t->group_rays;
     info->walk = t->walk_mode;
     info->tile = t->tile ? LENS_TILE_LARGE : LENS_TILE_STANDARD;
+    uint32_t split[2] = {0, 0};
+    LENS_CUDA(cudaDeviceSynchronize());
+    LENS_CUDA(cudaMemcpy(split, t->d_stats + 8, sizeof(split), cudaMemcpyDeviceToHost));
+    info->split_groups = (int32_t)split[0];
     return LENS_OK;
 }
 

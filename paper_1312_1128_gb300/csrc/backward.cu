@@ -70,6 +70,13 @@ template <typename T> struct BackParams {
     uint32_t* counter;
     int* stack;
     uint32_t* err;
+    const uint32_t* order;  // heaviest-first order of the groups, or null
+    // split heavy groups (heavy_first_order): hdr {Kc, Hn} and Hn slice
+    // entries, or null.  Every slice walks the group's tree and takes every
+    // ns-th accepted cell, leaf particle and kept big-list entry: the
+    // gradients are sums of atomics, so a slice needs no partial buffer.
+    const uint32_t* heavy_hdr;
+    const uint32_t* heavy;
 };
 
 constexpr int kMaxGroup = 64;
@@ -175,6 +182,8 @@ template <int KIND, typename T> struct BackCtx {
     int nr;  // rays in the group
     v2_t<T> H;
     vec4_t<T> box;
+    int sl = 0, ns = 1;               // this item's slice of the group's work
+    int seq_f = 0, seq_n = 0, seq_b = 0;  // cells, leaf particles, kept big entries met so far
 
     LENS_DEV BackCtx(const BackParams<T>& p, BackShared<KIND, T>& s) : P(p), S(s) {}
 
@@ -268,7 +277,6 @@ template <int KIND, typename T>
 LENS_DEV void back_append_near(BackCtx<KIND, T>& C, int cnt, int first, int& nbuf, const vec4_t<T>* src0,
                                const vec4_t<T>* src1)
 {
-    const unsigned full = 0xffffffffu;
     int lane = threadIdx.x & 31;
     int tot;
     int off = warp_exclusive_scan(cnt, &tot);
@@ -278,13 +286,21 @@ LENS_DEV void back_append_near(BackCtx<KIND, T>& C, int cnt, int first, int& nbu
     S.rs_first[lane] = first;
     if (lane == 31) S.rs_off[32] = tot;
     __syncwarp();
-    for (int base = 0; base < tot; base += 32) {
+    // a slice takes particles i = i0, i0 + ns, ... (its share of the group's sequence)
+    int i0 = 0, cnt_s = tot;
+    if (C.ns > 1) {
+        i0 = (C.sl - C.seq_n % C.ns + C.ns) % C.ns;
+        cnt_s = tot > i0 ? (tot - i0 + C.ns - 1) / C.ns : 0;
+        C.seq_n += tot;
+    }
+    for (int base = 0; base < cnt_s; base += 32) {
         if (nbuf + 32 > kBackNear) {
             C.flush_near(nbuf);
             nbuf = 0;
         }
-        int i = base + lane;
-        if (i < tot) {
+        int j = base + lane;
+        if (j < cnt_s) {
+            int i = i0 + j * C.ns;
             int lo = 0, hi = 32;
             while (hi - lo > 1) {
                 int mid = (lo + hi) >> 1;
@@ -299,10 +315,9 @@ LENS_DEV void back_append_near(BackCtx<KIND, T>& C, int cnt, int first, int& nbu
             if constexpr (KIND == LENS_NFW) S.n1[nbuf + lane] = src1[p];
             S.npid[nbuf + lane] = p;
         }
-        nbuf += tot - base < 32 ? tot - base : 32;
+        nbuf += cnt_s - base < 32 ? cnt_s - base : 32;
         __syncwarp();
     }
-    (void)full;
 }
 
 // Same selection as the forward's big-list append (two-level support boxes,
@@ -368,6 +383,12 @@ LENS_DEV void back_append_big(BackCtx<KIND, T>& C, bool has, int v, int z, int w
                 }
             }
             unsigned kb = __ballot_sync(full, keep);
+            if (C.ns > 1) {
+                const int q = C.seq_b + __popc(kb & ((1u << lane) - 1u));
+                C.seq_b += __popc(kb);
+                keep = keep && q % C.ns == C.sl;
+                kb = __ballot_sync(full, keep);
+            }
             if (keep) {
                 int slot = nbuf + __popc(kb & ((1u << lane) - 1u));
                 S.b0[slot] = q0;
@@ -391,11 +412,30 @@ back_kernel(BackParams<T> P)
     int* stack = P.stack + ((int64_t)blockIdx.x * kWalkWarps + warp) * kStackCap;
     BackCtx<KIND, T> C(P, S);
 
+    uint32_t Kc = 0, Hn = 0;
+    if (P.heavy_hdr) {
+        Kc = P.heavy_hdr[0];
+        Hn = P.heavy_hdr[1];
+    }
+    const int64_t n_items = P.n_groups - (int64_t)Kc + (int64_t)Hn;
     for (;;) {
-        uint32_t g = 0;
-        if (lane == 0) g = atomicAdd(P.counter, 1u);
-        g = __shfl_sync(full, g, 0);
-        if ((int64_t)g >= P.n_groups) break;
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(P.counter, 1u);
+        item = __shfl_sync(full, item, 0);
+        if ((int64_t)item >= n_items) break;
+        uint32_t g;
+        C.sl = 0;
+        C.ns = 1;
+        if (item < Hn) {
+            const uint32_t e = P.heavy[item];
+            g = P.order[e >> 10];
+            C.sl = (int)((e >> 5) & 31u);
+            C.ns = (int)(e & 31u) + 1;
+        } else {
+            const uint32_t j = item - Hn + Kc;
+            g = P.order ? P.order[j] : j;
+        }
+        C.seq_f = C.seq_n = C.seq_b = 0;
         C.H = P.gH[g];
         C.box = P.gbox[g];
         uint2 rg = P.grange[g];
@@ -444,7 +484,14 @@ back_kernel(BackParams<T> P)
                         open = !acc && !leaf;
                     }
                     unsigned ball = __ballot_sync(full, acc);
-                    if (acc) {
+                    bool take = acc;  // this slice's share of the accepted cells
+                    if (C.ns > 1) {
+                        const int q = C.seq_f + __popc(ball & ((1u << lane) - 1u));
+                        C.seq_f += __popc(ball);
+                        take = acc && q % C.ns == C.sl;
+                        ball = __ballot_sync(full, take);
+                    }
+                    if (take) {
                         int pos = nf + __popc(ball & ((1u << lane) - 1u));
                         v2_t<T> Q = P.nodeB[v];
                         S.fdx[pos] = dxv;
@@ -479,7 +526,7 @@ back_kernel(BackParams<T> P)
         }
 
         // analytic halos: lanes own rays; reduce each halo's gradient over the warp
-        if (P.n_halos > 0 && P.ghalo) {
+        if (P.n_halos > 0 && P.ghalo && C.sl == 0) {
             for (int h = 0; h < P.n_halos; ++h) {
                 const HaloDev& hd = P.halos[h];
                 T hx = (T)((double)C.H.x - hd.x), hy = (T)((double)C.H.y - hd.y);
@@ -679,6 +726,12 @@ static lens_status backward_typed(lens_tree* t, double ox, double oy, const void
     LENS_TRY(upload_batches(t, 1, off, orig, s, &plan));
     if (32 * plan.R > kMaxGroup) return lens_set_error(LENS_ERR_INTERNAL, "group larger than the adjoint buffer");
     LENS_TRY(enqueue_groups<T>(t, plan, dx, dy, dtype, s));
+    // the forward call on these rays recorded its groups' work: heaviest first
+    RayKey key;
+    key.dx = dx; key.dy = dy; key.n = n; key.dtype = dtype; key.R = plan.R; key.ox = ox; key.oy = oy;
+    // (a quarter of one warp's share for a launch of about 16 warps per SM)
+    const HeavyPlan hp = (flags & LENS_DIRECT) ? HeavyPlan{}
+                                               : heavy_first_order<T>(t, plan, key, (int64_t)t->num_sms * 16, s);
     Layout Lay = make_layout(t->ray_cap, t->batch_cap, max_slots(t));
     char* base = (char*)t->ray_scratch.ptr;
     BackParams<T> P{};
@@ -690,6 +743,11 @@ static lens_status backward_typed(lens_tree* t, double ox, double oy, const void
     P.n_groups = (int64_t)plan.ng;
     P.stack = (int*)(base + Lay.stack);
     P.err = t->d_err;
+    P.order = hp.order;
+    P.heavy_hdr = hp.hdr;
+    P.heavy = hp.table;
+    if (hp.hdr) LENS_CUDA(cudaMemcpyAsync(t->d_stats + 8, hp.hdr, 2 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    else LENS_CUDA(cudaMemsetAsync(t->d_stats + 8, 0, 2 * sizeof(uint32_t), s));
     P.ga1 = (const T*)g[0];
     P.ga2 = (const T*)g[1];
     uint32_t* counter = (uint32_t*)(base + Lay.counter);

@@ -89,8 +89,15 @@ struct lens_tree {
     int device = 0;
     long long wait_cycles = 4000000000ll;   // bound of a wait between cooperating warps (~2 s at 2 GHz)
     std::vector<lens::GraphEntry*> graphs;
-    unsigned long long* d_stats = nullptr;  // 8 walk counters (LENS_COUNT)
+    unsigned long long* d_stats = nullptr;  // 8 walk counters (LENS_COUNT), then the last adjoint's split {Kc, Hn}
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // LENS_TIMING: start, grouped, walked
+    // the rays whose per-group work the scratch holds (walk_shared.cuh), as
+    // an opaque copy of their identity: pointers, size, dtype, origin, R
+    const void* cost_dx = nullptr;
+    const void* cost_dy = nullptr;
+    int64_t cost_n = -1;
+    int cost_dtype = -1, cost_R = 0;
+    double cost_ox = 0, cost_oy = 0;
     bool timed = false;
     void* noalloc_scratch = nullptr;        // device address of the no-alloc scratch array (walk.cu)
     void* amr_ws = nullptr;                 // image-finding workspace (amr.cu), kept between calls

@@ -241,7 +241,8 @@ walk_kernel(WalkParams<T> P)
         if (lane == 0) item = atomicAdd(P.counter, 1u);
         item = __shfl_sync(full, item, 0);
         if ((int64_t)item >= P.n_groups * NS) break;
-        const uint32_t g = item / (uint32_t)NS, slice = item % (uint32_t)NS;
+        const uint32_t slice = item % (uint32_t)NS;
+        const uint32_t g = P.order ? P.order[item / (uint32_t)NS] : item / (uint32_t)NS;
         C.H = P.gH[g];
         C.box = P.gbox[g];
         uint2 rg = P.grange[g];
@@ -283,6 +284,7 @@ walk_kernel(WalkParams<T> P)
             }
         }
         if (P.n_halos > 0 && slice == 0) C.halos();
+        if (P.gcost && lane == 0) P.gcost[g] += (uint32_t)(c_vis + c_acc + c_near + c_bigk);
         if (P.stats && lane == 0) {
             unsigned long long nr = rg.y;
             if (slice == 0) atomicAdd(&P.stats[0], 1ull);
@@ -378,6 +380,7 @@ lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s)
     int64_t nn = std::max(n, t->ray_cap), bb = std::max(nb, t->batch_cap);
     Layout L = make_layout(nn, bb, max_slots(t));
     free_graphs(t);  // captured graphs point into the old scratch
+    t->cost_n = -1;  // so does the work record
     if (t->ray_scratch.ptr) cudaFreeAsync(t->ray_scratch.ptr, s);
     t->ray_scratch.ptr = nullptr;
     t->ray_cap = t->batch_cap = 0;
@@ -464,6 +467,8 @@ lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const
     plan->nb = nb;
     plan->ng = ng;
     plan->R = R;
+    plan->ox = nb == 1 ? h_orig[0] : 0.0;
+    plan->oy = nb == 1 ? h_orig[1] : 0.0;
     return LENS_OK;
 }
 
@@ -516,6 +521,8 @@ lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, 
 template lens_status enqueue_groups<float>(lens_tree*, const ShootPlan&, const void*, const void*, int, cudaStream_t);
 template lens_status enqueue_groups<double>(lens_tree*, const ShootPlan&, const void*, const void*, int, cudaStream_t);
 
+void set_cost_key(lens_tree* t, const RayKey& k);
+
 // Enqueue the kernels of one shoot call (no allocation, no host sync: safe
 // to capture into a CUDA graph).
 template <typename T>
@@ -547,6 +554,14 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
         LENS_CUDA(cudaEventRecord(t->ev[0], s));
     }
     if (n > 0) LENS_TRY(enqueue_groups<T>(t, plan, dx, dy, dtype, s));
+    // a tree walk of one batch records its groups' work, and takes them
+    // heaviest first when these rays were walked before on this tree
+    RayKey key;
+    key.dx = dx; key.dy = dy; key.n = n; key.dtype = dtype; key.R = R; key.ox = plan.ox; key.oy = plan.oy;
+    const bool record = n > 0 && nb == 1 && !(flags & LENS_DIRECT);
+    const uint32_t* order = record ? heavy_first_order<T>(t, plan, key, 0, s).order : nullptr;
+    uint32_t* gcost = record ? (uint32_t*)(base + L.gcost) : nullptr;
+    if (gcost) LENS_CUDA(cudaMemsetAsync(gcost, 0, ng * sizeof(uint32_t), s));
 
     if (timing) LENS_CUDA(cudaEventRecord(t->ev[1], s));
     WalkParams<T> P{};
@@ -556,6 +571,8 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
     P.stack = stack;
     P.err = t->d_err;
     P.wait_cycles = t->wait_cycles;
+    P.order = order;
+    P.gcost = gcost;
     for (int q = 0; q < 5; ++q) P.out[q] = (T*)out[q];
     const bool ao = (flags & LENS_ALPHA_ONLY) != 0;
     const bool direct = (flags & LENS_DIRECT) != 0;
@@ -623,6 +640,7 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
         LENS_CUDA(cudaEventRecord(t->ev[2], s));
         t->timed = true;
     }
+    if (record) set_cost_key(t, key);
     LENS_CUDA(cudaGetLastError());
     return LENS_OK;
 }
@@ -644,6 +662,112 @@ lens_status shoot(lens_tree* t, int64_t nb, const int64_t* h_off, const double* 
 
 // Scratch views shared with the backward walk.
 void* scratch_base(lens_tree* t) { return t->ray_scratch.ptr; }
+
+__global__ void k_cost_keys(uint32_t ng, const uint32_t* gcost, uint32_t* keys, uint32_t* vals,
+                            unsigned long long* total)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t c = g < ng ? gcost[g] : 0u;
+    if (g < ng) {
+        keys[g] = ~c;  // ascending sort of the complement: heaviest first, ties in group order
+        vals[g] = g;
+    }
+    unsigned long long w = c;
+    for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, w);
+}
+
+// Slices of the heaviest groups (one block of kHeavyGroups threads; thread
+// i owns the group at position i of the order).  The slice counts are
+// non-increasing along the order, so the split groups are its first Kc.
+__global__ void __launch_bounds__(kHeavyGroups) k_heavy_plan(uint32_t ng, const uint32_t* sorted_keys,
+                                                             unsigned long long n_warps, uint32_t* hdr,
+                                                             uint32_t* table)
+{
+    __shared__ uint32_t wsum[kHeavyGroups / 32];
+    const uint32_t i = threadIdx.x, lane = i & 31, warp = i >> 5;
+    const unsigned long long total = *(const unsigned long long*)(hdr + 8);
+    unsigned long long cap = total / (4ull * n_warps);  // a quarter of one warp's share
+    if (cap < 1) cap = 1;
+    uint32_t v = 0;  // slices of a split group, 0 for a whole one
+    if (i < ng) {
+        unsigned long long q = ((unsigned long long)(~sorted_keys[i]) + cap - 1) / cap;
+        if (q > 1) v = q > 32 ? 32u : (uint32_t)q;
+    }
+    uint32_t x = v;  // inclusive scan over the block
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    const int kc = __syncthreads_count(v > 0);
+    if (warp == 0) {
+        uint32_t w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= (uint32_t)o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t first = x - v + (warp ? wsum[warp - 1] : 0u);
+    for (uint32_t k = 0; k < v; ++k) table[first + k] = (i << 10) | (k << 5) | (v - 1);
+    if (i == 0) {
+        hdr[0] = (uint32_t)kc;
+        hdr[1] = wsum[kHeavyGroups / 32 - 1];
+    }
+}
+
+static bool cost_key_matches(const lens_tree* t, const RayKey& k)
+{
+    return t->cost_dx == k.dx && t->cost_dy == k.dy && t->cost_n == k.n && t->cost_dtype == k.dtype &&
+           t->cost_R == k.R && t->cost_ox == k.ox && t->cost_oy == k.oy;
+}
+
+void set_cost_key(lens_tree* t, const RayKey& k)
+{
+    t->cost_dx = k.dx;
+    t->cost_dy = k.dy;
+    t->cost_n = k.n;
+    t->cost_dtype = k.dtype;
+    t->cost_R = k.R;
+    t->cost_ox = k.ox;
+    t->cost_oy = k.oy;
+}
+
+template <typename T>
+HeavyPlan heavy_first_order(lens_tree* t, const ShootPlan& plan, const RayKey& key, int64_t n_warps,
+                            cudaStream_t s)
+{
+    HeavyPlan hp;
+    if (plan.nb != 1 || plan.ng < 2 || !cost_key_matches(t, key)) return hp;
+    Layout L = make_layout(t->ray_cap, t->batch_cap, max_slots(t));
+    char* base = (char*)t->ray_scratch.ptr;
+    uint32_t* k0 = (uint32_t*)(base + L.k0);
+    uint32_t* k1 = (uint32_t*)(base + L.k1);
+    uint32_t* v0 = (uint32_t*)(base + L.v0);
+    uint32_t* v1 = (uint32_t*)(base + L.v1);
+    uint32_t* hdr = (uint32_t*)(base + L.heavy);
+    uint32_t* table = hdr + 16;
+    const uint32_t ng = (uint32_t)plan.ng;
+    if (cudaMemsetAsync(hdr, 0, 64, s) != cudaSuccess) return hp;
+    {
+        k_cost_keys<<<grid_for(ng, 256), 256, 0, s>>>(ng, (const uint32_t*)(base + L.gcost), k0, v0,
+                                                       (unsigned long long*)(hdr + 8));
+        note_launch();
+    }
+    uint32_t *sk, *sv;
+    radix_sort_pairs<uint32_t>(k0, v0, k1, v1, ng, 0, 32, base + L.tmp, s, &sk, &sv);
+    hp.order = sv;
+    if (n_warps > 0) {
+        { k_heavy_plan<<<1, kHeavyGroups, 0, s>>>(ng, sk, (unsigned long long)n_warps, hdr, table); note_launch(); }
+        hp.hdr = hdr;
+        hp.table = table;
+    }
+    return hp;
+}
+template HeavyPlan heavy_first_order<float>(lens_tree*, const ShootPlan&, const RayKey&, int64_t, cudaStream_t);
+template HeavyPlan heavy_first_order<double>(lens_tree*, const ShootPlan&, const RayKey&, int64_t, cudaStream_t);
 
 }  // namespace lens
 

@@ -44,6 +44,10 @@ template <typename T> struct WalkParams {
     int n_slices;
     int64_t split_n;
     T* split;
+    // group order and work record (walk_shared.cuh): item g walks group
+    // order[g] (identity if null); the walk adds each group's work to gcost[g]
+    const uint32_t* order;
+    uint32_t* gcost;
 };
 
 // The shared-memory tiles of the near field: TILE 0 holds kNearCap leaf

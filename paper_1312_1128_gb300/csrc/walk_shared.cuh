@@ -44,8 +44,12 @@ LENS_DEV bool box_reaches_group(const vec4_t<T>& b, const v2_t<T>& H, const vec4
 
 struct Layout {
     size_t boff, borig, gfirst, bbox, k0, k1, v0, v1, tmp, rl, ridx, gH, gbox, grange, counter,
-        stack, split, total;
+        stack, split, gcost, heavy, total;
 };
+
+// Split heavy groups (heavy_first_order): at most kHeavyGroups groups, each
+// in at most 32 slices; the plan's table holds one entry per slice.
+constexpr int kHeavyGroups = 1024, kHeavyItems = kHeavyGroups * 32;
 
 // Partial sums of a direct sum split over particle slices: room for 32 rays
 // per warp slot of the device, five outputs, FP64 (see split_slices).
@@ -74,6 +78,8 @@ inline Layout make_layout(int64_t n, int64_t nb, int64_t slots)
     L.counter = o; o += al(64 * sizeof(uint32_t));
     L.stack = o; o += al((size_t)slots * kStackCap * sizeof(int));
     L.split = o; o += al(split_values(slots) * 5 * sizeof(double));
+    L.gcost = o; o += al(ng * sizeof(uint32_t));
+    L.heavy = o; o += al(64 + (size_t)kHeavyItems * sizeof(uint32_t));
     L.total = o;
     return L;
 }
@@ -86,7 +92,42 @@ struct ShootPlan {
     int64_t n = 0, nb = 0;
     uint64_t ng = 0;
     int R = 1;
+    double ox = 0, oy = 0;  // the origin of a single batch
 };
+
+// Work order of the ray groups: a tree walk records every group's work
+// (boxes visited + cells + leaf particles + kept big-list entries) in the
+// scratch; a later walk over the same rays (the adjoint of a forward call, a
+// repeated shot) takes the groups heaviest first, so that a heavy group (rays
+// in the densest region) does not run alone at the end of the launch.
+struct RayKey {
+    const void* dx = nullptr;
+    const void* dy = nullptr;
+    int64_t n = -1;
+    int dtype = -1, R = 0;
+    double ox = 0, oy = 0;
+    bool operator==(const RayKey& o) const
+    {
+        return dx == o.dx && dy == o.dy && n == o.n && dtype == o.dtype && R == o.R && ox == o.ox && oy == o.oy;
+    }
+};
+// The heaviest-first order of the plan's groups if the tree's recorded costs
+// belong to these rays (order null otherwise); uses the ray sort's buffers.
+// With n_warps > 0 it also splits the heaviest groups for a launch of that
+// many warps: a group whose work exceeds a quarter of one warp's share gets
+// ns = ceil(work / quarter share) slices (at most 32).  hdr[0] = Kc (groups
+// split; they lead the order), hdr[1] = Hn (their slices); table[k] for
+// k < Hn = (i << 10) | (slice << 5) | (ns - 1), i the group's position in
+// the order.  Work item k < Hn is that slice; item k >= Hn walks the whole
+// group order[k - Hn + Kc].
+struct HeavyPlan {
+    const uint32_t* order = nullptr;
+    const uint32_t* hdr = nullptr;
+    const uint32_t* table = nullptr;
+};
+template <typename T>
+HeavyPlan heavy_first_order(lens_tree* t, const ShootPlan& plan, const RayKey& key, int64_t n_warps,
+                            cudaStream_t s);
 
 lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s);
 lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig,

@@ -168,6 +168,7 @@ LENS_DEV void ws_produce(const WalkParams<T>& P, WsPair<KIND, T, CONS>& W, int* 
             C.handoff(kWsStop);
             return;
         }
+        if (P.order) g = P.order[g];
         C.g = (int)g;
         C.H = P.gH[g];
         C.box = P.gbox[g];
@@ -175,6 +176,7 @@ LENS_DEV void ws_produce(const WalkParams<T>& P, WsPair<KIND, T, CONS>& W, int* 
         traverse(C, stack, c_vis, c_acc, c_near, c_bigs, c_bigk);
         C.handoff(kWsLast);
         if (!C.alive) return;
+        if (P.gcost && lane == 0) P.gcost[g] += (uint32_t)(c_vis + c_acc + c_near + c_bigk);
         if (P.stats && lane == 0) {
             unsigned long long nr = P.grange[g].y;
             atomicAdd(&P.stats[0], 1ull);

@@ -16,7 +16,10 @@ Eq. lens_eq):
   (every ray inside a support meets the full profile in the walk);
 * analytic halos of every kind: dL/d(m or r_E, x, y, p0, p1) against the
   oracle in direct and tree mode;
-* through torch.autograd, including a rebuild after an in-place update.
+* through torch.autograd, including a rebuild after an in-place update;
+* after a forward call on the same rays, the adjoint splits the heaviest
+  ray groups into slices: particle, cell and halo gradients equal those of
+  an unsplit adjoint up to the order of the FP64 atomic sums.
 """
 import numpy as np
 import pytest
@@ -336,3 +339,39 @@ def test_autograd_function_and_rebuild():
     torch.testing.assert_close(alpha2.detach(), 2 * alpha.detach(), rtol=1e-5, atol=1e-7)
     fresh.close()
     lens.close()
+
+
+def _split_case(lens, dx, dy, g1, g2, n_halos, forward_first):
+    if forward_first:
+        lens.shoot(dx, dy, flags=L.ALPHA_ONLY)  # records every group's work
+    gh = torch.zeros(n_halos, 5, dtype=torch.float64, device="cuda") if n_halos else None
+    (grad,) = lens.backward(dx, dy, g1, g2, g_halos=gh)
+    split = lens.info()["split_groups"]
+    return grad.double().cpu().numpy(), (gh.cpu().numpy() if n_halos else None), split
+
+
+@pytest.mark.parametrize("n_part,grid,theta", [(20000, 128, 0.3), (100_000, 1000, 0.3)])
+def test_split_heavy_groups_same_gradient(n_part, grid, theta):
+    """Few groups (128^2 rays: every group split, up to 32 slices each) and
+    the lens-fit size (1000^2 rays, 1e5 particles: only the groups over the
+    NFW cusp split), with two analytic halos (taken once per group)."""
+    parts = lensgen.nfw_particles(n_part, 91, fixed_sigma=0.01)
+    rx, ry = lensgen.grid_rays(grid, -1.0, 1.0, dtype=np.float32)
+    g = lensgen.rng(92)
+    g1 = cu((0.01 * g.standard_normal(rx.size)).astype(np.float32))
+    g2 = cu((0.01 * g.standard_normal(rx.size)).astype(np.float32))
+    halos = [L.Halo.gauss(0.05, -0.02, 0.05, 0.1, 3.0), L.Halo.nfw(-0.1, 0.04, 0.05, 0.08, 0.4)]
+    dx, dy = cu(rx), cu(ry)
+    res = []
+    for forward_first in (False, True):
+        lens = L.Lens([L.Species.gauss(cu(parts), 3.0)], halos, theta=theta)
+        res.append(_split_case(lens, dx, dy, g1, g2, len(halos), forward_first))
+        lens.close()
+    (ref, href, s0), (got, hgot, s1) = res
+    print(f"split groups: {s0} without a recorded walk, {s1} after the forward call")
+    assert s0 == 0 and s1 > 0
+    for k in range(4):
+        scale = np.abs(ref[:, k]).max()
+        err = np.abs(got[:, k] - ref[:, k]).max()
+        assert err <= 1e-6 * scale, (k, err, scale)
+    np.testing.assert_allclose(hgot, href, rtol=1e-10, atol=1e-12 * np.abs(href).max())
