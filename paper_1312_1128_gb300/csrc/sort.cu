@@ -124,10 +124,16 @@ __global__ void radix_hist_kernel(const K* keys, int64_t n, int shift, uint32_t*
     __shared__ uint32_t cnt[kRadix];
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) cnt[d] = 0;
     __syncthreads();
+    const int lane = threadIdx.x & 31;
     int64_t base = (int64_t)blockIdx.x * kSortTile;
     for (int r = 0; r < kSortItems; ++r) {
         int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
-        if (idx < n) atomicAdd(&cnt[(uint32_t)(keys[idx] >> shift) & 0xffu], 1u);
+        const bool valid = idx < n;
+        const uint32_t d = valid ? ((uint32_t)(keys[idx] >> shift) & 0xffu) : 0xffffffffu;
+        // one shared atomic per distinct digit of the warp (the high digits of
+        // Morton keys are few: lanes with equal digits would serialise)
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
@@ -153,120 +159,81 @@ __global__ void __launch_bounds__(kScanThreads) radix_colscan_kernel(uint32_t* h
     if (threadIdx.x == 0) digit_tot[blockIdx.x] = run;
 }
 
-// Stable scatter: element (block, r, t) precedes (block, r', t') iff
-// (r, t) < (r', t'), i.e. global index order, and equal digits keep it.  The
-// tile is first ordered by digit in shared memory (each element at its
-// digit's start in the tile plus its stable rank among the tile's equal
-// digits), then written out in that order: a digit's run of the tile goes to
-// consecutive output positions, so the stores coalesce.
+// Stable scatter.  Warp w of the block holds elements [w, w + 1) * 32 *
+// kSortItems of the tile, round r its 32 elements from r * 32, so (warp,
+// round, lane) is the elements' index order.  Each warp ranks its elements
+// among its own equal digits (match_any per round, running counts in a
+// warp-private shared histogram); one scan over (digit, warp) then gives each
+// element its place in the tile ordered by digit, equal digits in index
+// order.  The ordered tile is written out so that a digit's run of the tile
+// goes to consecutive output positions and the stores coalesce.
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const K* kin, const uint32_t* vin, K* kout,
                                                                      uint32_t* vout, int64_t n, int shift,
                                                                      const uint32_t* offs, const uint32_t* digit_tot,
                                                                      int64_t nblocks)
 {
+    constexpr int kWarps = kSortThreads / 32;
+    static_assert(kSortThreads == kRadix && kSortThreads == kScanThreads, "one thread per digit");
     __shared__ K sk[kSortTile];
     __shared__ uint32_t sv[kSortTile];
-    __shared__ uint32_t wcnt[kSortThreads / 32][kRadix];
-    __shared__ uint32_t run[kRadix];
-    __shared__ uint32_t tstart[kRadix];
-    __shared__ uint32_t base_off[kRadix];
+    __shared__ uint32_t wcnt[kWarps][kRadix];  // a warp's digit counts, then its start within the digit's run
+    __shared__ uint32_t tstart[kRadix];        // the digit's start in the ordered tile
+    __shared__ uint32_t base_off[kRadix];      // the digit's first output position for this tile
+    __shared__ uint32_t scan_tot;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
     const int tile_n = (int)(n - base < kSortTile ? n - base : kSortTile);
-    // the digits' global starts (an exclusive scan of the digit totals, by one
-    // warp) plus this tile's place among the tiles of each digit
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
-        run[d] = 0;
-        tstart[d] = 0;
-        base_off[d] = digit_tot[d];
-    }
+    const int d_own = threadIdx.x;  // the digit this thread scans
+    for (int w = 0; w < kWarps; ++w) wcnt[w][d_own] = 0;
+    // the digits' global starts plus this tile's place among the tiles of each digit
+    const uint32_t gstart = block_exclusive_scan(digit_tot[d_own], &scan_tot);
+    base_off[d_own] = gstart + offs[(int64_t)d_own * nblocks + blockIdx.x];
     __syncthreads();
-    if (threadIdx.x < 32) {
-        constexpr int per = kRadix / 32;
-        uint32_t c[per], tot = 0;
+    K key[kSortItems];
+    uint32_t val[kSortItems], lrank[kSortItems];
 #pragma unroll
-        for (int q = 0; q < per; ++q) {
-            c[q] = base_off[lane * per + q];
-            tot += c[q];
-        }
-        uint32_t incl = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        uint32_t acc = incl - tot;
-#pragma unroll
-        for (int q = 0; q < per; ++q) {
-            base_off[lane * per + q] = acc + offs[(int64_t)(lane * per + q) * nblocks + blockIdx.x];
-            acc += c[q];
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < tile_n; e += kSortThreads)
-        atomicAdd(&tstart[(uint32_t)(kin[base + e] >> shift) & 0xffu], 1u);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        // 256 digits: each lane scans its 8 consecutive counts, then the lanes' totals
-        constexpr int per = kRadix / 32;
-        uint32_t c[per], tot = 0;
-#pragma unroll
-        for (int q = 0; q < per; ++q) {
-            c[q] = tstart[lane * per + q];
-            tot += c[q];
-        }
-        uint32_t incl = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        uint32_t acc = incl - tot;
-#pragma unroll
-        for (int q = 0; q < per; ++q) {
-            tstart[lane * per + q] = acc;
-            acc += c[q];
-        }
-    }
-    __syncthreads();
-    // stable ranks, 256 elements at a time, placed in shared memory
     for (int r = 0; r < kSortItems; ++r) {
-        for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads)
-            (&wcnt[0][0])[i] = 0;
-        __syncthreads();
-        const int e = r * kSortThreads + threadIdx.x;
+        const int e = wid * 32 * kSortItems + r * 32 + lane;
         const bool valid = e < tile_n;
-        const K key = valid ? kin[base + e] : K(0);
-        const uint32_t d = valid ? ((uint32_t)(key >> shift) & 0xffu) : 0xffffffffu;
+        key[r] = valid ? kin[base + e] : K(0);
+        val[r] = valid ? vin[base + e] : 0u;
+        const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & 0xffu) : 0xffffffffu;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-        if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
-        __syncthreads();
-        for (int dd = threadIdx.x; dd < kRadix; dd += kSortThreads) {
-            uint32_t s = run[dd];
-            for (int w = 0; w < kSortThreads / 32; ++w) {
-                const uint32_t t = wcnt[w][dd];
-                wcnt[w][dd] = s;
-                s += t;
-            }
-            run[dd] = s;
-        }
-        __syncthreads();
-        if (valid) {
-            const uint32_t tp = tstart[d] + wcnt[wid][d] + rank;
-            sk[tp] = key;
-            sv[tp] = vin[base + e];
-        }
-        __syncthreads();
+        const uint32_t prev = valid ? wcnt[wid][d] : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[wid][d] = prev + __popc(peers);
+        __syncwarp();
+        lrank[r] = prev + __popc(peers & ((1u << lane) - 1u));
     }
+    __syncthreads();
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = wcnt[w][d_own];
+        wcnt[w][d_own] = tot;
+        tot += c;
+    }
+    tstart[d_own] = block_exclusive_scan(tot, &scan_tot);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int e = wid * 32 * kSortItems + r * 32 + lane;
+        if (e < tile_n) {
+            const uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
+            const uint32_t tp = tstart[d] + wcnt[wid][d] + lrank[r];
+            sk[tp] = key[r];
+            sv[tp] = val[r];
+        }
+    }
+    __syncthreads();
     // out in digit order: element e of the ordered tile has digit d and goes to
     // base_off[d] + (e - tstart[d])
     for (int e = threadIdx.x; e < tile_n; e += kSortThreads) {
-        const K key = sk[e];
-        const uint32_t d = (uint32_t)(key >> shift) & 0xffu;
+        const K k = sk[e];
+        const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
         const uint32_t pos = base_off[d] + (uint32_t)e - tstart[d];
-        kout[pos] = key;
+        kout[pos] = k;
         vout[pos] = sv[e];
     }
 }

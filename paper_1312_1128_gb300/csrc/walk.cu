@@ -220,6 +220,121 @@ __global__ void k_groups(int64_t n_groups, const int64_t* boff, const uint32_t* 
     }
 }
 
+// One batch of FP32 offsets (the common case) needs no FP64 on the grouping
+// path (FP64 runs at 1/64 of the FP32 rate here): the offsets' bounding box
+// from order-preserving uint32 images of the floats, 32-bit Morton keys of
+// the offsets (relative positions do not depend on the origin), and, when
+// the origin is zero, groups anchored at H = 0 with l = the offsets
+// themselves -- what the FP64 path computes in that case.
+__device__ __forceinline__ uint32_t flt_to_ordered(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_flt(uint32_t u)
+{
+    u = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    return __uint_as_float(u);
+}
+
+// bb = {min x, min y, max x, max y} as ordered images; the caller sets the
+// minima to 0xffffffff and the maxima to 0 first.
+__global__ void __launch_bounds__(256) k_ray_bbox32(const float* dx, const float* dy, int64_t n, uint32_t* bb)
+{
+    __shared__ uint32_t red[4][8];
+    const unsigned full = 0xffffffffu;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t v[4] = {~0u, ~0u, 0u, 0u};
+    if (i < n) {
+        v[0] = v[2] = flt_to_ordered(dx[i]);
+        v[1] = v[3] = flt_to_ordered(dy[i]);
+    }
+    for (int o = 16; o; o >>= 1) {
+        v[0] = min(v[0], __shfl_xor_sync(full, v[0], o));
+        v[1] = min(v[1], __shfl_xor_sync(full, v[1], o));
+        v[2] = max(v[2], __shfl_xor_sync(full, v[2], o));
+        v[3] = max(v[3], __shfl_xor_sync(full, v[3], o));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 4; ++q) red[q][w] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            v[0] = min(v[0], red[0][k]);
+            v[1] = min(v[1], red[1][k]);
+            v[2] = max(v[2], red[2][k]);
+            v[3] = max(v[3], red[3][k]);
+        }
+        atomicMin(&bb[0], v[0]);
+        atomicMin(&bb[1], v[1]);
+        atomicMax(&bb[2], v[2]);
+        atomicMax(&bb[3], v[3]);
+    }
+}
+
+__global__ void k_ray_keys32(const float* dx, const float* dy, int64_t n, const uint32_t* bb, uint32_t* keys,
+                             uint32_t* vals)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x0 = ordered_to_flt(bb[0]), y0 = ordered_to_flt(bb[1]);
+    const float ext = fmaxf(ordered_to_flt(bb[2]) - x0, ordered_to_flt(bb[3]) - y0);
+    const float inv = ext > 0.f ? 65535.99f / ext : 0.f;
+    const uint32_t qx = (uint32_t)fminf(fmaxf((dx[i] - x0) * inv, 0.f), 65535.f);
+    const uint32_t qy = (uint32_t)fminf(fmaxf((dy[i] - y0) * inv, 0.f), 65535.f);
+    keys[i] = spread16(qx) | (spread16(qy) << 1);
+    vals[i] = (uint32_t)i;
+}
+
+// Groups of one batch of FP32 offsets at origin zero: every ray is exact in
+// T, so H = 0 and l = the offset (as k_groups then has it).
+template <typename T, int R>
+__global__ void k_groups32(int64_t n_groups, int64_t n, const float* dx, const float* dy, const uint32_t* svals,
+                           v2_t<T>* gH, vec4_t<T>* gbox, uint2* grange, v2_t<T>* ray_l, uint32_t* ray_idx)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= n_groups) return;
+    const int64_t first = g * (32 * R);
+    const int count = (int)(n - first < 32 * R ? n - first : 32 * R);
+    T lxmin = (T)INFINITY, lxmax = (T)-INFINITY, lymin = (T)INFINITY, lymax = (T)-INFINITY;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int k = r * 32 + lane;
+        if (k >= count) continue;
+        const uint32_t idx = svals[first + k];
+        v2_t<T> l;
+        l.x = (T)dx[idx];
+        l.y = (T)dy[idx];
+        lxmin = fmin(lxmin, l.x); lxmax = fmax(lxmax, l.x);
+        lymin = fmin(lymin, l.y); lymax = fmax(lymax, l.y);
+        ray_l[first + k] = l;
+        ray_idx[first + k] = idx;
+    }
+    for (int o = 16; o; o >>= 1) {
+        lxmin = fmin(lxmin, __shfl_xor_sync(full, lxmin, o));
+        lxmax = fmax(lxmax, __shfl_xor_sync(full, lxmax, o));
+        lymin = fmin(lymin, __shfl_xor_sync(full, lymin, o));
+        lymax = fmax(lymax, __shfl_xor_sync(full, lymax, o));
+    }
+    if (lane == 0) {
+        T cx = T(0.5) * (lxmin + lxmax), cy = T(0.5) * (lymin + lymax);
+        T hx = fmax(lxmax - cx, cx - lxmin), hy = fmax(lymax - cy, cy - lymin);
+        hx = hx * T(1.0 + 1e-5) + T(1e-30);
+        hy = hy * T(1.0 + 1e-5) + T(1e-30);
+        v2_t<T> H;
+        H.x = T(0);
+        H.y = T(0);
+        gH[g] = H;
+        vec4_t<T> bx;
+        bx.x = cx; bx.y = cy; bx.z = hx; bx.w = hy;
+        gbox[g] = bx;
+        grange[g] = make_uint2((uint32_t)first, (uint32_t)count);
+    }
+}
+
 // ---------------------------------------------------------------- walk
 
 template <int KIND, typename T, int R, bool AO, bool DIRECT, int TILE>
@@ -492,7 +607,37 @@ lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, 
     T2* gH = (T2*)(base + L.gH);
     T4* gbox = (T4*)(base + L.gbox);
     uint2* grange = (uint2*)(base + L.grange);
-    {
+    if (nb == 1 && dtype == LENS_F32) {
+        const int TB = 256;
+        const float* fx = (const float*)dx;
+        const float* fy = (const float*)dy;
+        uint32_t* bb = (uint32_t*)d_bbox;
+        uint32_t* k0 = (uint32_t*)(base + L.k0);
+        uint32_t* k1 = (uint32_t*)(base + L.k1);
+        uint32_t* v0 = (uint32_t*)(base + L.v0);
+        uint32_t* v1 = (uint32_t*)(base + L.v1);
+        LENS_CUDA(cudaMemsetAsync(bb, 0xff, 2 * sizeof(uint32_t), s));
+        LENS_CUDA(cudaMemsetAsync(bb + 2, 0, 2 * sizeof(uint32_t), s));
+        { k_ray_bbox32<<<grid_for(n, TB), TB, 0, s>>>(fx, fy, n, bb); note_launch(); }
+        { k_ray_keys32<<<grid_for(n, TB), TB, 0, s>>>(fx, fy, n, bb, k0, v0); note_launch(); }
+        uint32_t *sk, *sv;
+        radix_sort_pairs<uint32_t>(k0, v0, k1, v1, n, 0, 32, base + L.tmp, s, &sk, &sv);
+        unsigned gg = grid_for((int64_t)ng * 32, TB);
+        if (plan.ox == 0.0 && plan.oy == 0.0) {
+            if (R == 1)
+                { k_groups32<T, 1><<<gg, TB, 0, s>>>((int64_t)ng, n, fx, fy, sv, gH, gbox, grange, ray_l, ray_idx);
+                  note_launch(); }
+            else
+                { k_groups32<T, 2><<<gg, TB, 0, s>>>((int64_t)ng, n, fx, fy, sv, gH, gbox, grange, ray_l, ray_idx);
+                  note_launch(); }
+        } else if (R == 1) {
+            { k_groups<T, 1><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
+                                             sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
+        } else {
+            { k_groups<T, 2><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
+                                             sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
+        }
+    } else {
         const int TB = 256;
         { k_bbox_init<<<grid_for(nb, 128), 128, 0, s>>>(d_bbox, nb); note_launch(); }
         { k_ray_bbox<<<grid_for(n, TB), TB, 0, s>>>(d_boff, (int)nb, d_borig, dx, dy, dtype, n, d_bbox); note_launch(); }
