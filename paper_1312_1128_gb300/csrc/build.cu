@@ -198,12 +198,26 @@ __global__ void k_levels(const uint64_t* K, int64_t n, int N, uint8_t* Lp, uint3
     cnt[j] = L >= s ? (uint32_t)(L - s + 1) : 0u;
 }
 
-// First index e > j whose key leaves j's box at level l (n if none).
+// First index e > j whose key leaves j's box at level l (n if none): a
+// galloping search (steps 1, 2, 4, ... from j, then bisection of the last
+// step), so a box of c particles costs about 2 log2 c probes.
 __device__ __forceinline__ int64_t run_end(const uint64_t* K, int64_t n, int64_t j, int l)
 {
     if (l == 0) return n;
     uint64_t kj = K[j];
-    int64_t lo = j, hi = n;  // lcp(kj, K[lo]) >= l; hi is the first failing candidate
+    int64_t lo = j, step = 1;  // lcp(kj, K[lo]) >= l
+    int64_t hi = n;            // the first failing candidate, or n
+    for (;;) {
+        const int64_t probe = j + step;
+        if (probe >= n) break;
+        if (lcp_digits(kj, K[probe]) >= l) {
+            lo = probe;
+            step <<= 1;
+        } else {
+            hi = probe;
+            break;
+        }
+    }
     while (hi - lo > 1) {
         int64_t mid = lo + ((hi - lo) >> 1);
         if (lcp_digits(kj, K[mid]) >= l) lo = mid;
@@ -389,9 +403,9 @@ __device__ __forceinline__ void node_moments(uint32_t b, int l, const uint32_t* 
 // a leaf's thread computes the leaf, then counts it at its parent (one
 // atomic per box), and the child that completes the count computes the
 // parent from its children and climbs on.  Every box is computed once, by
-// whichever child finishes last; no thread ever waits for another.  A fence
-// before each count publishes the box; a fence after the completing count
-// orders the reads of its siblings.
+// whichever child finishes last; no thread ever waits for another.  Each
+// count is an acquire-release atomic: it publishes the box's moments, and the
+// completing count sees every sibling's.
 template <typename T>
 __global__ void k_moments_up(uint32_t n_nodes, const uint8_t* node_level, const uint32_t* first_bfs,
                              const int4* link, const int* parent, const vec4_t<T>* sorted, const uint64_t* K,
@@ -408,10 +422,11 @@ __global__ void k_moments_up(uint32_t n_nodes, const uint8_t* node_level, const 
             node_moments<T, double>(b, l, first_bfs, link, sorted, K, rb, inv_theta2, mom, q2, nodeA, nodeB, rcm_out);
         int p = parent[b];
         if (p < 0) return;
-        __threadfence();
-        uint32_t done = atomicAdd(&ready[p], 1u) + 1u;
-        if (done < (uint32_t)link[p].y) return;   // a box's y is its child count
-        __threadfence();
+        // release: this box's moments before the count; acquire: the
+        // siblings' moments after the completing count
+        uint32_t done;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(done) : "l"(ready + p) : "memory");
+        if (done + 1u < (uint32_t)link[p].y) return;   // a box's y is its child count
         b = (uint32_t)p;
     }
 }
@@ -466,10 +481,21 @@ __global__ void k_biglevel(const vec4_t<T>* sorted, int64_t n, const uint8_t* no
         double s = support_radius(kind, shape, (double)sorted[j].w);
         const uint32_t leaf = leaf_of[j];
         const int L = node_level[leaf];
+        // the smallest l with s > c 2^-l, c = lambda * side0 (2^-l scales
+        // exactly): with c = mc 2^ec and s = ms 2^es (mantissas in [0.5, 1)),
+        // l = ec - es if ms > mc, else ec - es + 1 (at least 0)
+        const double c = lambda * (2.0 * rb->half);
         int lp = -1;
-        double side0 = 2.0 * rb->half;
-        for (int l = 0; l <= L; ++l) {
-            if (s > lambda * side0 / (double)(1u << l)) { lp = l; break; }
+        if (s > 0.0) {
+            if (c == 0.0) {
+                lp = 0;
+            } else {
+                int ec, es;
+                const double mc = frexp(c, &ec), ms = frexp(s, &es);
+                const int l0 = ec - es + (ms > mc ? 0 : 1);
+                lp = l0 < 0 ? 0 : l0;
+                if (lp > L) lp = -1;
+            }
         }
         bval[j] = (uint32_t)j;
         if (lp < 0) {
@@ -599,13 +625,20 @@ template <typename T>
 __global__ void k_nodebox(const int4* link, uint32_t n_nodes, const vec4_t<T>* big0,
                           const vec4_t<T>* chunk, vec4_t<T>* out)
 {
-    int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (v >= n_nodes) return;
-    int4 L = link[v];
-    T x0 = T(INFINITY), y0 = T(INFINITY), x1 = T(-INFINITY), y1 = T(-INFINITY);
-    if (L.w > 0) {
-        int64_t z = L.z, e = (int64_t)L.z + L.w;
+    // one thread per node; the warp walks the listed nodes of its 32 together
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = v < n_nodes;
+    const int4 L = valid ? link[v] : make_int4(0, 0, 0, 0);
+    vec4_t<T> mine;
+    mine.x = T(INFINITY); mine.y = T(INFINITY); mine.z = T(-INFINITY); mine.w = T(-INFINITY);
+    unsigned todo = __ballot_sync(0xffffffffu, valid && L.w > 0);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t z = __shfl_sync(0xffffffffu, L.z, src);
+        const int64_t e = z + __shfl_sync(0xffffffffu, L.w, src);
+        T x0 = T(INFINITY), y0 = T(INFINITY), x1 = T(-INFINITY), y1 = T(-INFINITY);
         int64_t c0 = (z + 31) >> 5, c1 = e >> 5;  // whole chunks [c0, c1)
         for (int64_t c = c0 + lane; c < c1; c += 32) {
             vec4_t<T> b = chunk[c];
@@ -621,12 +654,11 @@ __global__ void k_nodebox(const int4* link, uint32_t n_nodes, const vec4_t<T>* b
             y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, o));
             y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, o));
         }
+        if (lane == src) {
+            mine.x = x0; mine.y = y0; mine.z = x1; mine.w = y1;
+        }
     }
-    if (lane == 0) {
-        vec4_t<T> r;
-        r.x = x0; r.y = y0; r.z = x1; r.w = y1;
-        out[v] = r;
-    }
+    if (valid) out[v] = mine;
 }
 
 __global__ void k_iota_u32(uint32_t* a, uint32_t n)
@@ -871,7 +903,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
         LENS_CUDA(lens_malloc_async((void**)&st.node_bigbox, (size_t)n_nodes * sizeof(T4), s));
         { k_chunkbox<T><<<grid_for(max_chunks, TB), TB, 0, s>>>((T4*)st.big0, d_nbig, max_chunks,
                                                               (T4*)st.big_chunk); note_launch(); }
-        { k_nodebox<T><<<grid_for((int64_t)n_nodes * 32, TB), TB, 0, s>>>(st.link, n_nodes, (T4*)st.big0,
+        { k_nodebox<T><<<grid_for((int64_t)n_nodes, TB), TB, 0, s>>>(st.link, n_nodes, (T4*)st.big0,
                                                                       (T4*)st.big_chunk, (T4*)st.node_bigbox); note_launch(); }
     }
     LENS_CUDA(cudaEventRecord(st.ev[3], s));

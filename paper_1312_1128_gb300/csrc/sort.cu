@@ -124,16 +124,10 @@ __global__ void radix_hist_kernel(const K* keys, int64_t n, int shift, uint32_t*
     __shared__ uint32_t cnt[kRadix];
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) cnt[d] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
     int64_t base = (int64_t)blockIdx.x * kSortTile;
     for (int r = 0; r < kSortItems; ++r) {
         int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
-        const bool valid = idx < n;
-        const uint32_t d = valid ? ((uint32_t)(keys[idx] >> shift) & 0xffu) : 0xffffffffu;
-        // one shared atomic per distinct digit of the warp (the high digits of
-        // Morton keys are few: lanes with equal digits would serialise)
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+        if (idx < n) atomicAdd(&cnt[(uint32_t)(keys[idx] >> shift) & 0xffu], 1u);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
