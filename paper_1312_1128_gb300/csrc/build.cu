@@ -326,17 +326,16 @@ template <> __device__ __forceinline__ double round_up<double>(double x) { retur
 constexpr int kFp64Levels = 8;
 
 template <typename T, typename A>
-__device__ __forceinline__ void node_moments(uint32_t b, int l, const uint32_t* first_bfs, const int4* link,
-                                             const vec4_t<T>* sorted, const uint64_t* K, const RootBox* rb,
-                                             double inv_theta2, dbl4* mom, double2* q2, vec4_t<T>* nodeA,
+__device__ __forceinline__ void node_moments(uint32_t b, int l, uint32_t ix, uint32_t iy, const int4 L,
+                                             const vec4_t<T>* sorted, const RootBox* rb, double inv_theta2,
+                                             dbl4* mom, double2* q2, vec4_t<T>* nodeA,
                                              typename V2<T>::type* nodeB, float* rcm_out)
 {
-    const double side = 2.0 * rb->half / (double)(1u << l);
-    const uint64_t key = K[first_bfs[b]];
-    const uint32_t ix = compact24(key) >> (kMaxDepth - l), iy = compact24(key >> 1) >> (kMaxDepth - l);
+    // box (ix, iy) of level l
+    // 2^-l built from its exponent: exact, and no FP64 division (slow here)
+    const double side = (2.0 * rb->half) * __longlong_as_double((long long)(1023 - l) << 52);
     const double cxd = rb->x0 + (ix + 0.5) * side, cyd = rb->y0 + (iy + 0.5) * side;
     const A cx = (A)cxd, cy = (A)cyd;   // the moments are taken about this point
-    const int4 L = link[b];
     A M = 0, sx = 0, sy = 0, qr = 0, qi = 0;
     if (L.y & kLeafBit) {
         const int cnt = L.y & kCountMask;
@@ -403,9 +402,7 @@ __device__ __forceinline__ void node_moments(uint32_t b, int l, const uint32_t* 
 // a leaf's thread computes the leaf, then counts it at its parent (one
 // atomic per box), and the child that completes the count computes the
 // parent from its children and climbs on.  Every box is computed once, by
-// whichever child finishes last; no thread ever waits for another.  Each
-// count is an acquire-release atomic: it publishes the box's moments, and the
-// completing count sees every sibling's.
+// whichever child finishes last; no thread ever waits for another.
 template <typename T>
 __global__ void k_moments_up(uint32_t n_nodes, const uint8_t* node_level, const uint32_t* first_bfs,
                              const int4* link, const int* parent, const vec4_t<T>* sorted, const uint64_t* K,
@@ -413,21 +410,35 @@ __global__ void k_moments_up(uint32_t n_nodes, const uint8_t* node_level, const 
                              typename V2<T>::type* nodeB, float* rcm_out, uint32_t* ready)
 {
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_nodes || !(link[b].y & kLeafBit)) return;
+    if (b >= n_nodes) return;
+    int4 L = link[b];
+    if (!(L.y & kLeafBit)) return;
+    int l = node_level[b];
+    const uint64_t key = K[first_bfs[b]];
+    // the climb derives each parent's cell from its child's: no further
+    // loads of keys or levels on the way up
+    uint32_t ix = compact24(key) >> (kMaxDepth - l), iy = compact24(key >> 1) >> (kMaxDepth - l);
+    int p = parent[b];
     for (;;) {
-        const int l = node_level[b];
         if (sizeof(T) == 4 && l >= kFp64Levels)
-            node_moments<T, float>(b, l, first_bfs, link, sorted, K, rb, inv_theta2, mom, q2, nodeA, nodeB, rcm_out);
+            node_moments<T, float>(b, l, ix, iy, L, sorted, rb, inv_theta2, mom, q2, nodeA, nodeB, rcm_out);
         else
-            node_moments<T, double>(b, l, first_bfs, link, sorted, K, rb, inv_theta2, mom, q2, nodeA, nodeB, rcm_out);
-        int p = parent[b];
+            node_moments<T, double>(b, l, ix, iy, L, sorted, rb, inv_theta2, mom, q2, nodeA, nodeB, rcm_out);
         if (p < 0) return;
-        // release: this box's moments before the count; acquire: the
-        // siblings' moments after the completing count
+        // the parent's links (written by earlier launches) are read beside
+        // the count.  The count is an acquire-release atomic: it publishes this
+        // box's moments, and the completing count sees every sibling's.
+        const int4 Lp = link[p];
+        const int pp = parent[p];
         uint32_t done;
         asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(done) : "l"(ready + p) : "memory");
-        if (done + 1u < (uint32_t)link[p].y) return;   // a box's y is its child count
+        if (done + 1u < (uint32_t)Lp.y) return;   // a box's y is its child count
         b = (uint32_t)p;
+        L = Lp;
+        p = pp;
+        --l;
+        ix >>= 1;
+        iy >>= 1;
     }
 }
 
@@ -615,50 +626,123 @@ __global__ void k_chunkbox(const vec4_t<T>* big0, const uint32_t* d_nbig, int64_
     out[c] = support_box<T>(big0, b, e);
 }
 
-// One warp per node: the node's list [z, z + w) is covered by the boxes of
-// its whole 32-entry chunks plus the single entries of the partial chunks at
-// its two ends; lanes stride over both and reduce in the tree's precision
-// (chunk boxes are already rounded outwards; min and max do not round).  A
-// node without a list gets the empty box (+inf, +inf, -inf, -inf), which no
-// reader looks at.
+// Boxes of 1,024-entry superchunks (32 chunks): one warp each.
 template <typename T>
-__global__ void k_nodebox(const int4* link, uint32_t n_nodes, const vec4_t<T>* big0,
-                          const vec4_t<T>* chunk, vec4_t<T>* out)
+__global__ void k_superbox(const vec4_t<T>* chunk, const uint32_t* d_nbig, int64_t n_super, vec4_t<T>* out)
 {
-    // one thread per node; the warp walks the listed nodes of its 32 together
+    const int64_t sc = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sc >= n_super) return;
+    const int64_t nbig = *d_nbig, c = 32 * sc + lane;
+    T x0 = T(INFINITY), y0 = T(INFINITY), x1 = T(-INFINITY), y1 = T(-INFINITY);
+    if (32 * c < nbig) {
+        vec4_t<T> b = chunk[c];
+        x0 = b.x; y0 = b.y; x1 = b.z; y1 = b.w;
+    }
+    for (int o = 16; o; o >>= 1) {
+        x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    }
+    if (lane == 0) {
+        vec4_t<T> r;
+        r.x = x0; r.y = y0; r.z = x1; r.w = y1;
+        out[sc] = r;
+    }
+}
+
+// Entries [z, e) of a list by this lane: whole 32-entry chunks by their
+// boxes, the partial chunks at the two ends entry by entry.
+template <typename T>
+__device__ __forceinline__ void range_extent(int64_t z, int64_t e, int lane, const vec4_t<T>* big0,
+                                             const vec4_t<T>* chunk, T& x0, T& y0, T& x1, T& y1)
+{
+    int64_t c0 = (z + 31) >> 5, c1 = e >> 5;  // whole chunks [c0, c1)
+    for (int64_t c = c0 + lane; c < c1; c += 32) {
+        vec4_t<T> b = chunk[c];
+        x0 = fmin(x0, b.x); y0 = fmin(y0, b.y);
+        x1 = fmax(x1, b.z); y1 = fmax(y1, b.w);
+    }
+    int64_t head_end = c0 < c1 ? 32 * c0 : e, tail_begin = c0 < c1 ? 32 * c1 : e;
+    for (int64_t i = z + lane; i < head_end; i += 32) entry_extent(big0[i], x0, y0, x1, y1);
+    for (int64_t i = tail_begin + lane; i < e; i += 32) entry_extent(big0[i], x0, y0, x1, y1);
+}
+
+// Big-list box of every node, in two launches.  k_nodebox: one thread per
+// node; a node without a list gets the empty box (+inf, +inf, -inf, -inf),
+// which no reader looks at; a list of at most kShortList entries is reduced
+// by its own thread; a longer list is queued.  k_nodebox_long: each warp
+// takes queued lists one at a time, all 32 lanes on one list [z, z + w):
+// covered by the boxes of its whole 1,024-entry superchunks, of the whole
+// 32-entry chunks at its two ends and by the single entries of the partial
+// chunks, reduced in the tree's precision (chunk boxes are already rounded
+// outwards; min and max do not round).  The long lists are those of the top
+// levels: spread over warps rather than met one after another by the warp
+// that holds the first boxes.
+constexpr int kShortList = 32;
+
+template <typename T>
+__global__ void k_nodebox(const int4* link, uint32_t n_nodes, const vec4_t<T>* big0, vec4_t<T>* out,
+                          uint32_t* queue, uint32_t* n_queued)
+{
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool valid = v < n_nodes;
     const int4 L = valid ? link[v] : make_int4(0, 0, 0, 0);
-    vec4_t<T> mine;
-    mine.x = T(INFINITY); mine.y = T(INFINITY); mine.z = T(-INFINITY); mine.w = T(-INFINITY);
-    unsigned todo = __ballot_sync(0xffffffffu, valid && L.w > 0);
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int64_t z = __shfl_sync(0xffffffffu, L.z, src);
-        const int64_t e = z + __shfl_sync(0xffffffffu, L.w, src);
+    const bool longl = valid && L.w > kShortList;
+    const unsigned q = __ballot_sync(0xffffffffu, longl);
+    uint32_t at = 0;
+    if (lane == 0 && q) at = atomicAdd(n_queued, (uint32_t)__popc(q));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (longl) queue[at + __popc(q & ((1u << lane) - 1u))] = (uint32_t)v;
+    if (!valid || longl) return;
+    T x0 = T(INFINITY), y0 = T(INFINITY), x1 = T(-INFINITY), y1 = T(-INFINITY);
+#pragma unroll 4
+    for (int k = 0; k < L.w; ++k) entry_extent(big0[(int64_t)L.z + k], x0, y0, x1, y1);
+    vec4_t<T> r;
+    r.x = x0; r.y = y0; r.z = x1; r.w = y1;
+    out[v] = r;
+}
+
+template <typename T>
+__global__ void k_nodebox_long(const int4* link, const vec4_t<T>* big0, const vec4_t<T>* chunk,
+                               const vec4_t<T>* super, const uint32_t* queue, const uint32_t* n_queued,
+                               vec4_t<T>* out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t nq = *n_queued;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t k = ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nq; k += nw) {
+        const uint32_t v = queue[k];
+        const int4 L = link[v];
+        const int64_t z = L.z, e = z + L.w;
         T x0 = T(INFINITY), y0 = T(INFINITY), x1 = T(-INFINITY), y1 = T(-INFINITY);
-        int64_t c0 = (z + 31) >> 5, c1 = e >> 5;  // whole chunks [c0, c1)
-        for (int64_t c = c0 + lane; c < c1; c += 32) {
-            vec4_t<T> b = chunk[c];
-            x0 = fmin(x0, b.x); y0 = fmin(y0, b.y);
-            x1 = fmax(x1, b.z); y1 = fmax(y1, b.w);
+        // whole superchunks [s0, s1) by their boxes, the ends by range_extent
+        const int64_t s0 = (z + 1023) >> 10, s1 = e >> 10;
+        if (s0 < s1) {
+            for (int64_t sc = s0 + lane; sc < s1; sc += 32) {
+                vec4_t<T> b = super[sc];
+                x0 = fmin(x0, b.x); y0 = fmin(y0, b.y);
+                x1 = fmax(x1, b.z); y1 = fmax(y1, b.w);
+            }
+            range_extent<T>(z, 1024 * s0, lane, big0, chunk, x0, y0, x1, y1);
+            range_extent<T>(1024 * s1, e, lane, big0, chunk, x0, y0, x1, y1);
+        } else {
+            range_extent<T>(z, e, lane, big0, chunk, x0, y0, x1, y1);
         }
-        int64_t head_end = c0 < c1 ? 32 * c0 : e, tail_begin = c0 < c1 ? 32 * c1 : e;
-        for (int64_t i = z + lane; i < head_end; i += 32) entry_extent(big0[i], x0, y0, x1, y1);
-        for (int64_t i = tail_begin + lane; i < e; i += 32) entry_extent(big0[i], x0, y0, x1, y1);
         for (int o = 16; o; o >>= 1) {
             x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, o));
             x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, o));
             y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, o));
             y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, o));
         }
-        if (lane == src) {
-            mine.x = x0; mine.y = y0; mine.z = x1; mine.w = y1;
+        if (lane == 0) {
+            vec4_t<T> r;
+            r.x = x0; r.y = y0; r.z = x1; r.w = y1;
+            out[v] = r;
         }
     }
-    if (valid) out[v] = mine;
 }
 
 __global__ void k_iota_u32(uint32_t* a, uint32_t n)
@@ -743,7 +827,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     { k_morton<T><<<G, TB, 0, s>>>(staged, n, rb, k0, v0); note_launch(); }
     uint64_t* K;
     uint32_t* P;
-    radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, kKeyBits, tmp, s, &K, &P);
+    radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, kKeyBits, tmp, s, &K, &P, t->d_err);
     { k_gather<T><<<G, TB, 0, s>>>(staged, P, n, sorted); note_launch(); }
     LENS_CUDA(cudaEventRecord(st.ev[1], s));
 
@@ -802,7 +886,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     LENS_CUDA(tmps.get(&ids, n_nodes * sizeof(uint32_t)));
     { k_iota_u32<<<GN, TB, 0, s>>>(ids, n_nodes); note_launch(); }
     uint32_t *lvl_sorted, *bfs2pre;
-    radix_sort_pairs<uint32_t>(lv0, ids, lv1, lk1, n_nodes, 0, 8, tmp, s, &lvl_sorted, &bfs2pre);
+    radix_sort_pairs<uint32_t>(lv0, ids, lv1, lk1, n_nodes, 0, 8, tmp, s, &lvl_sorted, &bfs2pre, t->d_err);
     { k_invert<<<GN, TB, 0, s>>>(bfs2pre, n_nodes, pre2bfs); note_launch(); }
     { k_level_bounds<<<GN, TB, 0, s>>>(lvl_sorted, n_nodes, level_start); note_launch(); }
     LENS_CUDA(lens_malloc_async(&st.d_meta, sizeof(BuildMeta), s));
@@ -886,7 +970,7 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
         while (bits < 32 && ((1ull << bits) <= (uint64_t)n_nodes)) ++bits;
         bits = (bits + 7) & ~7;
         uint32_t *skey, *sval;
-        radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, n, 0, bits, tmp, s, &skey, &sval);
+        radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, n, 0, bits, tmp, s, &skey, &sval, t->d_err);
         { k_bigcsr<<<G, TB, 0, s>>>(skey, n, n_nodes, st.link, end); note_launch(); }
         { k_bigcount<<<GN, TB, 0, s>>>(n_nodes, st.link, end); note_launch(); }
         // the big arrays hold up to one entry per particle (the count is read
@@ -903,8 +987,20 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
         LENS_CUDA(lens_malloc_async((void**)&st.node_bigbox, (size_t)n_nodes * sizeof(T4), s));
         { k_chunkbox<T><<<grid_for(max_chunks, TB), TB, 0, s>>>((T4*)st.big0, d_nbig, max_chunks,
                                                               (T4*)st.big_chunk); note_launch(); }
+        const int64_t n_super = (max_chunks + 31) / 32;
+        T4* super = nullptr;
+        LENS_CUDA(tmps.get(&super, n_super * sizeof(T4)));
+        { k_superbox<T><<<grid_for(n_super * 32, TB), TB, 0, s>>>((T4*)st.big_chunk, d_nbig, n_super, super);
+          note_launch(); }
+        uint32_t* queue = nullptr;
+        LENS_CUDA(tmps.get(&queue, (n_nodes + 1) * sizeof(uint32_t)));
+        uint32_t* n_queued = queue + n_nodes;
+        LENS_CUDA(cudaMemsetAsync(n_queued, 0, sizeof(uint32_t), s));
         { k_nodebox<T><<<grid_for((int64_t)n_nodes, TB), TB, 0, s>>>(st.link, n_nodes, (T4*)st.big0,
-                                                                      (T4*)st.big_chunk, (T4*)st.node_bigbox); note_launch(); }
+                                                                      (T4*)st.node_bigbox, queue, n_queued);
+          note_launch(); }
+        { k_nodebox_long<T><<<t->num_sms * 8, TB, 0, s>>>(st.link, (T4*)st.big0, (T4*)st.big_chunk, super, queue,
+                                                          n_queued, (T4*)st.node_bigbox); note_launch(); }
     }
     LENS_CUDA(cudaEventRecord(st.ev[3], s));
 

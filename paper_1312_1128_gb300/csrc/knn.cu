@@ -349,7 +349,7 @@ extern "C" lens_status lens_smoothing_lengths(const float* xyz, int64_t n, int32
         note_launch();
         uint64_t* sk;
         uint32_t* sv;
-        radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, 3 * kKnnBits, base + o_tmp, s, &sk, &sv);
+        radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, 3 * kKnnBits, base + o_tmp, s, &sk, &sv, err);
         k_knn_gather<<<(unsigned)G, TB, 0, s>>>(xyz, n, sv, sp);
         note_launch();
         const unsigned qb = (unsigned)((n + 32 * kKnnWarps - 1) / (32 * kKnnWarps));

@@ -1,6 +1,7 @@
 // sort.cu -- device-wide exclusive scan and stable LSD radix sort of
 // (key, value) pairs, used by the tree build (Morton order, level order,
 // big-list grouping) and by ray grouping.  Hand-written; no CUB/Thrust.
+#include "common.cuh"
 #include "sort.cuh"
 
 namespace lens {
@@ -165,7 +166,7 @@ template <typename K>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const K* kin, const uint32_t* vin, K* kout,
                                                                      uint32_t* vout, int64_t n, int shift,
                                                                      const uint32_t* offs, const uint32_t* digit_tot,
-                                                                     int64_t nblocks)
+                                                                     int64_t nblocks, uint32_t* err)
 {
     constexpr int kWarps = kSortThreads / 32;
     static_assert(kSortThreads == kRadix && kSortThreads == kScanThreads, "one thread per digit");
@@ -216,6 +217,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const K* ki
         if (e < tile_n) {
             const uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
             const uint32_t tp = tstart[d] + wcnt[wid][d] + lrank[r];
+            if (tp >= (uint32_t)tile_n) {  // cannot happen: the ranks are a permutation of the tile
+                if (err) atomicOr(err, DERR_INDEX);
+                continue;
+            }
             sk[tp] = key[r];
             sv[tp] = val[r];
         }
@@ -227,6 +232,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const K* ki
         const K k = sk[e];
         const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
         const uint32_t pos = base_off[d] + (uint32_t)e - tstart[d];
+        if ((int64_t)pos >= n) {  // cannot happen: the offsets are a scan of the histogram
+            if (err) atomicOr(err, DERR_INDEX);
+            continue;
+        }
         kout[pos] = k;
         vout[pos] = sv[e];
     }
@@ -240,12 +249,24 @@ size_t radix_sort_temp_bytes(int64_t n)
     return hist + kRadix * sizeof(uint32_t) + 256;
 }
 
+#ifdef LENS_SORT_DEBUG
+__global__ void k_perm_mark(const uint32_t* v, int64_t n, uint32_t* bits, uint32_t* err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t x = v[i];
+    if ((int64_t)x >= n) { atomicOr(err, DERR_BUFFER); return; }
+    const uint32_t old = atomicOr(bits + (x >> 5), 1u << (x & 31));
+    if (old & (1u << (x & 31))) atomicOr(err, DERR_BUFFER);
+}
+#endif
+
 // Sort (keys, vals) by bits [begin_bit, end_bit) of the key.  Uses the
 // alternate buffers; on return *kres / *vres point at the sorted data (one of
 // the two buffers).  n must be < 2^32.
 template <typename K>
 void radix_sort_pairs(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int begin_bit,
-                      int end_bit, void* tmp, cudaStream_t s, K** kres, uint32_t** vres)
+                      int end_bit, void* tmp, cudaStream_t s, K** kres, uint32_t** vres, uint32_t* err)
 {
     K* ki = k0; uint32_t* vi = v0;
     K* ko = k1; uint32_t* vo = v1;
@@ -256,12 +277,23 @@ void radix_sort_pairs(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int b
         for (int b = begin_bit; b < end_bit; b += 8) {
             { radix_hist_kernel<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ki, n, b, hist, nb); note_launch(); }
             { radix_colscan_kernel<<<kRadix, kScanThreads, 0, s>>>(hist, nb, dtot); note_launch(); }
-            { radix_scatter_kernel<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, b, hist, dtot, nb);
+            { radix_scatter_kernel<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, b, hist, dtot, nb,
+                                                                                err);
               note_launch(); }
             K* tk = ki; ki = ko; ko = tk;
             uint32_t* tv = vi; vi = vo; vo = tv;
         }
     }
+#ifdef LENS_SORT_DEBUG
+    if (n > 1 && err) {
+        // every caller sorts an index array 0..n-1: check that a permutation comes out
+        uint32_t* bits = nullptr;
+        cudaMallocAsync((void**)&bits, ((n + 31) / 32) * 4, s);
+        cudaMemsetAsync(bits, 0, ((n + 31) / 32) * 4, s);
+        k_perm_mark<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(vi, n, bits, err);
+        cudaFreeAsync(bits, s);
+    }
+#endif
     *kres = ki;
     *vres = vi;
 }
@@ -269,8 +301,8 @@ void radix_sort_pairs(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int b
 template size_t radix_sort_temp_bytes<uint64_t>(int64_t);
 template size_t radix_sort_temp_bytes<uint32_t>(int64_t);
 template void radix_sort_pairs<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, int64_t, int, int,
-                                         void*, cudaStream_t, uint64_t**, uint32_t**);
+                                         void*, cudaStream_t, uint64_t**, uint32_t**, uint32_t*);
 template void radix_sort_pairs<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t, int, int,
-                                         void*, cudaStream_t, uint32_t**, uint32_t**);
+                                         void*, cudaStream_t, uint32_t**, uint32_t**, uint32_t*);
 
 }  // namespace lens

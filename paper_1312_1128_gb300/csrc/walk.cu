@@ -621,7 +621,7 @@ lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, 
         { k_ray_bbox32<<<grid_for(n, TB), TB, 0, s>>>(fx, fy, n, bb); note_launch(); }
         { k_ray_keys32<<<grid_for(n, TB), TB, 0, s>>>(fx, fy, n, bb, k0, v0); note_launch(); }
         uint32_t *sk, *sv;
-        radix_sort_pairs<uint32_t>(k0, v0, k1, v1, n, 0, 32, base + L.tmp, s, &sk, &sv);
+        radix_sort_pairs<uint32_t>(k0, v0, k1, v1, n, 0, 32, base + L.tmp, s, &sk, &sv, t->d_err);
         unsigned gg = grid_for((int64_t)ng * 32, TB);
         if (plan.ox == 0.0 && plan.oy == 0.0) {
             if (R == 1)
@@ -651,7 +651,7 @@ lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, 
         int end_bit = (32 + bbits + 7) & ~7;
         uint64_t* sk;
         uint32_t* sv;
-        radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, end_bit, base + L.tmp, s, &sk, &sv);
+        radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, end_bit, base + L.tmp, s, &sk, &sv, t->d_err);
         unsigned gg = grid_for((int64_t)ng * 32, TB);
         if (R == 1)
             { k_groups<T, 1><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
@@ -902,7 +902,7 @@ HeavyPlan heavy_first_order(lens_tree* t, const ShootPlan& plan, const RayKey& k
         note_launch();
     }
     uint32_t *sk, *sv;
-    radix_sort_pairs<uint32_t>(k0, v0, k1, v1, ng, 0, 32, base + L.tmp, s, &sk, &sv);
+    radix_sort_pairs<uint32_t>(k0, v0, k1, v1, ng, 0, 32, base + L.tmp, s, &sk, &sv, t->d_err);
     hp.order = sv;
     if (n_warps > 0) {
         { k_heavy_plan<<<1, kHeavyGroups, 0, s>>>(ng, sk, (unsigned long long)n_warps, hdr, table); note_launch(); }
