@@ -87,6 +87,11 @@ constexpr int kBackNear = kNearCap, kBackBig = kBigCap;
 
 template <int KIND, typename T> struct BackShared {
     T rx[kMaxGroup], ry[kMaxGroup], rg1[kMaxGroup], rg2[kMaxGroup];
+    // FP32: the rays in pairs for the packed (f32x2) far-cell adjoint:
+    // pk_a[p] = (x_2p, x_2p+1, y_2p, y_2p+1), pk_b[p] = (g1, g1', g2, g2')
+    // (an odd group's last pair repeats its first ray with zero gradient)
+    float4 pk_a[sizeof(T) == 4 ? kMaxGroup / 2 : 1];
+    float4 pk_b[sizeof(T) == 4 ? kMaxGroup / 2 : 1];
     T fdx[kFarCap], fdy[kFarCap], fM[kFarCap], fqr[kFarCap], fqi[kFarCap];
     int fnode[kFarCap];
     vec4_t<T> n0[kBackNear];
@@ -193,6 +198,10 @@ template <int KIND, typename T> struct BackCtx {
     {
         int lane = threadIdx.x & 31;
         __syncwarp();
+        if constexpr (sizeof(T) == 4) {
+            flush_far_packed(nf);
+            return;
+        }
         for (int cell = lane; cell < nf; cell += 32) {
             T dx = S.fdx[cell], dy = S.fdy[cell], M = S.fM[cell], qr = S.fqr[cell], qi = S.fqi[cell];
             T aM = T(0), cr = T(0), ci = T(0), br = T(0), bi = T(0);
@@ -218,6 +227,56 @@ template <int KIND, typename T> struct BackCtx {
             atomicAdd(a + 2, (double)ci);
             atomicAdd(a + 3, (double)br);
             atomicAdd(a + 4, (double)bi);
+        }
+        __syncwarp();
+    }
+
+    // The same sums in FP32 two rays at a time (f32x2 multiply-adds): per ray
+    // pair 19 packed FMA-pipe operations and two reciprocals.
+    LENS_DEV void flush_far_packed(int nf)
+    {
+        const int lane = threadIdx.x & 31;
+        const int np = (nr + 1) >> 1;
+        const float2 M1 = make_float2(-1.f, -1.f);
+        for (int cell = lane; cell < nf; cell += 32) {
+            const float dx = (float)S.fdx[cell], dy = (float)S.fdy[cell], M = (float)S.fM[cell];
+            const float qr = (float)S.fqr[cell], qi = (float)S.fqi[cell];
+            const float2 NDX = make_float2(-dx, -dx), DY = make_float2(dy, dy), MM = make_float2(M, M);
+            const float2 QR3 = make_float2(3.f * qr, 3.f * qr), QI3 = make_float2(3.f * qi, 3.f * qi);
+            const float2 NQI3 = make_float2(-3.f * qi, -3.f * qi);
+            float2 aM = make_float2(0.f, 0.f), cr = aM, ci = aM, br = aM, bi = aM;
+            for (int p = 0; p < np; ++p) {
+                const float4 A = S.pk_a[p], B = S.pk_b[p];
+                const float2 G1 = make_float2(B.x, B.y), G2 = make_float2(B.z, B.w);
+                const float2 NG2 = __fmul2_rn(G2, M1);
+                const float2 wx = __fadd2_rn(make_float2(A.x, A.y), NDX);
+                const float2 nwy = __ffma2_rn(make_float2(A.z, A.w), M1, DY);  // -(y - y_cell)
+                const float2 r2 = __ffma2_rn(wx, wx, __fmul2_rn(nwy, nwy));
+                const float2 inv = make_float2(rcp(r2.x), rcp(r2.y));
+                // u = 1 / w and its powers
+                const float2 ux = __fmul2_rn(wx, inv), uy = __fmul2_rn(nwy, inv);
+                const float2 nuy = __fmul2_rn(uy, M1);
+                const float2 u2x = __ffma2_rn(ux, ux, __fmul2_rn(uy, nuy));
+                const float2 u2y = __fmul2_rn(__fadd2_rn(ux, ux), uy);
+                const float2 u3x = __ffma2_rn(u2x, ux, __fmul2_rn(u2y, nuy));
+                const float2 u3y = __ffma2_rn(u2x, uy, __fmul2_rn(u2y, ux));
+                const float2 nu2y = __fmul2_rn(u2y, M1);
+                const float2 u4x = __ffma2_rn(u2x, u2x, __fmul2_rn(u2y, nu2y));
+                const float2 u4y = __fmul2_rn(__fadd2_rn(u2x, u2x), u2y);
+                aM = __ffma2_rn(G1, ux, __ffma2_rn(NG2, uy, aM));
+                cr = __ffma2_rn(G1, u3x, __ffma2_rn(NG2, u3y, cr));
+                ci = __ffma2_rn(G1, u3y, __ffma2_rn(G2, u3x, ci));
+                const float2 tx = __ffma2_rn(MM, u2x, __ffma2_rn(QR3, u4x, __fmul2_rn(NQI3, u4y)));
+                const float2 ty = __ffma2_rn(MM, u2y, __ffma2_rn(QR3, u4y, __fmul2_rn(QI3, u4x)));
+                br = __ffma2_rn(G1, tx, __ffma2_rn(NG2, ty, br));
+                bi = __ffma2_rn(G1, ty, __ffma2_rn(G2, tx, bi));
+            }
+            double* a = P.adj + 5 * (int64_t)S.fnode[cell];
+            atomicAdd(a + 0, (double)(aM.x + aM.y));
+            atomicAdd(a + 1, (double)(cr.x + cr.y));
+            atomicAdd(a + 2, (double)(ci.x + ci.y));
+            atomicAdd(a + 3, (double)(br.x + br.y));
+            atomicAdd(a + 4, (double)(bi.x + bi.y));
         }
         __syncwarp();
     }
@@ -449,6 +508,15 @@ back_kernel(BackParams<T> P)
             S.rg2[k] = P.ga2[i];
         }
         __syncwarp();
+        if constexpr (sizeof(T) == 4) {
+            for (int p = lane; 2 * p < C.nr; p += 32) {
+                const bool two = 2 * p + 1 < C.nr;
+                const int j0 = 2 * p, j1 = two ? 2 * p + 1 : 2 * p;
+                S.pk_a[p] = make_float4(S.rx[j0], S.rx[j1], S.ry[j0], S.ry[j1]);
+                S.pk_b[p] = make_float4(S.rg1[j0], two ? S.rg1[j1] : 0.f, S.rg2[j0], two ? S.rg2[j1] : 0.f);
+            }
+            __syncwarp();
+        }
 
         if (P.n_part > 0) {
             int nn = 0, nb = 0;

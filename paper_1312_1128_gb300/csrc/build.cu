@@ -321,14 +321,24 @@ template <> __device__ __forceinline__ double round_up<double>(double x) { retur
 // from the stored centre of mass in every case (r_cm rounded down, r_cut^2
 // up).  Level and first particle come in BFS order.  Children are read
 // through L2 (__ldcg): other threads of the launch wrote them, and a line
-// cached in L1 before one of them was written would be stale.
+// cached in L1 before one of them was written would be stale.  A box's
+// (M, centre of mass, Q2) for its parent are kept in the type they were
+// computed in (mom/q2 in FP64, momf/q2f in FP32), so that a parent in FP32
+// reads its children without conversions on the FP64 pipe.
 // inv_theta2 = 1/theta^2 (infinite r_cut when theta = 0).
 constexpr int kFp64Levels = 8;
+
+struct MomentsOut {
+    dbl4* mom;      // FP64 boxes: {M, x_cm, y_cm, side}
+    double2* q2;
+    float4* momf;   // FP32 boxes: {M, x_cm, y_cm, 0}
+    float2* q2f;
+};
 
 template <typename T, typename A>
 __device__ __forceinline__ void node_moments(uint32_t b, int l, uint32_t ix, uint32_t iy, const int4 L,
                                              const vec4_t<T>* sorted, const RootBox* rb, double inv_theta2,
-                                             dbl4* mom, double2* q2, vec4_t<T>* nodeA,
+                                             const MomentsOut& O, vec4_t<T>* nodeA,
                                              typename V2<T>::type* nodeB, float* rcm_out)
 {
     // box (ix, iy) of level l
@@ -359,14 +369,27 @@ __device__ __forceinline__ void node_moments(uint32_t b, int l, uint32_t ix, uin
         sy = dy;
     } else {
         A cm[4], cxk[4], cyk[4], cqr[4], cqi[4];
-        for (int k = 0; k < L.y; ++k) {
-            const double* pm = reinterpret_cast<const double*>(mom + L.x + k);
-            const double2 cq = __ldcg(q2 + L.x + k);
-            cm[k] = (A)__ldcg(pm);
-            cxk[k] = (A)__ldcg(pm + 1) - cx;
-            cyk[k] = (A)__ldcg(pm + 2) - cy;
-            cqr[k] = (A)cq.x;
-            cqi[k] = (A)cq.y;
+        if (sizeof(T) == 4 && l + 1 >= kFp64Levels) {
+            // children stored in FP32
+            for (int k = 0; k < L.y; ++k) {
+                const float4 m4 = __ldcg(O.momf + L.x + k);
+                const float2 cq = __ldcg(O.q2f + L.x + k);
+                cm[k] = (A)m4.x;
+                cxk[k] = (A)m4.y - cx;
+                cyk[k] = (A)m4.z - cy;
+                cqr[k] = (A)cq.x;
+                cqi[k] = (A)cq.y;
+            }
+        } else {
+            for (int k = 0; k < L.y; ++k) {
+                const double* pm = reinterpret_cast<const double*>(O.mom + L.x + k);
+                const double2 cq = __ldcg(O.q2 + L.x + k);
+                cm[k] = (A)__ldcg(pm);
+                cxk[k] = (A)__ldcg(pm + 1) - cx;
+                cyk[k] = (A)__ldcg(pm + 2) - cy;
+                cqr[k] = (A)cq.x;
+                cqi[k] = (A)cq.y;
+            }
         }
         for (int k = 0; k < L.y; ++k) {
             M += cm[k];
@@ -384,8 +407,13 @@ __device__ __forceinline__ void node_moments(uint32_t b, int l, uint32_t ix, uin
         sy = dy;
     }
     const A cmx = cx + sx, cmy = cy + sy;
-    mom[b] = make_dbl4((double)M, (double)cmx, (double)cmy, side);
-    q2[b] = make_double2((double)qr, (double)qi);
+    if (sizeof(T) == 4 && l >= kFp64Levels) {
+        O.momf[b] = make_float4((float)M, (float)cmx, (float)cmy, 0.f);
+        O.q2f[b] = make_float2((float)qr, (float)qi);
+    } else {
+        O.mom[b] = make_dbl4((double)M, (double)cmx, (double)cmy, side);
+        O.q2[b] = make_double2((double)qr, (double)qi);
+    }
     // r_cm: distance from the centre of mass to the farthest corner of the box
     const double ex = fabs((double)cmx - cxd) + 0.5 * side, ey = fabs((double)cmy - cyd) + 0.5 * side;
     const double rcm2 = ex * ex + ey * ey;
@@ -406,7 +434,7 @@ __device__ __forceinline__ void node_moments(uint32_t b, int l, uint32_t ix, uin
 template <typename T>
 __global__ void k_moments_up(uint32_t n_nodes, const uint8_t* node_level, const uint32_t* first_bfs,
                              const int4* link, const int* parent, const vec4_t<T>* sorted, const uint64_t* K,
-                             const RootBox* rb, double inv_theta2, dbl4* mom, double2* q2, vec4_t<T>* nodeA,
+                             const RootBox* rb, double inv_theta2, MomentsOut O, vec4_t<T>* nodeA,
                              typename V2<T>::type* nodeB, float* rcm_out, uint32_t* ready)
 {
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -421,9 +449,9 @@ __global__ void k_moments_up(uint32_t n_nodes, const uint8_t* node_level, const 
     int p = parent[b];
     for (;;) {
         if (sizeof(T) == 4 && l >= kFp64Levels)
-            node_moments<T, float>(b, l, ix, iy, L, sorted, rb, inv_theta2, mom, q2, nodeA, nodeB, rcm_out);
+            node_moments<T, float>(b, l, ix, iy, L, sorted, rb, inv_theta2, O, nodeA, nodeB, rcm_out);
         else
-            node_moments<T, double>(b, l, ix, iy, L, sorted, rb, inv_theta2, mom, q2, nodeA, nodeB, rcm_out);
+            node_moments<T, double>(b, l, ix, iy, L, sorted, rb, inv_theta2, O, nodeA, nodeB, rcm_out);
         if (p < 0) return;
         // the parent's links (written by earlier launches) are read beside
         // the count.  The count is an acquire-release atomic: it publishes this
@@ -923,11 +951,16 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     uint32_t* ready = nullptr;
     LENS_CUDA(tmps.get(&mom, n_nodes * sizeof(dbl4)));
     LENS_CUDA(tmps.get(&q2, n_nodes * sizeof(double2)));
+    MomentsOut mo{mom, q2, nullptr, nullptr};
+    if (sizeof(T) == 4) {
+        LENS_CUDA(tmps.get(&mo.momf, n_nodes * sizeof(float4)));
+        LENS_CUDA(tmps.get(&mo.q2f, n_nodes * sizeof(float2)));
+    }
     LENS_CUDA(tmps.get(&ready, n_nodes * sizeof(uint32_t)));
     LENS_CUDA(cudaMemsetAsync(ready, 0, n_nodes * sizeof(uint32_t), s));
     const double inv_theta2 = t->theta > 0.0 ? 1.0 / (t->theta * t->theta) : INFINITY;
     { k_moments_up<T><<<GN, TB, 0, s>>>(n_nodes, st.node_level, first_bfs, st.link, st.parent, sorted, K, rb,
-                                      inv_theta2, mom, q2, (T4*)st.nodeA, (T2*)st.nodeB, st.node_rcm, ready);
+                                      inv_theta2, mo, (T4*)st.nodeA, (T2*)st.nodeB, st.node_rcm, ready);
       note_launch(); }
 
     // records
