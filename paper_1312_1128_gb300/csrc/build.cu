@@ -231,22 +231,32 @@ __device__ __forceinline__ int first_level(const uint64_t* K, int64_t j)
     return j == 0 ? 0 : lcp_digits(K[j - 1], K[j]) + 1;
 }
 
-__global__ void k_nodes(const uint64_t* K, int64_t n, const uint8_t* Lp, const uint32_t* off,
-                        uint32_t n_nodes, uint32_t* lvl, uint32_t* first, uint32_t* count,
-                        uint32_t* skip, uint8_t* isleaf)
+// The boxes in preorder, one thread per box (balanced: a particle may start
+// up to 25 boxes, most start none): k_owner writes, for every box, the
+// particle that starts it; k_nodes_by_box then finds the box's level and
+// run.
+__global__ void k_owner(int64_t n, const uint32_t* off, uint32_t* owner)
 {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    int L = Lp[j], s = first_level(K, j);
-    for (int l = s; l <= L; ++l) {
-        uint32_t v = off[j] + (uint32_t)(l - s);
-        int64_t e = run_end(K, n, j, l);
-        lvl[v] = (uint32_t)l;
-        first[v] = (uint32_t)j;
-        count[v] = (uint32_t)(e - j);
-        isleaf[v] = l == L ? 1 : 0;
-        skip[v] = e < n ? off[e] : n_nodes;
-    }
+    const uint32_t a = off[j], b = off[j + 1];
+    for (uint32_t v = a; v < b; ++v) owner[v] = (uint32_t)j;
+}
+
+__global__ void k_nodes_by_box(const uint64_t* K, int64_t n, const uint8_t* Lp, const uint32_t* off,
+                               const uint32_t* owner, uint32_t n_nodes, uint32_t* lvl, uint32_t* first,
+                               uint32_t* count, uint32_t* skip, uint8_t* isleaf)
+{
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_nodes) return;
+    const int64_t j = owner[v];
+    const int l = first_level(K, j) + (int)(v - off[j]);
+    const int64_t e = run_end(K, n, j, l);
+    lvl[v] = (uint32_t)l;
+    first[v] = (uint32_t)j;
+    count[v] = (uint32_t)(e - j);
+    isleaf[v] = l == Lp[j] ? 1 : 0;
+    skip[v] = e < n ? off[e] : n_nodes;
 }
 
 __global__ void k_nchild(uint32_t n_nodes, const uint8_t* isleaf, const uint32_t* skip,
@@ -906,7 +916,12 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     LENS_CUDA(tmps.get(&nchild, n_nodes));
     LENS_CUDA(cudaMemsetAsync(counters, 0, 4 * sizeof(uint32_t), s));
     LENS_CUDA(cudaMemsetAsync(level_start, 0xff, (kMaxDepth + 2) * sizeof(uint32_t), s));
-    { k_nodes<<<G, TB, 0, s>>>(K, n, Lp, off, n_nodes, lvl, first, count, skip, isleaf); note_launch(); }
+    {
+        uint32_t* owner = lv1;  // free until the level sort
+        { k_owner<<<G, TB, 0, s>>>(n, off, owner); note_launch(); }
+        { k_nodes_by_box<<<GN, TB, 0, s>>>(K, n, Lp, off, owner, n_nodes, lvl, first, count, skip, isleaf);
+          note_launch(); }
+    }
     { k_nchild<<<GN, TB, 0, s>>>(n_nodes, isleaf, skip, nchild, t->d_err); note_launch(); }
     // breadth-first order: stable sort of preorder ids by level
     LENS_CUDA(cudaMemcpyAsync(lv0, lvl, n_nodes * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
