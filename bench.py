@@ -609,9 +609,10 @@ class Microlensing(Workload):
 
 class Fit(Workload):
     """Lens fit: 1e5 Gaussians (r_sm 0.01), 1000^2 grid, theta 0.3; step =
-    build + forward alpha + adjoint of L = sum |alpha - alpha_t|^2.  The
-    adjoint is the dominant kernel: the line's roofline describes it, the
-    forward walk's is reported beside it."""
+    build + forward alpha (keeping its interaction lists) + adjoint of
+    L = sum |alpha - alpha_t|^2 (replaying them).  The adjoint is the
+    dominant kernel: the line's roofline describes it, the forward walk's is
+    reported beside it."""
     name = "fit_1e5_1000sq"
     FLOPS = FLOPS_ALPHA
 
@@ -662,12 +663,12 @@ class Fit(Workload):
         L = self.L
         lens = L.Lens([L.Species.gauss(self.parts, self.w["q"])], theta=self.theta, group_rays=self.group,
                       walk=self.walk, tile=self.tile)
-        lens.shoot(self.rx, self.ry, flags=flags | L.ALPHA_ONLY, out=self.outs)
+        lens.shoot(self.rx, self.ry, flags=flags | L.ALPHA_ONLY | L.KEEP_LISTS, out=self.outs)
         g1 = 2 * (self.outs[0] - self.at[0])
         g2 = 2 * (self.outs[1] - self.at[1])
         self.grad.zero_()
         self.back_ev[0].record()
-        lens.backward(self.rx, self.ry, g1, g2, grads=[self.grad])
+        lens.backward(self.rx, self.ry, g1, g2, grads=[self.grad], flags=L.KEEP_LISTS)
         self.back_ev[1].record()
         return lens
 
@@ -680,10 +681,11 @@ class Fit(Workload):
             d.copy_(h, non_blocking=True)
         lens = L.Lens([L.Species.gauss(self.d[0], w["q"])], theta=self.theta, group_rays=self.group,
                       walk=self.walk, tile=self.tile)
-        lens.shoot(self.d[1], self.d[2], flags=L.ALPHA_ONLY, out=self.outs)
+        lens.shoot(self.d[1], self.d[2], flags=L.ALPHA_ONLY | L.KEEP_LISTS, out=self.outs)
         r1, r2 = self.outs[0] - self.at[0], self.outs[1] - self.at[1]
         self.grad.zero_()
-        lens.backward(self.d[1], self.d[2], (2 * r1).contiguous(), (2 * r2).contiguous(), grads=[self.grad])
+        lens.backward(self.d[1], self.d[2], (2 * r1).contiguous(), (2 * r2).contiguous(), grads=[self.grad],
+                      flags=L.KEEP_LISTS)
         self.hloss.copy_((r1 * r1 + r2 * r2).sum().reshape(1), non_blocking=True)
         self.hgrad.copy_(self.grad, non_blocking=True)
         return lens, sum(x.numel() * 4 for x in self.h), self.hgrad.numel() * 4 + 4

@@ -84,8 +84,10 @@ enum {
     LENS_ACCUMULATE = 4,  /* add to the output arrays instead of overwriting them           */
     LENS_USE_GRAPH = 8,   /* lens_shoot_batches: replay a cached CUDA graph of the launch    */
     LENS_COUNT = 16,      /* accumulate walk interaction counters (lens_tree_counters)     */
-    LENS_TIMING = 32      /* time the grouping and walk kernels (lens_last_timing); not with *
+    LENS_TIMING = 32,     /* time the grouping and walk kernels (lens_last_timing); not with *
                            * LENS_USE_GRAPH (time a replay with events on the caller's stream) */
+    LENS_KEEP_LISTS = 64  /* lens_shoot_rays: keep the walk's interaction lists for the     *
+                           * adjoint; lens_shoot_rays_backward: replay them (see there)     */
 };
 
 /* One particle species: a homogeneous set of particles of one kind (Sec. 3.1
@@ -203,7 +205,15 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species,
  *       tree, double for an FP64 tree.  kappa, gamma1, gamma2 may be NULL
  *       only with LENS_ALPHA_ONLY.
  *   flags: LENS_ALPHA_ONLY, LENS_DIRECT, LENS_ACCUMULATE, LENS_COUNT,
- *       LENS_TIMING.
+ *       LENS_TIMING, LENS_KEEP_LISTS.  LENS_KEEP_LISTS (tree walk) also
+ *       stores, per ray group, the walk's interaction lists -- the cells it
+ *       accepted, the leaves it opened and the boxes whose big lists reach
+ *       the group, as tagged box indices, up to 512 per 32 rays -- for a
+ *       following lens_shoot_rays_backward on the same rays; they replace
+ *       the lists of the previous such call and are kept with the tree
+ *       (4 B per entry: 2 KB per 32 rays, from cudaMalloc when they grow).
+ *       A group whose lists exceed the room is marked and walked again by
+ *       the adjoint.
  * A tree without particles (analytic components only) is shot one thread
  * per ray with no ray grouping, except with LENS_COUNT or LENS_TIMING, whose
  * counters and times refer to the grouped walk (the same terms either way).
@@ -255,6 +265,13 @@ lens_status lens_shoot_batches(lens_tree* tree, int64_t n_batches, const int64_t
  *       the lens_halo fields (GAUSS r_sm, q; NFW r_s, R_max; SIS r_E again,
  *       0; DISK R, 0; POINT 0, 0).
  *   flags: LENS_DIRECT differentiates the direct sum instead of the tree.
+ *       LENS_KEEP_LISTS: if the last lens_shoot_rays with LENS_KEEP_LISTS on
+ *       this tree had these very rays (same arrays, unchanged since, same
+ *       count, dtype and origin), the adjoint replays that call's
+ *       interaction lists instead of walking the tree again (the forward's
+ *       near field is recomputed, not stored); otherwise the flag has no
+ *       effect.  Changing the ray values in between is the caller's error:
+ *       the replayed lists then belong to the old rays.
  * Tree gradients with respect to masses and positions follow the tree's
  * moments (so they carry the tree's own approximation error); size and halo
  * parameter gradients equal the direct sum's, since every ray inside a

@@ -36,7 +36,7 @@ __all__ = ["Lens", "Species", "Halo", "LensError", "shoot", "lib", "fp32_peak", 
 POINT, GAUSS, NFW, SIS, DISK = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 PREC_FP32, PREC_FP64 = 0, 1
-ALPHA_ONLY, DIRECT, ACCUMULATE, USE_GRAPH, COUNT, TIMING = 1, 2, 4, 8, 16, 32
+ALPHA_ONLY, DIRECT, ACCUMULATE, USE_GRAPH, COUNT, TIMING, KEEP_LISTS = 1, 2, 4, 8, 16, 32, 64
 WALK_DEFAULT, WALK_WARP, WALK_PAIRS, WALK_TRIOS = 0, 1, 2, 3
 TILE_DEFAULT, TILE_STANDARD, TILE_LARGE = 0, 1, 2
 REFINE_KAPPA_GAMMA, REFINE_DEFLECTION = 0, 1

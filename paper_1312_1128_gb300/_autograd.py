@@ -8,10 +8,12 @@ import torch
 class _ShootAlpha(torch.autograd.Function):
     @staticmethod
     def forward(ctx, lens, dx, dy, origin, *species_data):
-        from . import ALPHA_ONLY
+        from . import ALPHA_ONLY, KEEP_LISTS
         if not lens.built_from(species_data):
             lens.rebuild(species_data)   # new values: the old tree's moments are stale
-        out = lens.shoot(dx, dy, origin=origin, flags=ALPHA_ONLY)
+        # the walk's interaction lists are kept for the adjoint (dx, dy are
+        # saved: autograd refuses a backward after they change in place)
+        out = lens.shoot(dx, dy, origin=origin, flags=ALPHA_ONLY | KEEP_LISTS)
         ctx.lens = lens
         ctx.origin = origin
         ctx.save_for_backward(dx, dy)
@@ -23,7 +25,8 @@ class _ShootAlpha(torch.autograd.Function):
         lens = ctx.lens
         g = g.to(lens.out_dtype)
         g1, g2 = g[:, 0].contiguous(), g[:, 1].contiguous()
-        grads = lens.backward(dx, dy, g1, g2, origin=ctx.origin)
+        from . import KEEP_LISTS
+        grads = lens.backward(dx, dy, g1, g2, origin=ctx.origin, flags=KEEP_LISTS)
         out = []
         for s, gr in zip(lens.species, grads):
             gd = torch.zeros_like(s.data)

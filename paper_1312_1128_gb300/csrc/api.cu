@@ -178,6 +178,8 @@ void lens_free_tree(lens_tree* t)
     if (t->d_err) cudaFree(t->d_err);
     if (t->ray_scratch.ptr) cudaFreeAsync(t->ray_scratch.ptr, 0);
     if (t->d_stats) cudaFree(t->d_stats);
+    if (t->list_ids) cudaFree(t->list_ids);
+    if (t->list_n) cudaFree(t->list_n);
     if (t->amr_ws && t->amr_free) t->amr_free(t->amr_ws);
     for (int i = 0; i < 3; ++i)
         if (t->ev[i]) cudaEventDestroy(t->ev[i]);
@@ -289,7 +291,8 @@ static lens_status check_outputs(const lens_tree* t, void* a1, void* a2, void* k
                                  int32_t flags, int64_t n)
 {
     if (!t) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
-    if (flags & ~(LENS_ALPHA_ONLY | LENS_DIRECT | LENS_ACCUMULATE | LENS_USE_GRAPH | LENS_COUNT | LENS_TIMING))
+    if (flags & ~(LENS_ALPHA_ONLY | LENS_DIRECT | LENS_ACCUMULATE | LENS_USE_GRAPH | LENS_COUNT | LENS_TIMING |
+                  LENS_KEEP_LISTS))
         return lens_set_error(LENS_ERR_INVALID_ARG, "unknown flag bits");
     if (n < 0 || n >= (1ll << 31)) return lens_set_error(LENS_ERR_INVALID_ARG, "n must be in [0, 2^31)");
     if (n == 0) return LENS_OK;
@@ -342,6 +345,7 @@ lens_status lens_shoot_batches(lens_tree* tree, int64_t n_batches, const int64_t
     LENS_TRY(check_batches(n_batches, offsets, origins));
     int64_t n = offsets[n_batches];
     LENS_TRY(check_outputs(tree, alpha1, alpha2, kappa, gamma1, gamma2, flags, n));
+    if (flags & LENS_KEEP_LISTS) return lens_set_error(LENS_ERR_INVALID_ARG, "LENS_KEEP_LISTS is for lens_shoot_rays");
     if (ray_dtype != LENS_F32 && ray_dtype != LENS_F64) return lens_set_error(LENS_ERR_INVALID_ARG, "bad ray dtype");
     if (n == 0) return LENS_OK;
     if (!ray_dx || !ray_dy) return lens_set_error(LENS_ERR_INVALID_ARG, "ray arrays are NULL");
@@ -362,7 +366,8 @@ lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double or
                                      int32_t flags, void* stream)
 {
     if (!tree) return lens_set_error(LENS_ERR_INVALID_ARG, "tree is NULL");
-    if (flags & ~(LENS_DIRECT)) return lens_set_error(LENS_ERR_INVALID_ARG, "backward accepts LENS_DIRECT only");
+    if (flags & ~(LENS_DIRECT | LENS_KEEP_LISTS))
+        return lens_set_error(LENS_ERR_INVALID_ARG, "backward accepts LENS_DIRECT and LENS_KEEP_LISTS only");
     if (n < 0 || n >= (1ll << 31)) return lens_set_error(LENS_ERR_INVALID_ARG, "n must be in [0, 2^31)");
     if (g_kappa || g_gamma1 || g_gamma2)
         return lens_set_error(LENS_ERR_UNSUPPORTED, "gradients of kappa and gamma are not implemented");

@@ -77,6 +77,12 @@ template <typename T> struct BackParams {
     // gradients are sums of atomics, so a slice needs no partial buffer.
     const uint32_t* heavy_hdr;
     const uint32_t* heavy;
+    // the forward's kept interaction lists (LENS_KEEP_LISTS), or null: group
+    // g replays list_ids[g * list_K ...] (list_n[g] entries) instead of
+    // walking the tree, unless list_n[g] is kListOverflow
+    const uint32_t* list_ids;
+    const uint32_t* list_n;
+    int list_K;
 };
 
 constexpr int kMaxGroup = 64;
@@ -460,6 +466,46 @@ LENS_DEV void back_append_big(BackCtx<KIND, T>& C, bool has, int v, int z, int w
     }
 }
 
+// One step of boxes (one per lane): an accepted cell goes to the far buffer
+// (this item's share of them), an opened leaf's particles and a big list that
+// reaches the group to theirs.  The tree walk and the replay of kept lists
+// both feed it.
+template <int KIND, typename T>
+LENS_DEV void back_step(BackCtx<KIND, T>& C, int v, bool acc, bool leaf, bool big_has, const vec4_t<T>& A,
+                        const int4& Lk, T dxv, T dyv, int& nf, int& nn, int& nb)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const BackParams<T>& P = C.P;
+    BackShared<KIND, T>& S = C.S;
+    unsigned ball = __ballot_sync(full, acc);
+    bool take = acc;  // this slice's share of the accepted cells
+    if (C.ns > 1) {
+        const int q = C.seq_f + __popc(ball & ((1u << lane) - 1u));
+        C.seq_f += __popc(ball);
+        take = acc && q % C.ns == C.sl;
+        ball = __ballot_sync(full, take);
+    }
+    if (take) {
+        int pos = nf + __popc(ball & ((1u << lane) - 1u));
+        v2_t<T> Q = P.nodeB[v];
+        S.fdx[pos] = dxv;
+        S.fdy[pos] = dyv;
+        S.fM[pos] = A.z;
+        S.fqr[pos] = Q.x;
+        S.fqi[pos] = Q.y;
+        S.fnode[pos] = v;
+    }
+    nf += __popc(ball);
+    back_append_near<KIND, T>(C, leaf ? (Lk.y & kCountMask) : 0, Lk.x, nn, P.leaf0, P.leaf1);
+    if constexpr (KIND != LENS_POINT) back_append_big<KIND, T>(C, big_has, v, Lk.z, Lk.w, nb);
+    __syncwarp();
+    if (nf >= 32) {
+        C.flush_far(nf);
+        nf = 0;
+    }
+}
+
 template <int KIND, typename T, bool DIRECT>
 __global__ void __launch_bounds__(kWalkWarps * 32)
 back_kernel(BackParams<T> P)
@@ -528,64 +574,82 @@ back_kernel(BackParams<T> P)
                 }
                 C.flush_near(nn);
             } else {
+                // boxes 32 at a time, either replayed from the forward's kept
+                // lists of this group or found by walking the tree; one copy of
+                // the step's code serves both (the kernel's code stays small)
+                const uint32_t ln = P.list_n ? P.list_n[g] : kListOverflow;
+                const bool replay = ln != kListOverflow;
+                const uint32_t* ids = P.list_ids + (int64_t)g * P.list_K;
                 int nf = 0, sp = 1;
-                if (lane == 0) stack[0] = 0;
-                __syncwarp();
-                while (sp > 0) {
-                    int k = sp < 32 ? sp : 32;
-                    sp -= k;
-                    int v = lane < k ? stack[sp + lane] : -1;
+                uint32_t base = 0;
+                // replay: entries read two steps ahead, their boxes one step
+                // ahead (the lists come from DRAM, not from L1 like a stack)
+                uint32_t e0 = 0u, e1 = 0u;
+                int4 Lk1 = make_int4(0, 0, 0, 0);
+                vec4_t<T> A1{};
+                if (replay) {
+                    e0 = lane < ln ? __ldcs(ids + lane) : 0u;
+                    e1 = 32 + lane < ln ? __ldcs(ids + 32 + lane) : 0u;
+                    if (e0) Lk1 = P.link[e0 & kListIdMask];
+                    if (e0 & kListFar) A1 = P.nodeA[e0 & kListIdMask];
+                } else {
+                    if (lane == 0) stack[0] = 0;
                     __syncwarp();
-                    bool valid = v >= 0, acc = false, leaf = false, open = false;
-                    vec4_t<T> A;
+                }
+                while (replay ? base < ln : sp > 0) {
+                    int v = -1;
+                    bool acc = false, leaf = false, big = false;
+                    vec4_t<T> A{};
                     int4 Lk = make_int4(0, 0, 0, 0);
                     T dxv = T(0), dyv = T(0);
-                    if (valid) {
-                        A = P.nodeA[v];
-                        Lk = P.link[v];
-                        dxv = A.x - C.H.x;
-                        dyv = A.y - C.H.y;
-                        T ex = fmax(fabs(dxv - C.box.x) - C.box.z, T(0));
-                        T ey = fmax(fabs(dyv - C.box.y) - C.box.w, T(0));
-                        acc = fma(ex, ex, ey * ey) > A.w;
-                        leaf = !acc && (Lk.y & kLeafBit);
-                        open = !acc && !leaf;
+                    if (replay) {
+                        const uint32_t e = e0;
+                        Lk = Lk1;
+                        A = A1;
+                        const uint32_t e2 = base + 64 + lane < ln ? __ldcs(ids + base + 64 + lane) : 0u;
+                        Lk1 = e1 ? P.link[e1 & kListIdMask] : make_int4(0, 0, 0, 0);
+                        if (e1 & kListFar) A1 = P.nodeA[e1 & kListIdMask];
+                        e0 = e1;
+                        e1 = e2;
+                        base += 32;
+                        v = (int)(e & kListIdMask);
+                        acc = (e & kListFar) != 0u;
+                        leaf = (e & kListLeaf) != 0u;
+                        big = (e & kListBig) != 0u;
+                        if (acc) {
+                            dxv = A.x - C.H.x;
+                            dyv = A.y - C.H.y;
+                        }
+                    } else {
+                        int k = sp < 32 ? sp : 32;
+                        sp -= k;
+                        v = lane < k ? stack[sp + lane] : -1;
+                        __syncwarp();
+                        const bool valid = v >= 0;
+                        bool open = false;
+                        if (valid) {
+                            A = P.nodeA[v];
+                            Lk = P.link[v];
+                            dxv = A.x - C.H.x;
+                            dyv = A.y - C.H.y;
+                            T ex = fmax(fabs(dxv - C.box.x) - C.box.z, T(0));
+                            T ey = fmax(fabs(dyv - C.box.y) - C.box.w, T(0));
+                            acc = fma(ex, ex, ey * ey) > A.w;
+                            leaf = !acc && (Lk.y & kLeafBit);
+                            open = !acc && !leaf;
+                        }
+                        big = valid && Lk.w > 0;
+                        int nc = open ? Lk.y : 0;
+                        int totc;
+                        int offc = warp_exclusive_scan(nc, &totc);
+                        if (sp + totc > kStackCap) {
+                            if (lane == 0) atomicOr(P.err, DERR_STACK_OVERFLOW);
+                            break;
+                        }
+                        for (int c = 0; c < nc; ++c) stack[sp + offc + c] = Lk.x + c;
+                        sp += totc;
                     }
-                    unsigned ball = __ballot_sync(full, acc);
-                    bool take = acc;  // this slice's share of the accepted cells
-                    if (C.ns > 1) {
-                        const int q = C.seq_f + __popc(ball & ((1u << lane) - 1u));
-                        C.seq_f += __popc(ball);
-                        take = acc && q % C.ns == C.sl;
-                        ball = __ballot_sync(full, take);
-                    }
-                    if (take) {
-                        int pos = nf + __popc(ball & ((1u << lane) - 1u));
-                        v2_t<T> Q = P.nodeB[v];
-                        S.fdx[pos] = dxv;
-                        S.fdy[pos] = dyv;
-                        S.fM[pos] = A.z;
-                        S.fqr[pos] = Q.x;
-                        S.fqi[pos] = Q.y;
-                        S.fnode[pos] = v;
-                    }
-                    nf += __popc(ball);
-                    int nc = open ? Lk.y : 0;
-                    int totc;
-                    int offc = warp_exclusive_scan(nc, &totc);
-                    if (sp + totc > kStackCap) {
-                        if (lane == 0) atomicOr(P.err, DERR_STACK_OVERFLOW);
-                        break;
-                    }
-                    for (int c = 0; c < nc; ++c) stack[sp + offc + c] = Lk.x + c;
-                    sp += totc;
-                    back_append_near<KIND, T>(C, leaf ? (Lk.y & kCountMask) : 0, Lk.x, nn, P.leaf0, P.leaf1);
-                    if constexpr (KIND != LENS_POINT) back_append_big<KIND, T>(C, valid && Lk.w > 0, v, Lk.z, Lk.w, nb);
-                    __syncwarp();
-                    if (nf >= 32) {
-                        C.flush_far(nf);
-                        nf = 0;
-                    }
+                    back_step<KIND, T>(C, v, acc, leaf, big, A, Lk, dxv, dyv, nf, nn, nb);
                 }
                 C.flush_far(nf);
                 C.flush_near(nn);
@@ -814,6 +878,10 @@ static lens_status backward_typed(lens_tree* t, double ox, double oy, const void
     P.order = hp.order;
     P.heavy_hdr = hp.hdr;
     P.heavy = hp.table;
+    const uint32_t* lists = ((flags & LENS_KEEP_LISTS) && !(flags & LENS_DIRECT)) ? kept_lists(t, key) : nullptr;
+    P.list_ids = lists;
+    P.list_n = lists ? t->list_n : nullptr;
+    P.list_K = lists ? t->list_K : 0;
     if (hp.hdr) LENS_CUDA(cudaMemcpyAsync(t->d_stats + 8, hp.hdr, 2 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     else LENS_CUDA(cudaMemsetAsync(t->d_stats + 8, 0, 2 * sizeof(uint32_t), s));
     P.ga1 = (const T*)g[0];

@@ -75,6 +75,8 @@ template <int KIND, typename T, int R> struct PsiCtx {
     v2_t<T> H;
     vec4_t<T> box;
     int nf = 0, nn = 0, nb = 0;
+    uint32_t* rec = nullptr;  // (the potential keeps no interaction lists)
+    int rec_n = 0, rec_cap = 0;
     T lx[R], ly[R];
     T part[R][3];              // psi, alpha1, alpha2 of the current flush
     T tot_s[R][3], tot_c[R][3];  // compensated totals

@@ -98,6 +98,17 @@ struct lens_tree {
     int64_t cost_n = -1;
     int cost_dtype = -1, cost_R = 0;
     double cost_ox = 0, cost_oy = 0;
+    // interaction lists kept by the last lens_shoot_rays with LENS_KEEP_LISTS
+    // (walk_dev.cuh tags), for the rays identified as for the work record
+    uint32_t* list_ids = nullptr;  // list_groups x list_K tagged box indices
+    uint32_t* list_n = nullptr;    // per group: entries, or kListOverflow
+    int64_t list_groups = 0;
+    int list_K = 0;
+    const void* list_dx = nullptr;
+    const void* list_dy = nullptr;
+    int64_t list_rays = -1;
+    int list_dtype = -1, list_R = 0;
+    double list_ox = 0, list_oy = 0;
     bool timed = false;
     void* noalloc_scratch = nullptr;        // device address of the no-alloc scratch array (walk.cu)
     void* amr_ws = nullptr;                 // image-finding workspace (amr.cu), kept between calls

@@ -392,7 +392,12 @@ walk_kernel(WalkParams<T> P)
                 }
                 C.flush_near();
             } else {
-                traverse(C, stack, c_vis, c_acc, c_near, c_bigs, c_bigk);
+                C.rec = P.list_ids ? P.list_ids + (int64_t)g * P.list_K : nullptr;
+                C.rec_n = 0;
+                C.rec_cap = P.list_K;
+                const bool whole = traverse(C, stack, c_vis, c_acc, c_near, c_bigs, c_bigk);
+                if (C.rec && lane == 0)
+                    P.list_n[g] = whole && C.rec_n <= C.rec_cap ? (uint32_t)C.rec_n : kListOverflow;
                 C.flush_far();
                 C.flush_near();
                 if constexpr (KIND != LENS_POINT) C.flush_big();
@@ -707,6 +712,9 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
     const uint32_t* order = record ? heavy_first_order<T>(t, plan, key, 0, s).order : nullptr;
     uint32_t* gcost = record ? (uint32_t*)(base + L.gcost) : nullptr;
     if (gcost) LENS_CUDA(cudaMemsetAsync(gcost, 0, ng * sizeof(uint32_t), s));
+    // interaction lists for the adjoint (room made by the caller, shoot())
+    const bool keep = record && (flags & LENS_KEEP_LISTS) && t->list_ids && t->list_groups >= (int64_t)ng;
+    if (keep) LENS_CUDA(cudaMemsetAsync(t->list_n, 0xff, ng * sizeof(uint32_t), s));  // kListOverflow
 
     if (timing) LENS_CUDA(cudaEventRecord(t->ev[1], s));
     WalkParams<T> P{};
@@ -718,6 +726,9 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
     P.wait_cycles = t->wait_cycles;
     P.order = order;
     P.gcost = gcost;
+    P.list_ids = keep ? t->list_ids : nullptr;
+    P.list_n = keep ? t->list_n : nullptr;
+    P.list_K = keep ? t->list_K : 0;
     for (int q = 0; q < 5; ++q) P.out[q] = (T*)out[q];
     const bool ao = (flags & LENS_ALPHA_ONLY) != 0;
     const bool direct = (flags & LENS_DIRECT) != 0;
@@ -786,6 +797,15 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
         t->timed = true;
     }
     if (record) set_cost_key(t, key);
+    if (keep) {
+        t->list_dx = key.dx;
+        t->list_dy = key.dy;
+        t->list_rays = key.n;
+        t->list_dtype = key.dtype;
+        t->list_R = key.R;
+        t->list_ox = key.ox;
+        t->list_oy = key.oy;
+    }
     LENS_CUDA(cudaGetLastError());
     return LENS_OK;
 }
@@ -797,12 +817,52 @@ lens_status enqueue_shoot(lens_tree* t, const ShootPlan& plan, const void* dx, c
     return enqueue_typed<float>(t, plan, dx, dy, dtype, out, flags, s);
 }
 
+// Room for the interaction lists of ng groups of R * 32 rays (512 entries
+// per 32 rays).  The old lists are dropped.
+static lens_status reserve_lists(lens_tree* t, int64_t ng, int R, cudaStream_t s)
+{
+    const int K = 512 * R;
+    t->list_rays = -1;  // whatever is kept belongs to no rays until the walk records
+    if (t->list_ids && t->list_groups >= ng && t->list_K == K) return LENS_OK;
+    LENS_CUDA(cudaStreamSynchronize(s));  // the old lists may still be read
+    if (t->list_ids) cudaFree(t->list_ids);
+    if (t->list_n) cudaFree(t->list_n);
+    t->list_ids = t->list_n = nullptr;
+    t->list_groups = 0;
+    LENS_CUDA(lens_malloc((void**)&t->list_ids, (size_t)ng * K * sizeof(uint32_t)));
+    cudaError_t e = lens_malloc((void**)&t->list_n, (size_t)ng * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaFree(t->list_ids);
+        t->list_ids = nullptr;
+        return lens_cuda_check(e, "cudaMalloc(lists)");
+    }
+    t->list_groups = ng;
+    t->list_K = K;
+    return LENS_OK;
+}
+
 lens_status shoot(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig, const void* dx,
                   const void* dy, int dtype, void* const out[5], int flags, cudaStream_t s)
 {
     ShootPlan plan;
     LENS_TRY(upload_batches(t, nb, h_off, h_orig, s, &plan));
+    // kept lists hold box indices in 29 bits
+    bool small_tree = true;
+    for (const auto& st : t->sp) small_tree = small_tree && st.n_nodes < (int64_t)kListIdMask;
+    if ((flags & LENS_KEEP_LISTS) && !(flags & LENS_DIRECT) && nb == 1 && plan.n > 0 && small_tree)
+        LENS_TRY(reserve_lists(t, (int64_t)plan.ng, plan.R, s));
+    else
+        flags &= ~LENS_KEEP_LISTS;
     return enqueue_shoot(t, plan, dx, dy, dtype, out, flags, s);
+}
+
+// The kept interaction lists if they belong to these rays, else null.
+const uint32_t* kept_lists(const lens_tree* t, const RayKey& k)
+{
+    if (!t->list_ids || t->list_rays < 0) return nullptr;
+    const bool same = t->list_dx == k.dx && t->list_dy == k.dy && t->list_rays == k.n && t->list_dtype == k.dtype &&
+                      t->list_R == k.R && t->list_ox == k.ox && t->list_oy == k.oy;
+    return same ? t->list_ids : nullptr;
 }
 
 // Scratch views shared with the backward walk.

@@ -48,7 +48,26 @@ template <typename T> struct WalkParams {
     // order[g] (identity if null); the walk adds each group's work to gcost[g]
     const uint32_t* order;
     uint32_t* gcost;
+    // interaction lists kept for the adjoint (LENS_KEEP_LISTS): group g's
+    // tagged box indices at list_ids + g * list_K, their count in list_n[g]
+    uint32_t* list_ids;
+    uint32_t* list_n;
+    int list_K;
 };
+
+// Record one traversal step's boxes that matter to the adjoint (one entry
+// per box, lane order) into the context's list, if it keeps one.
+template <class Ctx>
+LENS_DEV void record_step(Ctx& C, int v, bool acc, bool leaf, bool big)
+{
+    if (!C.rec) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t tag = (acc ? kListFar : 0u) | (leaf ? kListLeaf : 0u) | (big ? kListBig : 0u);
+    const unsigned m = __ballot_sync(0xffffffffu, tag != 0u);
+    const int pos = C.rec_n + __popc(m & ((1u << lane) - 1u));
+    if (tag != 0u && pos < C.rec_cap) C.rec[pos] = (uint32_t)v | tag;
+    C.rec_n += __popc(m);
+}
 
 // The shared-memory tiles of the near field: TILE 0 holds kNearCap leaf
 // particles and kBigCap big-list entries per warp, TILE 1 twice as many
@@ -380,6 +399,8 @@ template <int KIND, typename T, int R, bool AO, int TILE = 0> struct WalkCtx : W
     static constexpr int kNear = Buf::kNear, kBig = Buf::kBig;
     WalkRanges* Rg;
     int nf = 0, nn = 0, nb = 0;  // entries in the far, near and big buffers
+    uint32_t* rec = nullptr;     // the group's kept interaction list, or null
+    int rec_n = 0, rec_cap = 0;
 
     LENS_DEV WalkCtx(const WalkParams<T>& p, WalkShared<KIND, T, TILE>& s)
         : WalkEval<KIND, T, R, AO, TILE>(p, &s.buf, &s.tot), Rg(&s.rng) {}
@@ -465,7 +486,7 @@ template <int KIND, typename T> LENS_DEV int big_used(int nbuf)
 // entries of the chunks that pass are tested one by one; entries whose
 // support reaches the group's box are appended to the big buffer.
 template <class Ctx, typename T = typename Ctx::value_type>
-LENS_DEV void append_big(Ctx& C, bool has, int v, int z, int w, int& n_seen, int& n_kept)
+LENS_DEV bool append_big(Ctx& C, bool has, int v, int z, int w, int& n_seen, int& n_kept)
 {
     constexpr int KIND = Ctx::kKind;
     const unsigned full = 0xffffffffu;
@@ -478,7 +499,7 @@ LENS_DEV void append_big(Ctx& C, bool has, int v, int z, int w, int& n_seen, int
     }
     int tot;
     int off = warp_exclusive_scan(cnt, &tot);
-    if (tot == 0) return;
+    if (tot == 0) return false;
     C.Rg->rs_off[lane] = off;
     C.Rg->rs_first[lane] = z;
     C.Rg->rs_end[lane] = z + w;
@@ -563,6 +584,7 @@ LENS_DEV void append_big(Ctx& C, bool has, int v, int z, int w, int& n_seen, int
             __syncwarp();
         }
     }
+    return cnt > 0;
 }
 
 
@@ -626,7 +648,9 @@ LENS_DEV bool traverse(Ctx& C, int* stack, int& c_vis, int& c_acc, int& c_near, 
         for (int c = 0; c < nc; ++c) stack[sp + offc + c] = Lk.x + c;
         sp += totc;
         append_ranges(C, leaf ? (Lk.y & kCountMask) : 0, Lk.x, P.leaf0, P.leaf1, c_near, c_dummy);
-        if constexpr (KIND != LENS_POINT) append_big(C, valid && Lk.w > 0, v, Lk.z, Lk.w, c_bigs, c_bigk);
+        bool big = false;
+        if constexpr (KIND != LENS_POINT) big = append_big(C, valid && Lk.w > 0, v, Lk.z, Lk.w, c_bigs, c_bigk);
+        record_step(C, v, acc, leaf, big);
         __syncwarp();
         if (C.nf >= 32) {
             C.flush_far();

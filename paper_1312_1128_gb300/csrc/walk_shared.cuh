@@ -47,6 +47,12 @@ struct Layout {
         stack, split, gcost, heavy, total;
 };
 
+// Tags of a kept interaction-list entry (LENS_KEEP_LISTS): the box's index
+// in the low 29 bits; a box may be accepted (far cell) or an opened leaf, and
+// its big list may reach the group as well.
+constexpr uint32_t kListFar = 1u << 31, kListLeaf = 1u << 30, kListBig = 1u << 29, kListIdMask = kListBig - 1u;
+constexpr uint32_t kListOverflow = 0xffffffffu;  // list_n value of a group whose lists did not fit
+
 // Split heavy groups (heavy_first_order): at most kHeavyGroups groups, each
 // in at most 32 slices; the plan's table holds one entry per slice.
 constexpr int kHeavyGroups = 1024, kHeavyItems = kHeavyGroups * 32;
@@ -128,6 +134,10 @@ struct HeavyPlan {
 template <typename T>
 HeavyPlan heavy_first_order(lens_tree* t, const ShootPlan& plan, const RayKey& key, int64_t n_warps,
                             cudaStream_t s);
+
+// The interaction lists kept by the last LENS_KEEP_LISTS walk if they belong
+// to these rays (walk.cu), else null.
+const uint32_t* kept_lists(const lens_tree* t, const RayKey& k);
 
 lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s);
 lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig,

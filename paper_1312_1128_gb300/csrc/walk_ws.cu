@@ -110,6 +110,8 @@ template <int KIND, typename T, int CONS> struct WsProducer {
     int g = 0;
     uint32_t use = 0;  // slots handed over so far
     bool alive = true;
+    uint32_t* rec = nullptr;  // the group's kept interaction list, or null
+    int rec_n = 0, rec_cap = 0;
 
     LENS_DEV WsProducer(const WalkParams<T>& p, WsPair<KIND, T, CONS>& w) : P(p), W(w), Rg(&w.rng) {}
 
@@ -173,9 +175,13 @@ LENS_DEV void ws_produce(const WalkParams<T>& P, WsPair<KIND, T, CONS>& W, int* 
         C.H = P.gH[g];
         C.box = P.gbox[g];
         int c_vis = 0, c_acc = 0, c_near = 0, c_bigs = 0, c_bigk = 0;
-        traverse(C, stack, c_vis, c_acc, c_near, c_bigs, c_bigk);
+        C.rec = P.list_ids ? P.list_ids + (int64_t)g * P.list_K : nullptr;
+        C.rec_n = 0;
+        C.rec_cap = P.list_K;
+        const bool whole = traverse(C, stack, c_vis, c_acc, c_near, c_bigs, c_bigk);
         C.handoff(kWsLast);
         if (!C.alive) return;
+        if (C.rec && lane == 0) P.list_n[g] = whole && C.rec_n <= C.rec_cap ? (uint32_t)C.rec_n : kListOverflow;
         if (P.gcost && lane == 0) P.gcost[g] += (uint32_t)(c_vis + c_acc + c_near + c_bigk);
         if (P.stats && lane == 0) {
             unsigned long long nr = P.grange[g].y;

@@ -19,7 +19,10 @@ Eq. lens_eq):
 * through torch.autograd, including a rebuild after an in-place update;
 * after a forward call on the same rays, the adjoint splits the heaviest
   ray groups into slices: particle, cell and halo gradients equal those of
-  an unsplit adjoint up to the order of the FP64 atomic sums.
+  an unsplit adjoint up to the order of the FP64 atomic sums;
+* with LENS_KEEP_LISTS the adjoint replays the forward's interaction lists
+  instead of walking the tree: the same gradients up to that order; lists
+  of other rays are not replayed.
 """
 import numpy as np
 import pytest
@@ -375,3 +378,44 @@ def test_split_heavy_groups_same_gradient(n_part, grid, theta):
         err = np.abs(got[:, k] - ref[:, k]).max()
         assert err <= 1e-6 * scale, (k, err, scale)
     np.testing.assert_allclose(hgot, href, rtol=1e-10, atol=1e-12 * np.abs(href).max())
+
+
+@pytest.mark.parametrize("n_part,grid", [(20000, 128), (100_000, 1000)])
+def test_kept_lists_same_gradient(n_part, grid):
+    parts = lensgen.nfw_particles(n_part, 93, fixed_sigma=0.01)
+    rx, ry = lensgen.grid_rays(grid, -1.0, 1.0, dtype=np.float32)
+    g = lensgen.rng(94)
+    g1 = cu((0.01 * g.standard_normal(rx.size)).astype(np.float32))
+    g2 = cu((0.01 * g.standard_normal(rx.size)).astype(np.float32))
+    halos = [L.Halo.nfw(-0.1, 0.04, 0.05, 0.08, 0.4)]
+    dx, dy = cu(rx), cu(ry)
+
+    def grads(lens, flags, gx=dx, gy=dy):
+        gh = torch.zeros(1, 5, dtype=torch.float64, device="cuda")
+        (gr,) = lens.backward(gx, gy, g1, g2, g_halos=gh, flags=flags)
+        return gr.double().cpu().numpy(), gh.cpu().numpy()
+
+    lens = L.Lens([L.Species.gauss(cu(parts), 3.0)], halos, theta=0.3)
+    ref, href = grads(lens, 0)                       # the tree walk
+    lens.shoot(dx, dy, flags=L.ALPHA_ONLY | L.KEEP_LISTS)
+    got, hgot = grads(lens, L.KEEP_LISTS)            # the replay
+    for k in range(4):
+        scale = np.abs(ref[:, k]).max()
+        assert np.abs(got[:, k] - ref[:, k]).max() <= 1e-6 * scale, k
+    np.testing.assert_allclose(hgot, href, rtol=1e-10, atol=1e-12 * np.abs(href).max())
+    # other rays (another array): the kept lists are not theirs, the walk runs
+    dx2, dy2 = (dx * 0.9).contiguous(), (dy * 0.9).contiguous()
+    ref2, _ = grads(L.Lens([L.Species.gauss(cu(parts), 3.0)], halos, theta=0.3), 0, dx2, dy2)
+    got2, _ = grads(lens, L.KEEP_LISTS, dx2, dy2)
+    for k in range(4):
+        assert np.abs(got2[:, k] - ref2[:, k]).max() <= 1e-6 * np.abs(ref2[:, k]).max(), k
+    # the same array moved in place (the caller's error the API names): the
+    # replayed lists belong to the old rays, so the replay path is the one taken
+    lens.shoot(dx, dy, flags=L.ALPHA_ONLY | L.KEEP_LISTS)
+    dx.add_(0.05)
+    moved, _ = grads(lens, L.KEEP_LISTS)
+    walked, _ = grads(lens, 0)
+    assert np.abs(moved - walked).max() > 1e-3 * np.abs(walked).max()
+    with pytest.raises(L.LensError):
+        lens.shoot_batches(np.array([0, rx.size]), np.zeros((1, 2)), dx, dy, flags=L.KEEP_LISTS)
+    lens.close()
