@@ -1507,10 +1507,32 @@ def run_once(args):
     """One build + shoot of the headline's lens (profiling: `ncu ... python
     bench.py --once`); with --workload potential, one potential shot; with
     --workload microlensing, one build of the 1e7-star tree (inputs larger
-    than L2) and a shot of a --grid^2 patch."""
+    than L2) and a shot of a --grid^2 patch; with --workload fit, one step of
+    the lens fit (build, forward keeping its lists, adjoint replaying them)."""
     import torch
 
     import paper_1312_1128_gb300 as L
+    if args.workload == "fit":
+        w = lensgen.workload_fit()
+        rx, ry = torch.from_numpy(w["rx"]).cuda(), torch.from_numpy(w["ry"]).cuda()
+        tl = L.Lens([L.Species.gauss(torch.from_numpy(w["target"]).cuda(), w["q"])], theta=0.3)
+        at = [a.clone() for a in tl.shoot(rx, ry, flags=L.ALPHA_ONLY)[:2]]
+        tl.close()
+        lens = L.Lens([L.Species.gauss(torch.from_numpy(w["gauss"]).cuda(), w["q"])], theta=0.3, group_rays=32,
+                      walk="pairs")
+        out = lens.shoot(rx, ry, flags=L.ALPHA_ONLY | L.KEEP_LISTS | L.TIMING)
+        lens.sync()
+        timing = lens.last_timing()
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record()
+        lens.backward(rx, ry, (2 * (out[0] - at[0])).contiguous(), (2 * (out[1] - at[1])).contiguous(),
+                      flags=L.KEEP_LISTS)
+        ev[1].record()
+        lens.sync()
+        print(json.dumps({"workload": "fit", "timing_ms": timing, "backward_ms": ev[0].elapsed_time(ev[1]),
+                          "split_groups": lens.info()["split_groups"]}))
+        lens.close()
+        return
     if args.workload == "microlensing":
         w = lensgen.workload_microlensing(n_grid=args.grid)
         stars = torch.from_numpy(w["points"]).cuda()
