@@ -486,7 +486,7 @@ class MixedBatches(Workload):
         best = None
         for g, walk, tile in [(32, "warp", "standard"), (64, "warp", "standard"), (32, "pairs", "standard"),
                               (64, "pairs", "standard"), (64, "trios", "standard"), (32, "warp", "large"),
-                              (64, "warp", "large")]:
+                              (64, "warp", "large"), (128, "warp", "standard")]:
             lens = L.Lens([L.Species.points(self.sp[0]), L.Species.nfw(self.sp[1], w["conc"])], theta=self.theta,
                           group_rays=g, walk=walk, tile=tile)
             lens.reserve(self.n_rays, 256)

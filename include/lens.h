@@ -118,7 +118,8 @@ typedef struct lens_params {
     double theta;        /* opening angle theta_force of Eq. r_cut (>= 0; 0 = never accept a cell) */
     int32_t leaf_max;    /* a box holding fewer than leaf_max particles is a leaf (>= 1; paper: 5)  */
     int32_t precision;   /* LENS_PREC_FP32 or LENS_PREC_FP64                                          */
-    int32_t group_rays;  /* rays sharing one interaction list: 0 = autotuned/default, else 32 or 64   */
+    int32_t group_rays;  /* rays sharing one interaction list: 0 = default (32), else 32, 64 or 128;  *
+                          * 128 serves the one-warp FP32 tree walk (other calls use 64)         */
     int32_t walk;        /* LENS_WALK_*: how warps share a group's walk (0 = default, autotuned)      */
     int32_t tile;        /* LENS_TILE_*: near-field tile of the walk (0 = default, autotuned)         */
     int32_t reserved;    /* 0                                                                         */
@@ -158,7 +159,7 @@ typedef struct lens_tree_info {
     double build_ms[8][4];    /* device time (CUDA events) of the build phases: stage +
                                  Morton sort, topology + node layout, moments + big
                                  lists, finish */
-    int32_t group_rays;       /* current ray-group size (32 or 64) */
+    int32_t group_rays;       /* current ray-group size (32, 64 or 128) */
     int32_t walk;             /* current walk form: LENS_WALK_WARP, _PAIRS or _TRIOS */
     int32_t tile;             /* current near-field tile: LENS_TILE_STANDARD or LENS_TILE_LARGE */
     int32_t split_groups;     /* ray groups the last lens_shoot_rays_backward split into
@@ -287,7 +288,7 @@ lens_status lens_shoot_rays_backward(lens_tree* tree, double origin_x, double or
 
 /*
  * lens_autotune -- pick the ray-group size (rays sharing one interaction
- * list: 32 or 64) and, unless the tree was built with them fixed in
+ * list: 32, 64, or 128 with the one-warp walk of an FP32 tree) and, unless the tree was built with them fixed in
  * lens_params, the walk form (LENS_WALK_WARP, _PAIRS or _TRIOS) and the
  * near-field tile (LENS_TILE_STANDARD or LENS_TILE_LARGE) for this tree by
  * timing the walk on the given rays (at most the first 8,388,608; same

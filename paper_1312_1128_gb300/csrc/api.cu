@@ -201,8 +201,8 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
         return lens_set_error(LENS_ERR_INVALID_ARG, "leaf_max must be in 1..64");
     if (params->precision != LENS_PREC_FP32 && params->precision != LENS_PREC_FP64)
         return lens_set_error(LENS_ERR_INVALID_ARG, "unknown precision %d", params->precision);
-    if (params->group_rays != 0 && params->group_rays != 32 && params->group_rays != 64)
-        return lens_set_error(LENS_ERR_INVALID_ARG, "group_rays must be 0, 32 or 64");
+    if (params->group_rays != 0 && params->group_rays != 32 && params->group_rays != 64 && params->group_rays != 128)
+        return lens_set_error(LENS_ERR_INVALID_ARG, "group_rays must be 0, 32, 64 or 128");
     if (params->walk < LENS_WALK_DEFAULT || params->walk > LENS_WALK_TRIOS)
         return lens_set_error(LENS_ERR_INVALID_ARG, "walk must be LENS_WALK_DEFAULT, _WARP, _PAIRS or _TRIOS");
     if (params->tile < LENS_TILE_DEFAULT || params->tile > LENS_TILE_LARGE)
@@ -399,15 +399,16 @@ lens_status lens_autotune(lens_tree* tree, double origin_x, double origin_y, con
     // candidates: group size x walk form x near-field tile (the walk form and
     // the tile only if the caller left them open; the large tile serves the
     // one-warp FP32 walk)
-    const int cand_g[7] = {32, 64, 32, 64, 64, 32, 64};
-    const int cand_w[7] = {LENS_WALK_WARP, LENS_WALK_WARP, LENS_WALK_PAIRS, LENS_WALK_PAIRS, LENS_WALK_TRIOS,
-                           LENS_WALK_WARP, LENS_WALK_WARP};
-    const int cand_t[7] = {0, 0, 0, 0, 0, 1, 1};
+    // (128-ray groups: the one-warp walk only)
+    const int cand_g[8] = {32, 64, 32, 64, 64, 32, 64, 128};
+    const int cand_w[8] = {LENS_WALK_WARP, LENS_WALK_WARP, LENS_WALK_PAIRS, LENS_WALK_PAIRS, LENS_WALK_TRIOS,
+                           LENS_WALK_WARP, LENS_WALK_WARP, LENS_WALK_WARP};
+    const int cand_t[8] = {0, 0, 0, 0, 0, 1, 1, 0};
     double best = 1e300;
     int best_g = tree->group_rays, best_w = tree->walk_mode, best_t = tree->tile;
     const int user_w = tree->walk_mode, user_t = tree->tile;
     lens_status st = LENS_OK;
-    for (int c = 0; c < 7 && st == LENS_OK; ++c) {
+    for (int c = 0; c < 8 && st == LENS_OK; ++c) {
         if (tree->precision == LENS_PREC_FP64 && (cand_g[c] != 32 || cand_t[c] != 0)) continue;
         if (tree->walk_fixed && cand_w[c] != user_w) continue;
         if (tree->tile_fixed && cand_t[c] != user_t) continue;

@@ -51,7 +51,7 @@ lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, co
                                 int flags, cudaStream_t s)
 {
     ShootPlan plan;
-    LENS_TRY(upload_batches(t, nb, off, orig, s, &plan));
+    LENS_TRY(upload_batches(t, nb, off, orig, s, &plan, shoot_max_r(t, flags)));
     for (GraphEntry* g : t->graphs) {
         bool same = g->n == plan.n && g->nb == plan.nb && g->ng == plan.ng && g->dx == dx && g->dy == dy &&
                     g->dtype == dtype && g->flags == flags && g->scratch == t->ray_scratch.ptr &&

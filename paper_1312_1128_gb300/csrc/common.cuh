@@ -30,7 +30,7 @@ constexpr int kStackCap = 4096;        // node entries per warp stack (bound: 12
 constexpr int kFarCap = 64;            // far-cell buffer entries per warp
 constexpr int kNearCap = 128;          // near-particle buffer entries per warp
 constexpr int kBigCap = 128;           // big-list buffer entries per warp
-constexpr int kMaxRaysPerLane = 2;     // rays per lane in the walk (32- or 64-ray groups)
+constexpr int kMaxRaysPerLane = 4;     // rays per lane in the walk (32-, 64- or 128-ray groups)
 
 // 32-byte aligned four-double record (CUDA 13 deprecates the plain double4).
 struct alignas(32) dbl4 {

@@ -338,13 +338,14 @@ __global__ void k_groups32(int64_t n_groups, int64_t n, const float* dx, const f
 // ---------------------------------------------------------------- walk
 
 template <int KIND, typename T, int R, bool AO, bool DIRECT, int TILE>
-__global__ void __launch_bounds__(kWalkWarps * 32, sizeof(T) == 4 ? (R == 2 ? 5 : 6) : 2)
+__global__ void __launch_bounds__(kWalkWarps * 32, sizeof(T) == 4 ? (R == 4 ? 4 : (R == 2 ? 5 : 6)) : 2)
 walk_kernel(WalkParams<T> P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const unsigned full = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WalkShared<KIND, T, TILE>& S = reinterpret_cast<WalkShared<KIND, T, TILE>*>(smem_raw)[warp];
+    using WS = WalkShared<KIND, T, TILE, tot_rays<R>()>;
+    WS& S = reinterpret_cast<WS*>(smem_raw)[warp];
     int* stack = P.stack + ((int64_t)blockIdx.x * kWalkWarps + warp) * kStackCap;
     WalkCtx<KIND, T, R, AO, TILE> C(P, S);
     uint32_t ridx[R];
@@ -476,7 +477,7 @@ static int walk_blocks_per_sm()
 {
     static int cached = -1;
     if (cached < 0) {
-        size_t smem = kWalkWarps * sizeof(WalkShared<KIND, T, TILE>);
+        size_t smem = kWalkWarps * sizeof(WalkShared<KIND, T, TILE, tot_rays<R>()>);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(walk_kernel<KIND, T, R, AO, DIRECT, TILE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -518,7 +519,7 @@ lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s)
 template <int KIND, typename T, int R, bool AO, bool DIRECT, int TILE>
 static void launch_one(const WalkParams<T>& P, int num_sms, cudaStream_t s)
 {
-    size_t smem = kWalkWarps * sizeof(WalkShared<KIND, T, TILE>);
+    size_t smem = kWalkWarps * sizeof(WalkShared<KIND, T, TILE, tot_rays<R>()>);
     int bps = walk_blocks_per_sm<KIND, T, R, AO, DIRECT, TILE>();
     if (bps > 16) bps = 16;  // stack slots are allocated for 16 blocks per SM
     int grid = num_sms * bps;
@@ -556,17 +557,40 @@ static void launch_dispatch(int kind, bool ao, bool direct, const WalkParams<T>&
     }
 }
 
-static int rays_per_lane(const lens_tree* t)
+// 128-ray groups (four rays per lane): the one-warp tree walk of an FP32 tree.
+template <typename T>
+static void launch_tree4(int kind, bool ao, const WalkParams<T>& P, int num_sms, cudaStream_t s, int tile)
 {
-    return (t->precision == LENS_PREC_FP64 || t->group_rays <= 32) ? 1 : 2;
+    if constexpr (sizeof(T) == 4) {
+        if (tile == 1) {
+            if (ao) launch_kind<T, 4, true, false, 1>(kind, P, num_sms, s);
+            else launch_kind<T, 4, false, false, 1>(kind, P, num_sms, s);
+        } else {
+            if (ao) launch_kind<T, 4, true, false, 0>(kind, P, num_sms, s);
+            else launch_kind<T, 4, false, false, 0>(kind, P, num_sms, s);
+        }
+    }
+}
+
+static int rays_per_lane(const lens_tree* t, int max_r)
+{
+    const int r = (t->precision == LENS_PREC_FP64 || t->group_rays <= 32) ? 1 : t->group_rays >= 128 ? 4 : 2;
+    return r < max_r ? r : max_r;
+}
+
+// 128-ray groups only for the one-warp tree walk of an FP32 tree.
+int shoot_max_r(const lens_tree* t, int flags)
+{
+    const bool ws = t->walk_mode == LENS_WALK_PAIRS || t->walk_mode == LENS_WALK_TRIOS;
+    return (flags & LENS_DIRECT) || ws || t->precision != LENS_PREC_FP32 ? 2 : 4;
 }
 
 // Copy the batch table to the device (stream ordered) and size the groups.
 lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig,
-                           cudaStream_t s, ShootPlan* plan)
+                           cudaStream_t s, ShootPlan* plan, int max_r)
 {
     const int64_t n = h_off[nb];
-    const int R = rays_per_lane(t);
+    const int R = rays_per_lane(t, max_r);
     const int GR = 32 * R;
     LENS_TRY(reserve_rays(t, n, nb, s));
     Layout L = make_layout(t->ray_cap, t->batch_cap, max_slots(t));
@@ -632,14 +656,20 @@ lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, 
             if (R == 1)
                 { k_groups32<T, 1><<<gg, TB, 0, s>>>((int64_t)ng, n, fx, fy, sv, gH, gbox, grange, ray_l, ray_idx);
                   note_launch(); }
-            else
+            else if (R == 2)
                 { k_groups32<T, 2><<<gg, TB, 0, s>>>((int64_t)ng, n, fx, fy, sv, gH, gbox, grange, ray_l, ray_idx);
+                  note_launch(); }
+            else
+                { k_groups32<T, 4><<<gg, TB, 0, s>>>((int64_t)ng, n, fx, fy, sv, gH, gbox, grange, ray_l, ray_idx);
                   note_launch(); }
         } else if (R == 1) {
             { k_groups<T, 1><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
                                              sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
-        } else {
+        } else if (R == 2) {
             { k_groups<T, 2><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
+                                             sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
+        } else {
+            { k_groups<T, 4><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
                                              sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
         }
     } else {
@@ -661,8 +691,11 @@ lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, 
         if (R == 1)
             { k_groups<T, 1><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
                                              sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
-        else
+        else if (R == 2)
             { k_groups<T, 2><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
+                                             sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
+        else
+            { k_groups<T, 4><<<gg, TB, 0, s>>>((int64_t)ng, d_boff, d_gfirst, (int)nb, d_borig, dx, dy, dtype,
                                              sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
     }
 
@@ -765,12 +798,15 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
             bool done = false;
             if (!direct && (t->walk_mode == LENS_WALK_PAIRS || t->walk_mode == LENS_WALK_TRIOS)) {
                 const int consumers = t->walk_mode == LENS_WALK_TRIOS ? 2 : 1;
-                done = R == 1 ? launch_ws<T, 1>(st.kind, ao, P, t->num_sms, s, consumers)
-                              : launch_ws<T, 2>(st.kind, ao, P, t->num_sms, s, consumers);
+                if (R <= 2)
+                    done = R == 1 ? launch_ws<T, 1>(st.kind, ao, P, t->num_sms, s, consumers)
+                                  : launch_ws<T, 2>(st.kind, ao, P, t->num_sms, s, consumers);
             }
             if (!done) {
                 if (R == 1) launch_dispatch<T, 1>(st.kind, ao, direct, P, t->num_sms, s, t->tile);
-                else launch_dispatch<T, 2>(st.kind, ao, direct, P, t->num_sms, s, t->tile);
+                else if (R == 2) launch_dispatch<T, 2>(st.kind, ao, direct, P, t->num_sms, s, t->tile);
+                else if (!direct) launch_tree4<T>(st.kind, ao, P, t->num_sms, s, t->tile);
+                else return lens_set_error(LENS_ERR_INTERNAL, "128-ray groups in a direct sum");
             }
             if (P.n_slices > 1) {
                 k_split_sum<T><<<grid_for(n, 256), 256, 0, s>>>(n, P.n_slices, ao ? 2 : 5, P.split, P.out[0], P.out[1],
@@ -790,7 +826,8 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
         P.counter = counter;
         LENS_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(uint32_t), s));
         if (R == 1) launch_dispatch<T, 1>(LENS_POINT, ao, true, P, t->num_sms, s);
-        else launch_dispatch<T, 2>(LENS_POINT, ao, true, P, t->num_sms, s);
+        else if (R == 2) launch_dispatch<T, 2>(LENS_POINT, ao, true, P, t->num_sms, s);
+        else return lens_set_error(LENS_ERR_INTERNAL, "128-ray groups without particles");
     }
     if (timing) {
         LENS_CUDA(cudaEventRecord(t->ev[2], s));
@@ -845,11 +882,12 @@ lens_status shoot(lens_tree* t, int64_t nb, const int64_t* h_off, const double* 
                   const void* dy, int dtype, void* const out[5], int flags, cudaStream_t s)
 {
     ShootPlan plan;
-    LENS_TRY(upload_batches(t, nb, h_off, h_orig, s, &plan));
+    LENS_TRY(upload_batches(t, nb, h_off, h_orig, s, &plan, shoot_max_r(t, flags)));
     // kept lists hold box indices in 29 bits
     bool small_tree = true;
     for (const auto& st : t->sp) small_tree = small_tree && st.n_nodes < (int64_t)kListIdMask;
-    if ((flags & LENS_KEEP_LISTS) && !(flags & LENS_DIRECT) && nb == 1 && plan.n > 0 && small_tree)
+    // (the adjoint groups at most 64 rays: lists of 128-ray groups would not be its)
+    if ((flags & LENS_KEEP_LISTS) && !(flags & LENS_DIRECT) && nb == 1 && plan.n > 0 && small_tree && plan.R <= 2)
         LENS_TRY(reserve_lists(t, (int64_t)plan.ng, plan.R, s));
     else
         flags &= ~LENS_KEEP_LISTS;

@@ -102,30 +102,35 @@ struct WalkRanges {
     int rs_end[32];
 };
 
-template <typename T> struct WalkTot {
-    T tot_s[5][kMaxRaysPerLane][32], tot_c[5][kMaxRaysPerLane][32];
+// NR: rays per lane the totals have room for (2, or 4 for 128-ray groups).
+template <typename T, int NR = 2> struct WalkTot {
+    T tot_s[5][NR][32], tot_c[5][NR][32];
 };
 
 // Shared memory of one warp of the walk kernel.
-template <int KIND, typename T, int TILE = 0> struct WalkShared {
+template <int KIND, typename T, int TILE = 0, int NR = 2> struct WalkShared {
     WalkBuf<KIND, T, TILE> buf;
     WalkRanges rng;
-    WalkTot<T> tot;
+    WalkTot<T, NR> tot;
 };
+
+// Room in the totals for R rays per lane.
+template <int R> constexpr int tot_rays() { return R > 2 ? R : 2; }
 
 template <int KIND, typename T, int R, bool AO, int TILE = 0> struct WalkEval {
     static_assert(R <= kMaxRaysPerLane, "rays per lane");
     static constexpr int kQ = AO ? 2 : 5;  // components accumulated
+    static constexpr int kNR = tot_rays<R>();
     using Buf = WalkBuf<KIND, T, TILE>;
     const WalkParams<T>& P;
     Buf* B;                // the buffers being evaluated
-    WalkTot<T>* Tt;        // compensated totals of the lane's rays
+    WalkTot<T, kNR>* Tt;   // compensated totals of the lane's rays
     T lx[R], ly[R];
     Acc5<T> part[R];
     v2_t<T> H;
     vec4_t<T> box;
 
-    LENS_DEV WalkEval(const WalkParams<T>& p, Buf* b, WalkTot<T>* t) : P(p), B(b), Tt(t) {}
+    LENS_DEV WalkEval(const WalkParams<T>& p, Buf* b, WalkTot<T, kNR>* t) : P(p), B(b), Tt(t) {}
 
     LENS_DEV void tot_zero()
     {
@@ -402,7 +407,7 @@ template <int KIND, typename T, int R, bool AO, int TILE = 0> struct WalkCtx : W
     uint32_t* rec = nullptr;     // the group's kept interaction list, or null
     int rec_n = 0, rec_cap = 0;
 
-    LENS_DEV WalkCtx(const WalkParams<T>& p, WalkShared<KIND, T, TILE>& s)
+    LENS_DEV WalkCtx(const WalkParams<T>& p, WalkShared<KIND, T, TILE, tot_rays<R>()>& s)
         : WalkEval<KIND, T, R, AO, TILE>(p, &s.buf, &s.tot), Rg(&s.rng) {}
     LENS_DEV void flush_far()
     {

@@ -140,8 +140,12 @@ HeavyPlan heavy_first_order(lens_tree* t, const ShootPlan& plan, const RayKey& k
 const uint32_t* kept_lists(const lens_tree* t, const RayKey& k);
 
 lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s);
+// max_r caps the rays per lane (4: 128-ray groups for the one-warp tree walk;
+// 2 for the other kernels, which hold at most 64 rays per group).
 lens_status upload_batches(lens_tree* t, int64_t nb, const int64_t* h_off, const double* h_orig,
-                           cudaStream_t s, ShootPlan* plan);
+                           cudaStream_t s, ShootPlan* plan, int max_r = 2);
+// The cap of upload_batches for a shoot call with these flags on this tree.
+int shoot_max_r(const lens_tree* t, int flags);
 // Ray grouping of one shoot call (sort + groups) into the tree's scratch.
 template <typename T>
 lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, const void* dy, int dtype,

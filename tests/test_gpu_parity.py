@@ -173,6 +173,48 @@ def test_walk_pairs_matches_warp(case, group_rays):
         assert np.median(ea) <= 1e-3
 
 
+@pytest.mark.parametrize("case", ["gauss", "points_origin"])
+def test_tree_128_ray_groups(case):
+    """128-ray groups (four rays per lane, the one-warp FP32 tree walk):
+    within the tree's bar of the oracle, kappa of a Gaussian lens exact away
+    from support edges; the calls that group at most 64 rays (direct sum,
+    potential) give the 64-ray lens's bits."""
+    g = lensgen.rng(41)
+    origin = (0.0, 0.0)
+    if case == "gauss":
+        parts = lensgen.nfw_particles(20000, 7, nsph=32)
+        species, comps = [L.Species.gauss(cu(parts), 3.0)], comps_gauss(parts, 3.0)
+        halos = []
+    else:
+        # FP64 origin with FP32 offsets: the FP64-anchored grouping path
+        p = lensgen.point_disk(5000, 43)
+        species, comps = [L.Species.points(cu(p))], comps_points(p)
+        halos = [L.Halo.sis(0.05, -0.02, 0.3)]
+        comps = oracle.concat(comps, oracle.make_components(oracle.SIS, 0.05, -0.02, 0, 0.3))
+        origin = (0.25, -0.125)
+    dx = g.uniform(-0.6, 0.6, 5000).astype(np.float32)
+    dy = g.uniform(-0.6, 0.6, 5000).astype(np.float32)
+    rx, ry = origin[0] + dx.astype(np.float64), origin[1] + dy.astype(np.float64)
+    lens = L.Lens(species, halos, theta=0.3, group_rays=128, walk="warp")
+    assert lens.info()["group_rays"] == 128
+    got = to_np(lens.shoot(cu(dx), cu(dy), origin=origin))
+    lens.sync()
+    ref = oracle.direct_sum(comps, rx, ry)
+    ea, ek, eg = rel_errors(got, ref)
+    assert np.median(ea) <= 1e-3 and np.median(eg) <= 1e-3, (np.median(ea), np.median(eg))
+    if case == "gauss":
+        amb = edge_mask(comps, rx, ry)
+        assert ek[~amb].max() <= 1e-5, ek[~amb].max()
+    l64 = L.Lens(species, halos, theta=0.3, group_rays=64, walk="warp")
+    for a, b in zip(lens.shoot(cu(dx), cu(dy), origin=origin, flags=L.DIRECT),
+                    l64.shoot(cu(dx), cu(dy), origin=origin, flags=L.DIRECT)):
+        assert torch.equal(a, b)
+    for a, b in zip(lens.potential(cu(dx), cu(dy), origin=origin), l64.potential(cu(dx), cu(dy), origin=origin)):
+        assert torch.equal(a, b)
+    lens.close()
+    l64.close()
+
+
 def test_tree_points_fp64_theta01():
     w = lensgen.workload_point_disk()
     p = w["points"]
