@@ -857,10 +857,13 @@ static lens_status backward_typed(lens_tree* t, double ox, double oy, const void
     ShootPlan plan;
     LENS_TRY(upload_batches(t, 1, off, orig, s, &plan));
     if (32 * plan.R > kMaxGroup) return lens_set_error(LENS_ERR_INTERNAL, "group larger than the adjoint buffer");
-    LENS_TRY(enqueue_groups<T>(t, plan, dx, dy, dtype, s));
-    // the forward call on these rays recorded its groups' work: heaviest first
     RayKey key;
     key.dx = dx; key.dy = dy; key.n = n; key.dtype = dtype; key.R = plan.R; key.ox = ox; key.oy = oy;
+    // with LENS_KEEP_LISTS the caller vouches that these are the forward's
+    // rays, unchanged: the forward's groups, still in the scratch, serve
+    const bool keep = (flags & LENS_KEEP_LISTS) && !(flags & LENS_DIRECT) && kept_lists(t, key);
+    if (!(keep && groups_hold(t, key))) LENS_TRY(enqueue_groups<T>(t, plan, dx, dy, dtype, s));
+    // the forward call on these rays recorded its groups' work: heaviest first
     // (a quarter of one warp's share for a launch of about 16 warps per SM)
     const HeavyPlan hp = (flags & LENS_DIRECT) ? HeavyPlan{}
                                                : heavy_first_order<T>(t, plan, key, (int64_t)t->num_sms * 16, s);
@@ -878,7 +881,7 @@ static lens_status backward_typed(lens_tree* t, double ox, double oy, const void
     P.order = hp.order;
     P.heavy_hdr = hp.hdr;
     P.heavy = hp.table;
-    const uint32_t* lists = ((flags & LENS_KEEP_LISTS) && !(flags & LENS_DIRECT)) ? kept_lists(t, key) : nullptr;
+    const uint32_t* lists = keep ? kept_lists(t, key) : nullptr;
     P.list_ids = lists;
     P.list_n = lists ? t->list_n : nullptr;
     P.list_K = lists ? t->list_K : 0;

@@ -52,6 +52,7 @@ lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, co
 {
     ShootPlan plan;
     LENS_TRY(upload_batches(t, nb, off, orig, s, &plan, shoot_max_r(t, flags)));
+    t->grp_n = -1;  // a replay regroups in the scratch without telling the host
     for (GraphEntry* g : t->graphs) {
         bool same = g->n == plan.n && g->nb == plan.nb && g->ng == plan.ng && g->dx == dx && g->dy == dy &&
                     g->dtype == dtype && g->flags == flags && g->scratch == t->ray_scratch.ptr &&

@@ -98,6 +98,13 @@ struct lens_tree {
     int64_t cost_n = -1;
     int cost_dtype = -1, cost_R = 0;
     double cost_ox = 0, cost_oy = 0;
+    // the rays whose groups the scratch holds (set by the grouping, n = -1 if
+    // none): the adjoint of a LENS_KEEP_LISTS call reuses them
+    const void* grp_dx = nullptr;
+    const void* grp_dy = nullptr;
+    int64_t grp_n = -1;
+    int grp_dtype = -1, grp_R = 0;
+    double grp_ox = 0, grp_oy = 0;
     // interaction lists kept by the last lens_shoot_rays with LENS_KEEP_LISTS
     // (walk_dev.cuh tags), for the rays identified as for the work record
     uint32_t* list_ids = nullptr;  // list_groups x list_K tagged box indices

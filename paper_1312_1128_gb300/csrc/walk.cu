@@ -502,6 +502,7 @@ lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s)
     Layout L = make_layout(nn, bb, max_slots(t));
     free_graphs(t);  // captured graphs point into the old scratch
     t->cost_n = -1;  // so does the work record
+    t->grp_n = -1;   // and the groups
     if (t->ray_scratch.ptr) cudaFreeAsync(t->ray_scratch.ptr, s);
     t->ray_scratch.ptr = nullptr;
     t->ray_cap = t->batch_cap = 0;
@@ -620,6 +621,7 @@ template <typename T>
 lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, const void* dy, int dtype,
                            cudaStream_t s)
 {
+    t->grp_n = -1;  // (set again below once these rays are grouped)
     using T4 = vec4_t<T>;
     using T2 = v2_t<T>;
     const int64_t n = plan.n, nb = plan.nb;
@@ -699,6 +701,15 @@ lens_status enqueue_groups(lens_tree* t, const ShootPlan& plan, const void* dx, 
                                              sv, gH, gbox, grange, ray_l, ray_idx); note_launch(); }
     }
 
+    if (nb == 1) {
+        t->grp_dx = dx;
+        t->grp_dy = dy;
+        t->grp_n = n;
+        t->grp_dtype = dtype;
+        t->grp_R = R;
+        t->grp_ox = plan.ox;
+        t->grp_oy = plan.oy;
+    }
     return LENS_OK;
 }
 template lens_status enqueue_groups<float>(lens_tree*, const ShootPlan&, const void*, const void*, int, cudaStream_t);
@@ -892,6 +903,12 @@ lens_status shoot(lens_tree* t, int64_t nb, const int64_t* h_off, const double* 
     else
         flags &= ~LENS_KEEP_LISTS;
     return enqueue_shoot(t, plan, dx, dy, dtype, out, flags, s);
+}
+
+bool groups_hold(const lens_tree* t, const RayKey& k)
+{
+    return t->grp_n >= 0 && t->grp_dx == k.dx && t->grp_dy == k.dy && t->grp_n == k.n &&
+           t->grp_dtype == k.dtype && t->grp_R == k.R && t->grp_ox == k.ox && t->grp_oy == k.oy;
 }
 
 // The kept interaction lists if they belong to these rays, else null.

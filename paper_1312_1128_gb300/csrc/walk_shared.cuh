@@ -138,6 +138,8 @@ HeavyPlan heavy_first_order(lens_tree* t, const ShootPlan& plan, const RayKey& k
 // The interaction lists kept by the last LENS_KEEP_LISTS walk if they belong
 // to these rays (walk.cu), else null.
 const uint32_t* kept_lists(const lens_tree* t, const RayKey& k);
+// Does the shoot scratch hold the groups of these rays (walk.cu)?
+bool groups_hold(const lens_tree* t, const RayKey& k);
 
 lens_status reserve_rays(lens_tree* t, int64_t n, int64_t nb, cudaStream_t s);
 // max_r caps the rays per lane (4: 128-ray groups for the one-warp tree walk;

@@ -403,6 +403,17 @@ def test_kept_lists_same_gradient(n_part, grid):
         scale = np.abs(ref[:, k]).max()
         assert np.abs(got[:, k] - ref[:, k]).max() <= 1e-6 * scale, k
     np.testing.assert_allclose(hgot, href, rtol=1e-10, atol=1e-12 * np.abs(href).max())
+    # other calls in between regroup the scratch (a potential, a batched
+    # graph capture and replay): the replay still gives the same gradients
+    lens.potential(dx * 0.5, dy * 0.5)
+    offs = np.array([0, rx.size // 2, rx.size], np.int64)
+    for _ in range(2):
+        lens.shoot_batches(offs, np.zeros((2, 2)), (dx * 0.7).contiguous(), (dy * 0.7).contiguous(),
+                           flags=L.USE_GRAPH)
+    got_b, hgot_b = grads(lens, L.KEEP_LISTS)
+    for k in range(4):
+        assert np.abs(got_b[:, k] - ref[:, k]).max() <= 1e-6 * np.abs(ref[:, k]).max(), k
+    np.testing.assert_allclose(hgot_b, href, rtol=1e-10, atol=1e-12 * np.abs(href).max())
     # other rays (another array): the kept lists are not theirs, the walk runs
     dx2, dy2 = (dx * 0.9).contiguous(), (dy * 0.9).contiguous()
     ref2, _ = grads(L.Lens([L.Species.gauss(cu(parts), 3.0)], halos, theta=0.3), 0, dx2, dy2)
