@@ -270,8 +270,9 @@ lens_status lens_shoot_batches(lens_tree* tree, int64_t n_batches, const int64_t
  *       this tree had these very rays (same arrays, unchanged since, same
  *       count, dtype and origin), the adjoint replays that call's
  *       interaction lists instead of walking the tree again (the forward's
- *       near field is recomputed, not stored); otherwise the flag has no
- *       effect.  Changing the ray values in between is the caller's error:
+ *       near field is recomputed, not stored), and reuses its ray groups
+ *       if no other call has grouped rays on this tree since; otherwise the
+ *       flag has no effect.  Changing the ray values in between is the caller's error:
  *       the replayed lists then belong to the old rays.
  * Tree gradients with respect to masses and positions follow the tree's
  * moments (so they carry the tree's own approximation error); size and halo
