@@ -348,6 +348,71 @@ LENS_DEV void gauss_correction_x2(Acc5x2& acc, float2 lx, float2 ly, float2 nx, 
     }
 }
 
+// Two big-list entries of the same ray at once when some ray of the group may
+// be inside the softening radius of one of them: gauss_correction (full -
+// softened point; the series below t = kTSeries; zero outside the support)
+// in packed FP32x2, each half choosing by select instead of a branch; a half
+// whose entry was queued for the closed form (no ray inside its softening
+// radius: ws = +inf) takes gauss_correction_fast's values instead, so that
+// an entry gets the same form whatever entry it is paired with.  Operands
+// are pairs over the two entries: nx, ny as above; t_c = c log2 e; kz =
+// m c/N_q; mN = m/N_q; nmass = -m (mass); ws = 1/r0^2; ic = 1/c; Uq2 =
+// q^2/2 log2 e; eU = e^-q^2/2.
+template <bool AO>
+LENS_DEV void gauss_correction_soft_x2(Acc5x2& acc, float2 lx, float2 ly, float2 nx, float2 ny, float2 t_c,
+                                       float2 kz, float2 mN, float2 nmass, float2 ws, float2 ic, float Uq2,
+                                       float eU)
+{
+    using namespace gser;
+    const float2 wx = __fadd2_rn(lx, nx);
+    const float2 wy = __fadd2_rn(ly, ny);
+    const float2 wyy = __fmul2_rn(wy, wy);
+    const float2 r2 = __ffma2_rn(wx, wx, wyy);
+    float2 inv, inv_s;
+    inv.x = r2.x > 0.0f ? rcp(r2.x) : 0.0f;
+    inv.y = r2.y > 0.0f ? rcp(r2.y) : 0.0f;
+    inv_s.x = fminf(inv.x, ws.x);
+    inv_s.y = fminf(inv.y, ws.y);
+    const float2 nkbp = __fmul2_rn(nmass, inv_s);  // minus the softened point's kb
+    const float2 t = __fmul2_rn(r2, t_c);
+    const float2 e = make_float2(exp2neg(t.x), exp2neg(t.y));
+    // h1 and g: the series (small t) and the closed form, chosen per half
+    const float2 hs = __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t,
+                      __ffma2_rn(t, make_float2(H7, H7), make_float2(H6, H6)), make_float2(H5, H5)),
+                      make_float2(H4, H4)), make_float2(H3, H3)), make_float2(H2, H2)), make_float2(H1, H1)),
+                      make_float2(H0, H0));
+    const float2 gs = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t,
+                      __ffma2_rn(t, __ffma2_rn(t, make_float2(G7, G7), make_float2(G6, G6)), make_float2(G5, G5)),
+                      make_float2(G4, G4)), make_float2(G3, G3)), make_float2(G2, G2)), make_float2(G1, G1)),
+                      make_float2(G0, G0)));
+    const float2 hc = __fmul2_rn(__ffma2_rn(e, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f)),
+                                 __fmul2_rn(inv, ic));
+    const float2 gc = __fadd2_rn(hc, __fmul2_rn(e, make_float2(-1.0f, -1.0f)));
+    const bool sx = t.x < kTSeries, sy = t.y < kTSeries;
+    const float2 h1 = make_float2(sx ? hs.x : hc.x, sy ? hs.y : hc.y);
+    const float2 g = make_float2(sx ? gs.x : gc.x, sy ? gs.y : gc.y);
+    const bool inx = t.x < Uq2, iny = t.y < Uq2;
+    const bool fx = ws.x == INFINITY, fy = ws.y == INFINITY;
+    // the closed form (full - point) of gauss_correction_fast
+    const float2 ef = make_float2(inx ? e.x : eU, iny ? e.y : eU);
+    const float2 dkbf = __fmul2_rn(__fmul2_rn(mN, inv), __fadd2_rn(make_float2(eU, eU), __fmul2_rn(ef, make_float2(-1.0f, -1.0f))));
+    const float2 dkbg = __ffma2_rn(kz, h1, nkbp);
+    const float2 ndkb = make_float2(fx ? -dkbf.x : (inx ? -dkbg.x : 0.0f), fy ? -dkbf.y : (iny ? -dkbg.y : 0.0f));
+    acc.na1 = __ffma2_rn(ndkb, wx, acc.na1);
+    acc.na2 = __ffma2_rn(ndkb, wy, acc.na2);
+    if (!AO) {
+        const float2 ke = __fmul2_rn(kz, e);
+        const float2 kap = make_float2(inx ? ke.x : 0.0f, iny ? ke.y : 0.0f);
+        acc.k = __fadd2_rn(acc.k, kap);
+        const float2 dDf = __fmul2_rn(__fadd2_rn(dkbf, __fmul2_rn(kap, make_float2(-1.0f, -1.0f))), inv);
+        const float2 dD = __ffma2_rn(__fmul2_rn(kz, g), inv, __fmul2_rn(nkbp, inv_s));
+        const float2 ndD = make_float2(fx ? -dDf.x : (inx ? -dD.x : 0.0f), fy ? -dDf.y : (iny ? -dD.y : 0.0f));
+        acc.g1p = __ffma2_rn(ndD, r2, acc.g1p);
+        acc.g1y = __ffma2_rn(ndD, wyy, acc.g1y);
+        acc.hg2 = __ffma2_rn(ndD, __fmul2_rn(wx, wy), acc.hg2);
+    }
+}
+
 // FP64 form of the same correction (q1.y holds c log2 e as well).
 template <bool AO>
 LENS_DEV void gauss_correction(Acc5<double>& acc, double wx, double wy, const dbl4& q, const dbl4& q1,

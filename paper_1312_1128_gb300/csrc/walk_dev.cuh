@@ -225,6 +225,25 @@ template <int KIND, typename T, int R, bool AO, int TILE = 0> struct WalkEval {
         }
     }
 
+    // Two entries of the other region of which some ray may come inside a
+    // softening radius: the packed general form.
+    LENS_DEV void big_pair_soft(int i, Acc5x2 (&pa)[R], const float2 (&LX)[R], const float2 (&LY)[R])
+    {
+        const float2 nx = *reinterpret_cast<const float2*>(&B->bnx[i]);
+        const float2 ny = *reinterpret_cast<const float2*>(&B->bny[i]);
+        const float2 cl = *reinterpret_cast<const float2*>(&B->bcl[i]);
+        const float2 mN = *reinterpret_cast<const float2*>(&B->bm[i]);
+        const float2 kz = *reinterpret_cast<const float2*>(&B->bk[i]);
+        const float2 w = *reinterpret_cast<const float2*>(&B->bw[i]);
+        const float2 ic = *reinterpret_cast<const float2*>(&B->bic[i]);
+        const float2 t_c = make_float2(-cl.x, -cl.y);
+        const float2 nmass = make_float2(-(mN.x * P.Nq), -(mN.y * P.Nq));
+        const float2 ws = make_float2(w.x < 0.0f ? INFINITY : w.x, w.y < 0.0f ? INFINITY : w.y);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            gauss_correction_soft_x2<AO>(pa[r], LX[r], LY[r], nx, ny, t_c, kz, mN, nmass, ws, ic, P.Uq2, P.eU);
+    }
+
     template <bool EDGE>
     LENS_DEV void big_pair_packed(int i, Acc5x2 (&pa)[R], const float2 (&LX)[R], const float2 (&LY)[R])
     {
@@ -241,8 +260,9 @@ template <int KIND, typename T, int R, bool AO, int TILE = 0> struct WalkEval {
 
     // FP32 Gaussian big buffer in packed arithmetic: the whole-group-inside
     // region four entries at a time without tests, then the other region
-    // pair by pair (packed closed form with the support edge, or scalar where
-    // a ray may be inside the softening radius).
+    // pair by pair (packed closed form with the support edge; where a ray may
+    // be inside a softening radius, the packed general form for alpha only,
+    // else entry by entry).
     LENS_DEV void eval_big_packed(int nbuf)
     {
         const int n_in = nbuf & 0xffff, n_out = nbuf >> 16;
@@ -270,6 +290,11 @@ template <int KIND, typename T, int R, bool AO, int TILE = 0> struct WalkEval {
             const float2 w = *reinterpret_cast<const float2*>(&B->bw[i]);
             if (w.x < 0.0f && w.y < 0.0f) {
                 big_pair_packed<true>(i, pa, LX, LY);
+            } else if constexpr (AO) {
+                // (alpha only: the registers allow the packed general form;
+                // with kappa and gamma it would push the walk's hot loop
+                // into spills)
+                big_pair_soft(i, pa, LX, LY);
             } else {
                 big_entry_scalar(i, pa);
                 big_entry_scalar(i + 1, pa);
