@@ -202,9 +202,14 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species,
  *   ray_dx, ray_dy: DEVICE arrays of n offsets of type ray_dtype; ray i sits
  *       at (origin_x + ray_dx[i], origin_y + ray_dy[i]), formed in FP64, so a
  *       microlensing patch keeps its resolution far from the coordinate zero.
- *   alpha1 .. gamma2: DEVICE output arrays of n elements, float for an FP32
- *       tree, double for an FP64 tree.  kappa, gamma1, gamma2 may be NULL
- *       only with LENS_ALPHA_ONLY.
+ *   alpha1 .. gamma2: output arrays of n elements, float for an FP32
+ *       tree, double for an FP64 tree, in device memory or in page-locked
+ *       host memory (cudaHostAlloc / cudaMallocHost: unified addressing maps
+ *       it for every device); the kernels write each element once, so
+ *       host outputs receive the results with no separate copy (read them
+ *       after the stream has synchronised; a second species or
+ *       LENS_ACCUMULATE also reads them back).  kappa, gamma1, gamma2 may be
+ *       NULL only with LENS_ALPHA_ONLY.
  *   flags: LENS_ALPHA_ONLY, LENS_DIRECT, LENS_ACCUMULATE, LENS_COUNT,
  *       LENS_TIMING, LENS_KEEP_LISTS.  LENS_KEEP_LISTS (tree walk) also
  *       stores, per ray group, the walk's interaction lists -- the cells it
@@ -346,7 +351,8 @@ lens_status lens_shoot_rays_direct_noalloc(lens_tree* tree, double origin_x, dou
  * additive constant is fixed by psi = m ln r outside its support (SIS:
  * r_E r).  LENS_DIRECT sums every particle's potential instead of walking.
  *   Same ray arguments as lens_shoot_rays; psi (required), alpha1, alpha2
- *   (may be NULL): device arrays of n values in the tree's precision.
+ *   (may be NULL): arrays of n values in the tree's precision, in device or
+ *   page-locked host memory as lens_shoot_rays' outputs.
  *   flags: LENS_DIRECT, LENS_ACCUMULATE, LENS_TIMING (lens_last_timing then
  *   reports this call's grouping and potential-walk times) and LENS_COUNT
  *   (the walk counters of lens_tree_counters) only.

@@ -169,6 +169,18 @@ def _dev_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _out_ptr(t):
+    """An output array: a CUDA tensor, or a page-locked CPU tensor (the
+    kernels write each element once, straight into host memory)."""
+    if t is not None and not t.is_cuda:
+        if not t.is_pinned():
+            raise ValueError("host outputs must be page-locked (tensor.pin_memory())")
+        if not t.is_contiguous():
+            raise ValueError("liblens takes contiguous tensors")
+        return ctypes.c_void_p(t.data_ptr())
+    return _dev_ptr(t)
+
+
 @dataclass
 class Species:
     """A homogeneous particle set: data is an (n, 4) CUDA tensor {x, y, m, p}."""
@@ -364,7 +376,9 @@ class Lens:
         return out
 
     def shoot(self, dx, dy, origin=(0.0, 0.0), flags: int = 0, out=None, stream=None):
-        """alpha1, alpha2, kappa, gamma1, gamma2 at rays origin + (dx, dy)."""
+        """alpha1, alpha2, kappa, gamma1, gamma2 at rays origin + (dx, dy).
+        `out` may hold CUDA tensors or page-locked CPU tensors (written
+        directly; synchronise the stream before reading them)."""
         torch = _torch()
         n = dx.numel()
         if dy.numel() != n or dx.dtype != dy.dtype or dx.dtype not in (torch.float32, torch.float64):
@@ -372,7 +386,7 @@ class Lens:
         out = self._outs(n, bool(flags & ALPHA_ONLY), out)
         rd = F32 if dx.dtype == torch.float32 else F64
         _check(lib().lens_shoot_rays(self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx),
-                                     _dev_ptr(dy), rd, n, *[_dev_ptr(o) for o in out], int(flags),
+                                     _dev_ptr(dy), rd, n, *[_out_ptr(o) for o in out], int(flags),
                                      _stream_ptr(stream)))
         return out
 
@@ -386,10 +400,15 @@ class Lens:
         dt = torch.float64 if self.precision == "fp64" else torch.float32
         if out is None:
             out = [torch.empty(n, dtype=dt, device=dx.device) for _ in range(3)]
+        out = list(out) + [None] * (3 - len(out))
+        if out[0] is None:
+            raise ValueError("psi output is required")
+        for o in out:
+            if o is not None and (o.dtype != dt or o.numel() < n):
+                raise ValueError(f"outputs must be {dt} with at least {n} elements")
         rd = F32 if dx.dtype == torch.float32 else F64
         _check(lib().lens_shoot_potential(self._h, float(origin[0]), float(origin[1]), _dev_ptr(dx), _dev_ptr(dy),
-                                          rd, n, *[_dev_ptr(o) if o is not None else None for o in out],
-                                          int(flags), _stream_ptr(stream)))
+                                          rd, n, *[_out_ptr(o) for o in out], int(flags), _stream_ptr(stream)))
         return out
 
     def find_images(self, sources, x0, y0, side, n=64, l_max=12, mu_min=0.01, f_area=5e-4, n_min=50,
@@ -449,7 +468,7 @@ class Lens:
         _check(lib().lens_shoot_batches(
             self._h, origins.shape[0], offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
             origins.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _dev_ptr(dx), _dev_ptr(dy), rd,
-            *[_dev_ptr(o) for o in out], int(flags), _stream_ptr(stream)))
+            *[_out_ptr(o) for o in out], int(flags), _stream_ptr(stream)))
         return out
 
     def backward(self, dx, dy, g_alpha1, g_alpha2, origin=(0.0, 0.0), flags: int = 0,

@@ -215,6 +215,36 @@ def test_tree_128_ray_groups(case):
     l64.close()
 
 
+def test_page_locked_host_outputs():
+    """Outputs in page-locked host memory receive the same bits as device
+    outputs (shoot, potential, batches); other host memory is refused."""
+    parts = lensgen.nfw_particles(5000, 51, nsph=32)
+    g = lensgen.rng(52)
+    dx = cu(g.uniform(-0.5, 0.5, 3000).astype(np.float32))
+    dy = cu(g.uniform(-0.5, 0.5, 3000).astype(np.float32))
+    lens = L.Lens([L.Species.gauss(cu(parts), 3.0)], theta=0.3)
+    host = [torch.empty(3000, dtype=torch.float32).pin_memory() for _ in range(5)]
+    ref = lens.shoot(dx, dy)
+    lens.shoot(dx, dy, out=host)
+    lens.sync()
+    for a, b in zip(ref, host):
+        assert torch.equal(a.cpu(), b)
+    pref = lens.potential(dx, dy)
+    lens.potential(dx, dy, out=host[:3])
+    lens.sync()
+    for a, b in zip(pref, host[:3]):
+        assert torch.equal(a.cpu(), b)
+    offs = np.array([0, 1000, 3000], np.int64)
+    bref = lens.shoot_batches(offs, np.zeros((2, 2)), dx, dy)
+    lens.shoot_batches(offs, np.zeros((2, 2)), dx, dy, out=host)
+    lens.sync()
+    for a, b in zip(bref, host):
+        assert torch.equal(a.cpu(), b)
+    with pytest.raises(ValueError):
+        lens.shoot(dx, dy, out=[torch.empty(3000, dtype=torch.float32) for _ in range(5)])
+    lens.close()
+
+
 def test_tree_points_fp64_theta01():
     w = lensgen.workload_point_disk()
     p = w["points"]
