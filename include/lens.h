@@ -181,10 +181,15 @@ typedef struct lens_tree_info {
  *   out: receives the new tree on LENS_OK, NULL otherwise.
  * The call synchronises on `stream` once per species, to size the node
  * arrays (and read the input check); the rest of the build is enqueued on
- * `stream` and finishes in stream order, so use the tree on that stream or
- * synchronise first, and keep the species data valid until then.  Counts the
- * host reports (lens_tree_get_info) are read from the device when first
- * asked for.
+ * `stream` and finishes in stream order.  The tree may then be used on any
+ * stream: the build records an event when it is complete, and every call
+ * that reads the tree makes its stream wait for that event on the device
+ * before its first kernel that reads the tree (a shoot or potential call
+ * groups its rays first, so on a second stream the grouping overlaps the
+ * end of the build).  A call captured into a CUDA graph does not wait:
+ * launch the graph after the build has completed or in stream order after
+ * it.  Counts the host reports (lens_tree_get_info) are read from the device
+ * when first asked for.
  * Errors: LENS_ERR_INVALID_ARG for NULL pointers, negative sizes, unknown
  * kinds or dtypes, theta < 0, leaf_max < 1 or a negative / non-finite mass or
  * size found on the device; LENS_ERR_OOM (nothing is kept); LENS_ERR_CUDA; a
@@ -486,7 +491,8 @@ lens_status lens_tree_counters(lens_tree* tree, int64_t* out, int32_t reset);
 /*
  * lens_last_timing -- device time of the last shooting call made with
  * LENS_TIMING, measured with CUDA events on its stream: grouping (ray sort
- * and group set-up) and walk (all species' walk or direct-sum kernels).
+ * and group set-up) and walk (all species' walk or direct-sum kernels, from
+ * the end of the stream's wait for the tree's build).
  * Synchronises on those events.  Both are 0 if no timed call was made.
  */
 lens_status lens_last_timing(lens_tree* tree, double* group_ms, double* walk_ms);

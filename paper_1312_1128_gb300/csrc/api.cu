@@ -181,8 +181,9 @@ void lens_free_tree(lens_tree* t)
     if (t->list_ids) cudaFree(t->list_ids);
     if (t->list_n) cudaFree(t->list_n);
     if (t->amr_ws && t->amr_free) t->amr_free(t->amr_ws);
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 4; ++i)
         if (t->ev[i]) cudaEventDestroy(t->ev[i]);
+    if (t->built) cudaEventDestroy(t->built);
     delete t;
 }
 
@@ -276,6 +277,9 @@ lens_status lens_build_tree(const lens_species* species, int32_t n_species, cons
     // device-side check that fails later is reported by lens_sync_status
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(lens_cuda_check(e, "tree build"));
+    e = cudaEventCreateWithFlags(&t->built, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(t->built, s);
+    if (e != cudaSuccess) return fail(lens_cuda_check(e, "cudaEventRecord(built)"));
     // the allocation-free shoot's scratch: its address on this device, taken
     // here (the first lookup on a device loads the array) so that the shoot
     // call itself makes no runtime lookup
@@ -488,10 +492,10 @@ lens_status lens_last_timing(lens_tree* t, double* group_ms, double* walk_ms)
     if (!t || !group_ms || !walk_ms) return lens_set_error(LENS_ERR_INVALID_ARG, "NULL argument");
     *group_ms = *walk_ms = 0.0;
     if (!t->timed) return LENS_OK;
-    LENS_CUDA(cudaEventSynchronize(t->ev[2]));
+    LENS_CUDA(cudaEventSynchronize(t->ev[3]));
     float a = 0, b = 0;
     LENS_CUDA(cudaEventElapsedTime(&a, t->ev[0], t->ev[1]));
-    LENS_CUDA(cudaEventElapsedTime(&b, t->ev[1], t->ev[2]));
+    LENS_CUDA(cudaEventElapsedTime(&b, t->ev[2], t->ev[3]));  // from the end of any wait for the build
     *group_ms = a;
     *walk_ms = b;
     return LENS_OK;

@@ -977,6 +977,7 @@ lens_status shoot_backward(lens_tree* t, double ox, double oy, const void* dx, c
                            int64_t n, const void* const g[5], void* const* g_species, void* g_halos,
                            int flags, cudaStream_t s)
 {
+    LENS_TRY(wait_built(t, s));
     if (t->precision == LENS_PREC_FP64)
         return backward_typed<double>(t, ox, oy, dx, dy, dtype, n, g, g_species, g_halos, flags, s);
     return backward_typed<float>(t, ox, oy, dx, dy, dtype, n, g, g_species, g_halos, flags, s);

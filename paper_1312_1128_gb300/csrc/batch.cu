@@ -59,6 +59,7 @@ lens_status graph_shoot_batches(lens_tree* t, int64_t nb, const int64_t* off, co
                     g->group_rays == t->group_rays && g->walk == t->walk_mode;
         for (int q = 0; q < 5 && same; ++q) same = g->out[q] == out[q];
         if (same) {
+            LENS_TRY(wait_built(t, s));  // the graph itself holds no wait
             LENS_CUDA(cudaGraphLaunch(g->exec, s));
             note_launches(g->kernels);
             return LENS_OK;

@@ -800,6 +800,16 @@ struct BuildMeta {
     RootBox rb;
 };
 
+lens_status wait_built(const lens_tree* t, cudaStream_t s)
+{
+    if (!t->built) return LENS_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LENS_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return LENS_OK;
+    LENS_CUDA(cudaStreamWaitEvent(s, t->built, 0));
+    return LENS_OK;
+}
+
 lens_status finish_species(SpeciesTree& st)
 {
     if (st.meta_ready || st.n == 0) return LENS_OK;

@@ -478,12 +478,14 @@ static lens_status psi_typed(lens_tree* t, const ShootPlan& plan, const void* dx
     char* base = (char*)t->ray_scratch.ptr;
     const bool timing = (flags & LENS_TIMING) != 0;
     if (timing) {
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 4; ++i)
             if (!t->ev[i]) LENS_CUDA(cudaEventCreate(&t->ev[i]));
         LENS_CUDA(cudaEventRecord(t->ev[0], s));
     }
     if (plan.n > 0) LENS_TRY(enqueue_groups<T>(t, plan, dx, dy, dtype, s));
     if (timing) LENS_CUDA(cudaEventRecord(t->ev[1], s));
+    LENS_TRY(wait_built(t, s));  // the grouping reads only the rays
+    if (timing) LENS_CUDA(cudaEventRecord(t->ev[2], s));
     WalkParams<T> P{};
     P.gH = (T2*)(base + L.gH);
     P.gbox = (T4*)(base + L.gbox);
@@ -551,7 +553,7 @@ static lens_status psi_typed(lens_tree* t, const ShootPlan& plan, const void* dx
         launch(LENS_POINT, PsiConsts<T>{});
     }
     if (timing) {
-        LENS_CUDA(cudaEventRecord(t->ev[2], s));
+        LENS_CUDA(cudaEventRecord(t->ev[3], s));
         t->timed = true;
     }
     LENS_CUDA(cudaGetLastError());

@@ -90,7 +90,10 @@ struct lens_tree {
     long long wait_cycles = 4000000000ll;   // bound of a wait between cooperating warps (~2 s at 2 GHz)
     std::vector<lens::GraphEntry*> graphs;
     unsigned long long* d_stats = nullptr;  // 8 walk counters (LENS_COUNT), then the last adjoint's split {Kc, Hn}
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // LENS_TIMING: start, grouped, walked
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // LENS_TIMING: start, grouped, tree ready, walked
+    // recorded on the build's stream when the build is complete: a call that
+    // reads the tree on another stream waits for it on the device first
+    cudaEvent_t built = nullptr;
     // the rays whose per-group work the scratch holds (walk_shared.cuh), as
     // an opaque copy of their identity: pointers, size, dtype, origin, R
     const void* cost_dx = nullptr;
@@ -127,5 +130,8 @@ namespace lens {
 lens_status build_species(lens_tree* t, SpeciesTree& st, const lens_species& in, cudaStream_t s);
 lens_status finish_species(SpeciesTree& st);  // host copies of the build's counts (synchronises once)
 void free_species(SpeciesTree& st);
+// Make stream s wait on the device for the end of the tree's build (no-op
+// while s is being captured into a graph: the graph's launch waits instead).
+lens_status wait_built(const lens_tree* t, cudaStream_t s);
 
 }  // namespace lens

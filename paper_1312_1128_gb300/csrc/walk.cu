@@ -743,7 +743,7 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
     int* stack = (int*)(base + L.stack);
     const bool timing = (flags & LENS_TIMING) != 0;
     if (timing) {
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 4; ++i)
             if (!t->ev[i]) LENS_CUDA(cudaEventCreate(&t->ev[i]));
         LENS_CUDA(cudaEventRecord(t->ev[0], s));
     }
@@ -761,6 +761,10 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
     if (keep) LENS_CUDA(cudaMemsetAsync(t->list_n, 0xff, ng * sizeof(uint32_t), s));  // kListOverflow
 
     if (timing) LENS_CUDA(cudaEventRecord(t->ev[1], s));
+    // the grouping above reads only the rays: it may overlap the end of a
+    // build on another stream; the walk reads the tree
+    LENS_TRY(wait_built(t, s));
+    if (timing) LENS_CUDA(cudaEventRecord(t->ev[2], s));
     WalkParams<T> P{};
     P.stats = (flags & LENS_COUNT) ? t->d_stats : nullptr;
     P.gH = gH; P.gbox = gbox; P.grange = grange; P.ray_l = ray_l; P.ray_idx = ray_idx;
@@ -841,7 +845,7 @@ static lens_status enqueue_typed(lens_tree* t, const ShootPlan& plan, const void
         else return lens_set_error(LENS_ERR_INTERNAL, "128-ray groups without particles");
     }
     if (timing) {
-        LENS_CUDA(cudaEventRecord(t->ev[2], s));
+        LENS_CUDA(cudaEventRecord(t->ev[3], s));
         t->timed = true;
     }
     if (record) set_cost_key(t, key);
@@ -1213,6 +1217,7 @@ extern "C" lens_status lens_shoot_rays_direct_noalloc(lens_tree* tree, double or
     if (dev != tree->device) return lens_set_error(LENS_ERR_INVALID_ARG, "tree was built on another device");
     void* out[5] = {alpha1, alpha2, kappa, gamma1, gamma2};
     cudaStream_t s = (cudaStream_t)stream;
+    LENS_TRY(wait_built(tree, s));
     if (tree->precision == LENS_PREC_FP64)
         return noalloc_typed<double>(tree, origin_x, origin_y, ray_dx, ray_dy, ray_dtype, n, out, flags, s);
     return noalloc_typed<float>(tree, origin_x, origin_y, ray_dx, ray_dy, ray_dtype, n, out, flags, s);

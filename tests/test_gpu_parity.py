@@ -245,6 +245,50 @@ def test_page_locked_host_outputs():
     lens.close()
 
 
+def test_tree_used_on_another_stream():
+    """Shoot, potential and adjoint calls issued on a second stream right
+    after a build, with no host synchronisation, wait for the build on the
+    device: the same results as the same calls made once the build has
+    completed (the forward bit for bit; the adjoint, which sums in FP64
+    atomics, to FP64 rounding)."""
+    parts = cu(lensgen.nfw_particles(200000, 61, nsph=32))
+    g = lensgen.rng(62)
+    n = 1 << 16
+    dx = cu(g.uniform(-0.5, 0.5, n).astype(np.float32))
+    dy = cu(g.uniform(-0.5, 0.5, n).astype(np.float32))
+    ga = [cu(g.normal(size=n).astype(np.float32)) for _ in range(2)]
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(5)]
+    pots = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    grad = torch.zeros(parts.shape[0], 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    for rep in range(2):
+        with torch.cuda.stream(a):
+            lens = L.Lens([L.Species.gauss(parts, 3.0)], theta=0.3)
+        if rep == 0:
+            lens.shoot(dx, dy, out=outs, stream=b)
+            lens.potential(dx, dy, out=pots, stream=b)
+        else:
+            lens.backward(dx, dy, ga[0], ga[1], grads=[grad], stream=b)
+        torch.cuda.synchronize()
+        if rep == 0:
+            ref = lens.shoot(dx, dy)
+            pref = lens.potential(dx, dy)
+            lens.sync()
+            for x, y in zip(ref, outs):
+                assert torch.equal(x, y)
+            for x, y in zip(pref, pots):
+                assert torch.equal(x, y)
+        else:
+            gref = torch.zeros_like(grad)
+            lens.backward(dx, dy, ga[0], ga[1], grads=[gref])
+            lens.sync()
+            gr, gg = gref.double().cpu().numpy(), grad.double().cpu().numpy()
+            scale = np.abs(gr).max(axis=0) + 1e-30
+            assert np.max(np.abs(gg - gr) / scale) < 1e-5
+        lens.close()
+
+
 def test_tree_points_fp64_theta01():
     w = lensgen.workload_point_disk()
     p = w["points"]
