@@ -171,11 +171,46 @@ __global__ void k_morton(const vec4_t<T>* staged, int64_t n, const RootBox* rb, 
     vals[i] = (uint32_t)i;
 }
 
+// Full-profile records of particle r (see walk.cu for their use).
 template <typename T>
-__global__ void k_gather(const vec4_t<T>* staged, const uint32_t* perm, int64_t n, vec4_t<T>* sorted)
+__device__ __forceinline__ void exact_records(const vec4_t<T>& r, int64_t j, int kind, double shape, double gX,
+                                              vec4_t<T>* e0, vec4_t<T>* e1, vec4_t<T>* leaf0)
+{
+    vec4_t<T> a;
+    a.x = r.x; a.y = r.y; a.z = r.z;
+    double p = (double)r.w;
+    if (kind == LENS_POINT) {
+        a.w = (T)0;
+    } else if (kind == LENS_GAUSS) {
+        a.w = (T)(1.0 / (2.0 * p * p));
+    } else {
+        double Rm = shape * p;
+        a.w = (T)(Rm * Rm);
+        vec4_t<T> b;
+        b.x = (T)((double)r.z / gX);
+        b.y = (T)(1.0 / p);
+        b.z = (T)0;
+        b.w = (T)0;
+        e1[j] = b;
+    }
+    e0[j] = a;
+    if (leaf0) leaf0[j] = a;
+}
+
+// The particles in key order, the order kept for the caller (out_perm) and
+// their full-profile records.
+template <typename T>
+__global__ void k_gather(const vec4_t<T>* staged, const uint32_t* perm, int64_t n, vec4_t<T>* sorted,
+                         uint32_t* out_perm, int kind, double shape, double gX, vec4_t<T>* e0, vec4_t<T>* e1,
+                         vec4_t<T>* leaf0)
 {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) sorted[j] = staged[perm[j]];
+    if (j >= n) return;
+    const uint32_t pj = perm[j];
+    const vec4_t<T> r = staged[pj];
+    sorted[j] = r;
+    out_perm[j] = pj;
+    exact_records<T>(r, j, kind, shape, gX, e0, e1, leaf0);
 }
 
 // --------------------------------------------------------- 3. topology
@@ -482,34 +517,6 @@ __global__ void k_moments_up(uint32_t n_nodes, const uint8_t* node_level, const 
 
 // ------------------------------------------- 6. records and big lists
 
-// Full-profile records (see walk.cu for their use).
-template <typename T>
-__global__ void k_records(const vec4_t<T>* sorted, int64_t n, int kind, double shape, double gX,
-                          vec4_t<T>* e0, vec4_t<T>* e1, vec4_t<T>* leaf0)
-{
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    vec4_t<T> r = sorted[j], a;
-    a.x = r.x; a.y = r.y; a.z = r.z;
-    double p = (double)r.w;
-    if (kind == LENS_POINT) {
-        a.w = (T)0;
-    } else if (kind == LENS_GAUSS) {
-        a.w = (T)(1.0 / (2.0 * p * p));
-    } else {
-        double Rm = shape * p;
-        a.w = (T)(Rm * Rm);
-        vec4_t<T> b;
-        b.x = (T)((double)r.z / gX);
-        b.y = (T)(1.0 / p);
-        b.z = (T)0;
-        b.w = (T)0;
-        e1[j] = b;
-    }
-    e0[j] = a;
-    if (leaf0) leaf0[j] = a;
-}
-
 __device__ __forceinline__ double support_radius(int kind, double shape, double p)
 {
     return kind == LENS_POINT ? 0.0 : shape * p;
@@ -518,11 +525,17 @@ __device__ __forceinline__ double support_radius(int kind, double shape, double 
 // Listing box of every particle: the shallowest box on its path whose side
 // times lambda its support radius s exceeds (found by climbing the parent
 // links from its leaf), and the softening radius r0 of a listed particle.
+// Sort keys: the listing level (kUnlisted if none).  Boxes are numbered
+// level by level, in Morton order within a level, and the particles are in
+// Morton order, so the particles listed at one level are already in the
+// order of their listing boxes: a stable sort by level is the stable sort by
+// box (one 8-bit radix pass instead of a pass per 8 bits of box index).
+constexpr uint32_t kUnlisted = 31;
 template <typename T>
 __global__ void k_biglevel(const vec4_t<T>* sorted, int64_t n, const uint8_t* node_level, const uint32_t* leaf_of,
                            const int* parent, const float* rcm, const RootBox* rb, int kind, double shape,
                            double theta, double lambda, uint32_t n_nodes, uint32_t* bkey, uint32_t* bval,
-                           double* r0sq, uint32_t* n_big)
+                           uint32_t* bnode, double* r0sq, uint32_t* n_big)
 {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool listed = false;
@@ -548,12 +561,14 @@ __global__ void k_biglevel(const vec4_t<T>* sorted, int64_t n, const uint8_t* no
         }
         bval[j] = (uint32_t)j;
         if (lp < 0) {
-            bkey[j] = n_nodes;
+            bkey[j] = kUnlisted;
+            bnode[j] = n_nodes;
             r0sq[j] = 0.0;
         } else {
             uint32_t v = leaf;
             for (int l = L; l > lp; --l) v = (uint32_t)parent[v];
-            bkey[j] = v;
+            bkey[j] = (uint32_t)lp;
+            bnode[j] = v;
             // softening radius of the listed particle inside its leaf: any cell
             // whose multipole contains the particle and is accepted lies farther
             // than r_cm(leaf) (1/theta - 1) from the ray (r_cm grows towards the root)
@@ -568,6 +583,13 @@ __global__ void k_biglevel(const vec4_t<T>* sorted, int64_t n, const uint8_t* no
     }
     const unsigned ball = __ballot_sync(0xffffffffu, listed);
     if ((threadIdx.x & 31) == 0 && ball) atomicAdd(n_big, (uint32_t)__popc(ball));
+}
+
+// The listing box of each entry in sorted order.
+__global__ void k_bigkeys(const uint32_t* sval, const uint32_t* bnode, int64_t n, uint32_t* skey)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) skey[i] = bnode[sval[i]];
 }
 
 __global__ void k_bigcsr(const uint32_t* skey, int64_t n, uint32_t n_nodes, int4* link, uint32_t* end)
@@ -876,7 +898,32 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     uint64_t* K;
     uint32_t* P;
     radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, kKeyBits, tmp, s, &K, &P, t->d_err);
-    { k_gather<T><<<G, TB, 0, s>>>(staged, P, n, sorted); note_launch(); }
+    // the per-particle arrays the tree keeps (sized by n alone)
+    LENS_CUDA(lens_malloc_async((void**)&st.perm, n * sizeof(uint32_t), s));
+    LENS_CUDA(lens_malloc_async((void**)&st.exact0, n * sizeof(T4), s));
+    if (in.kind == LENS_NFW) LENS_CUDA(lens_malloc_async((void**)&st.exact1, n * sizeof(T4), s));
+    if (in.kind != LENS_POINT) {
+        LENS_CUDA(lens_malloc_async((void**)&st.leaf0, n * sizeof(T4), s));
+        LENS_CUDA(lens_malloc_async((void**)&st.listed, n, s));
+        LENS_CUDA(cudaMemsetAsync(st.listed, 0, n, s));
+    }
+    double gX = 1.0;
+    if (in.kind == LENS_NFW) {
+        // host evaluation of g(X) = ln(X/2) + F(X), X = R_max / r_s
+        double X = in.shape, F;
+        if (std::fabs(1.0 - X * X) < 1e-4) {
+            double u = 1.0 - X * X, sF = 0.0;
+            for (int k = 12; k >= 0; --k) sF = sF * u + 1.0 / (2 * k + 1);
+            F = sF;
+        } else if (X < 1.0) {
+            F = std::acosh(1.0 / X) / std::sqrt(1.0 - X * X);
+        } else {
+            F = std::acos(1.0 / X) / std::sqrt(X * X - 1.0);
+        }
+        gX = std::log(0.5 * X) + F;
+    }
+    { k_gather<T><<<G, TB, 0, s>>>(staged, P, n, sorted, st.perm, in.kind, in.shape, gX, (T4*)st.exact0,
+                                 (T4*)st.exact1, (T4*)st.leaf0); note_launch(); }
     LENS_CUDA(cudaEventRecord(st.ev[1], s));
 
     // topology
@@ -953,15 +1000,6 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     LENS_CUDA(lens_malloc_async((void**)&st.node_rcm, n_nodes * sizeof(float), s));
     LENS_CUDA(lens_malloc_async((void**)&st.node_level, n_nodes, s));
     LENS_CUDA(lens_malloc_async((void**)&st.parent, n_nodes * sizeof(int), s));
-    LENS_CUDA(lens_malloc_async((void**)&st.perm, n * sizeof(uint32_t), s));
-    LENS_CUDA(lens_malloc_async((void**)&st.exact0, n * sizeof(T4), s));
-    if (in.kind == LENS_NFW) LENS_CUDA(lens_malloc_async((void**)&st.exact1, n * sizeof(T4), s));
-    if (in.kind != LENS_POINT) {
-        LENS_CUDA(lens_malloc_async((void**)&st.leaf0, n * sizeof(T4), s));
-        LENS_CUDA(lens_malloc_async((void**)&st.listed, n, s));
-        LENS_CUDA(cudaMemsetAsync(st.listed, 0, n, s));
-    }
-    LENS_CUDA(cudaMemcpyAsync(st.perm, P, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
 
     uint32_t* first_bfs = nullptr;  // first particle of every node, BFS order
     uint32_t* leaf_of = nullptr;    // leaf (BFS) of every particle
@@ -988,34 +1026,13 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
                                       inv_theta2, mo, (T4*)st.nodeA, (T2*)st.nodeB, st.node_rcm, ready);
       note_launch(); }
 
-    // records
-    double gX = 1.0;
-    if (in.kind == LENS_NFW) {
-        double F, f, g;
-        // host evaluation of g(X) = ln(X/2) + F(X), X = R_max / r_s
-        double X = in.shape;
-        if (std::fabs(1.0 - X * X) < 1e-4) {
-            double u = 1.0 - X * X, sF = 0.0;
-            for (int k = 12; k >= 0; --k) sF = sF * u + 1.0 / (2 * k + 1);
-            F = sF;
-        } else if (X < 1.0) {
-            F = std::acosh(1.0 / X) / std::sqrt(1.0 - X * X);
-        } else {
-            F = std::acos(1.0 / X) / std::sqrt(X * X - 1.0);
-        }
-        g = std::log(0.5 * X) + F;
-        (void)f;
-        gX = g;
-    }
-    { k_records<T><<<G, TB, 0, s>>>(sorted, n, in.kind, in.shape, gX, (T4*)st.exact0, (T4*)st.exact1,
-                                  (T4*)st.leaf0); note_launch(); }
-
     if (in.kind != LENS_POINT) {
         double lambda = 0.5;
         if (t->theta > 0.0) lambda = std::min(0.5, std::max(0.0, (1.0 / t->theta - 1.0) / std::sqrt(2.0)));
         double* r0sq = nullptr;
-        uint32_t *bk0 = nullptr, *bk1 = nullptr, *bv0 = nullptr, *bv1 = nullptr, *end = nullptr;
+        uint32_t *bk0 = nullptr, *bk1 = nullptr, *bv0 = nullptr, *bv1 = nullptr, *end = nullptr, *bnode = nullptr;
         LENS_CUDA(tmps.get(&r0sq, n * sizeof(double)));
+        LENS_CUDA(tmps.get(&bnode, n * sizeof(uint32_t)));
         LENS_CUDA(tmps.get(&bk0, n * sizeof(uint32_t)));
         LENS_CUDA(tmps.get(&bk1, n * sizeof(uint32_t)));
         LENS_CUDA(tmps.get(&bv0, n * sizeof(uint32_t)));
@@ -1023,13 +1040,13 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
         LENS_CUDA(tmps.get(&end, n_nodes * sizeof(uint32_t)));
         LENS_CUDA(cudaMemsetAsync(end, 0, n_nodes * sizeof(uint32_t), s));
         { k_biglevel<T><<<G, TB, 0, s>>>(sorted, n, st.node_level, leaf_of, st.parent, st.node_rcm, rb, in.kind, in.shape,
-                                       t->theta, lambda, n_nodes, bk0, bv0, r0sq, counters + 1); note_launch(); }
-        int bits = 1;
-        while (bits < 32 && ((1ull << bits) <= (uint64_t)n_nodes)) ++bits;
-        bits = (bits + 7) & ~7;
+                                       t->theta, lambda, n_nodes, bk0, bv0, bnode, r0sq, counters + 1);
+          note_launch(); }
         uint32_t *skey, *sval;
-        radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, n, 0, bits, tmp, s, &skey, &sval, t->d_err);
-        { k_bigcsr<<<G, TB, 0, s>>>(skey, n, n_nodes, st.link, end); note_launch(); }
+        radix_sort_pairs<uint32_t>(bk0, bv0, bk1, bv1, n, 0, 8, tmp, s, &skey, &sval, t->d_err);
+        uint32_t* nkey = skey == bk0 ? bk1 : bk0;
+        { k_bigkeys<<<G, TB, 0, s>>>(sval, bnode, n, nkey); note_launch(); }
+        { k_bigcsr<<<G, TB, 0, s>>>(nkey, n, n_nodes, st.link, end); note_launch(); }
         { k_bigcount<<<GN, TB, 0, s>>>(n_nodes, st.link, end); note_launch(); }
         // the big arrays hold up to one entry per particle (the count is read
         // on the device), so the build does not wait for it

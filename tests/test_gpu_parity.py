@@ -205,6 +205,13 @@ def test_tree_128_ray_groups(case):
     if case == "gauss":
         amb = edge_mask(comps, rx, ry)
         assert ek[~amb].max() <= 1e-5, ek[~amb].max()
+        # alpha only (the big entries of each half of a group, packed general
+        # form where a ray may be inside a softening radius)
+        ao = to_np(lens.shoot(cu(dx), cu(dy), origin=origin, flags=L.ALPHA_ONLY)[:2])
+        lens.sync()
+        ea_ao = rel_errors(np.concatenate([ao[:, :2], ref[:, 2:]], axis=1), ref)[0]
+        assert np.median(ea_ao) <= 1e-3, np.median(ea_ao)
+        assert np.max(np.abs(ao[:, :2] - got[:, :2])) <= 1e-5 * np.max(np.abs(got[:, :2]))
     l64 = L.Lens(species, halos, theta=0.3, group_rays=64, walk="warp")
     for a, b in zip(lens.shoot(cu(dx), cu(dy), origin=origin, flags=L.DIRECT),
                     l64.shoot(cu(dx), cu(dy), origin=origin, flags=L.DIRECT)):
