@@ -380,17 +380,34 @@ struct MomentsOut {
     float2* q2f;
 };
 
-template <typename T, typename A>
+// GEO: also r_cm and r_cut^2 here (the FP64 tree); the FP32 tree's boxes get
+// them from k_rcut, one thread per box, so that the FP64 arithmetic they
+// need runs in full warps rather than in the climb's divergent ones, and an
+// FP32 box's reference point is formed in FP32 (side0f = 2 half, x0f, y0f:
+// the root box in FP32).
+template <typename T, typename A, bool GEO>
 __device__ __forceinline__ void node_moments(uint32_t b, int l, uint32_t ix, uint32_t iy, const int4 L,
                                              const vec4_t<T>* sorted, const RootBox* rb, double inv_theta2,
                                              const MomentsOut& O, vec4_t<T>* nodeA,
-                                             typename V2<T>::type* nodeB, float* rcm_out)
+                                             typename V2<T>::type* nodeB, float* rcm_out, float side0f,
+                                             float x0f, float y0f)
 {
-    // box (ix, iy) of level l
+    // box (ix, iy) of level l; the moments are taken about its centre (any
+    // point of the box would do: in FP32 boxes the centre rounded in FP32)
     // 2^-l built from its exponent: exact, and no FP64 division (slow here)
-    const double side = (2.0 * rb->half) * __longlong_as_double((long long)(1023 - l) << 52);
-    const double cxd = rb->x0 + (ix + 0.5) * side, cyd = rb->y0 + (iy + 0.5) * side;
-    const A cx = (A)cxd, cy = (A)cyd;   // the moments are taken about this point
+    double side = 0.0, cxd = 0.0, cyd = 0.0;
+    A cx, cy;
+    if (GEO || sizeof(A) == 8) {
+        side = (2.0 * rb->half) * __longlong_as_double((long long)(1023 - l) << 52);
+        cxd = rb->x0 + (ix + 0.5) * side;
+        cyd = rb->y0 + (iy + 0.5) * side;
+        cx = (A)cxd;
+        cy = (A)cyd;
+    } else {
+        const float sf = side0f * __int_as_float((127 - l) << 23);
+        cx = (A)fmaf((float)ix + 0.5f, sf, x0f);
+        cy = (A)fmaf((float)iy + 0.5f, sf, y0f);
+    }
     A M = 0, sx = 0, sy = 0, qr = 0, qi = 0;
     if (L.y & kLeafBit) {
         const int cnt = L.y & kCountMask;
@@ -459,15 +476,39 @@ __device__ __forceinline__ void node_moments(uint32_t b, int l, uint32_t ix, uin
         O.mom[b] = make_dbl4((double)M, (double)cmx, (double)cmy, side);
         O.q2[b] = make_double2((double)qr, (double)qi);
     }
-    // r_cm: distance from the centre of mass to the farthest corner of the box
-    const double ex = fabs((double)cmx - cxd) + 0.5 * side, ey = fabs((double)cmy - cyd) + 0.5 * side;
-    const double rcm2 = ex * ex + ey * ey;
     vec4_t<T> Av;
-    Av.x = (T)cmx; Av.y = (T)cmy; Av.z = (T)M; Av.w = round_up<T>(rcm2 * inv_theta2);
+    Av.x = (T)cmx; Av.y = (T)cmy; Av.z = (T)M; Av.w = (T)0;
+    if constexpr (GEO) {
+        // r_cm: distance from the centre of mass to the farthest corner of the box
+        const double ex = fabs((double)cmx - cxd) + 0.5 * side, ey = fabs((double)cmy - cyd) + 0.5 * side;
+        const double rcm2 = ex * ex + ey * ey;
+        Av.w = round_up<T>(rcm2 * inv_theta2);
+        rcm_out[b] = __fsqrt_rd(__double2float_rd(rcm2));
+    }
     nodeA[b] = Av;
     typename V2<T>::type B;
     B.x = (T)qr; B.y = (T)qi;
     nodeB[b] = B;
+}
+
+// r_cm and r_cut^2 of every box of the FP32 tree from its stored centre of
+// mass (the one the walk uses), in FP64 about the exact box centre: r_cm
+// rounded down, r_cut^2 = r_cm^2 / theta^2 rounded up.
+__global__ void k_rcut(uint32_t n_nodes, const uint8_t* node_level, const uint32_t* first_bfs, const uint64_t* K,
+                       const RootBox* rb, double inv_theta2, float4* nodeA, float* rcm_out)
+{
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_nodes) return;
+    const int l = node_level[b];
+    const uint64_t key = K[first_bfs[b]];
+    const uint32_t ix = compact24(key) >> (kMaxDepth - l), iy = compact24(key >> 1) >> (kMaxDepth - l);
+    const double side = (2.0 * rb->half) * __longlong_as_double((long long)(1023 - l) << 52);
+    const double cxd = rb->x0 + (ix + 0.5) * side, cyd = rb->y0 + (iy + 0.5) * side;
+    float4 A = nodeA[b];
+    const double ex = fabs((double)A.x - cxd) + 0.5 * side, ey = fabs((double)A.y - cyd) + 0.5 * side;
+    const double rcm2 = ex * ex + ey * ey;
+    A.w = __double2float_ru(rcm2 * inv_theta2);
+    nodeA[b] = A;
     rcm_out[b] = __fsqrt_rd(__double2float_rd(rcm2));
 }
 
@@ -487,6 +528,9 @@ __global__ void k_moments_up(uint32_t n_nodes, const uint8_t* node_level, const 
     int4 L = link[b];
     if (!(L.y & kLeafBit)) return;
     int l = node_level[b];
+    constexpr bool GEO = sizeof(T) == 8;
+    const float side0f = GEO ? 0.f : (float)(2.0 * rb->half);
+    const float x0f = GEO ? 0.f : (float)rb->x0, y0f = GEO ? 0.f : (float)rb->y0;
     const uint64_t key = K[first_bfs[b]];
     // the climb derives each parent's cell from its child's: no further
     // loads of keys or levels on the way up
@@ -494,9 +538,11 @@ __global__ void k_moments_up(uint32_t n_nodes, const uint8_t* node_level, const 
     int p = parent[b];
     for (;;) {
         if (sizeof(T) == 4 && l >= kFp64Levels)
-            node_moments<T, float>(b, l, ix, iy, L, sorted, rb, inv_theta2, O, nodeA, nodeB, rcm_out);
+            node_moments<T, float, GEO>(b, l, ix, iy, L, sorted, rb, inv_theta2, O, nodeA, nodeB, rcm_out, side0f,
+                                        x0f, y0f);
         else
-            node_moments<T, double>(b, l, ix, iy, L, sorted, rb, inv_theta2, O, nodeA, nodeB, rcm_out);
+            node_moments<T, double, GEO>(b, l, ix, iy, L, sorted, rb, inv_theta2, O, nodeA, nodeB, rcm_out, side0f,
+                                         x0f, y0f);
         if (p < 0) return;
         // the parent's links (written by earlier launches) are read beside
         // the count.  The count is an acquire-release atomic: it publishes this
@@ -1025,6 +1071,9 @@ static lens_status build_typed(lens_tree* t, SpeciesTree& st, const lens_species
     { k_moments_up<T><<<GN, TB, 0, s>>>(n_nodes, st.node_level, first_bfs, st.link, st.parent, sorted, K, rb,
                                       inv_theta2, mo, (T4*)st.nodeA, (T2*)st.nodeB, st.node_rcm, ready);
       note_launch(); }
+    if (sizeof(T) == 4)
+        { k_rcut<<<GN, TB, 0, s>>>(n_nodes, st.node_level, first_bfs, K, rb, inv_theta2, (float4*)st.nodeA,
+                                   st.node_rcm); note_launch(); }
 
     if (in.kind != LENS_POINT) {
         double lambda = 0.5;
