@@ -705,11 +705,11 @@ class Fit(Workload):
 
     def step(self, flags):
         L = self.L
-        side = side_stream(self)
+        # (one stream: the grouping beside this small build saves less than
+        # the cross-stream hand-overs cost)
         lens = L.Lens([L.Species.gauss(self.parts, self.w["q"])], theta=self.theta, group_rays=self.group,
                       walk=self.walk, tile=self.tile)
-        lens.shoot(self.rx, self.ry, flags=flags | L.ALPHA_ONLY | L.KEEP_LISTS, out=self.outs, stream=side)
-        join(side)
+        lens.shoot(self.rx, self.ry, flags=flags | L.ALPHA_ONLY | L.KEEP_LISTS, out=self.outs)
         g1 = 2 * (self.outs[0] - self.at[0])
         g2 = 2 * (self.outs[1] - self.at[1])
         self.grad.zero_()

@@ -178,8 +178,8 @@ void lens_free_tree(lens_tree* t)
     if (t->d_err) cudaFree(t->d_err);
     if (t->ray_scratch.ptr) cudaFreeAsync(t->ray_scratch.ptr, 0);
     if (t->d_stats) cudaFree(t->d_stats);
-    if (t->list_ids) cudaFree(t->list_ids);
-    if (t->list_n) cudaFree(t->list_n);
+    if (t->list_ids) cudaFreeAsync(t->list_ids, 0);
+    if (t->list_n) cudaFreeAsync(t->list_n, 0);
     if (t->amr_ws && t->amr_free) t->amr_free(t->amr_ws);
     for (int i = 0; i < 4; ++i)
         if (t->ev[i]) cudaEventDestroy(t->ev[i]);

@@ -21,6 +21,8 @@
 //      are grouped per box by a stable sort (deterministic order).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "profiles.cuh"
 #include "sort.cuh"
@@ -878,12 +880,31 @@ lens_status wait_built(const lens_tree* t, cudaStream_t s)
     return LENS_OK;
 }
 
+// A non-blocking stream of the current device for the host's reads of a
+// finished build's counts: a copy on the legacy default stream would also
+// wait for whatever was queued after the build there (a walk, an adjoint).
+static lens_status meta_stream(cudaStream_t* out)
+{
+    static std::mutex mu;
+    static std::vector<cudaStream_t> streams;
+    int dev = 0;
+    LENS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)streams.size() <= dev) streams.resize(dev + 1, nullptr);
+    if (!streams[dev]) LENS_CUDA(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+    *out = streams[dev];
+    return LENS_OK;
+}
+
 lens_status finish_species(SpeciesTree& st)
 {
     if (st.meta_ready || st.n == 0) return LENS_OK;
-    LENS_CUDA(cudaEventSynchronize(st.ev[4]));
+    LENS_CUDA(cudaEventSynchronize(st.ev[4]));  // the build (and its count copies) are done
     BuildMeta m;
-    LENS_CUDA(cudaMemcpy(&m, st.d_meta, sizeof(m), cudaMemcpyDeviceToHost));
+    cudaStream_t ms;
+    LENS_TRY(meta_stream(&ms));
+    LENS_CUDA(cudaMemcpyAsync(&m, st.d_meta, sizeof(m), cudaMemcpyDeviceToHost, ms));
+    LENS_CUDA(cudaStreamSynchronize(ms));
     int depth = (int)m.level_start[kMaxDepth + 1];
     if (depth < 0 || depth > kMaxDepth) return lens_set_error(LENS_ERR_INTERNAL, "tree build: bad depth %d", depth);
     st.depth = depth;

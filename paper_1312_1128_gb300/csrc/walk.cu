@@ -876,17 +876,21 @@ static lens_status reserve_lists(lens_tree* t, int64_t ng, int R, cudaStream_t s
     const int K = 512 * R;
     t->list_rays = -1;  // whatever is kept belongs to no rays until the walk records
     if (t->list_ids && t->list_groups >= ng && t->list_K == K) return LENS_OK;
-    LENS_CUDA(cudaStreamSynchronize(s));  // the old lists may still be read
-    if (t->list_ids) cudaFree(t->list_ids);
-    if (t->list_n) cudaFree(t->list_n);
+    if (t->list_ids || t->list_n) {
+        LENS_CUDA(cudaStreamSynchronize(s));  // the old lists may still be read
+        if (t->list_ids) cudaFreeAsync(t->list_ids, s);
+        if (t->list_n) cudaFreeAsync(t->list_n, s);
+    }
     t->list_ids = t->list_n = nullptr;
     t->list_groups = 0;
-    LENS_CUDA(lens_malloc((void**)&t->list_ids, (size_t)ng * K * sizeof(uint32_t)));
-    cudaError_t e = lens_malloc((void**)&t->list_n, (size_t)ng * sizeof(uint32_t));
+    // from the stream-ordered pool: a new tree's first kept lists cost no
+    // device allocation call
+    LENS_CUDA(lens_malloc_async((void**)&t->list_ids, (size_t)ng * K * sizeof(uint32_t), s));
+    cudaError_t e = lens_malloc_async((void**)&t->list_n, (size_t)ng * sizeof(uint32_t), s);
     if (e != cudaSuccess) {
-        cudaFree(t->list_ids);
+        cudaFreeAsync(t->list_ids, s);
         t->list_ids = nullptr;
-        return lens_cuda_check(e, "cudaMalloc(lists)");
+        return lens_cuda_check(e, "cudaMallocAsync(lists)");
     }
     t->list_groups = ng;
     t->list_K = K;
