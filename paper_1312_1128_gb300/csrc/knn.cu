@@ -13,6 +13,7 @@
 // are scanned.  32 consecutive particles share one warp and one descent
 // (the union of what their queries need); each lane keeps its own k
 // smallest squared distances; the search is exact.
+#include <type_traits>
 #include <cmath>
 
 #include "common.cuh"
@@ -118,7 +119,7 @@ template <int K> struct KSmallest {
     float v[K];
     int k, cnt, iw;
     float worst;
-    LENS_DEV void reset(int kk, float bound)
+    LENS_DEV void reset(float*, int kk, float bound)
     {
         k = kk;
         cnt = 0;
@@ -158,6 +159,77 @@ template <int K> struct KSmallest {
     }
 };
 
+// The same in shared memory, for K <= 32: slot q of a lane at v[32 q] (the
+// lanes' slots interleaved: no bank conflicts), in groups of 8 slots whose
+// largest value and its slot stay in registers, so that a replacement
+// rescans one group (8 loads) instead of selecting through all K register
+// slots twice (the insertion held the query's ALU pipe).
+template <int K> struct KSmallestSh {
+    static constexpr int kS = 8, kG = K / kS;
+    static_assert(K % kS == 0, "groups of 8 slots");
+    float* v;
+    float gmax[kG];
+    int gidx[kG];
+    int k, cnt, iw;
+    float worst;
+    LENS_DEV void reset(float* base, int kk, float bound)
+    {
+        v = base;
+        k = kk;
+        cnt = 0;
+        iw = 0;
+        worst = bound;  // values above the bound are not kept
+#pragma unroll
+        for (int q = 0; q < K; ++q) v[32 * q] = -INFINITY;
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            gmax[g] = -INFINITY;
+            gidx[g] = g * kS;
+        }
+    }
+    // rescan group g, then take the largest of the groups' largest values
+    LENS_DEV void group(int g)
+    {
+        float m = -INFINITY;
+        int mi = g * kS;
+#pragma unroll
+        for (int t = 0; t < kS; ++t) {
+            const int q = g * kS + t;
+            const float x = v[32 * q];
+            if (x > m) {
+                m = x;
+                mi = q;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < kG; ++h)
+            if (h == g) {
+                gmax[h] = m;
+                gidx[h] = mi;
+            }
+        worst = gmax[0];
+        iw = gidx[0];
+#pragma unroll
+        for (int h = 1; h < kG; ++h)
+            if (gmax[h] > worst) {
+                worst = gmax[h];
+                iw = gidx[h];
+            }
+    }
+    LENS_DEV void offer(float d2)
+    {
+        if (cnt < k) {
+            if (d2 > worst) return;
+            v[32 * cnt] = d2;
+            if (++cnt == k)
+                for (int g = 0; g < kG; ++g) group(g);  // slots at or beyond k hold -inf
+        } else if (d2 < worst) {
+            v[32 * iw] = d2;
+            group(iw / kS);
+        }
+    }
+};
+
 LENS_DEV uint32_t lower_bound_u64(const uint64_t* a, uint32_t lo, uint32_t hi, uint64_t key)
 {
     while (lo < hi) {
@@ -191,17 +263,20 @@ __global__ void __launch_bounds__(kKnnWarps * 32)
 k_knn_query(const float4* sp4, const uint64_t* keys, int64_t n, int k, KnnCube c, float* r_out, uint32_t* err)
 {
     __shared__ KnnNode stacks[kKnnWarps][kKnnStack];
+    constexpr bool kShared = K <= 32;
+    __shared__ float kvals[kKnnWarps][kShared ? K : 1][32];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     KnnNode* stack = stacks[warp];
+    float* kbase = &kvals[warp][0][lane];
     const int64_t i0 = ((int64_t)blockIdx.x * kKnnWarps + warp) * 32;
     if (i0 >= n) return;
     const int64_t i = i0 + lane;
     const bool valid = i < n;
     const float4 p = valid ? sp4[i] : sp4[i0];
-    KSmallest<K> S;
+    typename std::conditional<kShared, KSmallestSh<K>, KSmallest<K>>::type S;
     // upper bound: the k nearest among the 2k neighbours in key order
-    S.reset(k, INFINITY);
+    S.reset(kbase, k, INFINITY);
     if (valid) {
         const int64_t w0 = i - k > 0 ? i - k : 0, w1 = i + k + 1 < n ? i + k + 1 : n;
         for (int64_t j = w0; j < w1; ++j) {
@@ -214,7 +289,7 @@ k_knn_query(const float4* sp4, const uint64_t* keys, int64_t n, int k, KnnCube c
     // descend with the bound as the initial search radius (inflated for the
     // rounding of the squared distances); an invalid lane needs nothing
     const float R2 = valid ? S.worst * 1.000002f : -1.0f;
-    S.reset(k, R2);
+    S.reset(kbase, k, R2);
     const float qlen = 1.0f / c.inv_q;  // length of one quantum
     int sp = 0;
     if (lane == 0) stack[0] = KnnNode{0ull, 0u, (uint32_t)n, 0};
