@@ -169,12 +169,25 @@ class ClockSampler:
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+        # wait (5 s at most) for the first sample: nvidia-smi's start-up,
+        # which loads the management library and queries the driver, would
+        # otherwise land in the timed region and delay the host side of
+        # short steps
+        self.first = []
+        if self.p is not None:
+            import select
+            ready, _, _ = select.select([self.p.stdout], [], [], 5.0)
+            if ready:
+                line = self.p.stdout.readline()
+                if line:
+                    self.first.append(line)
 
     def stop(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
         out, _ = self.p.communicate(timeout=10)
+        out = "".join(self.first) + out
         rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
