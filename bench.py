@@ -8,10 +8,12 @@ a 2048 x 2048 cell-centred grid over [-1, 1]^2; FP32 tree at theta = 0.3.
 
 One step = the whole hot path for one lens: tree build (stage, Morton sort,
 topology, moments, big lists) + ray grouping + tree walk for every ray,
-producing alpha1, alpha2, kappa, gamma1, gamma2.  `value` is rays per second
-over the whole job with inputs resident in HBM; `e2e` is the same through
-the public API with host buffers (pinned H2D of particles and rays, D2H of
-the five outputs inside the timed region).
+producing alpha1, alpha2, kappa, gamma1, gamma2; the shoot is issued on a
+second stream, so the ray grouping runs beside the end of the build and the
+walk waits for the build on the device.  `value` is rays per second over the
+whole job with inputs resident in HBM; `e2e` is the same through the public
+API with host buffers (pinned H2D of particles and rays, D2H of the five
+outputs inside the timed region).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
