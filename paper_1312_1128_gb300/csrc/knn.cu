@@ -13,7 +13,6 @@
 // are scanned.  32 consecutive particles share one warp and one descent
 // (the union of what their queries need); each lane keeps its own k
 // smallest squared distances; the search is exact.
-#include <type_traits>
 #include <cmath>
 
 #include "common.cuh"
@@ -112,58 +111,12 @@ __global__ void k_knn_gather(const float* xyz, int64_t n, const uint32_t* idx, f
     sp[i] = make_float4(xyz[3 * (int64_t)j], xyz[3 * (int64_t)j + 1], xyz[3 * (int64_t)j + 2], __uint_as_float(j));
 }
 
-// The k smallest values seen (k <= K), unordered, with the largest tracked;
-// K fixed at compile time and every index a compile-time constant (selects),
-// so the values stay in registers.
-template <int K> struct KSmallest {
-    float v[K];
-    int k, cnt, iw;
-    float worst;
-    LENS_DEV void reset(float*, int kk, float bound)
-    {
-        k = kk;
-        cnt = 0;
-        iw = 0;
-        worst = bound;  // values above the bound are not kept
-#pragma unroll
-        for (int q = 0; q < K; ++q) v[q] = -INFINITY;
-    }
-    LENS_DEV void put(int at, float d2)
-    {
-#pragma unroll
-        for (int q = 0; q < K; ++q)
-            if (q == at) v[q] = d2;
-    }
-    LENS_DEV void offer(float d2)
-    {
-        if (cnt < k) {
-            if (d2 > worst) return;
-            put(cnt++, d2);
-            if (cnt == k) rescan();
-        } else if (d2 < worst) {
-            put(iw, d2);
-            rescan();
-        }
-    }
-    // slots at or beyond k hold -inf and are never the largest
-    LENS_DEV void rescan()
-    {
-        iw = 0;
-        worst = v[0];
-#pragma unroll
-        for (int q = 1; q < K; ++q)
-            if (v[q] > worst) {
-                worst = v[q];
-                iw = q;
-            }
-    }
-};
-
-// The same in shared memory, for K <= 32: slot q of a lane at v[32 q] (the
-// lanes' slots interleaved: no bank conflicts), in groups of 8 slots whose
-// largest value and its slot stay in registers, so that a replacement
-// rescans one group (8 loads) instead of selecting through all K register
-// slots twice (the insertion held the query's ALU pipe).
+// The k smallest values seen (k <= K), unordered, in shared memory: slot q
+// of a lane at v[32 q] (the lanes' slots interleaved: no bank conflicts), in
+// groups of 8 slots whose largest value and its slot stay in registers, so
+// that a replacement writes one slot and rescans one group (8 loads).  (K
+// register slots cannot be indexed at run time: every replacement would
+// select through all of them twice, which held the query's ALU pipe.)
 template <int K> struct KSmallestSh {
     static constexpr int kS = 8, kG = K / kS;
     static_assert(K % kS == 0, "groups of 8 slots");
@@ -247,7 +200,11 @@ struct KnnNode {
     int level;
 };
 
-constexpr int kKnnWarps = 4;   // warps per block of the query
+constexpr int kKnnWarps = 4;   // warps per block of the query (k <= 32)
+// warps per block of the query with capacity K: the k smallest distances of
+// 64 slots take twice the shared memory, so two warps a block keep a block's
+// static shared memory under 48 KB
+template <int K> constexpr int knn_warps() { return K <= 32 ? kKnnWarps : 2; }
 
 // One warp per 32 consecutive particles of the key order (spatially close
 // queries, one per lane), sharing one descent of the octree: a child cell is
@@ -259,22 +216,22 @@ constexpr int kKnnWarps = 4;   // warps per block of the query
 // the warp's, in shared memory.  Exact: a lane never prunes a cell that
 // could hold one of its k nearest.
 template <int K>
-__global__ void __launch_bounds__(kKnnWarps * 32)
+__global__ void __launch_bounds__(knn_warps<K>() * 32)
 k_knn_query(const float4* sp4, const uint64_t* keys, int64_t n, int k, KnnCube c, float* r_out, uint32_t* err)
 {
-    __shared__ KnnNode stacks[kKnnWarps][kKnnStack];
-    constexpr bool kShared = K <= 32;
-    __shared__ float kvals[kKnnWarps][kShared ? K : 1][32];
+    constexpr int KW = knn_warps<K>();
+    __shared__ KnnNode stacks[KW][kKnnStack];
+    __shared__ float kvals[KW][K][32];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     KnnNode* stack = stacks[warp];
     float* kbase = &kvals[warp][0][lane];
-    const int64_t i0 = ((int64_t)blockIdx.x * kKnnWarps + warp) * 32;
+    const int64_t i0 = ((int64_t)blockIdx.x * KW + warp) * 32;
     if (i0 >= n) return;
     const int64_t i = i0 + lane;
     const bool valid = i < n;
     const float4 p = valid ? sp4[i] : sp4[i0];
-    typename std::conditional<kShared, KSmallestSh<K>, KSmallest<K>>::type S;
+    KSmallestSh<K> S;
     // upper bound: the k nearest among the 2k neighbours in key order
     S.reset(kbase, k, INFINITY);
     if (valid) {
@@ -427,9 +384,15 @@ extern "C" lens_status lens_smoothing_lengths(const float* xyz, int64_t n, int32
         radix_sort_pairs<uint64_t>(k0, v0, k1, v1, n, 0, 3 * kKnnBits, base + o_tmp, s, &sk, &sv, err);
         k_knn_gather<<<(unsigned)G, TB, 0, s>>>(xyz, n, sv, sp);
         note_launch();
-        const unsigned qb = (unsigned)((n + 32 * kKnnWarps - 1) / (32 * kKnnWarps));
-        if (k <= 32) k_knn_query<32><<<qb, kKnnWarps * 32, 0, s>>>(sp, sk, n, k, c, r_sm, err);
-        else k_knn_query<kKnnMax><<<qb, kKnnWarps * 32, 0, s>>>(sp, sk, n, k, c, r_sm, err);
+        if (k <= 32) {
+            constexpr int W = knn_warps<32>();
+            const unsigned qb = (unsigned)((n + 32 * W - 1) / (32 * W));
+            k_knn_query<32><<<qb, W * 32, 0, s>>>(sp, sk, n, k, c, r_sm, err);
+        } else {
+            constexpr int W = knn_warps<kKnnMax>();
+            const unsigned qb = (unsigned)((n + 32 * W - 1) / (32 * W));
+            k_knn_query<kKnnMax><<<qb, W * 32, 0, s>>>(sp, sk, n, k, c, r_sm, err);
+        }
         note_launch();
         e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
